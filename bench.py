@@ -1,0 +1,310 @@
+#!/usr/bin/env python3
+"""Benchmark: cumulant lag-terms/s of the long bispectrum workload on GB300.
+
+Workload (one step): the smoothed sample bispectrum of one AR(2) series of
+n = 2^21 samples (centred Exp(1) innovations), Parzen lag window L = 256,
+512 x 512 grid: FP64 mean removal, c3 contraction on the tensor cores,
+FP64 reduction + window, 2-D transform.  Metric unit: n (2L+1)^2 lag terms.
+
+  python bench.py [--gpus N --steps K --warmup W --precision bf16|fp32|simt]
+  python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
+
+Multi-GPU (torchrun, N > 1): every rank runs its own independent series
+(weak scaling, no collective); rank 0 prints the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "long_bispectrum_n2M_L256"
+METRIC = "cumulant lag-terms/s (n*(2L+1)^(k-1)) and % tensor peak, split-BF16 vs FP32, same GPU"
+UNIT = "lag-terms/s"
+
+
+def units_of(n, L, k=3):
+    return n * (2 * L + 1) ** (k - 1)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(x, L, n, seconds_target=10.0):
+    """The FP64 oracle as it stands, on this host's cores, over a bounded
+    sample of the same workload: whole rows w1 of the lag square (every w2,
+    every sample), extrapolated per lag term."""
+    import oracle
+    y = oracle.demean(x)
+    rows = 2
+    t0 = time.perf_counter()
+    oracle.c3_rows(y, L, 0, rows - 1)
+    dt = time.perf_counter() - t0
+    rows = max(2, min(2 * L + 1, int(rows * seconds_target / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.c3_rows(y, L, -(rows // 2), -(rows // 2) + rows - 1)
+    dt = time.perf_counter() - t0
+    terms = rows * (2 * L + 1) * n
+    return {"value": terms / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"c3 rows w1 in [{-(rows // 2)}, {-(rows // 2) + rows - 1}] x all {2 * L + 1} w2 x n={n} "
+                      f"({terms:.3e} lag terms, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    import hos_synth
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    oracle.build()
+    w = hos_synth.workload(WORKLOAD)
+    x, L = w["x"], w["L"]
+    n = x.size
+    y = oracle.demean(x)
+    rows = 8
+    times = []
+    for step in range(args.warmup + args.steps):
+        r0 = -L + (step * rows) % (2 * L + 1 - rows)
+        t0 = time.perf_counter()
+        oracle.c3_rows(y, L, r0, r0 + rows - 1)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    terms = rows * (2 * L + 1) * n
+    value = terms / statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "L": L, "grid": w["N"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"each step: c3 of {rows} rows w1 x all {2 * L + 1} w2 x n={n}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import hos_synth
+    import paper_1805_11775_gb300 as hos
+    from paper_1805_11775_gb300 import _native
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = hos_synth.workload(WORKLOAD)
+    x_host = w["x"] if rank == 0 else hos_synth.ar2(w["x"].size, 1002 + 100 * rank)
+    L, N = w["L"], w["N"]
+    n = x_host.size
+    prec = args.precision
+    xd = torch.from_numpy(x_host).cuda()
+    out = torch.empty((N, N), dtype=torch.complex64, device="cuda")
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+    ws = hos.Workspace()
+
+    def step():
+        hos.bispectrum(xd, L, precision=prec, out=out, workspace=ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    hos.set_profiling(True)
+    clocks = Clocks(local)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    contract_ms, stage_acc = [], {}
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = hos.launch_count()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush_buf.zero_()  # evict the previous step's data from L2 (outside the events)
+        ev0[i].record()
+        step()
+        ev1[i].record()
+        torch.cuda.synchronize()
+        for name, ms in hos.stage_times():
+            stage_acc.setdefault(name, []).append(ms)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    launches = hos.launch_count() - launches0
+    clk = clocks.stop()
+    hos.set_profiling(False)
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    ms = statistics.mean(step_ms)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    contract_ms = statistics.mean(stage_acc.get("contract", [float("nan")]))
+
+    # executed tensor-core work of the contraction: computed tiles x 128 rows x
+    # tile_n columns x padded samples x 3 products x 2 flops
+    tile_n = min(256, max(32, 1 << (2 * L - 1).bit_length()))
+    tiles_m, tiles_n = math.ceil(2 * L / 128), math.ceil(2 * L / tile_n)
+    ntiles = sum(1 for b in range(tiles_n) for a in range(tiles_m) if not (a * 128 >= b * tile_n + tile_n))
+    kpad = math.ceil(n / 1024) * 1024
+    products = 3 if prec in ("bf16", "fp32") else 1
+    flops = ntiles * 128 * tile_n * kpad * products * 2
+    pk, src = peaks()
+    if prec == "bf16":
+        peak = pk["bf16_tflops"]
+        peak_note = f"bf16 dense, {src} burst"
+    elif prec == "fp32":
+        peak = pk["bf16_tflops"] * (1.1 / 2.25)
+        peak_note = f"tf32 dense = {src} bf16 burst x 1.1/2.25 (nominal ratio)"
+    else:
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        peak_note = "FP32 FFMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
+    achieved = flops / (contract_ms * 1e-3) / 1e12
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", f"c3_tc_{prec}_traffic.json")
+    if os.path.exists(tr_path):
+        with open(tr_path) as f:
+            traffic = json.load(f).get("bytes_per_launch")
+
+    # end to end through the public API with host buffers
+    x_pin = torch.from_numpy(x_host).pin_memory()
+    e2e_t = []
+    for i in range(max(3, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B = hos.bispectrum(x_pin, L, precision=prec, workspace=ws)  # H2D, compute, D2H inside
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e_t)
+
+    units = units_of(n, L) * world
+    line = {
+        "metric": METRIC,
+        "value": units / (ms * 1e-3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"bf16": "bf16x3 (split-bf16, fp32 accumulate, fp64 reduce)",
+                  "fp32": "tf32x3 (fp32-class, fp32 accumulate, fp64 reduce)", "simt": "f32"}[prec],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "L": L, "grid": N, "precision": prec,
+                   "contraction": hos.last_contraction(), "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "stage_ms": {k: statistics.mean(v) for k, v in stage_acc.items()},
+        "roofline": {"bound": "tensor" if prec != "simt" else "alu", "kernel": hos.last_contraction(),
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_source": peak_note,
+                     "work": f"{ntiles} tiles x 128 x {tile_n} x {kpad} samples x {products} products x 2 flops"},
+        "e2e": {"value": units_of(n, L) / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(x_host.nbytes),
+                "d2h_bytes_per_step": int(N * N * 8)},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "wall_s_timed": t_wall,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(x_host, L, n)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "simt"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

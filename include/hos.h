@@ -1,0 +1,193 @@
+/*
+ * hos.h -- C ABI of the GB300 higher-order-spectra library.
+ *
+ * The library estimates the smoothed sample bispectrum and trispectrum of a
+ * real series X(1..n) (paper: Problem Statement, "compute smoothed sample
+ * bispectrum and trispectrum") by the indirect method the paper names in
+ * "Direct Method for HOS" (the Fourier transform of the third cumulant):
+ *
+ *   1. per-part mean removal in FP64          (Algorithm DBS steps 1-2);
+ *   2. sample cumulant c3 over the lag square, or c4 over the lag cube
+ *      (Problem Statement: moments m_k, cumulants, time averages);
+ *   3. lag window, and average over parts      (Algorithm DBS step 6);
+ *   4. 2-D / 3-D DFT onto the frequency grid   (Problem Statement; sign of
+ *      Algorithm DBS step 3).
+ *
+ * Definitions (the paper is silent on these; the library's readings):
+ *   c3(w1,w2)    = (1/n) sum_i y(i) y(i+w1) y(i+w2), samples outside the
+ *                  series are zero (biased estimator);
+ *   c4(w1,w2,w3) = m4(w1,w2,w3) - c2(w1)c2(w3-w2) - c2(w2)c2(w3-w1)
+ *                  - c2(w3)c2(w2-w1), with m4, c2 the same time averages;
+ *   Parzen d(u), u = |w|/L: 1-6u^2+6u^3 (u<=1/2), 2(1-u)^3 (u<=1), 0 beyond;
+ *   B(k1,k2)     = (2 pi)^-2 sum_w W(w) c3(w) exp(-i 2 pi (k1 w1 + k2 w2)/N),
+ *   T(k1,k2,k3)  = (2 pi)^-3 sum_w W(w) c4(w) exp(-i 2 pi k.w / N),
+ *                  k = 0..N-1 (unshifted), N = nfft (default 2L).
+ * Every window used has W = 0 at |w| = L, so the lag range computed is
+ * [-L, L-1] on each axis (2L lags) and no lag aliases on an N >= 2L grid.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* and every array argument are DEVICE pointers on the
+ *     current CUDA device, owned by the caller.  The library never allocates
+ *     or frees device memory: scratch lives in the caller's workspace `ws`
+ *     (size from hos_workspace_size, 256-byte aligned).
+ *   - All work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and the call returns without synchronising.
+ *   - Argument errors return synchronously and enqueue nothing.  A launch
+ *     failure returns HOS_ERR_CUDA.  Failures detected on the device (a wait
+ *     that ran past its time limit) are written to a status word in `ws`;
+ *     read it with hos_get_device_status after the stream completes.
+ *   - Complex outputs are interleaved float pairs (re, im), i.e. complex64.
+ *   - A workspace may be reused by consecutive calls on one stream; calls
+ *     that overlap in time need separate workspaces.
+ */
+#ifndef HOS_H
+#define HOS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* hos_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+    HOS_OK = 0,
+    HOS_ERR_INVALID_ARG = 1,  /* bad size, null pointer, bad enum value */
+    HOS_ERR_UNSUPPORTED = 2,  /* valid but not implemented (e.g. L too large for a path) */
+    HOS_ERR_WORKSPACE = 3,    /* ws too small or misaligned */
+    HOS_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed */
+    HOS_ERR_TIMEOUT = 5,      /* device status: a wait inside a kernel hit its limit */
+    HOS_ERR_DEVICE_FAULT = 6  /* device status: an internal consistency check failed */
+} hos_status;
+
+typedef enum { HOS_F32 = 0, HOS_F64 = 1 } hos_dtype;
+
+/* Arithmetic of the cumulant contraction (the dominant step).
+ *   FP32        : 3xTF32 split products on the tensor cores (tcgen05 kind::tf32),
+ *                 FP32 accumulation, FP64 cross-tile reduction (~1e-6 relative);
+ *   SPLIT_BF16  : x = hi + lo in bf16, three products on the tensor cores
+ *                 (tcgen05 kind::f16), FP32 accumulation, FP64 reduction (~1e-5);
+ *   SIMT_FP32   : plain FP32 FFMA on the CUDA cores (cross-check path).
+ * Mean removal, cross-chunk reduction and c2 are FP64 in every mode.       */
+typedef enum { HOS_PREC_FP32 = 0, HOS_PREC_SPLIT_BF16 = 1, HOS_PREC_SIMT_FP32 = 2 } hos_precision;
+
+/* Lag windows.  PARZEN: d(w1)d(w2)[d(w3)] (separable).  PARZEN_SYM (bispectrum
+ * only): d(w1)d(w2)d(w1-w2), which keeps c3's six-fold symmetry.  RECT: 1 for
+ * every |w| <= L-1.                                                        */
+typedef enum { HOS_WIN_PARZEN = 0, HOS_WIN_PARZEN_SYM = 1, HOS_WIN_RECT = 2 } hos_window;
+
+typedef enum {
+    HOS_OP_BISPECTRUM = 0,
+    HOS_OP_TRISPECTRUM = 1,
+    HOS_OP_BISPECTRUM_BATCHED = 2,
+    HOS_OP_BISPECTRUM_BACKWARD = 3,
+    HOS_OP_CUMULANT3 = 4,
+    HOS_OP_CUMULANT4 = 5
+} hos_op;
+
+typedef struct {
+    int32_t L;            /* maximum lag, 1 <= L <= 1024 (trispectrum: L <= 64) */
+    int32_t nfft;         /* grid points per axis; 0 -> 2L; otherwise >= 2L    */
+    int32_t precision;    /* hos_precision                                      */
+    int32_t window;       /* hos_window                                         */
+    int32_t remove_mean;  /* nonzero: subtract each part's mean (FP64)          */
+    int32_t segment_len;  /* 0: one part (K = 1); else parts of this many
+                             samples (the last may be shorter), each part's
+                             cumulant uses its own length, estimates averaged
+                             (Algorithm DBS steps 1, 2, 6)                      */
+    int32_t tile_n;       /* 0: automatic; else 128 or 256: width of the lag
+                             tile one CTA accumulates (tuning knob)             */
+    int32_t flush_chunks; /* 0: automatic; else the most 1024-sample chunks one
+                             tile accumulates in FP32 before its partial sum is
+                             handed to the FP64 reduction (tuning knob)         */
+} hos_params;
+
+/* Bytes of workspace an operation needs.
+ *   op        : hos_op
+ *   n_total   : samples (batched: total over all series)
+ *   n_series  : number of series (1 unless batched)
+ *   max_len   : longest series (batched), else n_total
+ * Returns HOS_ERR_INVALID_ARG for bad params.                              */
+hos_status hos_workspace_size(int32_t op, int64_t n_total, int32_t n_series, int64_t max_len,
+                              const hos_params* params, size_t* bytes);
+
+/* Smoothed sample bispectrum of one series.
+ *   d_x : n samples (dtype float32 or float64)
+ *   d_B : nfft*nfft complex64, row-major [k1][k2]                          */
+hos_status hos_bispectrum(const void* d_x, int32_t dtype, int64_t n, const hos_params* params, void* d_B,
+                          void* ws, size_t ws_bytes, hos_stream_t stream);
+
+/* Smoothed sample trispectrum of one series.
+ *   d_T : nfft^3 complex64, row-major [k1][k2][k3]                         */
+hos_status hos_trispectrum(const void* d_x, int32_t dtype, int64_t n, const hos_params* params, void* d_T,
+                           void* ws, size_t ws_bytes, hos_stream_t stream);
+
+/* Bispectra of S independent series of uneven length in one pass.
+ *   d_x       : concatenated samples, n_total of them
+ *   d_offsets : S+1 int64, series s is d_x[offsets[s] .. offsets[s+1]),
+ *               nondecreasing, offsets[0] = 0, offsets[S] = n_total
+ *   max_len   : an upper bound on any series length (sizes the workspace)
+ *   d_B       : S * nfft^2 complex64, series-major
+ * A series of length 0 yields B = 0.  segment_len must be 0.              */
+hos_status hos_bispectrum_batched(const void* d_x, int32_t dtype, const int64_t* d_offsets, int32_t S,
+                                  int64_t n_total, int64_t max_len, const hos_params* params, void* d_B, void* ws,
+                                  size_t ws_bytes, hos_stream_t stream);
+
+/* Adjoint of hos_bispectrum (one part only, segment_len = 0): the gradient of a
+ * real loss l through B.
+ *   d_dB : nfft^2 complex64 holding dl/dRe B + i dl/dIm B
+ *   d_dx : n values, same dtype as d_x, receives dl/dx (overwritten)
+ * Steps: adjoint transform and window, symmetrised; the two contractions of
+ * the triple-product loop's derivative; the mean-removal adjoint.          */
+hos_status hos_bispectrum_backward(const void* d_x, int32_t dtype, int64_t n, const hos_params* params,
+                                   const void* d_dB, void* d_dx, void* ws, size_t ws_bytes, hos_stream_t stream);
+
+/* Third-order sample cumulant, unwindowed, FP64.
+ *   d_c3 : (2L)*(2L) doubles, row-major [w1+L][w2+L], w in [-L, L-1]
+ * With segment_len > 0 it is the average of the parts' cumulants.          */
+hos_status hos_cumulant3(const void* d_x, int32_t dtype, int64_t n, const hos_params* params, double* d_c3,
+                         void* ws, size_t ws_bytes, hos_stream_t stream);
+
+/* Fourth-order sample cumulant, unwindowed, FP64.
+ *   d_c4 : (2L)^3 doubles, row-major [w1+L][w2+L][w3+L], w in [-L, L-1]    */
+hos_status hos_cumulant4(const void* d_x, int32_t dtype, int64_t n, const hos_params* params, double* d_c4,
+                         void* ws, size_t ws_bytes, hos_stream_t stream);
+
+/* Read (synchronously) the device status word of a workspace that a finished
+ * call used.  *status = HOS_OK, HOS_ERR_TIMEOUT or HOS_ERR_DEVICE_FAULT.     */
+hos_status hos_get_device_status(const void* ws, int32_t* status);
+
+/* Clear the device status word (enqueued on stream).                        */
+hos_status hos_reset_device_status(void* ws, hos_stream_t stream);
+
+/* Failure-detection self test: one CTA waits on a barrier that nothing
+ * signals, with a wait limit of timeout_us microseconds, then records
+ * HOS_ERR_TIMEOUT in the workspace status word and exits cleanly (no trap,
+ * no fault).  Lets a caller check that device-side timeouts are reported.   */
+hos_status hos_selftest_timeout(void* ws, size_t ws_bytes, int32_t timeout_us, hos_stream_t stream);
+
+/* Tracing.  When enabled, each call records CUDA events around its stages on
+ * its stream; hos_get_stage_times synchronises on the last call's events and
+ * returns per-stage milliseconds in stage order (prep, contraction, reduce,
+ * transform, ...), with names from hos_stage_name.  Not for use while a
+ * stream is being captured into a graph.                                   */
+hos_status hos_set_profiling(int32_t enable);
+hos_status hos_get_stage_times(float* ms, int32_t max_stages, int32_t* n_stages);
+const char* hos_stage_name(int32_t i);
+
+/* Total kernels this library has launched in the process (all devices).    */
+int64_t hos_launch_count(void);
+
+/* Name of the contraction kernel variant the last call used.               */
+const char* hos_last_contraction(void);
+
+const char* hos_status_string(int32_t status);
+const char* hos_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOS_H */

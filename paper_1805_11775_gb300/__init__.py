@@ -1,0 +1,300 @@
+"""GB300 (sm_103a) higher-order spectra: the smoothed sample bispectrum and
+trispectrum of a series, computed the indirect way (sample cumulant, lag
+window, Fourier transform), after Mamun et al., "Efficient Sequential and
+Parallel Algorithms for Estimating Higher Order Spectra" (Problem Statement;
+Algorithm DBS steps 1, 2 and 6 for the parts and their averaging).
+
+PyTorch supplies device memory and the current stream; the computation runs
+in ``libhos.so`` (hand-written CUDA for sm_103a) through its C ABI.
+
+    >>> import paper_1805_11775_gb300 as hos
+    >>> B = hos.bispectrum(x_cuda, L=256, precision="bf16")      # (512, 512) complex64
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import _native
+from ._native import HosError, HosParams
+
+__all__ = ["bispectrum", "bispectrum_batched", "trispectrum", "cumulant3", "cumulant4", "BispectrumFn",
+           "bispectrum_ad", "Workspace", "workspace_size", "device_status", "reset_device_status",
+           "selftest_timeout", "set_profiling", "stage_times", "launch_count", "last_contraction", "HosError",
+           "PRECISIONS", "WINDOWS"]
+
+PRECISIONS = {"fp32": 0, "3xtf32": 0, "bf16": 1, "split_bf16": 1, "simt": 2, "simt_fp32": 2}
+WINDOWS = {"parzen": 0, "parzen_sym": 1, "rect": 2}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def make_params(L, nfft=0, precision="bf16", window="parzen", remove_mean=True, segment_len=0, tile_n=0,
+                flush_chunks=0) -> HosParams:
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    win = WINDOWS[window] if isinstance(window, str) else int(window)
+    return HosParams(int(L), int(nfft or 0), prec, win, int(bool(remove_mean)), int(segment_len or 0),
+                     int(tile_n or 0), int(flush_chunks or 0))
+
+
+def workspace_size(op: int, n_total: int, n_series: int, max_len: int, params: HosParams) -> int:
+    out = ctypes.c_size_t(0)
+    _native.check(_native.lib().hos_workspace_size(op, int(n_total), int(n_series), int(max_len),
+                                                   ctypes.byref(params), ctypes.byref(out)), "hos_workspace_size")
+    return int(out.value)
+
+
+class Workspace:
+    """A growable device scratch buffer (a torch uint8 tensor) for the library."""
+
+    def __init__(self, device=None):
+        self.device = device
+        self.buf = None
+
+    def get(self, nbytes: int):
+        torch = _torch()
+        nbytes = max(int(nbytes), 256)
+        if self.buf is None or self.buf.numel() < nbytes:
+            dev = self.device if self.device is not None else torch.device("cuda", torch.cuda.current_device())
+            self.buf = None
+            self.buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        return self.buf
+
+    def ptr(self):
+        p = self.buf.data_ptr()
+        return p + ((-p) % 256)
+
+    def nbytes(self):
+        return self.buf.numel() - ((-self.buf.data_ptr()) % 256)
+
+
+_default_ws = {}
+_ws_lock = threading.Lock()
+
+
+def _workspace(ws, device):
+    if ws is not None:
+        return ws
+    with _ws_lock:
+        key = (device.type, device.index)
+        if key not in _default_ws:
+            _default_ws[key] = Workspace(device)
+        return _default_ws[key]
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _prepare(x):
+    """Return (device tensor, was_host).  Host input is copied to the GPU."""
+    torch = _torch()
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.ascontiguousarray(x))
+    if x.dtype not in (torch.float32, torch.float64):
+        raise TypeError("x must be float32 or float64")
+    host = x.device.type != "cuda"
+    if host:
+        x = x.to("cuda", non_blocking=True)
+    return x.contiguous(), host
+
+
+def _dtype_code(x):
+    torch = _torch()
+    return _native.F64 if x.dtype == torch.float64 else _native.F32
+
+
+def bispectrum(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=True, segment_len=0, tile_n=0,
+               flush_chunks=0, out=None, workspace=None, stream=None):
+    """Smoothed sample bispectrum B[k1, k2] (complex64, nfft x nfft, default nfft = 2L).
+
+    ``precision``: "bf16" (split-bf16 tensor cores), "fp32" (3xTF32 tensor
+    cores) or "simt" (FP32 CUDA cores).  Host input returns a host result."""
+    torch = _torch()
+    xd, host = _prepare(x)
+    p = make_params(L, nfft, precision, window, remove_mean, segment_len, tile_n, flush_chunks)
+    N = p.nfft or 2 * p.L
+    if out is None:
+        out = torch.empty((N, N), dtype=torch.complex64, device=xd.device)
+    ws = _workspace(workspace, xd.device)
+    ws.get(workspace_size(_native.OP_BISPECTRUM, xd.numel(), 1, xd.numel(), p))
+    _native.check(_native.lib().hos_bispectrum(xd.data_ptr(), _dtype_code(xd), xd.numel(), ctypes.byref(p),
+                                               out.data_ptr(), ws.ptr(), ws.nbytes(), _stream(stream)),
+                  "hos_bispectrum")
+    return out.cpu() if host else out
+
+
+def bispectrum_batched(values, offsets, L, nfft=0, precision="bf16", window="parzen", remove_mean=True, tile_n=0,
+                       flush_chunks=0, out=None, workspace=None, stream=None, max_len=None):
+    """Bispectra of S series concatenated in ``values`` with ``offsets`` (S+1).
+
+    Returns (S, nfft, nfft) complex64."""
+    torch = _torch()
+    vd, host = _prepare(values)
+    offs = torch.as_tensor(offsets, dtype=torch.int64)
+    if max_len is None:
+        oh = offs.cpu() if offs.device.type == "cuda" else offs
+        max_len = int((oh[1:] - oh[:-1]).max().item()) if oh.numel() > 1 else 0
+    od = offs.to(vd.device, non_blocking=True).contiguous()
+    S = od.numel() - 1
+    p = make_params(L, nfft, precision, window, remove_mean, 0, tile_n, flush_chunks)
+    N = p.nfft or 2 * p.L
+    if out is None:
+        out = torch.empty((S, N, N), dtype=torch.complex64, device=vd.device)
+    ws = _workspace(workspace, vd.device)
+    ws.get(workspace_size(_native.OP_BISPECTRUM_BATCHED, vd.numel(), S, max_len, p))
+    _native.check(_native.lib().hos_bispectrum_batched(vd.data_ptr(), _dtype_code(vd), od.data_ptr(), S, vd.numel(),
+                                                       int(max_len), ctypes.byref(p), out.data_ptr(), ws.ptr(),
+                                                       ws.nbytes(), _stream(stream)), "hos_bispectrum_batched")
+    return out.cpu() if host else out
+
+
+def cumulant3(x, L, precision="bf16", remove_mean=True, segment_len=0, tile_n=0, flush_chunks=0, workspace=None,
+              stream=None):
+    """Unwindowed sample c3 over [-L, L-1]^2 (float64, (2L, 2L), index w + L)."""
+    torch = _torch()
+    xd, host = _prepare(x)
+    p = make_params(L, 0, precision, "parzen", remove_mean, segment_len, tile_n, flush_chunks)
+    out = torch.empty((2 * p.L, 2 * p.L), dtype=torch.float64, device=xd.device)
+    ws = _workspace(workspace, xd.device)
+    ws.get(workspace_size(_native.OP_CUMULANT3, xd.numel(), 1, xd.numel(), p))
+    _native.check(_native.lib().hos_cumulant3(xd.data_ptr(), _dtype_code(xd), xd.numel(), ctypes.byref(p),
+                                              out.data_ptr(), ws.ptr(), ws.nbytes(), _stream(stream)),
+                  "hos_cumulant3")
+    return out.cpu() if host else out
+
+
+def trispectrum(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=True, segment_len=0, out=None,
+                workspace=None, stream=None):
+    """Smoothed sample trispectrum T[k1, k2, k3] (complex64, nfft^3)."""
+    torch = _torch()
+    xd, host = _prepare(x)
+    p = make_params(L, nfft, precision, window, remove_mean, segment_len)
+    N = p.nfft or 2 * p.L
+    if out is None:
+        out = torch.empty((N, N, N), dtype=torch.complex64, device=xd.device)
+    ws = _workspace(workspace, xd.device)
+    ws.get(workspace_size(_native.OP_TRISPECTRUM, xd.numel(), 1, xd.numel(), p))
+    _native.check(_native.lib().hos_trispectrum(xd.data_ptr(), _dtype_code(xd), xd.numel(), ctypes.byref(p),
+                                                out.data_ptr(), ws.ptr(), ws.nbytes(), _stream(stream)),
+                  "hos_trispectrum")
+    return out.cpu() if host else out
+
+
+def cumulant4(x, L, precision="bf16", remove_mean=True, segment_len=0, workspace=None, stream=None):
+    """Unwindowed sample c4 over [-L, L-1]^3 (float64, (2L, 2L, 2L))."""
+    torch = _torch()
+    xd, host = _prepare(x)
+    p = make_params(L, 0, precision, "parzen", remove_mean, segment_len)
+    out = torch.empty((2 * p.L,) * 3, dtype=torch.float64, device=xd.device)
+    ws = _workspace(workspace, xd.device)
+    ws.get(workspace_size(_native.OP_CUMULANT4, xd.numel(), 1, xd.numel(), p))
+    _native.check(_native.lib().hos_cumulant4(xd.data_ptr(), _dtype_code(xd), xd.numel(), ctypes.byref(p),
+                                              out.data_ptr(), ws.ptr(), ws.nbytes(), _stream(stream)),
+                  "hos_cumulant4")
+    return out.cpu() if host else out
+
+
+def bispectrum_backward(x, dB, L, nfft=0, precision="bf16", window="parzen", remove_mean=True, workspace=None,
+                        stream=None):
+    """dl/dx given dB = dl/dRe B + i dl/dIm B."""
+    torch = _torch()
+    xd, host = _prepare(x)
+    p = make_params(L, nfft, precision, window, remove_mean, 0)
+    g = dB.to(xd.device).to(torch.complex64).contiguous()
+    dx = torch.empty_like(xd)
+    ws = _workspace(workspace, xd.device)
+    ws.get(workspace_size(_native.OP_BISPECTRUM_BACKWARD, xd.numel(), 1, xd.numel(), p))
+    _native.check(_native.lib().hos_bispectrum_backward(xd.data_ptr(), _dtype_code(xd), xd.numel(), ctypes.byref(p),
+                                                        g.data_ptr(), dx.data_ptr(), ws.ptr(), ws.nbytes(),
+                                                        _stream(stream)), "hos_bispectrum_backward")
+    return dx.cpu() if host else dx
+
+
+class BispectrumFn:
+    """torch.autograd.Function wrapper, created lazily so that importing the
+    package does not import torch."""
+    _cls = None
+
+    @classmethod
+    def get(cls):
+        if cls._cls is None:
+            torch = _torch()
+
+            class _Fn(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, x, L, nfft, precision, window, remove_mean):
+                    ctx.save_for_backward(x)
+                    ctx.cfg = (L, nfft, precision, window, remove_mean)
+                    return bispectrum(x, L, nfft, precision, window, remove_mean)
+
+                @staticmethod
+                def backward(ctx, gB):
+                    (x,) = ctx.saved_tensors
+                    L, nfft, precision, window, remove_mean = ctx.cfg
+                    dx = bispectrum_backward(x, gB, L, nfft, precision, window, remove_mean)
+                    return dx, None, None, None, None, None
+
+            cls._cls = _Fn
+        return cls._cls
+
+
+def bispectrum_ad(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=True):
+    """Differentiable bispectrum (torch autograd)."""
+    return BispectrumFn.get().apply(x, L, nfft, precision, window, remove_mean)
+
+
+def device_status(workspace=None) -> int:
+    torch = _torch()
+    ws = _workspace(workspace, torch.device("cuda", torch.cuda.current_device()))
+    if ws.buf is None:
+        return 0
+    v = ctypes.c_int32(0)
+    _native.check(_native.lib().hos_get_device_status(ws.ptr(), ctypes.byref(v)), "hos_get_device_status")
+    return int(v.value)
+
+
+def reset_device_status(workspace=None, stream=None):
+    torch = _torch()
+    ws = _workspace(workspace, torch.device("cuda", torch.cuda.current_device()))
+    if ws.buf is not None:
+        _native.check(_native.lib().hos_reset_device_status(ws.ptr(), _stream(stream)), "hos_reset_device_status")
+
+
+def selftest_timeout(timeout_us=1000, workspace=None, stream=None) -> int:
+    """Run the device-side timeout self test; returns the status word it left."""
+    torch = _torch()
+    ws = _workspace(workspace, torch.device("cuda", torch.cuda.current_device()))
+    ws.get(256)
+    reset_device_status(ws, stream)
+    _native.check(_native.lib().hos_selftest_timeout(ws.ptr(), ws.nbytes(), int(timeout_us), _stream(stream)),
+                  "hos_selftest_timeout")
+    torch.cuda.synchronize()
+    return device_status(ws)
+
+
+def set_profiling(on: bool):
+    _native.lib().hos_set_profiling(int(bool(on)))
+
+
+def stage_times():
+    """[(stage name, ms)] of the last call made while profiling was on."""
+    arr = (ctypes.c_float * 8)()
+    n = ctypes.c_int32(0)
+    _native.check(_native.lib().hos_get_stage_times(arr, 8, ctypes.byref(n)), "hos_get_stage_times")
+    return [(_native.lib().hos_stage_name(i).decode(), float(arr[i])) for i in range(n.value)]
+
+
+def launch_count() -> int:
+    return int(_native.lib().hos_launch_count())
+
+
+def last_contraction() -> str:
+    return _native.lib().hos_last_contraction().decode()

@@ -1,0 +1,474 @@
+// abi.cu -- the C ABI (include/hos.h): argument validation, tile geometry,
+// workspace carving, and the stream-ordered launch sequence of each entry
+// point.  No device memory is allocated here: every buffer is carved from the
+// caller's workspace.
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "launch.cuh"
+
+namespace hos {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static const char* g_last_contraction = "none";
+
+// ---- tracing ------------------------------------------------------------------
+constexpr int MAX_STAGES = 8;
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static cudaEvent_t g_ev[MAX_STAGES + 1];
+static bool g_ev_made = false;
+static int g_prof_n = 0;  // events recorded by the last call
+static const char* g_cur_names[MAX_STAGES];
+
+struct Tracer {
+    cudaStream_t st;
+    int n = 0;
+    bool on;
+    explicit Tracer(cudaStream_t s) : st(s) {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        on = g_prof_on;
+        if (on && !g_ev_made) {
+            for (int i = 0; i <= MAX_STAGES; ++i) cudaEventCreate(&g_ev[i]);
+            g_ev_made = true;
+        }
+        if (on) g_prof_n = 0;
+    }
+    void mark(const char* next_stage) {
+        if (!on || n > MAX_STAGES) return;
+        cudaEventRecord(g_ev[n], st);
+        if (n < MAX_STAGES) g_cur_names[n] = next_stage;
+        ++n;
+        g_prof_n = n;
+    }
+};
+
+// ---- device properties -----------------------------------------------------------
+static int sm_count() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static int cache[64] = {0};
+    if (dev >= 0 && dev < 64 && cache[dev] > 0) return cache[dev];
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    if (dev >= 0 && dev < 64) cache[dev] = n;
+    return n;
+}
+
+static uint64_t wait_limit_ns() {
+    const char* v = getenv("HOS_WAIT_LIMIT_MS");
+    long ms = v ? atol(v) : 4000;
+    if (ms <= 0) ms = 4000;
+    return (uint64_t)ms * 1000000ull;
+}
+
+// ---- validation and geometry ------------------------------------------------------
+static int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+static int ilog2_exact(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return ((1 << l) == v) ? l : -1;
+}
+
+static hos_status check_params(const hos_params* p, int op) {
+    if (!p) return HOS_ERR_INVALID_ARG;
+    if (p->L < 1 || p->L > 1024) return p->L < 1 ? HOS_ERR_INVALID_ARG : HOS_ERR_UNSUPPORTED;
+    if (p->nfft != 0 && (p->nfft < 2 * p->L || p->nfft > 4096)) return HOS_ERR_INVALID_ARG;
+    {   // a grid size that is not a power of two uses the direct transform (<= 2048 points)
+        const int nf = p->nfft ? p->nfft : 2 * p->L;
+        if ((nf & (nf - 1)) != 0 && nf > 2048) return HOS_ERR_UNSUPPORTED;
+    }
+    if (p->precision < 0 || p->precision > 2) return HOS_ERR_INVALID_ARG;
+    if (p->window < 0 || p->window > 2) return HOS_ERR_INVALID_ARG;
+    if (p->segment_len < 0) return HOS_ERR_INVALID_ARG;
+    if (p->tile_n != 0 && p->tile_n != 32 && p->tile_n != 64 && p->tile_n != 128 && p->tile_n != 256)
+        return HOS_ERR_INVALID_ARG;
+    if (p->flush_chunks < 0) return HOS_ERR_INVALID_ARG;
+    if (op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT4) {
+        if (p->L > 64) return HOS_ERR_UNSUPPORTED;
+        if (p->window == HOS_WIN_PARZEN_SYM) return HOS_ERR_UNSUPPORTED;
+    }
+    if (op == HOS_OP_BISPECTRUM_BACKWARD && p->segment_len != 0) return HOS_ERR_UNSUPPORTED;
+    if (op == HOS_OP_BISPECTRUM_BATCHED && p->segment_len != 0) return HOS_ERR_INVALID_ARG;
+    return HOS_OK;
+}
+
+static C3Geom make_geom(const hos_params* p, int G) {
+    C3Geom g;
+    memset(&g, 0, sizeof(g));
+    const int twoL = 2 * p->L;
+    g.L = p->L;
+    int N = p->tile_n ? p->tile_n : next_pow2(twoL);
+    if (N < 32) N = 32;
+    if (N > 256) N = 256;
+    g.tile_n = N;
+    g.tiles_m = (twoL + TILE_M - 1) / TILE_M;
+    g.tiles_n = (twoL + N - 1) / N;
+    int cnt = 0;
+    for (int a = 0; a < MAX_TILES_M; ++a)
+        for (int b = 0; b < MAX_TILES_N; ++b) g.tile_idx[a][b] = -1;
+    for (int b = 0; b < g.tiles_n; ++b)
+        for (int a = 0; a < g.tiles_m; ++a) {
+            // every w1 of the tile above every w2: mirrored, not computed
+            const bool skip = (a * TILE_M >= b * N + N);
+            if (skip) continue;
+            g.tile_idx[a][b] = (int8_t)cnt;
+            g.tile_a[cnt] = (uint8_t)a;
+            g.tile_b[cnt] = (uint8_t)b;
+            ++cnt;
+        }
+    g.ntiles = cnt;
+    g.flush = p->flush_chunks ? p->flush_chunks : 16;
+    g.G = G;
+    const int reach = (g.tiles_m * TILE_M > g.tiles_n * N) ? g.tiles_m * TILE_M : g.tiles_n * N;
+    g.pad_tail = reach + 64;
+    return g;
+}
+
+static int contraction_ctas(int precision) { return precision == HOS_PREC_SIMT_FP32 ? 4 * sm_count() : sm_count(); }
+
+static int plane_split(int precision) {
+    return precision == HOS_PREC_SPLIT_BF16 ? 1 : (precision == HOS_PREC_FP32 ? 2 : 0);
+}
+static int plane_elt(int precision) {
+    return precision == HOS_PREC_SPLIT_BF16 ? 2 : (precision == HOS_PREC_FP32 ? 4 : 0);
+}
+
+static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t status, off, pad, unit, win, mean, mpart, y32, hi, lo, partials, grid, tw, total;
+    int64_t plane_len, slots;
+    int nslices;
+    int groups;
+};
+
+// Carve the workspace.  S series (parts), n_total samples, longest max_len.
+static Layout make_layout(int op, const hos_params* p, const C3Geom& g, int64_t n_total, int S, int64_t max_len) {
+    Layout l;
+    memset(&l, 0, sizeof(l));
+    const int Nf = p->nfft ? p->nfft : 2 * p->L;
+    l.nslices = (int)(ceil_div(max_len > 0 ? max_len : 1, 8192));
+    if (l.nslices > 256) l.nslices = 256;
+    if (l.nslices < 1) l.nslices = 1;
+    l.plane_len = n_total + (int64_t)S * ((int64_t)p->L + KC + g.pad_tail + 64);
+    const int64_t chunks = ceil_div(n_total, KC) + S;
+    l.slots = (int64_t)g.ntiles * (chunks / g.flush + S + 1) + g.G;
+    l.groups = (op == HOS_OP_BISPECTRUM_BATCHED) ? S : 1;
+    size_t o = 0;
+    l.status = o; o = al256(o + 256);
+    l.off = o; o = al256(o + 8 * (size_t)(S + 1));
+    l.pad = o; o = al256(o + 8 * (size_t)(S + 1));
+    l.unit = o; o = al256(o + 8 * (size_t)(S + 1));
+    l.win = o; o = al256(o + 8 * (size_t)(S + 1));
+    l.mean = o; o = al256(o + 8 * (size_t)S);
+    l.mpart = o; o = al256(o + 8 * (size_t)S * l.nslices);
+    l.y32 = o; o = al256(o + 4 * (size_t)l.plane_len);
+    const int elt = plane_elt(p->precision);
+    l.hi = o; o = al256(o + (size_t)elt * l.plane_len + 64);
+    l.lo = o; o = al256(o + (size_t)elt * l.plane_len + 64);
+    l.partials = o; o = al256(o + 4 * (size_t)l.slots * TILE_M * g.tile_n);
+    const bool spectrum = (op == HOS_OP_BISPECTRUM || op == HOS_OP_BISPECTRUM_BATCHED);
+    l.grid = o; o = al256(o + (spectrum ? 4 * (size_t)l.groups * Nf * Nf : 0));
+    l.tw = o; o = al256(o + 8 * (size_t)Nf);
+    l.total = o;
+    return l;
+}
+
+// Everything a call needs to know before launching, computed in one place so
+// that hos_workspace_size and the entry points agree.
+struct Plan {
+    C3Geom g;
+    Layout l;
+    int S;           // series (batched) or parts (one series cut by segment_len)
+    int64_t seg;     // part length, 0 = one part
+    int64_t max_len; // longest series / part
+    int Nf;
+};
+
+static hos_status make_plan(int op, const hos_params* p, int64_t n_total, int S_in, int64_t max_len_in, Plan& P) {
+    hos_status s = check_params(p, op);
+    if (s != HOS_OK) return s;
+    P.Nf = p->nfft ? p->nfft : 2 * p->L;
+    int64_t U_known = -1;
+    if (op == HOS_OP_BISPECTRUM_BATCHED) {
+        P.S = S_in;
+        P.seg = 0;
+        P.max_len = max_len_in;
+    } else {
+        P.seg = (p->segment_len > 0 && p->segment_len < n_total) ? p->segment_len : 0;
+        const int64_t S64 = P.seg ? ceil_div(n_total, P.seg) : 1;
+        if (S64 > 65535) return HOS_ERR_UNSUPPORTED;
+        P.S = (int)S64;
+        P.max_len = P.seg ? P.seg : n_total;
+        // exact chunk count: full parts plus the (possibly shorter) last one
+        const int64_t last = n_total - (P.S - 1) * (P.seg ? P.seg : 0);
+        U_known = (P.S - 1) * ceil_div(P.max_len, KC) + ceil_div(last, KC);
+    }
+    if (P.S > 65535) return HOS_ERR_UNSUPPORTED;
+    int G = contraction_ctas(p->precision);
+    P.g = make_geom(p, G);
+    if (U_known >= 0) {
+        const int64_t U = U_known * P.g.ntiles;
+        if (U < G) P.g.G = (int)(U > 0 ? U : 1);
+    }
+    P.l = make_layout(op, p, P.g, n_total, P.S, P.max_len);
+    return HOS_OK;
+}
+
+template <typename T>
+static T* at(void* ws, size_t off) {
+    return reinterpret_cast<T*>(reinterpret_cast<uint8_t*>(ws) + off);
+}
+
+#define HOS_CUDA_TRY(expr)                         \
+    do {                                           \
+        cudaError_t e__ = (expr);                  \
+        if (e__ != cudaSuccess) return HOS_ERR_CUDA; \
+    } while (0)
+
+static LineGeom line_geom(int N, int64_t nlines, int64_t inner, int64_t outer, int64_t elem) {
+    LineGeom g;
+    g.N = N;
+    g.log2N = ilog2_exact(N);
+    g.nlines = nlines;
+    g.inner = inner;
+    g.outer_stride = outer;
+    g.elem_stride = elem;
+    int lpb = (g.log2N >= 0) ? 4096 / N : 2048 / N;
+    if (lpb < 1) lpb = 1;
+    if (lpb > nlines) lpb = (int)(nlines > 0 ? nlines : 1);
+    g.lpb = lpb;
+    return g;
+}
+
+// Steps shared by the c3 operations: plan, mean, planes, contraction, reduce.
+static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int64_t* d_offsets, const Plan& P,
+                         const hos_params* p, void* ws, size_t ws_bytes, cudaStream_t st, Tracer& tr, int red_mode,
+                         float* grid_out, double* c3_out) {
+    const C3Geom& g = P.g;
+    const Layout& l = P.l;
+    const int S = P.S;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < l.total) return HOS_ERR_WORKSPACE;
+    int* status = at<int>(ws, l.status);
+    int64_t* off = at<int64_t>(ws, l.off);
+    int64_t* pad = at<int64_t>(ws, l.pad);
+    int64_t* unit = at<int64_t>(ws, l.unit);
+    int64_t* win = at<int64_t>(ws, l.win);
+    double* mean = at<double>(ws, l.mean);
+    float* y32 = at<float>(ws, l.y32);
+    void* hi = at<void>(ws, l.hi);
+    void* lo = at<void>(ws, l.lo);
+    float* partials = at<float>(ws, l.partials);
+
+    tr.mark("prep");
+    const int mode = (op == HOS_OP_BISPECTRUM_BATCHED) ? 1 : 0;
+    HOS_CUDA_TRY(launch_plan_series(mode, n, P.seg, d_offsets, S, p->L, g.ntiles, g.flush, g.pad_tail, off, pad,
+                                    unit, win, st));
+    HOS_CUDA_TRY(launch_mean(x, dtype, off, S, l.nslices, at<double>(ws, l.mpart), p->remove_mean, mean, st));
+    const int64_t maxpad = (int64_t)p->L + P.max_len + KC + g.pad_tail + 64;
+    int bx = (int)ceil_div(maxpad, 256 * 4);
+    if (bx < 1) bx = 1;
+    if (bx > 65535) bx = 65535;
+    HOS_CUDA_TRY(launch_planes(x, dtype, off, pad, mean, p->L, plane_split(p->precision), y32, hi, lo, S, bx, st));
+
+    SeriesView sv{off, pad, unit, win, mean, S};
+    tr.mark("contract");
+    if (p->precision == HOS_PREC_SIMT_FP32) {
+        C3SimtParams cp{g, sv, y32, partials};
+        HOS_CUDA_TRY(launch_c3_simt(cp, g.G, st));
+        g_last_contraction = "c3_simt_fp32";
+    } else {
+        C3TcParams cp{g, sv, y32, hi, lo, partials, status, wait_limit_ns()};
+        const bool tf32 = (p->precision == HOS_PREC_FP32);
+        HOS_CUDA_TRY(launch_c3_tc(tf32, cp, g.G, st));
+        g_last_contraction = tf32 ? "c3_tcgen05_3xtf32" : "c3_tcgen05_split_bf16";
+    }
+
+    tr.mark("reduce");
+    Reduce3Params rp;
+    rp.geom = g;
+    rp.ser = sv;
+    rp.partials = partials;
+    rp.window = p->window;
+    rp.nfft = P.Nf;
+    rp.mode = red_mode;
+    rp.per_series_groups = (op == HOS_OP_BISPECTRUM_BATCHED) ? 1 : 0;
+    rp.scale = 1.0 / (4.0 * 3.14159265358979323846 * 3.14159265358979323846);
+    rp.grid = grid_out;
+    rp.c3out = c3_out;
+    const int groups = rp.per_series_groups ? S : 1;
+    if (red_mode == 0 && P.Nf > 2 * p->L) HOS_CUDA_TRY(launch_zero_f32(grid_out, (int64_t)groups * P.Nf * P.Nf, st));
+    HOS_CUDA_TRY(launch_reduce3(rp, groups, st));
+    return HOS_OK;
+}
+
+static hos_status run_dft2(float* grid, float2* out, int groups, int Nf, float2* tw, cudaStream_t st) {
+    HOS_CUDA_TRY(launch_twiddles(Nf, tw, st));
+    // along the last axis (contiguous), real input
+    LineGeom g1 = line_geom(Nf, (int64_t)groups * Nf, 1, Nf, 1);
+    HOS_CUDA_TRY(launch_lines(true, grid, out, g1, tw, -1, 1.0f, st));
+    // along the first axis, in place
+    LineGeom g2 = line_geom(Nf, (int64_t)groups * Nf, Nf, (int64_t)Nf * Nf, Nf);
+    HOS_CUDA_TRY(launch_lines(false, out, out, g2, tw, -1, 1.0f, st));
+    return HOS_OK;
+}
+
+}  // namespace hos
+
+using namespace hos;
+
+extern "C" {
+
+const char* hos_version(void) { return "hos-gb300 0.1 (sm_103a)"; }
+
+const char* hos_status_string(int32_t s) {
+    switch (s) {
+        case HOS_OK: return "ok";
+        case HOS_ERR_INVALID_ARG: return "invalid argument";
+        case HOS_ERR_UNSUPPORTED: return "unsupported";
+        case HOS_ERR_WORKSPACE: return "workspace too small or misaligned";
+        case HOS_ERR_CUDA: return "CUDA error";
+        case HOS_ERR_TIMEOUT: return "device wait timed out";
+        case HOS_ERR_DEVICE_FAULT: return "device consistency check failed";
+        default: return "unknown status";
+    }
+}
+
+int64_t hos_launch_count(void) { return g_launches.load(); }
+const char* hos_last_contraction(void) { return g_last_contraction; }
+
+hos_status hos_workspace_size(int32_t op, int64_t n_total, int32_t n_series, int64_t max_len, const hos_params* p,
+                              size_t* bytes) {
+    if (!bytes || n_total < 0 || n_series < 1 || max_len < 0) return HOS_ERR_INVALID_ARG;
+    if (op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT4 || op == HOS_OP_BISPECTRUM_BACKWARD)
+        return HOS_ERR_UNSUPPORTED;
+    if (op < 0 || op > HOS_OP_CUMULANT4) return HOS_ERR_INVALID_ARG;
+    Plan P;
+    hos_status s = make_plan(op, p, n_total, n_series, max_len, P);
+    if (s != HOS_OK) return s;
+    *bytes = P.l.total;
+    return HOS_OK;
+}
+
+hos_status hos_bispectrum(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, void* d_B, void* ws,
+                          size_t ws_bytes, hos_stream_t stream) {
+    if (!d_x || !d_B || n < 1 || (dtype != HOS_F32 && dtype != HOS_F64)) return HOS_ERR_INVALID_ARG;
+    Plan P;
+    hos_status s = make_plan(HOS_OP_BISPECTRUM, p, n, 1, n, P);
+    if (s != HOS_OK) return s;
+    if (!ws || ws_bytes < P.l.total) return HOS_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Tracer tr(st);
+    s = run_c3(HOS_OP_BISPECTRUM, d_x, dtype, n, nullptr, P, p, ws, ws_bytes, st, tr, 0, at<float>(ws, P.l.grid),
+               nullptr);
+    if (s != HOS_OK) return s;
+    tr.mark("transform");
+    s = run_dft2(at<float>(ws, P.l.grid), reinterpret_cast<float2*>(d_B), 1, P.Nf, at<float2>(ws, P.l.tw), st);
+    tr.mark("");
+    return s;
+}
+
+hos_status hos_bispectrum_batched(const void* d_x, int32_t dtype, const int64_t* d_offsets, int32_t S,
+                                  int64_t n_total, int64_t max_len, const hos_params* p, void* d_B, void* ws,
+                                  size_t ws_bytes, hos_stream_t stream) {
+    if (!d_x || !d_B || !d_offsets || S < 1 || n_total < 0 || max_len < 0 || (dtype != HOS_F32 && dtype != HOS_F64))
+        return HOS_ERR_INVALID_ARG;
+    Plan P;
+    hos_status s = make_plan(HOS_OP_BISPECTRUM_BATCHED, p, n_total, S, max_len, P);
+    if (s != HOS_OK) return s;
+    if (!ws || ws_bytes < P.l.total) return HOS_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Tracer tr(st);
+    s = run_c3(HOS_OP_BISPECTRUM_BATCHED, d_x, dtype, n_total, d_offsets, P, p, ws, ws_bytes, st, tr, 0,
+               at<float>(ws, P.l.grid), nullptr);
+    if (s != HOS_OK) return s;
+    tr.mark("transform");
+    s = run_dft2(at<float>(ws, P.l.grid), reinterpret_cast<float2*>(d_B), S, P.Nf, at<float2>(ws, P.l.tw), st);
+    tr.mark("");
+    return s;
+}
+
+hos_status hos_cumulant3(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, double* d_c3, void* ws,
+                         size_t ws_bytes, hos_stream_t stream) {
+    if (!d_x || !d_c3 || n < 1 || (dtype != HOS_F32 && dtype != HOS_F64)) return HOS_ERR_INVALID_ARG;
+    Plan P;
+    hos_status s = make_plan(HOS_OP_CUMULANT3, p, n, 1, n, P);
+    if (s != HOS_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Tracer tr(st);
+    s = run_c3(HOS_OP_CUMULANT3, d_x, dtype, n, nullptr, P, p, ws, ws_bytes, st, tr, 1, nullptr, d_c3);
+    tr.mark("");
+    return s;
+}
+
+hos_status hos_trispectrum(const void*, int32_t, int64_t, const hos_params*, void*, void*, size_t, hos_stream_t) {
+    return HOS_ERR_UNSUPPORTED;
+}
+hos_status hos_cumulant4(const void*, int32_t, int64_t, const hos_params*, double*, void*, size_t, hos_stream_t) {
+    return HOS_ERR_UNSUPPORTED;
+}
+hos_status hos_bispectrum_backward(const void*, int32_t, int64_t, const hos_params*, const void*, void*, void*,
+                                   size_t, hos_stream_t) {
+    return HOS_ERR_UNSUPPORTED;
+}
+
+hos_status hos_get_device_status(const void* ws, int32_t* status) {
+    if (!ws || !status) return HOS_ERR_INVALID_ARG;
+    int v = 0;
+    if (cudaMemcpy(&v, ws, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return HOS_ERR_CUDA;
+    *status = v;
+    return HOS_OK;
+}
+
+hos_status hos_reset_device_status(void* ws, hos_stream_t stream) {
+    if (!ws) return HOS_ERR_INVALID_ARG;
+    if (cudaMemsetAsync(ws, 0, sizeof(int), reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return HOS_ERR_CUDA;
+    return HOS_OK;
+}
+
+hos_status hos_selftest_timeout(void* ws, size_t ws_bytes, int32_t timeout_us, hos_stream_t stream) {
+    if (!ws || ws_bytes < 256 || timeout_us < 1) return HOS_ERR_INVALID_ARG;
+    if (launch_timeout_selftest(reinterpret_cast<int*>(ws), (uint64_t)timeout_us * 1000ull,
+                                reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return HOS_ERR_CUDA;
+    return HOS_OK;
+}
+
+hos_status hos_set_profiling(int32_t enable) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = enable != 0;
+    return HOS_OK;
+}
+
+hos_status hos_get_stage_times(float* ms, int32_t max_stages, int32_t* n_stages) {
+    if (!ms || !n_stages) return HOS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    int n = g_prof_n - 1;
+    if (n < 0) n = 0;
+    if (n > max_stages) n = max_stages;
+    for (int i = 0; i < n; ++i) {
+        if (cudaEventSynchronize(g_ev[i + 1]) != cudaSuccess) return HOS_ERR_CUDA;
+        if (cudaEventElapsedTime(&ms[i], g_ev[i], g_ev[i + 1]) != cudaSuccess) return HOS_ERR_CUDA;
+    }
+    *n_stages = n;
+    return HOS_OK;
+}
+
+const char* hos_stage_name(int32_t i) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (i < 0 || i >= MAX_STAGES || i >= g_prof_n) return "";
+    return g_cur_names[i] ? g_cur_names[i] : "";
+}
+
+}  // extern "C"

@@ -1,0 +1,333 @@
+// c3_tc.cu -- third-order cumulant contraction on the 5th-generation tensor
+// cores (tcgen05, TMEM accumulators), sm_103a.
+//
+// The sample cumulant c3(w1,w2) = (1/n) sum_i y(i) y(i+w1) y(i+w2) (Problem
+// Statement; biased time average, zero outside the series) is the contraction
+//     C[w1, w2] = sum_i Y[w1, i] * X[i, w2],
+//     Y[w1, i] = y(i) y(i+w1)          (lag-product rows),
+//     X[i, w2] = y(i + w2)             (Hankel matrix of the series).
+//
+// Operands of one tcgen05.mma (M = 128 rows of w1, N = tile_n columns of w2,
+// K = 16 samples for kind::f16, 8 for kind::tf32):
+//   A = Y, built by four "builder" warps in registers and stored straight into
+//       tensor memory (tcgen05.st); the MMA reads A from TMEM, so shared memory
+//       carries only B.
+//   B = X, never expanded.  Eight (bf16) or four (tf32) copies of the 1-D
+//       sample window, each shifted by one sample, are interleaved in 16-byte
+//       blocks: block (q, r) = samples [R*q + r, R*q + r + 16/elt).  In the
+//       no-swizzle K-major canonical layout a core matrix is 8 rows of 16
+//       bytes at a 16-byte pitch, so row n of the core matrix at group q is
+//       block (q, n): the unit shift between Hankel rows falls out of the
+//       layout, with LBO (K direction) and SBO (N direction) equal to the byte
+//       distance of the next 8 (resp. 4) samples.
+//   D = FP32 accumulator, 128 lanes x tile_n columns of TMEM.
+//
+// Precision: y = hi + lo (bf16 pair, or tf32 pair); Y is formed in FP32 and
+// split the same way; three products hi*hi + hi*lo + lo*hi per step.
+//
+// Warp roles (320 threads, one CTA per SM, persistent, stream-K ranges):
+//   warps 0-3 builders (TMEM lane quadrants 0-3), warps 4-7 epilogue,
+//   warp 8 producer (1-D bulk copies + window interleave), warp 9 MMA issuer.
+// Every wait is bounded; on a timeout the CTA records HOS_ERR_TIMEOUT, drains
+// its MMAs, frees TMEM and exits.
+#include "launch.cuh"
+
+namespace hos {
+
+
+// ---- shared-memory plan ------------------------------------------------------
+constexpr int NSTAGE = 4;        // A stages in TMEM (64 columns each)
+constexpr int WIN_SAMPLES = KC + 256 + 16;
+constexpr int WIN_BYTES = WIN_SAMPLES * 16;  // interleaved window, one plane
+constexpr int YA_FLOATS = KC + TILE_M;
+constexpr int YI_FLOATS = KC + 4;
+
+struct __align__(16) C3Smem {
+    uint8_t win_hi[2][WIN_BYTES];
+    uint8_t win_lo[2][WIN_BYTES];
+    float ya[2][YA_FLOATS];
+    float yi[2][YI_FLOATS];
+    uint8_t lin_hi[WIN_SAMPLES * 4];  // linear staging of the hi plane window
+    uint8_t lin_lo[WIN_SAMPLES * 4];
+    uint64_t full_b[2], empty_b[2], full_a[NSTAGE], empty_a[NSTAGE];
+    uint64_t acc_full, acc_empty, drain, tma_bar;
+    uint32_t tmem_base;
+    int abort;
+};
+
+HOS_DEV void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+HOS_DEV void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+template <bool TF32>
+__global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    C3Smem& sm = *reinterpret_cast<C3Smem*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const C3Geom& geo = P.geom;
+    const int N = geo.tile_n;
+    const int L = geo.L;
+    constexpr int ELT = TF32 ? 4 : 2;              // bytes per plane element
+    constexpr int R = 16 / ELT;                    // samples per 16-byte block
+    constexpr int KB = TF32 ? 32 : 64;             // samples per A stage
+    constexpr int KSTEP = TF32 ? 8 : 16;           // samples per MMA
+    constexpr uint32_t GROUP_BYTES = 16u * R;      // bytes per R-sample group
+    constexpr uint32_t LBO = GROUP_BYTES;          // next core matrix along K: +R samples
+    constexpr uint32_t SBO = 16u * 8u;             // next 8 rows along N: +8 samples = 128 bytes
+    const uint32_t idesc = make_idesc(TF32, TILE_M, N);
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&sm.full_b[i], 32);
+            mbar_init(&sm.empty_b[i], 1);
+        }
+        for (int i = 0; i < NSTAGE; ++i) {
+            mbar_init(&sm.full_a[i], 128);
+            mbar_init(&sm.empty_a[i], 1);
+        }
+        mbar_init(&sm.acc_full, 1);
+        mbar_init(&sm.acc_empty, 128);
+        mbar_init(&sm.drain, 1);
+        mbar_init(&sm.tma_bar, 1);
+        sm.abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 9) {
+        tmem_alloc(&sm.tmem_base, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem_base;
+    volatile int* abort = &sm.abort;
+    const uint64_t lim = P.limit_ns;
+
+    Walk walk;
+    walk.init(geo, P.ser, blockIdx.x, gridDim.x);
+    Part part;
+
+    if (warp == 8) {
+        // ------------------------------------------------------------ producer
+        uint32_t kc = 0, tph = 0;
+        bool ok = true;
+        while (ok && walk.next(part)) {
+            const int a = geo.tile_a[part.t], b = geo.tile_b[part.t];
+            const int64_t base = P.ser.pad[part.s];
+            for (int64_t c = part.c0; c < part.c1 && ok; ++c, ++kc) {
+                const int buf = kc & 1;
+                ok = mbar_wait(&sm.empty_b[buf], ((kc >> 1) & 1) ^ 1, abort, P.status, lim);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                const int64_t i0 = c * KC;
+                const int64_t wb = base + i0 + (int64_t)b * N;            // plane index of window start
+                const int64_t ab = base + i0 + (int64_t)a * TILE_M;       // y(i0 + w1_0)
+                const int64_t ib = base + L + i0;                          // y(i0)
+                const int64_t ib_al = ib & ~(int64_t)3;
+                const uint32_t wbytes = (uint32_t)(KC + N + 16) * ELT;
+                if (lane == 0) {
+                    mbar_expect_tx(&sm.tma_bar, 2 * wbytes + YA_FLOATS * 4 + YI_FLOATS * 4);
+                    bulk_g2s(sm.lin_hi, (const uint8_t*)P.hi + wb * ELT, wbytes, &sm.tma_bar);
+                    bulk_g2s(sm.lin_lo, (const uint8_t*)P.lo + wb * ELT, wbytes, &sm.tma_bar);
+                    bulk_g2s(sm.ya[buf], P.y32 + ab, YA_FLOATS * 4, &sm.tma_bar);
+                    bulk_g2s(sm.yi[buf], P.y32 + ib_al, YI_FLOATS * 4, &sm.tma_bar);
+                }
+                ok = mbar_wait(&sm.tma_bar, tph, abort, P.status, lim);
+                tph ^= 1;
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                // interleave: block (q, r) <- samples [R q + r, R q + r + R)
+                const int ngroups = (KC + N) / R + 2;
+                const int nblocks = ngroups * R;
+                for (int blk = lane; blk < nblocks; blk += 32) {
+                    const int q = blk / R, r = blk % R;
+                    const int e0 = R * q + r;  // first sample of the block
+                    uint4 vh, vl;
+                    if constexpr (TF32) {
+                        const uint32_t* sh = reinterpret_cast<const uint32_t*>(sm.lin_hi);
+                        const uint32_t* sl = reinterpret_cast<const uint32_t*>(sm.lin_lo);
+                        vh = make_uint4(sh[e0], sh[e0 + 1], sh[e0 + 2], sh[e0 + 3]);
+                        vl = make_uint4(sl[e0], sl[e0 + 1], sl[e0 + 2], sl[e0 + 3]);
+                    } else {
+                        const uint32_t* sh = reinterpret_cast<const uint32_t*>(sm.lin_hi);
+                        const uint32_t* sl = reinterpret_cast<const uint32_t*>(sm.lin_lo);
+                        const int w0 = e0 >> 1;
+                        const uint32_t sft = (e0 & 1) * 16;
+                        uint32_t h[5], l[5];
+#pragma unroll
+                        for (int k = 0; k < 5; ++k) {
+                            h[k] = sh[w0 + k];
+                            l[k] = sl[w0 + k];
+                        }
+                        vh = make_uint4(__funnelshift_r(h[0], h[1], sft), __funnelshift_r(h[1], h[2], sft),
+                                        __funnelshift_r(h[2], h[3], sft), __funnelshift_r(h[3], h[4], sft));
+                        vl = make_uint4(__funnelshift_r(l[0], l[1], sft), __funnelshift_r(l[1], l[2], sft),
+                                        __funnelshift_r(l[2], l[3], sft), __funnelshift_r(l[3], l[4], sft));
+                    }
+                    *reinterpret_cast<uint4*>(sm.win_hi[buf] + (size_t)blk * 16) = vh;
+                    *reinterpret_cast<uint4*>(sm.win_lo[buf] + (size_t)blk * 16) = vl;
+                }
+                fence_proxy_async_smem();
+                mbar_arrive(&sm.full_b[buf]);
+            }
+        }
+    } else if (warp < 4) {
+        // ------------------------------------------------------------ builders
+        const int m = warp * 32 + lane;  // TMEM lane = row of Y (w1 index in tile)
+        uint32_t kc = 0, ks = 0;
+        bool ok = true;
+        while (ok && walk.next(part)) {
+            const int ishift = (int)((P.ser.pad[part.s] + L) & 3);  // yi staged from an aligned start
+            for (int64_t c = part.c0; c < part.c1 && ok; ++c, ++kc) {
+                const int buf = kc & 1;
+                ok = mbar_wait(&sm.full_b[buf], (kc >> 1) & 1, abort, P.status, lim);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                const float* ya = sm.ya[buf] + m;
+                const float* yi = sm.yi[buf] + ishift;
+                for (int kb = 0; kb < KC / KB; ++kb, ++ks) {
+                    const int st = ks % NSTAGE;
+                    ok = mbar_wait(&sm.empty_a[st], ((ks / NSTAGE) & 1) ^ 1, abort, P.status, lim);
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (!ok) break;
+                    tc_fence_after();  // the MMAs that read this stage have completed
+                    uint32_t H[32], Lw[32];
+                    const float* pa = ya + kb * KB;
+                    const float* pi = yi + kb * KB;
+                    if constexpr (TF32) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float p = pi[j] * pa[j];
+                            const uint32_t h = to_tf32(p);
+                            H[j] = h;
+                            Lw[j] = to_tf32(p - __uint_as_float(h));
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float p0 = pi[2 * j] * pa[2 * j];
+                            const float p1 = pi[2 * j + 1] * pa[2 * j + 1];
+                            const uint32_t h = pack_bf16x2(p0, p1);
+                            H[j] = h;
+                            Lw[j] = pack_bf16x2(p0 - __uint_as_float(h << 16), p1 - __uint_as_float(h & 0xFFFF0000u));
+                        }
+                    }
+                    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + 256u + (uint32_t)st * 64u;
+                    tmem_st32(ta, H);
+                    tmem_st32(ta + 32u, Lw);
+                    tmem_wait_st();
+                    tc_fence_before();
+                    mbar_arrive(&sm.full_a[st]);
+                }
+            }
+        }
+    } else if (warp < 8) {
+        // ------------------------------------------------------------ epilogue
+        const int q = warp - 4;  // lane quadrant
+        const int m = q * 32 + lane;
+        uint32_t it = 0;
+        bool ok = true;
+        while (ok && walk.next(part)) {
+            ok = mbar_wait(&sm.acc_full, it & 1, abort, P.status, lim);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            tc_fence_after();
+            float* dst = P.partials + part.slot * (int64_t)(TILE_M * N) + m;
+            for (int cc = 0; cc < N; cc += 32) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)cc, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) dst[(int64_t)(cc + j) * TILE_M] = __uint_as_float(v[j]);
+            }
+            tc_fence_before();
+            mbar_arrive(&sm.acc_empty);
+            ++it;
+        }
+    } else if (warp == 9 && lane == 0) {
+        // ------------------------------------------------------------ MMA issuer
+        uint32_t kc = 0, ks = 0, it = 0;
+        bool ok = true;
+        const uint32_t wh0 = smem_u32(sm.win_hi[0]), wl0 = smem_u32(sm.win_lo[0]);
+        while (ok && walk.next(part)) {
+            ok = mbar_wait(&sm.acc_empty, (it & 1) ^ 1, abort, P.status, lim);
+            if (!ok) break;
+            tc_fence_after();
+            uint32_t acc = 0;
+            for (int64_t c = part.c0; c < part.c1 && ok; ++c, ++kc) {
+                const int buf = kc & 1;
+                ok = mbar_wait(&sm.full_b[buf], (kc >> 1) & 1, abort, P.status, lim);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t wh = wh0 + (uint32_t)buf * WIN_BYTES, wl = wl0 + (uint32_t)buf * WIN_BYTES;
+                for (int kb = 0; kb < KC / KB; ++kb, ++ks) {
+                    const int st = ks % NSTAGE;
+                    ok = mbar_wait(&sm.full_a[st], (ks / NSTAGE) & 1, abort, P.status, lim);
+                    if (!ok) break;
+                    tc_fence_after();
+#pragma unroll
+                    for (int k = 0; k < KB / KSTEP; ++k) {
+                        const uint32_t a_hi = tmem + 256u + (uint32_t)st * 64u + (uint32_t)k * 8u;
+                        const uint32_t a_lo = a_hi + 32u;
+                        const uint32_t koff = (uint32_t)(kb * KB + k * KSTEP);  // samples into the chunk
+                        const uint32_t boff = (koff / R) * GROUP_BYTES;
+                        const uint64_t bh = make_sdesc(wh + boff, LBO, SBO);
+                        const uint64_t bl = make_sdesc(wl + boff, LBO, SBO);
+                        mma_ts<TF32>(tmem, a_hi, bh, idesc, acc);
+                        acc = 1;
+                        mma_ts<TF32>(tmem, a_hi, bl, idesc, 1);
+                        mma_ts<TF32>(tmem, a_lo, bh, idesc, 1);
+                    }
+                    mma_commit(&sm.empty_a[st]);
+                }
+                mma_commit(&sm.empty_b[buf]);
+            }
+            if (!ok) break;
+            mma_commit(&sm.acc_full);
+            ++it;
+        }
+        // drain every MMA this thread issued before TMEM is released
+        mma_commit(&sm.drain);
+        mbar_wait(&sm.drain, 0, abort, P.status, lim);
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 9) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+template __global__ void c3_tc_kernel<false>(const C3TcParams);
+template __global__ void c3_tc_kernel<true>(const C3TcParams);
+
+cudaError_t launch_c3_tc(bool tf32, const C3TcParams& p, int G, cudaStream_t st) {
+    // at least 116 KB so that exactly one CTA (and one 512-column TMEM
+    // allocation) lands on each SM
+    const size_t smem = sizeof(C3Smem) > 118784 ? sizeof(C3Smem) : 118784;
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[tf32]) {
+        cudaError_t e = tf32 ? cudaFuncSetAttribute(c3_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                             : cudaFuncSetAttribute(c3_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set[tf32] = true;
+    }
+    if (tf32) c3_tc_kernel<true><<<G, 320, smem, st>>>(p);
+    else c3_tc_kernel<false><<<G, 320, smem, st>>>(p);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace hos

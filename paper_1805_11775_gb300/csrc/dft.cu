@@ -1,0 +1,135 @@
+// dft.cu -- transform of the windowed cumulant onto the N-point grid, one axis
+// at a time (the separable form of the 2-D / 3-D DFT), staged in shared memory.
+//
+//   out[k] = sum_e in[e] exp(sign * i 2 pi e k / N)     (sign -1: forward, the
+//   sign of Algorithm DBS step 3; +1: the adjoint)
+//
+// A "line" is one 1-D transform along an axis of a row-major array:
+//   line l starts at (l / inner) * outer_stride + (l % inner), element e at
+//   + e * elem_stride.
+// N a power of two: radix-2 Cooley-Tukey in shared memory (bit-reversed load,
+// log2 N butterfly stages).  Otherwise: direct O(N^2) sum per line.
+// Twiddles tw[k] = exp(-i 2 pi k / N), k < N, from FP64 sincospi, rounded to
+// FP32 once per call.
+#include "launch.cuh"
+
+namespace hos {
+
+__global__ void twiddle_kernel(int N, float2* tw) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    double s, c;
+    sincospi(2.0 * (double)k / (double)N, &s, &c);
+    tw[k] = make_float2((float)c, (float)-s);
+}
+
+
+HOS_DEV int64_t line_base(const LineGeom& g, int64_t l) { return (l / g.inner) * g.outer_stride + (l % g.inner); }
+
+HOS_DEV float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+
+template <bool REAL_IN>
+HOS_DEV float2 load_in(const void* in, int64_t idx) {
+    if constexpr (REAL_IN) return make_float2(reinterpret_cast<const float*>(in)[idx], 0.0f);
+    else return reinterpret_cast<const float2*>(in)[idx];
+}
+
+// in and out may alias (every CTA reads all its lines before writing them).
+template <bool REAL_IN>
+__global__ void fft_lines_kernel(const void* in, float2* out, const LineGeom g, const float2* __restrict__ tw,
+                                 int sign, float scale) {
+    extern __shared__ float2 sbuf[];
+    const int N = g.N, lpb = g.lpb;
+    const int64_t l0 = (int64_t)blockIdx.x * lpb;
+    const int nl = (int)((g.nlines - l0) < lpb ? (g.nlines - l0) : lpb);
+    const int total = nl * N;
+    const bool contiguous = (g.elem_stride == 1);
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int l, e;
+        if (contiguous) { l = idx / N; e = idx % N; }
+        else { e = idx / nl; l = idx % nl; }
+        const float2 v = load_in<REAL_IN>(in, line_base(g, l0 + l) + (int64_t)e * g.elem_stride);
+        const int r = (int)(__brev((unsigned)e) >> (32 - g.log2N));
+        sbuf[l * N + r] = v;
+    }
+    __syncthreads();
+    for (int h = 1; h < N; h <<= 1) {
+        const int tstride = N / (2 * h);
+        for (int bf = threadIdx.x; bf < nl * (N / 2); bf += blockDim.x) {
+            const int l = bf / (N / 2), k = bf % (N / 2);
+            const int j = k % h, blk = k / h;
+            const int i0 = l * N + blk * 2 * h + j, i1 = i0 + h;
+            float2 w = tw[j * tstride];
+            if (sign > 0) w.y = -w.y;
+            const float2 a = sbuf[i0], b = cmul(sbuf[i1], w);
+            sbuf[i0] = make_float2(a.x + b.x, a.y + b.y);
+            sbuf[i1] = make_float2(a.x - b.x, a.y - b.y);
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int l, e;
+        if (contiguous) { l = idx / N; e = idx % N; }
+        else { e = idx / nl; l = idx % nl; }
+        const float2 v = sbuf[l * N + e];
+        out[line_base(g, l0 + l) + (int64_t)e * g.elem_stride] = make_float2(v.x * scale, v.y * scale);
+    }
+}
+
+template <bool REAL_IN>
+__global__ void dft_lines_kernel(const void* in, float2* out, const LineGeom g, const float2* __restrict__ tw,
+                                 int sign, float scale) {
+    extern __shared__ float2 sbuf[];
+    const int N = g.N, lpb = g.lpb;
+    const int64_t l0 = (int64_t)blockIdx.x * lpb;
+    const int nl = (int)((g.nlines - l0) < lpb ? (g.nlines - l0) : lpb);
+    const int total = nl * N;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int l = idx / N, e = idx % N;
+        sbuf[idx] = load_in<REAL_IN>(in, line_base(g, l0 + l) + (int64_t)e * g.elem_stride);
+    }
+    __syncthreads();
+    float2* res = sbuf + lpb * N;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int l = idx / N, k = idx % N;
+        float ax = 0.0f, ay = 0.0f;
+        for (int e = 0; e < N; ++e) {
+            float2 w = tw[(int)(((int64_t)e * k) % N)];
+            if (sign > 0) w.y = -w.y;
+            const float2 v = sbuf[l * N + e];
+            ax += v.x * w.x - v.y * w.y;
+            ay += v.x * w.y + v.y * w.x;
+        }
+        res[idx] = make_float2(ax * scale, ay * scale);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int l = idx / N, e = idx % N;
+        out[line_base(g, l0 + l) + (int64_t)e * g.elem_stride] = res[idx];
+    }
+}
+
+cudaError_t launch_twiddles(int N, float2* tw, cudaStream_t st) {
+    twiddle_kernel<<<(unsigned)ceil_div(N, 256), 256, 0, st>>>(N, tw);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lines(bool real_in, const void* in, float2* out, LineGeom g, const float2* tw, int sign,
+                         float scale, cudaStream_t st) {
+    if (g.nlines <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)ceil_div(g.nlines, g.lpb);
+    if (g.log2N >= 0) {
+        const size_t smem = (size_t)g.lpb * g.N * sizeof(float2);
+        if (real_in) fft_lines_kernel<true><<<blocks, 256, smem, st>>>(in, out, g, tw, sign, scale);
+        else fft_lines_kernel<false><<<blocks, 256, smem, st>>>(in, out, g, tw, sign, scale);
+    } else {
+        const size_t smem = 2 * (size_t)g.lpb * g.N * sizeof(float2);
+        if (real_in) dft_lines_kernel<true><<<blocks, 256, smem, st>>>(in, out, g, tw, sign, scale);
+        else dft_lines_kernel<false><<<blocks, 256, smem, st>>>(in, out, g, tw, sign, scale);
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace hos

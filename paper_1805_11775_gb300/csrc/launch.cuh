@@ -1,0 +1,71 @@
+// launch.cuh -- parameter blocks of the kernels and the host-side launch
+// wrappers the ABI layer calls.  Each wrapper enqueues on `stream`, counts the
+// launch, and returns the launch error.
+#pragma once
+
+#include "hos_internal.cuh"
+
+namespace hos {
+
+struct C3TcParams {
+    C3Geom geom;
+    SeriesView ser;
+    const float* y32;
+    const void* hi;
+    const void* lo;
+    float* partials;
+    int* status;
+    uint64_t limit_ns;
+};
+
+struct C3SimtParams {
+    C3Geom geom;
+    SeriesView ser;
+    const float* y32;
+    float* partials;
+};
+
+// mode 0: spectrum input grid[g][(w2 mod Nf)][(w1 mod Nf)] = scale * W * c3 (fp32)
+// mode 1: raw cumulant c3out[g][w2+L][w1+L] (fp64, symmetric so also [w1][w2])
+struct Reduce3Params {
+    C3Geom geom;
+    SeriesView ser;
+    const float* partials;
+    int window;
+    int nfft;
+    int mode;
+    int per_series_groups;
+    double scale;
+    float* grid;
+    double* c3out;
+};
+
+struct LineGeom {
+    int N;
+    int log2N;  // -1 when N is not a power of two
+    int64_t nlines;
+    int64_t inner;
+    int64_t outer_stride;
+    int64_t elem_stride;
+    int lpb;  // lines per CTA
+};
+
+void count_launch();
+
+cudaError_t launch_plan_series(int mode, int64_t n, int64_t seg, const int64_t* d_user_off, int S, int L, int ntiles,
+                               int flush, int pad_tail, int64_t* off, int64_t* pad, int64_t* unit, int64_t* win,
+                               cudaStream_t st);
+cudaError_t launch_mean(const void* x, int dtype, const int64_t* off, int S, int nslices, double* part,
+                        int remove_mean, double* mean, cudaStream_t st);
+cudaError_t launch_planes(const void* x, int dtype, const int64_t* off, const int64_t* pad, const double* mean, int L,
+                          int split, float* y32, void* hi, void* lo, int S, int blocks_x, cudaStream_t st);
+cudaError_t launch_c3_tc(bool tf32, const C3TcParams& p, int G, cudaStream_t st);
+cudaError_t launch_c3_simt(const C3SimtParams& p, int G, cudaStream_t st);
+cudaError_t launch_reduce3(const Reduce3Params& p, int groups, cudaStream_t st);
+cudaError_t launch_zero_f32(float* p, int64_t n, cudaStream_t st);
+cudaError_t launch_twiddles(int N, float2* tw, cudaStream_t st);
+cudaError_t launch_lines(bool real_in, const void* in, float2* out, LineGeom g, const float2* tw, int sign,
+                         float scale, cudaStream_t st);
+cudaError_t launch_timeout_selftest(int* status, uint64_t limit_ns, cudaStream_t st);
+
+}  // namespace hos

@@ -1,0 +1,179 @@
+// prep.cu -- series layout planning and mean removal (Algorithm DBS steps 1-2).
+//
+// plan_series_kernel : per-series offsets, zero-padded block starts, work-unit
+//                      and flush-window prefix sums (one block, scan).
+// mean_partial_kernel / mean_final_kernel : FP64 per-series mean, two-level
+//                      tree, fixed order (deterministic).
+// planes_kernel      : y = x - mean into the padded sample planes: FP32 y, and
+//                      its hi/lo split (bf16 pair, or tf32-rounded FP32 pair).
+#include "launch.cuh"
+
+namespace hos {
+
+// Block-wide exclusive scan of int64 over blockDim.x <= 1024 values.
+__device__ int64_t block_exclusive_scan(int64_t v, int64_t* sh, int64_t* total) {
+    const int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int d = 1; d < blockDim.x; d <<= 1) {
+        int64_t a = (t >= d) ? sh[t - d] : 0;
+        __syncthreads();
+        sh[t] += a;
+        __syncthreads();
+    }
+    int64_t incl = sh[t];
+    *total = sh[blockDim.x - 1];
+    __syncthreads();
+    return incl - v;
+}
+
+// mode 0: single series of n samples cut into parts of seg (seg <= 0: one part)
+// mode 1: S series given by device offsets d_user_off[S+1]
+__global__ void plan_series_kernel(int mode, int64_t n, int64_t seg, const int64_t* __restrict__ d_user_off, int S,
+                                   int L, int ntiles, int flush, int pad_tail, int64_t* off, int64_t* pad,
+                                   int64_t* unit, int64_t* win) {
+    __shared__ int64_t sh[1024];
+    __shared__ int64_t carry[3];
+    if (threadIdx.x == 0) carry[0] = carry[1] = carry[2] = 0;
+    __syncthreads();
+    for (int base = 0; base < S; base += blockDim.x) {
+        const int s = base + threadIdx.x;
+        int64_t o0 = 0, o1 = 0;
+        if (s < S) {
+            if (mode == 0) {
+                o0 = (seg > 0) ? (int64_t)s * seg : 0;
+                o1 = (seg > 0) ? ((int64_t)(s + 1) * seg < n ? (int64_t)(s + 1) * seg : n) : n;
+            } else {
+                o0 = d_user_off[s];
+                o1 = d_user_off[s + 1];
+            }
+        }
+        const int64_t len = (s < S && o1 > o0) ? (o1 - o0) : 0;
+        const int64_t nch = ceil_div(len, KC);
+        const int64_t plen = (s < S) ? round_up((int64_t)L + nch * KC + pad_tail, 64) : 0;
+        const int64_t nu = (int64_t)ntiles * nch;
+        const int64_t nw = (int64_t)ntiles * ceil_div(nch, flush);
+        int64_t tot;
+        const int64_t ep = block_exclusive_scan(plen, sh, &tot);
+        const int64_t c0 = carry[0];
+        __syncthreads();
+        if (s < S) pad[s] = c0 + ep;
+        if (threadIdx.x == 0) carry[0] = c0 + tot;
+        __syncthreads();
+        const int64_t eu = block_exclusive_scan(nu, sh, &tot);
+        const int64_t c1 = carry[1];
+        __syncthreads();
+        if (s < S) unit[s] = c1 + eu;
+        if (threadIdx.x == 0) carry[1] = c1 + tot;
+        __syncthreads();
+        const int64_t ew = block_exclusive_scan(nw, sh, &tot);
+        const int64_t c2 = carry[2];
+        __syncthreads();
+        if (s < S) {
+            win[s] = c2 + ew;
+            off[s] = o0;
+        }
+        if (threadIdx.x == 0) carry[2] = c2 + tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        pad[S] = carry[0];
+        unit[S] = carry[1];
+        win[S] = carry[2];
+        off[S] = (mode == 0) ? n : d_user_off[S];
+    }
+}
+
+// Partial sums of each series: blockIdx.y = series, blockIdx.x = slice.
+template <typename T>
+__global__ void mean_partial_kernel(const T* __restrict__ x, const int64_t* __restrict__ off, int nslices,
+                                    double* __restrict__ part) {
+    __shared__ double sh[256];
+    const int s = blockIdx.y;
+    const int64_t o0 = off[s], len = off[s + 1] - o0;
+    const int64_t per = ceil_div(len, nslices);
+    const int64_t b0 = (int64_t)blockIdx.x * per;
+    const int64_t b1 = b0 + per < len ? b0 + per : len;
+    double acc = 0.0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) acc += (double)x[o0 + i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int d = blockDim.x / 2; d > 0; d >>= 1) {
+        if (threadIdx.x < d) sh[threadIdx.x] += sh[threadIdx.x + d];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(int64_t)s * nslices + blockIdx.x] = sh[0];
+}
+
+__global__ void mean_final_kernel(const double* __restrict__ part, const int64_t* __restrict__ off, int S,
+                                  int nslices, int remove_mean, double* __restrict__ mean) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int64_t len = off[s + 1] - off[s];
+    double acc = 0.0;
+    for (int k = 0; k < nslices; ++k) acc += part[(int64_t)s * nslices + k];
+    mean[s] = (remove_mean && len > 0) ? acc / (double)len : 0.0;
+}
+
+// y = x - mean into the padded planes.  blockIdx.y = series; the block's
+// x-slices stride over that series' padded block [pad[s], pad[s+1]).
+// split: 0 = none (f32 plane only), 1 = bf16 hi/lo, 2 = tf32 hi/lo (as f32).
+template <typename T>
+__global__ void planes_kernel(const T* __restrict__ x, const int64_t* __restrict__ off,
+                              const int64_t* __restrict__ pad, const double* __restrict__ mean, int L, int split,
+                              float* __restrict__ y32, void* __restrict__ hi, void* __restrict__ lo) {
+    const int s = blockIdx.y;
+    const int64_t p0 = pad[s], p1 = pad[s + 1];
+    const int64_t o0 = off[s], len = off[s + 1] - o0;
+    const double mu = mean[s];
+    for (int64_t p = p0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < p1;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = p - p0 - L;
+        float v = 0.0f;
+        if (i >= 0 && i < len) v = (float)((double)x[o0 + i] - mu);
+        y32[p] = v;
+        if (split == 1) {
+            __nv_bfloat16* h = reinterpret_cast<__nv_bfloat16*>(hi);
+            __nv_bfloat16* l = reinterpret_cast<__nv_bfloat16*>(lo);
+            const __nv_bfloat16 hb = __float2bfloat16_rn(v);
+            h[p] = hb;
+            l[p] = __float2bfloat16_rn(v - __bfloat162float(hb));
+        } else if (split == 2) {
+            const uint32_t hb = to_tf32(v);
+            reinterpret_cast<uint32_t*>(hi)[p] = hb;
+            reinterpret_cast<uint32_t*>(lo)[p] = to_tf32(v - __uint_as_float(hb));
+        }
+    }
+}
+
+cudaError_t launch_plan_series(int mode, int64_t n, int64_t seg, const int64_t* d_user_off, int S, int L, int ntiles,
+                               int flush, int pad_tail, int64_t* off, int64_t* pad, int64_t* unit, int64_t* win,
+                               cudaStream_t st) {
+    plan_series_kernel<<<1, 1024, 0, st>>>(mode, n, seg, d_user_off, S, L, ntiles, flush, pad_tail, off, pad, unit, win);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mean(const void* x, int dtype, const int64_t* off, int S, int nslices, double* part,
+                        int remove_mean, double* mean, cudaStream_t st) {
+    dim3 g1((unsigned)nslices, (unsigned)S);
+    if (dtype == HOS_F64) mean_partial_kernel<double><<<g1, 256, 0, st>>>((const double*)x, off, nslices, part);
+    else mean_partial_kernel<float><<<g1, 256, 0, st>>>((const float*)x, off, nslices, part);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    mean_final_kernel<<<(unsigned)ceil_div(S, 256), 256, 0, st>>>(part, off, S, nslices, remove_mean, mean);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_planes(const void* x, int dtype, const int64_t* off, const int64_t* pad, const double* mean, int L,
+                          int split, float* y32, void* hi, void* lo, int S, int blocks_x, cudaStream_t st) {
+    dim3 g((unsigned)blocks_x, (unsigned)S);
+    if (dtype == HOS_F64) planes_kernel<double><<<g, 256, 0, st>>>((const double*)x, off, pad, mean, L, split, y32, hi, lo);
+    else planes_kernel<float><<<g, 256, 0, st>>>((const float*)x, off, pad, mean, L, split, y32, hi, lo);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace hos

@@ -1,0 +1,92 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds for
+sm_103a, loads, exports every entry point include/hos.h declares, and
+rejects bad arguments synchronously without touching the device."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hos.h")
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                                reason="nvcc not available")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1805_11775_gb300 import build, _native
+    build.build()
+    return _native.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hos_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_header():
+    from paper_1805_11775_gb300 import _native
+    assert set(declared_functions()) == set(_native._SIGS)
+
+
+def test_params_struct_matches_header():
+    from paper_1805_11775_gb300 import _native
+    text = open(HEADER).read()
+    body = text[text.index("typedef struct {"):text.index("} hos_params;")]
+    fields = re.findall(r"int32_t\s+(\w+);", body)
+    assert [f for f, _ in _native.HosParams._fields_] == fields
+
+
+def _params(**kw):
+    from paper_1805_11775_gb300 import make_params
+    return make_params(**kw)
+
+
+def test_status_strings(lib):
+    for s in range(7):
+        assert lib.hos_status_string(s)
+    assert b"sm_103a" in lib.hos_version()
+
+
+def test_invalid_arguments_return_synchronously(lib):
+    from paper_1805_11775_gb300 import _native
+    p = _params(L=32)
+    dummy = ctypes.c_void_p(0x1000)
+    # null pointers, bad sizes, bad dtype: rejected before any CUDA call
+    assert lib.hos_bispectrum(None, 1, 100, ctypes.byref(p), dummy, dummy, 1 << 20, None) == 1
+    assert lib.hos_bispectrum(dummy, 7, 100, ctypes.byref(p), dummy, dummy, 1 << 20, None) == 1
+    assert lib.hos_bispectrum(dummy, 1, 0, ctypes.byref(p), dummy, dummy, 1 << 20, None) == 1
+    for bad in (dict(L=0), dict(L=32, nfft=10), dict(L=32, precision=9), dict(L=32, window=5),
+                dict(L=32, tile_n=48), dict(L=32, segment_len=-1)):
+        q = _params(**bad)
+        assert lib.hos_bispectrum(dummy, 1, 100, ctypes.byref(q), dummy, dummy, 1 << 20, None) == 1, bad
+    big = _params(L=2048)
+    assert lib.hos_bispectrum(dummy, 1, 100, ctypes.byref(big), dummy, dummy, 1 << 20, None) == 2
+    # workspace too small
+    assert lib.hos_bispectrum(dummy, 1, 100, ctypes.byref(p), dummy, dummy, 16, None) == 3
+    assert lib.hos_bispectrum_batched(dummy, 1, None, 3, 10, 5, ctypes.byref(p), dummy, dummy, 1 << 30, None) == 1
+    assert lib.hos_get_device_status(None, None) == 1
+    assert _native.STATUS_NAMES[3] == "HOS_ERR_WORKSPACE"
+
+
+def test_workspace_size_grows_with_the_problem(lib):
+    from paper_1805_11775_gb300 import workspace_size, _native
+    p = _params(L=256)
+    a = workspace_size(_native.OP_BISPECTRUM, 1 << 16, 1, 1 << 16, p)
+    b = workspace_size(_native.OP_BISPECTRUM, 1 << 21, 1, 1 << 21, p)
+    assert 0 < a < b
+    c = workspace_size(_native.OP_BISPECTRUM_BATCHED, 45_000_000, 4096, 20000, _params(L=128))
+    assert c > 4096 * 256 * 256 * 4  # at least the transform grid
+    # the full-size long workload stays far below the device memory
+    assert b < 2 << 30

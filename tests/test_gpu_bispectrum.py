@@ -1,0 +1,215 @@
+"""GPU parity of the bispectrum path (C ABI -> sm_103a kernels) against the
+FP64 oracle.
+
+Tolerances (normwise: max |got - ref| / max |ref| per output tensor), as the
+accuracy targets of the three contraction precisions:
+  split-bf16 tensor cores 1e-4; 3xTF32 tensor cores 1e-5; FP32 SIMT 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import hos_synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no GPU", allow_module_level=True)
+
+TOL = {"bf16": 1e-4, "fp32": 1e-5, "simt": 1e-5}
+PRECS = ["simt", "fp32", "bf16"]
+TWO_PI = 2 * math.pi
+
+
+@pytest.fixture(scope="module")
+def hos():
+    from paper_1805_11775_gb300 import build
+    build.build()
+    import paper_1805_11775_gb300 as h
+    return h
+
+
+def normwise(got, ref):
+    d = np.abs(np.asarray(got, dtype=np.complex128) - ref).max()
+    s = np.abs(ref).max()
+    return d / s if s > 0 else d
+
+
+def lag_slice(c_oracle, L):
+    """Oracle c3 over [-L, L]^2 -> the library's [-L, L-1]^2 layout."""
+    return c_oracle[:2 * L, :2 * L]
+
+
+# ------------------------------------------------------------- workload 1
+@pytest.mark.parametrize("prec", PRECS)
+def test_bispectrum_n2048_L32(hos, oracle, prec):
+    w = hos_synth.workload("bispectrum_n2048_L32")
+    ref = oracle.bispectrum(w["x"], w["L"], w["N"])
+    got = hos.bispectrum(torch.from_numpy(w["x"]).cuda(), w["L"], precision=prec).cpu().numpy()
+    assert normwise(got, ref) <= TOL[prec]
+    assert hos.device_status() == 0
+
+
+# ------------------------------------------------------------- cumulant, tiles, ragged tails
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,L", [(1, 1), (2, 3), (3, 1), (7, 2), (100, 64), (1500, 31), (5000, 32),
+                                 (3000, 128), (2600, 200), (9000, 256)])
+def test_cumulant3_elementwise(hos, oracle, prec, n, L):
+    x = hos_synth.ar2(n, 10 * n + L)
+    ref = lag_slice(oracle.c3(oracle.demean(x), L), L)
+    got = hos.cumulant3(torch.from_numpy(x).cuda(), L, precision=prec).cpu().numpy()
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= TOL[prec] * scale + 1e-300
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,L,N,window", [(1500, 31, 64, "parzen"), (3000, 128, 256, "parzen"),
+                                          (2600, 50, 100, "parzen"), (800, 12, 40, "parzen_sym"),
+                                          (800, 12, 24, "rect"), (4100, 256, 512, "parzen")])
+def test_bispectrum_elementwise(hos, oracle, prec, n, L, N, window):
+    x = hos_synth.ma(n, 77 + n)
+    wk = {"parzen": oracle.WIN_PARZEN, "parzen_sym": oracle.WIN_PARZEN_SYM, "rect": oracle.WIN_RECT}[window]
+    ref = oracle.bispectrum(x, L, N, window=wk)
+    got = hos.bispectrum(torch.from_numpy(x).cuda(), L, nfft=N, precision=prec, window=window).cpu().numpy()
+    assert normwise(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("tile_n,flush", [(128, 1), (256, 3), (64, 2)])
+def test_tile_and_flush_variants_agree(hos, oracle, tile_n, flush):
+    x = hos_synth.ar2(7000, 5)
+    L = 100
+    ref = lag_slice(oracle.c3(oracle.demean(x), L), L)
+    for prec in ("bf16", "fp32"):
+        got = hos.cumulant3(torch.from_numpy(x).cuda(), L, precision=prec, tile_n=tile_n,
+                            flush_chunks=flush).cpu().numpy()
+        assert np.abs(got - ref).max() <= TOL[prec] * np.abs(ref).max()
+
+
+def test_float32_input_and_no_mean_removal(hos, oracle):
+    x = (hos_synth.exp_noise(3000, 3) + 0.25).astype(np.float32)
+    for rm in (True, False):
+        ref = oracle.bispectrum(x.astype(np.float64), 40, 80, remove_mean=rm)
+        got = hos.bispectrum(torch.from_numpy(x).cuda(), 40, precision="fp32", remove_mean=rm).cpu().numpy()
+        assert normwise(got, ref) <= 1e-5
+
+
+def test_segments_average(hos, oracle):
+    x = hos_synth.ar2(10_000, 8)
+    ref = oracle.bispectrum(x, 24, 48, segment_len=3000)
+    for prec in PRECS:
+        got = hos.bispectrum(torch.from_numpy(x).cuda(), 24, precision=prec, segment_len=3000).cpu().numpy()
+        assert normwise(got, ref) <= TOL[prec]
+
+
+def test_zero_and_nan_inputs(hos):
+    z = torch.zeros(5000, dtype=torch.float64, device="cuda")
+    for prec in PRECS:
+        assert torch.count_nonzero(hos.bispectrum(z, 32, precision=prec)).item() == 0
+    x = torch.from_numpy(hos_synth.exp_noise(5000, 1)).cuda()
+    x[1234] = float("nan")
+    B = hos.bispectrum(x, 32, precision="bf16")
+    assert torch.isnan(B.real).any()
+
+
+def test_deterministic(hos):
+    x = torch.from_numpy(hos_synth.ar2(50_000, 2)).cuda()
+    for prec in PRECS:
+        a = hos.bispectrum(x, 128, precision=prec)
+        b = hos.bispectrum(x, 128, precision=prec)
+        assert torch.equal(a, b)
+
+
+# ------------------------------------------------------------- batching
+def test_batched_matches_oracle_per_series(hos, oracle):
+    lens = np.array([0, 1, 700, 2500, 1024, 3100, 17, 2048], dtype=np.int64)
+    vals, offs = hos_synth.student_t_returns(lens, 11)
+    L, N = 40, 80
+    for prec in PRECS:
+        got = hos.bispectrum_batched(torch.from_numpy(vals).cuda(), torch.from_numpy(offs), L,
+                                     precision=prec).cpu().numpy()
+        for s in range(lens.size):
+            seg = vals[offs[s]:offs[s + 1]]
+            if seg.size == 0:
+                assert np.count_nonzero(got[s]) == 0
+                continue
+            ref = oracle.bispectrum(seg, L, N)
+            assert normwise(got[s], ref) <= TOL[prec], (prec, s)
+
+
+def test_batched_equals_single_calls(hos):
+    lens = hos_synth.intraday_lengths(24, 4)
+    vals, offs = hos_synth.student_t_returns(lens, 4)
+    xb = torch.from_numpy(vals).cuda()
+    Bb = hos.bispectrum_batched(xb, torch.from_numpy(offs), 128, precision="bf16")
+    for s in range(0, 24, 5):
+        Bs = hos.bispectrum(xb[offs[s]:offs[s + 1]].contiguous(), 128, precision="bf16")
+        assert normwise(Bb[s].cpu().numpy(), Bs.cpu().numpy().astype(np.complex128)) <= 2e-5
+
+
+# ------------------------------------------------------------- long workload at full size
+@pytest.fixture(scope="module")
+def long_inputs():
+    w = hos_synth.workload("long_bispectrum_n2M_L256")
+    return w
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_long_full_size_sampled_lags(hos, oracle, long_inputs, prec):
+    """n = 2^21, L = 256: lags sampled over the whole square (including every
+    tile, the mirrored ones and the boundary lags) against the oracle's
+    per-lag sums."""
+    x, L = long_inputs["x"], long_inputs["L"]
+    y = oracle.demean(x)
+    rng = np.random.default_rng(0)
+    lags = np.concatenate([rng.integers(-L, L, size=(40, 2)),
+                           np.array([[0, 0], [-L, -L], [L - 1, L - 1], [-L, L - 1], [L - 1, -L], [1, 2], [2, 1],
+                                     [-5, 7], [200, -100], [-100, 200]])])
+    ref = oracle.c3_at(y, lags)
+    got = hos.cumulant3(torch.from_numpy(x).cuda(), L, precision=prec).cpu().numpy()
+    g = got[lags[:, 0] + L, lags[:, 1] + L]
+    assert np.abs(g - ref).max() <= TOL[prec] * abs(oracle.c3_at(y, [[0, 0]])[0])
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_long_full_size_spectrum_properties(hos, oracle, long_inputs, prec):
+    """At full size the transform is checked through properties that hold at
+    any size: Hermitian symmetry, B(k1,k2) = B(k2,k1), and the inverse
+    transform at sampled lags equals (2 pi)^-2 W(w) c3(w) from the oracle."""
+    x, L, N = long_inputs["x"], long_inputs["L"], long_inputs["N"]
+    B = hos.bispectrum(torch.from_numpy(x).cuda(), L, precision=prec).cpu().numpy().astype(np.complex128)
+    k = np.arange(N)
+    scale = np.abs(B).max()
+    assert np.abs(B[(-k[:, None]) % N, (-k[None, :]) % N] - np.conj(B)).max() <= 1e-6 * scale
+    assert np.abs(B - B.T).max() <= 1e-6 * scale
+    y = oracle.demean(x)
+    lags = np.array([[0, 0], [1, 0], [3, -2], [10, 20], [-40, 17], [100, 101], [-200, 50], [250, -250]])
+    ref = oracle.c3_at(y, lags) * np.array([oracle.window2(a, b, L) for a, b in lags]) / TWO_PI ** 2
+    ph = np.exp(2j * np.pi * (np.outer(lags[:, 0], k)[:, :, None] + np.outer(lags[:, 1], k)[:, None, :]) / N)
+    inv = (B[None, :, :] * ph).sum(axis=(1, 2)).real / (N * N)
+    assert np.abs(inv - ref).max() <= TOL[prec] * abs(ref[0])
+
+
+# ------------------------------------------------------------- failure detection, tracing
+def test_device_timeout_is_reported_without_a_fault(hos):
+    assert hos.selftest_timeout(2000) == 5  # HOS_ERR_TIMEOUT
+    hos.reset_device_status()
+    torch.cuda.synchronize()
+    assert hos.device_status() == 0
+    x = torch.from_numpy(hos_synth.exp_noise(4096, 9)).cuda()
+    B = hos.bispectrum(x, 32)
+    torch.cuda.synchronize()
+    assert torch.isfinite(B.real).all() and hos.device_status() == 0
+
+
+def test_stage_times_and_launch_count(hos):
+    x = torch.from_numpy(hos_synth.exp_noise(100_000, 9)).cuda()
+    n0 = hos.launch_count()
+    hos.set_profiling(True)
+    hos.bispectrum(x, 64, precision="bf16")
+    st = hos.stage_times()
+    hos.set_profiling(False)
+    assert [s for s, _ in st] == ["prep", "contract", "reduce", "transform"]
+    assert all(ms >= 0 for _, ms in st)
+    assert hos.launch_count() - n0 >= 7
+    assert hos.last_contraction() == "c3_tcgen05_split_bf16"
