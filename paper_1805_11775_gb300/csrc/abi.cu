@@ -127,7 +127,12 @@ static C3Geom make_geom(const hos_params* p, int G) {
             ++cnt;
         }
     g.ntiles = cnt;
-    g.flush = p->flush_chunks ? p->flush_chunks : 16;
+    // The tensor cores' FP32 accumulation loses a little on every MMA step, one-sidedly,
+    // so its error grows with the steps one partial accumulates.  The 3xTF32 path
+    // (8 samples per step) hands its partial to the FP64 reduction after every
+    // 1024-sample chunk; split-bf16 (16 samples per step, 1e-4 target) and SIMT
+    // (FP32 FFMA, round to nearest) after 16 chunks.
+    g.flush = p->flush_chunks ? p->flush_chunks : (p->precision == HOS_PREC_FP32 ? 1 : 16);
     g.G = G;
     const int reach = (g.tiles_m * TILE_M > g.tiles_n * N) ? g.tiles_m * TILE_M : g.tiles_n * N;
     g.pad_tail = reach + 64;

@@ -46,7 +46,8 @@ struct __align__(16) C3Smem {
     uint8_t win_hi[2][WIN_BYTES];
     uint8_t win_lo[2][WIN_BYTES];
     float ya[2][YA_FLOATS];
-    float yi[2][YI_FLOATS];
+    float yi[2][KC];                  // y(i0 + t), 16-byte aligned for broadcast loads
+    float yi_raw[YI_FLOATS];          // staging: copied from an aligned global start
     uint8_t lin_hi[WIN_SAMPLES * 4];  // linear staging of the hi plane window
     uint8_t lin_lo[WIN_SAMPLES * 4];
     uint64_t full_b[2], empty_b[2], full_a[NSTAGE], empty_a[NSTAGE];
@@ -126,8 +127,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
             const int64_t base = P.ser.pad[part.s];
             for (int64_t c = part.c0; c < part.c1 && ok; ++c, ++kc) {
                 const int buf = kc & 1;
-                ok = mbar_wait(&sm.empty_b[buf], ((kc >> 1) & 1) ^ 1, abort, P.status, lim);
-                ok = __all_sync(0xffffffffu, ok);
+                ok = warp_wait(&sm.empty_b[buf], ((kc >> 1) & 1) ^ 1, abort, P.status, lim, 2000);
                 if (!ok) break;
                 const int64_t i0 = c * KC;
                 const int64_t wb = base + i0 + (int64_t)b * N;            // plane index of window start
@@ -140,12 +140,15 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                     bulk_g2s(sm.lin_hi, (const uint8_t*)P.hi + wb * ELT, wbytes, &sm.tma_bar);
                     bulk_g2s(sm.lin_lo, (const uint8_t*)P.lo + wb * ELT, wbytes, &sm.tma_bar);
                     bulk_g2s(sm.ya[buf], P.y32 + ab, YA_FLOATS * 4, &sm.tma_bar);
-                    bulk_g2s(sm.yi[buf], P.y32 + ib_al, YI_FLOATS * 4, &sm.tma_bar);
+                    bulk_g2s(sm.yi_raw, P.y32 + ib_al, YI_FLOATS * 4, &sm.tma_bar);
                 }
-                ok = mbar_wait(&sm.tma_bar, tph, abort, P.status, lim);
+                ok = warp_wait(&sm.tma_bar, tph, abort, P.status, lim, 1000);
                 tph ^= 1;
-                ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
+                {   // realign y(i0 + t) so that builders can use 16-byte broadcast loads
+                    const int ish = (int)(ib - ib_al);
+                    for (int t = lane; t < KC; t += 32) sm.yi[buf][t] = sm.yi_raw[ish + t];
+                }
                 // interleave: block (q, r) <- samples [R q + r, R q + r + R)
                 const int ngroups = (KC + N) / R + 2;
                 const int nblocks = ngroups * R;
@@ -187,39 +190,46 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
         uint32_t kc = 0, ks = 0;
         bool ok = true;
         while (ok && walk.next(part)) {
-            const int ishift = (int)((P.ser.pad[part.s] + L) & 3);  // yi staged from an aligned start
             for (int64_t c = part.c0; c < part.c1 && ok; ++c, ++kc) {
                 const int buf = kc & 1;
-                ok = mbar_wait(&sm.full_b[buf], (kc >> 1) & 1, abort, P.status, lim);
-                ok = __all_sync(0xffffffffu, ok);
+                ok = warp_wait(&sm.full_b[buf], (kc >> 1) & 1, abort, P.status, lim, 2000);
                 if (!ok) break;
                 const float* ya = sm.ya[buf] + m;
-                const float* yi = sm.yi[buf] + ishift;
+                const float* yi = sm.yi[buf];
                 for (int kb = 0; kb < KC / KB; ++kb, ++ks) {
                     const int st = ks % NSTAGE;
-                    ok = mbar_wait(&sm.empty_a[st], ((ks / NSTAGE) & 1) ^ 1, abort, P.status, lim);
-                    ok = __all_sync(0xffffffffu, ok);
+                    ok = warp_wait(&sm.empty_a[st], ((ks / NSTAGE) & 1) ^ 1, abort, P.status, lim, 1000);
                     if (!ok) break;
                     tc_fence_after();  // the MMAs that read this stage have completed
                     uint32_t H[32], Lw[32];
                     const float* pa = ya + kb * KB;
                     const float* pi = yi + kb * KB;
+                    const float4* pi4 = reinterpret_cast<const float4*>(pi);
                     if constexpr (TF32) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const float p = pi[j] * pa[j];
-                            const uint32_t h = to_tf32(p);
-                            H[j] = h;
-                            Lw[j] = to_tf32(p - __uint_as_float(h));
+                        for (int q = 0; q < 8; ++q) {
+                            const float4 v = pi4[q];
+                            const float pv[4] = {v.x * pa[4 * q], v.y * pa[4 * q + 1], v.z * pa[4 * q + 2],
+                                                 v.w * pa[4 * q + 3]};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const uint32_t h = to_tf32(pv[e]);
+                                H[4 * q + e] = h;
+                                Lw[4 * q + e] = to_tf32(pv[e] - __uint_as_float(h));
+                            }
                         }
                     } else {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const float p0 = pi[2 * j] * pa[2 * j];
-                            const float p1 = pi[2 * j + 1] * pa[2 * j + 1];
-                            const uint32_t h = pack_bf16x2(p0, p1);
-                            H[j] = h;
-                            Lw[j] = pack_bf16x2(p0 - __uint_as_float(h << 16), p1 - __uint_as_float(h & 0xFFFF0000u));
+                        for (int q = 0; q < 16; ++q) {
+                            const float4 v = pi4[q];
+                            const float p0 = v.x * pa[4 * q], p1 = v.y * pa[4 * q + 1];
+                            const float p2 = v.z * pa[4 * q + 2], p3 = v.w * pa[4 * q + 3];
+                            const uint32_t h0 = pack_bf16x2(p0, p1), h1 = pack_bf16x2(p2, p3);
+                            H[2 * q] = h0;
+                            H[2 * q + 1] = h1;
+                            Lw[2 * q] = pack_bf16x2(p0 - __uint_as_float(h0 << 16), p1 - __uint_as_float(h0 & 0xFFFF0000u));
+                            Lw[2 * q + 1] =
+                                pack_bf16x2(p2 - __uint_as_float(h1 << 16), p3 - __uint_as_float(h1 & 0xFFFF0000u));
                         }
                     }
                     const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + 256u + (uint32_t)st * 64u;
@@ -238,8 +248,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
         uint32_t it = 0;
         bool ok = true;
         while (ok && walk.next(part)) {
-            ok = mbar_wait(&sm.acc_full, it & 1, abort, P.status, lim);
-            ok = __all_sync(0xffffffffu, ok);
+            ok = warp_wait(&sm.acc_full, it & 1, abort, P.status, lim, 20000);
             if (!ok) break;
             tc_fence_after();
             float* dst = P.partials + part.slot * (int64_t)(TILE_M * N) + m;

@@ -176,13 +176,24 @@ HOS_DEV void mbar_arrive(uint64_t* bar) {
                  : "memory");
 }
 
-HOS_DEV bool mbar_try(uint64_t* bar, uint32_t parity) {
+// Test the phase; the thread may be suspended up to hint_ns waiting for it.
+HOS_DEV bool mbar_try(uint64_t* bar, uint32_t parity, uint32_t hint_ns = 0) {
     uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
+    if (hint_ns) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+    }
     return ok != 0;
 }
 
@@ -190,12 +201,13 @@ HOS_DEV bool mbar_try(uint64_t* bar, uint32_t parity) {
 // false) when another thread of the CTA has raised `abort`, or after
 // `limit_ns` nanoseconds, in which case it raises `abort` and records
 // HOS_ERR_TIMEOUT in the device status word.
-HOS_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* status, uint64_t limit_ns) {
+HOS_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* status, uint64_t limit_ns,
+                       uint32_t hint_ns = 0) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     for (uint32_t it = 1;; ++it) {
-        if (mbar_try(bar, parity)) return true;
-        if ((it & 31u) == 0) {
+        if (mbar_try(bar, parity, hint_ns)) return true;
+        if ((it & 7u) == 0) {
             if (*abort) return false;
             if (global_timer_ns() - t0 > limit_ns) {
                 *abort = 1;
@@ -204,6 +216,16 @@ HOS_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int*
             }
         }
     }
+}
+
+// Warp-wide wait: lane 0 polls, the warp then synchronises (which orders the
+// memory the barrier protects for every lane) and shares the outcome.
+HOS_DEV bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* status, uint64_t limit_ns,
+                       uint32_t hint_ns = 0) {
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort, status, limit_ns, hint_ns);
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
 
 HOS_DEV void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }

