@@ -155,6 +155,32 @@ hos_status hos_cumulant3(const void* d_x, int32_t dtype, int64_t n, const hos_pa
 hos_status hos_cumulant4(const void* d_x, int32_t dtype, int64_t n, const hos_params* params, double* d_c4,
                          void* ws, size_t ws_bytes, hos_stream_t stream);
 
+/* Bispectrum without a caller-supplied workspace, for callers that cannot
+ * allocate device memory (no allocator at hand, or a context where calling
+ * cudaMalloc is not allowed, such as a host callback or a plug-in whose host
+ * owns all allocations).  The paper has no counterpart: this is a deployment
+ * convenience.
+ *
+ * Same arguments and result as hos_bispectrum, minus `ws`/`ws_bytes`.  The
+ * scratch is a fixed array of HOS_NOALLOC_SCRATCH_BYTES inside the library:
+ * every GPU that loads the library holds that much device memory until the
+ * process exits.  A problem whose hos_workspace_size exceeds it returns
+ * HOS_ERR_WORKSPACE and enqueues nothing (for example split-bf16 with the
+ * default tiles fits n = 2^20 at L = 32).  Nothing is allocated or freed.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins.  All calls on a device share the one
+ * array, which keeps the previous call's contents (each call clears the
+ * status word it needs at zero): calls that overlap in time on the GPU
+ * (different streams, or different host threads) race with each other and
+ * must be serialised by the caller.  A device-side timeout is recorded in
+ * the array's own status word, which callers cannot read; the next call
+ * clears it.                                                                */
+#define HOS_NOALLOC_SCRATCH_BYTES (32u << 20)
+hos_status hos_bispectrum_noalloc(const void* d_x, int32_t dtype, int64_t n, const hos_params* params, void* d_B,
+                                  hos_stream_t stream);
+
 /* Read (synchronously) the device status word of a workspace that a finished
  * call used.  *status = HOS_OK, HOS_ERR_TIMEOUT or HOS_ERR_DEVICE_FAULT.     */
 hos_status hos_get_device_status(const void* ws, int32_t* status);

@@ -44,6 +44,7 @@ _SIGS = {
     "hos_bispectrum_batched": [_VP, ctypes.c_int32, _VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P, _VP,
                                _VP, ctypes.c_size_t, _VP],
     "hos_bispectrum_backward": [_VP, ctypes.c_int32, ctypes.c_int64, _P, _VP, _VP, _VP, ctypes.c_size_t, _VP],
+    "hos_bispectrum_noalloc": [_VP, ctypes.c_int32, ctypes.c_int64, _P, _VP, _VP],
     "hos_cumulant3": [_VP, ctypes.c_int32, ctypes.c_int64, _P, _VP, _VP, ctypes.c_size_t, _VP],
     "hos_cumulant4": [_VP, ctypes.c_int32, ctypes.c_int64, _P, _VP, _VP, ctypes.c_size_t, _VP],
     "hos_get_device_status": [_VP, ctypes.POINTER(ctypes.c_int32)],
