@@ -60,7 +60,7 @@ class Clocks:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -95,6 +95,32 @@ class Clocks:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("c3_tc.cu", "hos_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1805_11775_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(prec):
+    """DRAM bytes per launch of the contraction from the committed ncu summary,
+    or None when the kernel source has changed since those counters were taken."""
+    path = os.path.join(ROOT, "profiles", f"c3_tc_{prec}_long_n2M_L256.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    with open(path) as f:
+        for ln in f:
+            if ":" in ln and ln.split(":")[0].strip() in ("kernel_source_sha256_16", "traffic_bytes_per_launch"):
+                k, v = ln.split(":", 1)
+                fields[k.strip()] = v.strip()
+    if fields.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return int(fields["traffic_bytes_per_launch"]) if "traffic_bytes_per_launch" in fields else None
 
 
 def cpu_baseline(x, L, n, seconds_target=10.0):
@@ -235,11 +261,9 @@ def run_ours(args):
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         peak_note = "FP32 FFMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
     achieved = flops / (contract_ms * 1e-3) / 1e12
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", f"c3_tc_{prec}_traffic.json")
-    if os.path.exists(tr_path):
-        with open(tr_path) as f:
-            traffic = json.load(f).get("bytes_per_launch")
+    traffic = profiled_traffic(prec) if hos.last_contraction().startswith("c3_tcgen05") else None
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    clock_peak = nsm * (8192 if prec == "bf16" else 4096) * (clk["sm_mhz"] or 2070.0) * 1e6 / 1e12
 
     # end to end through the public API with host buffers
     x_pin = torch.from_numpy(x_host).pin_memory()
@@ -273,6 +297,7 @@ def run_ours(args):
         "roofline": {"bound": "tensor" if prec != "simt" else "alu", "kernel": hos.last_contraction(),
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_source": peak_note,
+                     "frac_clock_matched": achieved / clock_peak if prec != "simt" else None,
                      "work": f"{ntiles} tiles x 128 x {tile_n} x {kpad} samples x {products} products x 2 flops"},
         "e2e": {"value": units_of(n, L) / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(x_host.nbytes),
                 "d2h_bytes_per_step": int(N * N * 8)},
@@ -293,8 +318,8 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
