@@ -67,6 +67,8 @@ def _load():
             lib.hos_oracle_bispectrum.argtypes = [_D, _I64, _I64, _I64, ctypes.c_int, ctypes.c_int, _I64, _D]
             lib.hos_oracle_trispectrum.argtypes = [_D, _I64, _I64, _I64, ctypes.c_int, ctypes.c_int, _I64, _D]
             lib.hos_oracle_bispectrum_grad.argtypes = [_D, _I64, _I64, _I64, ctypes.c_int, ctypes.c_int, _D, _D]
+            lib.hos_oracle_grad_lag.argtypes = [_D, _I64, _I64, ctypes.c_int, _D]
+            lib.hos_oracle_dy_at.argtypes = [_D, _I64, _I64, _D, ctypes.POINTER(_I64), _I64, _D]
             _lib = lib
     return _lib
 
@@ -194,6 +196,26 @@ def bispectrum_grad(x, L: int, G, N: int = 0, window: int = WIN_PARZEN, remove_m
     out = np.empty_like(x)
     _load().hos_oracle_bispectrum_grad(_p(x), x.size, int(L), int(N), int(window), int(bool(remove_mean)),
                                        _p(np.ascontiguousarray(g)), _p(out))
+    return out
+
+
+def grad_lag(G, L: int, N: int, window: int = WIN_PARZEN) -> np.ndarray:
+    """dl/dc3 over [-L, L]^2 for dl/dRe B + i dl/dIm B = G (complex N x N)."""
+    g = np.ascontiguousarray(np.asarray(G, dtype=np.complex128).reshape(N, N)).view(np.float64).ravel()
+    W = 2 * L + 1
+    out = np.empty(W * W)
+    _load().hos_oracle_grad_lag(_p(np.ascontiguousarray(g)), int(L), int(N), int(window), _p(out))
+    return out.reshape(W, W)
+
+
+def dy_at(y, L: int, dc, js) -> np.ndarray:
+    """Gradient with respect to the mean-removed samples y at indices js."""
+    y = _f64(y)
+    dcf = _f64(dc)
+    jj = np.ascontiguousarray(np.asarray(js, dtype=np.int64))
+    out = np.empty(jj.size)
+    _load().hos_oracle_dy_at(_p(y), y.size, int(L), _p(dcf), jj.ctypes.data_as(ctypes.POINTER(_I64)), jj.size,
+                             _p(out))
     return out
 
 

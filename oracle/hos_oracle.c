@@ -419,3 +419,65 @@ void hos_oracle_bispectrum_grad(const double* x, int64_t n, int64_t L, int64_t N
     free(dc);
     free(dy);
 }
+
+/* ------------------------------------------------------------------ */
+/* Step 1 of the gradient alone, for large grids: dl/dc3(w) on [-L, L]^2,
+ *   W(w) (2 pi)^-2 Re sum_k G(k) e^{+i 2 pi k.w / N},
+ * with the double sum over k taken one axis at a time (inner sum over k2).  */
+void hos_oracle_grad_lag(const double* G, int64_t L, int64_t N, int window, double* dc)
+{
+    const int64_t W = 2 * L + 1;
+    double* t = (double*)calloc((size_t)(N * W * 2), sizeof(double)); /* t[k1][w2] complex */
+    for (int64_t k1 = 0; k1 < N; ++k1)
+        for (int64_t b = 0; b < W; ++b) {
+            double re = 0.0, im = 0.0;
+            for (int64_t k2 = 0; k2 < N; ++k2) {
+                double c, s;
+                phase(k2, b - L, N, +1.0, &c, &s);
+                const double gr = G[(k1 * N + k2) * 2], gi = G[(k1 * N + k2) * 2 + 1];
+                re += gr * c - gi * s;
+                im += gr * s + gi * c;
+            }
+            t[(k1 * W + b) * 2] = re;
+            t[(k1 * W + b) * 2 + 1] = im;
+        }
+    const double scale = 1.0 / ((2.0 * HOS_ORACLE_PI) * (2.0 * HOS_ORACLE_PI));
+    for (int64_t a = 0; a < W; ++a)
+        for (int64_t b = 0; b < W; ++b) {
+            double re = 0.0;
+            for (int64_t k1 = 0; k1 < N; ++k1) {
+                double c, s;
+                phase(k1, a - L, N, +1.0, &c, &s);
+                re += t[(k1 * W + b) * 2] * c - t[(k1 * W + b) * 2 + 1] * s;
+            }
+            dc[a * W + b] = hos_oracle_window2(a - L, b - L, L, window) * scale * re;
+        }
+    free(t);
+}
+
+/* Step 2 of the gradient at chosen samples j (no mean removal):
+ *   dy(j) = (1/n) sum_w dc(w) [ y(j+w1) y(j+w2) + y(j-w1) y(j-w1+w2) + y(j-w2) y(j-w2+w1) ],
+ * the three places sample j can occupy in a triple product of the c3 loop
+ * (samples outside [0, n) are zero).                                        */
+void hos_oracle_dy_at(const double* y, int64_t n, int64_t L, const double* dc, const int64_t* js, int64_t count,
+                      double* out)
+{
+    const int64_t W = 2 * L + 1;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t q = 0; q < count; ++q) {
+        const int64_t j = js[q];
+        double acc = 0.0;
+        for (int64_t w1 = -L; w1 <= L; ++w1)
+            for (int64_t w2 = -L; w2 <= L; ++w2) {
+                const double g = dc[(w1 + L) * W + (w2 + L)];
+                if (g == 0.0) continue;
+#define YV(k) (((k) >= 0 && (k) < n) ? y[(k)] : 0.0)
+                double term = YV(j + w1) * YV(j + w2);
+                term += YV(j - w1) * YV(j - w1 + w2);
+                term += YV(j - w2) * YV(j - w2 + w1);
+#undef YV
+                acc += g * term;
+            }
+        out[q] = acc / (double)n;
+    }
+}

@@ -328,6 +328,138 @@ static hos_status run_dft2(float* grid, float2* out, int groups, int Nf, float2*
     return HOS_OK;
 }
 
+// ---- fourth order --------------------------------------------------------------------
+struct Plan4 {
+    int S;
+    int64_t seg, max_len, total_groups;
+    int Nf, W3, npb, nslices, pad_tail;
+    size_t status, off, pad, unit, win, mean, mpart, y32, c2, partials, grid, tw, total;
+};
+
+static hos_status make_plan4(int op, const hos_params* p, int64_t n, Plan4& P) {
+    hos_status s = check_params(p, op);
+    if (s != HOS_OK) return s;
+    const int L = p->L, twoL = 2 * L;
+    P.Nf = p->nfft ? p->nfft : twoL;
+    P.seg = (p->segment_len > 0 && p->segment_len < n) ? p->segment_len : 0;
+    const int64_t S64 = P.seg ? ceil_div(n, P.seg) : 1;
+    if (S64 > 65535) return HOS_ERR_UNSUPPORTED;
+    P.S = (int)S64;
+    P.max_len = P.seg ? P.seg : n;
+    const int64_t last = n - (P.S - 1) * (P.seg ? P.seg : 0);
+    auto groups = [](int64_t len) { return ceil_div(ceil_div(len, KC), C4_CHUNK_GROUP); };
+    P.total_groups = (P.S - 1) * groups(P.max_len) + groups(last);
+    if (P.total_groups > 65535) return HOS_ERR_UNSUPPORTED;
+    P.W3 = 16 * ((twoL + 15) / 16);
+    const int npairs = twoL * (twoL + 1) / 2;
+    P.npb = (npairs + C4_PAIRS_PER_CTA - 1) / C4_PAIRS_PER_CTA;
+    P.pad_tail = 32 + 128 + 64 + 64;
+    P.nslices = (int)ceil_div(P.max_len > 0 ? P.max_len : 1, 8192);
+    if (P.nslices > 256) P.nslices = 256;
+    if (P.nslices < 1) P.nslices = 1;
+    const int64_t plane_len = n + (int64_t)P.S * ((int64_t)L + KC + P.pad_tail + 64);
+    size_t o = 0;
+    P.status = o; o = al256(o + 256);
+    P.off = o; o = al256(o + 8 * (size_t)(P.S + 1));
+    P.pad = o; o = al256(o + 8 * (size_t)(P.S + 1));
+    P.unit = o; o = al256(o + 8 * (size_t)(P.S + 1));
+    P.win = o; o = al256(o + 8 * (size_t)(P.S + 1));
+    P.mean = o; o = al256(o + 8 * (size_t)P.S);
+    P.mpart = o; o = al256(o + 8 * (size_t)P.S * P.nslices);
+    P.y32 = o; o = al256(o + 4 * (size_t)plane_len);
+    P.c2 = o; o = al256(o + 8 * (size_t)P.S * (4 * L - 1));
+    P.partials = o; o = al256(o + 4 * (size_t)P.total_groups * P.npb * C4_PAIRS_PER_CTA * P.W3);
+    P.grid = o; o = al256(o + (op == HOS_OP_TRISPECTRUM ? 4 * (size_t)P.Nf * P.Nf * P.Nf : 0));
+    P.tw = o; o = al256(o + 8 * (size_t)P.Nf);
+    P.total = o;
+    return HOS_OK;
+}
+
+static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, const hos_params* p, void* ws,
+                         size_t ws_bytes, cudaStream_t st, Tracer& tr, int mode, double* c4out) {
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < P.total) return HOS_ERR_WORKSPACE;
+    int64_t* off = at<int64_t>(ws, P.off);
+    int64_t* pad = at<int64_t>(ws, P.pad);
+    int64_t* unit = at<int64_t>(ws, P.unit);
+    int64_t* win = at<int64_t>(ws, P.win);
+    double* mean = at<double>(ws, P.mean);
+    float* y32 = at<float>(ws, P.y32);
+    tr.mark("prep");
+    HOS_CUDA_TRY(launch_plan_series(0, n, P.seg, nullptr, P.S, p->L, 1, C4_CHUNK_GROUP, P.pad_tail, off, pad, unit,
+                                    win, st));
+    HOS_CUDA_TRY(launch_mean(x, dtype, off, P.S, P.nslices, at<double>(ws, P.mpart), p->remove_mean, mean, st));
+    const int64_t maxpad = (int64_t)p->L + P.max_len + KC + P.pad_tail + 64;
+    int bx = (int)ceil_div(maxpad, 256 * 4);
+    if (bx < 1) bx = 1;
+    if (bx > 65535) bx = 65535;
+    HOS_CUDA_TRY(launch_planes(x, dtype, off, pad, mean, p->L, 0, y32, nullptr, nullptr, P.S, bx, st));
+    tr.mark("contract");
+    C4ReduceArgs r;
+    r.window = p->window;
+    r.nfft = P.Nf;
+    r.mode = mode;
+    r.scale = 1.0 / (8.0 * 3.14159265358979323846 * 3.14159265358979323846 * 3.14159265358979323846);
+    r.grid = at<float>(ws, P.grid);
+    r.c4out = c4out;
+    if (mode == 0 && P.Nf > 2 * p->L) HOS_CUDA_TRY(launch_zero_f32(r.grid, (int64_t)P.Nf * P.Nf * P.Nf, st));
+    HOS_CUDA_TRY(launch_c4(y32, off, pad, win, P.S, p->L, C4_CHUNK_GROUP, P.total_groups, at<double>(ws, P.c2),
+                           at<float>(ws, P.partials), r, st));
+    g_last_contraction = "m4_simt_fp32";
+    return HOS_OK;
+}
+
+static hos_status run_dft3(float* grid, float2* out, int Nf, float2* tw, cudaStream_t st) {
+    const int64_t N = Nf, N2 = N * N;
+    HOS_CUDA_TRY(launch_twiddles(Nf, tw, st));
+    LineGeom g2 = line_geom(Nf, N2, 1, N, 1);  // along k3 (contiguous), real input
+    HOS_CUDA_TRY(launch_lines(true, grid, out, g2, tw, -1, 1.0f, st));
+    LineGeom g1 = line_geom(Nf, N2, N, N2, N);  // along k2
+    HOS_CUDA_TRY(launch_lines(false, out, out, g1, tw, -1, 1.0f, st));
+    LineGeom g0 = line_geom(Nf, N2, N2, N2 * N, N2);  // along k1
+    HOS_CUDA_TRY(launch_lines(false, out, out, g0, tw, -1, 1.0f, st));
+    return HOS_OK;
+}
+
+// ---- adjoint ----------------------------------------------------------------------------
+struct PlanB {
+    C3Geom g;
+    int Nf, nslices;
+    int64_t nctas;
+    size_t status, off, pad, unit, win, mean, mpart, y32, gc, gs, t1, t2p, gbuf, gmean, gmpart, tw, total;
+};
+
+static hos_status make_planb(const hos_params* p, int64_t n, PlanB& P) {
+    hos_status s = check_params(p, HOS_OP_BISPECTRUM_BACKWARD);
+    if (s != HOS_OK) return s;
+    const int L = p->L, twoL = 2 * L;
+    P.g = make_geom(p, 1);
+    P.Nf = p->nfft ? p->nfft : twoL;
+    P.nslices = (int)ceil_div(n, 8192);
+    if (P.nslices > 256) P.nslices = 256;
+    if (P.nslices < 1) P.nslices = 1;
+    P.nctas = ceil_div(n, ADJ_ROWS_PER_CTA);
+    const int64_t plane_len = n + ((int64_t)L + KC + P.g.pad_tail + 64);
+    size_t o = 0;
+    P.status = o; o = al256(o + 256);
+    P.off = o; o = al256(o + 16);
+    P.pad = o; o = al256(o + 16);
+    P.unit = o; o = al256(o + 16);
+    P.win = o; o = al256(o + 16);
+    P.mean = o; o = al256(o + 8);
+    P.mpart = o; o = al256(o + 8 * (size_t)P.nslices);
+    P.y32 = o; o = al256(o + 4 * (size_t)plane_len);
+    P.gc = o; o = al256(o + 8 * (size_t)P.Nf * P.Nf);
+    P.gs = o; o = al256(o + 4 * (size_t)twoL * twoL);
+    P.t1 = o; o = al256(o + 4 * (size_t)P.nctas * ADJ_ROWS_PER_CTA);
+    P.t2p = o; o = al256(o + 4 * (size_t)P.nctas * (ADJ_ROWS_PER_CTA + twoL));
+    P.gbuf = o; o = al256(o + 4 * (size_t)n);
+    P.gmean = o; o = al256(o + 8);
+    P.gmpart = o; o = al256(o + 8 * (size_t)P.nslices);
+    P.tw = o; o = al256(o + 8 * (size_t)P.Nf);
+    P.total = o;
+    return HOS_OK;
+}
+
 }  // namespace hos
 
 using namespace hos;
@@ -355,9 +487,21 @@ const char* hos_last_contraction(void) { return g_last_contraction; }
 hos_status hos_workspace_size(int32_t op, int64_t n_total, int32_t n_series, int64_t max_len, const hos_params* p,
                               size_t* bytes) {
     if (!bytes || n_total < 0 || n_series < 1 || max_len < 0) return HOS_ERR_INVALID_ARG;
-    if (op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT4 || op == HOS_OP_BISPECTRUM_BACKWARD)
-        return HOS_ERR_UNSUPPORTED;
     if (op < 0 || op > HOS_OP_CUMULANT4) return HOS_ERR_INVALID_ARG;
+    if (op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT4) {
+        Plan4 P4;
+        hos_status s4 = make_plan4(op, p, n_total, P4);
+        if (s4 != HOS_OK) return s4;
+        *bytes = P4.total;
+        return HOS_OK;
+    }
+    if (op == HOS_OP_BISPECTRUM_BACKWARD) {
+        PlanB PB;
+        hos_status sb = make_planb(p, n_total, PB);
+        if (sb != HOS_OK) return sb;
+        *bytes = PB.total;
+        return HOS_OK;
+    }
     Plan P;
     hos_status s = make_plan(op, p, n_total, n_series, max_len, P);
     if (s != HOS_OK) return s;
@@ -416,15 +560,78 @@ hos_status hos_cumulant3(const void* d_x, int32_t dtype, int64_t n, const hos_pa
     return s;
 }
 
-hos_status hos_trispectrum(const void*, int32_t, int64_t, const hos_params*, void*, void*, size_t, hos_stream_t) {
-    return HOS_ERR_UNSUPPORTED;
+hos_status hos_trispectrum(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, void* d_T, void* ws,
+                           size_t ws_bytes, hos_stream_t stream) {
+    if (!d_x || !d_T || n < 1 || (dtype != HOS_F32 && dtype != HOS_F64)) return HOS_ERR_INVALID_ARG;
+    Plan4 P;
+    hos_status s = make_plan4(HOS_OP_TRISPECTRUM, p, n, P);
+    if (s != HOS_OK) return s;
+    if (!ws || ws_bytes < P.total) return HOS_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Tracer tr(st);
+    s = run_c4(d_x, dtype, n, P, p, ws, ws_bytes, st, tr, 0, nullptr);
+    if (s != HOS_OK) return s;
+    tr.mark("transform");
+    s = run_dft3(at<float>(ws, P.grid), reinterpret_cast<float2*>(d_T), P.Nf, at<float2>(ws, P.tw), st);
+    tr.mark("");
+    return s;
 }
-hos_status hos_cumulant4(const void*, int32_t, int64_t, const hos_params*, double*, void*, size_t, hos_stream_t) {
-    return HOS_ERR_UNSUPPORTED;
+
+hos_status hos_cumulant4(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, double* d_c4, void* ws,
+                         size_t ws_bytes, hos_stream_t stream) {
+    if (!d_x || !d_c4 || n < 1 || (dtype != HOS_F32 && dtype != HOS_F64)) return HOS_ERR_INVALID_ARG;
+    Plan4 P;
+    hos_status s = make_plan4(HOS_OP_CUMULANT4, p, n, P);
+    if (s != HOS_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Tracer tr(st);
+    s = run_c4(d_x, dtype, n, P, p, ws, ws_bytes, st, tr, 1, d_c4);
+    tr.mark("");
+    return s;
 }
-hos_status hos_bispectrum_backward(const void*, int32_t, int64_t, const hos_params*, const void*, void*, void*,
-                                   size_t, hos_stream_t) {
-    return HOS_ERR_UNSUPPORTED;
+hos_status hos_bispectrum_backward(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, const void* d_dB,
+                                   void* d_dx, void* ws, size_t ws_bytes, hos_stream_t stream) {
+    if (!d_x || !d_dB || !d_dx || n < 1 || (dtype != HOS_F32 && dtype != HOS_F64)) return HOS_ERR_INVALID_ARG;
+    PlanB P;
+    hos_status s = make_planb(p, n, P);
+    if (s != HOS_OK) return s;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < P.total) return HOS_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Tracer tr(st);
+    int64_t* off = at<int64_t>(ws, P.off);
+    int64_t* pad = at<int64_t>(ws, P.pad);
+    float* y32 = at<float>(ws, P.y32);
+    const int L = p->L, Nf = P.Nf;
+    tr.mark("prep");
+    HOS_CUDA_TRY(launch_plan_series(0, n, 0, nullptr, 1, L, 1, 16, P.g.pad_tail, off, pad, at<int64_t>(ws, P.unit),
+                                    at<int64_t>(ws, P.win), st));
+    HOS_CUDA_TRY(launch_mean(d_x, dtype, off, 1, P.nslices, at<double>(ws, P.mpart), p->remove_mean,
+                             at<double>(ws, P.mean), st));
+    int bx = (int)ceil_div((int64_t)L + n + KC + P.g.pad_tail + 64, 256 * 4);
+    if (bx > 65535) bx = 65535;
+    HOS_CUDA_TRY(launch_planes(d_x, dtype, off, pad, at<double>(ws, P.mean), L, 0, y32, nullptr, nullptr, 1, bx, st));
+    tr.mark("transform");
+    float2* tw = at<float2>(ws, P.tw);
+    float2* gc = at<float2>(ws, P.gc);
+    HOS_CUDA_TRY(launch_twiddles(Nf, tw, st));
+    LineGeom g1 = line_geom(Nf, Nf, 1, Nf, 1);
+    HOS_CUDA_TRY(launch_lines(false, d_dB, gc, g1, tw, +1, 1.0f, st));
+    LineGeom g2 = line_geom(Nf, Nf, Nf, (int64_t)Nf * Nf, Nf);
+    HOS_CUDA_TRY(launch_lines(false, gc, gc, g2, tw, +1, 1.0f, st));
+    tr.mark("contract");
+    // y(i) of the single series sits at pad[0] + L + i; pad[0] = 0 for one series
+    const float* yS = y32 + L;
+    const double scale = 1.0 / (4.0 * 3.14159265358979323846 * 3.14159265358979323846 * (double)n);
+    float* g = at<float>(ws, P.gbuf);
+    HOS_CUDA_TRY(launch_adjoint(yS, n, L, gc, Nf, p->window, scale, at<float>(ws, P.gs), at<float>(ws, P.t1),
+                                at<float>(ws, P.t2p), g, st));
+    g_last_contraction = "adjoint_simt_fp32";
+    tr.mark("reduce");
+    HOS_CUDA_TRY(launch_mean(g, HOS_F32, off, 1, P.nslices, at<double>(ws, P.gmpart), p->remove_mean,
+                             at<double>(ws, P.gmean), st));
+    HOS_CUDA_TRY(launch_adjoint_finish(g, n, at<double>(ws, P.gmean), p->remove_mean, dtype, d_dx, st));
+    tr.mark("");
+    return HOS_OK;
 }
 
 hos_status hos_get_device_status(const void* ws, int32_t* status) {

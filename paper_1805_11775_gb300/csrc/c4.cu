@@ -1,0 +1,225 @@
+// c4.cu -- fourth-order cumulant over the lag cube (trispectrum path).
+//
+//   c4(w1,w2,w3) = m4(w1,w2,w3) - c2(w1) c2(w3-w2) - c2(w2) c2(w3-w1) - c2(w3) c2(w2-w1)
+//   m4(w1,w2,w3) = (1/n) sum_i y(i) y(i+w1) y(i+w2) y(i+w3),   c2(t) = (1/n) sum_i y(i) y(i+t)
+// (Problem Statement: moments and cumulants "and so on"; the zero-mean
+// moment-to-cumulant identity is the reading of the fourth order.)
+//
+// m4 is symmetric in (w1, w2, w3), so only pairs w1 <= w2 are contracted:
+//   M[p, w3] = sum_i T[p, i] * y(i + w3),   T[p, i] = y(i) y(i + w1_p) y(i + w2_p),
+// an FP32 FFMA contraction (SIMT) over blocks of 128 pairs, in chunk groups of
+// CG * 1024 samples, each group's FP32 partial summed by the FP64 reduction.
+// c2 is accumulated in FP64 directly.
+#include "launch.cuh"
+
+namespace hos {
+
+// lag pair index of (w1, w2), w1 <= w2, both in [-L, L): row-major over the triangle
+HOS_HD int pair_index(int w1, int w2, int L) {
+    const int a = w1 + L, b = w2 + L, twoL = 2 * L;
+    return a * twoL - (a * (a - 1)) / 2 + (b - a);
+}
+
+// c2_s(t) for t in [-(2L-1), 2L-1] of every part s, FP64.  blockIdx.x = lag, .y = part.
+__global__ void c2_kernel(const float* __restrict__ y32, const int64_t* __restrict__ off,
+                          const int64_t* __restrict__ pad, int L, double* __restrict__ c2) {
+    __shared__ double sh[256];
+    const int T = 2 * L - 1;
+    const int t = (int)blockIdx.x - T;
+    const int s = blockIdx.y;
+    const int64_t len = off[s + 1] - off[s];
+    const float* y = y32 + pad[s] + L;  // y[i], zero-padded on both sides by >= L
+    double acc = 0.0;
+    const int64_t i0 = t < 0 ? -t : 0, i1 = t > 0 ? len - t : len;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += (double)y[i] * (double)y[i + t];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int d = blockDim.x / 2; d > 0; d >>= 1) {
+        if (threadIdx.x < d) sh[threadIdx.x] += sh[threadIdx.x + d];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) c2[(int64_t)s * (2 * T + 1) + blockIdx.x] = len > 0 ? sh[0] / (double)len : 0.0;
+}
+
+constexpr int M4_PAIRS = 128;  // pairs per CTA
+constexpr int M4_KI = 32;      // samples per inner step
+
+// blockIdx.x = pair block, blockIdx.y = global chunk group (series found by
+// search in the group prefix win[]).  Thread (tq, tp): pairs tp + 16a (a < 8),
+// w3 = -L + tq + 16b (b < NB, NB = 2L/16).
+template <int NB>
+__global__ void __launch_bounds__(256) m4_simt_kernel(const float* __restrict__ y32, const int64_t* __restrict__ off,
+                                                      const int64_t* __restrict__ pad, const int64_t* __restrict__ win,
+                                                      int S, int L, int CG, int npairs, float* __restrict__ part) {
+    constexpr int W3 = 16 * NB;  // w3 columns, 2L rounded up to a multiple of 16
+    __shared__ float T[M4_KI][M4_PAIRS];
+    __shared__ float yw[M4_KI + W3];  // yw[k] = y(i0 + k - L)
+    __shared__ int pw1[M4_PAIRS], pw2[M4_PAIRS];
+    const int tq = threadIdx.x & 15, tp = threadIdx.x >> 4;
+    const int twoL = 2 * L;
+    const int64_t g = blockIdx.y;
+    int lo = 0, hi = S;  // series with win[s] <= g < win[s+1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (win[mid] <= g) lo = mid; else hi = mid;
+    }
+    const int s = lo;
+    const int64_t len = off[s + 1] - off[s];
+    const int64_t cg = g - win[s];
+    const int64_t i_begin = cg * CG * KC;
+    const int64_t i_end = (i_begin + (int64_t)CG * KC < len) ? i_begin + (int64_t)CG * KC : len;
+    const float* y = y32 + pad[s] + L;  // y[i] valid for i in [-L, len + pad_tail)
+    // this block's pairs
+    for (int q = threadIdx.x; q < M4_PAIRS; q += blockDim.x) {
+        const int p = blockIdx.x * M4_PAIRS + q;
+        int w1 = L, w2 = L;  // out of range marks an unused slot
+        if (p < npairs) {
+            int a = 0;
+            while (a < twoL - 1 && pair_index(a + 1 - L, a + 1 - L, L) <= p) ++a;
+            w1 = a - L;
+            w2 = w1 + (p - pair_index(w1, w1, L));
+        }
+        pw1[q] = w1;
+        pw2[q] = w2;
+    }
+    float acc[8][NB];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) acc[a][b] = 0.0f;
+    for (int64_t i0 = i_begin; i0 < i_end; i0 += M4_KI) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < M4_KI + W3; k += blockDim.x) yw[k] = y[i0 + k - L];
+        __syncthreads();
+        // T[k][q] = y(i0+k) y(i0+k+w1) y(i0+k+w2); samples past the series are zero
+        for (int e = threadIdx.x; e < M4_KI * M4_PAIRS; e += blockDim.x) {
+            const int k = e / M4_PAIRS, q = e % M4_PAIRS;
+            const int w1 = pw1[q], w2 = pw2[q];
+            float v = 0.0f;
+            if (w1 < L && w2 < L) v = yw[k + L] * yw[k + L + w1] * yw[k + L + w2];
+            T[k][q] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < M4_KI; ++k) {
+            float tv[8], yv[NB];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) tv[a] = T[k][tp + 16 * a];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) yv[b] = yw[k + tq + 16 * b];  // y(i0 + k + w3), w3 = -L + tq + 16b
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < NB; ++b) acc[a][b] = fmaf(tv[a], yv[b], acc[a][b]);
+        }
+    }
+    // partial[g][pair][w3 + L], rows of W3
+    const int64_t ppad = (int64_t)gridDim.x * M4_PAIRS;
+    float* dst = part + g * ppad * W3;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int64_t p = (int64_t)blockIdx.x * M4_PAIRS + tp + 16 * a;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) dst[p * W3 + tq + 16 * b] = acc[a][b];
+    }
+}
+
+// mode 0: grid3[(w1 mod N)][(w2 mod N)][(w3 mod N)] = scale * W * c4 (fp32)
+// mode 1: c4out[w1+L][w2+L][w3+L] = c4 (fp64)
+struct Reduce4Params {
+    const float* partials;
+    int w3;
+    const double* c2;
+    const int64_t* off;
+    const int64_t* win;
+    int S;
+    int L;
+    int npblocks;
+    int window;
+    int nfft;
+    int mode;
+    double scale;
+    float* grid;
+    double* c4out;
+};
+
+__global__ void reduce4_kernel(const Reduce4Params P) {
+    const int L = P.L, twoL = 2 * L, T = 2 * L - 1, W3 = P.w3;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)twoL * twoL * twoL) return;
+    const int w3 = (int)(e % twoL) - L;
+    const int w2 = (int)((e / twoL) % twoL) - L;
+    const int w1 = (int)(e / ((int64_t)twoL * twoL)) - L;
+    const int p = (w1 <= w2) ? pair_index(w1, w2, L) : pair_index(w2, w1, L);
+    const int64_t ppad = (int64_t)P.npblocks * M4_PAIRS;
+    double c4 = 0.0;
+    int k = 0;
+    for (int s = 0; s < P.S; ++s) {
+        const int64_t len = P.off[s + 1] - P.off[s];
+        if (len <= 0) continue;
+        double m4 = 0.0;
+        const int64_t g0 = P.win[s], g1 = P.win[s + 1];
+        for (int64_t gb = g0; gb < g1; gb += 16) {  // groups of 16 as a two-float sum, added in FP64
+            const int64_t ge = (gb + 16 < g1) ? gb + 16 : g1;
+            float hi = 0.0f, lo = 0.0f;
+            for (int64_t g = gb; g < ge; ++g) {
+                const float v = P.partials[(g * ppad + p) * W3 + (w3 + L)];
+                const float sum = hi + v;
+                const float bv = sum - hi;
+                lo += (hi - (sum - bv)) + (v - bv);
+                hi = sum;
+            }
+            m4 += (double)hi + (double)lo;
+        }
+        m4 /= (double)len;
+        const double* c2 = P.c2 + (int64_t)s * (2 * T + 1) + T;  // c2[t], t in [-T, T]
+        c4 += m4 - c2[w1] * c2[w3 - w2] - c2[w2] * c2[w3 - w1] - c2[w3] * c2[w2 - w1];
+        ++k;
+    }
+    if (k > 0) c4 /= (double)k;
+    if (P.mode == 1) {
+        P.c4out[((int64_t)(w1 + L) * twoL + (w2 + L)) * twoL + (w3 + L)] = c4;
+        return;
+    }
+    const double wv = (P.window == HOS_WIN_RECT && (w1 == -L || w2 == -L || w3 == -L))
+                          ? 0.0
+                          : lag_window3(w1, w2, w3, L, P.window);
+    const int N = P.nfft;
+    const int k1 = (w1 % N + N) % N, k2 = (w2 % N + N) % N, k3 = (w3 % N + N) % N;
+    P.grid[((int64_t)k1 * N + k2) * N + k3] = (float)(P.scale * wv * c4);
+}
+
+cudaError_t launch_c4(const float* y32, const int64_t* off, const int64_t* pad, const int64_t* win, int S, int L,
+                      int CG, int64_t total_groups, double* c2, float* partials, const C4ReduceArgs& r,
+                      cudaStream_t st) {
+    const int T = 2 * L - 1;
+    c2_kernel<<<dim3((unsigned)(2 * T + 1), (unsigned)S), 256, 0, st>>>(y32, off, pad, L, c2);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int twoL = 2 * L;
+    const int npairs = twoL * (twoL + 1) / 2;
+    const int npb = (npairs + M4_PAIRS - 1) / M4_PAIRS;
+    const int nb = (twoL + 15) / 16;
+    if (total_groups > 0) {
+        dim3 grid((unsigned)npb, (unsigned)total_groups);
+#define HOS_M4_CASE(K) \
+    case K: m4_simt_kernel<K><<<grid, 256, 0, st>>>(y32, off, pad, win, S, L, CG, npairs, partials); break;
+        switch (nb) {
+            HOS_M4_CASE(1) HOS_M4_CASE(2) HOS_M4_CASE(3) HOS_M4_CASE(4)
+            HOS_M4_CASE(5) HOS_M4_CASE(6) HOS_M4_CASE(7) HOS_M4_CASE(8)
+            default: return cudaErrorInvalidValue;
+        }
+#undef HOS_M4_CASE
+        count_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    Reduce4Params rp{partials, 16 * nb, c2, off, win, S, L, npb, r.window, r.nfft, r.mode, r.scale, r.grid, r.c4out};
+    const int64_t n3 = (int64_t)twoL * twoL * twoL;
+    reduce4_kernel<<<(unsigned)ceil_div(n3, 256), 256, 0, st>>>(rp);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace hos

@@ -50,6 +50,19 @@ struct LineGeom {
     int lpb;  // lines per CTA
 };
 
+struct C4ReduceArgs {
+    int window;
+    int nfft;
+    int mode;  // 0: windowed transform grid (fp32), 1: raw c4 (fp64)
+    double scale;
+    float* grid;
+    double* c4out;
+};
+
+// m4 contraction geometry shared by the host plan and the kernels
+constexpr int C4_PAIRS_PER_CTA = 128;
+constexpr int C4_CHUNK_GROUP = 4;  // 1024-sample chunks per FP32 partial
+
 void count_launch();
 
 cudaError_t launch_plan_series(int mode, int64_t n, int64_t seg, const int64_t* d_user_off, int S, int L, int ntiles,
@@ -66,6 +79,14 @@ cudaError_t launch_zero_f32(float* p, int64_t n, cudaStream_t st);
 cudaError_t launch_twiddles(int N, float2* tw, cudaStream_t st);
 cudaError_t launch_lines(bool real_in, const void* in, float2* out, LineGeom g, const float2* tw, int sign,
                          float scale, cudaStream_t st);
+cudaError_t launch_c4(const float* y32, const int64_t* off, const int64_t* pad, const int64_t* win, int S, int L,
+                      int CG, int64_t total_groups, double* c2, float* partials, const C4ReduceArgs& r,
+                      cudaStream_t st);
+cudaError_t launch_adjoint(const float* yS, int64_t n, int L, const float2* Gc, int N, int window, double scale,
+                           float* Gs, float* T1, float* t2p, float* g, cudaStream_t st);
+cudaError_t launch_adjoint_finish(const float* g, int64_t n, const double* gmean, int remove_mean, int dtype, void* dx,
+                                  cudaStream_t st);
+constexpr int ADJ_ROWS_PER_CTA = 64;
 cudaError_t launch_timeout_selftest(int* status, uint64_t limit_ns, cudaStream_t st);
 
 }  // namespace hos

@@ -1,0 +1,75 @@
+"""GPU parity of the trispectrum path (c2, m4 over symmetric lag pairs, the
+c2*c2 correction, window, 3-axis transform) against the FP64 oracle.
+Normwise tolerance 1e-5 (FP32 contraction, FP64 reductions)."""
+import math
+
+import numpy as np
+import pytest
+
+import hos_synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no GPU", allow_module_level=True)
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def hos():
+    from paper_1805_11775_gb300 import build
+    build.build()
+    import paper_1805_11775_gb300 as h
+    return h
+
+
+def normwise(got, ref):
+    return np.abs(np.asarray(got, dtype=np.complex128) - ref).max() / np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n,L", [(5, 1), (40, 3), (700, 8), (1500, 13), (2100, 32), (1200, 64)])
+def test_cumulant4_elementwise(hos, oracle, n, L):
+    x = hos_synth.ma(n, 5 * n + L)
+    ref = oracle.c4(oracle.demean(x), L)[:2 * L, :2 * L, :2 * L]
+    got = hos.cumulant4(torch.from_numpy(x).cuda(), L).cpu().numpy()
+    assert np.abs(got - ref).max() <= TOL * np.abs(ref).max()
+
+
+def test_cumulant4_is_symmetric(hos):
+    x = torch.from_numpy(hos_synth.exp_noise(5000, 2)).cuda()
+    c = hos.cumulant4(x, 8).cpu().numpy()
+    # w1 <-> w2 reads the same lag-pair partial sums: exact
+    assert np.array_equal(np.transpose(c, (1, 0, 2)), c)
+    # swaps with w3 pair the samples differently, so they agree to FP32 rounding
+    for perm in [(2, 1, 0), (0, 2, 1)]:
+        assert np.abs(np.transpose(c, perm) - c).max() <= 1e-6 * np.abs(c).max()
+
+
+def test_trispectrum_full_size_workload(hos, oracle):
+    """n = 65536 float32 MA(3) series, L = 32, 64^3 grid: the whole output
+    against the oracle."""
+    w = hos_synth.workload("trispectrum_n65536_L32")
+    ref = oracle.trispectrum(w["x"].astype(np.float64), w["L"], w["N"])
+    got = hos.trispectrum(torch.from_numpy(w["x"]).cuda(), w["L"]).cpu().numpy()
+    assert normwise(got, ref) <= TOL
+
+
+@pytest.mark.parametrize("n,L,N,seg", [(3000, 6, 14, 0), (5000, 10, 20, 1700), (2500, 16, 32, 0)])
+def test_trispectrum_grids_and_parts(hos, oracle, n, L, N, seg):
+    x = hos_synth.ar2(n, 3 * n)
+    ref = oracle.trispectrum(x, L, N, segment_len=seg)
+    got = hos.trispectrum(torch.from_numpy(x).cuda(), L, nfft=N, segment_len=seg).cpu().numpy()
+    assert normwise(got, ref) <= TOL
+
+
+def test_trispectrum_hermitian_and_flat_level(hos):
+    """Centred Exp(1) noise: c4(0,0,0) estimates the fourth cumulant 6, so the
+    grid average of (2 pi)^3 T is near 6, and T(-k) = conj T(k)."""
+    x = torch.from_numpy(hos_synth.exp_noise(1 << 20, 12)).cuda()
+    T = hos.trispectrum(x, 8).cpu().numpy().astype(np.complex128)
+    N = T.shape[0]
+    k = np.arange(N)
+    neg = T[(-k[:, None, None]) % N, (-k[None, :, None]) % N, (-k[None, None, :]) % N]
+    assert np.abs(neg - np.conj(T)).max() <= 1e-6 * np.abs(T).max()
+    assert abs(T.real.mean() * (2 * math.pi) ** 3 - 6.0) < 0.6

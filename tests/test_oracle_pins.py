@@ -361,3 +361,34 @@ def test_gradient_dot_product_identity(oracle):
     lhs = (Jv.real * G.real + Jv.imag * G.imag).sum()
     rhs = v @ oracle.bispectrum_grad(x, L, G, N)
     assert lhs == pytest.approx(rhs, rel=1e-8)
+
+
+def test_sampled_gradient_matches_the_full_chain_rule(oracle):
+    """grad_lag + dy_at (used to check large problems at chosen samples) give
+    the same values as the central-difference-pinned bispectrum_grad."""
+    n, L, N = 60, 7, 16
+    x = hos_synth.ar2(n, 51)
+    rng = np.random.default_rng(5)
+    G = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    full = oracle.bispectrum_grad(x, L, G, N, remove_mean=False)
+    dc = oracle.grad_lag(G, L, N)
+    js = np.arange(n)
+    np.testing.assert_allclose(oracle.dy_at(x, L, dc, js), full, rtol=1e-10, atol=1e-14)
+
+
+def test_gradient_central_differences_n1024(oracle):
+    """The FP64 gradient against central differences at n = 1024 on sampled
+    coordinates (loss: principal-domain squared distance to a target)."""
+    n, L, N = 1024, 8, 16
+    x = hos_synth.ar2(n, 61)
+    Bt = oracle.bispectrum(hos_synth.ar2(n, 62), L, N)
+    mask = _principal_mask(N)
+    G = 2.0 * (oracle.bispectrum(x, L, N) - Bt) * mask
+    g = oracle.bispectrum_grad(x, L, G, N)
+    h = 1e-6 * np.sqrt((x ** 2).mean())
+    for i in np.random.default_rng(6).choice(n, 48, replace=False):
+        e = np.zeros(n)
+        e[i] = h
+        lp = (np.abs(oracle.bispectrum(x + e, L, N) - Bt) ** 2 * mask).sum()
+        lm = (np.abs(oracle.bispectrum(x - e, L, N) - Bt) ** 2 * mask).sum()
+        assert (lp - lm) / (2 * h) == pytest.approx(g[i], rel=1e-6, abs=1e-6 * np.abs(g).max())
