@@ -39,8 +39,9 @@ def test_cumulant4_elementwise(hos, oracle, n, L):
 def test_cumulant4_is_symmetric(hos):
     x = torch.from_numpy(hos_synth.exp_noise(5000, 2)).cuda()
     c = hos.cumulant4(x, 8).cpu().numpy()
-    # w1 <-> w2 reads the same lag-pair partial sums: exact
-    assert np.array_equal(np.transpose(c, (1, 0, 2)), c)
+    # w1 <-> w2 reads the same lag-pair partial sums; only the FP64 c2*c2
+    # terms change order
+    assert np.abs(np.transpose(c, (1, 0, 2)) - c).max() <= 1e-12 * np.abs(c).max()
     # swaps with w3 pair the samples differently, so they agree to FP32 rounding
     for perm in [(2, 1, 0), (0, 2, 1)]:
         assert np.abs(np.transpose(c, perm) - c).max() <= 1e-6 * np.abs(c).max()
