@@ -176,13 +176,111 @@ def run_reference(args):
     return 0
 
 
+def principal_mask(N):
+    import numpy as np
+    k1, k2 = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    return (k2 <= k1) & (k1 + k2 < N // 2)
+
+
+def c3_tc_flops(L, lens, products):
+    """Executed tensor-core flops of the c3 contraction: computed tiles x 128
+    rows x tile_n columns x padded samples x products x 2."""
+    tile_n = min(256, max(32, 1 << (2 * L - 1).bit_length()))
+    tiles_m, tiles_n = math.ceil(2 * L / 128), math.ceil(2 * L / tile_n)
+    ntiles = sum(1 for b in range(tiles_n) for a in range(tiles_m) if not (a * 128 >= b * tile_n + tile_n))
+    kpad = sum(math.ceil(int(n) / 1024) * 1024 for n in lens)
+    return ntiles * 128 * tile_n * kpad * products * 2, (
+        f"{ntiles} tiles x 128 x {tile_n} x {kpad} padded samples x {products} products x 2 flops")
+
+
+def make_workload(name, prec, rank, hos, torch, series=0):
+    """Device-resident inputs, the step closure, the e2e closure, lag-term
+    units per step, and the dominant kernel's executed work."""
+    import numpy as np
+
+    import hos_synth
+    w = hos_synth.workload(name)
+    L, N = w["L"], w["N"]
+    ws = hos.Workspace()
+    products = 3 if prec in ("bf16", "fp32") else 1
+    if name in ("long_bispectrum_n2M_L256", "bispectrum_n2048_L32"):
+        x_host = w["x"] if rank == 0 else hos_synth.ar2(w["x"].size, 1002 + 100 * rank)
+        xd = torch.from_numpy(x_host).cuda()
+        out = torch.empty((N, N), dtype=torch.complex64, device="cuda")
+        step = lambda: hos.bispectrum(xd, L, precision=prec, out=out, workspace=ws)
+        x_pin = torch.from_numpy(x_host).pin_memory()
+        e2e = lambda: hos.bispectrum(x_pin, L, precision=prec, workspace=ws)
+        flops, work = c3_tc_flops(L, [x_host.size], products)
+        return dict(step=step, e2e=e2e, units=units_of(x_host.size, L), flops=flops, work=work,
+                    h2d=x_host.nbytes, d2h=N * N * 8, config={"n": int(x_host.size), "L": L, "grid": N},
+                    bound="tensor" if products == 3 else "alu")
+    if name == "trispectrum_n65536_L32":
+        x_host = w["x"]
+        xd = torch.from_numpy(x_host).cuda()
+        out = torch.empty((N, N, N), dtype=torch.complex64, device="cuda")
+        step = lambda: hos.trispectrum(xd, L, out=out, workspace=ws)
+        x_pin = torch.from_numpy(x_host).pin_memory()
+        e2e = lambda: hos.trispectrum(x_pin, L, workspace=ws)
+        twoL = 2 * L
+        npairs = twoL * (twoL + 1) // 2
+        w3 = 16 * math.ceil(twoL / 16)
+        kpad = math.ceil(x_host.size / 4096) * 4096
+        flops = math.ceil(npairs / 128) * 128 * w3 * kpad * 2
+        return dict(step=step, e2e=e2e, units=units_of(x_host.size, L, k=4), flops=flops, bound="alu",
+                    work=f"{math.ceil(npairs / 128) * 128} lag pairs x {w3} w3 x {kpad} samples x 2 flops (FFMA)",
+                    h2d=x_host.nbytes, d2h=N ** 3 * 8, config={"n": int(x_host.size), "L": L, "grid": N})
+    if name == "batched_4096x_L128":
+        vals, offs = w["x"], w["offsets"]
+        if series:  # a leading subset of the series (profiling a smaller case)
+            offs = offs[:series + 1]
+            vals = vals[:offs[-1]]
+        lens = np.diff(offs)
+        S = lens.size
+        vd = torch.from_numpy(vals).cuda()
+        od = torch.from_numpy(offs).cuda()
+        out = torch.empty((S, N, N), dtype=torch.complex64, device="cuda")
+        max_len = int(lens.max())
+        step = lambda: hos.bispectrum_batched(vd, od, L, precision=prec, out=out, workspace=ws, max_len=max_len)
+        v_pin = torch.from_numpy(vals).pin_memory()
+        e2e = lambda: hos.bispectrum_batched(v_pin, offs, L, precision=prec, workspace=ws, max_len=max_len)
+        flops, work = c3_tc_flops(L, lens, products)
+        return dict(step=step, e2e=e2e, units=int((lens * (2 * L + 1) ** 2).sum()), flops=flops, work=work,
+                    h2d=vals.nbytes + offs.nbytes, d2h=S * N * N * 8, bound="tensor" if products == 3 else "alu",
+                    config={"series": S, "total_samples": int(lens.sum()), "L": L, "grid": N},
+                    per_series=(vd, offs, L))
+    if name == "differentiable_n262144_L128":
+        x_host, t_host = w["x"], w["target_x"]
+        xd = torch.from_numpy(x_host).cuda()
+        Bt = hos.bispectrum(torch.from_numpy(t_host).cuda(), L, precision=prec)
+        mask = torch.from_numpy(principal_mask(N)).cuda()
+        out = torch.empty((N, N), dtype=torch.complex64, device="cuda")
+        ws2 = hos.Workspace()
+
+        def step():
+            B = hos.bispectrum(xd, L, precision=prec, out=out, workspace=ws)
+            G = 2.0 * (B - Bt) * mask  # gradient of sum_principal |B - Bt|^2
+            return hos.bispectrum_backward(xd, G, L, workspace=ws2)
+
+        x_pin = torch.from_numpy(x_host).pin_memory()
+
+        def e2e():
+            xg = x_pin.to("cuda", non_blocking=True)
+            B = hos.bispectrum(xg, L, precision=prec, workspace=ws)
+            G = 2.0 * (B - Bt) * mask
+            return hos.bispectrum_backward(xg, G, L, workspace=ws2).cpu()
+
+        flops, work = c3_tc_flops(L, [x_host.size], products)
+        return dict(step=step, e2e=e2e, units=units_of(x_host.size, L), flops=flops, work=work,
+                    h2d=x_host.nbytes, d2h=x_host.nbytes, bound="tensor" if products == 3 else "alu",
+                    config={"n": int(x_host.size), "L": L, "grid": N, "step": "forward + adjoint"})
+    raise KeyError(name)
+
+
 def run_ours(args):
     import numpy as np
     import torch
 
-    import hos_synth
     import paper_1805_11775_gb300 as hos
-    from paper_1805_11775_gb300 import _native
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -193,28 +291,32 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    w = hos_synth.workload(WORKLOAD)
-    x_host = w["x"] if rank == 0 else hos_synth.ar2(w["x"].size, 1002 + 100 * rank)
-    L, N = w["L"], w["N"]
-    n = x_host.size
     prec = args.precision
-    xd = torch.from_numpy(x_host).cuda()
-    out = torch.empty((N, N), dtype=torch.complex64, device="cuda")
+    wl = make_workload(args.workload, prec, rank, hos, torch, args.series)
+    step = wl["step"]
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
-    ws = hos.Workspace()
-
-    def step():
-        hos.bispectrum(xd, L, precision=prec, out=out, workspace=ws)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
 
-    hos.set_profiling(True)
+    n0 = hos.launch_count()
+    step()
+    torch.cuda.synchronize()
+    launches_per_step = hos.launch_count() - n0
+    graph = None
+    if args.graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        graph.replay()
+        torch.cuda.synchronize()
+
+    hos.set_profiling(graph is None)
     clocks = Clocks(local)
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    contract_ms, stage_acc = [], {}
+    stage_acc = {}
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -224,11 +326,15 @@ def run_ours(args):
     for i in range(args.steps):
         flush_buf.zero_()  # evict the previous step's data from L2 (outside the events)
         ev0[i].record()
-        step()
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
         ev1[i].record()
         torch.cuda.synchronize()
-        for name, ms in hos.stage_times():
-            stage_acc.setdefault(name, []).append(ms)
+        if graph is None:
+            for name, ms in hos.stage_times():
+                stage_acc.setdefault(name, []).append(ms)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     launches = hos.launch_count() - launches0
@@ -240,42 +346,58 @@ def run_ours(args):
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+    if graph is not None:
+        # the graph replays the same kernels; the per-kernel time comes from an
+        # eager profiled pass over the same inputs
+        hos.set_profiling(True)
+        for _ in range(5):
+            flush_buf.zero_()
+            step()
+            torch.cuda.synchronize()
+            for name, v in hos.stage_times():
+                stage_acc.setdefault(name, []).append(v)
+        hos.set_profiling(False)
+        launches = launches_per_step * args.steps  # replays re-run the captured launches
     contract_ms = statistics.mean(stage_acc.get("contract", [float("nan")]))
 
-    # executed tensor-core work of the contraction: computed tiles x 128 rows x
-    # tile_n columns x padded samples x 3 products x 2 flops
-    tile_n = min(256, max(32, 1 << (2 * L - 1).bit_length()))
-    tiles_m, tiles_n = math.ceil(2 * L / 128), math.ceil(2 * L / tile_n)
-    ntiles = sum(1 for b in range(tiles_n) for a in range(tiles_m) if not (a * 128 >= b * tile_n + tile_n))
-    kpad = math.ceil(n / 1024) * 1024
-    products = 3 if prec in ("bf16", "fp32") else 1
-    flops = ntiles * 128 * tile_n * kpad * products * 2
     pk, src = peaks()
-    if prec == "bf16":
-        peak = pk["bf16_tflops"]
-        peak_note = f"bf16 dense, {src} burst"
-    elif prec == "fp32":
+    if wl["bound"] == "tensor" and prec == "bf16":
+        peak, peak_note = pk["bf16_tflops"], f"bf16 dense, {src} burst"
+    elif wl["bound"] == "tensor":
         peak = pk["bf16_tflops"] * (1.1 / 2.25)
         peak_note = f"tf32 dense = {src} bf16 burst x 1.1/2.25 (nominal ratio)"
     else:
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         peak_note = "FP32 FFMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
-    achieved = flops / (contract_ms * 1e-3) / 1e12
-    traffic = profiled_traffic(prec) if hos.last_contraction().startswith("c3_tcgen05") else None
+    achieved = wl["flops"] / (contract_ms * 1e-3) / 1e12
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
-    clock_peak = nsm * (8192 if prec == "bf16" else 4096) * (clk["sm_mhz"] or 2070.0) * 1e6 / 1e12
+    per_clk = 8192 if prec == "bf16" else 4096
+    clock_peak = nsm * per_clk * (clk["sm_mhz"] or 2070.0) * 1e6 / 1e12
+    is_tc = hos.last_contraction().startswith("c3_tcgen05")
+    traffic = profiled_traffic(prec) if (is_tc and args.workload == WORKLOAD) else None
 
-    # end to end through the public API with host buffers
-    x_pin = torch.from_numpy(x_host).pin_memory()
     e2e_t = []
-    for i in range(max(3, args.steps // 2)):
+    for i in range(max(3, min(50, args.steps // 2))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        B = hos.bispectrum(x_pin, L, precision=prec, workspace=ws)  # H2D, compute, D2H inside
+        wl["e2e"]()  # host input -> device, compute, result -> host
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = statistics.median(e2e_t)
 
-    units = units_of(n, L) * world
+    extra = {}
+    if "per_series" in wl and rank == 0:
+        vd, offs, L = wl["per_series"]
+        ws1 = hos.Workspace()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for s_ in range(offs.size - 1):
+            hos.bispectrum(vd[offs[s_]:offs[s_ + 1]], L, precision=prec, workspace=ws1)
+        e1.record()
+        torch.cuda.synchronize()
+        extra["per_series_launches_ms"] = e0.elapsed_time(e1)
+
+    units = wl["units"] * world
     line = {
         "metric": METRIC,
         "value": units / (ms * 1e-3),
@@ -290,23 +412,26 @@ def run_ours(args):
         "dtype": {"bf16": "bf16x3 (split-bf16, fp32 accumulate, fp64 reduce)",
                   "fp32": "tf32x3 (fp32-class, fp32 accumulate, fp64 reduce)", "simt": "f32"}[prec],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "L": L, "grid": N, "precision": prec,
-                   "contraction": hos.last_contraction(), "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": dict({"workload": args.workload, "precision": prec, "contraction": hos.last_contraction(),
+                        "l2": "flushed between timed steps (256 MB write)",
+                        "launch": "cuda graph replay" if graph is not None else "eager (C ABI per step)",
+                        "parallelism": "replicas" if world > 1 else "single"}, **wl["config"]),
         "stage_ms": {k: statistics.mean(v) for k, v in stage_acc.items()},
-        "roofline": {"bound": "tensor" if prec != "simt" else "alu", "kernel": hos.last_contraction(),
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_source": peak_note,
-                     "frac_clock_matched": achieved / clock_peak if prec != "simt" else None,
-                     "work": f"{ntiles} tiles x 128 x {tile_n} x {kpad} samples x {products} products x 2 flops"},
-        "e2e": {"value": units_of(n, L) / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(x_host.nbytes),
-                "d2h_bytes_per_step": int(N * N * 8)},
+        "roofline": {"bound": wl["bound"], "kernel": hos.last_contraction(), "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "peak_source": peak_note,
+                     "frac_clock_matched": achieved / clock_peak if wl["bound"] == "tensor" else None,
+                     "work": wl["work"]},
+        "e2e": {"value": wl["units"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(wl["h2d"]),
+                "d2h_bytes_per_step": int(wl["d2h"])},
         "gpu_launches": launches,
         "clocks": clk,
         "wall_s_timed": t_wall,
     }
-    if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(x_host, L, n)
+    line.update(extra)
+    if rank == 0 and not args.no_cpu_baseline and args.workload == WORKLOAD:
+        import hos_synth
+        x_host = hos_synth.workload(WORKLOAD)["x"]
+        line["cpu_baseline"] = cpu_baseline(x_host, 256, x_host.size)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -323,6 +448,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "bispectrum_n2048_L32", "trispectrum_n65536_L32", "batched_4096x_L128",
+                             "differentiable_n262144_L128"])
+    ap.add_argument("--graph", action="store_true", help="capture one step in a CUDA graph and replay it")
+    ap.add_argument("--series", type=int, default=0, help="batched workload: use only the first K series")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -171,12 +171,12 @@ def cumulant3(x, L, precision="bf16", remove_mean=True, segment_len=0, tile_n=0,
     return out.cpu() if host else out
 
 
-def trispectrum(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=True, segment_len=0, out=None,
-                workspace=None, stream=None):
+def trispectrum(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=True, segment_len=0, flush_chunks=0,
+                out=None, workspace=None, stream=None):
     """Smoothed sample trispectrum T[k1, k2, k3] (complex64, nfft^3)."""
     torch = _torch()
     xd, host = _prepare(x)
-    p = make_params(L, nfft, precision, window, remove_mean, segment_len)
+    p = make_params(L, nfft, precision, window, remove_mean, segment_len, 0, flush_chunks)
     N = p.nfft or 2 * p.L
     if out is None:
         out = torch.empty((N, N, N), dtype=torch.complex64, device=xd.device)
@@ -188,11 +188,11 @@ def trispectrum(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=Tru
     return out.cpu() if host else out
 
 
-def cumulant4(x, L, precision="bf16", remove_mean=True, segment_len=0, workspace=None, stream=None):
+def cumulant4(x, L, precision="bf16", remove_mean=True, segment_len=0, flush_chunks=0, workspace=None, stream=None):
     """Unwindowed sample c4 over [-L, L-1]^3 (float64, (2L, 2L, 2L))."""
     torch = _torch()
     xd, host = _prepare(x)
-    p = make_params(L, 0, precision, "parzen", remove_mean, segment_len)
+    p = make_params(L, 0, precision, "parzen", remove_mean, segment_len, 0, flush_chunks)
     out = torch.empty((2 * p.L,) * 3, dtype=torch.float64, device=xd.device)
     ws = _workspace(workspace, xd.device)
     ws.get(workspace_size(_native.OP_CUMULANT4, xd.numel(), 1, xd.numel(), p))

@@ -151,7 +151,7 @@ static int plane_elt(int precision) {
 static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t status, off, pad, unit, win, mean, mpart, y32, hi, lo, partials, grid, tw, total;
+    size_t status, off, pad, unit, win, mean, mpart, bnd, xr, y32, hi, lo, partials, grid, tw, total;
     int64_t plane_len, slots;
     int nslices;
     int groups;
@@ -177,6 +177,8 @@ static Layout make_layout(int op, const hos_params* p, const C3Geom& g, int64_t 
     l.win = o; o = al256(o + 8 * (size_t)(S + 1));
     l.mean = o; o = al256(o + 8 * (size_t)S);
     l.mpart = o; o = al256(o + 8 * (size_t)S * l.nslices);
+    l.bnd = o; o = al256(o + 8 * (size_t)(g.G + 1));
+    l.xr = o; o = al256(o + 8 * (size_t)S * g.ntiles);
     l.y32 = o; o = al256(o + 4 * (size_t)l.plane_len);
     const int elt = plane_elt(p->precision);
     l.hi = o; o = al256(o + (size_t)elt * l.plane_len + 64);
@@ -250,6 +252,9 @@ static LineGeom line_geom(int N, int64_t nlines, int64_t inner, int64_t outer, i
     g.outer_stride = outer;
     g.elem_stride = elem;
     int lpb = (g.log2N >= 0) ? 4096 / N : 2048 / N;
+    // few lines: fewer per CTA so that the grid covers the SMs
+    const int64_t spread = nlines / (2 * (int64_t)sm_count());
+    if (spread < lpb) lpb = (int)(spread > 0 ? spread : 1);
     if (lpb < 1) lpb = 1;
     if (lpb > nlines) lpb = (int)(nlines > 0 ? nlines : 1);
     g.lpb = lpb;
@@ -295,7 +300,7 @@ static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int6
     } else {
         C3TcParams cp{g, sv, y32, hi, lo, partials, status, wait_limit_ns()};
         const bool tf32 = (p->precision == HOS_PREC_FP32);
-        HOS_CUDA_TRY(launch_c3_tc(tf32, cp, g.G, st));
+        HOS_CUDA_TRY(launch_c3_tc(tf32, 3, cp, g.G, st));
         g_last_contraction = tf32 ? "c3_tcgen05_3xtf32" : "c3_tcgen05_split_bf16";
     }
 
@@ -313,7 +318,7 @@ static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int6
     rp.c3out = c3_out;
     const int groups = rp.per_series_groups ? S : 1;
     if (red_mode == 0 && P.Nf > 2 * p->L) HOS_CUDA_TRY(launch_zero_f32(grid_out, (int64_t)groups * P.Nf * P.Nf, st));
-    HOS_CUDA_TRY(launch_reduce3(rp, groups, st));
+    HOS_CUDA_TRY(launch_reduce3(rp, groups, at<int64_t>(ws, l.bnd), at<int2>(ws, l.xr), st));
     return HOS_OK;
 }
 
@@ -333,8 +338,36 @@ struct Plan4 {
     int S;
     int64_t seg, max_len, total_groups;
     int Nf, W3, npb, nslices, pad_tail;
-    size_t status, off, pad, unit, win, mean, mpart, y32, c2, partials, grid, tw, total;
+    bool tc;    // tensor-core m4 (split-bf16 / 3xTF32) instead of FP32 SIMT
+    C3Geom g4;  // tensor-core geometry: tiles = blocks of 128 lag pairs, columns = w3
+    size_t status, off, pad, unit, win, mean, mpart, y32, hi, lo, bnd, xr, m4buf, c2, partials, grid, tw, total;
 };
+
+// Geometry of the tensor-core m4 contraction: tile t = pairs [128t, 128t+128)
+// of the lag triangle w1 <= w2 (rows), all w3 in [-L, L) (columns).
+static C3Geom make_geom4(const hos_params* p, int G) {
+    C3Geom g;
+    memset(&g, 0, sizeof(g));
+    const int twoL = 2 * p->L;
+    g.L = p->L;
+    int N = next_pow2(twoL);
+    if (N < 32) N = 32;
+    g.tile_n = N;
+    const int npairs = twoL * (twoL + 1) / 2;
+    g.tiles_m = (npairs + TILE_M - 1) / TILE_M;
+    g.tiles_n = 1;
+    g.ntiles = g.tiles_m;
+    for (int a = 0; a < MAX_TILES_M; ++a)
+        for (int b = 0; b < MAX_TILES_N; ++b) g.tile_idx[a][b] = -1;
+    for (int t = 0; t < g.ntiles; ++t) {
+        g.tile_a[t] = (uint8_t)t;
+        g.tile_b[t] = 0;
+    }
+    g.flush = p->flush_chunks ? p->flush_chunks : (p->precision == HOS_PREC_FP32 ? 1 : 16);
+    g.G = G;
+    g.pad_tail = 128 + N + 128;
+    return g;
+}
 
 static hos_status make_plan4(int op, const hos_params* p, int64_t n, Plan4& P) {
     hos_status s = check_params(p, op);
@@ -354,6 +387,13 @@ static hos_status make_plan4(int op, const hos_params* p, int64_t n, Plan4& P) {
     const int npairs = twoL * (twoL + 1) / 2;
     P.npb = (npairs + C4_PAIRS_PER_CTA - 1) / C4_PAIRS_PER_CTA;
     P.pad_tail = 32 + 128 + 64 + 64;
+    P.tc = (p->precision != HOS_PREC_SIMT_FP32);
+    if (P.tc) {
+        P.g4 = make_geom4(p, sm_count());
+        const int64_t U = (int64_t)P.g4.ntiles * ((P.S - 1) * ceil_div(P.max_len, KC) + ceil_div(last, KC));
+        if (U < P.g4.G) P.g4.G = (int)(U > 0 ? U : 1);
+        P.pad_tail = P.g4.pad_tail;
+    }
     P.nslices = (int)ceil_div(P.max_len > 0 ? P.max_len : 1, 8192);
     if (P.nslices > 256) P.nslices = 256;
     if (P.nslices < 1) P.nslices = 1;
@@ -368,7 +408,21 @@ static hos_status make_plan4(int op, const hos_params* p, int64_t n, Plan4& P) {
     P.mpart = o; o = al256(o + 8 * (size_t)P.S * P.nslices);
     P.y32 = o; o = al256(o + 4 * (size_t)plane_len);
     P.c2 = o; o = al256(o + 8 * (size_t)P.S * (4 * L - 1));
-    P.partials = o; o = al256(o + 4 * (size_t)P.total_groups * P.npb * C4_PAIRS_PER_CTA * P.W3);
+    if (P.tc) {
+        const C3Geom& g = P.g4;
+        const int elt = plane_elt(p->precision);
+        const int64_t chunks = ceil_div(n, KC) + P.S;
+        const int64_t slots = (int64_t)g.ntiles * (chunks / g.flush + P.S + 1) + g.G;
+        const size_t tsz = (size_t)TILE_M * g.tile_n;
+        P.hi = o; o = al256(o + (size_t)elt * plane_len + 64);
+        P.lo = o; o = al256(o + (size_t)elt * plane_len + 64);
+        P.bnd = o; o = al256(o + 8 * (size_t)(g.G + 1));
+        P.xr = o; o = al256(o + 8 * (size_t)P.S * g.ntiles);
+        P.partials = o; o = al256(o + 4 * (size_t)slots * tsz);
+        P.m4buf = o; o = al256(o + 8 * (size_t)P.S * g.ntiles * tsz);
+    } else {
+        P.partials = o; o = al256(o + 4 * (size_t)P.total_groups * P.npb * C4_PAIRS_PER_CTA * P.W3);
+    }
     P.grid = o; o = al256(o + (op == HOS_OP_TRISPECTRUM ? 4 * (size_t)P.Nf * P.Nf * P.Nf : 0));
     P.tw = o; o = al256(o + 8 * (size_t)P.Nf);
     P.total = o;
@@ -385,14 +439,19 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
     double* mean = at<double>(ws, P.mean);
     float* y32 = at<float>(ws, P.y32);
     tr.mark("prep");
-    HOS_CUDA_TRY(launch_plan_series(0, n, P.seg, nullptr, P.S, p->L, 1, C4_CHUNK_GROUP, P.pad_tail, off, pad, unit,
-                                    win, st));
+    const int ntiles = P.tc ? P.g4.ntiles : 1;
+    const int flush = P.tc ? P.g4.flush : C4_CHUNK_GROUP;
+    HOS_CUDA_TRY(launch_plan_series(0, n, P.seg, nullptr, P.S, p->L, ntiles, flush, P.pad_tail, off, pad, unit, win,
+                                    st));
     HOS_CUDA_TRY(launch_mean(x, dtype, off, P.S, P.nslices, at<double>(ws, P.mpart), p->remove_mean, mean, st));
     const int64_t maxpad = (int64_t)p->L + P.max_len + KC + P.pad_tail + 64;
     int bx = (int)ceil_div(maxpad, 256 * 4);
     if (bx < 1) bx = 1;
     if (bx > 65535) bx = 65535;
-    HOS_CUDA_TRY(launch_planes(x, dtype, off, pad, mean, p->L, 0, y32, nullptr, nullptr, P.S, bx, st));
+    void* hi = P.tc ? at<void>(ws, P.hi) : nullptr;
+    void* lo = P.tc ? at<void>(ws, P.lo) : nullptr;
+    HOS_CUDA_TRY(launch_planes(x, dtype, off, pad, mean, p->L, P.tc ? plane_split(p->precision) : 0, y32, hi, lo,
+                               P.S, bx, st));
     tr.mark("contract");
     C4ReduceArgs r;
     r.window = p->window;
@@ -402,9 +461,24 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
     r.grid = at<float>(ws, P.grid);
     r.c4out = c4out;
     if (mode == 0 && P.Nf > 2 * p->L) HOS_CUDA_TRY(launch_zero_f32(r.grid, (int64_t)P.Nf * P.Nf * P.Nf, st));
-    HOS_CUDA_TRY(launch_c4(y32, off, pad, win, P.S, p->L, C4_CHUNK_GROUP, P.total_groups, at<double>(ws, P.c2),
-                           at<float>(ws, P.partials), r, st));
-    g_last_contraction = "m4_simt_fp32";
+    if (!P.tc) {
+        HOS_CUDA_TRY(launch_c4(y32, off, pad, win, P.S, p->L, C4_CHUNK_GROUP, P.total_groups, at<double>(ws, P.c2),
+                               at<float>(ws, P.partials), r, st));
+        g_last_contraction = "m4_simt_fp32";
+        return HOS_OK;
+    }
+    double* c2 = at<double>(ws, P.c2);
+    HOS_CUDA_TRY(launch_c2(y32, off, pad, P.S, p->L, c2, st));
+    SeriesView sv{off, pad, unit, win, mean, P.S};
+    C3TcParams cp{P.g4, sv, y32, hi, lo, at<float>(ws, P.partials), at<int>(ws, P.status), wait_limit_ns()};
+    const bool tf32 = (p->precision == HOS_PREC_FP32);
+    HOS_CUDA_TRY(launch_c3_tc(tf32, 4, cp, P.g4.G, st));
+    g_last_contraction = tf32 ? "m4_tcgen05_3xtf32" : "m4_tcgen05_split_bf16";
+    tr.mark("reduce");
+    double* m4buf = at<double>(ws, P.m4buf);
+    HOS_CUDA_TRY(launch_m4_tile_reduce(P.g4, sv, at<float>(ws, P.partials), at<int64_t>(ws, P.bnd),
+                                       at<int2>(ws, P.xr), m4buf, st));
+    HOS_CUDA_TRY(launch_c4_assemble(m4buf, c2, off, P.S, p->L, P.g4.ntiles, P.g4.tile_n, r, st));
     return HOS_OK;
 }
 

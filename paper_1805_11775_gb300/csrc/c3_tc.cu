@@ -70,7 +70,11 @@ HOS_DEV void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                  : "memory");
 }
 
-template <bool TF32>
+// ORDER 3: rows of A are lags w1 (Y = y(i) y(i+w1)), tile row a covers
+//          w1 = -L + 128a + m; columns are lags w2 of tile column b.
+// ORDER 4: rows of A are lag pairs p = 128a + m with w1 <= w2
+//          (T = y(i) y(i+w1) y(i+w2)); columns are lags w3 = -L + j.
+template <bool TF32, int ORDER>
 __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     C3Smem& sm = *reinterpret_cast<C3Smem*>(smem_raw);
@@ -131,7 +135,8 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                 if (!ok) break;
                 const int64_t i0 = c * KC;
                 const int64_t wb = base + i0 + (int64_t)b * N;            // plane index of window start
-                const int64_t ab = base + i0 + (int64_t)a * TILE_M;       // y(i0 + w1_0)
+                // A window: y(i0 + w1_0 + t) for ORDER 3; y(i0 - L + t) for ORDER 4
+                const int64_t ab = (ORDER == 3) ? base + i0 + (int64_t)a * TILE_M : base + i0;
                 const int64_t ib = base + L + i0;                          // y(i0)
                 const int64_t ib_al = ib & ~(int64_t)3;
                 const uint32_t wbytes = (uint32_t)(KC + N + 16) * ELT;
@@ -186,15 +191,35 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
         }
     } else if (warp < 4) {
         // ------------------------------------------------------------ builders
-        const int m = warp * 32 + lane;  // TMEM lane = row of Y (w1 index in tile)
+        const int m = warp * 32 + lane;  // TMEM lane = row of A (lag w1, or lag pair, in the tile)
         uint32_t kc = 0, ks = 0;
         bool ok = true;
         while (ok && walk.next(part)) {
+            // ORDER 4: this row's lag pair (w1 <= w2); rows past the last pair give zeros
+            int o1 = 0, o2 = 0;
+            float live = 1.0f;
+            if constexpr (ORDER == 4) {
+                const int twoL = 2 * L, npairs = twoL * (twoL + 1) / 2;
+                const int pidx = geo.tile_a[part.t] * TILE_M + m;
+                int r = 0, start = 0;  // row r of the triangle holds pairs (r, r..2L-1)
+                while (r < twoL - 1 && start + (twoL - r) <= pidx) {
+                    start += twoL - r;
+                    ++r;
+                }
+                if (pidx >= npairs) {
+                    live = 0.0f;
+                    r = 0;
+                    start = 0;
+                }
+                o1 = L + (r - L);                  // ya index offset of y(i + w1): L + w1
+                o2 = L + (r + (pidx - start) - L);  // ya index offset of y(i + w2)
+                if (pidx >= npairs) o2 = L;
+            }
             for (int64_t c = part.c0; c < part.c1 && ok; ++c, ++kc) {
                 const int buf = kc & 1;
                 ok = warp_wait(&sm.full_b[buf], (kc >> 1) & 1, abort, P.status, lim, 2000);
                 if (!ok) break;
-                const float* ya = sm.ya[buf] + m;
+                const float* ya = sm.ya[buf] + (ORDER == 3 ? m : 0);
                 const float* yi = sm.yi[buf];
                 for (int kb = 0; kb < KC / KB; ++kb, ++ks) {
                     const int st = ks % NSTAGE;
@@ -205,7 +230,43 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                     const float* pa = ya + kb * KB;
                     const float* pi = yi + kb * KB;
                     const float4* pi4 = reinterpret_cast<const float4*>(pi);
-                    if constexpr (TF32) {
+                    if constexpr (ORDER == 4) {
+                        // T = y(i) y(i+w1) y(i+w2); ya[t] = y(i0 - L + t)
+                        const float* q1 = pa + o1;
+                        const float* q2 = pa + o2;
+                        if constexpr (TF32) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                const float4 v = pi4[q];
+                                const float pv[4] = {v.x * q1[4 * q] * q2[4 * q] * live,
+                                                     v.y * q1[4 * q + 1] * q2[4 * q + 1] * live,
+                                                     v.z * q1[4 * q + 2] * q2[4 * q + 2] * live,
+                                                     v.w * q1[4 * q + 3] * q2[4 * q + 3] * live};
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    const uint32_t h = to_tf32(pv[e]);
+                                    H[4 * q + e] = h;
+                                    Lw[4 * q + e] = to_tf32(pv[e] - __uint_as_float(h));
+                                }
+                            }
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) {
+                                const float4 v = pi4[q];
+                                const float p0 = v.x * q1[4 * q] * q2[4 * q] * live;
+                                const float p1 = v.y * q1[4 * q + 1] * q2[4 * q + 1] * live;
+                                const float p2 = v.z * q1[4 * q + 2] * q2[4 * q + 2] * live;
+                                const float p3 = v.w * q1[4 * q + 3] * q2[4 * q + 3] * live;
+                                const uint32_t h0 = pack_bf16x2(p0, p1), h1 = pack_bf16x2(p2, p3);
+                                H[2 * q] = h0;
+                                H[2 * q + 1] = h1;
+                                Lw[2 * q] = pack_bf16x2(p0 - __uint_as_float(h0 << 16),
+                                                        p1 - __uint_as_float(h0 & 0xFFFF0000u));
+                                Lw[2 * q + 1] = pack_bf16x2(p2 - __uint_as_float(h1 << 16),
+                                                            p3 - __uint_as_float(h1 & 0xFFFF0000u));
+                            }
+                        }
+                    } else if constexpr (TF32) {
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
                             const float4 v = pi4[q];
@@ -319,24 +380,28 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
     }
 }
 
-template __global__ void c3_tc_kernel<false>(const C3TcParams);
-template __global__ void c3_tc_kernel<true>(const C3TcParams);
 
-cudaError_t launch_c3_tc(bool tf32, const C3TcParams& p, int G, cudaStream_t st) {
+
+template <bool TF32, int ORDER>
+static cudaError_t launch_one(const C3TcParams& p, int G, cudaStream_t st) {
     // at least 116 KB so that exactly one CTA (and one 512-column TMEM
     // allocation) lands on each SM
     const size_t smem = sizeof(C3Smem) > 118784 ? sizeof(C3Smem) : 118784;
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[tf32]) {
-        cudaError_t e = tf32 ? cudaFuncSetAttribute(c3_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                             : cudaFuncSetAttribute(c3_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e =
+            cudaFuncSetAttribute(c3_tc_kernel<TF32, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set[tf32] = true;
+        attr_set = true;
     }
-    if (tf32) c3_tc_kernel<true><<<G, 320, smem, st>>>(p);
-    else c3_tc_kernel<false><<<G, 320, smem, st>>>(p);
+    c3_tc_kernel<TF32, ORDER><<<G, 320, smem, st>>>(p);
     count_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_c3_tc(bool tf32, int order, const C3TcParams& p, int G, cudaStream_t st) {
+    if (order == 4) return tf32 ? launch_one<true, 4>(p, G, st) : launch_one<false, 4>(p, G, st);
+    return tf32 ? launch_one<true, 3>(p, G, st) : launch_one<false, 3>(p, G, st);
 }
 
 }  // namespace hos

@@ -189,6 +189,60 @@ __global__ void reduce4_kernel(const Reduce4Params P) {
     P.grid[((int64_t)k1 * N + k2) * N + k3] = (float)(P.scale * wv * c4);
 }
 
+// Fourth order from the tensor-core path: c4 of each part from its m4 (m4buf)
+// and c2, averaged over parts, then windowed onto the grid (mode 0) or
+// written raw (mode 1).
+__global__ void c4_assemble_kernel(const double* __restrict__ m4buf, const double* __restrict__ c2,
+                                   const int64_t* __restrict__ off, int S, int L, int ntiles, int tile_n,
+                                   C4ReduceArgs r) {
+    const int twoL = 2 * L, T = 2 * L - 1;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)twoL * twoL * twoL) return;
+    const int w3 = (int)(e % twoL) - L;
+    const int w2 = (int)((e / twoL) % twoL) - L;
+    const int w1 = (int)(e / ((int64_t)twoL * twoL)) - L;
+    const int p = (w1 <= w2) ? pair_index(w1, w2, L) : pair_index(w2, w1, L);
+    const int t = p / TILE_M, m = p % TILE_M;
+    const int64_t tsz = (int64_t)TILE_M * tile_n;
+    const int64_t elem = (int64_t)(w3 + L) * TILE_M + m;
+    double c4 = 0.0;
+    int k = 0;
+    for (int s = 0; s < S; ++s) {
+        if (off[s + 1] <= off[s]) continue;
+        const double m4 = m4buf[((int64_t)s * ntiles + t) * tsz + elem];
+        const double* c = c2 + (int64_t)s * (2 * T + 1) + T;
+        c4 += m4 - c[w1] * c[w3 - w2] - c[w2] * c[w3 - w1] - c[w3] * c[w2 - w1];
+        ++k;
+    }
+    if (k > 0) c4 /= (double)k;
+    if (r.mode == 1) {
+        r.c4out[((int64_t)(w1 + L) * twoL + (w2 + L)) * twoL + (w3 + L)] = c4;
+        return;
+    }
+    const double wv = (r.window == HOS_WIN_RECT && (w1 == -L || w2 == -L || w3 == -L))
+                          ? 0.0
+                          : lag_window3(w1, w2, w3, L, r.window);
+    const int N = r.nfft;
+    const int k1 = (w1 % N + N) % N, k2 = (w2 % N + N) % N, k3 = (w3 % N + N) % N;
+    r.grid[((int64_t)k1 * N + k2) * N + k3] = (float)(r.scale * wv * c4);
+}
+
+cudaError_t launch_c2(const float* y32, const int64_t* off, const int64_t* pad, int S, int L, double* c2,
+                      cudaStream_t st) {
+    const int T = 2 * L - 1;
+    c2_kernel<<<dim3((unsigned)(2 * T + 1), (unsigned)S), 256, 0, st>>>(y32, off, pad, L, c2);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_c4_assemble(const double* m4buf, const double* c2, const int64_t* off, int S, int L, int ntiles,
+                               int tile_n, const C4ReduceArgs& r, cudaStream_t st) {
+    const int64_t n3 = 8LL * L * L * L;
+    c4_assemble_kernel<<<(unsigned)ceil_div(n3, 256), 256, 0, st>>>(m4buf, c2, off, S, L, ntiles, tile_n, r);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_c4(const float* y32, const int64_t* off, const int64_t* pad, const int64_t* win, int S, int L,
                       int CG, int64_t total_groups, double* c2, float* partials, const C4ReduceArgs& r,
                       cudaStream_t st) {

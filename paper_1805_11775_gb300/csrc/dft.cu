@@ -28,6 +28,11 @@ HOS_DEV int64_t line_base(const LineGeom& g, int64_t l) { return (l / g.inner) *
 
 HOS_DEV float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 
+// Shared-memory slot of element i of a line: one float2 of padding every 16
+// keeps bit-reversed and strided butterfly accesses off a single bank.
+HOS_DEV int sk(int i) { return i + (i >> 4); }
+HOS_HD int skewed_len(int N) { return N + (N >> 4); }
+
 template <bool REAL_IN>
 HOS_DEV float2 load_in(const void* in, int64_t idx) {
     if constexpr (REAL_IN) return make_float2(reinterpret_cast<const float*>(in)[idx], 0.0f);
@@ -39,40 +44,45 @@ template <bool REAL_IN>
 __global__ void fft_lines_kernel(const void* in, float2* out, const LineGeom g, const float2* __restrict__ tw,
                                  int sign, float scale) {
     extern __shared__ float2 sbuf[];
-    const int N = g.N, lpb = g.lpb;
+    const int N = g.N, lpb = g.lpb, SL = skewed_len(N);
+    int64_t* lbase = reinterpret_cast<int64_t*>(sbuf + (size_t)lpb * SL);  // line starts, computed once
     const int64_t l0 = (int64_t)blockIdx.x * lpb;
     const int nl = (int)((g.nlines - l0) < lpb ? (g.nlines - l0) : lpb);
     const int total = nl * N;
     const bool contiguous = (g.elem_stride == 1);
+    for (int l = threadIdx.x; l < nl; l += blockDim.x) lbase[l] = line_base(g, l0 + l);
+    __syncthreads();
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         int l, e;
-        if (contiguous) { l = idx / N; e = idx % N; }
-        else { e = idx / nl; l = idx % nl; }
-        const float2 v = load_in<REAL_IN>(in, line_base(g, l0 + l) + (int64_t)e * g.elem_stride);
+        if (contiguous) { l = idx >> g.log2N; e = idx & (N - 1); }
+        else { e = idx / nl; l = idx - e * nl; }
+        const float2 v = load_in<REAL_IN>(in, lbase[l] + (int64_t)e * g.elem_stride);
         const int r = (int)(__brev((unsigned)e) >> (32 - g.log2N));
-        sbuf[l * N + r] = v;
+        sbuf[l * SL + sk(r)] = v;
     }
     __syncthreads();
-    for (int h = 1; h < N; h <<= 1) {
-        const int tstride = N / (2 * h);
+    const int lg = g.log2N;
+    for (int sh = 0; sh < lg; ++sh) {  // butterfly span h = 2^sh, twiddle stride N / 2h
+        const int h = 1 << sh;
         for (int bf = threadIdx.x; bf < nl * (N / 2); bf += blockDim.x) {
-            const int l = bf / (N / 2), k = bf % (N / 2);
-            const int j = k % h, blk = k / h;
-            const int i0 = l * N + blk * 2 * h + j, i1 = i0 + h;
-            float2 w = tw[j * tstride];
+            const int l = bf >> (lg - 1), k = bf & ((N >> 1) - 1);
+            const int j = k & (h - 1), blk = k >> sh;
+            const int i0 = (blk << (sh + 1)) + j, i1 = i0 + h;
+            float2 w = tw[j << (lg - 1 - sh)];
             if (sign > 0) w.y = -w.y;
-            const float2 a = sbuf[i0], b = cmul(sbuf[i1], w);
-            sbuf[i0] = make_float2(a.x + b.x, a.y + b.y);
-            sbuf[i1] = make_float2(a.x - b.x, a.y - b.y);
+            float2* row = sbuf + l * SL;
+            const float2 a = row[sk(i0)], b = cmul(row[sk(i1)], w);
+            row[sk(i0)] = make_float2(a.x + b.x, a.y + b.y);
+            row[sk(i1)] = make_float2(a.x - b.x, a.y - b.y);
         }
         __syncthreads();
     }
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         int l, e;
-        if (contiguous) { l = idx / N; e = idx % N; }
-        else { e = idx / nl; l = idx % nl; }
-        const float2 v = sbuf[l * N + e];
-        out[line_base(g, l0 + l) + (int64_t)e * g.elem_stride] = make_float2(v.x * scale, v.y * scale);
+        if (contiguous) { l = idx >> g.log2N; e = idx & (N - 1); }
+        else { e = idx / nl; l = idx - e * nl; }
+        const float2 v = sbuf[l * SL + sk(e)];
+        out[lbase[l] + (int64_t)e * g.elem_stride] = make_float2(v.x * scale, v.y * scale);
     }
 }
 
@@ -81,12 +91,15 @@ __global__ void dft_lines_kernel(const void* in, float2* out, const LineGeom g, 
                                  int sign, float scale) {
     extern __shared__ float2 sbuf[];
     const int N = g.N, lpb = g.lpb;
+    int64_t* lbase = reinterpret_cast<int64_t*>(sbuf + 2 * (size_t)lpb * N);
     const int64_t l0 = (int64_t)blockIdx.x * lpb;
     const int nl = (int)((g.nlines - l0) < lpb ? (g.nlines - l0) : lpb);
     const int total = nl * N;
+    for (int l = threadIdx.x; l < nl; l += blockDim.x) lbase[l] = line_base(g, l0 + l);
+    __syncthreads();
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int l = idx / N, e = idx % N;
-        sbuf[idx] = load_in<REAL_IN>(in, line_base(g, l0 + l) + (int64_t)e * g.elem_stride);
+        sbuf[idx] = load_in<REAL_IN>(in, lbase[l] + (int64_t)e * g.elem_stride);
     }
     __syncthreads();
     float2* res = sbuf + lpb * N;
@@ -105,7 +118,7 @@ __global__ void dft_lines_kernel(const void* in, float2* out, const LineGeom g, 
     __syncthreads();
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int l = idx / N, e = idx % N;
-        out[line_base(g, l0 + l) + (int64_t)e * g.elem_stride] = res[idx];
+        out[lbase[l] + (int64_t)e * g.elem_stride] = res[idx];
     }
 }
 
@@ -120,11 +133,11 @@ cudaError_t launch_lines(bool real_in, const void* in, float2* out, LineGeom g, 
     if (g.nlines <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)ceil_div(g.nlines, g.lpb);
     if (g.log2N >= 0) {
-        const size_t smem = (size_t)g.lpb * g.N * sizeof(float2);
+        const size_t smem = (size_t)g.lpb * skewed_len(g.N) * sizeof(float2) + (size_t)g.lpb * sizeof(int64_t);
         if (real_in) fft_lines_kernel<true><<<blocks, 256, smem, st>>>(in, out, g, tw, sign, scale);
         else fft_lines_kernel<false><<<blocks, 256, smem, st>>>(in, out, g, tw, sign, scale);
     } else {
-        const size_t smem = 2 * (size_t)g.lpb * g.N * sizeof(float2);
+        const size_t smem = 2 * (size_t)g.lpb * g.N * sizeof(float2) + (size_t)g.lpb * sizeof(int64_t);
         if (real_in) dft_lines_kernel<true><<<blocks, 256, smem, st>>>(in, out, g, tw, sign, scale);
         else dft_lines_kernel<false><<<blocks, 256, smem, st>>>(in, out, g, tw, sign, scale);
     }

@@ -72,9 +72,9 @@ cudaError_t launch_mean(const void* x, int dtype, const int64_t* off, int S, int
                         int remove_mean, double* mean, cudaStream_t st);
 cudaError_t launch_planes(const void* x, int dtype, const int64_t* off, const int64_t* pad, const double* mean, int L,
                           int split, float* y32, void* hi, void* lo, int S, int blocks_x, cudaStream_t st);
-cudaError_t launch_c3_tc(bool tf32, const C3TcParams& p, int G, cudaStream_t st);
+cudaError_t launch_c3_tc(bool tf32, int order, const C3TcParams& p, int G, cudaStream_t st);
 cudaError_t launch_c3_simt(const C3SimtParams& p, int G, cudaStream_t st);
-cudaError_t launch_reduce3(const Reduce3Params& p, int groups, cudaStream_t st);
+cudaError_t launch_reduce3(const Reduce3Params& p, int groups, int64_t* bnd, int2* xr, cudaStream_t st);
 cudaError_t launch_zero_f32(float* p, int64_t n, cudaStream_t st);
 cudaError_t launch_twiddles(int N, float2* tw, cudaStream_t st);
 cudaError_t launch_lines(bool real_in, const void* in, float2* out, LineGeom g, const float2* tw, int sign,
@@ -87,6 +87,12 @@ cudaError_t launch_adjoint(const float* yS, int64_t n, int L, const float2* Gc, 
 cudaError_t launch_adjoint_finish(const float* g, int64_t n, const double* gmean, int remove_mean, int dtype, void* dx,
                                   cudaStream_t st);
 constexpr int ADJ_ROWS_PER_CTA = 64;
+cudaError_t launch_m4_tile_reduce(const C3Geom& geo, const SeriesView& sv, const float* partials, int64_t* bnd,
+                                  int2* xr, double* m4buf, cudaStream_t st);
+cudaError_t launch_c2(const float* y32, const int64_t* off, const int64_t* pad, int S, int L, double* c2,
+                      cudaStream_t st);
+cudaError_t launch_c4_assemble(const double* m4buf, const double* c2, const int64_t* off, int S, int L, int ntiles,
+                               int tile_n, const C4ReduceArgs& r, cudaStream_t st);
 cudaError_t launch_timeout_selftest(int* status, uint64_t limit_ns, cudaStream_t st);
 
 }  // namespace hos

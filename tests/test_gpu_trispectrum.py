@@ -1,6 +1,7 @@
 """GPU parity of the trispectrum path (c2, m4 over symmetric lag pairs, the
 c2*c2 correction, window, 3-axis transform) against the FP64 oracle.
-Normwise tolerance 1e-5 (FP32 contraction, FP64 reductions)."""
+Normwise tolerances as for the bispectrum: split-bf16 tensor cores 1e-4,
+3xTF32 tensor cores 1e-5, FP32 SIMT 1e-5."""
 import math
 
 import numpy as np
@@ -13,7 +14,8 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no GPU", allow_module_level=True)
 
-TOL = 1e-5
+TOL = {"bf16": 1e-4, "fp32": 1e-5, "simt": 1e-5}
+PRECS = ["simt", "fp32", "bf16"]
 
 
 @pytest.fixture(scope="module")
@@ -28,47 +30,56 @@ def normwise(got, ref):
     return np.abs(np.asarray(got, dtype=np.complex128) - ref).max() / np.abs(ref).max()
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("n,L", [(5, 1), (40, 3), (700, 8), (1500, 13), (2100, 32), (1200, 64)])
-def test_cumulant4_elementwise(hos, oracle, n, L):
+def test_cumulant4_elementwise(hos, oracle, n, L, prec):
     x = hos_synth.ma(n, 5 * n + L)
     ref = oracle.c4(oracle.demean(x), L)[:2 * L, :2 * L, :2 * L]
-    got = hos.cumulant4(torch.from_numpy(x).cuda(), L).cpu().numpy()
-    assert np.abs(got - ref).max() <= TOL * np.abs(ref).max()
+    got = hos.cumulant4(torch.from_numpy(x).cuda(), L, precision=prec).cpu().numpy()
+    assert np.abs(got - ref).max() <= TOL[prec] * np.abs(ref).max()
 
 
-def test_cumulant4_is_symmetric(hos):
+@pytest.mark.parametrize("prec", PRECS)
+def test_cumulant4_is_symmetric(hos, prec):
     x = torch.from_numpy(hos_synth.exp_noise(5000, 2)).cuda()
-    c = hos.cumulant4(x, 8).cpu().numpy()
+    c = hos.cumulant4(x, 8, precision=prec).cpu().numpy()
     # w1 <-> w2 reads the same lag-pair partial sums; only the FP64 c2*c2
     # terms change order
     assert np.abs(np.transpose(c, (1, 0, 2)) - c).max() <= 1e-12 * np.abs(c).max()
     # swaps with w3 pair the samples differently, so they agree to FP32 rounding
     for perm in [(2, 1, 0), (0, 2, 1)]:
-        assert np.abs(np.transpose(c, perm) - c).max() <= 1e-6 * np.abs(c).max()
+        assert np.abs(np.transpose(c, perm) - c).max() <= (1e-6 if prec == "simt" else TOL[prec]) * np.abs(c).max()
 
 
-def test_trispectrum_full_size_workload(hos, oracle):
+@pytest.fixture(scope="module")
+def tri_ref(oracle):
+    w = hos_synth.workload("trispectrum_n65536_L32")
+    return w, oracle.trispectrum(w["x"].astype(np.float64), w["L"], w["N"])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_trispectrum_full_size_workload(hos, tri_ref, prec):
     """n = 65536 float32 MA(3) series, L = 32, 64^3 grid: the whole output
     against the oracle."""
-    w = hos_synth.workload("trispectrum_n65536_L32")
-    ref = oracle.trispectrum(w["x"].astype(np.float64), w["L"], w["N"])
-    got = hos.trispectrum(torch.from_numpy(w["x"]).cuda(), w["L"]).cpu().numpy()
-    assert normwise(got, ref) <= TOL
+    w, ref = tri_ref
+    got = hos.trispectrum(torch.from_numpy(w["x"]).cuda(), w["L"], precision=prec).cpu().numpy()
+    assert normwise(got, ref) <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("n,L,N,seg", [(3000, 6, 14, 0), (5000, 10, 20, 1700), (2500, 16, 32, 0)])
-def test_trispectrum_grids_and_parts(hos, oracle, n, L, N, seg):
+def test_trispectrum_grids_and_parts(hos, oracle, n, L, N, seg, prec):
     x = hos_synth.ar2(n, 3 * n)
     ref = oracle.trispectrum(x, L, N, segment_len=seg)
-    got = hos.trispectrum(torch.from_numpy(x).cuda(), L, nfft=N, segment_len=seg).cpu().numpy()
-    assert normwise(got, ref) <= TOL
+    got = hos.trispectrum(torch.from_numpy(x).cuda(), L, nfft=N, segment_len=seg, precision=prec).cpu().numpy()
+    assert normwise(got, ref) <= TOL[prec]
 
 
 def test_trispectrum_hermitian_and_flat_level(hos):
     """Centred Exp(1) noise: c4(0,0,0) estimates the fourth cumulant 6, so the
     grid average of (2 pi)^3 T is near 6, and T(-k) = conj T(k)."""
     x = torch.from_numpy(hos_synth.exp_noise(1 << 20, 12)).cuda()
-    T = hos.trispectrum(x, 8).cpu().numpy().astype(np.complex128)
+    T = hos.trispectrum(x, 8, precision="bf16").cpu().numpy().astype(np.complex128)
     N = T.shape[0]
     k = np.arange(N)
     neg = T[(-k[:, None, None]) % N, (-k[None, :, None]) % N, (-k[None, None, :]) % N]
