@@ -218,9 +218,9 @@ def make_workload(name, prec, rank, hos, torch, series=0):
         x_host = w["x"]
         xd = torch.from_numpy(x_host).cuda()
         out = torch.empty((N, N, N), dtype=torch.complex64, device="cuda")
-        step = lambda: hos.trispectrum(xd, L, out=out, workspace=ws)
+        step = lambda: hos.trispectrum(xd, L, precision=prec, out=out, workspace=ws)
         x_pin = torch.from_numpy(x_host).pin_memory()
-        e2e = lambda: hos.trispectrum(x_pin, L, workspace=ws)
+        e2e = lambda: hos.trispectrum(x_pin, L, precision=prec, workspace=ws)
         twoL = 2 * L
         npairs = twoL * (twoL + 1) // 2
         w3 = 16 * math.ceil(twoL / 16)

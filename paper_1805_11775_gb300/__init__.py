@@ -42,6 +42,15 @@ def make_params(L, nfft=0, precision="bf16", window="parzen", remove_mean=True, 
                      int(tile_n or 0), int(flush_chunks or 0))
 
 
+def _tuned(op, L, n_total, n_series, precision, tile_n, flush_chunks):
+    """The caller's knobs, else the autotuner's cached choice, else automatic."""
+    if tile_n or flush_chunks:
+        return tile_n, flush_chunks
+    from . import tune
+    r = tune.lookup(op, L, n_total, n_series, precision if isinstance(precision, str) else str(precision))
+    return r if r else (0, 0)
+
+
 def workspace_size(op: int, n_total: int, n_series: int, max_len: int, params: HosParams) -> int:
     out = ctypes.c_size_t(0)
     _native.check(_native.lib().hos_workspace_size(op, int(n_total), int(n_series), int(max_len),
@@ -119,6 +128,7 @@ def bispectrum(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=True
     cores) or "simt" (FP32 CUDA cores).  Host input returns a host result."""
     torch = _torch()
     xd, host = _prepare(x)
+    tile_n, flush_chunks = _tuned("bispectrum", L, xd.numel(), 1, precision, tile_n, flush_chunks)
     p = make_params(L, nfft, precision, window, remove_mean, segment_len, tile_n, flush_chunks)
     N = p.nfft or 2 * p.L
     if out is None:
@@ -144,6 +154,7 @@ def bispectrum_batched(values, offsets, L, nfft=0, precision="bf16", window="par
         max_len = int((oh[1:] - oh[:-1]).max().item()) if oh.numel() > 1 else 0
     od = offs.to(vd.device, non_blocking=True).contiguous()
     S = od.numel() - 1
+    tile_n, flush_chunks = _tuned("bispectrum_batched", L, vd.numel(), S, precision, tile_n, flush_chunks)
     p = make_params(L, nfft, precision, window, remove_mean, 0, tile_n, flush_chunks)
     N = p.nfft or 2 * p.L
     if out is None:

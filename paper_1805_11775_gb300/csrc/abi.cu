@@ -133,6 +133,7 @@ static C3Geom make_geom(const hos_params* p, int G) {
     // 1024-sample chunk; split-bf16 (16 samples per step, 1e-4 target) and SIMT
     // (FP32 FFMA, round to nearest) after 16 chunks.
     g.flush = p->flush_chunks ? p->flush_chunks : (p->precision == HOS_PREC_FP32 ? 1 : 16);
+    g.kc = KC;
     g.G = G;
     const int reach = (g.tiles_m * TILE_M > g.tiles_n * N) ? g.tiles_m * TILE_M : g.tiles_n * N;
     g.pad_tail = reach + 64;
@@ -166,7 +167,7 @@ static Layout make_layout(int op, const hos_params* p, const C3Geom& g, int64_t 
     if (l.nslices > 256) l.nslices = 256;
     if (l.nslices < 1) l.nslices = 1;
     l.plane_len = n_total + (int64_t)S * ((int64_t)p->L + KC + g.pad_tail + 64);
-    const int64_t chunks = ceil_div(n_total, KC) + S;
+    const int64_t chunks = ceil_div(n_total, g.kc) + S;
     l.slots = (int64_t)g.ntiles * (chunks / g.flush + S + 1) + g.G;
     l.groups = (op == HOS_OP_BISPECTRUM_BATCHED) ? S : 1;
     size_t o = 0;
@@ -219,7 +220,7 @@ static hos_status make_plan(int op, const hos_params* p, int64_t n_total, int S_
         P.max_len = P.seg ? P.seg : n_total;
         // exact chunk count: full parts plus the (possibly shorter) last one
         const int64_t last = n_total - (P.S - 1) * (P.seg ? P.seg : 0);
-        U_known = (P.S - 1) * ceil_div(P.max_len, KC) + ceil_div(last, KC);
+        U_known = (P.S - 1) * ceil_div(P.max_len, KC) + ceil_div(last, KC);  // chunks at KC = make_geom's kc
     }
     if (P.S > 65535) return HOS_ERR_UNSUPPORTED;
     int G = contraction_ctas(p->precision);
@@ -282,8 +283,8 @@ static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int6
 
     tr.mark("prep");
     const int mode = (op == HOS_OP_BISPECTRUM_BATCHED) ? 1 : 0;
-    HOS_CUDA_TRY(launch_plan_series(mode, n, P.seg, d_offsets, S, p->L, g.ntiles, g.flush, g.pad_tail, off, pad,
-                                    unit, win, st));
+    HOS_CUDA_TRY(launch_plan_series(mode, n, P.seg, d_offsets, S, p->L, g.ntiles, g.flush, g.kc, g.pad_tail, off,
+                                    pad, unit, win, st));
     HOS_CUDA_TRY(launch_mean(x, dtype, off, S, l.nslices, at<double>(ws, l.mpart), p->remove_mean, mean, st));
     const int64_t maxpad = (int64_t)p->L + P.max_len + KC + g.pad_tail + 64;
     int bx = (int)ceil_div(maxpad, 256 * 4);
@@ -363,7 +364,11 @@ static C3Geom make_geom4(const hos_params* p, int G) {
         g.tile_a[t] = (uint8_t)t;
         g.tile_b[t] = 0;
     }
-    g.flush = p->flush_chunks ? p->flush_chunks : (p->precision == HOS_PREC_FP32 ? 1 : 16);
+    // c4 = m4 - sum c2*c2 cancels, which magnifies the tensor cores' one-sided
+    // FP32 accumulation loss: partials go to the FP64 reduction after every
+    // chunk, and 3xTF32 chunks are 128 samples (48 MMA steps)
+    g.flush = p->flush_chunks ? p->flush_chunks : 1;
+    g.kc = (p->precision == HOS_PREC_FP32) ? 128 : KC;
     g.G = G;
     g.pad_tail = 128 + N + 128;
     return g;
@@ -390,7 +395,7 @@ static hos_status make_plan4(int op, const hos_params* p, int64_t n, Plan4& P) {
     P.tc = (p->precision != HOS_PREC_SIMT_FP32);
     if (P.tc) {
         P.g4 = make_geom4(p, sm_count());
-        const int64_t U = (int64_t)P.g4.ntiles * ((P.S - 1) * ceil_div(P.max_len, KC) + ceil_div(last, KC));
+        const int64_t U = (int64_t)P.g4.ntiles * ((P.S - 1) * ceil_div(P.max_len, P.g4.kc) + ceil_div(last, P.g4.kc));
         if (U < P.g4.G) P.g4.G = (int)(U > 0 ? U : 1);
         P.pad_tail = P.g4.pad_tail;
     }
@@ -411,7 +416,7 @@ static hos_status make_plan4(int op, const hos_params* p, int64_t n, Plan4& P) {
     if (P.tc) {
         const C3Geom& g = P.g4;
         const int elt = plane_elt(p->precision);
-        const int64_t chunks = ceil_div(n, KC) + P.S;
+        const int64_t chunks = ceil_div(n, g.kc) + P.S;
         const int64_t slots = (int64_t)g.ntiles * (chunks / g.flush + P.S + 1) + g.G;
         const size_t tsz = (size_t)TILE_M * g.tile_n;
         P.hi = o; o = al256(o + (size_t)elt * plane_len + 64);
@@ -441,8 +446,9 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
     tr.mark("prep");
     const int ntiles = P.tc ? P.g4.ntiles : 1;
     const int flush = P.tc ? P.g4.flush : C4_CHUNK_GROUP;
-    HOS_CUDA_TRY(launch_plan_series(0, n, P.seg, nullptr, P.S, p->L, ntiles, flush, P.pad_tail, off, pad, unit, win,
-                                    st));
+    const int kc = P.tc ? P.g4.kc : KC;
+    HOS_CUDA_TRY(launch_plan_series(0, n, P.seg, nullptr, P.S, p->L, ntiles, flush, kc, P.pad_tail, off, pad, unit,
+                                    win, st));
     HOS_CUDA_TRY(launch_mean(x, dtype, off, P.S, P.nslices, at<double>(ws, P.mpart), p->remove_mean, mean, st));
     const int64_t maxpad = (int64_t)p->L + P.max_len + KC + P.pad_tail + 64;
     int bx = (int)ceil_div(maxpad, 256 * 4);
@@ -677,8 +683,8 @@ hos_status hos_bispectrum_backward(const void* d_x, int32_t dtype, int64_t n, co
     float* y32 = at<float>(ws, P.y32);
     const int L = p->L, Nf = P.Nf;
     tr.mark("prep");
-    HOS_CUDA_TRY(launch_plan_series(0, n, 0, nullptr, 1, L, 1, 16, P.g.pad_tail, off, pad, at<int64_t>(ws, P.unit),
-                                    at<int64_t>(ws, P.win), st));
+    HOS_CUDA_TRY(launch_plan_series(0, n, 0, nullptr, 1, L, 1, 16, KC, P.g.pad_tail, off, pad,
+                                    at<int64_t>(ws, P.unit), at<int64_t>(ws, P.win), st));
     HOS_CUDA_TRY(launch_mean(d_x, dtype, off, 1, P.nslices, at<double>(ws, P.mpart), p->remove_mean,
                              at<double>(ws, P.mean), st));
     int bx = (int)ceil_div((int64_t)L + n + KC + P.g.pad_tail + 64, 256 * 4);

@@ -31,18 +31,19 @@ __global__ void __launch_bounds__(256) c3_simt_kernel(const C3SimtParams P) {
         for (int r = 0; r < 8; ++r)
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[r][c] = 0.0f;
+        const int kc = geo.kc;
         for (int64_t ch = part.c0; ch < part.c1; ++ch) {
-            const int64_t i0 = ch * KC;
+            const int64_t i0 = ch * kc;
             const float* ga = P.y32 + base + i0 + (int64_t)a * TILE_M;
             const float* gi = P.y32 + base + geo.L + i0;
             const float* gb = P.y32 + base + i0 + (int64_t)b * N;
             __syncthreads();
-            for (int t = threadIdx.x; t < KC + TILE_M; t += 256) ya[t] = ga[t];
-            for (int t = threadIdx.x; t < KC; t += 256) yi[t] = gi[t];
-            for (int t = threadIdx.x; t < KC + N; t += 256) yb[t] = gb[t];
+            for (int t = threadIdx.x; t < kc + TILE_M; t += 256) ya[t] = ga[t];
+            for (int t = threadIdx.x; t < kc; t += 256) yi[t] = gi[t];
+            for (int t = threadIdx.x; t < kc + N; t += 256) yb[t] = gb[t];
             __syncthreads();
 #pragma unroll 4
-            for (int i = 0; i < KC; ++i) {
+            for (int i = 0; i < kc; ++i) {
                 const float v = yi[i];
                 float av[8], bv[NC];
 #pragma unroll

@@ -51,7 +51,7 @@ struct __align__(16) C3Smem {
     uint8_t lin_hi[WIN_SAMPLES * 4];  // linear staging of the hi plane window
     uint8_t lin_lo[WIN_SAMPLES * 4];
     uint64_t full_b[2], empty_b[2], full_a[NSTAGE], empty_a[NSTAGE];
-    uint64_t acc_full, acc_empty, drain, tma_bar;
+    uint64_t acc_full[2], acc_empty[2], drain, tma_bar;
     uint32_t tmem_base;
     int abort;
 };
@@ -90,6 +90,11 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
     constexpr uint32_t LBO = GROUP_BYTES;          // next core matrix along K: +R samples
     constexpr uint32_t SBO = 16u * 8u;             // next 8 rows along N: +8 samples = 128 bytes
     const uint32_t idesc = make_idesc(TF32, TILE_M, N);
+    const int kc = geo.kc;  // samples per chunk
+    // accumulators: two TMEM buffers (columns [0,128) and [128,256)) when the
+    // tile is at most 128 wide, so the epilogue drains one while the MMAs fill
+    // the other; one buffer of N columns otherwise
+    const uint32_t nacc = (N <= 128) ? 2u : 1u;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; ++i) {
@@ -100,8 +105,10 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
             mbar_init(&sm.full_a[i], 128);
             mbar_init(&sm.empty_a[i], 1);
         }
-        mbar_init(&sm.acc_full, 1);
-        mbar_init(&sm.acc_empty, 128);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&sm.acc_full[i], 1);
+            mbar_init(&sm.acc_empty[i], 128);
+        }
         mbar_init(&sm.drain, 1);
         mbar_init(&sm.tma_bar, 1);
         sm.abort = 0;
@@ -133,29 +140,30 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                 const int buf = kc & 1;
                 ok = warp_wait(&sm.empty_b[buf], ((kc >> 1) & 1) ^ 1, abort, P.status, lim, 2000);
                 if (!ok) break;
-                const int64_t i0 = c * KC;
+                const int64_t i0 = c * kc;
                 const int64_t wb = base + i0 + (int64_t)b * N;            // plane index of window start
                 // A window: y(i0 + w1_0 + t) for ORDER 3; y(i0 - L + t) for ORDER 4
                 const int64_t ab = (ORDER == 3) ? base + i0 + (int64_t)a * TILE_M : base + i0;
                 const int64_t ib = base + L + i0;                          // y(i0)
                 const int64_t ib_al = ib & ~(int64_t)3;
-                const uint32_t wbytes = (uint32_t)(KC + N + 16) * ELT;
+                const uint32_t wbytes = (uint32_t)(kc + N + 16) * ELT;
                 if (lane == 0) {
-                    mbar_expect_tx(&sm.tma_bar, 2 * wbytes + YA_FLOATS * 4 + YI_FLOATS * 4);
+                    const uint32_t yab = (uint32_t)(kc + TILE_M) * 4, yib = (uint32_t)(kc + 4) * 4;
+                    mbar_expect_tx(&sm.tma_bar, 2 * wbytes + yab + yib);
                     bulk_g2s(sm.lin_hi, (const uint8_t*)P.hi + wb * ELT, wbytes, &sm.tma_bar);
                     bulk_g2s(sm.lin_lo, (const uint8_t*)P.lo + wb * ELT, wbytes, &sm.tma_bar);
-                    bulk_g2s(sm.ya[buf], P.y32 + ab, YA_FLOATS * 4, &sm.tma_bar);
-                    bulk_g2s(sm.yi_raw, P.y32 + ib_al, YI_FLOATS * 4, &sm.tma_bar);
+                    bulk_g2s(sm.ya[buf], P.y32 + ab, yab, &sm.tma_bar);
+                    bulk_g2s(sm.yi_raw, P.y32 + ib_al, yib, &sm.tma_bar);
                 }
                 ok = warp_wait(&sm.tma_bar, tph, abort, P.status, lim, 1000);
                 tph ^= 1;
                 if (!ok) break;
                 {   // realign y(i0 + t) so that builders can use 16-byte broadcast loads
                     const int ish = (int)(ib - ib_al);
-                    for (int t = lane; t < KC; t += 32) sm.yi[buf][t] = sm.yi_raw[ish + t];
+                    for (int t = lane; t < kc; t += 32) sm.yi[buf][t] = sm.yi_raw[ish + t];
                 }
                 // interleave: block (q, r) <- samples [R q + r, R q + r + R)
-                const int ngroups = (KC + N) / R + 2;
+                const int ngroups = (kc + N) / R + 2;
                 const int nblocks = ngroups * R;
                 for (int blk = lane; blk < nblocks; blk += 32) {
                     const int q = blk / R, r = blk % R;
@@ -221,7 +229,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                 if (!ok) break;
                 const float* ya = sm.ya[buf] + (ORDER == 3 ? m : 0);
                 const float* yi = sm.yi[buf];
-                for (int kb = 0; kb < KC / KB; ++kb, ++ks) {
+                for (int kb = 0; kb < kc / KB; ++kb, ++ks) {
                     const int st = ks % NSTAGE;
                     ok = warp_wait(&sm.empty_a[st], ((ks / NSTAGE) & 1) ^ 1, abort, P.status, lim, 1000);
                     if (!ok) break;
@@ -309,19 +317,20 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
         uint32_t it = 0;
         bool ok = true;
         while (ok && walk.next(part)) {
-            ok = warp_wait(&sm.acc_full, it & 1, abort, P.status, lim, 20000);
+            const uint32_t ab_ = it % nacc;
+            ok = warp_wait(&sm.acc_full[ab_], (it / nacc) & 1, abort, P.status, lim, 20000);
             if (!ok) break;
             tc_fence_after();
             float* dst = P.partials + part.slot * (int64_t)(TILE_M * N) + m;
             for (int cc = 0; cc < N; cc += 32) {
                 uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)cc, v);
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + ab_ * 128u + (uint32_t)cc, v);
                 tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < 32; ++j) dst[(int64_t)(cc + j) * TILE_M] = __uint_as_float(v[j]);
             }
             tc_fence_before();
-            mbar_arrive(&sm.acc_empty);
+            mbar_arrive(&sm.acc_empty[ab_]);
             ++it;
         }
     } else if (warp == 9 && lane == 0) {
@@ -330,7 +339,9 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
         bool ok = true;
         const uint32_t wh0 = smem_u32(sm.win_hi[0]), wl0 = smem_u32(sm.win_lo[0]);
         while (ok && walk.next(part)) {
-            ok = mbar_wait(&sm.acc_empty, (it & 1) ^ 1, abort, P.status, lim);
+            const uint32_t ab_ = it % nacc;
+            const uint32_t dacc = tmem + ab_ * 128u;  // this part's accumulator
+            ok = mbar_wait(&sm.acc_empty[ab_], ((it / nacc) & 1) ^ 1, abort, P.status, lim);
             if (!ok) break;
             tc_fence_after();
             uint32_t acc = 0;
@@ -340,7 +351,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t wh = wh0 + (uint32_t)buf * WIN_BYTES, wl = wl0 + (uint32_t)buf * WIN_BYTES;
-                for (int kb = 0; kb < KC / KB; ++kb, ++ks) {
+                for (int kb = 0; kb < kc / KB; ++kb, ++ks) {
                     const int st = ks % NSTAGE;
                     ok = mbar_wait(&sm.full_a[st], (ks / NSTAGE) & 1, abort, P.status, lim);
                     if (!ok) break;
@@ -353,17 +364,17 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                         const uint32_t boff = (koff / R) * GROUP_BYTES;
                         const uint64_t bh = make_sdesc(wh + boff, LBO, SBO);
                         const uint64_t bl = make_sdesc(wl + boff, LBO, SBO);
-                        mma_ts<TF32>(tmem, a_hi, bh, idesc, acc);
+                        mma_ts<TF32>(dacc, a_hi, bh, idesc, acc);
                         acc = 1;
-                        mma_ts<TF32>(tmem, a_hi, bl, idesc, 1);
-                        mma_ts<TF32>(tmem, a_lo, bh, idesc, 1);
+                        mma_ts<TF32>(dacc, a_hi, bl, idesc, 1);
+                        mma_ts<TF32>(dacc, a_lo, bh, idesc, 1);
                     }
                     mma_commit(&sm.empty_a[st]);
                 }
                 mma_commit(&sm.empty_b[buf]);
             }
             if (!ok) break;
-            mma_commit(&sm.acc_full);
+            mma_commit(&sm.acc_full[ab_]);
             ++it;
         }
         // drain every MMA this thread issued before TMEM is released

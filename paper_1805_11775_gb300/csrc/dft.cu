@@ -29,9 +29,11 @@ HOS_DEV int64_t line_base(const LineGeom& g, int64_t l) { return (l / g.inner) *
 HOS_DEV float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 
 // Shared-memory slot of element i of a line: one float2 of padding every 16
-// keeps bit-reversed and strided butterfly accesses off a single bank.
+// keeps bit-reversed and strided butterfly accesses off a single bank; the
+// line stride is odd (in float2) so that the same element of neighbouring
+// lines falls in different banks.
 HOS_DEV int sk(int i) { return i + (i >> 4); }
-HOS_HD int skewed_len(int N) { return N + (N >> 4); }
+HOS_HD int skewed_len(int N) { return N + (N >> 4) + 1; }
 
 template <bool REAL_IN>
 HOS_DEV float2 load_in(const void* in, int64_t idx) {
@@ -52,13 +54,25 @@ __global__ void fft_lines_kernel(const void* in, float2* out, const LineGeom g, 
     const bool contiguous = (g.elem_stride == 1);
     for (int l = threadIdx.x; l < nl; l += blockDim.x) lbase[l] = line_base(g, l0 + l);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        int l, e;
-        if (contiguous) { l = idx >> g.log2N; e = idx & (N - 1); }
-        else { e = idx / nl; l = idx - e * nl; }
-        const float2 v = load_in<REAL_IN>(in, lbase[l] + (int64_t)e * g.elem_stride);
-        const int r = (int)(__brev((unsigned)e) >> (32 - g.log2N));
-        sbuf[l * SL + sk(r)] = v;
+    // loads in batches of 8 per thread so that several are in flight
+    for (int base = 0; base < total; base += 8 * blockDim.x) {
+        float2 v[8];
+        int dst[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = base + u * blockDim.x + threadIdx.x;
+            dst[u] = -1;
+            if (idx < total) {
+                int l, e;
+                if (contiguous) { l = idx >> g.log2N; e = idx & (N - 1); }
+                else { e = idx / nl; l = idx - e * nl; }
+                v[u] = load_in<REAL_IN>(in, lbase[l] + (int64_t)e * g.elem_stride);
+                dst[u] = l * SL + sk((int)(__brev((unsigned)e) >> (32 - g.log2N)));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (dst[u] >= 0) sbuf[dst[u]] = v[u];
     }
     __syncthreads();
     const int lg = g.log2N;

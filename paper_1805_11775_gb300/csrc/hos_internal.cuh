@@ -34,12 +34,13 @@ namespace hos {
 // order, the main slot and the CTA slots of every window.
 // ---------------------------------------------------------------------------
 constexpr int TILE_M = 128;
-constexpr int KC = 1024;         // samples per chunk
+constexpr int KC = 1024;         // most samples per chunk (shared-memory sizing); plans use geo.kc <= KC
 constexpr int MAX_TILES_M = 16;  // L <= 1024
 constexpr int MAX_TILES_N = 16;
 
 struct C3Geom {
     int L;
+    int kc;         // samples per chunk (multiple of 64, <= KC)
     int tile_n;     // 16..256, power of two
     int tiles_m;    // ceil(2L / 128)
     int tiles_n;    // ceil(2L / tile_n)
@@ -86,7 +87,7 @@ struct Part {
 struct Walk {
     int64_t u, ue, U, total_win;
     int s, S, g;
-    int flush, ntiles;
+    int flush, ntiles, kc;
     const int64_t* unit;
     const int64_t* win;
     const int64_t* off;
@@ -98,6 +99,7 @@ struct Walk {
         off = sv.off;
         flush = geo.flush;
         ntiles = geo.ntiles;
+        kc = geo.kc;
         g = gidx;
         U = unit[S];
         total_win = win[S];
@@ -115,7 +117,7 @@ struct Walk {
         if (u >= ue) return false;
         while (s < S - 1 && unit[s + 1] <= u) ++s;
         const int64_t len = off[s + 1] - off[s];
-        const int64_t nch = ceil_div(len, KC);
+        const int64_t nch = ceil_div(len, kc);
         const int64_t r = u - unit[s];
         const int t = (int)(r / nch);
         const int64_t c = r % nch;

@@ -66,8 +66,8 @@ constexpr int C4_CHUNK_GROUP = 4;  // 1024-sample chunks per FP32 partial
 void count_launch();
 
 cudaError_t launch_plan_series(int mode, int64_t n, int64_t seg, const int64_t* d_user_off, int S, int L, int ntiles,
-                               int flush, int pad_tail, int64_t* off, int64_t* pad, int64_t* unit, int64_t* win,
-                               cudaStream_t st);
+                               int flush, int kc, int pad_tail, int64_t* off, int64_t* pad, int64_t* unit,
+                               int64_t* win, cudaStream_t st);
 cudaError_t launch_mean(const void* x, int dtype, const int64_t* off, int S, int nslices, double* part,
                         int remove_mean, double* mean, cudaStream_t st);
 cudaError_t launch_planes(const void* x, int dtype, const int64_t* off, const int64_t* pad, const double* mean, int L,

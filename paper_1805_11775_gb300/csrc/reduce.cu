@@ -44,7 +44,7 @@ __global__ void part_ranges_kernel(const C3Geom geo, const SeriesView sv, const 
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= (int64_t)sv.S * geo.ntiles) return;
     const int s = (int)(q / geo.ntiles), t = (int)(q % geo.ntiles);
-    const int64_t nch = ceil_div(sv.off[s + 1] - sv.off[s], KC);
+    const int64_t nch = ceil_div(sv.off[s + 1] - sv.off[s], geo.kc);
     const int64_t ub = sv.unit[s] + (int64_t)t * nch, ue = ub + nch;
     int lo = 0, hi = geo.G;  // first CTA starting after ub
     while (lo < hi) {
@@ -67,7 +67,7 @@ HOS_DEV double tile_part_sum(const C3Geom& geo, const SeriesView& sv, const floa
     const int64_t tsz = (int64_t)TILE_M * geo.tile_n;
     const int64_t total_win = sv.win[sv.S];
     const int64_t len = sv.off[s + 1] - sv.off[s];
-    const int64_t nch = ceil_div(len, KC), nwin = ceil_div(nch, F);
+    const int64_t nch = ceil_div(len, geo.kc), nwin = ceil_div(nch, F);
     const int64_t ub = sv.unit[s] + (int64_t)t * nch;
     const float* p = partials + (sv.win[s] + (int64_t)t * nwin) * tsz + el;
     double acc = 0.0;

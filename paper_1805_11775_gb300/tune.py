@@ -1,0 +1,112 @@
+"""Autotuner for the contraction's tile width and flush length.
+
+For a problem shape (op, L, size bucket, series-count bucket, precision) it
+times every candidate (tile_n, flush_chunks) through the C ABI with CUDA
+events on the current stream, keeps the fastest, and stores it in a JSON
+cache (``$HOS_TUNE_CACHE``, default ``~/.cache/hos_gb300/tune.json``) keyed by
+the device name.  The public calls consult the cache when the caller leaves
+``tile_n`` / ``flush_chunks`` at 0.  The 3xTF32 path keeps short flushes only:
+its FP32 accumulation error grows with the MMA steps one partial holds.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import threading
+
+_lock = threading.Lock()
+_cache = None
+
+
+def cache_path() -> str:
+    return os.environ.get("HOS_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "hos_gb300", "tune.json"))
+
+
+def _load():
+    global _cache
+    with _lock:
+        if _cache is None:
+            try:
+                with open(cache_path()) as f:
+                    _cache = json.load(f)
+            except (OSError, ValueError):  # missing or corrupt: start afresh
+                _cache = {}
+    return _cache
+
+
+def _save():
+    path = cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = f"{path}.{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            json.dump(_cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
+def _bucket(v: int) -> int:
+    return int(math.ceil(math.log2(max(int(v), 1))))
+
+
+def key(device_name: str, op: str, L: int, n_total: int, n_series: int, precision: str) -> str:
+    return f"{device_name}|{op}|L{L}|n2^{_bucket(n_total)}|S2^{_bucket(n_series)}|{precision}"
+
+
+def lookup(op: str, L: int, n_total: int, n_series: int, precision: str):
+    """(tile_n, flush_chunks) tuned for this shape on the current device, or None."""
+    import torch
+    if not torch.cuda.is_available():
+        return None
+    k = key(torch.cuda.get_device_name(), op, L, n_total, n_series, precision)
+    v = _load().get(k)
+    return (int(v["tile_n"]), int(v["flush_chunks"])) if v else None
+
+
+def candidates(L: int, precision: str):
+    two_l = 2 * L
+    tiles = sorted({t for t in (128, 256) if t <= max(32, 1 << (two_l - 1).bit_length())} or {0})
+    flushes = (1, 2) if precision in ("fp32", "3xtf32") else (4, 8, 16, 32)
+    return [(t, f) for t in tiles for f in flushes]
+
+
+def tune(run, op: str, L: int, n_total: int, n_series: int, precision: str, repeats: int = 5, store: bool = True):
+    """Time ``run(tile_n, flush_chunks)`` for every candidate; cache the best.
+
+    ``run`` enqueues one call on the current stream.  Returns
+    (best (tile_n, flush_chunks), {candidate: ms})."""
+    import torch
+    times = {}
+    for cand in candidates(L, precision):
+        run(*cand)  # first call: workspace growth, kernel attributes
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(repeats):
+            run(*cand)
+        e1.record()
+        torch.cuda.synchronize()
+        times[cand] = e0.elapsed_time(e1) / repeats
+    best = min(times, key=times.get)
+    if store:
+        k = key(torch.cuda.get_device_name(), op, L, n_total, n_series, precision)
+        with _lock:
+            _load()[k] = {"tile_n": best[0], "flush_chunks": best[1], "ms": times[best]}
+            _save()
+    return best, times
+
+
+def tune_bispectrum(x, L: int, precision: str = "bf16", repeats: int = 5):
+    import paper_1805_11775_gb300 as hos
+    return tune(lambda t, f: hos.bispectrum(x, L, precision=precision, tile_n=t, flush_chunks=f), "bispectrum", L,
+                x.numel(), 1, precision, repeats)
+
+
+def tune_bispectrum_batched(values, offsets, L: int, precision: str = "bf16", repeats: int = 3, max_len=None):
+    import paper_1805_11775_gb300 as hos
+    S = len(offsets) - 1
+    return tune(lambda t, f: hos.bispectrum_batched(values, offsets, L, precision=precision, tile_n=t, flush_chunks=f,
+                                                    max_len=max_len), "bispectrum_batched", L, values.numel(), S,
+                precision, repeats)

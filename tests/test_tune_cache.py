@@ -1,0 +1,30 @@
+"""Autotuner cache logic (no GPU): keys, candidate sets, corrupt-cache recovery."""
+import json
+
+import pytest
+
+from paper_1805_11775_gb300 import tune
+
+
+def test_candidates_respect_precision_and_lag_range():
+    assert all(f <= 2 for _, f in tune.candidates(256, "fp32"))
+    assert {t for t, _ in tune.candidates(256, "bf16")} == {128, 256}
+    assert {t for t, _ in tune.candidates(40, "bf16")} == {128}
+
+
+def test_key_buckets_sizes():
+    a = tune.key("GB300", "bispectrum", 128, 3000, 1, "bf16")
+    b = tune.key("GB300", "bispectrum", 128, 4000, 1, "bf16")
+    c = tune.key("GB300", "bispectrum", 128, 5000, 1, "bf16")
+    assert a == b != c
+
+
+def test_corrupt_cache_is_rebuilt(tmp_path, monkeypatch):
+    p = tmp_path / "tune.json"
+    p.write_text("{not json")
+    monkeypatch.setenv("HOS_TUNE_CACHE", str(p))
+    monkeypatch.setattr(tune, "_cache", None)
+    assert tune._load() == {}
+    tune._cache["k"] = {"tile_n": 256, "flush_chunks": 8, "ms": 1.0}
+    tune._save()
+    assert json.loads(p.read_text())["k"]["flush_chunks"] == 8
