@@ -505,7 +505,9 @@ struct PlanB {
     C3Geom g;
     int Nf, nslices;
     int64_t nctas;
-    size_t status, off, pad, unit, win, mean, mpart, y32, gc, gs, t1, t2p, gbuf, gmean, gmpart, tw, total;
+    bool tc;  // tensor-core adjoint (split-bf16, L <= 128)
+    size_t status, off, pad, unit, win, mean, mpart, y32, hi, lo, gc, gs, gsb, t1, t2p, gbuf, gmean, gmpart, tw,
+        total;
 };
 
 static hos_status make_planb(const hos_params* p, int64_t n, PlanB& P) {
@@ -513,6 +515,9 @@ static hos_status make_planb(const hos_params* p, int64_t n, PlanB& P) {
     if (s != HOS_OK) return s;
     const int L = p->L, twoL = 2 * L;
     P.g = make_geom(p, 1);
+    // the adjoint reads y(u + w1) windows up to 2L + 256 samples past a row tile
+    if (P.g.pad_tail < twoL + 320) P.g.pad_tail = twoL + 320;
+    P.tc = (p->precision == HOS_PREC_SPLIT_BF16) && adjoint_tc_supported(L);
     P.Nf = p->nfft ? p->nfft : twoL;
     P.nslices = (int)ceil_div(n, 8192);
     if (P.nslices > 256) P.nslices = 256;
@@ -528,10 +533,13 @@ static hos_status make_planb(const hos_params* p, int64_t n, PlanB& P) {
     P.mean = o; o = al256(o + 8);
     P.mpart = o; o = al256(o + 8 * (size_t)P.nslices);
     P.y32 = o; o = al256(o + 4 * (size_t)plane_len);
+    P.hi = o; o = al256(o + (P.tc ? 2 * (size_t)plane_len + 64 : 0));
+    P.lo = o; o = al256(o + (P.tc ? 2 * (size_t)plane_len + 64 : 0));
     P.gc = o; o = al256(o + 8 * (size_t)P.Nf * P.Nf);
     P.gs = o; o = al256(o + 4 * (size_t)twoL * twoL);
-    P.t1 = o; o = al256(o + 4 * (size_t)P.nctas * ADJ_ROWS_PER_CTA);
-    P.t2p = o; o = al256(o + 4 * (size_t)P.nctas * (ADJ_ROWS_PER_CTA + twoL));
+    P.gsb = o; o = al256(o + (P.tc ? adjoint_tc_gs_bytes(L) : 0));
+    P.t1 = o; o = al256(o + 4 * (P.tc ? adjoint_tc_t1_floats(L, n) : (size_t)P.nctas * ADJ_ROWS_PER_CTA));
+    P.t2p = o; o = al256(o + 4 * (P.tc ? adjoint_tc_t2_floats(L, n) : (size_t)P.nctas * (ADJ_ROWS_PER_CTA + twoL)));
     P.gbuf = o; o = al256(o + 4 * (size_t)n);
     P.gmean = o; o = al256(o + 8);
     P.gmpart = o; o = al256(o + 8 * (size_t)P.nslices);
@@ -689,7 +697,9 @@ hos_status hos_bispectrum_backward(const void* d_x, int32_t dtype, int64_t n, co
                              at<double>(ws, P.mean), st));
     int bx = (int)ceil_div((int64_t)L + n + KC + P.g.pad_tail + 64, 256 * 4);
     if (bx > 65535) bx = 65535;
-    HOS_CUDA_TRY(launch_planes(d_x, dtype, off, pad, at<double>(ws, P.mean), L, 0, y32, nullptr, nullptr, 1, bx, st));
+    void* hi = P.tc ? at<void>(ws, P.hi) : nullptr;
+    void* lo = P.tc ? at<void>(ws, P.lo) : nullptr;
+    HOS_CUDA_TRY(launch_planes(d_x, dtype, off, pad, at<double>(ws, P.mean), L, P.tc ? 1 : 0, y32, hi, lo, 1, bx, st));
     tr.mark("transform");
     float2* tw = at<float2>(ws, P.tw);
     float2* gc = at<float2>(ws, P.gc);
@@ -703,9 +713,18 @@ hos_status hos_bispectrum_backward(const void* d_x, int32_t dtype, int64_t n, co
     const float* yS = y32 + L;
     const double scale = 1.0 / (4.0 * 3.14159265358979323846 * 3.14159265358979323846 * (double)n);
     float* g = at<float>(ws, P.gbuf);
-    HOS_CUDA_TRY(launch_adjoint(yS, n, L, gc, Nf, p->window, scale, at<float>(ws, P.gs), at<float>(ws, P.t1),
-                                at<float>(ws, P.t2p), g, st));
-    g_last_contraction = "adjoint_simt_fp32";
+    if (P.tc) {
+        HOS_CUDA_TRY(launch_gs(gc, Nf, L, p->window, scale, at<float>(ws, P.gs), st));
+        HOS_CUDA_TRY(launch_adjoint_tc(y32, reinterpret_cast<const uint16_t*>(hi), reinterpret_cast<const uint16_t*>(lo),
+                                       n, L, at<float>(ws, P.gs), at<uint8_t>(ws, P.gsb), at<float>(ws, P.t1),
+                                       at<float>(ws, P.t2p), g, at<int>(ws, P.status), wait_limit_ns(), sm_count(),
+                                       st));
+        g_last_contraction = "adjoint_tcgen05_split_bf16";
+    } else {
+        HOS_CUDA_TRY(launch_adjoint(yS, n, L, gc, Nf, p->window, scale, at<float>(ws, P.gs), at<float>(ws, P.t1),
+                                    at<float>(ws, P.t2p), g, st));
+        g_last_contraction = "adjoint_simt_fp32";
+    }
     tr.mark("reduce");
     HOS_CUDA_TRY(launch_mean(g, HOS_F32, off, 1, P.nslices, at<double>(ws, P.gmpart), p->remove_mean,
                              at<double>(ws, P.gmean), st));

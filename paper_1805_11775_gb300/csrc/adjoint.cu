@@ -166,6 +166,13 @@ cudaError_t launch_adjoint(const float* yS, int64_t n, int L, const float2* Gc, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_gs(const float2* Gc, int N, int L, int window, double scale, float* Gs, cudaStream_t st) {
+    const int twoL = 2 * L;
+    gs_kernel<<<(unsigned)ceil_div((int64_t)twoL * twoL, 256), 256, 0, st>>>(Gc, N, L, window, scale, Gs);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_adjoint_finish(const float* g, int64_t n, const double* gmean, int remove_mean, int dtype, void* dx,
                                   cudaStream_t st) {
     const unsigned b = (unsigned)ceil_div(n, 256);

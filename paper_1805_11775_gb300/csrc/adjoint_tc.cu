@@ -1,0 +1,368 @@
+// adjoint_tc.cu -- the adjoint contraction U[u, w1] = sum_w2 y(u + w2) Gs(w1, w2)
+// on the tensor cores (tcgen05, split-bf16, FP32 accumulate), with both
+// gradient terms taken in the epilogue:
+//   T1(u) = sum_w1 U[u, w1] y(u + w1)         (row sums, per thread)
+//   T2(j) = sum_w1 U[j - w1, w1] y(j - w1)    (anti-diagonal sums)
+//
+// MMA operands (M = 128 rows u, N = 128 lags w1 of one block, K = 16 lags w2):
+//   A = Hankel X[u, w2] = y(u + w2): the interleaved 1-D window of the forward
+//       kernel (8 copies shifted by one sample, 16-byte blocks), read straight
+//       by the descriptor (LBO = SBO = 128 bytes) -- never expanded.
+//   B = Gs(w1, w2) of one 128-lag block of w1, K-major canonical layout,
+//       loaded once per block and kept in shared memory (all K = 2L lags).
+//   D = two FP32 TMEM accumulators (128 columns each), so the epilogue drains
+//       one item while the MMAs fill the next.
+// T2 is swept per warp with shuffles: stepping through the columns c, each
+// lane adds U[u, c] y(u) to a running sum that moves one lane down per step,
+// so lane 0 holds a finished anti-diagonal after every step; the four warps'
+// diagonals are then added in warp order.  Every sum runs in a fixed order.
+//
+// Work items (w1 block b, 128-row tile of u), b-major, split into equal
+// contiguous ranges over the persistent CTAs.  Every wait is bounded.
+#include "launch.cuh"
+
+namespace hos {
+
+namespace {
+
+constexpr int AU = 128;               // rows u per item
+constexpr int AW = 128;               // lags w1 per block
+constexpr int AMAXK = 256;            // K = 2L <= 256 (L <= 128)
+constexpr int AWIN = AU + AMAXK + 16;  // window samples (u0 - L .. u0 + 128 + L + 16)
+constexpr int B_BYTES = (AMAXK / 8) * 2048;  // one Gs plane of a block: (K/8) x 16 groups x 128 B
+
+struct __align__(16) AdjSmem {
+    uint8_t gs_hi[B_BYTES];
+    uint8_t gs_lo[B_BYTES];
+    uint8_t win_hi[2][AWIN * 16];
+    uint8_t win_lo[2][AWIN * 16];
+    uint16_t lin_hi[AWIN + 16];
+    uint16_t lin_lo[AWIN + 16];
+    float yw[2][AU + AW];   // y(u0 + w1_0 + t): the y(u + w1) of T1
+    float yu[2][AU + 4];    // y(u0 + t - sh) from a 16-byte aligned start, sh = L & 3
+    float t2w[4][AU / 4 + AW];  // each warp's anti-diagonal sums (private to the warp)
+    uint64_t full[2], empty[2], acc_full[2], acc_empty[2], b_full, b_empty, tma_bar, btma_bar, drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+}  // namespace
+
+struct AdjTcParams {
+    const float* y32;       // padded sample planes of the series: y(i) at index L + i
+    const uint16_t* hi;     // bf16 planes
+    const uint16_t* lo;
+    const uint8_t* gsb;     // Gs hi/lo planes per block, canonical layout, 2 * B_BYTES per block
+    float* t1p;             // [nb][n_round]
+    float* t2p;             // [items][4 warps][32 + AW - 1]
+    int64_t n;
+    int L;
+    int kpad;               // 2L rounded up to 16
+    int nb;                 // w1 blocks
+    int64_t nut;            // u tiles
+    int* status;
+    uint64_t limit_ns;
+};
+
+HOS_DEV void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+HOS_DEV void expect_bytes(uint64_t* bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    AdjSmem& sm = *reinterpret_cast<AdjSmem*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int L = P.L, K = P.kpad;
+    const uint32_t idesc = make_idesc(false, AU, AW);
+    const int64_t items = (int64_t)P.nb * P.nut;
+    const int64_t it0 = range_begin(blockIdx.x, items, gridDim.x), it1 = range_begin(blockIdx.x + 1, items, gridDim.x);
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&sm.full[i], 32);
+            mbar_init(&sm.empty[i], 1 + 4);  // MMA commit + four epilogue warps
+            mbar_init(&sm.acc_full[i], 1);
+            mbar_init(&sm.acc_empty[i], 128);
+        }
+        mbar_init(&sm.b_full, 1);
+        mbar_init(&sm.b_empty, 1);
+        mbar_init(&sm.tma_bar, 1);
+        mbar_init(&sm.btma_bar, 1);
+        mbar_init(&sm.drain, 1);
+        sm.abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 5) {
+        tmem_alloc(&sm.tmem_base, 256);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem_base;
+    volatile int* abort = &sm.abort;
+    const uint64_t lim = P.limit_ns;
+
+    if (warp == 4) {
+        // ---------------------------------------------------------- producer
+        uint32_t tph = 0, bph = 0;
+        int cur_b = -1;
+        uint32_t nbl = 0;  // blocks loaded
+        bool ok = true;
+        for (int64_t it = it0, k = 0; it < it1 && ok; ++it, ++k) {
+            const int b = (int)(it / P.nut);
+            const int64_t u0 = (it % P.nut) * AU;
+            if (b != cur_b) {  // the Gs block: wait until every MMA on the previous one is done
+                ok = warp_wait(&sm.b_empty, (nbl & 1) ^ 1, abort, P.status, lim, 2000);
+                if (!ok) break;
+                if (lane == 0) {
+                    expect_bytes(&sm.btma_bar, 2 * (uint32_t)((K / 8) * 2048));
+                    const uint8_t* src = P.gsb + (size_t)b * 2 * B_BYTES;
+                    bulk_copy(sm.gs_hi, src, (K / 8) * 2048, &sm.btma_bar);
+                    bulk_copy(sm.gs_lo, src + B_BYTES, (K / 8) * 2048, &sm.btma_bar);
+                }
+                ok = warp_wait(&sm.btma_bar, bph, abort, P.status, lim, 1000);
+                bph ^= 1;
+                if (!ok) break;
+                if (lane == 0) mbar_arrive(&sm.b_full);
+                cur_b = b;
+                ++nbl;
+            }
+            const int buf = (int)(k & 1);
+            ok = warp_wait(&sm.empty[buf], ((k >> 1) & 1) ^ 1, abort, P.status, lim, 2000);
+            if (!ok) break;
+            // window of y(u0 - L + t): plane index u0 (multiple of 128, 16-byte aligned for bf16)
+            const uint32_t wsamp = (uint32_t)(AU + K + 16);
+            const int64_t w1b = (int64_t)b * AW - L;  // first lag of the block
+            if (lane == 0) {
+                expect_bytes(&sm.tma_bar, 2 * wsamp * 2 + (AU + AW) * 4 + (AU + 4) * 4);
+                bulk_copy(sm.lin_hi, P.hi + u0, wsamp * 2, &sm.tma_bar);
+                bulk_copy(sm.lin_lo, P.lo + u0, wsamp * 2, &sm.tma_bar);
+                bulk_copy(sm.yw[buf], P.y32 + (L + u0 + w1b), (AU + AW) * 4, &sm.tma_bar);  // u0 + 128 b: aligned
+                bulk_copy(sm.yu[buf], P.y32 + ((L + u0) & ~(int64_t)3), (AU + 4) * 4, &sm.tma_bar);
+            }
+            ok = warp_wait(&sm.tma_bar, tph, abort, P.status, lim, 1000);
+            tph ^= 1;
+            if (!ok) break;
+            // interleave: block (q, r) <- samples [8q + r, 8q + r + 8)
+            const int nblocks = (int)(((AU + K) / 8 + 2) * 8);
+            const uint32_t* sh = reinterpret_cast<const uint32_t*>(sm.lin_hi);
+            const uint32_t* sl = reinterpret_cast<const uint32_t*>(sm.lin_lo);
+            for (int blk = lane; blk < nblocks; blk += 32) {
+                const int e0 = blk;  // 8q + r
+                const int w0 = e0 >> 1;
+                const uint32_t sft = (e0 & 1) * 16;
+                uint32_t h[5], l[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    h[q] = sh[w0 + q];
+                    l[q] = sl[w0 + q];
+                }
+                *reinterpret_cast<uint4*>(sm.win_hi[buf] + (size_t)blk * 16) =
+                    make_uint4(__funnelshift_r(h[0], h[1], sft), __funnelshift_r(h[1], h[2], sft),
+                               __funnelshift_r(h[2], h[3], sft), __funnelshift_r(h[3], h[4], sft));
+                *reinterpret_cast<uint4*>(sm.win_lo[buf] + (size_t)blk * 16) =
+                    make_uint4(__funnelshift_r(l[0], l[1], sft), __funnelshift_r(l[1], l[2], sft),
+                               __funnelshift_r(l[2], l[3], sft), __funnelshift_r(l[3], l[4], sft));
+            }
+            fence_proxy_async_smem();
+            mbar_arrive(&sm.full[buf]);
+        }
+    } else if (warp == 5 && lane == 0) {
+        // ---------------------------------------------------------- MMA issuer
+        int cur_b = -1;
+        uint32_t nbl = 0;
+        bool ok = true;
+        const uint32_t wh0 = smem_u32(sm.win_hi[0]), wl0 = smem_u32(sm.win_lo[0]);
+        const uint32_t gh = smem_u32(sm.gs_hi), gl = smem_u32(sm.gs_lo);
+        for (int64_t it = it0, k = 0; it < it1 && ok; ++it, ++k) {
+            const int b = (int)(it / P.nut);
+            if (b != cur_b) {
+                if (cur_b >= 0) mma_commit(&sm.b_empty);  // MMAs on the previous block are all issued
+                ok = mbar_wait(&sm.b_full, nbl & 1, abort, P.status, lim);
+                if (!ok) break;
+                cur_b = b;
+                ++nbl;
+            }
+            const int buf = (int)(k & 1);
+            const uint32_t ab = (uint32_t)(k & 1);
+            ok = mbar_wait(&sm.acc_empty[ab], ((k >> 1) & 1) ^ 1, abort, P.status, lim);
+            if (!ok) break;
+            ok = mbar_wait(&sm.full[buf], (k >> 1) & 1, abort, P.status, lim);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t d = tmem + ab * 128u;
+            const uint32_t wh = wh0 + (uint32_t)buf * (AWIN * 16), wl = wl0 + (uint32_t)buf * (AWIN * 16);
+            uint32_t acc = 0;
+            for (int ks = 0; ks < K / 16; ++ks) {
+                // A rows u, K = lags w2 (-L + 16 ks ..): window offset 16 ks samples = 2 groups of 128 B
+                const uint64_t ah = make_sdesc(wh + (uint32_t)ks * 256u, 128, 128);
+                const uint64_t al = make_sdesc(wl + (uint32_t)ks * 256u, 128, 128);
+                // B rows w1 (16 groups of 8 at 128 B), K groups of 8 lags at 2048 B
+                const uint64_t bh = make_sdesc(gh + (uint32_t)ks * 4096u, 2048, 128);
+                const uint64_t bl = make_sdesc(gl + (uint32_t)ks * 4096u, 2048, 128);
+                mma_ss<false>(d, ah, bh, idesc, acc);
+                acc = 1;
+                mma_ss<false>(d, ah, bl, idesc, 1);
+                mma_ss<false>(d, al, bh, idesc, 1);
+            }
+            mma_commit(&sm.empty[buf]);
+            mma_commit(&sm.acc_full[ab]);
+        }
+        if (ok && cur_b >= 0) mma_commit(&sm.b_empty);
+        mma_commit(&sm.drain);
+        mbar_wait(&sm.drain, 0, abort, P.status, lim);
+    } else if (warp < 4) {
+        // ---------------------------------------------------------- epilogue
+        const int m = warp * 32 + lane;  // row u - u0
+        const int ysh = L & 3;           // yu was staged from an aligned start
+        bool ok = true;
+        for (int64_t it = it0, k = 0; it < it1 && ok; ++it, ++k) {
+            const int b = (int)(it / P.nut);
+            const int64_t ut = it % P.nut, u0 = ut * AU;
+            const int buf = (int)(k & 1);
+            const uint32_t ab = (uint32_t)(k & 1);
+            ok = warp_wait(&sm.full[buf], (k >> 1) & 1, abort, P.status, lim, 2000);  // this item's windows
+            if (!ok) break;
+            ok = warp_wait(&sm.acc_full[ab], (k >> 1) & 1, abort, P.status, lim, 5000);
+            if (!ok) break;
+            tc_fence_after();
+            const float yu = sm.yu[buf][ysh + m];
+            const float* yw = sm.yw[buf] + m;  // y(u + w1_0 + c)
+            float t1 = 0.f, diag = 0.f;
+            float* t2w = sm.t2w[warp];
+            for (int c0 = 0; c0 < AW; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + ab * 128u + (uint32_t)c0, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float uval = __uint_as_float(v[j]);
+                    t1 = fmaf(uval, yw[c0 + j], t1);
+                    // running anti-diagonal: take the next lane's sum, add this row's term;
+                    // afterwards lane 0 holds the finished diagonal c0 + j of this warp
+                    float nx = __shfl_down_sync(0xffffffffu, diag, 1);
+                    if (lane == 31) nx = 0.f;
+                    diag = fmaf(uval, yu, nx);
+                    if (lane == 0) t2w[c0 + j] = diag;
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&sm.acc_empty[ab]);  // this item's accumulator may be reused
+            if (lane > 0) t2w[AW - 1 + lane] = diag;  // diagonals 128 .. 158 are finished too
+            __syncwarp();
+            if (u0 + m < P.n) P.t1p[(int64_t)b * (P.nut * AU) + u0 + m] = t1;
+            float* dst = P.t2p + (it * 4 + warp) * (32 + AW - 1);
+            for (int e = lane; e < 32 + AW - 1; e += 32) dst[e] = t2w[e];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.empty[buf]);  // yu / yw of this buffer are no longer read
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 5) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, 256);
+    }
+}
+
+// Gs hi/lo per w1 block in the canonical K-major layout the kernel reads:
+// byte (n % 8) * 16 + (n / 8) * 128 + (k / 8) * 2048 + (k % 8) * 2 of a plane,
+// n = w1 - block start (128 per block), k = w2 + L (K = kpad, zero beyond 2L).
+__global__ void gs_layout_kernel(const float* __restrict__ Gs, int L, int kpad, int nb, uint8_t* __restrict__ out) {
+    const int twoL = 2 * L;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)nb * AW * kpad) return;
+    const int b = (int)(e / ((int64_t)AW * kpad));
+    const int r = (int)(e % ((int64_t)AW * kpad));
+    const int n = r / kpad, k = r % kpad;
+    const int w1i = b * AW + n;  // index w1 + L
+    float v = 0.f;
+    if (w1i < twoL && k < twoL) v = Gs[(int64_t)w1i * twoL + k];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    const size_t off = (size_t)(n % 8) * 16 + (size_t)(n / 8) * 128 + (size_t)(k / 8) * 2048 + (size_t)(k % 8) * 2;
+    uint8_t* base = out + (size_t)b * 2 * B_BYTES;
+    *reinterpret_cast<__nv_bfloat16*>(base + off) = h;
+    *reinterpret_cast<__nv_bfloat16*>(base + B_BYTES + off) = l;
+}
+
+// g(j) = sum_b T1p[b][j] + 2 sum over the items (b, ut) covering j and their
+// four warps (warp w's diagonal d covers item position 32 w + d), in the
+// order (b, ut, w).
+__global__ void adjoint_tc_gather_kernel(const float* __restrict__ t1p, const float* __restrict__ t2p, int64_t n,
+                                         int L, int nb, int64_t nut, float* __restrict__ g) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int E = AU + AW - 1, D = 32 + AW - 1;
+    double t1 = 0.0, t2 = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        t1 += (double)t1p[(int64_t)b * (nut * AU) + j];
+        const int64_t w1b = (int64_t)b * AW - L;
+        int64_t lo = j - w1b - (E - 1);
+        lo = lo <= 0 ? 0 : ceil_div(lo, AU);
+        int64_t hi = (j - w1b) >= 0 ? (j - w1b) / AU : -1;
+        if (hi > nut - 1) hi = nut - 1;
+        for (int64_t ut = lo; ut <= hi; ++ut) {
+            const int64_t e = j - ut * AU - w1b;  // position in the item
+            if (e < 0 || e >= E) continue;
+            const float* it = t2p + (((int64_t)b * nut + ut) * 4) * D;
+            for (int w = 0; w < 4; ++w) {
+                const int64_t d = e - 32 * w;
+                if (d >= 0 && d < D) t2 += (double)it[w * D + d];
+            }
+        }
+    }
+    g[j] = (float)(t1 + 2.0 * t2);
+}
+
+bool adjoint_tc_supported(int L) { return L >= 1 && L <= AMAXK / 2; }
+size_t adjoint_tc_gs_bytes(int L) { return (size_t)((2 * L + AW - 1) / AW) * 2 * B_BYTES; }
+size_t adjoint_tc_t2_floats(int L, int64_t n) {
+    return (size_t)((2 * L + AW - 1) / AW) * (size_t)ceil_div(n, AU) * 4 * (32 + AW - 1);
+}
+size_t adjoint_tc_t1_floats(int L, int64_t n) { return (size_t)((2 * L + AW - 1) / AW) * (size_t)ceil_div(n, AU) * AU; }
+
+cudaError_t launch_adjoint_tc(const float* y32, const uint16_t* hi, const uint16_t* lo, int64_t n, int L,
+                              const float* Gs, uint8_t* gsb, float* t1p, float* t2p, float* g, int* status,
+                              uint64_t limit_ns, int G, cudaStream_t st) {
+    const int kpad = ((2 * L + 15) / 16) * 16;
+    const int nb = (2 * L + AW - 1) / AW;
+    const int64_t nut = ceil_div(n, AU);
+    const int64_t tot = (int64_t)nb * AW * kpad;
+    gs_layout_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(Gs, L, kpad, nb, gsb);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    AdjTcParams p{y32, hi, lo, gsb, t1p, t2p, n, L, kpad, nb, nut, status, limit_ns};
+    const size_t smem = sizeof(AdjSmem);
+    static bool attr = false;
+    if (!attr) {
+        e = cudaFuncSetAttribute(adjoint_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int64_t items = (int64_t)nb * nut;
+    const int grid = (int)(items < G ? items : G);
+    adjoint_tc_kernel<<<grid, 192, smem, st>>>(p);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    adjoint_tc_gather_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(t1p, t2p, n, L, nb, nut, g);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace hos

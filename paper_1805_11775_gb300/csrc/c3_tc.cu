@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
     constexpr uint32_t LBO = GROUP_BYTES;          // next core matrix along K: +R samples
     constexpr uint32_t SBO = 16u * 8u;             // next 8 rows along N: +8 samples = 128 bytes
     const uint32_t idesc = make_idesc(TF32, TILE_M, N);
-    const int kc = geo.kc;  // samples per chunk
+    const int csz = geo.kc;  // samples per chunk (the role loops below count chunks in kc)
     // accumulators: two TMEM buffers (columns [0,128) and [128,256)) when the
     // tile is at most 128 wide, so the epilogue drains one while the MMAs fill
     // the other; one buffer of N columns otherwise
@@ -140,15 +140,15 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                 const int buf = kc & 1;
                 ok = warp_wait(&sm.empty_b[buf], ((kc >> 1) & 1) ^ 1, abort, P.status, lim, 2000);
                 if (!ok) break;
-                const int64_t i0 = c * kc;
+                const int64_t i0 = c * csz;
                 const int64_t wb = base + i0 + (int64_t)b * N;            // plane index of window start
                 // A window: y(i0 + w1_0 + t) for ORDER 3; y(i0 - L + t) for ORDER 4
                 const int64_t ab = (ORDER == 3) ? base + i0 + (int64_t)a * TILE_M : base + i0;
                 const int64_t ib = base + L + i0;                          // y(i0)
                 const int64_t ib_al = ib & ~(int64_t)3;
-                const uint32_t wbytes = (uint32_t)(kc + N + 16) * ELT;
+                const uint32_t wbytes = (uint32_t)(csz + N + 16) * ELT;
                 if (lane == 0) {
-                    const uint32_t yab = (uint32_t)(kc + TILE_M) * 4, yib = (uint32_t)(kc + 4) * 4;
+                    const uint32_t yab = (uint32_t)(csz + TILE_M) * 4, yib = (uint32_t)(csz + 4) * 4;
                     mbar_expect_tx(&sm.tma_bar, 2 * wbytes + yab + yib);
                     bulk_g2s(sm.lin_hi, (const uint8_t*)P.hi + wb * ELT, wbytes, &sm.tma_bar);
                     bulk_g2s(sm.lin_lo, (const uint8_t*)P.lo + wb * ELT, wbytes, &sm.tma_bar);
@@ -160,10 +160,10 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                 if (!ok) break;
                 {   // realign y(i0 + t) so that builders can use 16-byte broadcast loads
                     const int ish = (int)(ib - ib_al);
-                    for (int t = lane; t < kc; t += 32) sm.yi[buf][t] = sm.yi_raw[ish + t];
+                    for (int t = lane; t < csz; t += 32) sm.yi[buf][t] = sm.yi_raw[ish + t];
                 }
                 // interleave: block (q, r) <- samples [R q + r, R q + r + R)
-                const int ngroups = (kc + N) / R + 2;
+                const int ngroups = (csz + N) / R + 2;
                 const int nblocks = ngroups * R;
                 for (int blk = lane; blk < nblocks; blk += 32) {
                     const int q = blk / R, r = blk % R;
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                 if (!ok) break;
                 const float* ya = sm.ya[buf] + (ORDER == 3 ? m : 0);
                 const float* yi = sm.yi[buf];
-                for (int kb = 0; kb < kc / KB; ++kb, ++ks) {
+                for (int kb = 0; kb < csz / KB; ++kb, ++ks) {
                     const int st = ks % NSTAGE;
                     ok = warp_wait(&sm.empty_a[st], ((ks / NSTAGE) & 1) ^ 1, abort, P.status, lim, 1000);
                     if (!ok) break;
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t wh = wh0 + (uint32_t)buf * WIN_BYTES, wl = wl0 + (uint32_t)buf * WIN_BYTES;
-                for (int kb = 0; kb < kc / KB; ++kb, ++ks) {
+                for (int kb = 0; kb < csz / KB; ++kb, ++ks) {
                     const int st = ks % NSTAGE;
                     ok = mbar_wait(&sm.full_a[st], (ks / NSTAGE) & 1, abort, P.status, lim);
                     if (!ok) break;

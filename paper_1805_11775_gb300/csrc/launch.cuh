@@ -87,6 +87,14 @@ cudaError_t launch_adjoint(const float* yS, int64_t n, int L, const float2* Gc, 
 cudaError_t launch_adjoint_finish(const float* g, int64_t n, const double* gmean, int remove_mean, int dtype, void* dx,
                                   cudaStream_t st);
 constexpr int ADJ_ROWS_PER_CTA = 64;
+bool adjoint_tc_supported(int L);
+size_t adjoint_tc_gs_bytes(int L);
+size_t adjoint_tc_t2_floats(int L, int64_t n);
+size_t adjoint_tc_t1_floats(int L, int64_t n);
+cudaError_t launch_adjoint_tc(const float* y32, const uint16_t* hi, const uint16_t* lo, int64_t n, int L,
+                              const float* Gs, uint8_t* gsb, float* t1p, float* t2p, float* g, int* status,
+                              uint64_t limit_ns, int G, cudaStream_t st);
+cudaError_t launch_gs(const float2* Gc, int N, int L, int window, double scale, float* Gs, cudaStream_t st);
 cudaError_t launch_m4_tile_reduce(const C3Geom& geo, const SeriesView& sv, const float* partials, int64_t* bnd,
                                   int2* xr, double* m4buf, cudaStream_t st);
 cudaError_t launch_c2(const float* y32, const int64_t* off, const int64_t* pad, int S, int L, double* c2,
