@@ -196,6 +196,11 @@ __global__ void c4_assemble_kernel(const double* __restrict__ m4buf, const doubl
                                    const int64_t* __restrict__ off, int S, int L, int ntiles, int tile_n,
                                    C4ReduceArgs r) {
     const int twoL = 2 * L, T = 2 * L - 1;
+    // per-lag window factor d(w) (RECT: 0 at w = -L), FP32 like the grid
+    __shared__ float wsh[2 * 64];
+    for (int i = threadIdx.x; i < twoL; i += blockDim.x)
+        wsh[i] = (r.window == HOS_WIN_RECT) ? (i == 0 ? 0.0f : 1.0f) : (float)parzen(i - L, L);
+    __syncthreads();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)twoL * twoL * twoL) return;
     const int w3 = (int)(e % twoL) - L;
@@ -219,12 +224,10 @@ __global__ void c4_assemble_kernel(const double* __restrict__ m4buf, const doubl
         r.c4out[((int64_t)(w1 + L) * twoL + (w2 + L)) * twoL + (w3 + L)] = c4;
         return;
     }
-    const double wv = (r.window == HOS_WIN_RECT && (w1 == -L || w2 == -L || w3 == -L))
-                          ? 0.0
-                          : lag_window3(w1, w2, w3, L, r.window);
-    const int N = r.nfft;
-    const int k1 = (w1 % N + N) % N, k2 = (w2 % N + N) % N, k3 = (w3 % N + N) % N;
-    r.grid[((int64_t)k1 * N + k2) * N + k3] = (float)(r.scale * wv * c4);
+    const float wv = wsh[w1 + L] * wsh[w2 + L] * wsh[w3 + L];
+    const int N = r.nfft;  // >= 2L, so w + N >= 0
+    const int k1 = w1 < 0 ? w1 + N : w1, k2 = w2 < 0 ? w2 + N : w2, k3 = w3 < 0 ? w3 + N : w3;
+    r.grid[((int64_t)k1 * N + k2) * N + k3] = (float)c4 * ((float)r.scale * wv);
 }
 
 cudaError_t launch_c2(const float* y32, const int64_t* off, const int64_t* pad, int S, int L, double* c2,

@@ -100,6 +100,146 @@ __global__ void fft_lines_kernel(const void* in, float2* out, const LineGeom g, 
     }
 }
 
+// Radix-8 passes in registers.  A pass covers r <= 3 consecutive radix-2
+// stages s0 .. s0+r-1 (span h = 2^s0): the index set {i0 + m h : m < 2^r},
+// i0 = blk 2^(s0+r) + j (j < h), is closed under those stages, so one thread
+// holds it in registers and does all r stages there (r 2^(r-1) butterflies).
+// Each thread holds 8 values: 2^(3-r) such groups, g = q T + t (T = N/8
+// threads per line).  The first pass reads the bit-reversed input straight
+// from global memory, the last writes natural-order output straight back;
+// passes in between exchange through shared memory.  Thread-to-line
+// mapping: lanes run along the line when the line is contiguous, across
+// lines when lines are strided (so that a warp's accesses are coalesced
+// either way).
+HOS_DEV int bitrev_n(int i, int lg) { return (int)(__brev((unsigned)i) >> (32 - lg)); }
+
+template <int R>
+HOS_DEV int group_index(int q, int m, int s0, int t, int T) {
+    const int gidx = q * T + t, h = 1 << s0;
+    return ((gidx >> s0) << (s0 + R)) + (gidx & (h - 1)) + m * h;
+}
+
+template <int R>
+HOS_DEV void radix_pass(float2 (&v)[8], int s0, int lg, int t, int T, const float2* __restrict__ tws) {
+    const int h = 1 << s0;
+#pragma unroll
+    for (int q = 0; q < (8 >> R); ++q) {
+        const int j = (q * T + t) & (h - 1);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+#pragma unroll
+            for (int m = 0; m < (1 << R); ++m) {
+                if (m & (1 << k)) continue;
+                const int jj = j + (m & ((1 << k) - 1)) * h;  // index within the span 2^(s0+k) h
+                const float2 w = tws[jj << (lg - 1 - (s0 + k))];
+                float2& a = v[q * (1 << R) + m];
+                float2& b = v[q * (1 << R) + m + (1 << k)];
+                const float2 bw = cmul(b, w);
+                b = make_float2(a.x - bw.x, a.y - bw.y);
+                a = make_float2(a.x + bw.x, a.y + bw.y);
+            }
+        }
+    }
+}
+
+template <int R>
+HOS_DEV void pass_store(const float2 (&v)[8], float2* row, int s0, int t, int T) {
+#pragma unroll
+    for (int q = 0; q < (8 >> R); ++q)
+#pragma unroll
+        for (int m = 0; m < (1 << R); ++m) row[sk(group_index<R>(q, m, s0, t, T))] = v[q * (1 << R) + m];
+}
+
+template <int R>
+HOS_DEV void pass_load(float2 (&v)[8], const float2* row, int s0, int t, int T) {
+#pragma unroll
+    for (int q = 0; q < (8 >> R); ++q)
+#pragma unroll
+        for (int m = 0; m < (1 << R); ++m) v[q * (1 << R) + m] = row[sk(group_index<R>(q, m, s0, t, T))];
+}
+
+template <bool REAL_IN, bool STRIDED>
+__global__ void __launch_bounds__(512) fft_r8_kernel(const void* in, float2* out, const LineGeom g,
+                                                     const float2* __restrict__ tw, int sign, float scale) {
+    extern __shared__ float2 sbuf[];
+    const int N = g.N, lg = g.log2N, lpb = g.lpb, SL = skewed_len(N), T = N >> 3;
+    float2* tws = sbuf + (size_t)lpb * SL;                          // N/2 twiddles, conjugated when sign > 0
+    int64_t* lbase = reinterpret_cast<int64_t*>(tws + (N >> 1));  // line starts
+    const int64_t l0 = (int64_t)blockIdx.x * lpb;
+    const int nl = (int)((g.nlines - l0) < lpb ? (g.nlines - l0) : lpb);
+    for (int k = threadIdx.x; k < (N >> 1); k += blockDim.x) {
+        float2 w = tw[k];
+        if (sign > 0) w.y = -w.y;
+        tws[k] = w;
+    }
+    for (int l = threadIdx.x; l < nl; l += blockDim.x) lbase[l] = line_base(g, l0 + l);
+    __syncthreads();
+    const int l = STRIDED ? (int)(threadIdx.x % lpb) : (int)(threadIdx.x / T);
+    const int t = STRIDED ? (int)(threadIdx.x / lpb) : (int)(threadIdx.x % T);
+    const bool live = l < nl;
+    const int64_t base = live ? lbase[l] : 0;
+    const int64_t es = g.elem_stride;
+    float2* row = sbuf + (size_t)l * SL;
+    float2 v[8];
+    // first pass (s0 = 0, radix 8): group t holds inputs bitrev(8t + m)
+    if (live) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = load_in<REAL_IN>(in, base + (int64_t)bitrev_n(8 * t + m, lg) * es);
+    }
+    radix_pass<3>(v, 0, lg, t, T, tws);
+    int s0 = 3;
+    while (s0 < lg) {
+        const int r = (lg - s0) < 3 ? (lg - s0) : 3;
+        __syncthreads();  // previous pass's reads of the rows are done (none before the first store)
+        if (live) pass_store<3>(v, row, s0 - 3, t, T);  // layout of the previous (radix-8) pass
+        __syncthreads();
+        // the stored layout is the previous pass's; reload in this pass's groups
+        if (r == 3) { if (live) pass_load<3>(v, row, s0, t, T); radix_pass<3>(v, s0, lg, t, T, tws); }
+        else if (r == 2) { if (live) pass_load<2>(v, row, s0, t, T); radix_pass<2>(v, s0, lg, t, T, tws); }
+        else { if (live) pass_load<1>(v, row, s0, t, T); radix_pass<1>(v, s0, lg, t, T, tws); }
+        if (s0 + r >= lg) {  // last pass: natural-order output straight to global memory
+            if (live) {
+                if (r == 3) {
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        const float2 o = v[m];
+                        out[base + (int64_t)group_index<3>(0, m, s0, t, T) * es] = make_float2(o.x * scale, o.y * scale);
+                    }
+                } else if (r == 2) {
+#pragma unroll
+                    for (int q = 0; q < 2; ++q)
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            const float2 o = v[q * 4 + m];
+                            out[base + (int64_t)group_index<2>(q, m, s0, t, T) * es] =
+                                make_float2(o.x * scale, o.y * scale);
+                        }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int m = 0; m < 2; ++m) {
+                            const float2 o = v[q * 2 + m];
+                            out[base + (int64_t)group_index<1>(q, m, s0, t, T) * es] =
+                                make_float2(o.x * scale, o.y * scale);
+                        }
+                }
+            }
+            return;
+        }
+        // a middle pass is always radix 8 (only the last can be shorter)
+        s0 += 3;
+    }
+    // lg == 3: the first pass was the whole transform
+    if (live) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const float2 o = v[m];
+            out[base + (int64_t)m * es] = make_float2(o.x * scale, o.y * scale);
+        }
+    }
+}
+
 template <bool REAL_IN>
 __global__ void dft_lines_kernel(const void* in, float2* out, const LineGeom g, const float2* __restrict__ tw,
                                  int sign, float scale) {
@@ -146,7 +286,33 @@ cudaError_t launch_lines(bool real_in, const void* in, float2* out, LineGeom g, 
                          float scale, cudaStream_t st) {
     if (g.nlines <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)ceil_div(g.nlines, g.lpb);
-    if (g.log2N >= 0) {
+    if (g.log2N >= 3) {
+        // radix-8 register passes: N/8 threads per line, <= 512 threads per CTA
+        const int T = g.N >> 3;
+        const bool strided = g.elem_stride != 1;
+        int lpb = strided ? 512 / T : 256 / T;
+        if (lpb > 32) lpb = 32;
+        if (lpb < 1) lpb = 1;
+        if (lpb > g.nlines) lpb = (int)g.nlines;
+        g.lpb = lpb;
+        const unsigned nb = (unsigned)ceil_div(g.nlines, lpb);
+        const size_t smem = (size_t)lpb * skewed_len(g.N) * sizeof(float2) + (size_t)(g.N >> 1) * sizeof(float2) +
+                            (size_t)lpb * sizeof(int64_t);
+        if (smem > 48 * 1024) {  // large nfft: opt in above the default 48 KB (per device, so on every such call)
+            cudaFuncSetAttribute(fft_r8_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(fft_r8_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(fft_r8_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(fft_r8_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        }
+        const unsigned th = (unsigned)(lpb * T);
+        if (real_in) {
+            if (strided) fft_r8_kernel<true, true><<<nb, th, smem, st>>>(in, out, g, tw, sign, scale);
+            else fft_r8_kernel<true, false><<<nb, th, smem, st>>>(in, out, g, tw, sign, scale);
+        } else {
+            if (strided) fft_r8_kernel<false, true><<<nb, th, smem, st>>>(in, out, g, tw, sign, scale);
+            else fft_r8_kernel<false, false><<<nb, th, smem, st>>>(in, out, g, tw, sign, scale);
+        }
+    } else if (g.log2N >= 0) {
         const size_t smem = (size_t)g.lpb * skewed_len(g.N) * sizeof(float2) + (size_t)g.lpb * sizeof(int64_t);
         if (real_in) fft_lines_kernel<true><<<blocks, 256, smem, st>>>(in, out, g, tw, sign, scale);
         else fft_lines_kernel<false><<<blocks, 256, smem, st>>>(in, out, g, tw, sign, scale);

@@ -48,6 +48,20 @@ def test_backward_matches_oracle(hos, oracle, n, L, N, window, rm, prec):
     assert normwise(got, ref) <= TOL[prec]
 
 
+@pytest.mark.parametrize("N", [8, 16, 1024])
+def test_backward_transform_sizes(hos, oracle, N):
+    """The adjoint transform (sign +1) on radix-8 register passes of every
+    last-pass radix (8: N = 8, 2: N = 16, 2: N = 1024 after three)."""
+    L = 3
+    x = hos_synth.ar2(600, 11 * N)
+    rng = np.random.default_rng(N)
+    G = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    ref = oracle.bispectrum_grad(x, L, G, N)
+    got = hos.bispectrum_backward(torch.from_numpy(x).cuda(), torch.from_numpy(G.astype(np.complex64)), L, nfft=N,
+                                  precision="fp32").cpu().numpy()
+    assert normwise(got, ref) <= TOL["fp32"]
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_autograd_bispectrum_matching_loss(hos, oracle, prec):
     """l = sum over the principal domain of |B(x) - B_target|^2 through

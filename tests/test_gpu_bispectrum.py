@@ -75,6 +75,18 @@ def test_bispectrum_elementwise(hos, oracle, prec, n, L, N, window):
     assert normwise(got, ref) <= TOL[prec]
 
 
+@pytest.mark.parametrize("N", [2, 4, 8, 16, 32, 128, 1024, 2048, 4096])
+def test_transform_sizes(hos, oracle, N):
+    """Every power-of-two grid size: radix-2 lines below 8 points, radix-8
+    register passes (one to four of them, the last of radix 8, 4 or 2) from 8
+    up to 4096.  Few lags keep the oracle's transform cheap on big grids."""
+    L = min(3, N // 2)
+    x = hos_synth.ar2(700, N)
+    ref = oracle.bispectrum(x, L, N)
+    got = hos.bispectrum(torch.from_numpy(x).cuda(), L, nfft=N, precision="fp32").cpu().numpy()
+    assert normwise(got, ref) <= TOL["fp32"]
+
+
 @pytest.mark.parametrize("tile_n,flush", [(128, 1), (256, 3), (64, 2)])
 def test_tile_and_flush_variants_agree(hos, oracle, tile_n, flush):
     x = hos_synth.ar2(7000, 5)

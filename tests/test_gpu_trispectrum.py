@@ -85,3 +85,14 @@ def test_trispectrum_hermitian_and_flat_level(hos):
     neg = T[(-k[:, None, None]) % N, (-k[None, :, None]) % N, (-k[None, None, :]) % N]
     assert np.abs(neg - np.conj(T)).max() <= 1e-6 * np.abs(T).max()
     assert abs(T.real.mean() * (2 * math.pi) ** 3 - 6.0) < 0.6
+
+
+@pytest.mark.parametrize("N", [8, 16, 128])
+def test_trispectrum_transform_sizes(hos, oracle, N):
+    """3-D transform on radix-8 register passes: contiguous lines along the
+    last axis, strided lines along the other two."""
+    L = 3
+    x = hos_synth.ar2(900, 5 * N)
+    ref = oracle.trispectrum(x, L, N)
+    got = hos.trispectrum(torch.from_numpy(x).cuda(), L, nfft=N, precision="fp32").cpu().numpy()
+    assert normwise(got, ref) <= TOL["fp32"]
