@@ -9,8 +9,12 @@ FP64 reduction + window, 2-D transform.  Metric unit: n (2L+1)^2 lag terms.
   python bench.py [--gpus N --steps K --warmup W --precision bf16|fp32|simt]
   python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
 
-Multi-GPU (torchrun, N > 1): every rank runs its own independent series
-(weak scaling, no collective); rank 0 prints the max-over-ranks time.
+Multi-GPU (torchrun, N > 1), weak scaling (2^21 samples per rank): the long
+workload becomes one series of N x 2^21 samples cut into time slices (each
+rank its slice plus L-sample halos; FP64 all-reduces of the series' sum and
+of c3; every rank transforms); the other workloads run one independent copy
+per rank.  Rank 0 prints the max-over-ranks time.  --time-slices runs the
+sliced layout on one rank.
 """
 from __future__ import annotations
 
@@ -193,7 +197,38 @@ def c3_tc_flops(L, lens, products):
         f"{ntiles} tiles x 128 x {tile_n} x {kpad} padded samples x {products} products x 2 flops")
 
 
-def make_workload(name, prec, rank, hos, torch, series=0):
+def m4_flops(L, n, prec):
+    """Executed flops of the m4 contraction.  Tensor cores: 128-pair tiles of
+    the lag triangle w1 <= w2 x next_pow2(2L) columns w3 x padded samples x 3
+    products x 2 (chunks of 1024 samples, 128 for 3xTF32).  SIMT: FFMA over
+    pair rows x w3 rounded to 16 x samples rounded to 4096."""
+    two_l = 2 * L
+    npairs = two_l * (two_l + 1) // 2
+    rows = math.ceil(npairs / 128) * 128
+    if prec in ("bf16", "fp32"):
+        cols = max(32, 1 << (two_l - 1).bit_length())
+        kc = 128 if prec == "fp32" else 1024
+        kpad = math.ceil(n / kc) * kc
+        return rows * cols * kpad * 6, f"{rows} lag pairs x {cols} w3 x {kpad} padded samples x 3 products x 2 flops"
+    w3 = 16 * math.ceil(two_l / 16)
+    kpad = math.ceil(n / 4096) * 4096
+    return rows * w3 * kpad * 2, f"{rows} lag pairs x {w3} w3 x {kpad} samples x 2 flops (FFMA)"
+
+
+def adjoint_flops(L, n, prec):
+    """Executed flops of the adjoint contraction U = Hankel(y) Gs.  Tensor
+    cores (split-bf16, L <= 128): 128-row tiles of u x 128-lag blocks of w1
+    x 2L rounded to 16 lags w2 x 3 products x 2.  SIMT: 2 flops per (u, w1, w2)."""
+    two_l = 2 * L
+    if prec == "bf16" and L <= 128:
+        kpad = 16 * math.ceil(two_l / 16)
+        nb, nut = math.ceil(two_l / 128), math.ceil(n / 128)
+        return nb * nut * 128 * 128 * kpad * 6, (
+            f"{nb} lag blocks x {nut} u tiles x 128 x 128 x {kpad} lags x 3 products x 2 flops")
+    return n * two_l * two_l * 2, f"{n} u x {two_l} x {two_l} lags x 2 flops (FFMA)"
+
+
+def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
     """Device-resident inputs, the step closure, the e2e closure, lag-term
     units per step, and the dominant kernel's executed work."""
     import numpy as np
@@ -203,13 +238,52 @@ def make_workload(name, prec, rank, hos, torch, series=0):
     L, N = w["L"], w["N"]
     ws = hos.Workspace()
     products = 3 if prec in ("bf16", "fp32") else 1
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if name == "long_bispectrum_n2M_L256" and (world > 1 or time_slices):
+        # one series of world x 2^21 samples, cut into time slices (one per
+        # rank, L-sample halos); two FP64 all-reduces join the ranks
+        import torch.distributed as dist
+        joined = dist.is_available() and dist.is_initialized()
+
+        from paper_1805_11775_gb300.shard import slice_with_halo
+        n_rank = w["x"].size
+        x_all = hos_synth.ar2(world * n_rank, 1002)
+        xh, hb, ha = slice_with_halo(x_all, rank, world, L)
+        xh = np.ascontiguousarray(xh)
+        xd = torch.from_numpy(xh).cuda()
+        step = lambda: hos.bispectrum_sharded(xd, L, hb, ha, x_all.size, precision=prec, workspace=ws)
+        x_pin = torch.from_numpy(xh).pin_memory()
+        e2e = lambda: hos.bispectrum_sharded(x_pin.to("cuda", non_blocking=True), L, hb, ha, x_all.size,
+                                             precision=prec, workspace=ws).cpu()
+
+        def profile():
+            """Stage times of one step, the library calls traced one by one."""
+            own = xd[hb:xd.numel() - ha]
+            tot = hos.series_sum(own, workspace=ws)
+            if joined:
+                dist.all_reduce(tot)
+            c3 = hos.cumulant3_slice(xd, L, hb, ha, tot, x_all.size, precision=prec, workspace=ws)
+            st = dict(hos.stage_times())
+            if joined:
+                dist.all_reduce(c3)
+            hos.bispectrum_from_cumulant(c3, L, workspace=ws)
+            for k, v in hos.stage_times():
+                st[k] = st.get(k, 0.0) + v
+            return list(st.items())
+
+        flops, work = c3_tc_flops(L, [xh.size - hb - ha], products)
+        return dict(step=step, e2e=e2e, profile=profile, units=units_of(xh.size - hb - ha, L), flops=flops,
+                    work=work, h2d=xh.nbytes, d2h=N * N * 8, bound="tensor" if products == 3 else "alu",
+                    config={"n": int(x_all.size), "n_per_rank": int(xh.size - hb - ha), "L": L, "grid": N,
+                            "parallelism": f"time slices x{world}, FP64 all-reduce of c3"})
     if name in ("long_bispectrum_n2M_L256", "bispectrum_n2048_L32"):
         x_host = w["x"] if rank == 0 else hos_synth.ar2(w["x"].size, 1002 + 100 * rank)
         xd = torch.from_numpy(x_host).cuda()
         out = torch.empty((N, N), dtype=torch.complex64, device="cuda")
         step = lambda: hos.bispectrum(xd, L, precision=prec, out=out, workspace=ws)
         x_pin = torch.from_numpy(x_host).pin_memory()
-        e2e = lambda: hos.bispectrum(x_pin, L, precision=prec, workspace=ws)
+        o_pin = torch.empty((N, N), dtype=torch.complex64).pin_memory()
+        e2e = lambda: hos.bispectrum(x_pin, L, precision=prec, workspace=ws, out=o_pin)
         flops, work = c3_tc_flops(L, [x_host.size], products)
         return dict(step=step, e2e=e2e, units=units_of(x_host.size, L), flops=flops, work=work,
                     h2d=x_host.nbytes, d2h=N * N * 8, config={"n": int(x_host.size), "L": L, "grid": N},
@@ -220,14 +294,11 @@ def make_workload(name, prec, rank, hos, torch, series=0):
         out = torch.empty((N, N, N), dtype=torch.complex64, device="cuda")
         step = lambda: hos.trispectrum(xd, L, precision=prec, out=out, workspace=ws)
         x_pin = torch.from_numpy(x_host).pin_memory()
-        e2e = lambda: hos.trispectrum(x_pin, L, precision=prec, workspace=ws)
-        twoL = 2 * L
-        npairs = twoL * (twoL + 1) // 2
-        w3 = 16 * math.ceil(twoL / 16)
-        kpad = math.ceil(x_host.size / 4096) * 4096
-        flops = math.ceil(npairs / 128) * 128 * w3 * kpad * 2
-        return dict(step=step, e2e=e2e, units=units_of(x_host.size, L, k=4), flops=flops, bound="alu",
-                    work=f"{math.ceil(npairs / 128) * 128} lag pairs x {w3} w3 x {kpad} samples x 2 flops (FFMA)",
+        o_pin = torch.empty((N, N, N), dtype=torch.complex64).pin_memory()
+        e2e = lambda: hos.trispectrum(x_pin, L, precision=prec, workspace=ws, out=o_pin)
+        flops, work = m4_flops(L, x_host.size, prec)
+        return dict(step=step, e2e=e2e, units=units_of(x_host.size, L, k=4), flops=flops,
+                    bound="tensor" if products == 3 else "alu", work=work,
                     h2d=x_host.nbytes, d2h=N ** 3 * 8, config={"n": int(x_host.size), "L": L, "grid": N})
     if name == "batched_4096x_L128":
         vals, offs = w["x"], w["offsets"]
@@ -242,7 +313,9 @@ def make_workload(name, prec, rank, hos, torch, series=0):
         max_len = int(lens.max())
         step = lambda: hos.bispectrum_batched(vd, od, L, precision=prec, out=out, workspace=ws, max_len=max_len)
         v_pin = torch.from_numpy(vals).pin_memory()
-        e2e = lambda: hos.bispectrum_batched(v_pin, offs, L, precision=prec, workspace=ws, max_len=max_len)
+        o_pin = torch.empty((S, N, N), dtype=torch.complex64).pin_memory()
+        e2e = lambda: hos.bispectrum_batched(v_pin, offs, L, precision=prec, workspace=ws, max_len=max_len,
+                                             out=o_pin)
         flops, work = c3_tc_flops(L, lens, products)
         return dict(step=step, e2e=e2e, units=int((lens * (2 * L + 1) ** 2).sum()), flops=flops, work=work,
                     h2d=vals.nbytes + offs.nbytes, d2h=S * N * N * 8, bound="tensor" if products == 3 else "alu",
@@ -269,9 +342,11 @@ def make_workload(name, prec, rank, hos, torch, series=0):
             G = 2.0 * (B - Bt) * mask
             return hos.bispectrum_backward(xg, G, L, workspace=ws2).cpu()
 
-        flops, work = c3_tc_flops(L, [x_host.size], products)
+        # the step's last call is the adjoint: its contraction is the timed stage
+        flops, work = adjoint_flops(L, x_host.size, prec)
         return dict(step=step, e2e=e2e, units=units_of(x_host.size, L), flops=flops, work=work,
-                    h2d=x_host.nbytes, d2h=x_host.nbytes, bound="tensor" if products == 3 else "alu",
+                    h2d=x_host.nbytes, d2h=x_host.nbytes,
+                    bound="tensor" if (prec == "bf16" and L <= 128) else "alu",
                     config={"n": int(x_host.size), "L": L, "grid": N, "step": "forward + adjoint"})
     raise KeyError(name)
 
@@ -292,7 +367,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     prec = args.precision
-    wl = make_workload(args.workload, prec, rank, hos, torch, args.series)
+    wl = make_workload(args.workload, prec, rank, hos, torch, args.series, args.time_slices)
     step = wl["step"]
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
 
@@ -312,7 +387,8 @@ def run_ours(args):
         graph.replay()
         torch.cuda.synchronize()
 
-    hos.set_profiling(graph is None)
+    traced = graph is None and "profile" not in wl  # stage times straight from each timed step
+    hos.set_profiling(traced)
     clocks = Clocks(local)
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -332,7 +408,7 @@ def run_ours(args):
             step()
         ev1[i].record()
         torch.cuda.synchronize()
-        if graph is None:
+        if traced:
             for name, ms in hos.stage_times():
                 stage_acc.setdefault(name, []).append(ms)
     torch.cuda.synchronize()
@@ -346,17 +422,22 @@ def run_ours(args):
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    if graph is not None:
-        # the graph replays the same kernels; the per-kernel time comes from an
-        # eager profiled pass over the same inputs
+    if not traced:
+        # graph replays (or a step of several traced calls): the per-stage time
+        # comes from an eager profiled pass over the same inputs
         hos.set_profiling(True)
         for _ in range(5):
             flush_buf.zero_()
-            step()
-            torch.cuda.synchronize()
-            for name, v in hos.stage_times():
+            if "profile" in wl:
+                st = wl["profile"]()
+            else:
+                step()
+                torch.cuda.synchronize()
+                st = hos.stage_times()
+            for name, v in st:
                 stage_acc.setdefault(name, []).append(v)
         hos.set_profiling(False)
+    if graph is not None:
         launches = launches_per_step * args.steps  # replays re-run the captured launches
     contract_ms = statistics.mean(stage_acc.get("contract", [float("nan")]))
 
@@ -453,6 +534,8 @@ def main():
                              "differentiable_n262144_L128"])
     ap.add_argument("--graph", action="store_true", help="capture one step in a CUDA graph and replay it")
     ap.add_argument("--series", type=int, default=0, help="batched workload: use only the first K series")
+    ap.add_argument("--time-slices", action="store_true",
+                    help="long workload: run the time-sliced path (the N > 1 layout) even on one rank")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

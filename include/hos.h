@@ -84,7 +84,10 @@ typedef enum {
     HOS_OP_BISPECTRUM_BATCHED = 2,
     HOS_OP_BISPECTRUM_BACKWARD = 3,
     HOS_OP_CUMULANT3 = 4,
-    HOS_OP_CUMULANT4 = 5
+    HOS_OP_CUMULANT4 = 5,
+    HOS_OP_SERIES_SUM = 6,
+    HOS_OP_CUMULANT3_SLICE = 7,
+    HOS_OP_BISPECTRUM_FROM_C3 = 8
 } hos_op;
 
 typedef struct {
@@ -154,6 +157,51 @@ hos_status hos_cumulant3(const void* d_x, int32_t dtype, int64_t n, const hos_pa
  *   d_c4 : (2L)^3 doubles, row-major [w1+L][w2+L][w3+L], w in [-L, L-1]    */
 hos_status hos_cumulant4(const void* d_x, int32_t dtype, int64_t n, const hos_params* params, double* d_c4,
                          void* ws, size_t ws_bytes, hos_stream_t stream);
+
+/* ---- One long series cut into time slices (one slice per GPU) -----------
+ * The time average c3(w1,w2) = (1/n) sum_i y(i)y(i+w1)y(i+w2) (Problem
+ * Statement) is a sum over i, so cutting i into slices [a_r, b_r) gives
+ * c3 = sum_r c3_r, where c3_r sums only the slice's i.  A slice needs its own
+ * samples, up to L samples on each side (its neighbours' halo) and the
+ * series' mean.  Per rank:
+ *   1. hos_series_sum over the slice's own samples; sum the ranks' sums
+ *      (FP64 all-reduce): the series' total;
+ *   2. hos_cumulant3_slice with that total;
+ *   3. sum the ranks' c3 (FP64 all-reduce of (2L)^2 doubles);
+ *   4. hos_bispectrum_from_cumulant on the summed c3.
+ * Up to FP64 rounding the result equals one hos_cumulant3 / hos_bispectrum
+ * call over the whole series.                                              */
+
+/* FP64 sum of d_x[0..n) into d_sum[0] (device), in a fixed order.
+ * Workspace: hos_workspace_size(HOS_OP_SERIES_SUM, n, 1, n, params, ...)
+ * (params may be NULL there).                                              */
+hos_status hos_series_sum(const void* d_x, int32_t dtype, int64_t n, double* d_sum, void* ws, size_t ws_bytes,
+                          hos_stream_t stream);
+
+/* One slice's share of c3 of a longer series.
+ *   d_x         : halo_before + n_slice + halo_after samples: the slice
+ *                 [a, a + n_slice) preceded by samples [a - halo_before, a)
+ *                 and followed by [a + n_slice, a + n_slice + halo_after);
+ *                 0 <= halo_* <= L, fewer than L only at the series' ends
+ *                 (outside the series the samples are zero)
+ *   d_sum       : device pointer to the FP64 sum of the whole series; the
+ *                 mean removed is *d_sum / n_total when params->remove_mean
+ *   n_total     : length of the whole series (the estimator's 1/n)
+ *   d_c3        : (2L)^2 doubles in hos_cumulant3's layout, receives
+ *                 (1/n_total) sum over i in the slice of y(i)y(i+w1)y(i+w2)
+ * segment_len must be 0.  Workspace: as hos_cumulant3 for n_slice samples
+ * (hos_workspace_size(HOS_OP_CUMULANT3_SLICE, n_slice, 1, n_slice, ...)).   */
+hos_status hos_cumulant3_slice(const void* d_x, int32_t dtype, int64_t n_slice, int64_t halo_before,
+                               int64_t halo_after, const double* d_sum, int64_t n_total, const hos_params* params,
+                               double* d_c3, void* ws, size_t ws_bytes, hos_stream_t stream);
+
+/* The last steps of hos_bispectrum from a given c3 (hos_cumulant3's layout):
+ * lag window, (2 pi)^-2, wrap onto the nfft grid, 2-D DFT into d_B (as
+ * hos_bispectrum).  The window and scale use the same FP32 arithmetic as
+ * hos_bispectrum, so c3 from hos_cumulant3 reproduces its output.
+ * Workspace: hos_workspace_size(HOS_OP_BISPECTRUM_FROM_C3, 0, 1, 0, ...).   */
+hos_status hos_bispectrum_from_cumulant(const double* d_c3, const hos_params* params, void* d_B, void* ws,
+                                        size_t ws_bytes, hos_stream_t stream);
 
 /* Bispectrum without a caller-supplied workspace, for callers that cannot
  * allocate device memory (no allocator at hand, or a context where calling

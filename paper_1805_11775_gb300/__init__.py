@@ -115,6 +115,23 @@ def _prepare(x):
     return x.contiguous(), host
 
 
+def _out_buffers(out, shape, device):
+    """(device result buffer, host tensor to fill or None).  A host ``out``
+    (pinned for a fast copy) receives the result after the device computes it."""
+    torch = _torch()
+    if out is not None and out.device.type == "cuda":
+        return out, None
+    dev = torch.empty(shape, dtype=torch.complex64, device=device)
+    return dev, out
+
+
+def _finish(dev, host_out, host_input):
+    if host_out is not None:
+        host_out.copy_(dev)
+        return host_out
+    return dev.cpu() if host_input else dev
+
+
 def _dtype_code(x):
     torch = _torch()
     return _native.F64 if x.dtype == torch.float64 else _native.F32
@@ -125,20 +142,20 @@ def bispectrum(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=True
     """Smoothed sample bispectrum B[k1, k2] (complex64, nfft x nfft, default nfft = 2L).
 
     ``precision``: "bf16" (split-bf16 tensor cores), "fp32" (3xTF32 tensor
-    cores) or "simt" (FP32 CUDA cores).  Host input returns a host result."""
+    cores) or "simt" (FP32 CUDA cores).  Host input returns a host result; a
+    host ``out`` (pinned for speed) receives the result."""
     torch = _torch()
     xd, host = _prepare(x)
     tile_n, flush_chunks = _tuned("bispectrum", L, xd.numel(), 1, precision, tile_n, flush_chunks)
     p = make_params(L, nfft, precision, window, remove_mean, segment_len, tile_n, flush_chunks)
     N = p.nfft or 2 * p.L
-    if out is None:
-        out = torch.empty((N, N), dtype=torch.complex64, device=xd.device)
+    dev, host_out = _out_buffers(out, (N, N), xd.device)
     ws = _workspace(workspace, xd.device)
     ws.get(workspace_size(_native.OP_BISPECTRUM, xd.numel(), 1, xd.numel(), p))
     _native.check(_native.lib().hos_bispectrum(xd.data_ptr(), _dtype_code(xd), xd.numel(), ctypes.byref(p),
-                                               out.data_ptr(), ws.ptr(), ws.nbytes(), _stream(stream)),
+                                               dev.data_ptr(), ws.ptr(), ws.nbytes(), _stream(stream)),
                   "hos_bispectrum")
-    return out.cpu() if host else out
+    return _finish(dev, host_out, host)
 
 
 def bispectrum_batched(values, offsets, L, nfft=0, precision="bf16", window="parzen", remove_mean=True, tile_n=0,
@@ -157,14 +174,13 @@ def bispectrum_batched(values, offsets, L, nfft=0, precision="bf16", window="par
     tile_n, flush_chunks = _tuned("bispectrum_batched", L, vd.numel(), S, precision, tile_n, flush_chunks)
     p = make_params(L, nfft, precision, window, remove_mean, 0, tile_n, flush_chunks)
     N = p.nfft or 2 * p.L
-    if out is None:
-        out = torch.empty((S, N, N), dtype=torch.complex64, device=vd.device)
+    dev, host_out = _out_buffers(out, (S, N, N), vd.device)
     ws = _workspace(workspace, vd.device)
     ws.get(workspace_size(_native.OP_BISPECTRUM_BATCHED, vd.numel(), S, max_len, p))
     _native.check(_native.lib().hos_bispectrum_batched(vd.data_ptr(), _dtype_code(vd), od.data_ptr(), S, vd.numel(),
-                                                       int(max_len), ctypes.byref(p), out.data_ptr(), ws.ptr(),
+                                                       int(max_len), ctypes.byref(p), dev.data_ptr(), ws.ptr(),
                                                        ws.nbytes(), _stream(stream)), "hos_bispectrum_batched")
-    return out.cpu() if host else out
+    return _finish(dev, host_out, host)
 
 
 def cumulant3(x, L, precision="bf16", remove_mean=True, segment_len=0, tile_n=0, flush_chunks=0, workspace=None,
@@ -189,14 +205,13 @@ def trispectrum(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=Tru
     xd, host = _prepare(x)
     p = make_params(L, nfft, precision, window, remove_mean, segment_len, 0, flush_chunks)
     N = p.nfft or 2 * p.L
-    if out is None:
-        out = torch.empty((N, N, N), dtype=torch.complex64, device=xd.device)
+    dev, host_out = _out_buffers(out, (N, N, N), xd.device)
     ws = _workspace(workspace, xd.device)
     ws.get(workspace_size(_native.OP_TRISPECTRUM, xd.numel(), 1, xd.numel(), p))
     _native.check(_native.lib().hos_trispectrum(xd.data_ptr(), _dtype_code(xd), xd.numel(), ctypes.byref(p),
-                                                out.data_ptr(), ws.ptr(), ws.nbytes(), _stream(stream)),
+                                                dev.data_ptr(), ws.ptr(), ws.nbytes(), _stream(stream)),
                   "hos_trispectrum")
-    return out.cpu() if host else out
+    return _finish(dev, host_out, host)
 
 
 def cumulant4(x, L, precision="bf16", remove_mean=True, segment_len=0, flush_chunks=0, workspace=None, stream=None):
@@ -211,6 +226,80 @@ def cumulant4(x, L, precision="bf16", remove_mean=True, segment_len=0, flush_chu
                                               out.data_ptr(), ws.ptr(), ws.nbytes(), _stream(stream)),
                   "hos_cumulant4")
     return out.cpu() if host else out
+
+
+def series_sum(x, workspace=None, stream=None):
+    """FP64 sum of x in the library's fixed order: a float64 device tensor of shape (1,)."""
+    torch = _torch()
+    xd, _ = _prepare(x)
+    out = torch.empty(1, dtype=torch.float64, device=xd.device)
+    ws = _workspace(workspace, xd.device)
+    ws.get(workspace_size(_native.OP_SERIES_SUM, xd.numel(), 1, xd.numel(), make_params(1)))
+    _native.check(_native.lib().hos_series_sum(xd.data_ptr(), _dtype_code(xd), xd.numel(), out.data_ptr(), ws.ptr(),
+                                               ws.nbytes(), _stream(stream)), "hos_series_sum")
+    return out
+
+
+def cumulant3_slice(x, L, halo_before, halo_after, total_sum, n_total, precision="bf16", remove_mean=True, tile_n=0,
+                    flush_chunks=0, workspace=None, stream=None):
+    """One time slice's share of c3 of a longer series (float64, (2L, 2L)).
+
+    ``x`` holds ``halo_before`` samples before the slice, the slice, and
+    ``halo_after`` samples after it (each <= L, fewer only at the series'
+    ends); ``total_sum`` is a float64 device tensor with the whole series' sum
+    and ``n_total`` its length.  Summing the slices' results gives c3 of the
+    whole series."""
+    torch = _torch()
+    xd, _ = _prepare(x)
+    n_slice = xd.numel() - int(halo_before) - int(halo_after)
+    p = make_params(L, 0, precision, "parzen", remove_mean, 0, tile_n, flush_chunks)
+    tot = total_sum.to(device=xd.device, dtype=torch.float64).contiguous()
+    out = torch.empty((2 * p.L, 2 * p.L), dtype=torch.float64, device=xd.device)
+    ws = _workspace(workspace, xd.device)
+    ws.get(workspace_size(_native.OP_CUMULANT3_SLICE, max(n_slice, 0), 1, max(n_slice, 0), p))
+    _native.check(_native.lib().hos_cumulant3_slice(xd.data_ptr(), _dtype_code(xd), n_slice, int(halo_before),
+                                                    int(halo_after), tot.data_ptr(), int(n_total), ctypes.byref(p),
+                                                    out.data_ptr(), ws.ptr(), ws.nbytes(), _stream(stream)),
+                  "hos_cumulant3_slice")
+    return out
+
+
+def bispectrum_from_cumulant(c3, L, nfft=0, window="parzen", out=None, workspace=None, stream=None):
+    """Window, scale and transform a c3 of :func:`cumulant3`'s layout into B."""
+    torch = _torch()
+    cd = c3.to(torch.float64).contiguous()
+    p = make_params(L, nfft, "bf16", window)
+    N = p.nfft or 2 * p.L
+    if out is None:
+        out = torch.empty((N, N), dtype=torch.complex64, device=cd.device)
+    ws = _workspace(workspace, cd.device)
+    ws.get(workspace_size(_native.OP_BISPECTRUM_FROM_C3, 0, 1, 0, p))
+    _native.check(_native.lib().hos_bispectrum_from_cumulant(cd.data_ptr(), ctypes.byref(p), out.data_ptr(), ws.ptr(),
+                                                             ws.nbytes(), _stream(stream)),
+                  "hos_bispectrum_from_cumulant")
+    return out
+
+
+def bispectrum_sharded(x_local, L, halo_before, halo_after, n_total, nfft=0, precision="bf16", window="parzen",
+                       remove_mean=True, group=None, workspace=None):
+    """Bispectrum of one long series whose time slices are spread over the
+    ranks of ``group`` (one GPU each; see :func:`shard.time_slices`).
+
+    ``x_local`` is this rank's slice with its halo.  Two FP64 sum
+    all-reduces: the series' total (for the mean) and the (2L)^2 c3.  Every
+    rank returns the full B.  Without an initialised process group this is
+    the single-rank case."""
+    import torch.distributed as dist
+    distributed = dist.is_available() and dist.is_initialized()
+    xd, _ = _prepare(x_local)
+    own = xd[int(halo_before):xd.numel() - int(halo_after)]
+    tot = series_sum(own, workspace=workspace)
+    if distributed:
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM, group=group)
+    c3 = cumulant3_slice(xd, L, halo_before, halo_after, tot, n_total, precision, remove_mean, workspace=workspace)
+    if distributed:
+        dist.all_reduce(c3, op=dist.ReduceOp.SUM, group=group)
+    return bispectrum_from_cumulant(c3, L, nfft, window, workspace=workspace)
 
 
 def bispectrum_backward(x, dB, L, nfft=0, precision="bf16", window="parzen", remove_mean=True, workspace=None,

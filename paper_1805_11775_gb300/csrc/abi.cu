@@ -102,7 +102,10 @@ static hos_status check_params(const hos_params* p, int op) {
     return HOS_OK;
 }
 
-static C3Geom make_geom(const hos_params* p, int G) {
+// skip_zero_window: leave out tiles where the window is zero at every lag
+// (PARZEN_SYM: d(w1 - w2) = 0 for |w1 - w2| >= L); the transform grid is
+// zero-filled there.  *zero_skipped counts them.
+static C3Geom make_geom(const hos_params* p, int G, bool skip_zero_window = false, int* zero_skipped = nullptr) {
     C3Geom g;
     memset(&g, 0, sizeof(g));
     const int twoL = 2 * p->L;
@@ -121,6 +124,16 @@ static C3Geom make_geom(const hos_params* p, int G) {
             // every w1 of the tile above every w2: mirrored, not computed
             const bool skip = (a * TILE_M >= b * N + N);
             if (skip) continue;
+            if (skip_zero_window) {
+                const int w1lo = -p->L + a * TILE_M, w1hi = w1lo + TILE_M - 1;
+                const int w2lo = -p->L + b * N, w2hi = w2lo + N - 1;
+                int gap = w1lo - w2hi;
+                if (w2lo - w1hi > gap) gap = w2lo - w1hi;
+                if (gap >= p->L) {  // min |w1 - w2| over the tile
+                    if (zero_skipped) ++*zero_skipped;
+                    continue;
+                }
+            }
             g.tile_idx[a][b] = (int8_t)cnt;
             g.tile_a[cnt] = (uint8_t)a;
             g.tile_b[cnt] = (uint8_t)b;
@@ -152,7 +165,7 @@ static int plane_elt(int precision) {
 static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t status, off, pad, unit, win, mean, mpart, bnd, xr, y32, hi, lo, partials, grid, tw, total;
+    size_t status, off, pad, unit, win, mean, mpart, bnd, xr, ilen, wtab, y32, hi, lo, partials, grid, tw, total;
     int64_t plane_len, slots;
     int nslices;
     int groups;
@@ -179,7 +192,9 @@ static Layout make_layout(int op, const hos_params* p, const C3Geom& g, int64_t 
     l.mean = o; o = al256(o + 8 * (size_t)S);
     l.mpart = o; o = al256(o + 8 * (size_t)S * l.nslices);
     l.bnd = o; o = al256(o + 8 * (size_t)(g.G + 1));
-    l.xr = o; o = al256(o + 8 * (size_t)S * g.ntiles);
+    l.xr = o; o = al256(o + sizeof(TileRec) * (size_t)S * g.ntiles);
+    l.ilen = o; o = al256(o + 8 * (size_t)S);
+    l.wtab = o; o = al256(o + 4 * (size_t)(4 * p->L));
     l.y32 = o; o = al256(o + 4 * (size_t)l.plane_len);
     const int elt = plane_elt(p->precision);
     l.hi = o; o = al256(o + (size_t)elt * l.plane_len + 64);
@@ -197,6 +212,7 @@ static Layout make_layout(int op, const hos_params* p, const C3Geom& g, int64_t 
 struct Plan {
     C3Geom g;
     Layout l;
+    int zero_tiles;  // tiles left out because the window is zero on them
     int S;           // series (batched) or parts (one series cut by segment_len)
     int64_t seg;     // part length, 0 = one part
     int64_t max_len; // longest series / part
@@ -224,7 +240,9 @@ static hos_status make_plan(int op, const hos_params* p, int64_t n_total, int S_
     }
     if (P.S > 65535) return HOS_ERR_UNSUPPORTED;
     int G = contraction_ctas(p->precision);
-    P.g = make_geom(p, G);
+    P.zero_tiles = 0;
+    const bool windowed = (op == HOS_OP_BISPECTRUM || op == HOS_OP_BISPECTRUM_BATCHED);
+    P.g = make_geom(p, G, windowed && p->window == HOS_WIN_PARZEN_SYM, &P.zero_tiles);
     if (U_known >= 0) {
         const int64_t U = U_known * P.g.ntiles;
         if (U < G) P.g.G = (int)(U > 0 ? U : 1);
@@ -262,10 +280,42 @@ static LineGeom line_geom(int N, int64_t nlines, int64_t inner, int64_t outer, i
     return g;
 }
 
+// A time slice of a longer series (hos_cumulant3_slice).
+struct SliceArgs {
+    int64_t halo_before, halo_after;  // neighbour samples around the slice in the input
+    const double* d_sum;              // FP64 sum of the whole series (device)
+    int64_t n_total;                  // length of the whole series
+};
+
+constexpr double kBispecScale = 1.0 / (4.0 * 3.14159265358979323846 * 3.14159265358979323846);  // (2 pi)^-2
+
+// hos_series_sum's workspace: off {0, n} (256 B), then one FP64 partial per slice
+static int sum_slices(int64_t n) {
+    int64_t k = ceil_div(n > 0 ? n : 1, 8192);
+    return (int)(k > 256 ? 256 : (k < 1 ? 1 : k));
+}
+static size_t sum_ws_bytes(int64_t n) { return 256 + al256(8 * (size_t)sum_slices(n)); }
+
+// hos_bispectrum_from_cumulant's workspace: window table, grid, twiddles
+struct FromC3Layout {
+    int Nf;
+    size_t wtab, grid, tw, total;
+};
+static FromC3Layout from_c3_layout(const hos_params* p) {
+    FromC3Layout l;
+    l.Nf = p->nfft ? p->nfft : 2 * p->L;
+    size_t o = 0;
+    l.wtab = o; o = al256(o + 4 * (size_t)(4 * p->L));
+    l.grid = o; o = al256(o + 4 * (size_t)l.Nf * l.Nf);
+    l.tw = o; o = al256(o + 8 * (size_t)l.Nf);
+    l.total = o;
+    return l;
+}
+
 // Steps shared by the c3 operations: plan, mean, planes, contraction, reduce.
 static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int64_t* d_offsets, const Plan& P,
                          const hos_params* p, void* ws, size_t ws_bytes, cudaStream_t st, Tracer& tr, int red_mode,
-                         float* grid_out, double* c3_out) {
+                         float* grid_out, double* c3_out, const SliceArgs* sl = nullptr) {
     const C3Geom& g = P.g;
     const Layout& l = P.l;
     const int S = P.S;
@@ -285,12 +335,19 @@ static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int6
     const int mode = (op == HOS_OP_BISPECTRUM_BATCHED) ? 1 : 0;
     HOS_CUDA_TRY(launch_plan_series(mode, n, P.seg, d_offsets, S, p->L, g.ntiles, g.flush, g.kc, g.pad_tail, off,
                                     pad, unit, win, st));
-    HOS_CUDA_TRY(launch_mean(x, dtype, off, S, l.nslices, at<double>(ws, l.mpart), p->remove_mean, mean, st));
+    const void* xs = x;
+    if (sl) {  // the whole series' mean; the slice's first sample follows its halo
+        HOS_CUDA_TRY(launch_slice_mean(sl->d_sum, sl->n_total, p->remove_mean, mean, st));
+        xs = reinterpret_cast<const uint8_t*>(x) + sl->halo_before * (dtype == HOS_F64 ? 8 : 4);
+    } else {
+        HOS_CUDA_TRY(launch_mean(x, dtype, off, S, l.nslices, at<double>(ws, l.mpart), p->remove_mean, mean, st));
+    }
     const int64_t maxpad = (int64_t)p->L + P.max_len + KC + g.pad_tail + 64;
     int bx = (int)ceil_div(maxpad, 256 * 4);
     if (bx < 1) bx = 1;
     if (bx > 65535) bx = 65535;
-    HOS_CUDA_TRY(launch_planes(x, dtype, off, pad, mean, p->L, plane_split(p->precision), y32, hi, lo, S, bx, st));
+    HOS_CUDA_TRY(launch_planes(xs, dtype, off, pad, mean, p->L, plane_split(p->precision), y32, hi, lo, S, bx, st,
+                               sl ? sl->halo_before : 0, sl ? sl->halo_after : 0));
 
     SeriesView sv{off, pad, unit, win, mean, S};
     tr.mark("contract");
@@ -314,12 +371,15 @@ static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int6
     rp.nfft = P.Nf;
     rp.mode = red_mode;
     rp.per_series_groups = (op == HOS_OP_BISPECTRUM_BATCHED) ? 1 : 0;
-    rp.scale = 1.0 / (4.0 * 3.14159265358979323846 * 3.14159265358979323846);
+    rp.scale = kBispecScale;
     rp.grid = grid_out;
     rp.c3out = c3_out;
+    rp.norm_len = sl ? sl->n_total : 0;
     const int groups = rp.per_series_groups ? S : 1;
-    if (red_mode == 0 && P.Nf > 2 * p->L) HOS_CUDA_TRY(launch_zero_f32(grid_out, (int64_t)groups * P.Nf * P.Nf, st));
-    HOS_CUDA_TRY(launch_reduce3(rp, groups, at<int64_t>(ws, l.bnd), at<int2>(ws, l.xr), st));
+    if (red_mode == 0 && (P.Nf > 2 * p->L || P.zero_tiles > 0))
+        HOS_CUDA_TRY(launch_zero_f32(grid_out, (int64_t)groups * P.Nf * P.Nf, st));
+    HOS_CUDA_TRY(launch_reduce3(rp, groups, P.max_len, at<int64_t>(ws, l.bnd), at<TileRec>(ws, l.xr), at<double>(ws, l.ilen),
+                                at<float>(ws, l.wtab), st));
     return HOS_OK;
 }
 
@@ -341,7 +401,7 @@ struct Plan4 {
     int Nf, W3, npb, nslices, pad_tail;
     bool tc;    // tensor-core m4 (split-bf16 / 3xTF32) instead of FP32 SIMT
     C3Geom g4;  // tensor-core geometry: tiles = blocks of 128 lag pairs, columns = w3
-    size_t status, off, pad, unit, win, mean, mpart, y32, hi, lo, bnd, xr, m4buf, c2, partials, grid, tw, total;
+    size_t status, off, pad, unit, win, mean, mpart, y32, hi, lo, bnd, xr, ilen, m4buf, c2, partials, grid, tw, total;
 };
 
 // Geometry of the tensor-core m4 contraction: tile t = pairs [128t, 128t+128)
@@ -422,7 +482,8 @@ static hos_status make_plan4(int op, const hos_params* p, int64_t n, Plan4& P) {
         P.hi = o; o = al256(o + (size_t)elt * plane_len + 64);
         P.lo = o; o = al256(o + (size_t)elt * plane_len + 64);
         P.bnd = o; o = al256(o + 8 * (size_t)(g.G + 1));
-        P.xr = o; o = al256(o + 8 * (size_t)P.S * g.ntiles);
+        P.xr = o; o = al256(o + sizeof(TileRec) * (size_t)P.S * g.ntiles);
+        P.ilen = o; o = al256(o + 8 * (size_t)P.S);
         P.partials = o; o = al256(o + 4 * (size_t)slots * tsz);
         P.m4buf = o; o = al256(o + 8 * (size_t)P.S * g.ntiles * tsz);
     } else {
@@ -482,8 +543,8 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
     g_last_contraction = tf32 ? "m4_tcgen05_3xtf32" : "m4_tcgen05_split_bf16";
     tr.mark("reduce");
     double* m4buf = at<double>(ws, P.m4buf);
-    HOS_CUDA_TRY(launch_m4_tile_reduce(P.g4, sv, at<float>(ws, P.partials), at<int64_t>(ws, P.bnd),
-                                       at<int2>(ws, P.xr), m4buf, st));
+    HOS_CUDA_TRY(launch_m4_tile_reduce(P.g4, sv, P.max_len, at<float>(ws, P.partials), at<int64_t>(ws, P.bnd),
+                                       at<TileRec>(ws, P.xr), at<double>(ws, P.ilen), m4buf, st));
     HOS_CUDA_TRY(launch_c4_assemble(m4buf, c2, off, P.S, p->L, P.g4.ntiles, P.g4.tile_n, r, st));
     return HOS_OK;
 }
@@ -575,7 +636,7 @@ const char* hos_last_contraction(void) { return g_last_contraction; }
 hos_status hos_workspace_size(int32_t op, int64_t n_total, int32_t n_series, int64_t max_len, const hos_params* p,
                               size_t* bytes) {
     if (!bytes || n_total < 0 || n_series < 1 || max_len < 0) return HOS_ERR_INVALID_ARG;
-    if (op < 0 || op > HOS_OP_CUMULANT4) return HOS_ERR_INVALID_ARG;
+    if (op < 0 || op > HOS_OP_BISPECTRUM_FROM_C3) return HOS_ERR_INVALID_ARG;
     if (op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT4) {
         Plan4 P4;
         hos_status s4 = make_plan4(op, p, n_total, P4);
@@ -590,11 +651,69 @@ hos_status hos_workspace_size(int32_t op, int64_t n_total, int32_t n_series, int
         *bytes = PB.total;
         return HOS_OK;
     }
+    if (op == HOS_OP_SERIES_SUM) {
+        *bytes = sum_ws_bytes(n_total);
+        return HOS_OK;
+    }
+    if (op == HOS_OP_BISPECTRUM_FROM_C3) {
+        hos_status sf = check_params(p, op);
+        if (sf != HOS_OK) return sf;
+        *bytes = from_c3_layout(p).total;
+        return HOS_OK;
+    }
     Plan P;
     hos_status s = make_plan(op, p, n_total, n_series, max_len, P);
     if (s != HOS_OK) return s;
     *bytes = P.l.total;
     return HOS_OK;
+}
+
+hos_status hos_series_sum(const void* d_x, int32_t dtype, int64_t n, double* d_sum, void* ws, size_t ws_bytes,
+                          hos_stream_t stream) {
+    if (!d_x || !d_sum || n < 1 || (dtype != HOS_F32 && dtype != HOS_F64)) return HOS_ERR_INVALID_ARG;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < sum_ws_bytes(n)) return HOS_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    HOS_CUDA_TRY(launch_series_sum(d_x, dtype, n, sum_slices(n), at<int64_t>(ws, 0), at<double>(ws, 256), d_sum,
+                                   st));
+    return HOS_OK;
+}
+
+hos_status hos_cumulant3_slice(const void* d_x, int32_t dtype, int64_t n_slice, int64_t halo_before,
+                               int64_t halo_after, const double* d_sum, int64_t n_total, const hos_params* p,
+                               double* d_c3, void* ws, size_t ws_bytes, hos_stream_t stream) {
+    if (!d_x || !d_c3 || !d_sum || !p || n_slice < 1 || (dtype != HOS_F32 && dtype != HOS_F64))
+        return HOS_ERR_INVALID_ARG;
+    if (halo_before < 0 || halo_after < 0 || halo_before > p->L || halo_after > p->L) return HOS_ERR_INVALID_ARG;
+    if (n_total < n_slice + halo_before + halo_after || p->segment_len != 0) return HOS_ERR_INVALID_ARG;
+    Plan P;
+    hos_status s = make_plan(HOS_OP_CUMULANT3_SLICE, p, n_slice, 1, n_slice, P);
+    if (s != HOS_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Tracer tr(st);
+    const SliceArgs sl{halo_before, halo_after, d_sum, n_total};
+    s = run_c3(HOS_OP_CUMULANT3_SLICE, d_x, dtype, n_slice, nullptr, P, p, ws, ws_bytes, st, tr, 1, nullptr, d_c3,
+               &sl);
+    tr.mark("");
+    return s;
+}
+
+hos_status hos_bispectrum_from_cumulant(const double* d_c3, const hos_params* p, void* d_B, void* ws,
+                                        size_t ws_bytes, hos_stream_t stream) {
+    if (!d_c3 || !d_B) return HOS_ERR_INVALID_ARG;
+    hos_status s = check_params(p, HOS_OP_BISPECTRUM_FROM_C3);
+    if (s != HOS_OK) return s;
+    const FromC3Layout l = from_c3_layout(p);
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < l.total) return HOS_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Tracer tr(st);
+    tr.mark("reduce");
+    float* grid = at<float>(ws, l.grid);
+    if (l.Nf > 2 * p->L) HOS_CUDA_TRY(launch_zero_f32(grid, (int64_t)l.Nf * l.Nf, st));
+    HOS_CUDA_TRY(launch_window_c3(d_c3, p->L, p->window, l.Nf, kBispecScale, at<float>(ws, l.wtab), grid, st));
+    tr.mark("transform");
+    s = run_dft2(grid, reinterpret_cast<float2*>(d_B), 1, l.Nf, at<float2>(ws, l.tw), st);
+    tr.mark("");
+    return s;
 }
 
 hos_status hos_bispectrum(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, void* d_B, void* ws,

@@ -26,6 +26,7 @@ __global__ void __launch_bounds__(256) c3_simt_kernel(const C3SimtParams P) {
     while (walk.next(part)) {
         const int a = geo.tile_a[part.t], b = geo.tile_b[part.t];
         const int64_t base = P.ser.pad[part.s];
+        const int64_t slen = P.ser.off[part.s + 1] - P.ser.off[part.s];  // rows i >= len: y(i) = 0
         float acc[8][NC];
 #pragma unroll
         for (int r = 0; r < 8; ++r)
@@ -39,7 +40,7 @@ __global__ void __launch_bounds__(256) c3_simt_kernel(const C3SimtParams P) {
             const float* gb = P.y32 + base + i0 + (int64_t)b * N;
             __syncthreads();
             for (int t = threadIdx.x; t < kc + TILE_M; t += 256) ya[t] = ga[t];
-            for (int t = threadIdx.x; t < kc; t += 256) yi[t] = gi[t];
+            for (int t = threadIdx.x; t < kc; t += 256) yi[t] = (i0 + t < slen) ? gi[t] : 0.0f;
             for (int t = threadIdx.x; t < kc + N; t += 256) yb[t] = gb[t];
             __syncthreads();
 #pragma unroll 4

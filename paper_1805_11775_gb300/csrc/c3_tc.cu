@@ -136,6 +136,9 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
         while (ok && walk.next(part)) {
             const int a = geo.tile_a[part.t], b = geo.tile_b[part.t];
             const int64_t base = P.ser.pad[part.s];
+            // rows i >= len carry y(i) = 0 (a time slice keeps its neighbour's
+            // samples after it in the plane, for the lags only)
+            const int64_t slen = P.ser.off[part.s + 1] - P.ser.off[part.s];
             for (int64_t c = part.c0; c < part.c1 && ok; ++c, ++kc) {
                 const int buf = kc & 1;
                 ok = warp_wait(&sm.empty_b[buf], ((kc >> 1) & 1) ^ 1, abort, P.status, lim, 2000);
@@ -160,7 +163,8 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                 if (!ok) break;
                 {   // realign y(i0 + t) so that builders can use 16-byte broadcast loads
                     const int ish = (int)(ib - ib_al);
-                    for (int t = lane; t < csz; t += 32) sm.yi[buf][t] = sm.yi_raw[ish + t];
+                    for (int t = lane; t < csz; t += 32)
+                        sm.yi[buf][t] = (i0 + t < slen) ? sm.yi_raw[ish + t] : 0.0f;
                 }
                 // interleave: block (q, r) <- samples [R q + r, R q + r + R)
                 const int ngroups = (csz + N) / R + 2;

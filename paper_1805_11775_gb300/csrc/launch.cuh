@@ -27,6 +27,16 @@ struct C3SimtParams {
 
 // mode 0: spectrum input grid[g][(w2 mod Nf)][(w1 mod Nf)] = scale * W * c3 (fp32)
 // mode 1: raw cumulant c3out[g][w2+L][w1+L] (fp64, symmetric so also [w1][w2])
+// Where the parts of one (series, computed tile) live (reduce.cu).
+struct TileRec {
+    int64_t slot;   // first main slot: one per flush window, contiguous
+    int64_t ub;     // first work unit of (series, tile)
+    int32_t nwin;   // main slots
+    int32_t xlo;    // CTAs [xlo, xhi) start inside (series, tile)
+    int32_t xhi;
+    int32_t pad;
+};
+
 struct Reduce3Params {
     C3Geom geom;
     SeriesView ser;
@@ -38,6 +48,7 @@ struct Reduce3Params {
     double scale;
     float* grid;
     double* c3out;
+    int64_t norm_len;  // > 0: divide by this length instead of each series' own (a time slice)
 };
 
 struct LineGeom {
@@ -68,13 +79,23 @@ void count_launch();
 cudaError_t launch_plan_series(int mode, int64_t n, int64_t seg, const int64_t* d_user_off, int S, int L, int ntiles,
                                int flush, int kc, int pad_tail, int64_t* off, int64_t* pad, int64_t* unit,
                                int64_t* win, cudaStream_t st);
+// remove_mean < 0: write each series' plain FP64 sum instead of its mean
 cudaError_t launch_mean(const void* x, int dtype, const int64_t* off, int S, int nslices, double* part,
                         int remove_mean, double* mean, cudaStream_t st);
+// ext_lo / ext_hi: halo samples before / after a time slice (see planes_kernel)
 cudaError_t launch_planes(const void* x, int dtype, const int64_t* off, const int64_t* pad, const double* mean, int L,
-                          int split, float* y32, void* hi, void* lo, int S, int blocks_x, cudaStream_t st);
+                          int split, float* y32, void* hi, void* lo, int S, int blocks_x, cudaStream_t st,
+                          int64_t ext_lo = 0, int64_t ext_hi = 0);
+cudaError_t launch_window_c3(const double* c3, int L, int window, int Nf, double scale, float* wtab, float* grid,
+                             cudaStream_t st);
+cudaError_t launch_series_sum(const void* x, int dtype, int64_t n, int nslices, int64_t* off, double* part,
+                              double* sum, cudaStream_t st);
+cudaError_t launch_slice_mean(const double* sum, int64_t n_total, int remove_mean, double* mean, cudaStream_t st);
 cudaError_t launch_c3_tc(bool tf32, int order, const C3TcParams& p, int G, cudaStream_t st);
 cudaError_t launch_c3_simt(const C3SimtParams& p, int G, cudaStream_t st);
-cudaError_t launch_reduce3(const Reduce3Params& p, int groups, int64_t* bnd, int2* xr, cudaStream_t st);
+// max_len: longest series (or part); it only sets how threads split the work.
+cudaError_t launch_reduce3(const Reduce3Params& p, int groups, int64_t max_len, int64_t* bnd, TileRec* rec,
+                           double* inv_len, float* wtab, cudaStream_t st);
 cudaError_t launch_zero_f32(float* p, int64_t n, cudaStream_t st);
 cudaError_t launch_twiddles(int N, float2* tw, cudaStream_t st);
 cudaError_t launch_lines(bool real_in, const void* in, float2* out, LineGeom g, const float2* tw, int sign,
@@ -95,8 +116,8 @@ cudaError_t launch_adjoint_tc(const float* y32, const uint16_t* hi, const uint16
                               const float* Gs, uint8_t* gsb, float* t1p, float* t2p, float* g, int* status,
                               uint64_t limit_ns, int G, cudaStream_t st);
 cudaError_t launch_gs(const float2* Gc, int N, int L, int window, double scale, float* Gs, cudaStream_t st);
-cudaError_t launch_m4_tile_reduce(const C3Geom& geo, const SeriesView& sv, const float* partials, int64_t* bnd,
-                                  int2* xr, double* m4buf, cudaStream_t st);
+cudaError_t launch_m4_tile_reduce(const C3Geom& geo, const SeriesView& sv, int64_t max_len, const float* partials,
+                                  int64_t* bnd, TileRec* rec, double* inv_len, double* m4buf, cudaStream_t st);
 cudaError_t launch_c2(const float* y32, const int64_t* off, const int64_t* pad, int S, int L, double* c2,
                       cudaStream_t st);
 cudaError_t launch_c4_assemble(const double* m4buf, const double* c2, const int64_t* off, int S, int L, int ntiles,

@@ -94,9 +94,18 @@ __global__ void mean_partial_kernel(const T* __restrict__ x, const int64_t* __re
     const int64_t per = ceil_div(len, nslices);
     const int64_t b0 = (int64_t)blockIdx.x * per;
     const int64_t b1 = b0 + per < len ? b0 + per : len;
-    double acc = 0.0;
-    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) acc += (double)x[o0 + i];
-    sh[threadIdx.x] = acc;
+    // four independent accumulators keep four loads in flight per thread
+    const int64_t bd = blockDim.x;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int64_t i = b0 + threadIdx.x;
+    for (; i + 3 * bd < b1; i += 4 * bd) {
+        a0 += (double)x[o0 + i];
+        a1 += (double)x[o0 + i + bd];
+        a2 += (double)x[o0 + i + 2 * bd];
+        a3 += (double)x[o0 + i + 3 * bd];
+    }
+    for (; i < b1; i += bd) a0 += (double)x[o0 + i];
+    sh[threadIdx.x] = (a0 + a1) + (a2 + a3);
     __syncthreads();
     for (int d = blockDim.x / 2; d > 0; d >>= 1) {
         if (threadIdx.x < d) sh[threadIdx.x] += sh[threadIdx.x + d];
@@ -105,23 +114,42 @@ __global__ void mean_partial_kernel(const T* __restrict__ x, const int64_t* __re
     if (threadIdx.x == 0) part[(int64_t)s * nslices + blockIdx.x] = sh[0];
 }
 
+// One warp per series: lanes take slices k = lane, lane + 32, ..., then a
+// fixed shuffle tree (deterministic).
 __global__ void mean_final_kernel(const double* __restrict__ part, const int64_t* __restrict__ off, int S,
                                   int nslices, int remove_mean, double* __restrict__ mean) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    const int64_t len = off[s + 1] - off[s];
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (s >= S) return;  // uniform per warp
     double acc = 0.0;
-    for (int k = 0; k < nslices; ++k) acc += part[(int64_t)s * nslices + k];
-    mean[s] = (remove_mean && len > 0) ? acc / (double)len : 0.0;
+    for (int k = lane; k < nslices; k += 32) acc += part[(int64_t)s * nslices + k];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
+    if (lane == 0) {
+        const int64_t len = off[s + 1] - off[s];
+        if (remove_mean < 0) mean[s] = acc;  // the plain sum (hos_series_sum)
+        else mean[s] = (remove_mean && len > 0) ? acc / (double)len : 0.0;
+    }
+}
+
+// Mean of a time slice of a longer series: the whole series' FP64 sum over
+// its length (or 0 without mean removal).
+__global__ void slice_mean_kernel(const double* __restrict__ sum, int64_t n_total, int remove_mean,
+                                  double* __restrict__ mean) {
+    if (threadIdx.x == 0) mean[0] = (remove_mean && n_total > 0) ? sum[0] / (double)n_total : 0.0;
 }
 
 // y = x - mean into the padded planes.  blockIdx.y = series; the block's
 // x-slices stride over that series' padded block [pad[s], pad[s+1]).
 // split: 0 = none (f32 plane only), 1 = bf16 hi/lo, 2 = tf32 hi/lo (as f32).
+// A time slice of a longer series also carries ext_lo samples before and
+// ext_hi after it (its neighbours' halo, x[o0 - ext_lo ..]); they go into the
+// zero padding on either side (ext_lo, ext_hi <= L).
 template <typename T>
 __global__ void planes_kernel(const T* __restrict__ x, const int64_t* __restrict__ off,
                               const int64_t* __restrict__ pad, const double* __restrict__ mean, int L, int split,
-                              float* __restrict__ y32, void* __restrict__ hi, void* __restrict__ lo) {
+                              int64_t ext_lo, int64_t ext_hi, float* __restrict__ y32, void* __restrict__ hi,
+                              void* __restrict__ lo) {
     const int s = blockIdx.y;
     const int64_t p0 = pad[s], p1 = pad[s + 1];
     const int64_t o0 = off[s], len = off[s + 1] - o0;
@@ -130,7 +158,7 @@ __global__ void planes_kernel(const T* __restrict__ x, const int64_t* __restrict
          p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = p - p0 - L;
         float v = 0.0f;
-        if (i >= 0 && i < len) v = (float)((double)x[o0 + i] - mu);
+        if (i >= -ext_lo && i < len + ext_hi) v = (float)((double)x[o0 + i] - mu);
         y32[p] = v;
         if (split == 1) {
             __nv_bfloat16* h = reinterpret_cast<__nv_bfloat16*>(hi);
@@ -163,18 +191,46 @@ cudaError_t launch_mean(const void* x, int dtype, const int64_t* off, int S, int
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    mean_final_kernel<<<(unsigned)ceil_div(S, 256), 256, 0, st>>>(part, off, S, nslices, remove_mean, mean);
+    mean_final_kernel<<<(unsigned)ceil_div(S, 8), 256, 0, st>>>(part, off, S, nslices, remove_mean, mean);
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_planes(const void* x, int dtype, const int64_t* off, const int64_t* pad, const double* mean, int L,
-                          int split, float* y32, void* hi, void* lo, int S, int blocks_x, cudaStream_t st) {
+                          int split, float* y32, void* hi, void* lo, int S, int blocks_x, cudaStream_t st,
+                          int64_t ext_lo, int64_t ext_hi) {
     dim3 g((unsigned)blocks_x, (unsigned)S);
-    if (dtype == HOS_F64) planes_kernel<double><<<g, 256, 0, st>>>((const double*)x, off, pad, mean, L, split, y32, hi, lo);
-    else planes_kernel<float><<<g, 256, 0, st>>>((const float*)x, off, pad, mean, L, split, y32, hi, lo);
+    if (dtype == HOS_F64)
+        planes_kernel<double><<<g, 256, 0, st>>>((const double*)x, off, pad, mean, L, split, ext_lo, ext_hi, y32, hi,
+                                                 lo);
+    else
+        planes_kernel<float><<<g, 256, 0, st>>>((const float*)x, off, pad, mean, L, split, ext_lo, ext_hi, y32, hi,
+                                                lo);
     count_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_slice_mean(const double* sum, int64_t n_total, int remove_mean, double* mean, cudaStream_t st) {
+    slice_mean_kernel<<<1, 32, 0, st>>>(sum, n_total, remove_mean, mean);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// off = {0, n}: the one-series view hos_series_sum reduces over
+__global__ void series_range_kernel(int64_t n, int64_t* off) {
+    if (threadIdx.x == 0) {
+        off[0] = 0;
+        off[1] = n;
+    }
+}
+
+cudaError_t launch_series_sum(const void* x, int dtype, int64_t n, int nslices, int64_t* off, double* part,
+                              double* sum, cudaStream_t st) {
+    series_range_kernel<<<1, 32, 0, st>>>(n, off);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_mean(x, dtype, off, 1, nslices, part, -1, sum, st);
 }
 
 }  // namespace hos

@@ -12,39 +12,20 @@ __global__ void bounds_kernel(const int64_t* __restrict__ unit, int S, int G, in
     if (g <= G) bnd[g] = range_begin(g, unit[S], G);
 }
 
-// Sum of one group of up to 16 consecutive main slots of (series, tile), as
-// an unevaluated sum of two floats (TwoSum, about 48 significant bits).
-HOS_DEV double group_sum(const float* __restrict__ p, int64_t tsz, int64_t cnt) {
-    float v[16];
-    if (cnt == 16) {
-#pragma unroll
-        for (int f = 0; f < 16; ++f) v[f] = p[f * tsz];  // independent loads in flight together
-    } else {
-#pragma unroll
-        for (int f = 0; f < 16; ++f) v[f] = (f < cnt) ? p[f * tsz] : 0.0f;
-    }
-    float hi = 0.0f, lo = 0.0f;
-#pragma unroll
-    for (int f = 0; f < 16; ++f) {
-        const float sum = hi + v[f];
-        const float bv = sum - hi;
-        lo += (hi - (sum - bv)) + (v[f] - bv);
-        hi = sum;
-    }
-    return (double)hi + (double)lo;
-}
-
 constexpr int REDUCE_THREADS = 256;
 
-// For every (series s, computed tile t): the CTAs whose unit range starts
-// strictly inside the (s, t) unit range, [xr.x, xr.y).  Those CTAs' first
-// parts that begin mid flush-window live in per-CTA slots.
+// For every (series s, computed tile t) a record of where its parts are:
+// the main slots (one per flush window, contiguous, in chunk order) and the
+// CTAs whose unit range starts strictly inside the (s, t) unit range,
+// [xlo, xhi) -- those CTAs' first parts, when they begin mid flush-window,
+// live in per-CTA slots.  Also 1/n of each series' time average.
 __global__ void part_ranges_kernel(const C3Geom geo, const SeriesView sv, const int64_t* __restrict__ bnd,
-                                   int2* __restrict__ xr) {
+                                   TileRec* __restrict__ rec, double* __restrict__ inv_len, int64_t norm_len) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= (int64_t)sv.S * geo.ntiles) return;
     const int s = (int)(q / geo.ntiles), t = (int)(q % geo.ntiles);
-    const int64_t nch = ceil_div(sv.off[s + 1] - sv.off[s], geo.kc);
+    const int64_t len = sv.off[s + 1] - sv.off[s];
+    const int64_t nch = ceil_div(len, geo.kc), nwin = ceil_div(nch, geo.flush);
     const int64_t ub = sv.unit[s] + (int64_t)t * nch, ue = ub + nch;
     int lo = 0, hi = geo.G;  // first CTA starting after ub
     while (lo < hi) {
@@ -53,117 +34,267 @@ __global__ void part_ranges_kernel(const C3Geom geo, const SeriesView sv, const 
     }
     int e = lo;
     while (e < geo.G && bnd[e] < ue) ++e;
-    xr[q] = make_int2(lo, e);
+    TileRec r;
+    r.slot = sv.win[s] + (int64_t)t * nwin;
+    r.ub = ub;
+    r.nwin = (int)nwin;
+    r.xlo = lo;
+    r.xhi = e;
+    r.pad = 0;
+    rec[q] = r;
+    // 1/n of the time average: the series' own length, or (a time slice of a
+    // longer series) that series' length
+    const int64_t nl = norm_len > 0 ? norm_len : len;
+    if (t == 0) inv_len[s] = len > 0 ? 1.0 / (double)nl : 0.0;
 }
 
-// Sum over the parts of (series s, computed tile t) at element `el`, divided
-// by the series length: the main parts (one per flush window, contiguous
-// slots in chunk order) in groups of 16 as two-float sums, the groups added
-// in FP64 in order, then the parts that start at a CTA boundary inside a
-// window, in CTA order.
-HOS_DEV double tile_part_sum(const C3Geom& geo, const SeriesView& sv, const float* __restrict__ partials, int s, int t,
-                             int64_t el, const int64_t* __restrict__ bnd, const int2* __restrict__ xr) {
-    const int F = geo.flush;
-    const int64_t tsz = (int64_t)TILE_M * geo.tile_n;
-    const int64_t total_win = sv.win[sv.S];
-    const int64_t len = sv.off[s + 1] - sv.off[s];
-    const int64_t nch = ceil_div(len, geo.kc), nwin = ceil_div(nch, F);
-    const int64_t ub = sv.unit[s] + (int64_t)t * nch;
-    const float* p = partials + (sv.win[s] + (int64_t)t * nwin) * tsz + el;
-    double acc = 0.0;
-    for (int64_t f0 = 0; f0 < nwin; f0 += 16) acc += group_sum(p + f0 * tsz, tsz, (nwin - f0 < 16) ? nwin - f0 : 16);
-    const int2 r = xr[(int64_t)s * geo.ntiles + t];
-    for (int g = r.x; g < r.y; ++g)
-        if ((int)(bnd[g] - ub) % F != 0 && bnd[g] < bnd[g + 1]) acc += (double)partials[(total_win + g) * tsz + el];
-    return acc / (double)len;
+// Lag-window table: wtab[t] = d(t - 2L) for t in [0, 4L) (the lags and
+// their differences), as FP32; RECT: 1 for |w| <= L-1, else 0.
+__global__ void window_table_kernel(int L, int kind, float* __restrict__ wtab) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 4 * L) return;
+    const int w = t - 2 * L;
+    wtab[t] = (kind == HOS_WIN_RECT) ? ((w >= -(L - 1) && w <= L - 1) ? 1.0f : 0.0f) : (float)parzen(w, L);
 }
 
-// One block = 256 consecutive elements (elem = j * 128 + m) of computed tile
-// blockIdx.y, output group blockIdx.z.  For each series of the group, thread
-// 0 lists the parts of (series, tile) that start at a CTA boundary inside a
-// flush window; then every thread sums its element: the main parts (one per
-// flush window, contiguous slots in chunk order) in groups of 16 as two-float
-// sums added in FP64 in order, then the listed parts in CTA order, and
-// divides by the series length.  Parts average over the group's series.
-// The value goes to lag (w1, w2) and, when the tile holding (w2, w1) is not
-// computed, to that mirrored lag as well (c3(w1,w2) = c3(w2,w1)).
-__global__ void __launch_bounds__(REDUCE_THREADS, 3) reduce3_kernel(const Reduce3Params P,
-                                                                    const int64_t* __restrict__ bnd,
-                                                                    const int2* __restrict__ xr) {
-    const C3Geom& geo = P.geom;
-    const SeriesView& sv = P.ser;
-    const int L = geo.L, N = geo.tile_n;
-    const int t = blockIdx.y, grp = blockIdx.z;
-    const int64_t tsz = (int64_t)TILE_M * N;
-    const int64_t elem = (int64_t)blockIdx.x * REDUCE_THREADS + threadIdx.x;
-    const int m = (int)(elem % TILE_M), j = (int)(elem / TILE_M);
-    const int w1 = -L + TILE_M * geo.tile_a[t] + m, w2 = -L + N * geo.tile_b[t] + j;
-    const bool live = elem < tsz && w1 < L && w2 < L;
-    const int64_t el = elem < tsz ? elem : 0;
-    const int s0 = P.per_series_groups ? grp : 0, s1 = P.per_series_groups ? grp + 1 : sv.S;
-    double c3 = 0.0;
-    int k = 0;
-    for (int s = s0; s < s1; ++s) {
-        if (sv.off[s + 1] <= sv.off[s]) continue;
-        c3 += tile_part_sum(geo, sv, P.partials, s, t, el, bnd, xr);
-        ++k;
+// This thread's share of the parts of (series s, computed tile t) at the
+// four consecutive elements of vector vi (elements 4 vi .. 4 vi + 3): the
+// main parts in groups of 16 windows, each group an unevaluated sum of two
+// floats per element (TwoSum in window order, about 48 significant bits),
+// groups gi, gi + gsplit, ... added in FP64 in that order; thread row gi = 0
+// then adds the parts that start at a CTA boundary inside a window, in CTA
+// order.  Not divided by the length.  Loads go four windows at a time.
+HOS_DEV void tile_share4(const float* __restrict__ partials, const TileRec& r, int tsz, int vi, int gi, int gsplit,
+                         int F, const int64_t* __restrict__ bnd, int64_t total_win, double (&acc)[4]) {
+    const int64_t st4 = tsz >> 2;  // float4 per slot
+    const float4* p4 = reinterpret_cast<const float4*>(partials + r.slot * (int64_t)tsz) + vi;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c] = 0.0;
+    for (int f0 = 16 * gi; f0 < r.nwin; f0 += 16 * gsplit) {
+        const int cnt = (r.nwin - f0 < 16) ? r.nwin - f0 : 16;
+        float hi[4] = {0.0f, 0.0f, 0.0f, 0.0f}, lo[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int f = 0; f < cnt; f += 4) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                v[u] = (f + u < cnt) ? p4[(int64_t)(f0 + f + u) * st4] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {  // a zero term leaves (hi, lo) unchanged
+                    const float sm = hi[c] + x[c];
+                    const float bv = sm - hi[c];
+                    lo[c] += (hi[c] - (sm - bv)) + (x[c] - bv);
+                    hi[c] = sm;
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] += (double)hi[c] + (double)lo[c];
     }
-    if (!P.per_series_groups && k > 0) c3 /= (double)k;
-    if (!live) return;
-    const int twoL = 2 * L;
-    const int ma = (w2 + L) / TILE_M, mb = (w1 + L) / N;
+    if (gi != 0) return;
+    for (int g = r.xlo; g < r.xhi; ++g) {
+        if ((int)(bnd[g] - r.ub) % F == 0 || bnd[g] >= bnd[g + 1]) continue;
+        const float4 x = reinterpret_cast<const float4*>(partials + (total_win + g) * (int64_t)tsz)[vi];
+        acc[0] += (double)x.x;
+        acc[1] += (double)x.y;
+        acc[2] += (double)x.z;
+        acc[3] += (double)x.w;
+    }
+}
+
+// Adds the gsplit thread rows' shares in row order (deterministic); the
+// result is valid in row 0.  Called by every thread of the block.
+HOS_DEV void combine_rows4(double (&v)[4], int ei, int gi, int es, int gsplit, double* red) {
+    if (gsplit == 1) return;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) red[(gi * es + ei) * 4 + c] = v[c];
+    __syncthreads();
+    if (gi == 0) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            double a = 0.0;
+            for (int r = 0; r < gsplit; ++r) a += red[(r * es + ei) * 4 + c];
+            v[c] = a;
+        }
+    }
+    __syncthreads();  // red is reused for the next series
+}
+
+// Window, scale and wrap of the c3 values of four consecutive elements
+// (elem0 = 4 vi, same lag w2, lags w1 .. w1 + 3) onto the transform grid, or
+// the raw values into the lag array; and their mirrors (w2, w1) when the tile
+// holding those lags is not computed (c3(w1,w2) = c3(w2,w1)).  Rows past the
+// last lag (w1 >= L) are padding.
+HOS_DEV void emit_c3x4(const Reduce3Params& P, const float* __restrict__ wtab, int grp, int t, int elem0,
+                       const double (&v)[4]) {
+    const C3Geom& geo = P.geom;
+    const int L = geo.L, N = geo.tile_n;
+    const int m0 = elem0 & (TILE_M - 1), j = elem0 >> 7;
+    const int w10 = -L + TILE_M * geo.tile_a[t] + m0, w2 = -L + N * geo.tile_b[t] + j;
+    if (w10 >= L || w2 >= L) return;
+    const int twoL = 2 * L, Nf = P.nfft;
+    const int ma = (w2 + L) / TILE_M, mb = (w10 + L) / N;  // the same for the four (N is a multiple of 4)
     const bool write_mirror = geo.tile_idx[ma][mb] < 0;
     if (P.mode == 1) {
         double* o = P.c3out + (int64_t)grp * twoL * twoL;
-        o[(int64_t)(w2 + L) * twoL + (w1 + L)] = c3;
-        if (write_mirror) o[(int64_t)(w1 + L) * twoL + (w2 + L)] = c3;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int w1 = w10 + c;
+            if (w1 >= L) break;
+            o[(int64_t)(w2 + L) * twoL + (w1 + L)] = v[c];
+            if (write_mirror) o[(int64_t)(w1 + L) * twoL + (w2 + L)] = v[c];
+        }
         return;
     }
-    const double wv = (P.window == HOS_WIN_RECT && (rect_excluded(w1, L) || rect_excluded(w2, L)))
-                          ? 0.0
-                          : lag_window2(w1, w2, L, P.window);
-    const int Nf = P.nfft;
-    const int k1 = (w1 % Nf + Nf) % Nf, k2 = (w2 % Nf + Nf) % Nf;
+    // window and scale in FP32 (the transform grid is FP32): W = d(w1) d(w2) [d(w1 - w2)]
+    float o[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int w1 = w10 + c;
+        float wv = wtab[w1 + twoL] * wtab[w2 + twoL];
+        if (P.window == HOS_WIN_PARZEN_SYM) wv *= wtab[w1 - w2 + twoL];
+        if (P.window == HOS_WIN_RECT && (rect_excluded(w1, L) || rect_excluded(w2, L))) wv = 0.0f;
+        o[c] = (float)v[c] * ((float)P.scale * wv);
+    }
     float* gr = P.grid + (int64_t)grp * Nf * Nf;
-    const float v = (float)(P.scale * wv * c3);
-    gr[(int64_t)k2 * Nf + k1] = v;
-    if (write_mirror) gr[(int64_t)k1 * Nf + k2] = v;
+    const int k2 = w2 < 0 ? w2 + Nf : w2;
+    const int k10 = w10 < 0 ? w10 + Nf : w10;
+    const int64_t at0 = (int64_t)grp * Nf * Nf + (int64_t)k2 * Nf + k10;  // the grid array is 256-byte aligned
+    if (w10 + 3 < L && (w10 >= 0 || w10 + 3 < 0) && (at0 & 3) == 0) {  // four live lags, no wrap, 16-byte store
+        *reinterpret_cast<float4*>(gr + (int64_t)k2 * Nf + k10) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int w1 = w10 + c;
+            if (w1 >= L) break;
+            const int k1 = w1 < 0 ? w1 + Nf : w1;
+            gr[(int64_t)k2 * Nf + k1] = o[c];
+        }
+    }
+    if (write_mirror) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int w1 = w10 + c;
+            if (w1 >= L) break;
+            const int k1 = w1 < 0 ? w1 + Nf : w1;
+            gr[(int64_t)k1 * Nf + k2] = o[c];
+        }
+    }
+}
+
+// Block = REDUCE_THREADS threads as gsplit rows x es = REDUCE_THREADS / gsplit
+// columns.  Column ei owns NV vectors of four consecutive elements (elem =
+// j * 128 + m) of computed tile blockIdx.y, output group blockIdx.z: vector
+// (blockIdx.x * NV + k) * es + ei.  Rows split the flush windows of long
+// series (gsplit > 1 with NV = 1); many short series take NV = 2 instead.
+// Per series: sum of its parts / its length; parts (segments) average over
+// the group.
+template <int NV>
+__global__ void __launch_bounds__(REDUCE_THREADS) reduce3_kernel(const Reduce3Params P, const int64_t* __restrict__ bnd,
+                                                                 const TileRec* __restrict__ rec,
+                                                                 const double* __restrict__ inv_len,
+                                                                 const float* __restrict__ wtab, int gsplit) {
+    __shared__ double red[REDUCE_THREADS * 4];
+    const C3Geom& geo = P.geom;
+    const SeriesView& sv = P.ser;
+    const int t = blockIdx.y, grp = blockIdx.z;
+    const int tsz = TILE_M * geo.tile_n, nvec = tsz >> 2;
+    const int es = REDUCE_THREADS / gsplit, ei = threadIdx.x % es, gi = threadIdx.x / es;
+    const int s0 = P.per_series_groups ? grp : 0, s1 = P.per_series_groups ? grp + 1 : sv.S;
+    const int64_t total_win = sv.win[sv.S];
+    int vi[NV];
+    double c3[NV][4];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        vi[k] = (blockIdx.x * NV + k) * es + ei;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) c3[k][c] = 0.0;
+    }
+    int cnt = 0;
+    for (int s = s0; s < s1; ++s) {
+        const TileRec r = rec[(int64_t)s * geo.ntiles + t];
+        if (r.nwin == 0) continue;  // empty series (uniform over the block)
+        const double il = inv_len[s];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double a[4];
+            tile_share4(P.partials, r, tsz, vi[k] < nvec ? vi[k] : 0, gi, gsplit, geo.flush, bnd, total_win, a);
+            combine_rows4(a, ei, gi, es, gsplit, red);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) c3[k][c] += a[c] * il;
+        }
+        ++cnt;
+    }
+    if (gi != 0) return;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        if (vi[k] >= nvec) continue;
+        if (!P.per_series_groups && cnt > 1)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) c3[k][c] /= (double)cnt;
+        emit_c3x4(P, wtab, grp, t, 4 * vi[k], c3[k]);
+    }
 }
 
 // Fourth order, tensor-core partials: m4buf[s][t][elem] = sum of the parts of
 // (part s, pair tile t) / length, FP64 (elem = (w3 + L) * 128 + pair in tile).
-__global__ void __launch_bounds__(REDUCE_THREADS, 3) m4_tile_reduce_kernel(const C3Geom geo, const SeriesView sv,
-                                                                           const float* __restrict__ partials,
-                                                                           const int64_t* __restrict__ bnd,
-                                                                           const int2* __restrict__ xr,
-                                                                           double* __restrict__ m4buf) {
+// Same thread layout as reduce3_kernel with NV = 1.
+__global__ void __launch_bounds__(REDUCE_THREADS) m4_tile_reduce_kernel(const C3Geom geo, const SeriesView sv,
+                                                                        const float* __restrict__ partials,
+                                                                        const int64_t* __restrict__ bnd,
+                                                                        const TileRec* __restrict__ rec,
+                                                                        const double* __restrict__ inv_len,
+                                                                        double* __restrict__ m4buf, int gsplit) {
+    __shared__ double red[REDUCE_THREADS * 4];
     const int t = blockIdx.y, s = blockIdx.z;
-    const int64_t tsz = (int64_t)TILE_M * geo.tile_n;
-    const int64_t elem = (int64_t)blockIdx.x * REDUCE_THREADS + threadIdx.x;
-    const int64_t el = elem < tsz ? elem : 0;
-    double v = 0.0;
-    if (sv.off[s + 1] > sv.off[s]) v = tile_part_sum(geo, sv, partials, s, t, el, bnd, xr);
-    if (elem < tsz) m4buf[((int64_t)s * geo.ntiles + t) * tsz + elem] = v;
+    const int tsz = TILE_M * geo.tile_n, nvec = tsz >> 2;
+    const int es = REDUCE_THREADS / gsplit, ei = threadIdx.x % es, gi = threadIdx.x / es;
+    const int vi = blockIdx.x * es + ei;
+    const TileRec r = rec[(int64_t)s * geo.ntiles + t];
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    if (r.nwin > 0) {  // uniform over the block
+        tile_share4(partials, r, tsz, vi < nvec ? vi : 0, gi, gsplit, geo.flush, bnd, sv.win[sv.S], a);
+        combine_rows4(a, ei, gi, es, gsplit, red);
+    }
+    if (gi != 0 || vi >= nvec) return;
+    const double il = inv_len[s];
+    double2* o = reinterpret_cast<double2*>(m4buf + ((int64_t)s * geo.ntiles + t) * tsz + 4 * (int64_t)vi);
+    o[0] = make_double2(a[0] * il, a[1] * il);
+    o[1] = make_double2(a[2] * il, a[3] * il);
 }
 
-static cudaError_t launch_part_index(const C3Geom& geo, const SeriesView& sv, int64_t* bnd, int2* xr,
-                                     cudaStream_t st) {
+// Rows of threads that split a (series, tile)'s flush windows: one per group
+// of 16 windows, at most 8; 1 when the longest series has one group.
+static int window_split(const C3Geom& geo, int64_t max_len) {
+    const int64_t nch = ceil_div(max_len > 0 ? max_len : 1, geo.kc);
+    const int64_t groups = ceil_div(ceil_div(nch, geo.flush), 16);
+    int g = 1;
+    while (g < 8 && 2 * g <= groups) g *= 2;
+    return g;
+}
+
+static cudaError_t launch_part_index(const C3Geom& geo, const SeriesView& sv, int64_t* bnd, TileRec* rec,
+                                     double* inv_len, int64_t norm_len, cudaStream_t st) {
     bounds_kernel<<<(unsigned)ceil_div(geo.G + 1, 256), 256, 0, st>>>(sv.unit, sv.S, geo.G, bnd);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    part_ranges_kernel<<<(unsigned)ceil_div((int64_t)sv.S * geo.ntiles, 256), 256, 0, st>>>(geo, sv, bnd, xr);
+    part_ranges_kernel<<<(unsigned)ceil_div((int64_t)sv.S * geo.ntiles, 256), 256, 0, st>>>(geo, sv, bnd, rec, inv_len,
+                                                                                              norm_len);
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_m4_tile_reduce(const C3Geom& geo, const SeriesView& sv, const float* partials, int64_t* bnd,
-                                  int2* xr, double* m4buf, cudaStream_t st) {
-    cudaError_t e = launch_part_index(geo, sv, bnd, xr, st);
+cudaError_t launch_m4_tile_reduce(const C3Geom& geo, const SeriesView& sv, int64_t max_len, const float* partials,
+                                  int64_t* bnd, TileRec* rec, double* inv_len, double* m4buf, cudaStream_t st) {
+    cudaError_t e = launch_part_index(geo, sv, bnd, rec, inv_len, 0, st);
     if (e != cudaSuccess) return e;
-    const int64_t tsz = (int64_t)TILE_M * geo.tile_n;
-    dim3 grid((unsigned)ceil_div(tsz, REDUCE_THREADS), (unsigned)geo.ntiles, (unsigned)sv.S);
-    m4_tile_reduce_kernel<<<grid, REDUCE_THREADS, 0, st>>>(geo, sv, partials, bnd, xr, m4buf);
+    const int64_t nvec = (int64_t)TILE_M * geo.tile_n / 4;
+    const int gsplit = window_split(geo, max_len);
+    dim3 grid((unsigned)ceil_div(nvec, REDUCE_THREADS / gsplit), (unsigned)geo.ntiles, (unsigned)sv.S);
+    m4_tile_reduce_kernel<<<grid, REDUCE_THREADS, 0, st>>>(geo, sv, partials, bnd, rec, inv_len, m4buf, gsplit);
     count_launch();
     return cudaGetLastError();
 }
@@ -189,12 +320,51 @@ __global__ void timeout_selftest_kernel(int* status, uint64_t limit_ns) {
     __syncthreads();
 }
 
-cudaError_t launch_reduce3(const Reduce3Params& p, int groups, int64_t* bnd, int2* xr, cudaStream_t st) {
-    cudaError_t e = launch_part_index(p.geom, p.ser, bnd, xr, st);
+cudaError_t launch_reduce3(const Reduce3Params& p, int groups, int64_t max_len, int64_t* bnd, TileRec* rec,
+                           double* inv_len, float* wtab, cudaStream_t st) {
+    cudaError_t e = launch_part_index(p.geom, p.ser, bnd, rec, inv_len, p.norm_len, st);
     if (e != cudaSuccess) return e;
-    const int64_t tsz = (int64_t)TILE_M * p.geom.tile_n;
-    dim3 grid((unsigned)ceil_div(tsz, REDUCE_THREADS), (unsigned)p.geom.ntiles, (unsigned)groups);
-    reduce3_kernel<<<grid, REDUCE_THREADS, 0, st>>>(p, bnd, xr);
+    window_table_kernel<<<(unsigned)ceil_div(4 * p.geom.L, 256), 256, 0, st>>>(p.geom.L, p.window, wtab);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t nvec = (int64_t)TILE_M * p.geom.tile_n / 4;
+    const int gsplit = window_split(p.geom, max_len);
+    if (gsplit == 1 && ceil_div(nvec, REDUCE_THREADS) * p.geom.ntiles * groups >= 4096) {
+        // many (short) output groups: two vectors per thread
+        dim3 grid((unsigned)ceil_div(nvec, 2 * REDUCE_THREADS), (unsigned)p.geom.ntiles, (unsigned)groups);
+        reduce3_kernel<2><<<grid, REDUCE_THREADS, 0, st>>>(p, bnd, rec, inv_len, wtab, 1);
+    } else {
+        dim3 grid((unsigned)ceil_div(nvec, REDUCE_THREADS / gsplit), (unsigned)p.geom.ntiles, (unsigned)groups);
+        reduce3_kernel<1><<<grid, REDUCE_THREADS, 0, st>>>(p, bnd, rec, inv_len, wtab, gsplit);
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Window, scale and wrap of a given c3 (hos_cumulant3's layout: element
+// (w2 + L) * 2L + (w1 + L)) onto the transform grid, in the arithmetic of
+// emit_c3x4, so that a c3 from hos_cumulant3 gives hos_bispectrum's grid.
+__global__ void window_c3_kernel(const double* __restrict__ c3, int L, int window, const float* __restrict__ wtab,
+                                 int Nf, double scale, float* __restrict__ grid) {
+    const int twoL = 2 * L;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= twoL * twoL) return;
+    const int w1 = e % twoL - L, w2 = e / twoL - L;
+    float wv = wtab[w1 + twoL] * wtab[w2 + twoL];
+    if (window == HOS_WIN_PARZEN_SYM) wv *= wtab[w1 - w2 + twoL];
+    if (window == HOS_WIN_RECT && (rect_excluded(w1, L) || rect_excluded(w2, L))) wv = 0.0f;
+    const int k1 = w1 < 0 ? w1 + Nf : w1, k2 = w2 < 0 ? w2 + Nf : w2;
+    grid[(int64_t)k2 * Nf + k1] = (float)c3[e] * ((float)scale * wv);
+}
+
+cudaError_t launch_window_c3(const double* c3, int L, int window, int Nf, double scale, float* wtab, float* grid,
+                             cudaStream_t st) {
+    window_table_kernel<<<(unsigned)ceil_div(4 * L, 256), 256, 0, st>>>(L, window, wtab);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    window_c3_kernel<<<(unsigned)ceil_div(4 * L * L, 256), 256, 0, st>>>(c3, L, window, wtab, Nf, scale, grid);
     count_launch();
     return cudaGetLastError();
 }

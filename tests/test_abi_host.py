@@ -78,6 +78,21 @@ def test_invalid_arguments_return_synchronously(lib):
     assert lib.hos_bispectrum_batched(dummy, 1, None, 3, 10, 5, ctypes.byref(p), dummy, dummy, 1 << 30, None) == 1
     assert lib.hos_get_device_status(None, None) == 1
     assert _native.STATUS_NAMES[3] == "HOS_ERR_WORKSPACE"
+    # time slices: halos longer than L, a whole series shorter than its slice,
+    # parts inside a slice, null pointers
+    ws = ctypes.c_void_p(0x100000)
+    assert lib.hos_cumulant3_slice(dummy, 1, 100, 33, 0, dummy, 1000, ctypes.byref(p), dummy, ws, 1 << 30, None) == 1
+    assert lib.hos_cumulant3_slice(dummy, 1, 100, 4, 4, dummy, 107, ctypes.byref(p), dummy, ws, 1 << 30, None) == 1
+    seg = _params(L=32, segment_len=50)
+    assert lib.hos_cumulant3_slice(dummy, 1, 100, 0, 0, dummy, 100, ctypes.byref(seg), dummy, ws, 1 << 30,
+                                   None) == 1
+    assert lib.hos_cumulant3_slice(dummy, 1, 100, 0, 0, None, 100, ctypes.byref(p), dummy, ws, 1 << 30, None) == 1
+    assert lib.hos_series_sum(dummy, 1, 0, dummy, ws, 1 << 20, None) == 1
+    assert lib.hos_series_sum(dummy, 1, 100, dummy, ws, 8, None) == 3
+    assert lib.hos_bispectrum_from_cumulant(None, ctypes.byref(p), dummy, ws, 1 << 20, None) == 1
+    assert lib.hos_bispectrum_from_cumulant(dummy, ctypes.byref(_params(L=32, nfft=8)), dummy, ws, 1 << 20,
+                                            None) == 1
+    assert lib.hos_bispectrum_from_cumulant(dummy, ctypes.byref(p), dummy, ws, 64, None) == 3
 
 
 def test_workspace_size_grows_with_the_problem(lib):

@@ -87,6 +87,20 @@ def test_transform_sizes(hos, oracle, N):
     assert normwise(got, ref) <= TOL["fp32"]
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_symmetric_window_leaves_out_zero_tiles(hos, oracle, prec):
+    """With d(w1 - w2) in the window, lag tiles where |w1 - w2| >= L
+    everywhere are not contracted (1 of 10 tiles at tile width 128, 2 of 20
+    at 64, L = 256); their grid entries are zero like the window."""
+    x = hos_synth.ma(3000, 5)
+    L = 256
+    ref = oracle.bispectrum(x, L, 512, window=oracle.WIN_PARZEN_SYM)
+    xd = torch.from_numpy(x).cuda()
+    for tile_n in (128, 64):
+        got = hos.bispectrum(xd, L, precision=prec, window="parzen_sym", tile_n=tile_n).cpu().numpy()
+        assert normwise(got, ref) <= TOL[prec]
+
+
 @pytest.mark.parametrize("tile_n,flush", [(128, 1), (256, 3), (64, 2)])
 def test_tile_and_flush_variants_agree(hos, oracle, tile_n, flush):
     x = hos_synth.ar2(7000, 5)

@@ -1,6 +1,8 @@
-"""The multi-process path on CPU (gloo, world size 2): series sharding covers
-every series exactly once, each rank's shard computed separately equals the
-single-process result, and the timing reduction takes the maximum."""
+"""The multi-process path on CPU (gloo, world size 2 and 3): series sharding
+covers every series exactly once, each rank's shard computed separately
+equals the single-process result, the timing reduction takes the maximum,
+and one long series cut into time slices with halos, joined by two FP64 sum
+all-reduces (series total, then c3), gives the whole series' c3."""
 import os
 import socket
 
@@ -8,7 +10,7 @@ import numpy as np
 import pytest
 
 import hos_synth
-from paper_1805_11775_gb300.shard import max_over_ranks, series_shard, shard_arrays
+from paper_1805_11775_gb300.shard import max_over_ranks, series_shard, shard_arrays, slice_with_halo, time_slices
 
 
 def test_series_shard_partitions_and_balances():
@@ -64,3 +66,66 @@ def test_two_gloo_ranks_match_one_process(tmp_path, oracle):
     assert ranges[0][0] == 0 and ranges[0][1] == ranges[1][0] and ranges[1][1] == lens.size
     np.testing.assert_array_equal(np.concatenate(parts), whole)
     assert all(float(np.load(tmp_path / f"tmax{r}.npy")[0]) == 2.0 for r in range(world))
+
+
+def test_time_slices_cover_the_series_with_halos():
+    for n, world, L in [(1000, 1, 8), (1000, 3, 8), (97, 4, 30), (10, 8, 4), (5, 3, 9)]:
+        sl = time_slices(n, world, L)
+        assert sl[0][0] == 0 and sl[-1][1] == n
+        for (a0, b0, _, _), (a1, _, _, _) in zip(sl, sl[1:]):
+            assert b0 == a1
+        for a, b, hb, ha in sl:
+            assert a <= b and hb == min(L, a) and ha == min(L, n - b)
+    x = np.arange(50.0)
+    piece, hb, ha = slice_with_halo(x, 1, 3, 4)
+    a, b, _, _ = time_slices(50, 3, 4)[1]
+    np.testing.assert_array_equal(piece, x[a - 4:b + 4])
+    assert (hb, ha) == (4, 4)
+
+
+def _slice_share(xh, hb, ha, mean, L, n_total):
+    """(1/n) sum over the slice's i of y(i)y(i+w1)y(i+w2), y = x - mean on the
+    window xh, zero outside it, as [w2 + L, w1 + L] (lags in [-L, L-1])."""
+    y = xh - mean
+    m = y.size
+    idx = np.arange(hb, m - ha)
+    out = np.zeros((2 * L, 2 * L))
+    for w1 in range(-L, L):
+        j1 = idx + w1
+        y1 = np.where((j1 >= 0) & (j1 < m), y[np.clip(j1, 0, m - 1)], 0.0)
+        for w2 in range(-L, L):
+            j2 = idx + w2
+            y2 = np.where((j2 >= 0) & (j2 < m), y[np.clip(j2, 0, m - 1)], 0.0)
+            out[w2 + L, w1 + L] = np.sum(y[idx] * y1 * y2) / n_total
+    return out
+
+
+def _slice_rank_main(rank, world, port, out_dir):
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    x = hos_synth.ar2(701, 31)
+    L = 6
+    xh, hb, ha = slice_with_halo(x, rank, world, L)
+    tot = torch.tensor([np.sum(xh[hb:xh.size - ha])], dtype=torch.float64)
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    c3 = torch.from_numpy(_slice_share(xh, hb, ha, float(tot[0]) / x.size, L, x.size))
+    dist.all_reduce(c3, op=dist.ReduceOp.SUM)
+    np.save(os.path.join(out_dir, f"c3_{rank}.npy"), c3.numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_time_sliced_ranks_sum_to_the_whole_series_c3(tmp_path, oracle, world):
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    mp.start_processes(_slice_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    x = hos_synth.ar2(701, 31)
+    L = 6
+    ref = oracle.c3(oracle.demean(x), L)[:2 * L, :2 * L].T  # [w2 + L, w1 + L]
+    for r in range(world):
+        got = np.load(tmp_path / f"c3_{r}.npy")
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
