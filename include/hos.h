@@ -66,11 +66,15 @@ typedef enum { HOS_F32 = 0, HOS_F64 = 1 } hos_dtype;
 
 /* Arithmetic of the cumulant contraction (the dominant step).
  *   FP32        : 3xTF32 split products on the tensor cores (tcgen05 kind::tf32),
- *                 FP32 accumulation, FP64 cross-tile reduction (~1e-6 relative);
+ *                 FP32 accumulation, FP64-class cross-tile reduction (~1e-6);
  *   SPLIT_BF16  : x = hi + lo in bf16, three products on the tensor cores
- *                 (tcgen05 kind::f16), FP32 accumulation, FP64 reduction (~1e-5);
+ *                 (tcgen05 kind::f16), FP32 accumulation, FP64-class
+ *                 reduction (~1e-5);
  *   SIMT_FP32   : plain FP32 FFMA on the CUDA cores (cross-check path).
- * Mean removal, cross-chunk reduction and c2 are FP64 in every mode.       */
+ * Mean removal is FP64.  The cross-chunk reduction and c2 are FP64-class in
+ * every mode: double-float sums (two floats, TwoSum / FMA, about 44-48
+ * significant bits) on the FP32 pipes, since GB300 issues FP64 at about 1/64
+ * of its FP32 rate.                                                        */
 typedef enum { HOS_PREC_FP32 = 0, HOS_PREC_SPLIT_BF16 = 1, HOS_PREC_SIMT_FP32 = 2 } hos_precision;
 
 /* Lag windows.  PARZEN: d(w1)d(w2)[d(w3)] (separable).  PARZEN_SYM (bispectrum
@@ -104,7 +108,7 @@ typedef struct {
                              tile one CTA accumulates (tuning knob)             */
     int32_t flush_chunks; /* 0: automatic; else the most 1024-sample chunks one
                              tile accumulates in FP32 before its partial sum is
-                             handed to the FP64 reduction (tuning knob)         */
+                             handed to the cross-chunk reduction (tuning knob)  */
 } hos_params;
 
 /* Bytes of workspace an operation needs.

@@ -142,7 +142,7 @@ static C3Geom make_geom(const hos_params* p, int G, bool skip_zero_window = fals
     g.ntiles = cnt;
     // The tensor cores' FP32 accumulation loses a little on every MMA step, one-sidedly,
     // so its error grows with the steps one partial accumulates.  The 3xTF32 path
-    // (8 samples per step) hands its partial to the FP64 reduction after every
+    // (8 samples per step) hands its partial to the reduction after every
     // 1024-sample chunk; split-bf16 (16 samples per step, 1e-4 target) and SIMT
     // (FP32 FFMA, round to nearest) after 16 chunks.
     g.flush = p->flush_chunks ? p->flush_chunks : (p->precision == HOS_PREC_FP32 ? 1 : 16);
@@ -378,8 +378,8 @@ static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int6
     const int groups = rp.per_series_groups ? S : 1;
     if (red_mode == 0 && (P.Nf > 2 * p->L || P.zero_tiles > 0))
         HOS_CUDA_TRY(launch_zero_f32(grid_out, (int64_t)groups * P.Nf * P.Nf, st));
-    HOS_CUDA_TRY(launch_reduce3(rp, groups, P.max_len, at<int64_t>(ws, l.bnd), at<TileRec>(ws, l.xr), at<double>(ws, l.ilen),
-                                at<float>(ws, l.wtab), st));
+    HOS_CUDA_TRY(launch_reduce3(rp, groups, P.max_len, at<int64_t>(ws, l.bnd), at<TileRec>(ws, l.xr),
+                                at<float2>(ws, l.ilen), at<float>(ws, l.wtab), st));
     return HOS_OK;
 }
 
@@ -425,7 +425,7 @@ static C3Geom make_geom4(const hos_params* p, int G) {
         g.tile_b[t] = 0;
     }
     // c4 = m4 - sum c2*c2 cancels, which magnifies the tensor cores' one-sided
-    // FP32 accumulation loss: partials go to the FP64 reduction after every
+    // FP32 accumulation loss: partials go to the reduction after every
     // chunk, and 3xTF32 chunks are 128 samples (48 MMA steps)
     g.flush = p->flush_chunks ? p->flush_chunks : 1;
     g.kc = (p->precision == HOS_PREC_FP32) ? 128 : KC;
@@ -544,7 +544,7 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
     tr.mark("reduce");
     double* m4buf = at<double>(ws, P.m4buf);
     HOS_CUDA_TRY(launch_m4_tile_reduce(P.g4, sv, P.max_len, at<float>(ws, P.partials), at<int64_t>(ws, P.bnd),
-                                       at<TileRec>(ws, P.xr), at<double>(ws, P.ilen), m4buf, st));
+                                       at<TileRec>(ws, P.xr), at<float2>(ws, P.ilen), m4buf, st));
     HOS_CUDA_TRY(launch_c4_assemble(m4buf, c2, off, P.S, p->L, P.g4.ntiles, P.g4.tile_n, r, st));
     return HOS_OK;
 }

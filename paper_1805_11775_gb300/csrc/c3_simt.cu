@@ -1,6 +1,6 @@
 // c3_simt.cu -- the same contraction C[w1,w2] = sum_i y(i) y(i+w1) y(i+w2) in
 // plain FP32 FFMA on the CUDA cores.  It walks the same stream-K unit ranges
-// and writes the same partial tiles as the tensor-core kernel, so the FP64
+// and writes the same partial tiles as the tensor-core kernel, so the
 // reduction is shared; it serves as the FP32 cross-check path.
 //
 // CTA = 256 threads over a 128 x N tile: thread (tx, ty) owns rows

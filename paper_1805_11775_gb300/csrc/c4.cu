@@ -8,8 +8,8 @@
 // m4 is symmetric in (w1, w2, w3), so only pairs w1 <= w2 are contracted:
 //   M[p, w3] = sum_i T[p, i] * y(i + w3),   T[p, i] = y(i) y(i + w1_p) y(i + w2_p),
 // an FP32 FFMA contraction (SIMT) over blocks of 128 pairs, in chunk groups of
-// CG * 1024 samples, each group's FP32 partial summed by the FP64 reduction.
-// c2 is accumulated in FP64 directly.
+// CG * 1024 samples, each group's FP32 partial summed in FP64 (this SIMT
+// cross-check path).  c2 is accumulated in double-float (c2_kernel).
 #include "launch.cuh"
 
 namespace hos {
@@ -20,25 +20,49 @@ HOS_HD int pair_index(int w1, int w2, int L) {
     return a * twoL - (a * (a - 1)) / 2 + (b - a);
 }
 
-// c2_s(t) for t in [-(2L-1), 2L-1] of every part s, FP64.  blockIdx.x = lag, .y = part.
-__global__ void c2_kernel(const float* __restrict__ y32, const int64_t* __restrict__ off,
-                          const int64_t* __restrict__ pad, int L, double* __restrict__ c2) {
-    __shared__ double sh[256];
+// c2_s(t) for t in [-(2L-1), 2L-1] of every part s.  blockIdx.x = lag, .y =
+// part.  GB300 issues FP64 at about 1/64 of its FP32 rate, so the sum runs in
+// double-float on the FP32 pipes: each product y(i) y(i+t) of two floats is
+// split exactly into p + e (FMA), and p, e are added to a TwoSum chain per
+// thread; the block combines the chains in a fixed tree and writes FP64.
+constexpr int C2_THREADS = 512;
+__global__ void __launch_bounds__(C2_THREADS) c2_kernel(const float* __restrict__ y32, const int64_t* __restrict__ off,
+                                                        const int64_t* __restrict__ pad, int L,
+                                                        double* __restrict__ c2) {
+    __shared__ float2 sh[C2_THREADS];
     const int T = 2 * L - 1;
     const int t = (int)blockIdx.x - T;
     const int s = blockIdx.y;
     const int64_t len = off[s + 1] - off[s];
     const float* y = y32 + pad[s] + L;  // y[i], zero-padded on both sides by >= L
-    double acc = 0.0;
+    float hi = 0.0f, lo = 0.0f;
     const int64_t i0 = t < 0 ? -t : 0, i1 = t > 0 ? len - t : len;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += (double)y[i] * (double)y[i + t];
-    sh[threadIdx.x] = acc;
+#pragma unroll 4
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += C2_THREADS) {
+        const float a = y[i], b = y[i + t];
+        const float p = a * b;
+        const float e = fmaf(a, b, -p);  // a b = p + e exactly
+        const float sm = hi + p;
+        const float bv = sm - hi;
+        lo += ((hi - (sm - bv)) + (p - bv)) + e;
+        hi = sm;
+    }
+    sh[threadIdx.x] = make_float2(hi, lo);
     __syncthreads();
-    for (int d = blockDim.x / 2; d > 0; d >>= 1) {
-        if (threadIdx.x < d) sh[threadIdx.x] += sh[threadIdx.x + d];
+    for (int d = C2_THREADS / 2; d > 0; d >>= 1) {
+        if (threadIdx.x < d) {  // (a.h + a.l) + (b.h + b.l), renormalised
+            const float2 a = sh[threadIdx.x], b = sh[threadIdx.x + d];
+            const float sm = a.x + b.x;
+            const float bb = sm - a.x;
+            float e = (a.x - (sm - bb)) + (b.x - bb);
+            e += a.y + b.y;
+            const float h = sm + e;
+            sh[threadIdx.x] = make_float2(h, e - (h - sm));
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) c2[(int64_t)s * (2 * T + 1) + blockIdx.x] = len > 0 ? sh[0] / (double)len : 0.0;
+    if (threadIdx.x == 0)
+        c2[(int64_t)s * (2 * T + 1) + blockIdx.x] = len > 0 ? ((double)sh[0].x + (double)sh[0].y) / (double)len : 0.0;
 }
 
 constexpr int M4_PAIRS = 128;  // pairs per CTA
@@ -233,7 +257,7 @@ __global__ void c4_assemble_kernel(const double* __restrict__ m4buf, const doubl
 cudaError_t launch_c2(const float* y32, const int64_t* off, const int64_t* pad, int S, int L, double* c2,
                       cudaStream_t st) {
     const int T = 2 * L - 1;
-    c2_kernel<<<dim3((unsigned)(2 * T + 1), (unsigned)S), 256, 0, st>>>(y32, off, pad, L, c2);
+    c2_kernel<<<dim3((unsigned)(2 * T + 1), (unsigned)S), C2_THREADS, 0, st>>>(y32, off, pad, L, c2);
     count_launch();
     return cudaGetLastError();
 }
@@ -250,7 +274,7 @@ cudaError_t launch_c4(const float* y32, const int64_t* off, const int64_t* pad, 
                       int CG, int64_t total_groups, double* c2, float* partials, const C4ReduceArgs& r,
                       cudaStream_t st) {
     const int T = 2 * L - 1;
-    c2_kernel<<<dim3((unsigned)(2 * T + 1), (unsigned)S), 256, 0, st>>>(y32, off, pad, L, c2);
+    c2_kernel<<<dim3((unsigned)(2 * T + 1), (unsigned)S), C2_THREADS, 0, st>>>(y32, off, pad, L, c2);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -95,7 +95,7 @@ cudaError_t launch_c3_tc(bool tf32, int order, const C3TcParams& p, int G, cudaS
 cudaError_t launch_c3_simt(const C3SimtParams& p, int G, cudaStream_t st);
 // max_len: longest series (or part); it only sets how threads split the work.
 cudaError_t launch_reduce3(const Reduce3Params& p, int groups, int64_t max_len, int64_t* bnd, TileRec* rec,
-                           double* inv_len, float* wtab, cudaStream_t st);
+                           float2* inv_len, float* wtab, cudaStream_t st);
 cudaError_t launch_zero_f32(float* p, int64_t n, cudaStream_t st);
 cudaError_t launch_twiddles(int N, float2* tw, cudaStream_t st);
 cudaError_t launch_lines(bool real_in, const void* in, float2* out, LineGeom g, const float2* tw, int sign,
@@ -117,7 +117,7 @@ cudaError_t launch_adjoint_tc(const float* y32, const uint16_t* hi, const uint16
                               uint64_t limit_ns, int G, cudaStream_t st);
 cudaError_t launch_gs(const float2* Gc, int N, int L, int window, double scale, float* Gs, cudaStream_t st);
 cudaError_t launch_m4_tile_reduce(const C3Geom& geo, const SeriesView& sv, int64_t max_len, const float* partials,
-                                  int64_t* bnd, TileRec* rec, double* inv_len, double* m4buf, cudaStream_t st);
+                                  int64_t* bnd, TileRec* rec, float2* inv_len, double* m4buf, cudaStream_t st);
 cudaError_t launch_c2(const float* y32, const int64_t* off, const int64_t* pad, int S, int L, double* c2,
                       cudaStream_t st);
 cudaError_t launch_c4_assemble(const double* m4buf, const double* c2, const int64_t* off, int S, int L, int ntiles,

@@ -1,7 +1,7 @@
-// reduce.cu -- deterministic FP64 reduction of the contraction's FP32 partial
-// tiles into c3, the 1/n time average, the average over parts (Algorithm DBS
-// step 6), the lag window, and the wrap of lags onto the N-point transform
-// grid (lag w -> index w mod N).
+// reduce.cu -- deterministic FP64-class (double-float) reduction of the
+// contraction's FP32 partial tiles into c3, the 1/n time average, the average
+// over parts (Algorithm DBS step 6), the lag window, and the wrap of lags onto
+// the N-point transform grid (lag w -> index w mod N).
 #include "launch.cuh"
 
 namespace hos {
@@ -20,7 +20,7 @@ constexpr int REDUCE_THREADS = 256;
 // [xlo, xhi) -- those CTAs' first parts, when they begin mid flush-window,
 // live in per-CTA slots.  Also 1/n of each series' time average.
 __global__ void part_ranges_kernel(const C3Geom geo, const SeriesView sv, const int64_t* __restrict__ bnd,
-                                   TileRec* __restrict__ rec, double* __restrict__ inv_len, int64_t norm_len) {
+                                   TileRec* __restrict__ rec, float2* __restrict__ inv_len, int64_t norm_len) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= (int64_t)sv.S * geo.ntiles) return;
     const int s = (int)(q / geo.ntiles), t = (int)(q % geo.ntiles);
@@ -45,7 +45,11 @@ __global__ void part_ranges_kernel(const C3Geom geo, const SeriesView sv, const 
     // 1/n of the time average: the series' own length, or (a time slice of a
     // longer series) that series' length
     const int64_t nl = norm_len > 0 ? norm_len : len;
-    if (t == 0) inv_len[s] = len > 0 ? 1.0 / (double)nl : 0.0;
+    if (t == 0) {  // as a double-float
+        const double inv = len > 0 ? 1.0 / (double)nl : 0.0;
+        const float h = (float)inv;
+        inv_len[s] = make_float2(h, (float)(inv - (double)h));
+    }
 }
 
 // Lag-window table: wtab[t] = d(t - 2L) for t in [0, 4L) (the lags and
@@ -57,29 +61,58 @@ __global__ void window_table_kernel(int L, int kind, float* __restrict__ wtab) {
     wtab[t] = (kind == HOS_WIN_RECT) ? ((w >= -(L - 1) && w <= L - 1) ? 1.0f : 0.0f) : (float)parzen(w, L);
 }
 
+// ---- double-float arithmetic ------------------------------------------------
+// GB300 issues FP64 at about 1/64 of its FP32 rate, so the cross-partial sums
+// run as unevaluated sums of two floats (h + l, TwoSum and FMA-based
+// products: about 44-48 significant bits, FP64-class for a sum whose terms
+// carry FP32 rounding) on the FP32 pipes; FP64 appears only where an FP64
+// array is written.
+struct DF {
+    float h, l;
+};
+HOS_DEV DF df_zero() { return DF{0.0f, 0.0f}; }
+// (a.h + a.l) + (b.h + b.l), renormalised
+HOS_DEV DF df_add(DF a, DF b) {
+    const float s = a.h + b.h;
+    const float bb = s - a.h;
+    float e = (a.h - (s - bb)) + (b.h - bb);
+    e += a.l + b.l;
+    const float h = s + e;
+    return DF{h, e - (h - s)};
+}
+// (a.h + a.l) * (b.h + b.l)
+HOS_DEV DF df_mul(DF a, DF b) {
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+    const float h = p + e;
+    return DF{h, e - (h - p)};
+}
+HOS_DEV double df_to_double(DF a) { return (double)a.h + (double)a.l; }
+
 // This thread's share of the parts of (series s, computed tile t) at the
-// four consecutive elements of vector vi (elements 4 vi .. 4 vi + 3): the
-// main parts in groups of 16 windows, each group an unevaluated sum of two
-// floats per element (TwoSum in window order, about 48 significant bits),
-// groups gi, gi + gsplit, ... added in FP64 in that order; thread row gi = 0
-// then adds the parts that start at a CTA boundary inside a window, in CTA
-// order.  Not divided by the length.  Loads go four windows at a time.
+// four consecutive elements of vector vi (elements 4 vi .. 4 vi + 3), as
+// double-float: the main parts in groups of 16 windows, each group a TwoSum
+// chain in window order, groups gi, gi + gsplit, ... added in that order;
+// thread row gi = 0 then adds the parts that start at a CTA boundary inside a
+// window, in CTA order.  Not divided by the length.  Loads go eight windows
+// at a time.
 HOS_DEV void tile_share4(const float* __restrict__ partials, const TileRec& r, int tsz, int vi, int gi, int gsplit,
-                         int F, const int64_t* __restrict__ bnd, int64_t total_win, double (&acc)[4]) {
+                         int F, const int64_t* __restrict__ bnd, int64_t total_win, DF (&acc)[4]) {
     const int64_t st4 = tsz >> 2;  // float4 per slot
     const float4* p4 = reinterpret_cast<const float4*>(partials + r.slot * (int64_t)tsz) + vi;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[c] = 0.0;
+    for (int c = 0; c < 4; ++c) acc[c] = df_zero();
     for (int f0 = 16 * gi; f0 < r.nwin; f0 += 16 * gsplit) {
         const int cnt = (r.nwin - f0 < 16) ? r.nwin - f0 : 16;
         float hi[4] = {0.0f, 0.0f, 0.0f, 0.0f}, lo[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        for (int f = 0; f < cnt; f += 4) {
-            float4 v[4];
+        for (int f = 0; f < cnt; f += 8) {
+            float4 v[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
                 v[u] = (f + u < cnt) ? p4[(int64_t)(f0 + f + u) * st4] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {  // a zero term leaves (hi, lo) unchanged
@@ -91,31 +124,34 @@ HOS_DEV void tile_share4(const float* __restrict__ partials, const TileRec& r, i
             }
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[c] += (double)hi[c] + (double)lo[c];
+        for (int c = 0; c < 4; ++c) acc[c] = df_add(acc[c], DF{hi[c], lo[c]});
     }
     if (gi != 0) return;
     for (int g = r.xlo; g < r.xhi; ++g) {
         if ((int)(bnd[g] - r.ub) % F == 0 || bnd[g] >= bnd[g + 1]) continue;
         const float4 x = reinterpret_cast<const float4*>(partials + (total_win + g) * (int64_t)tsz)[vi];
-        acc[0] += (double)x.x;
-        acc[1] += (double)x.y;
-        acc[2] += (double)x.z;
-        acc[3] += (double)x.w;
+        acc[0] = df_add(acc[0], DF{x.x, 0.0f});
+        acc[1] = df_add(acc[1], DF{x.y, 0.0f});
+        acc[2] = df_add(acc[2], DF{x.z, 0.0f});
+        acc[3] = df_add(acc[3], DF{x.w, 0.0f});
     }
 }
 
 // Adds the gsplit thread rows' shares in row order (deterministic); the
 // result is valid in row 0.  Called by every thread of the block.
-HOS_DEV void combine_rows4(double (&v)[4], int ei, int gi, int es, int gsplit, double* red) {
+HOS_DEV void combine_rows4(DF (&v)[4], int ei, int gi, int es, int gsplit, float2* red) {
     if (gsplit == 1) return;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) red[(gi * es + ei) * 4 + c] = v[c];
+    for (int c = 0; c < 4; ++c) red[(gi * es + ei) * 4 + c] = make_float2(v[c].h, v[c].l);
     __syncthreads();
     if (gi == 0) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            double a = 0.0;
-            for (int r = 0; r < gsplit; ++r) a += red[(r * es + ei) * 4 + c];
+            DF a = df_zero();
+            for (int r = 0; r < gsplit; ++r) {
+                const float2 q = red[(r * es + ei) * 4 + c];
+                a = df_add(a, DF{q.x, q.y});
+            }
             v[c] = a;
         }
     }
@@ -128,7 +164,7 @@ HOS_DEV void combine_rows4(double (&v)[4], int ei, int gi, int es, int gsplit, d
 // holding those lags is not computed (c3(w1,w2) = c3(w2,w1)).  Rows past the
 // last lag (w1 >= L) are padding.
 HOS_DEV void emit_c3x4(const Reduce3Params& P, const float* __restrict__ wtab, int grp, int t, int elem0,
-                       const double (&v)[4]) {
+                       const DF (&v)[4]) {
     const C3Geom& geo = P.geom;
     const int L = geo.L, N = geo.tile_n;
     const int m0 = elem0 & (TILE_M - 1), j = elem0 >> 7;
@@ -143,8 +179,9 @@ HOS_DEV void emit_c3x4(const Reduce3Params& P, const float* __restrict__ wtab, i
         for (int c = 0; c < 4; ++c) {
             const int w1 = w10 + c;
             if (w1 >= L) break;
-            o[(int64_t)(w2 + L) * twoL + (w1 + L)] = v[c];
-            if (write_mirror) o[(int64_t)(w1 + L) * twoL + (w2 + L)] = v[c];
+            const double d = df_to_double(v[c]);
+            o[(int64_t)(w2 + L) * twoL + (w1 + L)] = d;
+            if (write_mirror) o[(int64_t)(w1 + L) * twoL + (w2 + L)] = d;
         }
         return;
     }
@@ -156,7 +193,7 @@ HOS_DEV void emit_c3x4(const Reduce3Params& P, const float* __restrict__ wtab, i
         float wv = wtab[w1 + twoL] * wtab[w2 + twoL];
         if (P.window == HOS_WIN_PARZEN_SYM) wv *= wtab[w1 - w2 + twoL];
         if (P.window == HOS_WIN_RECT && (rect_excluded(w1, L) || rect_excluded(w2, L))) wv = 0.0f;
-        o[c] = (float)v[c] * ((float)P.scale * wv);
+        o[c] = (v[c].h + v[c].l) * ((float)P.scale * wv);
     }
     float* gr = P.grid + (int64_t)grp * Nf * Nf;
     const int k2 = w2 < 0 ? w2 + Nf : w2;
@@ -194,9 +231,9 @@ HOS_DEV void emit_c3x4(const Reduce3Params& P, const float* __restrict__ wtab, i
 template <int NV>
 __global__ void __launch_bounds__(REDUCE_THREADS) reduce3_kernel(const Reduce3Params P, const int64_t* __restrict__ bnd,
                                                                  const TileRec* __restrict__ rec,
-                                                                 const double* __restrict__ inv_len,
+                                                                 const float2* __restrict__ inv_len,
                                                                  const float* __restrict__ wtab, int gsplit) {
-    __shared__ double red[REDUCE_THREADS * 4];
+    __shared__ float2 red[REDUCE_THREADS * 4];
     const C3Geom& geo = P.geom;
     const SeriesView& sv = P.ser;
     const int t = blockIdx.y, grp = blockIdx.z;
@@ -205,25 +242,25 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce3_kernel(const Reduce3Pa
     const int s0 = P.per_series_groups ? grp : 0, s1 = P.per_series_groups ? grp + 1 : sv.S;
     const int64_t total_win = sv.win[sv.S];
     int vi[NV];
-    double c3[NV][4];
+    DF c3[NV][4];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         vi[k] = (blockIdx.x * NV + k) * es + ei;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) c3[k][c] = 0.0;
+        for (int c = 0; c < 4; ++c) c3[k][c] = df_zero();
     }
     int cnt = 0;
     for (int s = s0; s < s1; ++s) {
         const TileRec r = rec[(int64_t)s * geo.ntiles + t];
         if (r.nwin == 0) continue;  // empty series (uniform over the block)
-        const double il = inv_len[s];
+        const float2 il = inv_len[s];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double a[4];
+            DF a[4];
             tile_share4(P.partials, r, tsz, vi[k] < nvec ? vi[k] : 0, gi, gsplit, geo.flush, bnd, total_win, a);
             combine_rows4(a, ei, gi, es, gsplit, red);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) c3[k][c] += a[c] * il;
+            for (int c = 0; c < 4; ++c) c3[k][c] = df_add(c3[k][c], df_mul(a[c], DF{il.x, il.y}));
         }
         ++cnt;
     }
@@ -231,9 +268,14 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce3_kernel(const Reduce3Pa
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         if (vi[k] >= nvec) continue;
-        if (!P.per_series_groups && cnt > 1)
+        if (!P.per_series_groups && cnt > 1) {  // average over parts (rare: FP64 is fine here)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) c3[k][c] /= (double)cnt;
+            for (int c = 0; c < 4; ++c) {
+                const double q = df_to_double(c3[k][c]) / (double)cnt;
+                const float h = (float)q;
+                c3[k][c] = DF{h, (float)(q - (double)h)};
+            }
+        }
         emit_c3x4(P, wtab, grp, t, 4 * vi[k], c3[k]);
     }
 }
@@ -245,24 +287,27 @@ __global__ void __launch_bounds__(REDUCE_THREADS) m4_tile_reduce_kernel(const C3
                                                                         const float* __restrict__ partials,
                                                                         const int64_t* __restrict__ bnd,
                                                                         const TileRec* __restrict__ rec,
-                                                                        const double* __restrict__ inv_len,
+                                                                        const float2* __restrict__ inv_len,
                                                                         double* __restrict__ m4buf, int gsplit) {
-    __shared__ double red[REDUCE_THREADS * 4];
+    __shared__ float2 red[REDUCE_THREADS * 4];
     const int t = blockIdx.y, s = blockIdx.z;
     const int tsz = TILE_M * geo.tile_n, nvec = tsz >> 2;
     const int es = REDUCE_THREADS / gsplit, ei = threadIdx.x % es, gi = threadIdx.x / es;
     const int vi = blockIdx.x * es + ei;
     const TileRec r = rec[(int64_t)s * geo.ntiles + t];
-    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    DF a[4] = {df_zero(), df_zero(), df_zero(), df_zero()};
     if (r.nwin > 0) {  // uniform over the block
         tile_share4(partials, r, tsz, vi < nvec ? vi : 0, gi, gsplit, geo.flush, bnd, sv.win[sv.S], a);
         combine_rows4(a, ei, gi, es, gsplit, red);
     }
     if (gi != 0 || vi >= nvec) return;
-    const double il = inv_len[s];
-    double2* o = reinterpret_cast<double2*>(m4buf + ((int64_t)s * geo.ntiles + t) * tsz + 4 * (int64_t)vi);
-    o[0] = make_double2(a[0] * il, a[1] * il);
-    o[1] = make_double2(a[2] * il, a[3] * il);
+    const float2 il = inv_len[s];
+    double o[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) o[c] = df_to_double(df_mul(a[c], DF{il.x, il.y}));
+    double2* dst = reinterpret_cast<double2*>(m4buf + ((int64_t)s * geo.ntiles + t) * tsz + 4 * (int64_t)vi);
+    dst[0] = make_double2(o[0], o[1]);
+    dst[1] = make_double2(o[2], o[3]);
 }
 
 // Rows of threads that split a (series, tile)'s flush windows: one per group
@@ -276,7 +321,7 @@ static int window_split(const C3Geom& geo, int64_t max_len) {
 }
 
 static cudaError_t launch_part_index(const C3Geom& geo, const SeriesView& sv, int64_t* bnd, TileRec* rec,
-                                     double* inv_len, int64_t norm_len, cudaStream_t st) {
+                                     float2* inv_len, int64_t norm_len, cudaStream_t st) {
     bounds_kernel<<<(unsigned)ceil_div(geo.G + 1, 256), 256, 0, st>>>(sv.unit, sv.S, geo.G, bnd);
     count_launch();
     cudaError_t e = cudaGetLastError();
@@ -288,7 +333,7 @@ static cudaError_t launch_part_index(const C3Geom& geo, const SeriesView& sv, in
 }
 
 cudaError_t launch_m4_tile_reduce(const C3Geom& geo, const SeriesView& sv, int64_t max_len, const float* partials,
-                                  int64_t* bnd, TileRec* rec, double* inv_len, double* m4buf, cudaStream_t st) {
+                                  int64_t* bnd, TileRec* rec, float2* inv_len, double* m4buf, cudaStream_t st) {
     cudaError_t e = launch_part_index(geo, sv, bnd, rec, inv_len, 0, st);
     if (e != cudaSuccess) return e;
     const int64_t nvec = (int64_t)TILE_M * geo.tile_n / 4;
@@ -321,7 +366,7 @@ __global__ void timeout_selftest_kernel(int* status, uint64_t limit_ns) {
 }
 
 cudaError_t launch_reduce3(const Reduce3Params& p, int groups, int64_t max_len, int64_t* bnd, TileRec* rec,
-                           double* inv_len, float* wtab, cudaStream_t st) {
+                           float2* inv_len, float* wtab, cudaStream_t st) {
     cudaError_t e = launch_part_index(p.geom, p.ser, bnd, rec, inv_len, p.norm_len, st);
     if (e != cudaSuccess) return e;
     window_table_kernel<<<(unsigned)ceil_div(4 * p.geom.L, 256), 256, 0, st>>>(p.geom.L, p.window, wtab);
