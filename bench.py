@@ -137,14 +137,27 @@ def cpu_baseline(x, L, n, seconds_target=10.0):
     t0 = time.perf_counter()
     oracle.c3_rows(y, L, 0, rows - 1)
     dt = time.perf_counter() - t0
-    rows = max(2, min(2 * L + 1, int(rows * seconds_target / max(dt, 1e-3))))
+    rows = max(2, min(2 * L, int(rows * seconds_target / max(dt, 1e-3))))
     t0 = time.perf_counter()
-    oracle.c3_rows(y, L, -(rows // 2), -(rows // 2) + rows - 1)
+    ref = oracle.c3_rows(y, L, -(rows // 2), -(rows // 2) + rows - 1)
     dt = time.perf_counter() - t0
     terms = rows * (2 * L + 1) * n
     return {"value": terms / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
             "sample": f"c3 rows w1 in [{-(rows // 2)}, {-(rows // 2) + rows - 1}] x all {2 * L + 1} w2 x n={n} "
-                      f"({terms:.3e} lag terms, {dt:.1f} s)"}
+                      f"({terms:.3e} lag terms, {dt:.1f} s)"}, (-(rows // 2), ref)
+
+
+def accuracy(hos, torch, x, L, prec, lo, ref):
+    """Normwise error of the GPU's c3 (same input, same contraction precision)
+    over the oracle rows the CPU baseline computed: max |d| / max |ref|."""
+    import numpy as np
+    c3 = hos.cumulant3(torch.from_numpy(x).cuda(), L, precision=prec).cpu().numpy()
+    rows = ref.shape[0]
+    got = c3[lo + L:lo + L + rows, :2 * L]  # c3 is symmetric: row w1 + L holds c3(w1, w2), w2 + L
+    want = ref[:, :2 * L]
+    return {"vs": "FP64 oracle", "quantity": "c3 (unwindowed cumulant)", "max_rel_err":
+            float(np.abs(got - want).max() / np.abs(want).max()),
+            "sample": f"rows w1 in [{lo}, {lo + rows - 1}] x w2 in [{-L}, {L - 1}]"}
 
 
 def run_reference(args):
@@ -285,9 +298,19 @@ def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
         o_pin = torch.empty((N, N), dtype=torch.complex64).pin_memory()
         e2e = lambda: hos.bispectrum(x_pin, L, precision=prec, workspace=ws, out=o_pin)
         flops, work = c3_tc_flops(L, [x_host.size], products)
+        extra = {}
+        if name == "bispectrum_n2048_L32":  # small enough for the whole oracle spectrum
+
+            def acc():
+                import oracle
+                ref = oracle.bispectrum(x_host, L, N)
+                return {"vs": "FP64 oracle", "quantity": "B (whole grid)", "sample": "all of B",
+                        "max_rel_err": float(np.abs(out.cpu().numpy() - ref).max() / np.abs(ref).max())}
+
+            extra["accuracy"] = acc
         return dict(step=step, e2e=e2e, units=units_of(x_host.size, L), flops=flops, work=work,
                     h2d=x_host.nbytes, d2h=N * N * 8, config={"n": int(x_host.size), "L": L, "grid": N},
-                    bound="tensor" if products == 3 else "alu")
+                    bound="tensor" if products == 3 else "alu", **extra)
     if name == "trispectrum_n65536_L32":
         x_host = w["x"]
         xd = torch.from_numpy(x_host).cuda()
@@ -297,7 +320,15 @@ def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
         o_pin = torch.empty((N, N, N), dtype=torch.complex64).pin_memory()
         e2e = lambda: hos.trispectrum(x_pin, L, precision=prec, workspace=ws, out=o_pin)
         flops, work = m4_flops(L, x_host.size, prec)
-        return dict(step=step, e2e=e2e, units=units_of(x_host.size, L, k=4), flops=flops,
+
+        def acc():
+            import oracle
+            ref = oracle.trispectrum(x_host.astype(np.float64), L, N)
+            got = out.cpu().numpy()
+            return {"vs": "FP64 oracle", "quantity": "T (whole grid)",
+                    "max_rel_err": float(np.abs(got - ref).max() / np.abs(ref).max()), "sample": "all of T"}
+
+        return dict(step=step, e2e=e2e, accuracy=acc, units=units_of(x_host.size, L, k=4), flops=flops,
                     bound="tensor" if products == 3 else "alu", work=work,
                     h2d=x_host.nbytes, d2h=N ** 3 * 8, config={"n": int(x_host.size), "L": L, "grid": N})
     if name == "batched_4096x_L128":
@@ -317,7 +348,19 @@ def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
         e2e = lambda: hos.bispectrum_batched(v_pin, offs, L, precision=prec, workspace=ws, max_len=max_len,
                                              out=o_pin)
         flops, work = c3_tc_flops(L, lens, products)
-        return dict(step=step, e2e=e2e, units=int((lens * (2 * L + 1) ** 2).sum()), flops=flops, work=work,
+
+        def acc():
+            import oracle
+            got = out[:8].cpu().numpy()
+            err = 0.0
+            for k in range(min(8, S)):
+                ref = oracle.bispectrum(vals[offs[k]:offs[k + 1]], L, N)
+                err = max(err, float(np.abs(got[k] - ref).max() / np.abs(ref).max()))
+            return {"vs": "FP64 oracle", "quantity": "B per series (worst of the sample)", "max_rel_err": err,
+                    "sample": "series 0..7, whole grids"}
+
+        return dict(step=step, e2e=e2e, accuracy=acc, units=int((lens * (2 * L + 1) ** 2).sum()), flops=flops,
+                    work=work,
                     h2d=vals.nbytes + offs.nbytes, d2h=S * N * N * 8, bound="tensor" if products == 3 else "alu",
                     config={"series": S, "total_samples": int(lens.sum()), "L": L, "grid": N},
                     per_series=(vd, offs, L))
@@ -509,10 +552,13 @@ def run_ours(args):
         "wall_s_timed": t_wall,
     }
     line.update(extra)
+    if rank == 0 and not args.no_cpu_baseline and "accuracy" in wl:
+        line["accuracy"] = wl["accuracy"]()
     if rank == 0 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         import hos_synth
         x_host = hos_synth.workload(WORKLOAD)["x"]
-        line["cpu_baseline"] = cpu_baseline(x_host, 256, x_host.size)
+        line["cpu_baseline"], (lo, ref) = cpu_baseline(x_host, 256, x_host.size)
+        line["accuracy"] = accuracy(hos, torch, x_host, 256, prec, lo, ref)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()

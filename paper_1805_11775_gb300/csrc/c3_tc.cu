@@ -36,7 +36,7 @@ namespace hos {
 
 
 // ---- shared-memory plan ------------------------------------------------------
-constexpr int NSTAGE = 4;        // A stages in TMEM (64 columns each)
+constexpr int MAX_STAGE = 6;     // A stages in TMEM (64 columns each): 4, or 6 when the tile is <= 64 wide
 constexpr int WIN_SAMPLES = KC + 256 + 16;
 constexpr int WIN_BYTES = WIN_SAMPLES * 16;  // interleaved window, one plane
 constexpr int YA_FLOATS = KC + TILE_M;
@@ -50,7 +50,7 @@ struct __align__(16) C3Smem {
     float yi_raw[YI_FLOATS];          // staging: copied from an aligned global start
     uint8_t lin_hi[WIN_SAMPLES * 4];  // linear staging of the hi plane window
     uint8_t lin_lo[WIN_SAMPLES * 4];
-    uint64_t full_b[2], empty_b[2], full_a[NSTAGE], empty_a[NSTAGE];
+    uint64_t full_b[2], empty_b[2], full_a[MAX_STAGE], empty_a[MAX_STAGE];
     uint64_t acc_full[2], acc_empty[2], drain, tma_bar;
     uint32_t tmem_base;
     int abort;
@@ -91,23 +91,29 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
     constexpr uint32_t SBO = 16u * 8u;             // next 8 rows along N: +8 samples = 128 bytes
     const uint32_t idesc = make_idesc(TF32, TILE_M, N);
     const int csz = geo.kc;  // samples per chunk (the role loops below count chunks in kc)
-    // accumulators: two TMEM buffers (columns [0,128) and [128,256)) when the
-    // tile is at most 128 wide, so the epilogue drains one while the MMAs fill
-    // the other; one buffer of N columns otherwise
+    // TMEM columns: accumulators first -- two buffers when the tile is at most
+    // 128 wide (the epilogue drains one while the MMAs fill the other), one of
+    // N columns otherwise -- then the A stages, 64 columns each.  A tile at
+    // most 64 wide has 4x less MMA work per stage than a 256-wide one, so it
+    // takes 6 stages (two 64-column accumulators) to keep as much work queued.
     const uint32_t nacc = (N <= 128) ? 2u : 1u;
+    const uint32_t acc_cols = (N <= 64) ? 64u : 128u;  // column stride between accumulators
+    const uint32_t a_base = (N <= 64) ? 128u : 256u;   // first A stage column
+    const int nst = (N <= 64) ? 6 : 4;                 // A stages
 
     if (threadIdx.x == 0) {
+        // one elected arrival per arriving warp
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&sm.full_b[i], 32);
+            mbar_init(&sm.full_b[i], 1);
             mbar_init(&sm.empty_b[i], 1);
         }
-        for (int i = 0; i < NSTAGE; ++i) {
-            mbar_init(&sm.full_a[i], 128);
+        for (int i = 0; i < MAX_STAGE; ++i) {
+            mbar_init(&sm.full_a[i], 4);
             mbar_init(&sm.empty_a[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&sm.acc_full[i], 1);
-            mbar_init(&sm.acc_empty[i], 128);
+            mbar_init(&sm.acc_empty[i], 4);
         }
         mbar_init(&sm.drain, 1);
         mbar_init(&sm.tma_bar, 1);
@@ -197,8 +203,9 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                     *reinterpret_cast<uint4*>(sm.win_hi[buf] + (size_t)blk * 16) = vh;
                     *reinterpret_cast<uint4*>(sm.win_lo[buf] + (size_t)blk * 16) = vl;
                 }
-                fence_proxy_async_smem();
-                mbar_arrive(&sm.full_b[buf]);
+                fence_proxy_async_smem();  // every lane's window writes, for the MMA's reads
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.full_b[buf]);
             }
         }
     } else if (warp < 4) {
@@ -234,8 +241,8 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                 const float* ya = sm.ya[buf] + (ORDER == 3 ? m : 0);
                 const float* yi = sm.yi[buf];
                 for (int kb = 0; kb < csz / KB; ++kb, ++ks) {
-                    const int st = ks % NSTAGE;
-                    ok = warp_wait(&sm.empty_a[st], ((ks / NSTAGE) & 1) ^ 1, abort, P.status, lim, 1000);
+                    const int st = (int)(ks % (uint32_t)nst);
+                    ok = warp_wait(&sm.empty_a[st], ((ks / (uint32_t)nst) & 1) ^ 1, abort, P.status, lim, 1000);
                     if (!ok) break;
                     tc_fence_after();  // the MMAs that read this stage have completed
                     uint32_t H[32], Lw[32];
@@ -305,12 +312,13 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                                 pack_bf16x2(p2 - __uint_as_float(h1 << 16), p3 - __uint_as_float(h1 & 0xFFFF0000u));
                         }
                     }
-                    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + 256u + (uint32_t)st * 64u;
+                    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + a_base + (uint32_t)st * 64u;
                     tmem_st32(ta, H);
                     tmem_st32(ta + 32u, Lw);
                     tmem_wait_st();
                     tc_fence_before();
-                    mbar_arrive(&sm.full_a[st]);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sm.full_a[st]);
                 }
             }
         }
@@ -328,13 +336,14 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
             float* dst = P.partials + part.slot * (int64_t)(TILE_M * N) + m;
             for (int cc = 0; cc < N; cc += 32) {
                 uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + ab_ * 128u + (uint32_t)cc, v);
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + ab_ * acc_cols + (uint32_t)cc, v);
                 tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < 32; ++j) dst[(int64_t)(cc + j) * TILE_M] = __uint_as_float(v[j]);
             }
             tc_fence_before();
-            mbar_arrive(&sm.acc_empty[ab_]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.acc_empty[ab_]);
             ++it;
         }
     } else if (warp == 9 && lane == 0) {
@@ -344,7 +353,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
         const uint32_t wh0 = smem_u32(sm.win_hi[0]), wl0 = smem_u32(sm.win_lo[0]);
         while (ok && walk.next(part)) {
             const uint32_t ab_ = it % nacc;
-            const uint32_t dacc = tmem + ab_ * 128u;  // this part's accumulator
+            const uint32_t dacc = tmem + ab_ * acc_cols;  // this part's accumulator
             ok = mbar_wait(&sm.acc_empty[ab_], ((it / nacc) & 1) ^ 1, abort, P.status, lim);
             if (!ok) break;
             tc_fence_after();
@@ -355,19 +364,23 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t wh = wh0 + (uint32_t)buf * WIN_BYTES, wl = wl0 + (uint32_t)buf * WIN_BYTES;
+                // descriptors of the chunk's first K step; later steps add their byte
+                // offset / 16 to the start-address field (addresses stay below 256 KB,
+                // so the 14-bit field does not carry)
+                const uint64_t bh0 = make_sdesc(wh, LBO, SBO), bl0 = make_sdesc(wl, LBO, SBO);
                 for (int kb = 0; kb < csz / KB; ++kb, ++ks) {
-                    const int st = ks % NSTAGE;
-                    ok = mbar_wait(&sm.full_a[st], (ks / NSTAGE) & 1, abort, P.status, lim);
+                    const int st = (int)(ks % (uint32_t)nst);
+                    ok = mbar_wait(&sm.full_a[st], (ks / (uint32_t)nst) & 1, abort, P.status, lim);
                     if (!ok) break;
                     tc_fence_after();
 #pragma unroll
                     for (int k = 0; k < KB / KSTEP; ++k) {
-                        const uint32_t a_hi = tmem + 256u + (uint32_t)st * 64u + (uint32_t)k * 8u;
+                        const uint32_t a_hi = tmem + a_base + (uint32_t)st * 64u + (uint32_t)k * 8u;
                         const uint32_t a_lo = a_hi + 32u;
                         const uint32_t koff = (uint32_t)(kb * KB + k * KSTEP);  // samples into the chunk
-                        const uint32_t boff = (koff / R) * GROUP_BYTES;
-                        const uint64_t bh = make_sdesc(wh + boff, LBO, SBO);
-                        const uint64_t bl = make_sdesc(wl + boff, LBO, SBO);
+                        const uint64_t boff16 = (uint64_t)((koff / R) * GROUP_BYTES) >> 4;
+                        const uint64_t bh = bh0 + boff16;
+                        const uint64_t bl = bl0 + boff16;
                         mma_ts<TF32>(dacc, a_hi, bh, idesc, acc);
                         acc = 1;
                         mma_ts<TF32>(dacc, a_hi, bl, idesc, 1);
