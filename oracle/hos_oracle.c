@@ -1,7 +1,9 @@
 /*
  * hos_oracle.c -- plain FP64 CPU statement of the smoothed sample bispectrum
  * and trispectrum computed the indirect way (sample cumulant -> lag window ->
- * Fourier transform), and of the exact gradient of the bispectrum.
+ * Fourier transform), of the exact gradient of the bispectrum, and of the
+ * paper's direct method (Algorithm DBS: part DFTs, raw triple products, box
+ * smoothing, average over parts).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the library path may call, link or
  * load this file; only the tests, the package smoke check and the CPU-baseline
@@ -480,4 +482,78 @@ void hos_oracle_dy_at(const double* y, int64_t n, int64_t L, const double* dc, c
             }
         out[q] = acc / (double)n;
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* The direct method, Algorithm DBS steps 1-6, as the paper states it:
+ *   1. K = floor(n / M) parts of M samples (the trailing n - K M samples
+ *      are not used);
+ *   2. each part minus its own mean (when remove_mean);
+ *   3. F_i(k) = sum_u X_i(u) e^{-j 2 pi u k / M}, k = 0..M-1, summed directly;
+ *   4. raw C3_i(k1,k2) = (1/M) F_i(k1) F_i(k2) F_i*(k1+k2) -- reading: the
+ *      conjugate on the third factor (the product with F(k1+k2) itself is
+ *      not the bispectrum); indices mod M, F being M-periodic, so the raw
+ *      estimate is defined on the whole M x M grid;
+ *   5. M3 x M3 box smoothing, (1/M3^2) sum_{n1,n2 = lo}^{lo+M3-1}
+ *      C3_i(k1+n1, k2+n2), lo = -floor(M3/2) (the paper's -M3/2 .. M3/2-1
+ *      for even M3), indices mod M;
+ *   6. average over the K parts.
+ * Step 5 is the plain double sum per output point (the paper's "Naive"
+ * smoothing), not window sums.  out: M*M complex, row-major [k1][k2].       */
+void hos_oracle_bispectrum_direct(const double* x, int64_t n, int64_t M, int64_t M3, int remove_mean, double* out)
+{
+    const int64_t K = n / M;
+    const int64_t lo = -(M3 / 2);
+    double* y = (double*)malloc((size_t)M * sizeof(double));
+    double* F = (double*)malloc((size_t)M * 2 * sizeof(double));
+    double* raw = (double*)malloc((size_t)(M * M * 2) * sizeof(double));
+    memset(out, 0, (size_t)(M * M * 2) * sizeof(double));
+    for (int64_t part = 0; part < K; ++part) {
+        const double* xp = x + part * M;
+        double mean = 0.0;
+        if (remove_mean) {
+            for (int64_t u = 0; u < M; ++u) mean += xp[u];
+            mean /= (double)M;
+        }
+        for (int64_t u = 0; u < M; ++u) y[u] = xp[u] - mean;
+        for (int64_t k = 0; k < M; ++k) { /* step 3 */
+            double re = 0.0, im = 0.0;
+            for (int64_t u = 0; u < M; ++u) {
+                double c, s;
+                phase(u, k, M, -1.0, &c, &s);
+                re += y[u] * c;
+                im += y[u] * s;
+            }
+            F[2 * k] = re;
+            F[2 * k + 1] = im;
+        }
+        for (int64_t k1 = 0; k1 < M; ++k1) /* step 4 */
+            for (int64_t k2 = 0; k2 < M; ++k2) {
+                const int64_t k3 = (k1 + k2) % M;
+                const double ar = F[2 * k1], ai = F[2 * k1 + 1];
+                const double br = F[2 * k2], bi = F[2 * k2 + 1];
+                const double cr = F[2 * k3], ci = -F[2 * k3 + 1]; /* conjugate */
+                const double pr = ar * br - ai * bi, pi = ar * bi + ai * br;
+                raw[(k1 * M + k2) * 2] = (pr * cr - pi * ci) / (double)M;
+                raw[(k1 * M + k2) * 2 + 1] = (pr * ci + pi * cr) / (double)M;
+            }
+#pragma omp parallel for schedule(static)
+        for (int64_t k1 = 0; k1 < M; ++k1) /* step 5, accumulated into step 6 */
+            for (int64_t k2 = 0; k2 < M; ++k2) {
+                double sr = 0.0, si = 0.0;
+                for (int64_t n1 = lo; n1 < lo + M3; ++n1)
+                    for (int64_t n2 = lo; n2 < lo + M3; ++n2) {
+                        int64_t a = (k1 + n1) % M, b = (k2 + n2) % M;
+                        if (a < 0) a += M;
+                        if (b < 0) b += M;
+                        sr += raw[(a * M + b) * 2];
+                        si += raw[(a * M + b) * 2 + 1];
+                    }
+                out[(k1 * M + k2) * 2] += sr / (double)(M3 * M3) / (double)K;
+                out[(k1 * M + k2) * 2 + 1] += si / (double)(M3 * M3) / (double)K;
+            }
+    }
+    free(y);
+    free(F);
+    free(raw);
 }
