@@ -247,9 +247,27 @@ def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
     import numpy as np
 
     import hos_synth
+    ws = hos.Workspace()
+    if name == "direct_bispectrum_n8192_M3_279":
+        # the paper's direct method at its largest reported size: one part
+        # (K = 1, M = n = 8192), 279 x 279 box smoothing
+        M, M3 = 8192, 279
+        x_host = hos_synth.ar2(M, 1006)
+        xd = torch.from_numpy(x_host).cuda()
+        out = torch.empty((M, M), dtype=torch.complex64, device="cuda")
+        step = lambda: hos.bispectrum_direct(xd, M, M3, out=out, workspace=ws)
+        x_pin = torch.from_numpy(x_host).pin_memory()
+        o_pin = torch.empty((M, M), dtype=torch.complex64).pin_memory()
+        e2e = lambda: hos.bispectrum_direct(x_pin, M, M3, workspace=ws, out=o_pin)
+        # the smoothing stage streams the M x M grid five times (raw write and read, column sums
+        # write and read, result write), 8 bytes per complex64 point
+        grid_bytes = 5 * M * M * 8
+        return dict(step=step, e2e=e2e, units=1, metric="bispectra/s (direct method, n = M = 8192, box 279)",
+                    unit="bispectra/s", paper_value=1.0 / 1.751, flops=0, work=f"5 passes x {M}^2 x 8 B",
+                    roof={"bound": "hbm", "bytes": grid_bytes, "stage": "smooth"}, bound="hbm",
+                    h2d=x_host.nbytes, d2h=M * M * 8, config={"n": M, "M": M, "M3": M3, "parts": 1})
     w = hos_synth.workload(name)
     L, N = w["L"], w["N"]
-    ws = hos.Workspace()
     products = 3 if prec in ("bf16", "fp32") else 1
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if name == "long_bispectrum_n2M_L256" and (world > 1 or time_slices):
@@ -493,7 +511,13 @@ def run_ours(args):
     else:
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         peak_note = "FP32 FFMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
-    achieved = wl["flops"] / (contract_ms * 1e-3) / 1e12
+    roof_unit = "TFLOP/s"
+    if "roof" in wl:  # a memory-bound stage: algorithmic bytes over its time
+        stage_ms = statistics.mean(stage_acc.get(wl["roof"]["stage"], [float("nan")]))
+        achieved = wl["roof"]["bytes"] / (stage_ms * 1e-3) / 1e9
+        peak, peak_note, roof_unit = pk["hbm_gbs"], f"HBM copy, {src}", "GB/s"
+    else:
+        achieved = wl["flops"] / (contract_ms * 1e-3) / 1e12
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     per_clk = 8192 if prec == "bf16" else 4096
     clock_peak = nsm * per_clk * (clk["sm_mhz"] or 2070.0) * 1e6 / 1e12
@@ -522,19 +546,21 @@ def run_ours(args):
         extra["per_series_launches_ms"] = e0.elapsed_time(e1)
 
     units = wl["units"] * world
+    value = units / (ms * 1e-3)
     line = {
-        "metric": METRIC,
-        "value": units / (ms * 1e-3),
-        "unit": UNIT,
+        "metric": wl.get("metric", METRIC),
+        "value": value,
+        "unit": wl.get("unit", UNIT),
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": ms,
         "higher_is_better": True,
         "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": {"bf16": "bf16x3 (split-bf16, fp32 accumulate, fp64 reduce)",
-                  "fp32": "tf32x3 (fp32-class, fp32 accumulate, fp64 reduce)", "simt": "f32"}[prec],
+        "vs_baseline": value / wl["paper_value"] if "paper_value" in wl else None,
+        "dtype": "f32 (transform, products), double-float window sums" if "roof" in wl else
+                 {"bf16": "bf16x3 (split-bf16, fp32 accumulate, fp64-class reduce)",
+                  "fp32": "tf32x3 (fp32-class, fp32 accumulate, fp64-class reduce)", "simt": "f32"}[prec],
         "data": "synthetic",
         "config": dict({"workload": args.workload, "precision": prec, "contraction": hos.last_contraction(),
                         "l2": "flushed between timed steps (256 MB write)",
@@ -542,10 +568,10 @@ def run_ours(args):
                         "parallelism": "replicas" if world > 1 else "single"}, **wl["config"]),
         "stage_ms": {k: statistics.mean(v) for k, v in stage_acc.items()},
         "roofline": {"bound": wl["bound"], "kernel": hos.last_contraction(), "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "peak_source": peak_note,
+                     "unit": roof_unit, "frac": achieved / peak, "traffic": traffic, "peak_source": peak_note,
                      "frac_clock_matched": achieved / clock_peak if wl["bound"] == "tensor" else None,
                      "work": wl["work"]},
-        "e2e": {"value": wl["units"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(wl["h2d"]),
+        "e2e": {"value": wl["units"] / e2e_s, "unit": wl.get("unit", UNIT), "h2d_bytes_per_step": int(wl["h2d"]),
                 "d2h_bytes_per_step": int(wl["d2h"])},
         "gpu_launches": launches,
         "clocks": clk,
@@ -577,7 +603,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "bispectrum_n2048_L32", "trispectrum_n65536_L32", "batched_4096x_L128",
-                             "differentiable_n262144_L128"])
+                             "differentiable_n262144_L128", "direct_bispectrum_n8192_M3_279"])
     ap.add_argument("--graph", action="store_true", help="capture one step in a CUDA graph and replay it")
     ap.add_argument("--series", type=int, default=0, help="batched workload: use only the first K series")
     ap.add_argument("--time-slices", action="store_true",

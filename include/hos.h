@@ -207,6 +207,26 @@ hos_status hos_cumulant3_slice(const void* d_x, int32_t dtype, int64_t n_slice, 
 hos_status hos_bispectrum_from_cumulant(const double* d_c3, const hos_params* params, void* d_B, void* ws,
                                         size_t ws_bytes, hos_stream_t stream);
 
+/* ---- The paper's direct method (Algorithm DBS) ------------------------------
+ * Steps: 1-2. K = floor(n / M) parts of M samples (the trailing n - K M
+ * samples are not used), each minus its own mean (FP64) when remove_mean;
+ * 3. F_p(k) = sum_u X_p(u) e^{-j 2 pi u k / M}; 4. raw (1/M) F_p(k1) F_p(k2)
+ * F_p*(k1+k2) (reading: the third factor conjugated), indices mod M, on the
+ * whole M x M grid; 5. M3 x M3 box average over offsets lo .. lo + M3 - 1,
+ * lo = -floor(M3/2) (the paper's -M3/2 .. M3/2 - 1 for even M3), indices mod
+ * M, computed by window sums (Algorithms WS / WS_PRAM); 6. average over the
+ * parts (done before step 5: both are linear).  No (2 pi) normalisation.
+ *   M    : part length and transform size: a power of two up to 8192, or any
+ *          value 2..2048; M + M3 - 1 <= 14848
+ *   M3   : side of the smoothing box, 1 <= M3 <= M (1: no smoothing)
+ *   d_B  : M * M complex64, row-major [k1][k2]; the principal domain
+ *          0 <= k2 <= k1, k1 + k2 < M/2 is the part the paper keeps
+ * The transform is FP32; the running window sums are double-float.
+ * Workspace: hos_bispectrum_direct_workspace_size.                          */
+hos_status hos_bispectrum_direct_workspace_size(int64_t n, int32_t M, int32_t M3, size_t* bytes);
+hos_status hos_bispectrum_direct(const void* d_x, int32_t dtype, int64_t n, int32_t M, int32_t M3,
+                                 int32_t remove_mean, void* d_B, void* ws, size_t ws_bytes, hos_stream_t stream);
+
 /* Bispectrum without a caller-supplied workspace, for callers that cannot
  * allocate device memory (no allocator at hand, or a context where calling
  * cudaMalloc is not allowed, such as a host callback or a plug-in whose host

@@ -302,6 +302,24 @@ def bispectrum_sharded(x_local, L, halo_before, halo_after, n_total, nfft=0, pre
     return bispectrum_from_cumulant(c3, L, nfft, window, workspace=workspace)
 
 
+def bispectrum_direct(x, M, M3, remove_mean=True, out=None, workspace=None, stream=None):
+    """The paper's direct method (Algorithm DBS): parts of M samples, raw
+    (1/M) F(k1) F(k2) F*(k1+k2), M3 x M3 box smoothing by window sums, average
+    over parts.  (M, M) complex64 over the whole grid, [k1][k2]."""
+    xd, host = _prepare(x)
+    dev, host_out = _out_buffers(out, (int(M), int(M)), xd.device)
+    nbytes = ctypes.c_size_t(0)
+    _native.check(_native.lib().hos_bispectrum_direct_workspace_size(xd.numel(), int(M), int(M3),
+                                                                       ctypes.byref(nbytes)),
+                  "hos_bispectrum_direct_workspace_size")
+    ws = _workspace(workspace, xd.device)
+    ws.get(nbytes.value)
+    _native.check(_native.lib().hos_bispectrum_direct(xd.data_ptr(), _dtype_code(xd), xd.numel(), int(M), int(M3),
+                                                      int(bool(remove_mean)), dev.data_ptr(), ws.ptr(), ws.nbytes(),
+                                                      _stream(stream)), "hos_bispectrum_direct")
+    return _finish(dev, host_out, host)
+
+
 def bispectrum_backward(x, dB, L, nfft=0, precision="bf16", window="parzen", remove_mean=True, workspace=None,
                         stream=None):
     """dl/dx given dB = dl/dRe B + i dl/dIm B."""

@@ -52,6 +52,10 @@ _SIGS = {
     "hos_cumulant3_slice": [_VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_int64,
                             _P, _VP, _VP, ctypes.c_size_t, _VP],
     "hos_bispectrum_from_cumulant": [_VP, _P, _VP, _VP, ctypes.c_size_t, _VP],
+    "hos_bispectrum_direct_workspace_size": [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_size_t)],
+    "hos_bispectrum_direct": [_VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                              _VP, _VP, ctypes.c_size_t, _VP],
     "hos_get_device_status": [_VP, ctypes.POINTER(ctypes.c_int32)],
     "hos_reset_device_status": [_VP, _VP],
     "hos_selftest_timeout": [_VP, ctypes.c_size_t, ctypes.c_int32, _VP],

@@ -716,6 +716,77 @@ hos_status hos_bispectrum_from_cumulant(const double* d_c3, const hos_params* p,
     return s;
 }
 
+// ---- the direct method (Algorithm DBS) ----------------------------------------------
+struct DirectLayout {
+    int64_t K;
+    int nslices;
+    size_t off, mean, mpart, y, F, tw, R, Cw, total;
+};
+
+static hos_status direct_layout(int64_t n, int32_t M, int32_t M3, DirectLayout& l) {
+    if (n < 1 || M < 2 || M3 < 1 || M3 > M) return HOS_ERR_INVALID_ARG;
+    const bool pow2 = (M & (M - 1)) == 0;
+    if ((pow2 && M > 8192) || (!pow2 && M > 2048)) return HOS_ERR_UNSUPPORTED;
+    if ((size_t)(M + M3 - 1) * 16 > 227 * 1024) return HOS_ERR_UNSUPPORTED;  // a row and its wrap in shared memory
+    l.K = n / M;
+    if (l.K < 1) return HOS_ERR_INVALID_ARG;
+    if (l.K > (1 << 24)) return HOS_ERR_UNSUPPORTED;
+    int64_t ns = ceil_div(M, 8192);
+    l.nslices = (int)(ns < 1 ? 1 : ns);
+    const size_t MM = (size_t)M * M;
+    size_t o = 0;
+    l.off = o; o = al256(o + 8 * (size_t)(l.K + 1));
+    l.mean = o; o = al256(o + 8 * (size_t)l.K);
+    l.mpart = o; o = al256(o + 8 * (size_t)l.K * l.nslices);
+    l.y = o; o = al256(o + 4 * (size_t)l.K * M);
+    l.F = o; o = al256(o + 8 * (size_t)l.K * M);
+    l.tw = o; o = al256(o + 8 * (size_t)M);
+    l.R = o; o = al256(o + 8 * MM);
+    l.Cw = o; o = al256(o + 8 * MM);
+    l.total = o;
+    return HOS_OK;
+}
+
+hos_status hos_bispectrum_direct_workspace_size(int64_t n, int32_t M, int32_t M3, size_t* bytes) {
+    if (!bytes) return HOS_ERR_INVALID_ARG;
+    DirectLayout l;
+    hos_status s = direct_layout(n, M, M3, l);
+    if (s != HOS_OK) return s;
+    *bytes = l.total;
+    return HOS_OK;
+}
+
+hos_status hos_bispectrum_direct(const void* d_x, int32_t dtype, int64_t n, int32_t M, int32_t M3,
+                                 int32_t remove_mean, void* d_B, void* ws, size_t ws_bytes, hos_stream_t stream) {
+    if (!d_x || !d_B || (dtype != HOS_F32 && dtype != HOS_F64)) return HOS_ERR_INVALID_ARG;
+    DirectLayout l;
+    hos_status s = direct_layout(n, M, M3, l);
+    if (s != HOS_OK) return s;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < l.total) return HOS_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Tracer tr(st);
+    tr.mark("prep");
+    int64_t* off = at<int64_t>(ws, l.off);
+    double* mean = at<double>(ws, l.mean);
+    float* y = at<float>(ws, l.y);
+    float2* F = at<float2>(ws, l.F);
+    float2* tw = at<float2>(ws, l.tw);
+    HOS_CUDA_TRY(launch_part_offsets(l.K, M, off, st));
+    HOS_CUDA_TRY(launch_mean(d_x, dtype, off, (int)l.K, l.nslices, at<double>(ws, l.mpart), remove_mean ? 1 : 0, mean,
+                             st));
+    HOS_CUDA_TRY(launch_demean_parts(d_x, dtype, l.K * M, M, mean, y, st));
+    tr.mark("transform");
+    HOS_CUDA_TRY(launch_twiddles(M, tw, st));
+    LineGeom g = line_geom(M, l.K, 1, M, 1);
+    HOS_CUDA_TRY(launch_lines(true, y, F, g, tw, -1, 1.0f, st));
+    tr.mark("smooth");
+    HOS_CUDA_TRY(launch_direct_smooth(F, (int)l.K, M, M3, at<float2>(ws, l.R), at<float2>(ws, l.Cw),
+                                      reinterpret_cast<float2*>(d_B), st));
+    tr.mark("");
+    g_last_contraction = "direct_triple_product";
+    return HOS_OK;
+}
+
 hos_status hos_bispectrum(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, void* d_B, void* ws,
                           size_t ws_bytes, hos_stream_t stream) {
     if (!d_x || !d_B || n < 1 || (dtype != HOS_F32 && dtype != HOS_F64)) return HOS_ERR_INVALID_ARG;

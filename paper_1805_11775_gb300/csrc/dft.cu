@@ -142,6 +142,40 @@ HOS_DEV void radix_pass(float2 (&v)[8], int s0, int lg, int t, int T, const floa
     }
 }
 
+// The first pass (stages 0-2, span 1): twiddles W_2^0, W_4^j, W_8^j only, so
+// they are constants -- 1, -/+i and (+/-1 -/+ i)/sqrt 2 -- and no table loads
+// or general complex products are needed.  sg = -1 forward, +1 adjoint.
+HOS_DEV void radix8_first(float2 (&v)[8], float sg) {
+    const float r = 0.70710678118654752f;  // 1/sqrt(2)
+#pragma unroll
+    for (int m = 0; m < 8; m += 2) {  // stage 0
+        const float2 a = v[m], b = v[m + 1];
+        v[m] = make_float2(a.x + b.x, a.y + b.y);
+        v[m + 1] = make_float2(a.x - b.x, a.y - b.y);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; q += 4) {  // stage 1: w = 1 (m = q), W_4^1 = (0, sg) (m = q + 1)
+        const float2 a0 = v[q], b0 = v[q + 2];
+        v[q] = make_float2(a0.x + b0.x, a0.y + b0.y);
+        v[q + 2] = make_float2(a0.x - b0.x, a0.y - b0.y);
+        const float2 a1 = v[q + 1], c = v[q + 3];
+        const float2 b1 = make_float2(-sg * c.y, sg * c.x);
+        v[q + 1] = make_float2(a1.x + b1.x, a1.y + b1.y);
+        v[q + 3] = make_float2(a1.x - b1.x, a1.y - b1.y);
+    }
+    float2 b[4];  // stage 2: w = W_8^m, m = 0..3
+    b[0] = v[4];
+    b[1] = make_float2(r * (v[5].x - sg * v[5].y), r * (sg * v[5].x + v[5].y));
+    b[2] = make_float2(-sg * v[6].y, sg * v[6].x);
+    b[3] = make_float2(r * (-v[7].x - sg * v[7].y), r * (sg * v[7].x - v[7].y));
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const float2 a = v[m];
+        v[m] = make_float2(a.x + b[m].x, a.y + b[m].y);
+        v[m + 4] = make_float2(a.x - b[m].x, a.y - b[m].y);
+    }
+}
+
 template <int R>
 HOS_DEV void pass_store(const float2 (&v)[8], float2* row, int s0, int t, int T) {
 #pragma unroll
@@ -159,7 +193,7 @@ HOS_DEV void pass_load(float2 (&v)[8], const float2* row, int s0, int t, int T) 
 }
 
 template <bool REAL_IN, bool STRIDED>
-__global__ void __launch_bounds__(512) fft_r8_kernel(const void* in, float2* out, const LineGeom g,
+__global__ void __launch_bounds__(1024) fft_r8_kernel(const void* in, float2* out, const LineGeom g,
                                                      const float2* __restrict__ tw, int sign, float scale) {
     extern __shared__ float2 sbuf[];
     const int N = g.N, lg = g.log2N, lpb = g.lpb, SL = skewed_len(N), T = N >> 3;
@@ -186,7 +220,7 @@ __global__ void __launch_bounds__(512) fft_r8_kernel(const void* in, float2* out
 #pragma unroll
         for (int m = 0; m < 8; ++m) v[m] = load_in<REAL_IN>(in, base + (int64_t)bitrev_n(8 * t + m, lg) * es);
     }
-    radix_pass<3>(v, 0, lg, t, T, tws);
+    radix8_first(v, sign > 0 ? 1.0f : -1.0f);
     int s0 = 3;
     while (s0 < lg) {
         const int r = (lg - s0) < 3 ? (lg - s0) : 3;
@@ -240,6 +274,71 @@ __global__ void __launch_bounds__(512) fft_r8_kernel(const void* in, float2* out
     }
 }
 
+// Two real contiguous lines a, b per complex transform: z = a + i b, Z =
+// FFT(z), then A[k] = (Z[k] + conj Z[N-k]) / 2 and B[k] = (Z[k] - conj
+// Z[N-k]) / (2i) (the transforms of real lines are Hermitian), which halves
+// the butterfly work of a real-input pass.  Same passes as fft_r8_kernel;
+// the last one leaves Z in shared memory in natural order for the split.
+// lpb (real lines per CTA) is even, and so is the line count.
+__global__ void __launch_bounds__(1024) fft_r8_pair_kernel(const float* __restrict__ in, float2* __restrict__ out,
+                                                          const LineGeom g, const float2* __restrict__ tw, int sign,
+                                                          float scale) {
+    extern __shared__ float2 sbuf[];
+    const int N = g.N, lg = g.log2N, lpb = g.lpb, SL = skewed_len(N), T = N >> 3;
+    float2* tws = sbuf + (size_t)(lpb >> 1) * SL;
+    int64_t* lbase = reinterpret_cast<int64_t*>(tws + (N >> 1));
+    const int64_t l0 = (int64_t)blockIdx.x * lpb;
+    const int nl = (int)((g.nlines - l0) < lpb ? (g.nlines - l0) : lpb);
+    for (int k = threadIdx.x; k < (N >> 1); k += blockDim.x) {
+        float2 w = tw[k];
+        if (sign > 0) w.y = -w.y;
+        tws[k] = w;
+    }
+    for (int l = threadIdx.x; l < nl; l += blockDim.x) lbase[l] = line_base(g, l0 + l);
+    __syncthreads();
+    const int pl = (int)(threadIdx.x / T), t = (int)(threadIdx.x % T);
+    const bool live = 2 * pl < nl;
+    const int64_t ba = live ? lbase[2 * pl] : 0, bb = live ? lbase[2 * pl + 1] : 0;
+    float2* row = sbuf + (size_t)pl * SL;
+    float2 v[8];
+    if (live) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int e = bitrev_n(8 * t + m, lg);
+            v[m] = make_float2(in[ba + e], in[bb + e]);
+        }
+    }
+    radix8_first(v, sign > 0 ? 1.0f : -1.0f);
+    int s0 = 3, slast = 0, rlast = 3;
+    while (s0 < lg) {
+        const int r = (lg - s0) < 3 ? (lg - s0) : 3;
+        __syncthreads();
+        if (live) pass_store<3>(v, row, s0 - 3, t, T);
+        __syncthreads();
+        if (r == 3) { if (live) pass_load<3>(v, row, s0, t, T); radix_pass<3>(v, s0, lg, t, T, tws); }
+        else if (r == 2) { if (live) pass_load<2>(v, row, s0, t, T); radix_pass<2>(v, s0, lg, t, T, tws); }
+        else { if (live) pass_load<1>(v, row, s0, t, T); radix_pass<1>(v, s0, lg, t, T, tws); }
+        slast = s0;
+        rlast = r;
+        if (s0 + r >= lg) break;
+        s0 += 3;
+    }
+    __syncthreads();  // the last pass's reads of the rows are done
+    if (live) {
+        if (rlast == 3) pass_store<3>(v, row, slast, t, T);
+        else if (rlast == 2) pass_store<2>(v, row, slast, t, T);
+        else pass_store<1>(v, row, slast, t, T);
+    }
+    __syncthreads();
+    if (!live) return;
+    const float h = 0.5f * scale;
+    for (int k = t; k < N; k += T) {
+        const float2 zk = row[sk(k)], zn = row[sk((N - k) & (N - 1))];
+        out[ba + k] = make_float2((zk.x + zn.x) * h, (zk.y - zn.y) * h);
+        out[bb + k] = make_float2((zk.y + zn.y) * h, (zn.x - zk.x) * h);
+    }
+}
+
 template <bool REAL_IN>
 __global__ void dft_lines_kernel(const void* in, float2* out, const LineGeom g, const float2* __restrict__ tw,
                                  int sign, float scale) {
@@ -286,8 +385,24 @@ cudaError_t launch_lines(bool real_in, const void* in, float2* out, LineGeom g, 
                          float scale, cudaStream_t st) {
     if (g.nlines <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)ceil_div(g.nlines, g.lpb);
-    if (g.log2N >= 3) {
-        // radix-8 register passes: N/8 threads per line, <= 512 threads per CTA
+    if (g.log2N >= 3 && real_in && g.elem_stride == 1 && g.nlines % 2 == 0) {
+        // real contiguous lines in pairs, one complex transform per pair
+        const int T = g.N >> 3;
+        int pairs = 256 / T;
+        if (pairs > 32) pairs = 32;
+        if (pairs < 1) pairs = 1;
+        int lpb = 2 * pairs;
+        if (lpb > g.nlines) lpb = (int)g.nlines;
+        g.lpb = lpb;
+        const unsigned nb = (unsigned)ceil_div(g.nlines, lpb);
+        const size_t smem = (size_t)(lpb / 2) * skewed_len(g.N) * sizeof(float2) +
+                            (size_t)(g.N >> 1) * sizeof(float2) + (size_t)lpb * sizeof(int64_t);
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(fft_r8_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fft_r8_pair_kernel<<<nb, (unsigned)((lpb / 2) * T), smem, st>>>(reinterpret_cast<const float*>(in), out, g,
+                                                                       tw, sign, scale);
+    } else if (g.log2N >= 3) {
+        // radix-8 register passes: N/8 threads per line (up to 1024 at N = 8192)
         const int T = g.N >> 3;
         const bool strided = g.elem_stride != 1;
         int lpb = strided ? 512 / T : 256 / T;

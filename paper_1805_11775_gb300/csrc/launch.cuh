@@ -90,6 +90,12 @@ cudaError_t launch_window_c3(const double* c3, int L, int window, int Nf, double
                              cudaStream_t st);
 cudaError_t launch_series_sum(const void* x, int dtype, int64_t n, int nslices, int64_t* off, double* part,
                               double* sum, cudaStream_t st);
+// direct method (direct.cu)
+cudaError_t launch_part_offsets(int64_t K, int64_t M, int64_t* off, cudaStream_t st);
+cudaError_t launch_demean_parts(const void* x, int dtype, int64_t total, int64_t M, const double* mean, float* y,
+                                cudaStream_t st);
+cudaError_t launch_direct_smooth(const float2* F, int K, int M, int M3, float2* R, float2* Cw, float2* B,
+                                 cudaStream_t st);
 cudaError_t launch_slice_mean(const double* sum, int64_t n_total, int remove_mean, double* mean, cudaStream_t st);
 cudaError_t launch_c3_tc(bool tf32, int order, const C3TcParams& p, int G, cudaStream_t st);
 cudaError_t launch_c3_simt(const C3SimtParams& p, int G, cudaStream_t st);

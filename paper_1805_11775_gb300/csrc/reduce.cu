@@ -103,7 +103,14 @@ HOS_DEV void tile_share4(const float* __restrict__ partials, const TileRec& r, i
     const float4* p4 = reinterpret_cast<const float4*>(partials + r.slot * (int64_t)tsz) + vi;
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[c] = df_zero();
-    for (int f0 = 16 * gi; f0 < r.nwin; f0 += 16 * gsplit) {
+    if (r.nwin == 1 && gi == 0) {  // one window (short series): the group sum is the value itself
+        const float4 x = p4[0];
+        acc[0] = DF{x.x, 0.0f};
+        acc[1] = DF{x.y, 0.0f};
+        acc[2] = DF{x.z, 0.0f};
+        acc[3] = DF{x.w, 0.0f};
+    }
+    for (int f0 = 16 * gi; f0 < r.nwin && r.nwin > 1; f0 += 16 * gsplit) {
         const int cnt = (r.nwin - f0 < 16) ? r.nwin - f0 : 16;
         float hi[4] = {0.0f, 0.0f, 0.0f, 0.0f}, lo[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int f = 0; f < cnt; f += 8) {
