@@ -69,7 +69,7 @@ def _load():
             lib.hos_oracle_bispectrum_grad.argtypes = [_D, _I64, _I64, _I64, ctypes.c_int, ctypes.c_int, _D, _D]
             lib.hos_oracle_grad_lag.argtypes = [_D, _I64, _I64, ctypes.c_int, _D]
             lib.hos_oracle_dy_at.argtypes = [_D, _I64, _I64, _D, ctypes.POINTER(_I64), _I64, _D]
-            lib.hos_oracle_bispectrum_direct.argtypes = [_D, _I64, _I64, _I64, ctypes.c_int, _D]
+            lib.hos_oracle_bispectrum_direct.argtypes = [_D, _I64, _I64, _I64, _I64, ctypes.c_int, _D]
             _lib = lib
     return _lib
 
@@ -220,12 +220,14 @@ def dy_at(y, L: int, dc, js) -> np.ndarray:
     return out
 
 
-def bispectrum_direct(x, M: int, M3: int, remove_mean: bool = True) -> np.ndarray:
-    """Algorithm DBS: parts of M samples, raw (1/M) F(k1)F(k2)F*(k1+k2), M3 x M3
-    box smoothing (indices mod M), average over parts.  (M, M) complex, [k1][k2]."""
+def bispectrum_direct(x, M: int, M3: int, remove_mean: bool = True, overlap: int = 0) -> np.ndarray:
+    """Algorithm DBS: parts of M samples (every M - overlap samples), raw (1/M)
+    F(k1)F(k2)F*(k1+k2), M3 x M3 box smoothing (indices mod M), average over
+    parts.  (M, M) complex, [k1][k2]."""
     x = _f64(x)
     out = np.empty(M * M * 2)
-    _load().hos_oracle_bispectrum_direct(_p(x), x.size, int(M), int(M3), int(bool(remove_mean)), _p(out))
+    _load().hos_oracle_bispectrum_direct(_p(x), x.size, int(M), int(M3), int(overlap), int(bool(remove_mean)),
+                                         _p(out))
     return _complex(out, (M, M))
 
 

@@ -486,8 +486,9 @@ void hos_oracle_dy_at(const double* y, int64_t n, int64_t L, const double* dc, c
 
 /* ------------------------------------------------------------------ */
 /* The direct method, Algorithm DBS steps 1-6, as the paper states it:
- *   1. K = floor(n / M) parts of M samples (the trailing n - K M samples
- *      are not used);
+ *   1. parts of M samples starting every M - overlap samples (overlap = 0:
+ *      the paper's partition, K = floor(n / M)); K = floor((n - M) /
+ *      (M - overlap)) + 1, trailing samples past the last part not used;
  *   2. each part minus its own mean (when remove_mean);
  *   3. F_i(k) = sum_u X_i(u) e^{-j 2 pi u k / M}, k = 0..M-1, summed directly;
  *   4. raw C3_i(k1,k2) = (1/M) F_i(k1) F_i(k2) F_i*(k1+k2) -- reading: the
@@ -500,16 +501,18 @@ void hos_oracle_dy_at(const double* y, int64_t n, int64_t L, const double* dc, c
  *   6. average over the K parts.
  * Step 5 is the plain double sum per output point (the paper's "Naive"
  * smoothing), not window sums.  out: M*M complex, row-major [k1][k2].       */
-void hos_oracle_bispectrum_direct(const double* x, int64_t n, int64_t M, int64_t M3, int remove_mean, double* out)
+void hos_oracle_bispectrum_direct(const double* x, int64_t n, int64_t M, int64_t M3, int64_t overlap,
+                                  int remove_mean, double* out)
 {
-    const int64_t K = n / M;
+    const int64_t step = M - overlap;
+    const int64_t K = n >= M ? (n - M) / step + 1 : 0;
     const int64_t lo = -(M3 / 2);
     double* y = (double*)malloc((size_t)M * sizeof(double));
     double* F = (double*)malloc((size_t)M * 2 * sizeof(double));
     double* raw = (double*)malloc((size_t)(M * M * 2) * sizeof(double));
     memset(out, 0, (size_t)(M * M * 2) * sizeof(double));
     for (int64_t part = 0; part < K; ++part) {
-        const double* xp = x + part * M;
+        const double* xp = x + part * step;
         double mean = 0.0;
         if (remove_mean) {
             for (int64_t u = 0; u < M; ++u) mean += xp[u];

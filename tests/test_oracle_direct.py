@@ -7,13 +7,16 @@ import pytest
 import hos_synth
 
 
-def numpy_raw(x, M, remove_mean=True):
-    """Average over parts of (1/M) F(k1) F(k2) conj F(k1 + k2), F = numpy FFT."""
-    K = x.size // M
+def numpy_raw(x, M, remove_mean=True, overlap=0):
+    """Average over parts of (1/M) F(k1) F(k2) conj F(k1 + k2), F = numpy FFT;
+    parts of M samples every M - overlap samples."""
+    step = M - overlap
+    starts = list(range(0, x.size - M + 1, step))
+    K = len(starts)
     k = np.arange(M)
     acc = np.zeros((M, M), complex)
-    for p in range(K):
-        y = x[p * M:(p + 1) * M].astype(np.float64)
+    for a in starts:
+        y = x[a:a + M].astype(np.float64)
         if remove_mean:
             y = y - y.mean()
         F = np.fft.fft(y)
@@ -37,6 +40,16 @@ def test_unsmoothed_direct_estimate_is_the_fft_triple_product(oracle, M, K, rm):
     x = hos_synth.ar2(M * K + 7, 3 + M)  # the 7 trailing samples are not used
     got = oracle.bispectrum_direct(x, M, 1, remove_mean=rm)
     ref = numpy_raw(x, M, rm)
+    assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("M,overlap,n", [(32, 16, 200), (40, 10, 131), (16, 15, 40), (64, 0, 64)])
+def test_overlapping_parts(oracle, M, overlap, n):
+    """Parts every M - overlap samples (the trailing samples past the last
+    whole part unused)."""
+    x = hos_synth.ar2(n, 5 + overlap)
+    got = oracle.bispectrum_direct(x, M, 3, overlap=overlap)
+    ref = roll_smooth(numpy_raw(x, M, overlap=overlap), 3)
     assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
 
 
