@@ -91,7 +91,8 @@ typedef enum {
     HOS_OP_CUMULANT4 = 5,
     HOS_OP_SERIES_SUM = 6,
     HOS_OP_CUMULANT3_SLICE = 7,
-    HOS_OP_BISPECTRUM_FROM_C3 = 8
+    HOS_OP_BISPECTRUM_FROM_C3 = 8,
+    HOS_OP_TRISPECTRUM_BATCHED = 9
 } hos_op;
 
 typedef struct {
@@ -141,6 +142,16 @@ hos_status hos_trispectrum(const void* d_x, int32_t dtype, int64_t n, const hos_
 hos_status hos_bispectrum_batched(const void* d_x, int32_t dtype, const int64_t* d_offsets, int32_t S,
                                   int64_t n_total, int64_t max_len, const hos_params* params, void* d_B, void* ws,
                                   size_t ws_bytes, hos_stream_t stream);
+
+/* Trispectra of S independent series of uneven length in one pass (the
+ * fourth-order counterpart of hos_bispectrum_batched; tensor-core precisions
+ * only, SIMT_FP32 returns HOS_ERR_UNSUPPORTED).
+ *   d_offsets, max_len : as hos_bispectrum_batched
+ *   d_T       : S * nfft^3 complex64, series-major, each [k1][k2][k3]
+ * A series of length 0 yields T = 0.  segment_len must be 0.              */
+hos_status hos_trispectrum_batched(const void* d_x, int32_t dtype, const int64_t* d_offsets, int32_t S,
+                                   int64_t n_total, int64_t max_len, const hos_params* params, void* d_T, void* ws,
+                                   size_t ws_bytes, hos_stream_t stream);
 
 /* Adjoint of hos_bispectrum (one part only, segment_len = 0): the gradient of a
  * real loss l through B.
@@ -208,8 +219,10 @@ hos_status hos_bispectrum_from_cumulant(const double* d_c3, const hos_params* pa
                                         size_t ws_bytes, hos_stream_t stream);
 
 /* ---- The paper's direct method (Algorithm DBS) ------------------------------
- * Steps: 1-2. K = floor(n / M) parts of M samples (the trailing n - K M
- * samples are not used), each minus its own mean (FP64) when remove_mean;
+ * Steps: 1-2. parts of M samples starting every M - overlap samples (overlap
+ * 0: the paper's partition into K = floor(n / M) parts; otherwise K =
+ * floor((n - M) / (M - overlap)) + 1; samples past the last whole part are
+ * not used), each minus its own mean (FP64) when remove_mean;
  * 3. F_p(k) = sum_u X_p(u) e^{-j 2 pi u k / M}; 4. raw (1/M) F_p(k1) F_p(k2)
  * F_p*(k1+k2) (reading: the third factor conjugated), indices mod M, on the
  * whole M x M grid; 5. M3 x M3 box average over offsets lo .. lo + M3 - 1,
@@ -217,14 +230,15 @@ hos_status hos_bispectrum_from_cumulant(const double* d_c3, const hos_params* pa
  * M, computed by window sums (Algorithms WS / WS_PRAM); 6. average over the
  * parts (done before step 5: both are linear).  No (2 pi) normalisation.
  *   M    : part length and transform size: a power of two up to 8192, or any
- *          value 2..2048; M + M3 - 1 <= 14848
+ *          value 2..2048; M + M3 - 1 <= 13504
  *   M3   : side of the smoothing box, 1 <= M3 <= M (1: no smoothing)
+ *   overlap : samples shared by consecutive parts, 0 <= overlap < M
  *   d_B  : M * M complex64, row-major [k1][k2]; the principal domain
  *          0 <= k2 <= k1, k1 + k2 < M/2 is the part the paper keeps
  * The transform is FP32; the running window sums are double-float.
  * Workspace: hos_bispectrum_direct_workspace_size.                          */
-hos_status hos_bispectrum_direct_workspace_size(int64_t n, int32_t M, int32_t M3, size_t* bytes);
-hos_status hos_bispectrum_direct(const void* d_x, int32_t dtype, int64_t n, int32_t M, int32_t M3,
+hos_status hos_bispectrum_direct_workspace_size(int64_t n, int32_t M, int32_t M3, int32_t overlap, size_t* bytes);
+hos_status hos_bispectrum_direct(const void* d_x, int32_t dtype, int64_t n, int32_t M, int32_t M3, int32_t overlap,
                                  int32_t remove_mean, void* d_B, void* ws, size_t ws_bytes, hos_stream_t stream);
 
 /* Bispectrum without a caller-supplied workspace, for callers that cannot

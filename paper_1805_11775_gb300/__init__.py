@@ -214,6 +214,29 @@ def trispectrum(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=Tru
     return _finish(dev, host_out, host)
 
 
+def trispectrum_batched(values, offsets, L, nfft=0, precision="bf16", window="parzen", remove_mean=True,
+                        flush_chunks=0, out=None, workspace=None, stream=None, max_len=None):
+    """Trispectra of S series concatenated in ``values`` with ``offsets`` (S+1):
+    (S, nfft, nfft, nfft) complex64.  Tensor-core precisions ("bf16", "fp32")."""
+    torch = _torch()
+    vd, host = _prepare(values)
+    offs = torch.as_tensor(offsets, dtype=torch.int64)
+    if max_len is None:
+        oh = offs.cpu() if offs.device.type == "cuda" else offs
+        max_len = int((oh[1:] - oh[:-1]).max().item()) if oh.numel() > 1 else 0
+    od = offs.to(vd.device, non_blocking=True).contiguous()
+    S = od.numel() - 1
+    p = make_params(L, nfft, precision, window, remove_mean, 0, 0, flush_chunks)
+    N = p.nfft or 2 * p.L
+    dev, host_out = _out_buffers(out, (S, N, N, N), vd.device)
+    ws = _workspace(workspace, vd.device)
+    ws.get(workspace_size(_native.OP_TRISPECTRUM_BATCHED, vd.numel(), S, max_len, p))
+    _native.check(_native.lib().hos_trispectrum_batched(vd.data_ptr(), _dtype_code(vd), od.data_ptr(), S, vd.numel(),
+                                                        int(max_len), ctypes.byref(p), dev.data_ptr(), ws.ptr(),
+                                                        ws.nbytes(), _stream(stream)), "hos_trispectrum_batched")
+    return _finish(dev, host_out, host)
+
+
 def cumulant4(x, L, precision="bf16", remove_mean=True, segment_len=0, flush_chunks=0, workspace=None, stream=None):
     """Unwindowed sample c4 over [-L, L-1]^3 (float64, (2L, 2L, 2L))."""
     torch = _torch()
@@ -302,21 +325,22 @@ def bispectrum_sharded(x_local, L, halo_before, halo_after, n_total, nfft=0, pre
     return bispectrum_from_cumulant(c3, L, nfft, window, workspace=workspace)
 
 
-def bispectrum_direct(x, M, M3, remove_mean=True, out=None, workspace=None, stream=None):
-    """The paper's direct method (Algorithm DBS): parts of M samples, raw
-    (1/M) F(k1) F(k2) F*(k1+k2), M3 x M3 box smoothing by window sums, average
-    over parts.  (M, M) complex64 over the whole grid, [k1][k2]."""
+def bispectrum_direct(x, M, M3, remove_mean=True, overlap=0, out=None, workspace=None, stream=None):
+    """The paper's direct method (Algorithm DBS): parts of M samples (every
+    M - overlap samples), raw (1/M) F(k1) F(k2) F*(k1+k2), M3 x M3 box
+    smoothing by window sums, average over parts.  (M, M) complex64 over the
+    whole grid, [k1][k2]."""
     xd, host = _prepare(x)
     dev, host_out = _out_buffers(out, (int(M), int(M)), xd.device)
     nbytes = ctypes.c_size_t(0)
-    _native.check(_native.lib().hos_bispectrum_direct_workspace_size(xd.numel(), int(M), int(M3),
+    _native.check(_native.lib().hos_bispectrum_direct_workspace_size(xd.numel(), int(M), int(M3), int(overlap),
                                                                        ctypes.byref(nbytes)),
                   "hos_bispectrum_direct_workspace_size")
     ws = _workspace(workspace, xd.device)
     ws.get(nbytes.value)
     _native.check(_native.lib().hos_bispectrum_direct(xd.data_ptr(), _dtype_code(xd), xd.numel(), int(M), int(M3),
-                                                      int(bool(remove_mean)), dev.data_ptr(), ws.ptr(), ws.nbytes(),
-                                                      _stream(stream)), "hos_bispectrum_direct")
+                                                      int(overlap), int(bool(remove_mean)), dev.data_ptr(), ws.ptr(),
+                                                      ws.nbytes(), _stream(stream)), "hos_bispectrum_direct")
     return _finish(dev, host_out, host)
 
 

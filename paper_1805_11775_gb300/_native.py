@@ -17,7 +17,7 @@ STATUS_NAMES = {0: "HOS_OK", 1: "HOS_ERR_INVALID_ARG", 2: "HOS_ERR_UNSUPPORTED",
                 4: "HOS_ERR_CUDA", 5: "HOS_ERR_TIMEOUT", 6: "HOS_ERR_DEVICE_FAULT"}
 F32, F64 = 0, 1
 (OP_BISPECTRUM, OP_TRISPECTRUM, OP_BISPECTRUM_BATCHED, OP_BISPECTRUM_BACKWARD, OP_CUMULANT3, OP_CUMULANT4,
- OP_SERIES_SUM, OP_CUMULANT3_SLICE, OP_BISPECTRUM_FROM_C3) = range(9)
+ OP_SERIES_SUM, OP_CUMULANT3_SLICE, OP_BISPECTRUM_FROM_C3, OP_TRISPECTRUM_BATCHED) = range(10)
 
 
 class HosParams(ctypes.Structure):
@@ -48,14 +48,16 @@ _SIGS = {
     "hos_bispectrum_noalloc": [_VP, ctypes.c_int32, ctypes.c_int64, _P, _VP, _VP],
     "hos_cumulant3": [_VP, ctypes.c_int32, ctypes.c_int64, _P, _VP, _VP, ctypes.c_size_t, _VP],
     "hos_cumulant4": [_VP, ctypes.c_int32, ctypes.c_int64, _P, _VP, _VP, ctypes.c_size_t, _VP],
+    "hos_trispectrum_batched": [_VP, ctypes.c_int32, _VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P, _VP,
+                                _VP, ctypes.c_size_t, _VP],
     "hos_series_sum": [_VP, ctypes.c_int32, ctypes.c_int64, _VP, _VP, ctypes.c_size_t, _VP],
     "hos_cumulant3_slice": [_VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_int64,
                             _P, _VP, _VP, ctypes.c_size_t, _VP],
     "hos_bispectrum_from_cumulant": [_VP, _P, _VP, _VP, ctypes.c_size_t, _VP],
-    "hos_bispectrum_direct_workspace_size": [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+    "hos_bispectrum_direct_workspace_size": [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                              ctypes.POINTER(ctypes.c_size_t)],
     "hos_bispectrum_direct": [_VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                              _VP, _VP, ctypes.c_size_t, _VP],
+                              ctypes.c_int32, _VP, _VP, ctypes.c_size_t, _VP],
     "hos_get_device_status": [_VP, ctypes.POINTER(ctypes.c_int32)],
     "hos_reset_device_status": [_VP, _VP],
     "hos_selftest_timeout": [_VP, ctypes.c_size_t, ctypes.c_int32, _VP],

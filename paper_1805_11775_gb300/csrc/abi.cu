@@ -93,12 +93,13 @@ static hos_status check_params(const hos_params* p, int op) {
     if (p->tile_n != 0 && p->tile_n != 32 && p->tile_n != 64 && p->tile_n != 128 && p->tile_n != 256)
         return HOS_ERR_INVALID_ARG;
     if (p->flush_chunks < 0) return HOS_ERR_INVALID_ARG;
-    if (op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT4) {
+    if (op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT4 || op == HOS_OP_TRISPECTRUM_BATCHED) {
         if (p->L > 64) return HOS_ERR_UNSUPPORTED;
         if (p->window == HOS_WIN_PARZEN_SYM) return HOS_ERR_UNSUPPORTED;
     }
     if (op == HOS_OP_BISPECTRUM_BACKWARD && p->segment_len != 0) return HOS_ERR_UNSUPPORTED;
-    if (op == HOS_OP_BISPECTRUM_BATCHED && p->segment_len != 0) return HOS_ERR_INVALID_ARG;
+    if ((op == HOS_OP_BISPECTRUM_BATCHED || op == HOS_OP_TRISPECTRUM_BATCHED) && p->segment_len != 0)
+        return HOS_ERR_INVALID_ARG;
     return HOS_OK;
 }
 
@@ -270,6 +271,8 @@ static LineGeom line_geom(int N, int64_t nlines, int64_t inner, int64_t outer, i
     g.inner = inner;
     g.outer_stride = outer;
     g.elem_stride = elem;
+    g.half_out = 0;
+    g.herm = 0;
     int lpb = (g.log2N >= 0) ? 4096 / N : 2048 / N;
     // few lines: fewer per CTA so that the grid covers the SMs
     const int64_t spread = nlines / (2 * (int64_t)sm_count());
@@ -385,18 +388,30 @@ static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int6
 
 static hos_status run_dft2(float* grid, float2* out, int groups, int Nf, float2* tw, cudaStream_t st) {
     HOS_CUDA_TRY(launch_twiddles(Nf, tw, st));
+    // The grid is real, so its 2-D transform is Hermitian: B(N-k2, N-k1) = conj B(k2, k1).
+    // For N a power of two >= 8 the row pass writes columns 0..N/2 only and the
+    // column pass transforms those columns and mirrors them into the rest.
+    const bool herm = (Nf >= 8) && ((Nf & (Nf - 1)) == 0);
     // along the last axis (contiguous), real input
     LineGeom g1 = line_geom(Nf, (int64_t)groups * Nf, 1, Nf, 1);
+    g1.half_out = herm ? 1 : 0;
     HOS_CUDA_TRY(launch_lines(true, grid, out, g1, tw, -1, 1.0f, st));
     // along the first axis, in place
-    LineGeom g2 = line_geom(Nf, (int64_t)groups * Nf, Nf, (int64_t)Nf * Nf, Nf);
-    HOS_CUDA_TRY(launch_lines(false, out, out, g2, tw, -1, 1.0f, st));
+    if (herm) {
+        LineGeom g2 = line_geom(Nf, (int64_t)groups * (Nf / 2 + 1), Nf / 2 + 1, (int64_t)Nf * Nf, Nf);
+        g2.herm = 1;
+        HOS_CUDA_TRY(launch_lines(false, out, out, g2, tw, -1, 1.0f, st));
+    } else {
+        LineGeom g2 = line_geom(Nf, (int64_t)groups * Nf, Nf, (int64_t)Nf * Nf, Nf);
+        HOS_CUDA_TRY(launch_lines(false, out, out, g2, tw, -1, 1.0f, st));
+    }
     return HOS_OK;
 }
 
 // ---- fourth order --------------------------------------------------------------------
 struct Plan4 {
     int S;
+    bool batched;  // S independent series from caller offsets, one spectrum each
     int64_t seg, max_len, total_groups;
     int Nf, W3, npb, nslices, pad_tail;
     bool tc;    // tensor-core m4 (split-bf16 / 3xTF32) instead of FP32 SIMT
@@ -434,17 +449,28 @@ static C3Geom make_geom4(const hos_params* p, int G) {
     return g;
 }
 
-static hos_status make_plan4(int op, const hos_params* p, int64_t n, Plan4& P) {
+static hos_status make_plan4(int op, const hos_params* p, int64_t n, Plan4& P, int S_in = 1, int64_t max_len_in = 0) {
     hos_status s = check_params(p, op);
     if (s != HOS_OK) return s;
     const int L = p->L, twoL = 2 * L;
     P.Nf = p->nfft ? p->nfft : twoL;
-    P.seg = (p->segment_len > 0 && p->segment_len < n) ? p->segment_len : 0;
-    const int64_t S64 = P.seg ? ceil_div(n, P.seg) : 1;
-    if (S64 > 65535) return HOS_ERR_UNSUPPORTED;
-    P.S = (int)S64;
-    P.max_len = P.seg ? P.seg : n;
-    const int64_t last = n - (P.S - 1) * (P.seg ? P.seg : 0);
+    P.batched = (op == HOS_OP_TRISPECTRUM_BATCHED);
+    int64_t last;
+    if (P.batched) {
+        if (p->precision == HOS_PREC_SIMT_FP32) return HOS_ERR_UNSUPPORTED;  // tensor-core path only
+        if (S_in < 1 || S_in > 65535) return S_in < 1 ? HOS_ERR_INVALID_ARG : HOS_ERR_UNSUPPORTED;
+        P.seg = 0;
+        P.S = S_in;
+        P.max_len = max_len_in;
+        last = max_len_in;
+    } else {
+        P.seg = (p->segment_len > 0 && p->segment_len < n) ? p->segment_len : 0;
+        const int64_t S64 = P.seg ? ceil_div(n, P.seg) : 1;
+        if (S64 > 65535) return HOS_ERR_UNSUPPORTED;
+        P.S = (int)S64;
+        P.max_len = P.seg ? P.seg : n;
+        last = n - (P.S - 1) * (P.seg ? P.seg : 0);
+    }
     auto groups = [](int64_t len) { return ceil_div(ceil_div(len, KC), C4_CHUNK_GROUP); };
     P.total_groups = (P.S - 1) * groups(P.max_len) + groups(last);
     if (P.total_groups > 65535) return HOS_ERR_UNSUPPORTED;
@@ -455,7 +481,10 @@ static hos_status make_plan4(int op, const hos_params* p, int64_t n, Plan4& P) {
     P.tc = (p->precision != HOS_PREC_SIMT_FP32);
     if (P.tc) {
         P.g4 = make_geom4(p, sm_count());
-        const int64_t U = (int64_t)P.g4.ntiles * ((P.S - 1) * ceil_div(P.max_len, P.g4.kc) + ceil_div(last, P.g4.kc));
+        // work units (tile, chunk); for caller offsets only an upper bound is known
+        const int64_t U = P.batched ? (int64_t)P.g4.ntiles * (ceil_div(n, P.g4.kc) + P.S)
+                                    : (int64_t)P.g4.ntiles *
+                                          ((P.S - 1) * ceil_div(P.max_len, P.g4.kc) + ceil_div(last, P.g4.kc));
         if (U < P.g4.G) P.g4.G = (int)(U > 0 ? U : 1);
         P.pad_tail = P.g4.pad_tail;
     }
@@ -489,14 +518,16 @@ static hos_status make_plan4(int op, const hos_params* p, int64_t n, Plan4& P) {
     } else {
         P.partials = o; o = al256(o + 4 * (size_t)P.total_groups * P.npb * C4_PAIRS_PER_CTA * P.W3);
     }
-    P.grid = o; o = al256(o + (op == HOS_OP_TRISPECTRUM ? 4 * (size_t)P.Nf * P.Nf * P.Nf : 0));
+    const bool spectra = (op == HOS_OP_TRISPECTRUM || op == HOS_OP_TRISPECTRUM_BATCHED);
+    P.grid = o; o = al256(o + (spectra ? 4 * (size_t)P.S * P.Nf * P.Nf * P.Nf : 0));
     P.tw = o; o = al256(o + 8 * (size_t)P.Nf);
     P.total = o;
     return HOS_OK;
 }
 
 static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, const hos_params* p, void* ws,
-                         size_t ws_bytes, cudaStream_t st, Tracer& tr, int mode, double* c4out) {
+                         size_t ws_bytes, cudaStream_t st, Tracer& tr, int mode, double* c4out,
+                         const int64_t* d_offsets = nullptr) {
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < P.total) return HOS_ERR_WORKSPACE;
     int64_t* off = at<int64_t>(ws, P.off);
     int64_t* pad = at<int64_t>(ws, P.pad);
@@ -508,8 +539,8 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
     const int ntiles = P.tc ? P.g4.ntiles : 1;
     const int flush = P.tc ? P.g4.flush : C4_CHUNK_GROUP;
     const int kc = P.tc ? P.g4.kc : KC;
-    HOS_CUDA_TRY(launch_plan_series(0, n, P.seg, nullptr, P.S, p->L, ntiles, flush, kc, P.pad_tail, off, pad, unit,
-                                    win, st));
+    HOS_CUDA_TRY(launch_plan_series(P.batched ? 1 : 0, n, P.seg, d_offsets, P.S, p->L, ntiles, flush, kc, P.pad_tail,
+                                    off, pad, unit, win, st));
     HOS_CUDA_TRY(launch_mean(x, dtype, off, P.S, P.nslices, at<double>(ws, P.mpart), p->remove_mean, mean, st));
     const int64_t maxpad = (int64_t)p->L + P.max_len + KC + P.pad_tail + 64;
     int bx = (int)ceil_div(maxpad, 256 * 4);
@@ -527,7 +558,9 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
     r.scale = 1.0 / (8.0 * 3.14159265358979323846 * 3.14159265358979323846 * 3.14159265358979323846);
     r.grid = at<float>(ws, P.grid);
     r.c4out = c4out;
-    if (mode == 0 && P.Nf > 2 * p->L) HOS_CUDA_TRY(launch_zero_f32(r.grid, (int64_t)P.Nf * P.Nf * P.Nf, st));
+    const int ngrids = P.batched ? P.S : 1;
+    if (mode == 0 && P.Nf > 2 * p->L)
+        HOS_CUDA_TRY(launch_zero_f32(r.grid, (int64_t)ngrids * P.Nf * P.Nf * P.Nf, st));
     if (!P.tc) {
         HOS_CUDA_TRY(launch_c4(y32, off, pad, win, P.S, p->L, C4_CHUNK_GROUP, P.total_groups, at<double>(ws, P.c2),
                                at<float>(ws, P.partials), r, st));
@@ -545,18 +578,19 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
     double* m4buf = at<double>(ws, P.m4buf);
     HOS_CUDA_TRY(launch_m4_tile_reduce(P.g4, sv, P.max_len, at<float>(ws, P.partials), at<int64_t>(ws, P.bnd),
                                        at<TileRec>(ws, P.xr), at<float2>(ws, P.ilen), m4buf, st));
-    HOS_CUDA_TRY(launch_c4_assemble(m4buf, c2, off, P.S, p->L, P.g4.ntiles, P.g4.tile_n, r, st));
+    HOS_CUDA_TRY(launch_c4_assemble(m4buf, c2, off, P.S, p->L, P.g4.ntiles, P.g4.tile_n, r, P.batched ? 1 : 0, st));
     return HOS_OK;
 }
 
-static hos_status run_dft3(float* grid, float2* out, int Nf, float2* tw, cudaStream_t st) {
-    const int64_t N = Nf, N2 = N * N;
+// 3-D transform of `grids` consecutive N^3 grids, one axis at a time.
+static hos_status run_dft3(float* grid, float2* out, int Nf, float2* tw, cudaStream_t st, int grids = 1) {
+    const int64_t N = Nf, N2 = N * N, G = grids;
     HOS_CUDA_TRY(launch_twiddles(Nf, tw, st));
-    LineGeom g2 = line_geom(Nf, N2, 1, N, 1);  // along k3 (contiguous), real input
+    LineGeom g2 = line_geom(Nf, G * N2, 1, N, 1);  // along k3 (contiguous), real input
     HOS_CUDA_TRY(launch_lines(true, grid, out, g2, tw, -1, 1.0f, st));
-    LineGeom g1 = line_geom(Nf, N2, N, N2, N);  // along k2
+    LineGeom g1 = line_geom(Nf, G * N2, N, N2, N);  // along k2
     HOS_CUDA_TRY(launch_lines(false, out, out, g1, tw, -1, 1.0f, st));
-    LineGeom g0 = line_geom(Nf, N2, N2, N2 * N, N2);  // along k1
+    LineGeom g0 = line_geom(Nf, G * N2, N2, N2 * N, N2);  // along k1
     HOS_CUDA_TRY(launch_lines(false, out, out, g0, tw, -1, 1.0f, st));
     return HOS_OK;
 }
@@ -636,10 +670,10 @@ const char* hos_last_contraction(void) { return g_last_contraction; }
 hos_status hos_workspace_size(int32_t op, int64_t n_total, int32_t n_series, int64_t max_len, const hos_params* p,
                               size_t* bytes) {
     if (!bytes || n_total < 0 || n_series < 1 || max_len < 0) return HOS_ERR_INVALID_ARG;
-    if (op < 0 || op > HOS_OP_BISPECTRUM_FROM_C3) return HOS_ERR_INVALID_ARG;
-    if (op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT4) {
+    if (op < 0 || op > HOS_OP_TRISPECTRUM_BATCHED) return HOS_ERR_INVALID_ARG;
+    if (op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT4 || op == HOS_OP_TRISPECTRUM_BATCHED) {
         Plan4 P4;
-        hos_status s4 = make_plan4(op, p, n_total, P4);
+        hos_status s4 = make_plan4(op, p, n_total, P4, n_series, max_len);
         if (s4 != HOS_OK) return s4;
         *bytes = P4.total;
         return HOS_OK;
@@ -718,26 +752,23 @@ hos_status hos_bispectrum_from_cumulant(const double* d_c3, const hos_params* p,
 
 // ---- the direct method (Algorithm DBS) ----------------------------------------------
 struct DirectLayout {
-    int64_t K;
-    int nslices;
-    size_t off, mean, mpart, y, F, tw, R, Cw, total;
+    int64_t K, step;
+    size_t mean, y, F, tw, R, Cw, total;
 };
 
-static hos_status direct_layout(int64_t n, int32_t M, int32_t M3, DirectLayout& l) {
-    if (n < 1 || M < 2 || M3 < 1 || M3 > M) return HOS_ERR_INVALID_ARG;
+static hos_status direct_layout(int64_t n, int32_t M, int32_t M3, int32_t overlap, DirectLayout& l) {
+    if (n < 1 || M < 2 || M3 < 1 || M3 > M || overlap < 0 || overlap >= M) return HOS_ERR_INVALID_ARG;
     const bool pow2 = (M & (M - 1)) == 0;
     if ((pow2 && M > 8192) || (!pow2 && M > 2048)) return HOS_ERR_UNSUPPORTED;
-    if ((size_t)(M + M3 - 1) * 16 > 227 * 1024) return HOS_ERR_UNSUPPORTED;  // a row and its wrap in shared memory
-    l.K = n / M;
+    // a row and its wrap in shared memory (16 B per point) next to 16 KB of run totals
+    if ((size_t)(M + M3 - 1) * 16 + 16 * 1024 > 227 * 1024) return HOS_ERR_UNSUPPORTED;
+    l.step = M - overlap;
+    l.K = n >= M ? (n - M) / l.step + 1 : 0;
     if (l.K < 1) return HOS_ERR_INVALID_ARG;
     if (l.K > (1 << 24)) return HOS_ERR_UNSUPPORTED;
-    int64_t ns = ceil_div(M, 8192);
-    l.nslices = (int)(ns < 1 ? 1 : ns);
     const size_t MM = (size_t)M * M;
     size_t o = 0;
-    l.off = o; o = al256(o + 8 * (size_t)(l.K + 1));
     l.mean = o; o = al256(o + 8 * (size_t)l.K);
-    l.mpart = o; o = al256(o + 8 * (size_t)l.K * l.nslices);
     l.y = o; o = al256(o + 4 * (size_t)l.K * M);
     l.F = o; o = al256(o + 8 * (size_t)l.K * M);
     l.tw = o; o = al256(o + 8 * (size_t)M);
@@ -747,34 +778,29 @@ static hos_status direct_layout(int64_t n, int32_t M, int32_t M3, DirectLayout& 
     return HOS_OK;
 }
 
-hos_status hos_bispectrum_direct_workspace_size(int64_t n, int32_t M, int32_t M3, size_t* bytes) {
+hos_status hos_bispectrum_direct_workspace_size(int64_t n, int32_t M, int32_t M3, int32_t overlap, size_t* bytes) {
     if (!bytes) return HOS_ERR_INVALID_ARG;
     DirectLayout l;
-    hos_status s = direct_layout(n, M, M3, l);
+    hos_status s = direct_layout(n, M, M3, overlap, l);
     if (s != HOS_OK) return s;
     *bytes = l.total;
     return HOS_OK;
 }
 
-hos_status hos_bispectrum_direct(const void* d_x, int32_t dtype, int64_t n, int32_t M, int32_t M3,
+hos_status hos_bispectrum_direct(const void* d_x, int32_t dtype, int64_t n, int32_t M, int32_t M3, int32_t overlap,
                                  int32_t remove_mean, void* d_B, void* ws, size_t ws_bytes, hos_stream_t stream) {
     if (!d_x || !d_B || (dtype != HOS_F32 && dtype != HOS_F64)) return HOS_ERR_INVALID_ARG;
     DirectLayout l;
-    hos_status s = direct_layout(n, M, M3, l);
+    hos_status s = direct_layout(n, M, M3, overlap, l);
     if (s != HOS_OK) return s;
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < l.total) return HOS_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     Tracer tr(st);
     tr.mark("prep");
-    int64_t* off = at<int64_t>(ws, l.off);
-    double* mean = at<double>(ws, l.mean);
     float* y = at<float>(ws, l.y);
     float2* F = at<float2>(ws, l.F);
     float2* tw = at<float2>(ws, l.tw);
-    HOS_CUDA_TRY(launch_part_offsets(l.K, M, off, st));
-    HOS_CUDA_TRY(launch_mean(d_x, dtype, off, (int)l.K, l.nslices, at<double>(ws, l.mpart), remove_mean ? 1 : 0, mean,
-                             st));
-    HOS_CUDA_TRY(launch_demean_parts(d_x, dtype, l.K * M, M, mean, y, st));
+    HOS_CUDA_TRY(launch_part_prep(d_x, dtype, l.K, M, l.step, remove_mean ? 1 : 0, at<double>(ws, l.mean), y, st));
     tr.mark("transform");
     HOS_CUDA_TRY(launch_twiddles(M, tw, st));
     LineGeom g = line_geom(M, l.K, 1, M, 1);
@@ -851,6 +877,25 @@ hos_status hos_trispectrum(const void* d_x, int32_t dtype, int64_t n, const hos_
     if (s != HOS_OK) return s;
     tr.mark("transform");
     s = run_dft3(at<float>(ws, P.grid), reinterpret_cast<float2*>(d_T), P.Nf, at<float2>(ws, P.tw), st);
+    tr.mark("");
+    return s;
+}
+
+hos_status hos_trispectrum_batched(const void* d_x, int32_t dtype, const int64_t* d_offsets, int32_t S,
+                                   int64_t n_total, int64_t max_len, const hos_params* p, void* d_T, void* ws,
+                                   size_t ws_bytes, hos_stream_t stream) {
+    if (!d_x || !d_T || !d_offsets || S < 1 || n_total < 0 || max_len < 0 || (dtype != HOS_F32 && dtype != HOS_F64))
+        return HOS_ERR_INVALID_ARG;
+    Plan4 P;
+    hos_status s = make_plan4(HOS_OP_TRISPECTRUM_BATCHED, p, n_total, P, S, max_len);
+    if (s != HOS_OK) return s;
+    if (!ws || ws_bytes < P.total) return HOS_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Tracer tr(st);
+    s = run_c4(d_x, dtype, n_total, P, p, ws, ws_bytes, st, tr, 0, nullptr, d_offsets);
+    if (s != HOS_OK) return s;
+    tr.mark("transform");
+    s = run_dft3(at<float>(ws, P.grid), reinterpret_cast<float2*>(d_T), P.Nf, at<float2>(ws, P.tw), st, P.S);
     tr.mark("");
     return s;
 }

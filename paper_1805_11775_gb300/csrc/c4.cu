@@ -216,9 +216,10 @@ __global__ void reduce4_kernel(const Reduce4Params P) {
 // Fourth order from the tensor-core path: c4 of each part from its m4 (m4buf)
 // and c2, averaged over parts, then windowed onto the grid (mode 0) or
 // written raw (mode 1).
+// per_series: blockIdx.y = series s, whose c4 goes to its own grid (no average).
 __global__ void c4_assemble_kernel(const double* __restrict__ m4buf, const double* __restrict__ c2,
                                    const int64_t* __restrict__ off, int S, int L, int ntiles, int tile_n,
-                                   C4ReduceArgs r) {
+                                   C4ReduceArgs r, int per_series) {
     const int twoL = 2 * L, T = 2 * L - 1;
     // per-lag window factor d(w) (RECT: 0 at w = -L), FP32 like the grid
     __shared__ float wsh[2 * 64];
@@ -236,7 +237,8 @@ __global__ void c4_assemble_kernel(const double* __restrict__ m4buf, const doubl
     const int64_t elem = (int64_t)(w3 + L) * TILE_M + m;
     double c4 = 0.0;
     int k = 0;
-    for (int s = 0; s < S; ++s) {
+    const int s0 = per_series ? (int)blockIdx.y : 0, s1 = per_series ? s0 + 1 : S;
+    for (int s = s0; s < s1; ++s) {
         if (off[s + 1] <= off[s]) continue;
         const double m4 = m4buf[((int64_t)s * ntiles + t) * tsz + elem];
         const double* c = c2 + (int64_t)s * (2 * T + 1) + T;
@@ -245,13 +247,15 @@ __global__ void c4_assemble_kernel(const double* __restrict__ m4buf, const doubl
     }
     if (k > 0) c4 /= (double)k;
     if (r.mode == 1) {
-        r.c4out[((int64_t)(w1 + L) * twoL + (w2 + L)) * twoL + (w3 + L)] = c4;
+        r.c4out[(int64_t)(per_series ? blockIdx.y : 0) * twoL * twoL * twoL +
+                ((int64_t)(w1 + L) * twoL + (w2 + L)) * twoL + (w3 + L)] = c4;
         return;
     }
     const float wv = wsh[w1 + L] * wsh[w2 + L] * wsh[w3 + L];
     const int N = r.nfft;  // >= 2L, so w + N >= 0
     const int k1 = w1 < 0 ? w1 + N : w1, k2 = w2 < 0 ? w2 + N : w2, k3 = w3 < 0 ? w3 + N : w3;
-    r.grid[((int64_t)k1 * N + k2) * N + k3] = (float)c4 * ((float)r.scale * wv);
+    r.grid[(int64_t)(per_series ? blockIdx.y : 0) * N * N * N + ((int64_t)k1 * N + k2) * N + k3] =
+        (float)c4 * ((float)r.scale * wv);
 }
 
 cudaError_t launch_c2(const float* y32, const int64_t* off, const int64_t* pad, int S, int L, double* c2,
@@ -263,9 +267,10 @@ cudaError_t launch_c2(const float* y32, const int64_t* off, const int64_t* pad, 
 }
 
 cudaError_t launch_c4_assemble(const double* m4buf, const double* c2, const int64_t* off, int S, int L, int ntiles,
-                               int tile_n, const C4ReduceArgs& r, cudaStream_t st) {
+                               int tile_n, const C4ReduceArgs& r, int per_series, cudaStream_t st) {
     const int64_t n3 = 8LL * L * L * L;
-    c4_assemble_kernel<<<(unsigned)ceil_div(n3, 256), 256, 0, st>>>(m4buf, c2, off, S, L, ntiles, tile_n, r);
+    dim3 grid((unsigned)ceil_div(n3, 256), per_series ? (unsigned)S : 1u);
+    c4_assemble_kernel<<<grid, 256, 0, st>>>(m4buf, c2, off, S, L, ntiles, tile_n, r, per_series);
     count_launch();
     return cudaGetLastError();
 }

@@ -213,6 +213,11 @@ __global__ void __launch_bounds__(1024) fft_r8_kernel(const void* in, float2* ou
     const bool live = l < nl;
     const int64_t base = live ? lbase[l] : 0;
     const int64_t es = g.elem_stride;
+    // Hermitian columns: line = column c of group gb; column N - c gets the conjugate mirror
+    const int64_t lglob = l0 + l;
+    const int hc = g.herm ? (int)(lglob % g.inner) : 0;
+    const bool mirror = g.herm && hc != 0 && 2 * hc != N;
+    const int64_t mbase = g.herm ? (lglob / g.inner) * g.outer_stride + (N - hc) : 0;
     float2* row = sbuf + (size_t)l * SL;
     float2 v[8];
     // first pass (s0 = 0, radix 8): group t holds inputs bitrev(8t + m)
@@ -233,30 +238,24 @@ __global__ void __launch_bounds__(1024) fft_r8_kernel(const void* in, float2* ou
         else { if (live) pass_load<1>(v, row, s0, t, T); radix_pass<1>(v, s0, lg, t, T, tws); }
         if (s0 + r >= lg) {  // last pass: natural-order output straight to global memory
             if (live) {
+                auto put = [&](int idx, float2 o) {
+                    const float2 w = make_float2(o.x * scale, o.y * scale);
+                    out[base + (int64_t)idx * es] = w;
+                    if (mirror) out[mbase + (int64_t)((N - idx) & (N - 1)) * es] = make_float2(w.x, -w.y);
+                };
                 if (r == 3) {
 #pragma unroll
-                    for (int m = 0; m < 8; ++m) {
-                        const float2 o = v[m];
-                        out[base + (int64_t)group_index<3>(0, m, s0, t, T) * es] = make_float2(o.x * scale, o.y * scale);
-                    }
+                    for (int m = 0; m < 8; ++m) put(group_index<3>(0, m, s0, t, T), v[m]);
                 } else if (r == 2) {
 #pragma unroll
                     for (int q = 0; q < 2; ++q)
 #pragma unroll
-                        for (int m = 0; m < 4; ++m) {
-                            const float2 o = v[q * 4 + m];
-                            out[base + (int64_t)group_index<2>(q, m, s0, t, T) * es] =
-                                make_float2(o.x * scale, o.y * scale);
-                        }
+                        for (int m = 0; m < 4; ++m) put(group_index<2>(q, m, s0, t, T), v[q * 4 + m]);
                 } else {
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
 #pragma unroll
-                        for (int m = 0; m < 2; ++m) {
-                            const float2 o = v[q * 2 + m];
-                            out[base + (int64_t)group_index<1>(q, m, s0, t, T) * es] =
-                                make_float2(o.x * scale, o.y * scale);
-                        }
+                        for (int m = 0; m < 2; ++m) put(group_index<1>(q, m, s0, t, T), v[q * 2 + m]);
                 }
             }
             return;
@@ -268,8 +267,9 @@ __global__ void __launch_bounds__(1024) fft_r8_kernel(const void* in, float2* ou
     if (live) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
-            const float2 o = v[m];
-            out[base + (int64_t)m * es] = make_float2(o.x * scale, o.y * scale);
+            const float2 w = make_float2(v[m].x * scale, v[m].y * scale);
+            out[base + (int64_t)m * es] = w;
+            if (mirror) out[mbase + (int64_t)((N - m) & (N - 1)) * es] = make_float2(w.x, -w.y);
         }
     }
 }
@@ -332,7 +332,8 @@ __global__ void __launch_bounds__(1024) fft_r8_pair_kernel(const float* __restri
     __syncthreads();
     if (!live) return;
     const float h = 0.5f * scale;
-    for (int k = t; k < N; k += T) {
+    const int kend = g.half_out ? (N >> 1) + 1 : N;
+    for (int k = t; k < kend; k += T) {
         const float2 zk = row[sk(k)], zn = row[sk((N - k) & (N - 1))];
         out[ba + k] = make_float2((zk.x + zn.x) * h, (zk.y - zn.y) * h);
         out[bb + k] = make_float2((zk.y + zn.y) * h, (zn.x - zk.x) * h);

@@ -1,6 +1,7 @@
 // direct.cu -- the paper's direct method (Algorithm DBS) on the GPU:
 //
-//   1-2. K = floor(n / M) parts of M samples, each minus its own mean (FP64);
+//   1-2. parts of M samples every M - overlap samples (overlap 0: the paper's
+//        partition into K = floor(n / M) parts), each minus its own mean (FP64);
 //   3.   F_p(k) = sum_u X_p(u) e^{-j 2 pi u k / M}: the transform kernels of
 //        dft.cu over the K part lines;
 //   4.   raw C3_p(k1,k2) = (1/M) F_p(k1) F_p(k2) F_p*(k1+k2), indices mod M,
@@ -37,18 +38,33 @@ HOS_DEV void df_acc(float& h, float& l, float bh, float bl) {
 
 }  // namespace
 
-// off[p] = p * M, p = 0..K (the parts as a series view for the mean kernels)
-__global__ void part_offsets_kernel(int64_t K, int64_t M, int64_t* __restrict__ off) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p <= K) off[p] = p * M;
+// mean[p] of part p = x[p step .. p step + M), FP64, fixed-order tree per
+// block (one block per part); 0 without mean removal.
+template <typename T>
+__global__ void __launch_bounds__(256) part_mean_kernel(const T* __restrict__ x, int64_t M, int64_t step,
+                                                        int remove_mean, double* __restrict__ mean) {
+    __shared__ double sh[256];
+    const T* xp = x + (int64_t)blockIdx.x * step;
+    double a = 0.0;
+    if (remove_mean)
+        for (int64_t u = threadIdx.x; u < M; u += 256) a += (double)xp[u];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int d = 128; d > 0; d >>= 1) {
+        if (threadIdx.x < d) sh[threadIdx.x] += sh[threadIdx.x + d];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) mean[blockIdx.x] = remove_mean ? sh[0] / (double)M : 0.0;
 }
 
-// y[p][u] = x[p M + u] - mean[p] (FP64 difference, FP32 result)
+// y[p][u] = x[p step + u] - mean[p] (FP64 difference, FP32 result)
 template <typename T>
-__global__ void demean_parts_kernel(const T* __restrict__ x, int64_t total, int64_t M,
+__global__ void demean_parts_kernel(const T* __restrict__ x, int64_t total, int64_t M, int64_t step,
                                     const double* __restrict__ mean, float* __restrict__ y) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = (float)((double)x[i] - mean[i / M]);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = i / M;
+        y[i] = (float)((double)x[p * step + (i - p * M)] - mean[p]);
+    }
 }
 
 // R[k1][k2] = (1 / (K M)) sum_p F_p(k1) F_p(k2) conj F_p((k1 + k2) mod M)
@@ -84,20 +100,22 @@ __global__ void col_window_sums_kernel(const float2* __restrict__ R, int M, int 
     const int lo = -(M3 / 2);
     auto row = [&](int k) { k %= M; if (k < 0) k += M; return k; };
     float rh = 0.0f, rl = 0.0f, ih = 0.0f, il = 0.0f;
-    for (int n = lo; n < lo + M3; ++n) {
+#pragma unroll 8
+    for (int n = lo; n < lo + M3; ++n) {  // independent loads: several in flight
         const float2 v = R[(int64_t)row(r0 + n) * M + k2];
         df_acc(rh, rl, v.x, 0.0f);
         df_acc(ih, il, v.y, 0.0f);
     }
-    for (int k1 = r0;; ++k1) {
-        Cw[(int64_t)k1 * M + k2] = make_float2(rh + rl, ih + il);
-        if (k1 + 1 >= r1) break;
-        const float2 out = R[(int64_t)row(k1 + lo) * M + k2];
-        const float2 in = R[(int64_t)row(k1 + lo + M3) * M + k2];
+    Cw[(int64_t)r0 * M + k2] = make_float2(rh + rl, ih + il);
+#pragma unroll 4
+    for (int k1 = r0 + 1; k1 < r1; ++k1) {
+        const float2 out = R[(int64_t)row(k1 - 1 + lo) * M + k2];
+        const float2 in = R[(int64_t)row(k1 - 1 + lo + M3) * M + k2];
         df_acc(rh, rl, in.x, 0.0f);  // each term added exactly (TwoSum)
         df_acc(rh, rl, -out.x, 0.0f);
         df_acc(ih, il, in.y, 0.0f);
         df_acc(ih, il, -out.y, 0.0f);
+        Cw[(int64_t)k1 * M + k2] = make_float2(rh + rl, ih + il);
     }
 }
 
@@ -105,10 +123,10 @@ __global__ void col_window_sums_kernel(const float2* __restrict__ R, int M, int 
 // its circular continuation (M + M3 - 1 values, starting at column lo) goes to
 // shared memory as double-float; an inclusive prefix sum P follows (each
 // thread scans a contiguous run; warp 0 turns the runs' totals into offsets,
-// 8 runs per lane in order, then a fixed-order scan across the lanes; each
+// 32 runs per lane in order, then a fixed-order scan across the lanes; each
 // thread adds its offset);
 // then B[k1][k2] = (P[k2 + M3 - 1] - P[k2 - 1]) / M3^2 (P[-1] = 0).
-constexpr int ROW_THREADS = 256;
+constexpr int ROW_THREADS = 1024;
 __global__ void __launch_bounds__(ROW_THREADS) row_window_sums_kernel(const float2* __restrict__ Cw, int M, int M3,
                                                               float2* __restrict__ B) {
     extern __shared__ float4 pre[];  // (re.h, re.l, im.h, im.l), M + M3 - 1 entries
@@ -117,9 +135,10 @@ __global__ void __launch_bounds__(ROW_THREADS) row_window_sums_kernel(const floa
     const int lo = -(M3 / 2);
     const int len = M + M3 - 1;
     const float2* src = Cw + (int64_t)k1 * M;
+#pragma unroll 4
     for (int j = threadIdx.x; j < len; j += blockDim.x) {
-        int k = (j + lo) % M;
-        if (k < 0) k += M;
+        int k = j + lo;  // lo > -M, j < M + M3 - 1 <= 2M - 1
+        k = k < 0 ? k + M : (k >= M ? k - M : k);
         const float2 v = src[k];
         pre[j] = make_float4(v.x, 0.0f, v.y, 0.0f);
     }
@@ -136,10 +155,10 @@ __global__ void __launch_bounds__(ROW_THREADS) row_window_sums_kernel(const floa
     }
     runs[threadIdx.x] = make_float4(rh, rl, ih, il);
     __syncthreads();
-    if (threadIdx.x < 32) {  // exclusive offsets of the runs: warp 0, 8 runs per lane, then a lane scan
+    if (threadIdx.x < 32) {  // exclusive offsets of the runs: warp 0, PER runs per lane, then a lane scan
         constexpr int PER = ROW_THREADS / 32;
         const int lane = threadIdx.x;
-        float oh = 0.0f, ol = 0.0f, qh = 0.0f, ql = 0.0f;  // this lane's 8 runs, inclusive
+        float oh = 0.0f, ol = 0.0f, qh = 0.0f, ql = 0.0f;  // this lane's PER runs, inclusive
         for (int t = lane * PER; t < lane * PER + PER; ++t) {
             const float4 r = runs[t];
             df_acc(oh, ol, r.x, r.y);
@@ -188,20 +207,21 @@ __global__ void __launch_bounds__(ROW_THREADS) row_window_sums_kernel(const floa
     }
 }
 
-cudaError_t launch_part_offsets(int64_t K, int64_t M, int64_t* off, cudaStream_t st) {
-    part_offsets_kernel<<<(unsigned)ceil_div(K + 1, 256), 256, 0, st>>>(K, M, off);
+cudaError_t launch_part_prep(const void* x, int dtype, int64_t K, int64_t M, int64_t step, int remove_mean,
+                             double* mean, float* y, cudaStream_t st) {
+    if (dtype == HOS_F64)
+        part_mean_kernel<double><<<(unsigned)K, 256, 0, st>>>((const double*)x, M, step, remove_mean, mean);
+    else
+        part_mean_kernel<float><<<(unsigned)K, 256, 0, st>>>((const float*)x, M, step, remove_mean, mean);
     count_launch();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_demean_parts(const void* x, int dtype, int64_t total, int64_t M, const double* mean, float* y,
-                                cudaStream_t st) {
-    int64_t b = ceil_div(total, 256);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int64_t b = ceil_div(K * M, 256);
     if (b > 8192) b = 8192;
     if (dtype == HOS_F64)
-        demean_parts_kernel<double><<<(unsigned)b, 256, 0, st>>>((const double*)x, total, M, mean, y);
+        demean_parts_kernel<double><<<(unsigned)b, 256, 0, st>>>((const double*)x, K * M, M, step, mean, y);
     else
-        demean_parts_kernel<float><<<(unsigned)b, 256, 0, st>>>((const float*)x, total, M, mean, y);
+        demean_parts_kernel<float><<<(unsigned)b, 256, 0, st>>>((const float*)x, K * M, M, step, mean, y);
     count_launch();
     return cudaGetLastError();
 }

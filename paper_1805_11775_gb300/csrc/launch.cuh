@@ -58,7 +58,10 @@ struct LineGeom {
     int64_t inner;
     int64_t outer_stride;
     int64_t elem_stride;
-    int lpb;  // lines per CTA
+    int lpb;       // lines per CTA
+    int half_out;  // real-input lines: write only k = 0..N/2 (the rest is their conjugate mirror)
+    int herm;      // 2-D grid of a real array: the lines are columns c = 0..N/2 of each group, and
+                   // each also fills column N - c as B(N - k, N - c) = conj B(k, c)
 };
 
 struct C4ReduceArgs {
@@ -91,9 +94,8 @@ cudaError_t launch_window_c3(const double* c3, int L, int window, int Nf, double
 cudaError_t launch_series_sum(const void* x, int dtype, int64_t n, int nslices, int64_t* off, double* part,
                               double* sum, cudaStream_t st);
 // direct method (direct.cu)
-cudaError_t launch_part_offsets(int64_t K, int64_t M, int64_t* off, cudaStream_t st);
-cudaError_t launch_demean_parts(const void* x, int dtype, int64_t total, int64_t M, const double* mean, float* y,
-                                cudaStream_t st);
+cudaError_t launch_part_prep(const void* x, int dtype, int64_t K, int64_t M, int64_t step, int remove_mean,
+                             double* mean, float* y, cudaStream_t st);
 cudaError_t launch_direct_smooth(const float2* F, int K, int M, int M3, float2* R, float2* Cw, float2* B,
                                  cudaStream_t st);
 cudaError_t launch_slice_mean(const double* sum, int64_t n_total, int remove_mean, double* mean, cudaStream_t st);
@@ -127,7 +129,7 @@ cudaError_t launch_m4_tile_reduce(const C3Geom& geo, const SeriesView& sv, int64
 cudaError_t launch_c2(const float* y32, const int64_t* off, const int64_t* pad, int S, int L, double* c2,
                       cudaStream_t st);
 cudaError_t launch_c4_assemble(const double* m4buf, const double* c2, const int64_t* off, int S, int L, int ntiles,
-                               int tile_n, const C4ReduceArgs& r, cudaStream_t st);
+                               int tile_n, const C4ReduceArgs& r, int per_series, cudaStream_t st);
 cudaError_t launch_timeout_selftest(int* status, uint64_t limit_ns, cudaStream_t st);
 
 }  // namespace hos

@@ -39,6 +39,14 @@ def test_direct_matches_oracle(hos, oracle, n, M, M3, rm):
     assert normwise(got, ref) <= TOL
 
 
+@pytest.mark.parametrize("n,M,M3,overlap", [(1000, 128, 5, 64), (700, 96, 4, 30), (4096, 512, 16, 500)])
+def test_direct_overlapping_parts(hos, oracle, n, M, M3, overlap):
+    x = hos_synth.ma(n, n + overlap)
+    ref = oracle.bispectrum_direct(x, M, M3, overlap=overlap)
+    got = hos.bispectrum_direct(torch.from_numpy(x).cuda(), M, M3, overlap=overlap).cpu().numpy()
+    assert normwise(got, ref) <= TOL
+
+
 def test_direct_float32_input_many_parts(hos, oracle):
     x = hos_synth.ma(64 * 200, 9).astype(np.float32)
     ref = oracle.bispectrum_direct(x.astype(np.float64), 64, 6)
@@ -70,8 +78,10 @@ def test_direct_large_grids(hos, M, M3):
 def test_direct_argument_errors(hos):
     from paper_1805_11775_gb300._native import HosError
     # fewer samples than one part, box wider than the grid, empty box, one-point
-    # grid, a non-power-of-two grid above 2048, a power of two above 8192
-    for n, M, M3 in [(100, 200, 4), (100, 64, 65), (100, 64, 0), (100, 1, 1), (6000, 3000, 4), (32768, 16384, 4)]:
+    # grid, a non-power-of-two grid above 2048, a power of two above 8192,
+    # overlap of a whole part, negative overlap
+    for n, M, M3, ov in [(100, 200, 4, 0), (100, 64, 65, 0), (100, 64, 0, 0), (100, 1, 1, 0), (6000, 3000, 4, 0),
+                         (32768, 16384, 4, 0), (100, 64, 4, 64), (100, 64, 4, -1)]:
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
         with pytest.raises(HosError):
-            hos.bispectrum_direct(x, M, M3)
+            hos.bispectrum_direct(x, M, M3, overlap=ov)

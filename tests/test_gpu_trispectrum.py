@@ -96,3 +96,30 @@ def test_trispectrum_transform_sizes(hos, oracle, N):
     ref = oracle.trispectrum(x, L, N)
     got = hos.trispectrum(torch.from_numpy(x).cuda(), L, nfft=N, precision="fp32").cpu().numpy()
     assert normwise(got, ref) <= TOL["fp32"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_trispectrum_batched_matches_oracle_per_series(hos, oracle, prec):
+    """Series of uneven length (one empty, one shorter than the lag range) in
+    one call: each spectrum against the oracle, and against a single call."""
+    lens = np.array([900, 0, 2500, 40, 1700], dtype=np.int64)
+    vals, offs = hos_synth.student_t_returns(lens, 21)
+    L, N = 8, 16
+    got = hos.trispectrum_batched(torch.from_numpy(vals).cuda(), offs, L, nfft=N, precision=prec).cpu().numpy()
+    assert got.shape == (lens.size, N, N, N)
+    for s in range(lens.size):
+        x = vals[offs[s]:offs[s + 1]]
+        if x.size == 0:
+            assert np.abs(got[s]).max() == 0.0
+            continue
+        ref = oracle.trispectrum(x, L, N)
+        assert normwise(got[s], ref) <= (3 * TOL[prec] if prec == "fp32" else TOL[prec])
+        one = hos.trispectrum(torch.from_numpy(x).cuda(), L, nfft=N, precision=prec).cpu().numpy()
+        assert normwise(got[s], one) <= 2 * TOL[prec]
+
+
+def test_trispectrum_batched_rejects_simt_and_parts(hos):
+    from paper_1805_11775_gb300._native import HosError
+    v = torch.zeros(100, dtype=torch.float64, device="cuda")
+    with pytest.raises(HosError):
+        hos.trispectrum_batched(v, [0, 50, 100], 4, precision="simt")
