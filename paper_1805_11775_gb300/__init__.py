@@ -158,12 +158,69 @@ def bispectrum(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=True
     return _finish(dev, host_out, host)
 
 
+def _batched_pipelined(values, offs, L, p, out, workspace, groups):
+    """Host input and pinned host output: the series in `groups` contiguous
+    groups of about equal sample counts, each group's input copied and
+    computed on the current stream while the previous group's spectra are
+    copied to the host on a second stream (two device output buffers)."""
+    torch = _torch()
+    from .shard import series_shard
+    N = p.nfft or 2 * p.L
+    cuts = [series_shard(offs, g, groups) for g in range(groups)]
+    cuts = [(a, b) for a, b in cuts if b > a]
+    smax = max(b - a for a, b in cuts)
+    lmax = int(np.max(offs[1:] - offs[:-1])) if offs.size > 1 else 0
+    comp = torch.cuda.current_stream()
+    copy = torch.cuda.Stream()
+    bufs = [torch.empty((smax, N, N), dtype=torch.complex64, device="cuda") for _ in range(2)]
+    ws = _workspace(workspace, torch.device("cuda"))
+    ws.get(max(workspace_size(_native.OP_BISPECTRUM_BATCHED, int(offs[b] - offs[a]), b - a, lmax, p)
+               for a, b in cuts))
+    freed = [None, None]
+    for g, (a, b) in enumerate(cuts):
+        buf = bufs[g % 2]
+        if freed[g % 2] is not None:
+            comp.wait_event(freed[g % 2])  # the copy out of this buffer is done
+        vd = values[int(offs[a]):int(offs[b])].to("cuda", non_blocking=True)
+        od = torch.from_numpy(offs[a:b + 1] - offs[a]).to("cuda", non_blocking=True)
+        _native.check(_native.lib().hos_bispectrum_batched(vd.data_ptr(), _dtype_code(vd), od.data_ptr(), b - a,
+                                                           vd.numel(), lmax, ctypes.byref(p), buf.data_ptr(),
+                                                           ws.ptr(), ws.nbytes(), ctypes.c_void_p(comp.cuda_stream)),
+                      "hos_bispectrum_batched")
+        done = torch.cuda.Event()
+        done.record(comp)
+        copy.wait_event(done)
+        with torch.cuda.stream(copy):
+            out[a:b].copy_(buf[:b - a], non_blocking=True)
+        freed[g % 2] = torch.cuda.Event()
+        freed[g % 2].record(copy)
+        vd.record_stream(comp)
+    copy.synchronize()
+    comp.synchronize()
+    return out
+
+
 def bispectrum_batched(values, offsets, L, nfft=0, precision="bf16", window="parzen", remove_mean=True, tile_n=0,
-                       flush_chunks=0, out=None, workspace=None, stream=None, max_len=None):
+                       flush_chunks=0, out=None, workspace=None, stream=None, max_len=None, pipeline=4):
     """Bispectra of S series concatenated in ``values`` with ``offsets`` (S+1).
 
-    Returns (S, nfft, nfft) complex64."""
+    Returns (S, nfft, nfft) complex64.  With host ``values`` and a pinned host
+    ``out``, the series go in ``pipeline`` groups whose transfers overlap the
+    next group's compute (``pipeline=1``: one call)."""
     torch = _torch()
+    if (pipeline > 1 and out is not None and out.device.type == "cpu" and out.is_pinned()
+            and not (isinstance(values, torch.Tensor) and values.device.type == "cuda") and stream is None):
+        offs_h = np.ascontiguousarray(np.asarray(offsets.cpu() if isinstance(offsets, torch.Tensor) else offsets,
+                                                 dtype=np.int64))
+        vals_h = values if isinstance(values, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(values))
+        if vals_h.dtype not in (torch.float32, torch.float64):
+            raise TypeError("values must be float32 or float64")
+        S = offs_h.size - 1
+        if S >= 2 * pipeline:
+            tile_n, flush_chunks = _tuned("bispectrum_batched", L, vals_h.numel(), S, precision, tile_n,
+                                          flush_chunks)
+            p = make_params(L, nfft, precision, window, remove_mean, 0, tile_n, flush_chunks)
+            return _batched_pipelined(vals_h, offs_h, L, p, out, workspace, pipeline)
     vd, host = _prepare(values)
     offs = torch.as_tensor(offsets, dtype=torch.int64)
     if max_len is None:

@@ -95,8 +95,9 @@ HOS_DEV double df_to_double(DF a) { return (double)a.h + (double)a.l; }
 // double-float: the main parts in groups of 16 windows, each group a TwoSum
 // chain in window order, groups gi, gi + gsplit, ... added in that order;
 // thread row gi = 0 then adds the parts that start at a CTA boundary inside a
-// window, in CTA order.  Not divided by the length.  Loads go eight windows
+// window, in CTA order.  Not divided by the length.  Loads go BATCH windows
 // at a time.
+template <int BATCH>
 HOS_DEV void tile_share4(const float* __restrict__ partials, const TileRec& r, int tsz, int vi, int gi, int gsplit,
                          int F, const int64_t* __restrict__ bnd, int64_t total_win, DF (&acc)[4]) {
     const int64_t st4 = tsz >> 2;  // float4 per slot
@@ -113,13 +114,13 @@ HOS_DEV void tile_share4(const float* __restrict__ partials, const TileRec& r, i
     for (int f0 = 16 * gi; f0 < r.nwin && r.nwin > 1; f0 += 16 * gsplit) {
         const int cnt = (r.nwin - f0 < 16) ? r.nwin - f0 : 16;
         float hi[4] = {0.0f, 0.0f, 0.0f, 0.0f}, lo[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        for (int f = 0; f < cnt; f += 8) {
-            float4 v[8];
+        for (int f = 0; f < cnt; f += BATCH) {
+            float4 v[BATCH];
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
+            for (int u = 0; u < BATCH; ++u)
                 v[u] = (f + u < cnt) ? p4[(int64_t)(f0 + f + u) * st4] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < BATCH; ++u) {
                 const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {  // a zero term leaves (hi, lo) unchanged
@@ -235,8 +236,8 @@ HOS_DEV void emit_c3x4(const Reduce3Params& P, const float* __restrict__ wtab, i
 // series (gsplit > 1 with NV = 1); many short series take NV = 2 instead.
 // Per series: sum of its parts / its length; parts (segments) average over
 // the group.
-template <int NV>
-__global__ void __launch_bounds__(REDUCE_THREADS) reduce3_kernel(const Reduce3Params P, const int64_t* __restrict__ bnd,
+template <int NV, int BATCH>
+__global__ void __launch_bounds__(REDUCE_THREADS, BATCH >= 16 ? 2 : 3) reduce3_kernel(const Reduce3Params P, const int64_t* __restrict__ bnd,
                                                                  const TileRec* __restrict__ rec,
                                                                  const float2* __restrict__ inv_len,
                                                                  const float* __restrict__ wtab, int gsplit) {
@@ -249,13 +250,35 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce3_kernel(const Reduce3Pa
     const int s0 = P.per_series_groups ? grp : 0, s1 = P.per_series_groups ? grp + 1 : sv.S;
     const int64_t total_win = sv.win[sv.S];
     int vi[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) vi[k] = (blockIdx.x * NV + k) * es + ei;
+    if (NV > 1 && P.per_series_groups) {
+        // one window and no part starting inside (most short series): c3 = x / len,
+        // the general path's arithmetic, with all NV vector loads in flight at once
+        const TileRec r = rec[(int64_t)grp * geo.ntiles + t];
+        if (r.nwin == 1 && r.xlo >= r.xhi) {
+            const float2 il = inv_len[grp];
+            const float4* p4 = reinterpret_cast<const float4*>(P.partials + r.slot * (int64_t)tsz);
+            float4 x[NV];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) x[k] = p4[vi[k] < nvec ? vi[k] : 0];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                if (vi[k] >= nvec) continue;
+                const float xv[4] = {x[k].x, x[k].y, x[k].z, x[k].w};
+                DF v[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) v[c] = df_mul(DF{xv[c], 0.0f}, DF{il.x, il.y});
+                emit_c3x4(P, wtab, grp, t, 4 * vi[k], v);
+            }
+            return;
+        }
+    }
     DF c3[NV][4];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        vi[k] = (blockIdx.x * NV + k) * es + ei;
+    for (int k = 0; k < NV; ++k)
 #pragma unroll
         for (int c = 0; c < 4; ++c) c3[k][c] = df_zero();
-    }
     int cnt = 0;
     for (int s = s0; s < s1; ++s) {
         const TileRec r = rec[(int64_t)s * geo.ntiles + t];
@@ -264,7 +287,8 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce3_kernel(const Reduce3Pa
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             DF a[4];
-            tile_share4(P.partials, r, tsz, vi[k] < nvec ? vi[k] : 0, gi, gsplit, geo.flush, bnd, total_win, a);
+            tile_share4<BATCH>(P.partials, r, tsz, vi[k] < nvec ? vi[k] : 0, gi, gsplit, geo.flush, bnd, total_win,
+                               a);
             combine_rows4(a, ei, gi, es, gsplit, red);
 #pragma unroll
             for (int c = 0; c < 4; ++c) c3[k][c] = df_add(c3[k][c], df_mul(a[c], DF{il.x, il.y}));
@@ -304,7 +328,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS) m4_tile_reduce_kernel(const C3
     const TileRec r = rec[(int64_t)s * geo.ntiles + t];
     DF a[4] = {df_zero(), df_zero(), df_zero(), df_zero()};
     if (r.nwin > 0) {  // uniform over the block
-        tile_share4(partials, r, tsz, vi < nvec ? vi : 0, gi, gsplit, geo.flush, bnd, sv.win[sv.S], a);
+        tile_share4<8>(partials, r, tsz, vi < nvec ? vi : 0, gi, gsplit, geo.flush, bnd, sv.win[sv.S], a);
         combine_rows4(a, ei, gi, es, gsplit, red);
     }
     if (gi != 0 || vi >= nvec) return;
@@ -383,12 +407,18 @@ cudaError_t launch_reduce3(const Reduce3Params& p, int groups, int64_t max_len, 
     const int64_t nvec = (int64_t)TILE_M * p.geom.tile_n / 4;
     const int gsplit = window_split(p.geom, max_len);
     if (gsplit == 1 && ceil_div(nvec, REDUCE_THREADS) * p.geom.ntiles * groups >= 4096) {
-        // many (short) output groups: two vectors per thread
-        dim3 grid((unsigned)ceil_div(nvec, 2 * REDUCE_THREADS), (unsigned)p.geom.ntiles, (unsigned)groups);
-        reduce3_kernel<2><<<grid, REDUCE_THREADS, 0, st>>>(p, bnd, rec, inv_len, wtab, 1);
+        // many (short) output groups: four vectors per thread
+        dim3 grid((unsigned)ceil_div(nvec, 4 * REDUCE_THREADS), (unsigned)p.geom.ntiles, (unsigned)groups);
+        reduce3_kernel<4, 4><<<grid, REDUCE_THREADS, 0, st>>>(p, bnd, rec, inv_len, wtab, 1);
     } else {
         dim3 grid((unsigned)ceil_div(nvec, REDUCE_THREADS / gsplit), (unsigned)p.geom.ntiles, (unsigned)groups);
-        reduce3_kernel<1><<<grid, REDUCE_THREADS, 0, st>>>(p, bnd, rec, inv_len, wtab, gsplit);
+        // a thread row with several groups of 16 windows keeps all 16 loads of a group in flight;
+        // with one group, 8 at a time leave room for a third resident block
+        const int64_t nwin_max = ceil_div(ceil_div(max_len > 0 ? max_len : 1, p.geom.kc), p.geom.flush);
+        if (nwin_max > 16 * (int64_t)gsplit)
+            reduce3_kernel<1, 16><<<grid, REDUCE_THREADS, 0, st>>>(p, bnd, rec, inv_len, wtab, gsplit);
+        else
+            reduce3_kernel<1, 8><<<grid, REDUCE_THREADS, 0, st>>>(p, bnd, rec, inv_len, wtab, gsplit);
     }
     count_launch();
     return cudaGetLastError();

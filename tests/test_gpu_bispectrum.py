@@ -170,6 +170,21 @@ def test_batched_matches_oracle_per_series(hos, oracle):
             assert normwise(got[s], ref) <= tol[prec], (prec, s)
 
 
+def test_batched_host_pipeline_matches_one_device_call(hos):
+    """Host input with a pinned host output: series in groups whose copies
+    overlap the next group's compute; the same spectra as one device call
+    within the 3xTF32 target (the groups' contraction splits differ, so the
+    FP32 accumulation order differs)."""
+    lens = hos_synth.intraday_lengths(37, 5)
+    vals, offs = hos_synth.student_t_returns(lens, 6)
+    L, N = 16, 32
+    dev = hos.bispectrum_batched(torch.from_numpy(vals).cuda(), offs, L, precision="fp32").cpu().numpy()
+    out = torch.empty((lens.size, N, N), dtype=torch.complex64).pin_memory()
+    got = hos.bispectrum_batched(torch.from_numpy(vals).pin_memory(), offs, L, precision="fp32", out=out,
+                                 pipeline=4).numpy()
+    assert normwise(got, dev) <= TOL["fp32"]
+
+
 def test_batched_equals_single_calls(hos):
     lens = hos_synth.intraday_lengths(24, 4)
     vals, offs = hos_synth.student_t_returns(lens, 4)
