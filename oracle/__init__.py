@@ -70,6 +70,10 @@ def _load():
             lib.hos_oracle_grad_lag.argtypes = [_D, _I64, _I64, ctypes.c_int, _D]
             lib.hos_oracle_dy_at.argtypes = [_D, _I64, _I64, _D, ctypes.POINTER(_I64), _I64, _D]
             lib.hos_oracle_bispectrum_direct.argtypes = [_D, _I64, _I64, _I64, _I64, ctypes.c_int, _D]
+            lib.hos_oracle_trispectrum_grad.argtypes = [_D, _I64, _I64, _I64, ctypes.c_int, ctypes.c_int, _D, _D]
+            lib.hos_oracle_grad_lag4.argtypes = [_D, _I64, _I64, ctypes.c_int, _D]
+            lib.hos_oracle_grad_c2.argtypes = [_D, _D, _I64, _D]
+            lib.hos_oracle_dy4_at.argtypes = [_D, _I64, _I64, _D, _D, ctypes.POINTER(_I64), _I64, _D]
             _lib = lib
     return _lib
 
@@ -217,6 +221,47 @@ def dy_at(y, L: int, dc, js) -> np.ndarray:
     out = np.empty(jj.size)
     _load().hos_oracle_dy_at(_p(y), y.size, int(L), _p(dcf), jj.ctypes.data_as(ctypes.POINTER(_I64)), jj.size,
                              _p(out))
+    return out
+
+
+def trispectrum_grad(x, L: int, G, N: int = 0, window: int = WIN_PARZEN, remove_mean: bool = True) -> np.ndarray:
+    """dl/dx for a loss with dl/dRe T + i dl/dIm T = G (complex N x N x N)."""
+    x = _f64(x)
+    N = N or 2 * L
+    g = np.ascontiguousarray(np.asarray(G, dtype=np.complex128).reshape(N, N, N)).view(np.float64).ravel()
+    out = np.empty_like(x)
+    _load().hos_oracle_trispectrum_grad(_p(x), x.size, int(L), int(N), int(window), int(bool(remove_mean)),
+                                        _p(np.ascontiguousarray(g)), _p(out))
+    return out
+
+
+def grad_lag4(G, L: int, N: int, window: int = WIN_PARZEN) -> np.ndarray:
+    """dl/dc4 over [-L, L]^3 for dl/dRe T + i dl/dIm T = G (complex N^3)."""
+    g = np.ascontiguousarray(np.asarray(G, dtype=np.complex128).reshape(N, N, N)).view(np.float64).ravel()
+    W = 2 * L + 1
+    out = np.empty(W ** 3)
+    _load().hos_oracle_grad_lag4(_p(np.ascontiguousarray(g)), int(L), int(N), int(window), _p(out))
+    return out.reshape(W, W, W)
+
+
+def grad_c2(dc4, c2v, L: int) -> np.ndarray:
+    """dl/dc2(t), t in [-2L, 2L], from dl/dc4 over [-L, L]^3 and c2 over [-2L, 2L]."""
+    d = _f64(dc4)
+    c = _f64(c2v)
+    out = np.empty(4 * L + 1)
+    _load().hos_oracle_grad_c2(_p(d), _p(c), int(L), _p(out))
+    return out
+
+
+def dy4_at(y, L: int, dc4, dc2, js) -> np.ndarray:
+    """Trispectrum gradient with respect to the mean-removed samples y at indices js."""
+    y = _f64(y)
+    d4 = _f64(dc4)
+    d2 = _f64(dc2)
+    jj = np.ascontiguousarray(np.asarray(js, dtype=np.int64))
+    out = np.empty(jj.size)
+    _load().hos_oracle_dy4_at(_p(y), y.size, int(L), _p(d4), _p(d2), jj.ctypes.data_as(ctypes.POINTER(_I64)),
+                              jj.size, _p(out))
     return out
 
 

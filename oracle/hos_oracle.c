@@ -1,7 +1,7 @@
 /*
  * hos_oracle.c -- plain FP64 CPU statement of the smoothed sample bispectrum
  * and trispectrum computed the indirect way (sample cumulant -> lag window ->
- * Fourier transform), of the exact gradient of the bispectrum, and of the
+ * Fourier transform), of the exact gradients of both, and of the
  * paper's direct method (Algorithm DBS: part DFTs, raw triple products, box
  * smoothing, average over parts).
  *
@@ -480,6 +480,180 @@ void hos_oracle_dy_at(const double* y, int64_t n, int64_t L, const double* dc, c
 #undef YV
                 acc += g * term;
             }
+        out[q] = acc / (double)n;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Gradient of a real loss l(T) through the trispectrum (one part, K = 1).
+ * Step 1 alone: dl/dc4(w) on [-L, L]^3 for G = dl/dRe T + i dl/dIm T on the
+ * N^3 grid,
+ *   W(w) (2 pi)^-3 Re sum_k G(k) e^{+i 2 pi k.w / N},
+ * the triple sum over k taken one axis at a time (k3, then k2, then k1).    */
+void hos_oracle_grad_lag4(const double* G, int64_t L, int64_t N, int window, double* dc)
+{
+    const int64_t W = 2 * L + 1;
+    /* t3[k1][k2][w3], t2[k1][w2][w3]: complex */
+    double* t3 = (double*)calloc((size_t)(N * N * W * 2), sizeof(double));
+    double* t2 = (double*)calloc((size_t)(N * W * W * 2), sizeof(double));
+    for (int64_t k1 = 0; k1 < N; ++k1)
+        for (int64_t k2 = 0; k2 < N; ++k2)
+            for (int64_t c = 0; c < W; ++c) {
+                double re = 0.0, im = 0.0;
+                for (int64_t k3 = 0; k3 < N; ++k3) {
+                    double cs, sn;
+                    phase(k3, c - L, N, +1.0, &cs, &sn);
+                    const double* g = G + ((k1 * N + k2) * N + k3) * 2;
+                    re += g[0] * cs - g[1] * sn;
+                    im += g[0] * sn + g[1] * cs;
+                }
+                t3[((k1 * N + k2) * W + c) * 2] = re;
+                t3[((k1 * N + k2) * W + c) * 2 + 1] = im;
+            }
+    for (int64_t k1 = 0; k1 < N; ++k1)
+        for (int64_t b = 0; b < W; ++b)
+            for (int64_t c = 0; c < W; ++c) {
+                double re = 0.0, im = 0.0;
+                for (int64_t k2 = 0; k2 < N; ++k2) {
+                    double cs, sn;
+                    phase(k2, b - L, N, +1.0, &cs, &sn);
+                    const double* t = t3 + ((k1 * N + k2) * W + c) * 2;
+                    re += t[0] * cs - t[1] * sn;
+                    im += t[0] * sn + t[1] * cs;
+                }
+                t2[((k1 * W + b) * W + c) * 2] = re;
+                t2[((k1 * W + b) * W + c) * 2 + 1] = im;
+            }
+    const double s = 2.0 * HOS_ORACLE_PI, scale = 1.0 / (s * s * s);
+    for (int64_t a = 0; a < W; ++a)
+        for (int64_t b = 0; b < W; ++b)
+            for (int64_t c = 0; c < W; ++c) {
+                double re = 0.0;
+                for (int64_t k1 = 0; k1 < N; ++k1) {
+                    double cs, sn;
+                    phase(k1, a - L, N, +1.0, &cs, &sn);
+                    const double* t = t2 + ((k1 * W + b) * W + c) * 2;
+                    re += t[0] * cs - t[1] * sn;
+                }
+                dc[(a * W + b) * W + c] = hos_oracle_window3(a - L, b - L, c - L, L, window) * scale * re;
+            }
+    free(t3);
+    free(t2);
+}
+
+/* Step 2 of the gradient: dl/dc2(t), t in [-2L, 2L], from dl/dc4 and c2
+ * through the three product terms of hos_oracle_c4; each term
+ * c2(a) c2(b) sends dc4 * c2(b) to c2(a) and dc4 * c2(a) to c2(b).
+ * dc2 has 4L + 1 entries, index t + 2L.                                     */
+void hos_oracle_grad_c2(const double* dc4, const double* c2, int64_t L, double* dc2)
+{
+    const int64_t W = 2 * L + 1, T = 2 * L;
+    for (int64_t t = 0; t < 2 * T + 1; ++t) dc2[t] = 0.0;
+    for (int64_t w1 = -L; w1 <= L; ++w1)
+        for (int64_t w2 = -L; w2 <= L; ++w2)
+            for (int64_t w3 = -L; w3 <= L; ++w3) {
+                const double g = dc4[((w1 + L) * W + (w2 + L)) * W + (w3 + L)];
+                if (g == 0.0) continue;
+                const int64_t a[3] = {w1, w2, w3}, b[3] = {w3 - w2, w3 - w1, w2 - w1};
+                for (int q = 0; q < 3; ++q) {
+                    dc2[a[q] + T] -= g * c2[b[q] + T];
+                    dc2[b[q] + T] -= g * c2[a[q] + T];
+                }
+            }
+}
+
+/* Gradient of a real loss l(T) through the trispectrum (one part, K = 1),
+ * G = dl/dRe T + i dl/dIm T on the N^3 grid.  The chain rule in reverse
+ * order of the forward:
+ *   1. dl/dc4 through the transform and window (hos_oracle_grad_lag4);
+ *   2. through c4 = m4 - (three c2 c2 terms): dl/dm4 = dl/dc4, and dl/dc2
+ *      from hos_oracle_grad_c2;
+ *   3. through the m4 loop: every term y(i) y(a) y(b) y(c) / n sends its
+ *      partial derivative to each of its four samples;
+ *   4. through the c2 loop: every term y(i) y(i+t) / n sends its partial to
+ *      both samples;
+ *   5. through the mean removal: dx = dy - mean(dy).                        */
+void hos_oracle_trispectrum_grad(const double* x, int64_t n, int64_t L, int64_t N, int window, int remove_mean,
+                                 const double* G, double* dx)
+{
+    const int64_t W = 2 * L + 1, T = 2 * L;
+    double* y = (double*)malloc(sizeof(double) * (size_t)n);
+    double* dc4 = (double*)malloc(sizeof(double) * (size_t)(W * W * W));
+    double* c2 = (double*)malloc(sizeof(double) * (size_t)(2 * T + 1));
+    double* dc2 = (double*)malloc(sizeof(double) * (size_t)(2 * T + 1));
+    double* dy = (double*)calloc((size_t)n, sizeof(double));
+    hos_oracle_demean(x, n, n, remove_mean, y);
+    hos_oracle_grad_lag4(G, L, N, window, dc4);
+    hos_oracle_c2(y, n, T, c2);
+    hos_oracle_grad_c2(dc4, c2, L, dc2);
+    for (int64_t w1 = -L; w1 <= L; ++w1)
+        for (int64_t w2 = -L; w2 <= L; ++w2)
+            for (int64_t w3 = -L; w3 <= L; ++w3) {
+                const double g = dc4[((w1 + L) * W + (w2 + L)) * W + (w3 + L)] / (double)n;
+                if (g == 0.0) continue;
+                for (int64_t i = 0; i < n; ++i) {
+                    const int64_t a = i + w1, b = i + w2, c = i + w3;
+                    if (a < 0 || a >= n || b < 0 || b >= n || c < 0 || c >= n) continue;
+                    dy[i] += g * y[a] * y[b] * y[c];
+                    dy[a] += g * y[i] * y[b] * y[c];
+                    dy[b] += g * y[i] * y[a] * y[c];
+                    dy[c] += g * y[i] * y[a] * y[b];
+                }
+            }
+    for (int64_t t = -T; t <= T; ++t) {
+        const double g = dc2[t + T] / (double)n;
+        if (g == 0.0) continue;
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t a = i + t;
+            if (a < 0 || a >= n) continue;
+            dy[i] += g * y[a];
+            dy[a] += g * y[i];
+        }
+    }
+    double mu = 0.0;
+    if (remove_mean) {
+        for (int64_t i = 0; i < n; ++i) mu += dy[i];
+        mu /= (double)n;
+    }
+    for (int64_t i = 0; i < n; ++i) dx[i] = dy[i] - mu;
+    free(y);
+    free(dc4);
+    free(c2);
+    free(dc2);
+    free(dy);
+}
+
+/* Steps 2-4 of the trispectrum gradient at chosen samples j (no mean
+ * removal), for series too long for the full loops:
+ *   dy(j) = (1/n) sum_w dc4(w) [ y(j+w1) y(j+w2) y(j+w3)
+ *            + y(j-w1) y(j-w1+w2) y(j-w1+w3) + y(j-w2) y(j-w2+w1) y(j-w2+w3)
+ *            + y(j-w3) y(j-w3+w1) y(j-w3+w2) ]
+ *         + (1/n) sum_t dc2(t) [ y(j+t) + y(j-t) ],
+ * the four places sample j can occupy in a product of the m4 loop and the
+ * two in a product of the c2 loop (samples outside [0, n) are zero).
+ * dc2 is hos_oracle_grad_c2 of dc4 and the series' c2.                      */
+void hos_oracle_dy4_at(const double* y, int64_t n, int64_t L, const double* dc4, const double* dc2,
+                       const int64_t* js, int64_t count, double* out)
+{
+    const int64_t W = 2 * L + 1, T = 2 * L;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < count; ++q) {
+        const int64_t j = js[q];
+        double acc = 0.0;
+#define YV(k) (((k) >= 0 && (k) < n) ? y[(k)] : 0.0)
+        for (int64_t w1 = -L; w1 <= L; ++w1)
+            for (int64_t w2 = -L; w2 <= L; ++w2)
+                for (int64_t w3 = -L; w3 <= L; ++w3) {
+                    const double g = dc4[((w1 + L) * W + (w2 + L)) * W + (w3 + L)];
+                    if (g == 0.0) continue;
+                    double term = YV(j + w1) * YV(j + w2) * YV(j + w3);
+                    term += YV(j - w1) * YV(j - w1 + w2) * YV(j - w1 + w3);
+                    term += YV(j - w2) * YV(j - w2 + w1) * YV(j - w2 + w3);
+                    term += YV(j - w3) * YV(j - w3 + w1) * YV(j - w3 + w2);
+                    acc += g * term;
+                }
+        for (int64_t t = -T; t <= T; ++t) acc += dc2[t + T] * (YV(j + t) + YV(j - t));
+#undef YV
         out[q] = acc / (double)n;
     }
 }
