@@ -228,6 +228,18 @@ def m4_flops(L, n, prec):
     return rows * w3 * kpad * 2, f"{rows} lag pairs x {w3} w3 x {kpad} samples x 2 flops (FFMA)"
 
 
+def adjoint4_flops(L, n):
+    """Executed flops of the trispectrum adjoint contraction
+    D[u, (w1, w2)] = sum_w3 y(u + w3) Gs(w1, w2, w3) (split-bf16): blocks of 128
+    (w1, w2) combinations x 128-row u tiles x 2L rounded to 16 lags w3 x 3
+    products x 2."""
+    two_l = 2 * L
+    kpad = 16 * math.ceil(two_l / 16)
+    nb, nut = math.ceil(two_l * two_l / 128), math.ceil(n / 128)
+    return nb * nut * 128 * 128 * kpad * 6, (
+        f"{nb} (w1, w2) blocks x {nut} u tiles x 128 x 128 x {kpad} lags w3 x 3 products x 2 flops")
+
+
 def adjoint_flops(L, n, prec):
     """Executed flops of the adjoint contraction U = Hankel(y) Gs.  Tensor
     cores (split-bf16, L <= 128): 128-row tiles of u x 128-lag blocks of w1
@@ -408,6 +420,44 @@ def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
         return dict(step=step, e2e=e2e, units=units_of(x_host.size, L), flops=flops, work=work,
                     h2d=x_host.nbytes, d2h=x_host.nbytes,
                     bound="tensor" if (prec == "bf16" and L <= 128) else "alu",
+                    config={"n": int(x_host.size), "L": L, "grid": N, "step": "forward + adjoint"})
+    if name == "differentiable_trispectrum_n65536_L32":
+        x_host, t_host = w["x"], w["target_x"]
+        xd = torch.from_numpy(x_host).cuda()
+        Tt = hos.trispectrum(torch.from_numpy(t_host).cuda(), L)
+        out = torch.empty((N, N, N), dtype=torch.complex64, device="cuda")
+        ws2 = hos.Workspace()
+        last_g = {}
+
+        def step():
+            T = hos.trispectrum(xd, L, out=out, workspace=ws)
+            G = 2.0 * (T - Tt)  # gradient of sum |T - Tt|^2
+            last_g["G"] = G
+            return hos.trispectrum_backward(xd, G, L, workspace=ws2)
+
+        x_pin = torch.from_numpy(x_host).pin_memory()
+
+        def e2e():
+            xg = x_pin.to("cuda", non_blocking=True)
+            T = hos.trispectrum(xg, L, workspace=ws)
+            return hos.trispectrum_backward(xg, 2.0 * (T - Tt), L, workspace=ws2).cpu()
+
+        def acc():
+            import oracle
+            G = last_g["G"]
+            dx = hos.trispectrum_backward(xd, G, L, remove_mean=False).cpu().numpy()
+            x64 = x_host.astype(np.float64)
+            dc4 = oracle.grad_lag4(G.cpu().numpy().astype(np.complex128), L, N)
+            dc2 = oracle.grad_c2(dc4, oracle.c2(x64, 2 * L), L)
+            js = np.concatenate([[0, 1, x64.size - 1], np.random.default_rng(9).integers(0, x64.size, 13)])
+            ref = oracle.dy4_at(x64, L, dc4, dc2, js)
+            return {"vs": "FP64 oracle", "quantity": "dl/dx (mean removal off, same dl/dT)",
+                    "max_rel_err": float(np.abs(dx[js] - ref).max() / np.abs(ref).max()),
+                    "sample": f"{js.size} samples incl. both ends"}
+
+        flops, work = adjoint4_flops(L, x_host.size)
+        return dict(step=step, e2e=e2e, accuracy=acc, units=units_of(x_host.size, L, k=4), flops=flops, work=work,
+                    h2d=x_host.nbytes, d2h=x_host.nbytes, bound="tensor",
                     config={"n": int(x_host.size), "L": L, "grid": N, "step": "forward + adjoint"})
     raise KeyError(name)
 
@@ -603,7 +653,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "bispectrum_n2048_L32", "trispectrum_n65536_L32", "batched_4096x_L128",
-                             "differentiable_n262144_L128", "direct_bispectrum_n8192_M3_279"])
+                             "differentiable_n262144_L128", "differentiable_trispectrum_n65536_L32",
+                             "direct_bispectrum_n8192_M3_279"])
     ap.add_argument("--graph", action="store_true", help="capture one step in a CUDA graph and replay it")
     ap.add_argument("--series", type=int, default=0, help="batched workload: use only the first K series")
     ap.add_argument("--time-slices", action="store_true",

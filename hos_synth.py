@@ -91,4 +91,7 @@ def workload(name: str, small: bool = False):
         n = 1 << 18 if not small else 4096
         return {"x": ar2(n, 1005).astype(np.float32), "target_x": ar2(n, 2005).astype(np.float32),
                 "L": 128, "N": 256}
+    if name == "differentiable_trispectrum_n65536_L32":
+        n = 65536 if not small else 4096
+        return {"x": ma(n, 1006).astype(np.float32), "target_x": ma(n, 2006).astype(np.float32), "L": 32, "N": 64}
     raise KeyError(name)

@@ -92,7 +92,8 @@ typedef enum {
     HOS_OP_SERIES_SUM = 6,
     HOS_OP_CUMULANT3_SLICE = 7,
     HOS_OP_BISPECTRUM_FROM_C3 = 8,
-    HOS_OP_TRISPECTRUM_BATCHED = 9
+    HOS_OP_TRISPECTRUM_BATCHED = 9,
+    HOS_OP_TRISPECTRUM_BACKWARD = 10
 } hos_op;
 
 typedef struct {
@@ -161,6 +162,23 @@ hos_status hos_trispectrum_batched(const void* d_x, int32_t dtype, const int64_t
  * the triple-product loop's derivative; the mean-removal adjoint.          */
 hos_status hos_bispectrum_backward(const void* d_x, int32_t dtype, int64_t n, const hos_params* params,
                                    const void* d_dB, void* d_dx, void* ws, size_t ws_bytes, hos_stream_t stream);
+
+/* Adjoint of hos_trispectrum (one part only, segment_len = 0; L <= 64;
+ * window PARZEN or RECT; precision SPLIT_BF16 only -- anything else returns
+ * HOS_ERR_UNSUPPORTED): the gradient of a real loss l through T.
+ *   d_dT : nfft^3 complex64 holding dl/dRe T + i dl/dIm T, [k1][k2][k3]
+ *   d_dx : n values, same dtype as d_x, receives dl/dx (overwritten)
+ * Steps, the chain rule in reverse through the forward (the Problem
+ * Statement's trispectrum as the transform of the windowed c4): adjoint
+ * 3-D transform and window, symmetrised over the six orders of the lags;
+ * through c4 = m4 - (three c2 c2 products), dl/dc2; the fourth-moment
+ * loop's derivative as one tensor-core contraction
+ * D[u, (w1, w2)] = sum_w3 y(u + w3) Gs(w1, w2, w3) whose epilogue forms
+ * E(u, w1) = sum_w2 D y(u + w2) and the two gradient terms; the c2 loop's
+ * derivative; the mean-removal adjoint.  Workspace grows as
+ * ((2L)^2 / 128) * n * 4 bytes for the per-block row partials.            */
+hos_status hos_trispectrum_backward(const void* d_x, int32_t dtype, int64_t n, const hos_params* params,
+                                    const void* d_dT, void* d_dx, void* ws, size_t ws_bytes, hos_stream_t stream);
 
 /* Third-order sample cumulant, unwindowed, FP64.
  *   d_c3 : (2L)*(2L) doubles, row-major [w1+L][w2+L], w in [-L, L-1]

@@ -20,8 +20,10 @@ import numpy as np
 from . import _native
 from ._native import HosError, HosParams
 
-__all__ = ["bispectrum", "bispectrum_batched", "trispectrum", "cumulant3", "cumulant4", "BispectrumFn",
-           "bispectrum_ad", "Workspace", "workspace_size", "device_status", "reset_device_status",
+__all__ = ["bispectrum", "bispectrum_batched", "trispectrum", "trispectrum_batched", "cumulant3", "cumulant4",
+           "bispectrum_backward", "trispectrum_backward", "BispectrumFn", "TrispectrumFn", "bispectrum_ad",
+           "trispectrum_ad", "bispectrum_direct", "series_sum", "cumulant3_slice", "bispectrum_from_cumulant",
+           "bispectrum_sharded", "Workspace", "workspace_size", "device_status", "reset_device_status",
            "selftest_timeout", "set_profiling", "stage_times", "launch_count", "last_contraction", "HosError",
            "PRECISIONS", "WINDOWS"]
 
@@ -448,6 +450,55 @@ class BispectrumFn:
 def bispectrum_ad(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=True):
     """Differentiable bispectrum (torch autograd)."""
     return BispectrumFn.get().apply(x, L, nfft, precision, window, remove_mean)
+
+
+def trispectrum_backward(x, dT, L, nfft=0, precision="bf16", window="parzen", remove_mean=True, workspace=None,
+                         stream=None):
+    """dl/dx given dT = dl/dRe T + i dl/dIm T (nfft^3).  Split-bf16 tensor-core
+    adjoint only (precision "bf16"), L <= 64, one part."""
+    torch = _torch()
+    xd, host = _prepare(x)
+    p = make_params(L, nfft, precision, window, remove_mean, 0)
+    g = dT.to(xd.device).to(torch.complex64).contiguous()
+    dx = torch.empty_like(xd)
+    ws = _workspace(workspace, xd.device)
+    ws.get(workspace_size(_native.OP_TRISPECTRUM_BACKWARD, xd.numel(), 1, xd.numel(), p))
+    _native.check(_native.lib().hos_trispectrum_backward(xd.data_ptr(), _dtype_code(xd), xd.numel(),
+                                                         ctypes.byref(p), g.data_ptr(), dx.data_ptr(), ws.ptr(),
+                                                         ws.nbytes(), _stream(stream)), "hos_trispectrum_backward")
+    return dx.cpu() if host else dx
+
+
+class TrispectrumFn:
+    """torch.autograd.Function wrapper of the trispectrum, created lazily."""
+    _cls = None
+
+    @classmethod
+    def get(cls):
+        if cls._cls is None:
+            torch = _torch()
+
+            class _Fn(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, x, L, nfft, precision, window, remove_mean):
+                    ctx.save_for_backward(x)
+                    ctx.cfg = (L, nfft, precision, window, remove_mean)
+                    return trispectrum(x, L, nfft, precision, window, remove_mean)
+
+                @staticmethod
+                def backward(ctx, gT):
+                    (x,) = ctx.saved_tensors
+                    L, nfft, precision, window, remove_mean = ctx.cfg
+                    dx = trispectrum_backward(x, gT, L, nfft, precision, window, remove_mean)
+                    return dx, None, None, None, None, None
+
+            cls._cls = _Fn
+        return cls._cls
+
+
+def trispectrum_ad(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=True):
+    """Differentiable trispectrum (torch autograd; split-bf16 forward and adjoint)."""
+    return TrispectrumFn.get().apply(x, L, nfft, precision, window, remove_mean)
 
 
 def device_status(workspace=None) -> int:

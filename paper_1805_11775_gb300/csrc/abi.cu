@@ -93,11 +93,15 @@ static hos_status check_params(const hos_params* p, int op) {
     if (p->tile_n != 0 && p->tile_n != 32 && p->tile_n != 64 && p->tile_n != 128 && p->tile_n != 256)
         return HOS_ERR_INVALID_ARG;
     if (p->flush_chunks < 0) return HOS_ERR_INVALID_ARG;
-    if (op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT4 || op == HOS_OP_TRISPECTRUM_BATCHED) {
+    if (op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT4 || op == HOS_OP_TRISPECTRUM_BATCHED ||
+        op == HOS_OP_TRISPECTRUM_BACKWARD) {
         if (p->L > 64) return HOS_ERR_UNSUPPORTED;
         if (p->window == HOS_WIN_PARZEN_SYM) return HOS_ERR_UNSUPPORTED;
     }
-    if (op == HOS_OP_BISPECTRUM_BACKWARD && p->segment_len != 0) return HOS_ERR_UNSUPPORTED;
+    if ((op == HOS_OP_BISPECTRUM_BACKWARD || op == HOS_OP_TRISPECTRUM_BACKWARD) && p->segment_len != 0)
+        return HOS_ERR_UNSUPPORTED;
+    // the trispectrum adjoint runs on the split-bf16 tensor-core contraction only
+    if (op == HOS_OP_TRISPECTRUM_BACKWARD && p->precision != HOS_PREC_SPLIT_BF16) return HOS_ERR_UNSUPPORTED;
     if ((op == HOS_OP_BISPECTRUM_BATCHED || op == HOS_OP_TRISPECTRUM_BATCHED) && p->segment_len != 0)
         return HOS_ERR_INVALID_ARG;
     return HOS_OK;
@@ -643,6 +647,53 @@ static hos_status make_planb(const hos_params* p, int64_t n, PlanB& P) {
     return HOS_OK;
 }
 
+// ---- trispectrum adjoint -------------------------------------------------------------
+struct PlanB4 {
+    C3Geom g;
+    int Nf, nslices;
+    size_t status, off, pad, unit, win, mean, mpart, y32, hi, lo, c2, gc, gs, gsb, gc2, t1, t2p, gbuf, gmean, gmpart,
+        tw, total;
+};
+
+static hos_status make_planb4(const hos_params* p, int64_t n, PlanB4& P) {
+    hos_status s = check_params(p, HOS_OP_TRISPECTRUM_BACKWARD);
+    if (s != HOS_OK) return s;
+    const int L = p->L, twoL = 2 * L;
+    P.g = make_geom(p, 1);
+    // the adjoint reads windows up to 2L + 256 samples past a row tile
+    if (P.g.pad_tail < twoL + 320) P.g.pad_tail = twoL + 320;
+    P.Nf = p->nfft ? p->nfft : twoL;
+    P.nslices = (int)ceil_div(n, 8192);
+    if (P.nslices > 256) P.nslices = 256;
+    if (P.nslices < 1) P.nslices = 1;
+    const int64_t plane_len = n + ((int64_t)L + KC + P.g.pad_tail + 64);
+    const int64_t N3 = (int64_t)P.Nf * P.Nf * P.Nf;
+    size_t o = 0;
+    P.status = o; o = al256(o + 256);
+    P.off = o; o = al256(o + 16);
+    P.pad = o; o = al256(o + 16);
+    P.unit = o; o = al256(o + 16);
+    P.win = o; o = al256(o + 16);
+    P.mean = o; o = al256(o + 8);
+    P.mpart = o; o = al256(o + 8 * (size_t)P.nslices);
+    P.y32 = o; o = al256(o + 4 * (size_t)plane_len);
+    P.hi = o; o = al256(o + 2 * (size_t)plane_len + 64);
+    P.lo = o; o = al256(o + 2 * (size_t)plane_len + 64);
+    P.c2 = o; o = al256(o + 8 * (size_t)(4 * L - 1));
+    P.gc = o; o = al256(o + 8 * (size_t)N3);
+    P.gs = o; o = al256(o + 4 * (size_t)twoL * twoL * twoL);
+    P.gsb = o; o = al256(o + adjoint_tc_gs_bytes(L, 4));
+    P.gc2 = o; o = al256(o + 8 * (size_t)(4 * L - 1));
+    P.t1 = o; o = al256(o + 4 * adjoint_tc_t1_floats(L, n, 4));
+    P.t2p = o; o = al256(o + 4 * adjoint_tc_t2_floats(L, n, 4));
+    P.gbuf = o; o = al256(o + 4 * (size_t)n);
+    P.gmean = o; o = al256(o + 8);
+    P.gmpart = o; o = al256(o + 8 * (size_t)P.nslices);
+    P.tw = o; o = al256(o + 8 * (size_t)P.Nf);
+    P.total = o;
+    return HOS_OK;
+}
+
 }  // namespace hos
 
 using namespace hos;
@@ -670,7 +721,14 @@ const char* hos_last_contraction(void) { return g_last_contraction; }
 hos_status hos_workspace_size(int32_t op, int64_t n_total, int32_t n_series, int64_t max_len, const hos_params* p,
                               size_t* bytes) {
     if (!bytes || n_total < 0 || n_series < 1 || max_len < 0) return HOS_ERR_INVALID_ARG;
-    if (op < 0 || op > HOS_OP_TRISPECTRUM_BATCHED) return HOS_ERR_INVALID_ARG;
+    if (op < 0 || op > HOS_OP_TRISPECTRUM_BACKWARD) return HOS_ERR_INVALID_ARG;
+    if (op == HOS_OP_TRISPECTRUM_BACKWARD) {
+        PlanB4 P4;
+        hos_status s4 = make_planb4(p, n_total, P4);
+        if (s4 != HOS_OK) return s4;
+        *bytes = P4.total;
+        return HOS_OK;
+    }
     if (op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT4 || op == HOS_OP_TRISPECTRUM_BATCHED) {
         Plan4 P4;
         hos_status s4 = make_plan4(op, p, n_total, P4, n_series, max_len);
@@ -960,6 +1018,63 @@ hos_status hos_bispectrum_backward(const void* d_x, int32_t dtype, int64_t n, co
                                     at<float>(ws, P.t2p), g, st));
         g_last_contraction = "adjoint_simt_fp32";
     }
+    tr.mark("reduce");
+    HOS_CUDA_TRY(launch_mean(g, HOS_F32, off, 1, P.nslices, at<double>(ws, P.gmpart), p->remove_mean,
+                             at<double>(ws, P.gmean), st));
+    HOS_CUDA_TRY(launch_adjoint_finish(g, n, at<double>(ws, P.gmean), p->remove_mean, dtype, d_dx, st));
+    tr.mark("");
+    return HOS_OK;
+}
+
+hos_status hos_trispectrum_backward(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, const void* d_dT,
+                                    void* d_dx, void* ws, size_t ws_bytes, hos_stream_t stream) {
+    if (!d_x || !d_dT || !d_dx || n < 1 || (dtype != HOS_F32 && dtype != HOS_F64)) return HOS_ERR_INVALID_ARG;
+    PlanB4 P;
+    hos_status s = make_planb4(p, n, P);
+    if (s != HOS_OK) return s;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < P.total) return HOS_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Tracer tr(st);
+    int64_t* off = at<int64_t>(ws, P.off);
+    int64_t* pad = at<int64_t>(ws, P.pad);
+    float* y32 = at<float>(ws, P.y32);
+    const int L = p->L, Nf = P.Nf;
+    tr.mark("prep");
+    HOS_CUDA_TRY(launch_plan_series(0, n, 0, nullptr, 1, L, 1, 16, KC, P.g.pad_tail, off, pad,
+                                    at<int64_t>(ws, P.unit), at<int64_t>(ws, P.win), st));
+    HOS_CUDA_TRY(launch_mean(d_x, dtype, off, 1, P.nslices, at<double>(ws, P.mpart), p->remove_mean,
+                             at<double>(ws, P.mean), st));
+    int bx = (int)ceil_div((int64_t)L + n + KC + P.g.pad_tail + 64, 256 * 4);
+    if (bx > 65535) bx = 65535;
+    void* hi = at<void>(ws, P.hi);
+    void* lo = at<void>(ws, P.lo);
+    HOS_CUDA_TRY(launch_planes(d_x, dtype, off, pad, at<double>(ws, P.mean), L, 1, y32, hi, lo, 1, bx, st));
+    double* c2 = at<double>(ws, P.c2);
+    HOS_CUDA_TRY(launch_c2(y32, off, pad, 1, L, c2, st));
+    tr.mark("transform");
+    // adjoint transform: Gc(w mod N) = sum_k G(k) e^{+i 2 pi k.w / N}, one axis at a time
+    float2* tw = at<float2>(ws, P.tw);
+    float2* gc = at<float2>(ws, P.gc);
+    const int64_t N = Nf, N2 = N * N;
+    HOS_CUDA_TRY(launch_twiddles(Nf, tw, st));
+    LineGeom g3 = line_geom(Nf, N2, 1, N, 1);  // along k3 (contiguous)
+    HOS_CUDA_TRY(launch_lines(false, d_dT, gc, g3, tw, +1, 1.0f, st));
+    LineGeom g2 = line_geom(Nf, N2, N, N2, N);  // along k2
+    HOS_CUDA_TRY(launch_lines(false, gc, gc, g2, tw, +1, 1.0f, st));
+    LineGeom g1 = line_geom(Nf, N2, N2, N2 * N, N2);  // along k1
+    HOS_CUDA_TRY(launch_lines(false, gc, gc, g1, tw, +1, 1.0f, st));
+    tr.mark("contract");
+    const double pi = 3.14159265358979323846;
+    const double scale = 1.0 / (8.0 * pi * pi * pi * (double)n);
+    float* gs4 = at<float>(ws, P.gs);
+    double* gc2 = at<double>(ws, P.gc2);
+    float* g = at<float>(ws, P.gbuf);
+    HOS_CUDA_TRY(launch_gs4(gc, Nf, L, p->window, scale, gs4, st));
+    HOS_CUDA_TRY(launch_gc2(gs4, c2, L, gc2, st));
+    HOS_CUDA_TRY(launch_adjoint4_tc(y32, reinterpret_cast<const uint16_t*>(hi), reinterpret_cast<const uint16_t*>(lo),
+                                    n, L, gs4, at<uint8_t>(ws, P.gsb), at<float>(ws, P.t1), at<float>(ws, P.t2p), gc2,
+                                    g, at<int>(ws, P.status), wait_limit_ns(), sm_count(), st));
+    g_last_contraction = "adjoint4_tcgen05_split_bf16";
     tr.mark("reduce");
     HOS_CUDA_TRY(launch_mean(g, HOS_F32, off, 1, P.nslices, at<double>(ws, P.gmpart), p->remove_mean,
                              at<double>(ws, P.gmean), st));

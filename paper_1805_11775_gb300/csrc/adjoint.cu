@@ -173,6 +173,91 @@ cudaError_t launch_gs(const float2* Gc, int N, int L, int window, double scale, 
     return cudaGetLastError();
 }
 
+// ---- fourth order ----------------------------------------------------------------
+// Gs4[((w1+L)*2L + (w2+L))*2L + (w3+L)] = scale W(w) (1/6) sum over the six
+// orders of (w1, w2, w3) of Re Gc[a mod N][b mod N][c mod N]: the lag-domain
+// gradient of c4 (adjoint transform, window, 1/n folded into scale),
+// symmetrised because c4 is symmetric in its three lags.
+__global__ void gs4_kernel(const float2* __restrict__ Gc, int N, int L, int window, float scale,
+                           float* __restrict__ Gs4) {
+    // per-lag window factor d(w) (RECT: 0 at w = -L), in FP32 like the forward's grid
+    __shared__ float wsh[2 * 64];
+    const int twoL = 2 * L;
+    for (int i = threadIdx.x; i < twoL; i += blockDim.x)
+        wsh[i] = (window == HOS_WIN_RECT) ? (i == 0 ? 0.0f : 1.0f) : (float)parzen(i - L, L);
+    __syncthreads();
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)twoL * twoL * twoL) return;
+    const int w3 = (int)(e % twoL) - L;
+    const int w2 = (int)((e / twoL) % twoL) - L;
+    const int w1 = (int)(e / ((int64_t)twoL * twoL)) - L;
+    auto re = [&](int a, int b, int c) -> float {
+        const int ka = a < 0 ? a + N : a, kb = b < 0 ? b + N : b, kc = c < 0 ? c + N : c;  // N >= 2L
+        return Gc[((int64_t)ka * N + kb) * N + kc].x;
+    };
+    const float sym = ((re(w1, w2, w3) + re(w1, w3, w2)) + (re(w2, w1, w3) + re(w2, w3, w1))) +
+                      (re(w3, w1, w2) + re(w3, w2, w1));
+    const float wv = wsh[w1 + L] * wsh[w2 + L] * wsh[w3 + L];
+    Gs4[e] = sym * (scale * wv * (1.0f / 6.0f));
+}
+
+// dl/dc2(t) (times 1/n, which Gs4 carries) through the three c2 c2 products of
+// c4(w) = m4(w) - c2(w1) c2(w3-w2) - c2(w2) c2(w3-w1) - c2(w3) c2(w2-w1):
+// each product c2(a) c2(b) sends -Gs4(w) c2(b) to c2(a) and -Gs4(w) c2(a) to
+// c2(b).  One block per t in [-(2L-1), 2L-1]; the six sums over the lag
+// planes where a or b equals t, per thread in FP64, then a fixed tree.
+constexpr int GC2_THREADS = 256;
+__global__ void __launch_bounds__(GC2_THREADS) gc2_kernel(const float* __restrict__ Gs4, const double* __restrict__ c2,
+                                                          int L, double* __restrict__ gc2) {
+    __shared__ double red[GC2_THREADS];
+    __shared__ float cs[4 * 64];
+    const int twoL = 2 * L, T = 2 * L - 1;
+    for (int i = threadIdx.x; i < 2 * T + 1; i += GC2_THREADS) cs[i] = (float)c2[i];
+    __syncthreads();
+    const int t = (int)blockIdx.x - T;
+    const float* c = cs + T;  // c[d], |d| <= T
+    auto G = [&](int a, int b, int d) -> float {
+        return Gs4[((int64_t)(a + L) * twoL + (b + L)) * twoL + (d + L)];
+    };
+    auto in = [&](int w) { return w >= -L && w < L; };
+    float acc = 0.0f;  // at most 6 (2L)^2 / 256 terms per thread
+    for (int q = threadIdx.x; q < twoL * twoL; q += GC2_THREADS) {
+        const int u = q / twoL - L, v = q % twoL - L;
+        if (in(t)) {
+            const float cv = c[v - u];
+            acc = fmaf(G(t, u, v), cv, acc);  // a = w1 = t, b = w3 - w2
+            acc = fmaf(G(u, t, v), cv, acc);  // a = w2 = t, b = w3 - w1
+            acc = fmaf(G(u, v, t), cv, acc);  // a = w3 = t, b = w2 - w1
+        }
+        if (in(v + t)) {
+            const float cu = c[u];
+            acc = fmaf(G(u, v, v + t), cu, acc);  // b = w3 - w2 = t, a = w1
+            acc = fmaf(G(v, u, v + t), cu, acc);  // b = w3 - w1 = t, a = w2
+            acc = fmaf(G(v, v + t, u), cu, acc);  // b = w2 - w1 = t, a = w3
+        }
+    }
+    red[threadIdx.x] = (double)acc;
+    __syncthreads();
+    for (int d = GC2_THREADS / 2; d > 0; d >>= 1) {
+        if (threadIdx.x < d) red[threadIdx.x] += red[threadIdx.x + d];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) gc2[t + T] = -red[0];
+}
+
+cudaError_t launch_gs4(const float2* Gc, int N, int L, int window, double scale, float* Gs4, cudaStream_t st) {
+    const int64_t tot = (int64_t)8 * L * L * L;
+    gs4_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(Gc, N, L, window, (float)scale, Gs4);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gc2(const float* Gs4, const double* c2, int L, double* gc2, cudaStream_t st) {
+    gc2_kernel<<<(unsigned)(4 * L - 1), GC2_THREADS, 0, st>>>(Gs4, c2, L, gc2);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_adjoint_finish(const float* g, int64_t n, const double* gmean, int remove_mean, int dtype, void* dx,
                                   cudaStream_t st) {
     const unsigned b = (unsigned)ceil_div(n, 256);

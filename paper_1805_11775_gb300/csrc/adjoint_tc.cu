@@ -19,6 +19,17 @@
 //
 // Work items (w1 block b, 128-row tile of u), b-major, split into equal
 // contiguous ranges over the persistent CTAs.  Every wait is bounded.
+//
+// Fourth order (the trispectrum adjoint).  With Gs the symmetrised lag-domain
+// gradient of c4 and E(u, w1) = sum_{w2,w3} Gs(w1, w2, w3) y(u + w2) y(u + w3),
+// the fourth-moment part of the gradient is T1 + 3 T2 with
+//   T1(u) = sum_w1 E(u, w1) y(u + w1),   T2(j) = sum_w1 E(j - w1, w1) y(j - w1).
+// The same MMA computes D[u, (w1, w2)] = sum_w3 y(u + w3) Gs(w1, w2, w3): the
+// B rows are the (w1, w2) combinations, 128 per block, w2 fastest, K = w3.
+// The epilogue forms E(u, w1) = sum_w2 D[u, (w1, w2)] y(u + w2) one w1 run at
+// a time (a run split between two blocks gives two partial E's, which T1 and
+// T2 take linearly) and adds E y(u + w1) to T1 and E y(u) to the warp's T2
+// positions u + w1.
 #include "launch.cuh"
 
 namespace hos {
@@ -30,18 +41,22 @@ constexpr int AW = 128;               // lags w1 per block
 constexpr int AMAXK = 256;            // K = 2L <= 256 (L <= 128)
 constexpr int AWIN = AU + AMAXK + 16;  // window samples (u0 - L .. u0 + 128 + L + 16)
 constexpr int B_BYTES = (AMAXK / 8) * 2048;  // one Gs plane of a block: (K/8) x 16 groups x 128 B
+// Item buffers (window, staging, y rows): the producer keeps NBUF - 1 items'
+// copies in flight ahead of the one it interleaves, so one item's copy
+// latency overlaps the others' work.
+constexpr int NBUF = 4;
 
 struct __align__(16) AdjSmem {
     uint8_t gs_hi[B_BYTES];
     uint8_t gs_lo[B_BYTES];
-    uint8_t win_hi[2][AWIN * 16];
-    uint8_t win_lo[2][AWIN * 16];
-    uint16_t lin_hi[AWIN + 16];
-    uint16_t lin_lo[AWIN + 16];
-    float yw[2][AU + AW];   // y(u0 + w1_0 + t): the y(u + w1) of T1
-    float yu[2][AU + 4];    // y(u0 + t - sh) from a 16-byte aligned start, sh = L & 3
+    uint8_t win_hi[NBUF][AWIN * 16];
+    uint8_t win_lo[NBUF][AWIN * 16];
+    uint16_t lin_hi[NBUF][AWIN + 16];
+    uint16_t lin_lo[NBUF][AWIN + 16];
+    float yw[NBUF][AU + AW];   // ORDER 3: y(u0 + w1_0 + t), the y(u + w1) of T1; ORDER 4: y(u0 - L + t)
+    float yu[NBUF][AU + 4];    // y(u0 + t - sh) from a 16-byte aligned start, sh = L & 3
     float t2w[4][AU / 4 + AW];  // each warp's anti-diagonal sums (private to the warp)
-    uint64_t full[2], empty[2], acc_full[2], acc_empty[2], b_full, b_empty, tma_bar, btma_bar, drain;
+    uint64_t full[NBUF], empty[NBUF], tma_bar[NBUF], acc_full[2], acc_empty[2], b_full, b_empty, btma_bar, drain;
     uint32_t tmem_base;
     int abort;
 };
@@ -50,6 +65,7 @@ struct __align__(16) AdjSmem {
 
 struct AdjTcParams {
     const float* y32;       // padded sample planes of the series: y(i) at index L + i
+    int t2d;                // floats per warp in t2p: 32 + (w1 values per block) - 1
     const uint16_t* hi;     // bf16 planes
     const uint16_t* lo;
     const uint8_t* gsb;     // Gs hi/lo planes per block, canonical layout, 2 * B_BYTES per block
@@ -78,6 +94,7 @@ HOS_DEV void expect_bytes(uint64_t* bar, uint32_t bytes) {
                  : "memory");
 }
 
+template <int ORDER>
 __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     AdjSmem& sm = *reinterpret_cast<AdjSmem*>(smem_raw);
@@ -88,15 +105,17 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
     const int64_t it0 = range_begin(blockIdx.x, items, gridDim.x), it1 = range_begin(blockIdx.x + 1, items, gridDim.x);
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NBUF; ++i) {
             mbar_init(&sm.full[i], 32);
             mbar_init(&sm.empty[i], 1 + 4);  // MMA commit + four epilogue warps
+            mbar_init(&sm.tma_bar[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
             mbar_init(&sm.acc_full[i], 1);
             mbar_init(&sm.acc_empty[i], 128);
         }
         mbar_init(&sm.b_full, 1);
         mbar_init(&sm.b_empty, 1);
-        mbar_init(&sm.tma_bar, 1);
         mbar_init(&sm.btma_bar, 1);
         mbar_init(&sm.drain, 1);
         sm.abort = 0;
@@ -115,13 +134,40 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
 
     if (warp == 4) {
         // ---------------------------------------------------------- producer
-        uint32_t tph = 0, bph = 0;
+        uint32_t bph = 0;
         int cur_b = -1;
         uint32_t nbl = 0;  // blocks loaded
         bool ok = true;
-        for (int64_t it = it0, k = 0; it < it1 && ok; ++it, ++k) {
+        const int64_t cnt = it1 - it0;
+        constexpr int PD = NBUF - 1;  // items whose copies run ahead
+        int64_t issued = 0, landed = 0;  // items whose copies were issued / have landed
+        bool b_pending = false;          // a Gs block copy issued and not yet waited for
+        // copies of item k (into buffer k % NBUF) once the consumers are done with
+        // the item that used the buffer before (k - NBUF, already published)
+        auto issue = [&](int64_t k) -> bool {
+            const int64_t it = it0 + k;
             const int b = (int)(it / P.nut);
             const int64_t u0 = (it % P.nut) * AU;
+            const int buf = (int)(k % NBUF);
+            if (!warp_wait(&sm.empty[buf], (uint32_t)((k / NBUF) & 1) ^ 1u, abort, P.status, lim, 2000)) return false;
+            // window of y(u0 - L + t): plane index u0 (multiple of 128, 16-byte aligned for bf16)
+            const uint32_t wsamp = (uint32_t)(AU + K + 16);
+            // ORDER 3: yw = y(u0 + w1b + t), w1b the block's first lag (L + u0 + w1b
+            // = u0 + 128 b, aligned); ORDER 4: yw = y(u0 - L + t) (plane index u0)
+            const int64_t yw0 = (ORDER == 3) ? (L + u0 + (int64_t)b * AW - L) : u0;
+            if (lane == 0) {
+                expect_bytes(&sm.tma_bar[buf], 2 * wsamp * 2 + (AU + AW) * 4 + (AU + 4) * 4);
+                bulk_copy(sm.lin_hi[buf], P.hi + u0, wsamp * 2, &sm.tma_bar[buf]);
+                bulk_copy(sm.lin_lo[buf], P.lo + u0, wsamp * 2, &sm.tma_bar[buf]);
+                bulk_copy(sm.yw[buf], P.y32 + yw0, (AU + AW) * 4, &sm.tma_bar[buf]);
+                bulk_copy(sm.yu[buf], P.y32 + ((L + u0) & ~(int64_t)3), (AU + 4) * 4, &sm.tma_bar[buf]);
+            }
+            issued = k + 1;
+            return true;
+        };
+        for (int64_t k = 0; k < PD && k < cnt && ok; ++k) ok = issue(k);
+        for (int64_t k = 0; k < cnt && ok; ++k) {
+            const int b = (int)((it0 + k) / P.nut);
             if (b != cur_b) {  // the Gs block: wait until every MMA on the previous one is done
                 ok = warp_wait(&sm.b_empty, (nbl & 1) ^ 1, abort, P.status, lim, 2000);
                 if (!ok) break;
@@ -131,33 +177,23 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
                     bulk_copy(sm.gs_hi, src, (K / 8) * 2048, &sm.btma_bar);
                     bulk_copy(sm.gs_lo, src + B_BYTES, (K / 8) * 2048, &sm.btma_bar);
                 }
+                b_pending = true;
                 ok = warp_wait(&sm.btma_bar, bph, abort, P.status, lim, 1000);
-                bph ^= 1;
                 if (!ok) break;
+                b_pending = false;
+                bph ^= 1;
                 if (lane == 0) mbar_arrive(&sm.b_full);
                 cur_b = b;
                 ++nbl;
             }
-            const int buf = (int)(k & 1);
-            ok = warp_wait(&sm.empty[buf], ((k >> 1) & 1) ^ 1, abort, P.status, lim, 2000);
+            const int buf = (int)(k % NBUF);
+            ok = warp_wait(&sm.tma_bar[buf], (uint32_t)((k / NBUF) & 1), abort, P.status, lim, 1000);
             if (!ok) break;
-            // window of y(u0 - L + t): plane index u0 (multiple of 128, 16-byte aligned for bf16)
-            const uint32_t wsamp = (uint32_t)(AU + K + 16);
-            const int64_t w1b = (int64_t)b * AW - L;  // first lag of the block
-            if (lane == 0) {
-                expect_bytes(&sm.tma_bar, 2 * wsamp * 2 + (AU + AW) * 4 + (AU + 4) * 4);
-                bulk_copy(sm.lin_hi, P.hi + u0, wsamp * 2, &sm.tma_bar);
-                bulk_copy(sm.lin_lo, P.lo + u0, wsamp * 2, &sm.tma_bar);
-                bulk_copy(sm.yw[buf], P.y32 + (L + u0 + w1b), (AU + AW) * 4, &sm.tma_bar);  // u0 + 128 b: aligned
-                bulk_copy(sm.yu[buf], P.y32 + ((L + u0) & ~(int64_t)3), (AU + 4) * 4, &sm.tma_bar);
-            }
-            ok = warp_wait(&sm.tma_bar, tph, abort, P.status, lim, 1000);
-            tph ^= 1;
-            if (!ok) break;
+            landed = k + 1;
             // interleave: block (q, r) <- samples [8q + r, 8q + r + 8)
             const int nblocks = (int)(((AU + K) / 8 + 2) * 8);
-            const uint32_t* sh = reinterpret_cast<const uint32_t*>(sm.lin_hi);
-            const uint32_t* sl = reinterpret_cast<const uint32_t*>(sm.lin_lo);
+            const uint32_t* sh = reinterpret_cast<const uint32_t*>(sm.lin_hi[buf]);
+            const uint32_t* sl = reinterpret_cast<const uint32_t*>(sm.lin_lo[buf]);
             for (int blk = lane; blk < nblocks; blk += 32) {
                 const int e0 = blk;  // 8q + r
                 const int w0 = e0 >> 1;
@@ -177,7 +213,20 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
             }
             fence_proxy_async_smem();
             mbar_arrive(&sm.full[buf]);
+            // after publishing item k: the copies of item k + PD, whose buffer
+            // item k - 1 frees, so that the consumers work on k - 1 and k meanwhile
+            if (k + PD < cnt) ok = issue(k + PD);
         }
+        // copies issued ahead of a failure still land in this CTA's shared
+        // memory: wait for them (bounded, whatever the abort flag says) before
+        // the CTA exits
+        if (!ok && lane == 0) {
+            volatile int keep_waiting = 0;
+            for (int64_t k = landed; k < issued; ++k)
+                mbar_wait(&sm.tma_bar[k % NBUF], (uint32_t)((k / NBUF) & 1), &keep_waiting, P.status, lim);
+            if (b_pending) mbar_wait(&sm.btma_bar, bph, &keep_waiting, P.status, lim);
+        }
+        __syncwarp();
     } else if (warp == 5 && lane == 0) {
         // ---------------------------------------------------------- MMA issuer
         int cur_b = -1;
@@ -194,11 +243,11 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
                 cur_b = b;
                 ++nbl;
             }
-            const int buf = (int)(k & 1);
+            const int buf = (int)(k % NBUF);
             const uint32_t ab = (uint32_t)(k & 1);
             ok = mbar_wait(&sm.acc_empty[ab], ((k >> 1) & 1) ^ 1, abort, P.status, lim);
             if (!ok) break;
-            ok = mbar_wait(&sm.full[buf], (k >> 1) & 1, abort, P.status, lim);
+            ok = mbar_wait(&sm.full[buf], (uint32_t)((k / NBUF) & 1), abort, P.status, lim);
             if (!ok) break;
             tc_fence_after();
             const uint32_t d = tmem + ab * 128u;
@@ -230,14 +279,71 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
         for (int64_t it = it0, k = 0; it < it1 && ok; ++it, ++k) {
             const int b = (int)(it / P.nut);
             const int64_t ut = it % P.nut, u0 = ut * AU;
-            const int buf = (int)(k & 1);
+            const int buf = (int)(k % NBUF);
             const uint32_t ab = (uint32_t)(k & 1);
-            ok = warp_wait(&sm.full[buf], (k >> 1) & 1, abort, P.status, lim, 2000);  // this item's windows
+            ok = warp_wait(&sm.full[buf], (uint32_t)((k / NBUF) & 1), abort, P.status, lim, 2000);  // this item's windows
             if (!ok) break;
             ok = warp_wait(&sm.acc_full[ab], (k >> 1) & 1, abort, P.status, lim, 5000);
             if (!ok) break;
             tc_fence_after();
             const float yu = sm.yu[buf][ysh + m];
+            if constexpr (ORDER == 4) {
+                const float* yw = sm.yw[buf] + m;  // yw[t] = y(u - L + t): y(u + w) = yw[w + L]
+                float* t2w = sm.t2w[warp];
+                for (int e = lane; e < P.t2d; e += 32) t2w[e] = 0.f;
+                __syncwarp();
+                const int twoL = 2 * L;
+                const int cb0 = b * AW;  // first (w1, w2) combination of the block
+                const int w1i0 = cb0 / twoL;
+                int w1i = w1i0, w2i = cb0 - w1i0 * twoL;
+                float ev = 0.f, t1 = 0.f;
+                auto flush = [&]() {  // end of a w1 run (uniform over the warp)
+                    if (w1i < twoL) {      // combinations past (2L)^2 are zero rows of B
+                        t1 = fmaf(ev, yw[w1i], t1);
+                        t2w[lane + (w1i - w1i0)] += ev * yu;
+                    }
+                    __syncwarp();
+                    ev = 0.f;
+                    w2i = 0;
+                    ++w1i;
+                };
+                for (int c0 = 0; c0 < AW; c0 += 32) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + ab * 128u + (uint32_t)c0, v);
+                    tmem_wait_ld();
+                    if (w2i + 32 <= twoL) {
+                        // the 32 columns lie in one w1 run: fixed offsets from yw + w2i,
+                        // four partial sums
+                        const float* yq = yw + w2i;
+                        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4) {
+                            p0 = fmaf(__uint_as_float(v[j]), yq[j], p0);
+                            p1 = fmaf(__uint_as_float(v[j + 1]), yq[j + 1], p1);
+                            p2 = fmaf(__uint_as_float(v[j + 2]), yq[j + 2], p2);
+                            p3 = fmaf(__uint_as_float(v[j + 3]), yq[j + 3], p3);
+                        }
+                        ev += (p0 + p1) + (p2 + p3);
+                        w2i += 32;
+                        if (w2i == twoL || c0 + 32 == AW) flush();
+                        continue;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        ev = fmaf(__uint_as_float(v[j]), yw[w2i], ev);
+                        if (++w2i == twoL || c0 + j == AW - 1) flush();
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&sm.acc_empty[ab]);
+                __syncwarp();
+                if (u0 + m < P.n) P.t1p[(int64_t)b * (P.nut * AU) + u0 + m] = t1;
+                float* dst = P.t2p + (it * 4 + warp) * P.t2d;
+                for (int e = lane; e < P.t2d; e += 32) dst[e] = t2w[e];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.empty[buf]);
+                continue;
+            }
             const float* yw = sm.yw[buf] + m;  // y(u + w1_0 + c)
             float t1 = 0.f, diag = 0.f;
             float* t2w = sm.t2w[warp];
@@ -262,8 +368,8 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
             if (lane > 0) t2w[AW - 1 + lane] = diag;  // diagonals 128 .. 158 are finished too
             __syncwarp();
             if (u0 + m < P.n) P.t1p[(int64_t)b * (P.nut * AU) + u0 + m] = t1;
-            float* dst = P.t2p + (it * 4 + warp) * (32 + AW - 1);
-            for (int e = lane; e < 32 + AW - 1; e += 32) dst[e] = t2w[e];
+            float* dst = P.t2p + (it * 4 + warp) * P.t2d;
+            for (int e = lane; e < P.t2d; e += 32) dst[e] = t2w[e];
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.empty[buf]);  // yu / yw of this buffer are no longer read
         }
@@ -278,10 +384,13 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
     }
 }
 
-// Gs hi/lo per w1 block in the canonical K-major layout the kernel reads:
-// byte (n % 8) * 16 + (n / 8) * 128 + (k / 8) * 2048 + (k % 8) * 2 of a plane,
-// n = w1 - block start (128 per block), k = w2 + L (K = kpad, zero beyond 2L).
-__global__ void gs_layout_kernel(const float* __restrict__ Gs, int L, int kpad, int nb, uint8_t* __restrict__ out) {
+// Gs hi/lo per block of 128 B rows in the canonical K-major layout the kernel
+// reads: byte (n % 8) * 16 + (n / 8) * 128 + (k / 8) * 2048 + (k % 8) * 2 of a
+// plane, n = row - block start, k = last lag + L (K = kpad, zero beyond 2L).
+// Rows: w1 (third order, nrows = 2L) or (w1, w2) combinations (fourth order,
+// nrows = (2L)^2); Gs is row-major with 2L values per row.
+__global__ void gs_layout_kernel(const float* __restrict__ Gs, int L, int kpad, int nb, int nrows,
+                                 uint8_t* __restrict__ out) {
     const int twoL = 2 * L;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)nb * AW * kpad) return;
@@ -290,7 +399,7 @@ __global__ void gs_layout_kernel(const float* __restrict__ Gs, int L, int kpad, 
     const int n = r / kpad, k = r % kpad;
     const int w1i = b * AW + n;  // index w1 + L
     float v = 0.f;
-    if (w1i < twoL && k < twoL) v = Gs[(int64_t)w1i * twoL + k];
+    if (w1i < nrows && k < twoL) v = Gs[(int64_t)w1i * twoL + k];
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
     const size_t off = (size_t)(n % 8) * 16 + (size_t)(n / 8) * 128 + (size_t)(k / 8) * 2048 + (size_t)(k % 8) * 2;
@@ -299,18 +408,49 @@ __global__ void gs_layout_kernel(const float* __restrict__ Gs, int L, int kpad, 
     *reinterpret_cast<__nv_bfloat16*>(base + B_BYTES + off) = l;
 }
 
-// g(j) = sum_b T1p[b][j] + 2 sum over the items (b, ut) covering j and their
-// four warps (warp w's diagonal d covers item position 32 w + d), in the
-// order (b, ut, w).
-__global__ void adjoint_tc_gather_kernel(const float* __restrict__ t1p, const float* __restrict__ t2p, int64_t n,
-                                         int L, int nb, int64_t nut, float* __restrict__ g) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// g(j) = sum_b T1p[b][j] + (ORDER - 1) sum over the items (b, ut) covering j
+// and their four warps (warp w's position d covers item position 32 w + d),
+// in the order (b, ut, w); fourth order adds the c2 part
+// sum_t gc2(t) (y(j + t) + y(j - t)), t in [-(2L-1), 2L-1].
+// R = w1 values per block (AW for third order); a block's first lag is w1b.
+// Compensated FP32 sum (TwoSum per addition): FP64 runs at a small fraction
+// of the FP32 rate on this part.
+struct CSum {
+    float hi = 0.f, lo = 0.f;
+    __device__ void add(float v) {
+        const float s = hi + v;
+        const float bv = s - hi;
+        lo += (hi - (s - bv)) + (v - bv);
+        hi = s;
+    }
+    __device__ float value() const { return hi + lo; }
+};
+
+constexpr int GATHER_THREADS = 256;
+template <int ORDER>
+__global__ void __launch_bounds__(GATHER_THREADS) adjoint_tc_gather_kernel(
+    const float* __restrict__ t1p, const float* __restrict__ t2p, int64_t n, int L, int nb, int64_t nut, int R,
+    const double* __restrict__ gc2, const float* __restrict__ y, float* __restrict__ g) {
+    // fourth order: gc2 as FP32 and the block's samples y(j0 - T .. j0 + 255 + T)
+    __shared__ float gcs[ORDER == 4 ? 4 * 64 : 1];
+    __shared__ float ys[ORDER == 4 ? GATHER_THREADS + 4 * 64 : 1];
+    const int64_t j0 = (int64_t)blockIdx.x * GATHER_THREADS;
+    const int64_t j = j0 + threadIdx.x;
+    if constexpr (ORDER == 4) {
+        const int T = 2 * L - 1;
+        for (int i = threadIdx.x; i < 2 * T + 1; i += GATHER_THREADS) gcs[i] = (float)gc2[i];
+        for (int i = threadIdx.x; i < GATHER_THREADS + 2 * T; i += GATHER_THREADS) {
+            const int64_t a = j0 - T + i;
+            ys[i] = (a >= 0 && a < n) ? y[a] : 0.0f;
+        }
+        __syncthreads();
+    }
     if (j >= n) return;
-    const int E = AU + AW - 1, D = 32 + AW - 1;
-    double t1 = 0.0, t2 = 0.0;
+    const int E = AU + R - 1, D = 32 + R - 1;
+    CSum t1, t2;
     for (int b = 0; b < nb; ++b) {
-        t1 += (double)t1p[(int64_t)b * (nut * AU) + j];
-        const int64_t w1b = (int64_t)b * AW - L;
+        t1.add(t1p[(int64_t)b * (nut * AU) + j]);
+        const int64_t w1b = (ORDER == 3) ? (int64_t)b * AW - L : (int64_t)(b * AW) / (2 * L) - L;
         int64_t lo = j - w1b - (E - 1);
         lo = lo <= 0 ? 0 : ceil_div(lo, AU);
         int64_t hi = (j - w1b) >= 0 ? (j - w1b) / AU : -1;
@@ -321,48 +461,83 @@ __global__ void adjoint_tc_gather_kernel(const float* __restrict__ t1p, const fl
             const float* it = t2p + (((int64_t)b * nut + ut) * 4) * D;
             for (int w = 0; w < 4; ++w) {
                 const int64_t d = e - 32 * w;
-                if (d >= 0 && d < D) t2 += (double)it[w * D + d];
+                if (d >= 0 && d < D) t2.add(it[w * D + d]);
             }
         }
     }
-    g[j] = (float)(t1 + 2.0 * t2);
+    CSum v;
+    v.add(t1.hi);
+    v.add(t1.lo);
+    v.add((float)(ORDER - 1) * t2.hi);
+    v.add((float)(ORDER - 1) * t2.lo);
+    if constexpr (ORDER == 4) {
+        const int T = 2 * L - 1;
+        const float* yj = ys + T + threadIdx.x;  // yj[t] = y(j + t), |t| <= T
+        for (int t = -T; t <= T; ++t) v.add(gcs[t + T] * (yj[t] + yj[-t]));
+    }
+    g[j] = v.value();
 }
 
 bool adjoint_tc_supported(int L) { return L >= 1 && L <= AMAXK / 2; }
-size_t adjoint_tc_gs_bytes(int L) { return (size_t)((2 * L + AW - 1) / AW) * 2 * B_BYTES; }
-size_t adjoint_tc_t2_floats(int L, int64_t n) {
-    return (size_t)((2 * L + AW - 1) / AW) * (size_t)ceil_div(n, AU) * 4 * (32 + AW - 1);
+static int adj_rows(int order, int L) { return order == 4 ? 4 * L * L : 2 * L; }
+static int adj_nb(int order, int L) { return (adj_rows(order, L) + AW - 1) / AW; }
+// w1 values a block of 128 rows touches: all 128 for third order; for fourth
+// order at most (AW - 1) / 2L + 2 runs, and never more than 2L
+static int adj_r(int order, int L) {
+    if (order == 3) return AW;
+    const int r = (AW - 1) / (2 * L) + 2;
+    return r < 2 * L ? r : 2 * L;
 }
-size_t adjoint_tc_t1_floats(int L, int64_t n) { return (size_t)((2 * L + AW - 1) / AW) * (size_t)ceil_div(n, AU) * AU; }
+size_t adjoint_tc_gs_bytes(int L, int order) { return (size_t)adj_nb(order, L) * 2 * B_BYTES; }
+size_t adjoint_tc_t2_floats(int L, int64_t n, int order) {
+    return (size_t)adj_nb(order, L) * (size_t)ceil_div(n, AU) * 4 * (size_t)(32 + adj_r(order, L) - 1);
+}
+size_t adjoint_tc_t1_floats(int L, int64_t n, int order) {
+    return (size_t)adj_nb(order, L) * (size_t)ceil_div(n, AU) * AU;
+}
 
-cudaError_t launch_adjoint_tc(const float* y32, const uint16_t* hi, const uint16_t* lo, int64_t n, int L,
-                              const float* Gs, uint8_t* gsb, float* t1p, float* t2p, float* g, int* status,
-                              uint64_t limit_ns, int G, cudaStream_t st) {
+template <int ORDER>
+static cudaError_t launch_adjoint_tc_order(const float* y32, const uint16_t* hi, const uint16_t* lo, int64_t n, int L,
+                                           const float* Gs, uint8_t* gsb, float* t1p, float* t2p, const double* gc2,
+                                           float* g, int* status, uint64_t limit_ns, int G, cudaStream_t st) {
     const int kpad = ((2 * L + 15) / 16) * 16;
-    const int nb = (2 * L + AW - 1) / AW;
+    const int nb = adj_nb(ORDER, L), R = adj_r(ORDER, L);
     const int64_t nut = ceil_div(n, AU);
     const int64_t tot = (int64_t)nb * AW * kpad;
-    gs_layout_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(Gs, L, kpad, nb, gsb);
+    gs_layout_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(Gs, L, kpad, nb, adj_rows(ORDER, L), gsb);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    AdjTcParams p{y32, hi, lo, gsb, t1p, t2p, n, L, kpad, nb, nut, status, limit_ns};
+    AdjTcParams p{y32, 32 + R - 1, hi, lo, gsb, t1p, t2p, n, L, kpad, nb, nut, status, limit_ns};
     const size_t smem = sizeof(AdjSmem);
     static bool attr = false;
     if (!attr) {
-        e = cudaFuncSetAttribute(adjoint_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(adjoint_tc_kernel<ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const int64_t items = (int64_t)nb * nut;
     const int grid = (int)(items < G ? items : G);
-    adjoint_tc_kernel<<<grid, 192, smem, st>>>(p);
+    adjoint_tc_kernel<ORDER><<<grid, 192, smem, st>>>(p);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    adjoint_tc_gather_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(t1p, t2p, n, L, nb, nut, g);
+    adjoint_tc_gather_kernel<ORDER><<<(unsigned)ceil_div(n, GATHER_THREADS), GATHER_THREADS, 0, st>>>(
+        t1p, t2p, n, L, nb, nut, R, gc2, y32 + L, g);
     count_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_tc(const float* y32, const uint16_t* hi, const uint16_t* lo, int64_t n, int L,
+                              const float* Gs, uint8_t* gsb, float* t1p, float* t2p, float* g, int* status,
+                              uint64_t limit_ns, int G, cudaStream_t st) {
+    return launch_adjoint_tc_order<3>(y32, hi, lo, n, L, Gs, gsb, t1p, t2p, nullptr, g, status, limit_ns, G, st);
+}
+
+cudaError_t launch_adjoint4_tc(const float* y32, const uint16_t* hi, const uint16_t* lo, int64_t n, int L,
+                               const float* Gs4, uint8_t* gsb, float* t1p, float* t2p, const double* gc2, float* g,
+                               int* status, uint64_t limit_ns, int G, cudaStream_t st) {
+    return launch_adjoint_tc_order<4>(y32, hi, lo, n, L, Gs4, gsb, t1p, t2p, gc2, g, status, limit_ns, G, st);
 }
 
 }  // namespace hos

@@ -40,12 +40,17 @@ constexpr int MAX_STAGE = 6;     // A stages in TMEM (64 columns each): 4, or 6 
 constexpr int WIN_SAMPLES = KC + 256 + 16;
 constexpr int WIN_BYTES = WIN_SAMPLES * 16;  // interleaved window, one plane
 constexpr int YA_FLOATS = KC + TILE_M;
+// Four copies of the A window, copy s shifted by s samples, so that a row at
+// any lag offset reads four consecutive samples with one aligned 16-byte
+// load.  The copy pitch is 8 words mod 32: eight lanes at consecutive
+// offsets then touch eight distinct bank quads.
+constexpr int YA_STRIDE = YA_FLOATS + 8;
 constexpr int YI_FLOATS = KC + 4;
 
 struct __align__(16) C3Smem {
     uint8_t win_hi[2][WIN_BYTES];
     uint8_t win_lo[2][WIN_BYTES];
-    float ya[2][YA_FLOATS];
+    float ya[2][4][YA_STRIDE];        // [buffer][shift]; copies 1-3 only for fourth order
     float yi[2][KC];                  // y(i0 + t), 16-byte aligned for broadcast loads
     float yi_raw[YI_FLOATS];          // staging: copied from an aligned global start
     uint8_t lin_hi[WIN_SAMPLES * 4];  // linear staging of the hi plane window
@@ -161,7 +166,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                     mbar_expect_tx(&sm.tma_bar, 2 * wbytes + yab + yib);
                     bulk_g2s(sm.lin_hi, (const uint8_t*)P.hi + wb * ELT, wbytes, &sm.tma_bar);
                     bulk_g2s(sm.lin_lo, (const uint8_t*)P.lo + wb * ELT, wbytes, &sm.tma_bar);
-                    bulk_g2s(sm.ya[buf], P.y32 + ab, yab, &sm.tma_bar);
+                    bulk_g2s(sm.ya[buf][0], P.y32 + ab, yab, &sm.tma_bar);
                     bulk_g2s(sm.yi_raw, P.y32 + ib_al, yib, &sm.tma_bar);
                 }
                 ok = warp_wait(&sm.tma_bar, tph, abort, P.status, lim, 1000);
@@ -171,6 +176,19 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                     const int ish = (int)(ib - ib_al);
                     for (int t = lane; t < csz; t += 32)
                         sm.yi[buf][t] = (i0 + t < slen) ? sm.yi_raw[ish + t] : 0.0f;
+                }
+                if constexpr (ORDER == 4) {
+                    // shifted copies: ya[buf][s][j] = ya[buf][0][j + s].  The last
+                    // group reads up to 4 words past the window (inside the pitch);
+                    // those land only at j + s past the window, which no row reads.
+                    const float* y0 = sm.ya[buf][0];
+                    for (int g = lane; g < (csz + TILE_M) / 4; g += 32) {
+                        const float4 u = *reinterpret_cast<const float4*>(y0 + 4 * g);
+                        const float4 v = *reinterpret_cast<const float4*>(y0 + 4 * g + 4);
+                        *reinterpret_cast<float4*>(sm.ya[buf][1] + 4 * g) = make_float4(u.y, u.z, u.w, v.x);
+                        *reinterpret_cast<float4*>(sm.ya[buf][2] + 4 * g) = make_float4(u.z, u.w, v.x, v.y);
+                        *reinterpret_cast<float4*>(sm.ya[buf][3] + 4 * g) = make_float4(u.w, v.x, v.y, v.z);
+                    }
                 }
                 // interleave: block (q, r) <- samples [R q + r, R q + r + R)
                 const int ngroups = (csz + N) / R + 2;
@@ -214,9 +232,9 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
         uint32_t kc = 0, ks = 0;
         bool ok = true;
         while (ok && walk.next(part)) {
-            // ORDER 4: this row's lag pair (w1 <= w2); rows past the last pair give zeros
+            // ORDER 4: this row's lag pair (w1 <= w2).  Rows past the last pair
+            // take the pair (-L, 0); nothing downstream reads those rows.
             int o1 = 0, o2 = 0;
-            float live = 1.0f;
             if constexpr (ORDER == 4) {
                 const int twoL = 2 * L, npairs = twoL * (twoL + 1) / 2;
                 const int pidx = geo.tile_a[part.t] * TILE_M + m;
@@ -226,7 +244,6 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                     ++r;
                 }
                 if (pidx >= npairs) {
-                    live = 0.0f;
                     r = 0;
                     start = 0;
                 }
@@ -238,7 +255,11 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                 const int buf = kc & 1;
                 ok = warp_wait(&sm.full_b[buf], (kc >> 1) & 1, abort, P.status, lim, 2000);
                 if (!ok) break;
-                const float* ya = sm.ya[buf] + (ORDER == 3 ? m : 0);
+                const float* ya = sm.ya[buf][0] + (ORDER == 3 ? m : 0);
+                // ORDER 4: y(i + w1) and y(i + w2) from the copies that put them on
+                // a 16-byte boundary
+                const float* c1 = sm.ya[buf][o1 & 3] + (o1 & ~3);
+                const float* c2 = sm.ya[buf][o2 & 3] + (o2 & ~3);
                 const float* yi = sm.yi[buf];
                 for (int kb = 0; kb < csz / KB; ++kb, ++ks) {
                     const int st = (int)(ks % (uint32_t)nst);
@@ -251,16 +272,14 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                     const float4* pi4 = reinterpret_cast<const float4*>(pi);
                     if constexpr (ORDER == 4) {
                         // T = y(i) y(i+w1) y(i+w2); ya[t] = y(i0 - L + t)
-                        const float* q1 = pa + o1;
-                        const float* q2 = pa + o2;
+                        const float4* q1 = reinterpret_cast<const float4*>(c1 + kb * KB);
+                        const float4* q2 = reinterpret_cast<const float4*>(c2 + kb * KB);
                         if constexpr (TF32) {
 #pragma unroll
                             for (int q = 0; q < 8; ++q) {
-                                const float4 v = pi4[q];
-                                const float pv[4] = {v.x * q1[4 * q] * q2[4 * q] * live,
-                                                     v.y * q1[4 * q + 1] * q2[4 * q + 1] * live,
-                                                     v.z * q1[4 * q + 2] * q2[4 * q + 2] * live,
-                                                     v.w * q1[4 * q + 3] * q2[4 * q + 3] * live};
+                                const float4 v = pi4[q], a1 = q1[q], a2 = q2[q];
+                                const float pv[4] = {v.x * a1.x * a2.x, v.y * a1.y * a2.y, v.z * a1.z * a2.z,
+                                                     v.w * a1.w * a2.w};
 #pragma unroll
                                 for (int e = 0; e < 4; ++e) {
                                     const uint32_t h = to_tf32(pv[e]);
@@ -271,11 +290,9 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                         } else {
 #pragma unroll
                             for (int q = 0; q < 16; ++q) {
-                                const float4 v = pi4[q];
-                                const float p0 = v.x * q1[4 * q] * q2[4 * q] * live;
-                                const float p1 = v.y * q1[4 * q + 1] * q2[4 * q + 1] * live;
-                                const float p2 = v.z * q1[4 * q + 2] * q2[4 * q + 2] * live;
-                                const float p3 = v.w * q1[4 * q + 3] * q2[4 * q + 3] * live;
+                                const float4 v = pi4[q], a1 = q1[q], a2 = q2[q];
+                                const float p0 = v.x * a1.x * a2.x, p1 = v.y * a1.y * a2.y;
+                                const float p2 = v.z * a1.z * a2.z, p3 = v.w * a1.w * a2.w;
                                 const uint32_t h0 = pack_bf16x2(p0, p1), h1 = pack_bf16x2(p2, p3);
                                 H[2 * q] = h0;
                                 H[2 * q + 1] = h1;

@@ -105,3 +105,24 @@ def test_workspace_size_grows_with_the_problem(lib):
     assert c > 4096 * 256 * 256 * 4  # at least the transform grid
     # the full-size long workload stays far below the device memory
     assert b < 2 << 30
+
+
+def test_trispectrum_backward_workspace_and_limits(lib):
+    """The trispectrum adjoint's workspace holds the adjoint grid, the per-block
+    row partials ((2L)^2 / 128 blocks x n floats) and the rest; precisions other
+    than split-bf16, L > 64 and the symmetric window are refused on the host."""
+    from paper_1805_11775_gb300 import workspace_size, _native, HosError
+    n = 1 << 16
+    a = workspace_size(_native.OP_TRISPECTRUM_BACKWARD, n, 1, n, _params(L=32, precision=1))
+    assert a > 32 * n * 4 + 64 ** 3 * 8
+    b = workspace_size(_native.OP_TRISPECTRUM_BACKWARD, n, 1, n, _params(L=64, precision=1))
+    assert b > a
+    for bad in (_params(L=32, precision=0), _params(L=32, precision=2), _params(L=65, precision=1),
+                _params(L=32, precision=1, window=1), _params(L=32, precision=1, segment_len=1000)):
+        with pytest.raises(HosError):
+            workspace_size(_native.OP_TRISPECTRUM_BACKWARD, n, 1, n, bad)
+    dummy = ctypes.c_void_p(16)
+    ws = ctypes.c_void_p(256)
+    p = _params(L=8, precision=1)
+    assert lib.hos_trispectrum_backward(None, 0, 100, ctypes.byref(p), dummy, dummy, ws, 1 << 20, None) == 1
+    assert lib.hos_trispectrum_backward(dummy, 0, 100, ctypes.byref(p), dummy, dummy, ws, 64, None) == 3

@@ -96,3 +96,69 @@ def test_backward_full_size_sampled(hos, oracle, prec):
     js = np.concatenate([[0, 1, L, x.size - 1, x.size - L], rng.integers(0, x.size, 300)])
     ref = oracle.dy_at(x.astype(np.float64), L, dc, js)
     assert np.abs(dx[js] - ref).max() <= TOL[prec] * np.abs(ref).max()
+
+
+# ------------------------------------------------------------------ trispectrum adjoint
+@pytest.mark.parametrize("n,L,N,window,rm", [(40, 3, 6, "parzen", True), (700, 4, 8, "parzen", False),
+                                             (1000, 8, 16, "rect", True), (1500, 13, 30, "parzen", True),
+                                             (2000, 16, 32, "parzen", True), (800, 32, 64, "parzen", False),
+                                             (500, 1, 2, "parzen", True), (300, 48, 96, "rect", False),
+                                             (200, 64, 128, "parzen", True), (333, 5, 17, "parzen", True)])
+def test_trispectrum_backward_matches_oracle(hos, oracle, n, L, N, window, rm):
+    """Split-bf16 adjoint of the trispectrum against the oracle's FP64 chain
+    rule (pinned by central differences), random complex dl/dT."""
+    x = hos_synth.ar2(n, 13 * n + L)
+    rng = np.random.default_rng(n + L)
+    G = rng.standard_normal((N, N, N)) + 1j * rng.standard_normal((N, N, N))
+    wk = {"parzen": oracle.WIN_PARZEN, "rect": oracle.WIN_RECT}[window]
+    ref = oracle.trispectrum_grad(x, L, G, N, window=wk, remove_mean=rm)
+    got = hos.trispectrum_backward(torch.from_numpy(x).cuda(), torch.from_numpy(G.astype(np.complex64)), L, nfft=N,
+                                   window=window, remove_mean=rm).cpu().numpy()
+    assert normwise(got, ref) <= TOL["bf16"]
+
+
+def test_autograd_trispectrum_matching_loss(hos, oracle):
+    """l = sum |T(x) - T_target|^2 through torch.autograd; the gradient equals
+    the oracle's for the same dl/dT."""
+    n, L = 2000, 16
+    N = 2 * L
+    x = torch.from_numpy(hos_synth.ar2(n, 21)).cuda().float().requires_grad_(True)
+    Tt = hos.trispectrum(torch.from_numpy(hos_synth.ar2(n, 22)).cuda().float(), L)
+    T = hos.trispectrum_ad(x, L)
+    loss = ((T - Tt).abs() ** 2).sum()
+    loss.backward()
+    G = (2 * (T.detach() - Tt)).cpu().numpy().astype(np.complex128)
+    ref = oracle.trispectrum_grad(x.detach().cpu().numpy().astype(np.float64), L, G, N)
+    assert normwise(x.grad.cpu().numpy(), ref) <= TOL["bf16"]
+
+
+def test_trispectrum_backward_full_size_sampled(hos, oracle):
+    """The trispectrum workload's series (n = 65536, L = 32, 64^3 grid), loss
+    against a second seeded series' trispectrum: the gradient at sampled
+    samples, edges included (mean removal off, so each sample's gradient is
+    local), from the oracle's transform, c2 and per-sample steps."""
+    w = hos_synth.workload("trispectrum_n65536_L32")
+    x, L = w["x"], 32
+    N = 2 * L
+    xd = torch.from_numpy(x).cuda()
+    T = hos.trispectrum(xd, L, precision="fp32", remove_mean=False)
+    Tt = hos.trispectrum(torch.from_numpy(hos_synth.ar2(x.size, 5)).cuda(), L, precision="fp32", remove_mean=False)
+    G = (2 * (T - Tt)).cpu().numpy()
+    dx = hos.trispectrum_backward(xd, torch.from_numpy(G), L, remove_mean=False).cpu().numpy()
+    x64 = x.astype(np.float64)
+    dc4 = oracle.grad_lag4(G.astype(np.complex128), L, N)
+    dc2 = oracle.grad_c2(dc4, oracle.c2(x64, 2 * L), L)
+    rng = np.random.default_rng(4)
+    js = np.concatenate([[0, 1, L, 2 * L, x.size - 1, x.size - L, x.size - 2 * L], rng.integers(0, x.size, 57)])
+    ref = oracle.dy4_at(x64, L, dc4, dc2, js)
+    assert np.abs(dx[js] - ref).max() <= TOL["bf16"] * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("kw", [{"precision": "fp32"}, {"precision": "simt"}, {"window": "parzen_sym"}])
+def test_trispectrum_backward_unsupported(hos, kw):
+    x = torch.from_numpy(hos_synth.ar2(500, 9)).cuda()
+    G = torch.zeros((16, 16, 16), dtype=torch.complex64)
+    with pytest.raises(hos.HosError):
+        hos.trispectrum_backward(x, G, 8, **kw)
+    with pytest.raises(hos.HosError):
+        hos.trispectrum_backward(x, torch.zeros((130, 130, 130), dtype=torch.complex64), 65)
