@@ -12,10 +12,10 @@
 //       loaded once per block and kept in shared memory (all K = 2L lags).
 //   D = two FP32 TMEM accumulators (128 columns each), so the epilogue drains
 //       one item while the MMAs fill the next.
-// T2 is swept per warp with shuffles: stepping through the columns c, each
-// lane adds U[u, c] y(u) to a running sum that moves one lane down per step,
-// so lane 0 holds a finished anti-diagonal after every step; the four warps'
-// diagonals are then added in warp order.  Every sum runs in a fixed order.
+// T2 is summed per warp and 32-column chunk: the products U[u, c] y(u) go to
+// shared memory, lane l adds up the chunk's anti-diagonals l and l + 32, and
+// the chunk sums accumulate per warp; the four warps' diagonals are then added
+// in warp order.  Every sum runs in a fixed order.
 //
 // Work items (w1 block b, 128-row tile of u), b-major, split into equal
 // contiguous ranges over the persistent CTAs.  Every wait is bounded.
@@ -41,7 +41,7 @@ constexpr int AW = 128;               // lags w1 per block
 constexpr int AMAXK = 256;            // K = 2L <= 256 (L <= 128)
 constexpr int AWIN = AU + AMAXK + 16;  // window samples (u0 - L .. u0 + 128 + L + 16)
 constexpr int B_BYTES = (AMAXK / 8) * 2048;  // one Gs plane of a block: (K/8) x 16 groups x 128 B
-// Item buffers (window, staging, y rows): the producer keeps NBUF - 1 items'
+// Item buffers (window, staging, y rows): the producer keeps NBUF - 2 items'
 // copies in flight ahead of the one it interleaves, so one item's copy
 // latency overlaps the others' work.
 constexpr int NBUF = 4;
@@ -56,6 +56,7 @@ struct __align__(16) AdjSmem {
     float yw[NBUF][AU + AW];   // ORDER 3: y(u0 + w1_0 + t), the y(u + w1) of T1; ORDER 4: y(u0 - L + t)
     float yu[NBUF][AU + 4];    // y(u0 + t - sh) from a 16-byte aligned start, sh = L & 3
     float t2w[4][AU / 4 + AW];  // each warp's anti-diagonal sums (private to the warp)
+    float pw[4][32 * 33];       // third order: one 32 x 32 chunk of U y(u) per warp, row pitch 33
     uint64_t full[NBUF], empty[NBUF], tma_bar[NBUF], acc_full[2], acc_empty[2], b_full, b_empty, btma_bar, drain;
     uint32_t tmem_base;
     int abort;
@@ -106,13 +107,13 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < NBUF; ++i) {
-            mbar_init(&sm.full[i], 32);
+            mbar_init(&sm.full[i], 1);  // one elected arrival per arriving warp
             mbar_init(&sm.empty[i], 1 + 4);  // MMA commit + four epilogue warps
             mbar_init(&sm.tma_bar[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&sm.acc_full[i], 1);
-            mbar_init(&sm.acc_empty[i], 128);
+            mbar_init(&sm.acc_empty[i], 4);
         }
         mbar_init(&sm.b_full, 1);
         mbar_init(&sm.b_empty, 1);
@@ -139,7 +140,10 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
         uint32_t nbl = 0;  // blocks loaded
         bool ok = true;
         const int64_t cnt = it1 - it0;
-        constexpr int PD = NBUF - 1;  // items whose copies run ahead
+        // items whose copies run ahead; the buffer item k + PD reuses was freed by
+        // item k + PD - NBUF = k - 2, so the producer never waits on the item the
+        // consumers are working on
+        constexpr int PD = NBUF - 2;
         int64_t issued = 0, landed = 0;  // items whose copies were issued / have landed
         bool b_pending = false;          // a Gs block copy issued and not yet waited for
         // copies of item k (into buffer k % NBUF) once the consumers are done with
@@ -211,10 +215,10 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
                     make_uint4(__funnelshift_r(l[0], l[1], sft), __funnelshift_r(l[1], l[2], sft),
                                __funnelshift_r(l[2], l[3], sft), __funnelshift_r(l[3], l[4], sft));
             }
-            fence_proxy_async_smem();
-            mbar_arrive(&sm.full[buf]);
-            // after publishing item k: the copies of item k + PD, whose buffer
-            // item k - 1 frees, so that the consumers work on k - 1 and k meanwhile
+            fence_proxy_async_smem();  // every lane's window writes, for the MMA's reads
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.full[buf]);
+            // after publishing item k: the copies of item k + PD
             if (k + PD < cnt) ok = issue(k + PD);
         }
         // copies issued ahead of a failure still land in this CTA's shared
@@ -273,7 +277,8 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
         mbar_wait(&sm.drain, 0, abort, P.status, lim);
     } else if (warp < 4) {
         // ---------------------------------------------------------- epilogue
-        const int m = warp * 32 + lane;  // row u - u0
+        const int q = warp;                // TMEM lane quadrant
+        const int m = q * 32 + lane;       // row u - u0
         const int ysh = L & 3;           // yu was staged from an aligned start
         bool ok = true;
         for (int64_t it = it0, k = 0; it < it1 && ok; ++it, ++k) {
@@ -289,7 +294,7 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
             const float yu = sm.yu[buf][ysh + m];
             if constexpr (ORDER == 4) {
                 const float* yw = sm.yw[buf] + m;  // yw[t] = y(u - L + t): y(u + w) = yw[w + L]
-                float* t2w = sm.t2w[warp];
+                float* t2w = sm.t2w[q];
                 for (int e = lane; e < P.t2d; e += 32) t2w[e] = 0.f;
                 __syncwarp();
                 const int twoL = 2 * L;
@@ -307,10 +312,7 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
                     w2i = 0;
                     ++w1i;
                 };
-                for (int c0 = 0; c0 < AW; c0 += 32) {
-                    uint32_t v[32];
-                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + ab * 128u + (uint32_t)c0, v);
-                    tmem_wait_ld();
+                auto chunk = [&](const uint32_t* v, int c0) {
                     if (w2i + 32 <= twoL) {
                         // the 32 columns lie in one w1 run: fixed offsets from yw + w2i,
                         // four partial sums
@@ -326,49 +328,78 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
                         ev += (p0 + p1) + (p2 + p3);
                         w2i += 32;
                         if (w2i == twoL || c0 + 32 == AW) flush();
-                        continue;
+                        return;
                     }
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         ev = fmaf(__uint_as_float(v[j]), yw[w2i], ev);
                         if (++w2i == twoL || c0 + j == AW - 1) flush();
                     }
+                };
+                // two 32-column loads in flight per wait
+                for (int c0 = 0; c0 < AW; c0 += 64) {
+                    uint32_t v0[32], v1[32];
+                    const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + ab * 128u + (uint32_t)c0;
+                    tmem_ld32(ta, v0);
+                    tmem_ld32(ta + 32u, v1);
+                    tmem_wait_ld();
+                    chunk(v0, c0);
+                    chunk(v1, c0 + 32);
                 }
                 tc_fence_before();
-                mbar_arrive(&sm.acc_empty[ab]);
                 __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.acc_empty[ab]);
                 if (u0 + m < P.n) P.t1p[(int64_t)b * (P.nut * AU) + u0 + m] = t1;
-                float* dst = P.t2p + (it * 4 + warp) * P.t2d;
+                float* dst = P.t2p + (it * 4 + q) * P.t2d;
                 for (int e = lane; e < P.t2d; e += 32) dst[e] = t2w[e];
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sm.empty[buf]);
                 continue;
             }
             const float* yw = sm.yw[buf] + m;  // y(u + w1_0 + c)
-            float t1 = 0.f, diag = 0.f;
-            float* t2w = sm.t2w[warp];
-            for (int c0 = 0; c0 < AW; c0 += 32) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + ab * 128u + (uint32_t)c0, v);
-                tmem_wait_ld();
+            float t1 = 0.f;
+            float* t2w = sm.t2w[q];
+            float* pw = sm.pw[q];
+            for (int e = lane; e < AU / 4 + AW; e += 32) t2w[e] = 0.f;
+            __syncwarp();
+            // per 32-column chunk: T1 per row; the products U[u, c] y(u) go to pw, and
+            // lane l then sums anti-diagonals d = l and d = l + 32 of the chunk
+            // (row r, column d - r), adding them at t2w[c0 + d]
+            auto chunk = [&](const uint32_t* v, int c0) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const float uval = __uint_as_float(v[j]);
                     t1 = fmaf(uval, yw[c0 + j], t1);
-                    // running anti-diagonal: take the next lane's sum, add this row's term;
-                    // afterwards lane 0 holds the finished diagonal c0 + j of this warp
-                    float nx = __shfl_down_sync(0xffffffffu, diag, 1);
-                    if (lane == 31) nx = 0.f;
-                    diag = fmaf(uval, yu, nx);
-                    if (lane == 0) t2w[c0 + j] = diag;
+                    pw[lane * 33 + j] = uval * yu;
                 }
+                __syncwarp();
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+                for (int r = 0; r < 32; r += 2) {
+                    // address 32 r + l (+ 32): bank l, no conflicts
+                    const float pa = pw[r * 33 + (r <= lane ? lane - r : lane + 32 - r)];
+                    const float pb = pw[(r + 1) * 33 + (r + 1 <= lane ? lane - r - 1 : lane + 31 - r)];
+                    if (r <= lane) s0 += pa; else s1 += pa;
+                    if (r + 1 <= lane) s2 += pb; else s3 += pb;
+                }
+                t2w[c0 + lane] += s0 + s2;
+                t2w[c0 + 32 + lane] += s1 + s3;
+                __syncwarp();
+            };
+            for (int c0 = 0; c0 < AW; c0 += 64) {
+                uint32_t v0[32], v1[32];
+                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + ab * 128u + (uint32_t)c0;
+                tmem_ld32(ta, v0);
+                tmem_ld32(ta + 32u, v1);
+                tmem_wait_ld();
+                chunk(v0, c0);
+                chunk(v1, c0 + 32);
             }
             tc_fence_before();
-            mbar_arrive(&sm.acc_empty[ab]);  // this item's accumulator may be reused
-            if (lane > 0) t2w[AW - 1 + lane] = diag;  // diagonals 128 .. 158 are finished too
             __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.acc_empty[ab]);  // this item's accumulator may be reused
             if (u0 + m < P.n) P.t1p[(int64_t)b * (P.nut * AU) + u0 + m] = t1;
-            float* dst = P.t2p + (it * 4 + warp) * P.t2d;
+            float* dst = P.t2p + (it * 4 + q) * P.t2d;
             for (int e = lane; e < P.t2d; e += 32) dst[e] = t2w[e];
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.empty[buf]);  // yu / yw of this buffer are no longer read
