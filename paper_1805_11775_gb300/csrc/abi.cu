@@ -420,7 +420,9 @@ struct Plan4 {
     int Nf, W3, npb, nslices, pad_tail;
     bool tc;    // tensor-core m4 (split-bf16 / 3xTF32) instead of FP32 SIMT
     C3Geom g4;  // tensor-core geometry: tiles = blocks of 128 lag pairs, columns = w3
-    size_t status, off, pad, unit, win, mean, mpart, y32, hi, lo, bnd, xr, ilen, m4buf, c2, partials, grid, tw, total;
+    size_t status, off, pad, unit, win, mean, mpart, y32, hi, lo, bnd, xr, ilen, m4buf, c2, c2p, partials, grid, tw,
+        total;
+    int c2s;  // slices per part of the c2 sums
 };
 
 // Geometry of the tensor-core m4 contraction: tile t = pairs [128t, 128t+128)
@@ -506,6 +508,8 @@ static hos_status make_plan4(int op, const hos_params* p, int64_t n, Plan4& P, i
     P.mpart = o; o = al256(o + 8 * (size_t)P.S * P.nslices);
     P.y32 = o; o = al256(o + 4 * (size_t)plane_len);
     P.c2 = o; o = al256(o + 8 * (size_t)P.S * (4 * L - 1));
+    P.c2s = c2_slices(P.S, P.max_len);
+    P.c2p = o; o = al256(o + (P.c2s > 1 ? 8 * (size_t)P.S * (4 * L - 1) * P.c2s : 0));
     if (P.tc) {
         const C3Geom& g = P.g4;
         const int elt = plane_elt(p->precision);
@@ -572,7 +576,7 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
         return HOS_OK;
     }
     double* c2 = at<double>(ws, P.c2);
-    HOS_CUDA_TRY(launch_c2(y32, off, pad, P.S, p->L, c2, st));
+    HOS_CUDA_TRY(launch_c2(y32, off, pad, P.S, p->L, P.c2s, c2, at<float2>(ws, P.c2p), st));
     SeriesView sv{off, pad, unit, win, mean, P.S};
     C3TcParams cp{P.g4, sv, y32, hi, lo, at<float>(ws, P.partials), at<int>(ws, P.status), wait_limit_ns()};
     const bool tf32 = (p->precision == HOS_PREC_FP32);
@@ -651,8 +655,9 @@ static hos_status make_planb(const hos_params* p, int64_t n, PlanB& P) {
 struct PlanB4 {
     C3Geom g;
     int Nf, nslices;
-    size_t status, off, pad, unit, win, mean, mpart, y32, hi, lo, c2, gc, gs, gsb, gc2, t1, t2p, gbuf, gmean, gmpart,
-        tw, total;
+    size_t status, off, pad, unit, win, mean, mpart, y32, hi, lo, c2, c2p, gc, gs, gsb, gc2, t1, t2p, gbuf, gmean,
+        gmpart, tw, total;
+    int c2s;
 };
 
 static hos_status make_planb4(const hos_params* p, int64_t n, PlanB4& P) {
@@ -680,6 +685,8 @@ static hos_status make_planb4(const hos_params* p, int64_t n, PlanB4& P) {
     P.hi = o; o = al256(o + 2 * (size_t)plane_len + 64);
     P.lo = o; o = al256(o + 2 * (size_t)plane_len + 64);
     P.c2 = o; o = al256(o + 8 * (size_t)(4 * L - 1));
+    P.c2s = c2_slices(1, n);
+    P.c2p = o; o = al256(o + (P.c2s > 1 ? 8 * (size_t)(4 * L - 1) * P.c2s : 0));
     P.gc = o; o = al256(o + 8 * (size_t)N3);
     P.gs = o; o = al256(o + 4 * (size_t)twoL * twoL * twoL);
     P.gsb = o; o = al256(o + adjoint_tc_gs_bytes(L, 4));
@@ -1050,7 +1057,7 @@ hos_status hos_trispectrum_backward(const void* d_x, int32_t dtype, int64_t n, c
     void* lo = at<void>(ws, P.lo);
     HOS_CUDA_TRY(launch_planes(d_x, dtype, off, pad, at<double>(ws, P.mean), L, 1, y32, hi, lo, 1, bx, st));
     double* c2 = at<double>(ws, P.c2);
-    HOS_CUDA_TRY(launch_c2(y32, off, pad, 1, L, c2, st));
+    HOS_CUDA_TRY(launch_c2(y32, off, pad, 1, L, P.c2s, c2, at<float2>(ws, P.c2p), st));
     tr.mark("transform");
     // adjoint transform: Gc(w mod N) = sum_k G(k) e^{+i 2 pi k.w / N}, one axis at a time
     float2* tw = at<float2>(ws, P.tw);

@@ -195,8 +195,13 @@ __global__ void gs4_kernel(const float2* __restrict__ Gc, int N, int L, int wind
         const int ka = a < 0 ? a + N : a, kb = b < 0 ? b + N : b, kc = c < 0 ? c + N : c;  // N >= 2L
         return Gc[((int64_t)ka * N + kb) * N + kc].x;
     };
-    const float sym = ((re(w1, w2, w3) + re(w1, w3, w2)) + (re(w2, w1, w3) + re(w2, w3, w1))) +
-                      (re(w3, w1, w2) + re(w3, w2, w1));
+    // the six terms in an order fixed by the sorted lags, so that every
+    // permutation of (w1, w2, w3) gets the same FP32 value (exact symmetry)
+    int a = w1, b = w2, c = w3, tmp;
+    if (a > b) { tmp = a; a = b; b = tmp; }
+    if (b > c) { tmp = b; b = c; c = tmp; }
+    if (a > b) { tmp = a; a = b; b = tmp; }
+    const float sym = ((re(a, b, c) + re(a, c, b)) + (re(b, a, c) + re(b, c, a))) + (re(c, a, b) + re(c, b, a));
     const float wv = wsh[w1 + L] * wsh[w2 + L] * wsh[w3 + L];
     Gs4[e] = sym * (scale * wv * (1.0f / 6.0f));
 }
@@ -204,8 +209,13 @@ __global__ void gs4_kernel(const float2* __restrict__ Gc, int N, int L, int wind
 // dl/dc2(t) (times 1/n, which Gs4 carries) through the three c2 c2 products of
 // c4(w) = m4(w) - c2(w1) c2(w3-w2) - c2(w2) c2(w3-w1) - c2(w3) c2(w2-w1):
 // each product c2(a) c2(b) sends -Gs4(w) c2(b) to c2(a) and -Gs4(w) c2(a) to
-// c2(b).  One block per t in [-(2L-1), 2L-1]; the six sums over the lag
-// planes where a or b equals t, per thread in FP64, then a fixed tree.
+// c2(b).  Gs4 is exactly symmetric in its three lags (gs4_kernel), so the
+// three terms where a lag equals t are equal, H(t) = sum_{u,v} Gs4(t, u, v)
+// c2(v - u), and so are the three where a lag difference equals t,
+// K(t) = sum_{w2} sum_{w1} Gs4(w2, w2 + t, w1) c2(w1):
+//   dl/dc2(t) = -3 (H(t) + K(t)),
+// both read with the last lag fastest (coalesced).  One block per t in
+// [-(2L-1), 2L-1]; FP32 per thread, FP64 tree across the block.
 constexpr int GC2_THREADS = 256;
 __global__ void __launch_bounds__(GC2_THREADS) gc2_kernel(const float* __restrict__ Gs4, const double* __restrict__ c2,
                                                           int L, double* __restrict__ gc2) {
@@ -219,22 +229,11 @@ __global__ void __launch_bounds__(GC2_THREADS) gc2_kernel(const float* __restric
     auto G = [&](int a, int b, int d) -> float {
         return Gs4[((int64_t)(a + L) * twoL + (b + L)) * twoL + (d + L)];
     };
-    auto in = [&](int w) { return w >= -L && w < L; };
-    float acc = 0.0f;  // at most 6 (2L)^2 / 256 terms per thread
+    float acc = 0.0f;  // at most 2 (2L)^2 / 256 terms per thread
     for (int q = threadIdx.x; q < twoL * twoL; q += GC2_THREADS) {
-        const int u = q / twoL - L, v = q % twoL - L;
-        if (in(t)) {
-            const float cv = c[v - u];
-            acc = fmaf(G(t, u, v), cv, acc);  // a = w1 = t, b = w3 - w2
-            acc = fmaf(G(u, t, v), cv, acc);  // a = w2 = t, b = w3 - w1
-            acc = fmaf(G(u, v, t), cv, acc);  // a = w3 = t, b = w2 - w1
-        }
-        if (in(v + t)) {
-            const float cu = c[u];
-            acc = fmaf(G(u, v, v + t), cu, acc);  // b = w3 - w2 = t, a = w1
-            acc = fmaf(G(v, u, v + t), cu, acc);  // b = w3 - w1 = t, a = w2
-            acc = fmaf(G(v, v + t, u), cu, acc);  // b = w2 - w1 = t, a = w3
-        }
+        const int u = q / twoL - L, v = q % twoL - L;  // v fastest
+        if (t >= -L && t < L) acc = fmaf(G(t, u, v), c[v - u], acc);          // H: a lag equals t
+        if (u + t >= -L && u + t < L) acc = fmaf(G(u, u + t, v), c[v], acc);  // K: w2 = u, w1 = v
     }
     red[threadIdx.x] = (double)acc;
     __syncthreads();
@@ -242,7 +241,7 @@ __global__ void __launch_bounds__(GC2_THREADS) gc2_kernel(const float* __restric
         if (threadIdx.x < d) red[threadIdx.x] += red[threadIdx.x + d];
         __syncthreads();
     }
-    if (threadIdx.x == 0) gc2[t + T] = -red[0];
+    if (threadIdx.x == 0) gc2[t + T] = -3.0 * red[0];
 }
 
 cudaError_t launch_gs4(const float2* Gc, int N, int L, int window, double scale, float* Gs4, cudaStream_t st) {

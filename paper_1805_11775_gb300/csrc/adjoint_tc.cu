@@ -457,56 +457,78 @@ struct CSum {
     __device__ float value() const { return hi + lo; }
 };
 
+// Gather: GJ samples j per CTA, GG thread groups per sample splitting the
+// blocks b (b = g, g + GG, ...) and the c2 lags; the groups' compensated sums
+// are then added in group order.  Third order has at most two blocks: one
+// group.
 constexpr int GATHER_THREADS = 256;
+template <int ORDER>
+__host__ __device__ constexpr int gather_groups() { return ORDER == 4 ? 4 : 1; }
 template <int ORDER>
 __global__ void __launch_bounds__(GATHER_THREADS) adjoint_tc_gather_kernel(
     const float* __restrict__ t1p, const float* __restrict__ t2p, int64_t n, int L, int nb, int64_t nut, int R,
     const double* __restrict__ gc2, const float* __restrict__ y, float* __restrict__ g) {
-    // fourth order: gc2 as FP32 and the block's samples y(j0 - T .. j0 + 255 + T)
+    // fourth order: gc2 as FP32 and the CTA's samples y(j0 - T .. j0 + GJ - 1 + T)
     __shared__ float gcs[ORDER == 4 ? 4 * 64 : 1];
-    __shared__ float ys[ORDER == 4 ? GATHER_THREADS + 4 * 64 : 1];
-    const int64_t j0 = (int64_t)blockIdx.x * GATHER_THREADS;
-    const int64_t j = j0 + threadIdx.x;
+    __shared__ float ys[ORDER == 4 ? GATHER_THREADS / gather_groups<ORDER>() + 4 * 64 : 1];
+    __shared__ int w1bs[ORDER == 4 ? 128 : 1];  // first lag of each block (nb <= 128 for L <= 64)
+    constexpr int GG = gather_groups<ORDER>(), GJ = GATHER_THREADS / GG;
+    __shared__ float2 part[GG][GJ];
+    const int jj = threadIdx.x % GJ, grp = threadIdx.x / GJ;
+    const int64_t j0 = (int64_t)blockIdx.x * GJ;
+    const int64_t j = j0 + jj;
+    const int T = 2 * L - 1;
     if constexpr (ORDER == 4) {
-        const int T = 2 * L - 1;
+        for (int b = threadIdx.x; b < nb; b += GATHER_THREADS) w1bs[b] = (b * AW) / (2 * L) - L;
         for (int i = threadIdx.x; i < 2 * T + 1; i += GATHER_THREADS) gcs[i] = (float)gc2[i];
-        for (int i = threadIdx.x; i < GATHER_THREADS + 2 * T; i += GATHER_THREADS) {
+        for (int i = threadIdx.x; i < GJ + 2 * T; i += GATHER_THREADS) {
             const int64_t a = j0 - T + i;
             ys[i] = (a >= 0 && a < n) ? y[a] : 0.0f;
         }
         __syncthreads();
     }
-    if (j >= n) return;
     const int E = AU + R - 1, D = 32 + R - 1;
-    CSum t1, t2;
-    for (int b = 0; b < nb; ++b) {
-        t1.add(t1p[(int64_t)b * (nut * AU) + j]);
-        const int64_t w1b = (ORDER == 3) ? (int64_t)b * AW - L : (int64_t)(b * AW) / (2 * L) - L;
-        int64_t lo = j - w1b - (E - 1);
-        lo = lo <= 0 ? 0 : ceil_div(lo, AU);
-        int64_t hi = (j - w1b) >= 0 ? (j - w1b) / AU : -1;
-        if (hi > nut - 1) hi = nut - 1;
-        for (int64_t ut = lo; ut <= hi; ++ut) {
-            const int64_t e = j - ut * AU - w1b;  // position in the item
-            if (e < 0 || e >= E) continue;
-            const float* it = t2p + (((int64_t)b * nut + ut) * 4) * D;
-            for (int w = 0; w < 4; ++w) {
-                const int64_t d = e - 32 * w;
-                if (d >= 0 && d < D) t2.add(it[w * D + d]);
+    CSum t1, t2, v;
+    if (j < n) {
+        for (int b = grp; b < nb; b += GG) {
+            t1.add(t1p[(int64_t)b * (nut * AU) + j]);
+            const int64_t w1b = (ORDER == 3) ? (int64_t)b * AW - L : (int64_t)w1bs[b];
+            int64_t lo = j - w1b - (E - 1);
+            lo = lo <= 0 ? 0 : ceil_div(lo, AU);
+            int64_t hi = (j - w1b) >= 0 ? (j - w1b) / AU : -1;
+            if (hi > nut - 1) hi = nut - 1;
+            for (int64_t ut = lo; ut <= hi; ++ut) {
+                const int64_t e = j - ut * AU - w1b;  // position in the item
+                if (e < 0 || e >= E) continue;
+                const float* it = t2p + (((int64_t)b * nut + ut) * 4) * D;
+                for (int w = 0; w < 4; ++w) {
+                    const int64_t d = e - 32 * w;
+                    if (d >= 0 && d < D) t2.add(it[w * D + d]);
+                }
             }
         }
+        v.add(t1.hi);
+        v.add(t1.lo);
+        v.add((float)(ORDER - 1) * t2.hi);
+        v.add((float)(ORDER - 1) * t2.lo);
+        if constexpr (ORDER == 4) {
+            const float* yj = ys + T + jj;  // yj[t] = y(j + t), |t| <= T
+            for (int t = -T + grp; t <= T; t += GG) v.add(gcs[t + T] * (yj[t] + yj[-t]));
+        }
     }
-    CSum v;
-    v.add(t1.hi);
-    v.add(t1.lo);
-    v.add((float)(ORDER - 1) * t2.hi);
-    v.add((float)(ORDER - 1) * t2.lo);
-    if constexpr (ORDER == 4) {
-        const int T = 2 * L - 1;
-        const float* yj = ys + T + threadIdx.x;  // yj[t] = y(j + t), |t| <= T
-        for (int t = -T; t <= T; ++t) v.add(gcs[t + T] * (yj[t] + yj[-t]));
+    if constexpr (GG == 1) {
+        if (j < n) g[j] = v.value();
+        return;
     }
-    g[j] = v.value();
+    part[grp][jj] = make_float2(v.hi, v.lo);
+    __syncthreads();
+    if (grp != 0 || j >= n) return;
+    CSum r;
+    for (int q = 0; q < GG; ++q) {
+        r.add(part[q][jj].x);
+        r.add(part[q][jj].y);
+    }
+    g[j] = r.value();
 }
 
 bool adjoint_tc_supported(int L) { return L >= 1 && L <= AMAXK / 2; }
@@ -553,7 +575,8 @@ static cudaError_t launch_adjoint_tc_order(const float* y32, const uint16_t* hi,
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    adjoint_tc_gather_kernel<ORDER><<<(unsigned)ceil_div(n, GATHER_THREADS), GATHER_THREADS, 0, st>>>(
+    adjoint_tc_gather_kernel<ORDER><<<(unsigned)ceil_div(n, GATHER_THREADS / gather_groups<ORDER>()), GATHER_THREADS,
+                                      0, st>>>(
         t1p, t2p, n, L, nb, nut, R, gc2, y32 + L, g);
     count_launch();
     return cudaGetLastError();

@@ -21,22 +21,36 @@ HOS_HD int pair_index(int w1, int w2, int L) {
 }
 
 // c2_s(t) for t in [-(2L-1), 2L-1] of every part s.  blockIdx.x = lag, .y =
-// part.  GB300 issues FP64 at about 1/64 of its FP32 rate, so the sum runs in
-// double-float on the FP32 pipes: each product y(i) y(i+t) of two floats is
-// split exactly into p + e (FMA), and p, e are added to a TwoSum chain per
-// thread; the block combines the chains in a fixed tree and writes FP64.
+// part, .z = slice of the part's samples (P slices).  GB300 issues FP64 at
+// about 1/64 of its FP32 rate, so the sum runs in double-float on the FP32
+// pipes: each product y(i) y(i+t) of two floats is split exactly into p + e
+// (FMA), and p, e are added to a TwoSum chain per thread; the block combines
+// the chains in a fixed tree.  P = 1 writes FP64 c2 directly; otherwise each
+// slice writes its double-float sum and c2_finish_kernel adds the P slices
+// in order.
 constexpr int C2_THREADS = 512;
+HOS_DEV float2 df2_add(float2 a, float2 b) {  // (a.h + a.l) + (b.h + b.l), renormalised
+    const float sm = a.x + b.x;
+    const float bb = sm - a.x;
+    float e = (a.x - (sm - bb)) + (b.x - bb);
+    e += a.y + b.y;
+    const float h = sm + e;
+    return make_float2(h, e - (h - sm));
+}
+
 __global__ void __launch_bounds__(C2_THREADS) c2_kernel(const float* __restrict__ y32, const int64_t* __restrict__ off,
-                                                        const int64_t* __restrict__ pad, int L,
-                                                        double* __restrict__ c2) {
+                                                        const int64_t* __restrict__ pad, int L, int P,
+                                                        double* __restrict__ c2, float2* __restrict__ c2p) {
     __shared__ float2 sh[C2_THREADS];
     const int T = 2 * L - 1;
     const int t = (int)blockIdx.x - T;
-    const int s = blockIdx.y;
+    const int s = blockIdx.y, z = blockIdx.z;
     const int64_t len = off[s + 1] - off[s];
     const float* y = y32 + pad[s] + L;  // y[i], zero-padded on both sides by >= L
     float hi = 0.0f, lo = 0.0f;
-    const int64_t i0 = t < 0 ? -t : 0, i1 = t > 0 ? len - t : len;
+    const int64_t a0 = t < 0 ? -t : 0, a1 = t > 0 ? len - t : len;
+    const int64_t span = a1 > a0 ? a1 - a0 : 0, per = (span + P - 1) / P;
+    const int64_t i0 = a0 + per * z, i1 = (i0 + per < a1) ? i0 + per : a1;
 #pragma unroll 4
     for (int64_t i = i0 + threadIdx.x; i < i1; i += C2_THREADS) {
         const float a = y[i], b = y[i + t];
@@ -50,19 +64,25 @@ __global__ void __launch_bounds__(C2_THREADS) c2_kernel(const float* __restrict_
     sh[threadIdx.x] = make_float2(hi, lo);
     __syncthreads();
     for (int d = C2_THREADS / 2; d > 0; d >>= 1) {
-        if (threadIdx.x < d) {  // (a.h + a.l) + (b.h + b.l), renormalised
-            const float2 a = sh[threadIdx.x], b = sh[threadIdx.x + d];
-            const float sm = a.x + b.x;
-            const float bb = sm - a.x;
-            float e = (a.x - (sm - bb)) + (b.x - bb);
-            e += a.y + b.y;
-            const float h = sm + e;
-            sh[threadIdx.x] = make_float2(h, e - (h - sm));
-        }
+        if (threadIdx.x < d) sh[threadIdx.x] = df2_add(sh[threadIdx.x], sh[threadIdx.x + d]);
         __syncthreads();
     }
-    if (threadIdx.x == 0)
-        c2[(int64_t)s * (2 * T + 1) + blockIdx.x] = len > 0 ? ((double)sh[0].x + (double)sh[0].y) / (double)len : 0.0;
+    if (threadIdx.x != 0) return;
+    const int64_t e = (int64_t)s * (2 * T + 1) + blockIdx.x;
+    if (P == 1) c2[e] = len > 0 ? ((double)sh[0].x + (double)sh[0].y) / (double)len : 0.0;
+    else c2p[e * P + z] = sh[0];
+}
+
+__global__ void c2_finish_kernel(const float2* __restrict__ c2p, const int64_t* __restrict__ off, int S, int L, int P,
+                                 double* __restrict__ c2) {
+    const int T = 2 * L - 1;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)S * (2 * T + 1)) return;
+    const int s = (int)(e / (2 * T + 1));
+    const int64_t len = off[s + 1] - off[s];
+    float2 a = c2p[e * P];
+    for (int z = 1; z < P; ++z) a = df2_add(a, c2p[e * P + z]);
+    c2[e] = len > 0 ? ((double)a.x + (double)a.y) / (double)len : 0.0;
 }
 
 constexpr int M4_PAIRS = 128;  // pairs per CTA
@@ -258,10 +278,22 @@ __global__ void c4_assemble_kernel(const double* __restrict__ m4buf, const doubl
         (float)c4 * ((float)r.scale * wv);
 }
 
-cudaError_t launch_c2(const float* y32, const int64_t* off, const int64_t* pad, int S, int L, double* c2,
-                      cudaStream_t st) {
+int c2_slices(int S, int64_t max_len) {
+    if (S > 16) return 1;  // S x (4L - 1) blocks already fill the GPU
+    int64_t p = max_len / 8192;
+    return (int)(p < 1 ? 1 : (p > 16 ? 16 : p));
+}
+
+cudaError_t launch_c2(const float* y32, const int64_t* off, const int64_t* pad, int S, int L, int P, double* c2,
+                      float2* c2p, cudaStream_t st) {
     const int T = 2 * L - 1;
-    c2_kernel<<<dim3((unsigned)(2 * T + 1), (unsigned)S), C2_THREADS, 0, st>>>(y32, off, pad, L, c2);
+    c2_kernel<<<dim3((unsigned)(2 * T + 1), (unsigned)S, (unsigned)P), C2_THREADS, 0, st>>>(y32, off, pad, L, P, c2,
+                                                                                             c2p);
+    count_launch();
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess || P == 1) return err;
+    const int64_t tot = (int64_t)S * (2 * T + 1);
+    c2_finish_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(c2p, off, S, L, P, c2);
     count_launch();
     return cudaGetLastError();
 }
@@ -279,7 +311,7 @@ cudaError_t launch_c4(const float* y32, const int64_t* off, const int64_t* pad, 
                       int CG, int64_t total_groups, double* c2, float* partials, const C4ReduceArgs& r,
                       cudaStream_t st) {
     const int T = 2 * L - 1;
-    c2_kernel<<<dim3((unsigned)(2 * T + 1), (unsigned)S), C2_THREADS, 0, st>>>(y32, off, pad, L, c2);
+    c2_kernel<<<dim3((unsigned)(2 * T + 1), (unsigned)S), C2_THREADS, 0, st>>>(y32, off, pad, L, 1, c2, nullptr);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

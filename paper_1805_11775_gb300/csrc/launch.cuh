@@ -132,8 +132,10 @@ cudaError_t launch_adjoint4_tc(const float* y32, const uint16_t* hi, const uint1
                                int* status, uint64_t limit_ns, int G, cudaStream_t st);
 cudaError_t launch_m4_tile_reduce(const C3Geom& geo, const SeriesView& sv, int64_t max_len, const float* partials,
                                   int64_t* bnd, TileRec* rec, float2* inv_len, double* m4buf, cudaStream_t st);
-cudaError_t launch_c2(const float* y32, const int64_t* off, const int64_t* pad, int S, int L, double* c2,
-                      cudaStream_t st);
+// P slices of each part's samples (c2_slices); c2p: S * (4L - 1) * P float2 when P > 1
+int c2_slices(int S, int64_t max_len);
+cudaError_t launch_c2(const float* y32, const int64_t* off, const int64_t* pad, int S, int L, int P, double* c2,
+                      float2* c2p, cudaStream_t st);
 cudaError_t launch_c4_assemble(const double* m4buf, const double* c2, const int64_t* off, int S, int L, int ntiles,
                                int tile_n, const C4ReduceArgs& r, int per_series, cudaStream_t st);
 cudaError_t launch_timeout_selftest(int* status, uint64_t limit_ns, cudaStream_t st);
