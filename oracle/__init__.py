@@ -70,6 +70,11 @@ def _load():
             lib.hos_oracle_grad_lag.argtypes = [_D, _I64, _I64, ctypes.c_int, _D]
             lib.hos_oracle_dy_at.argtypes = [_D, _I64, _I64, _D, ctypes.POINTER(_I64), _I64, _D]
             lib.hos_oracle_bispectrum_direct.argtypes = [_D, _I64, _I64, _I64, _I64, ctypes.c_int, _D]
+            lib.hos_oracle_bispectrum_overlap.argtypes = [_D, _I64, _I64, _I64, ctypes.c_int, ctypes.c_int, _I64,
+                                                          _I64, _D]
+            lib.hos_oracle_trispectrum_overlap.argtypes = [_D, _I64, _I64, _I64, ctypes.c_int, ctypes.c_int, _I64,
+                                                           _I64, _D]
+            lib.hos_oracle_cumulant_overlap.argtypes = [_D, _I64, _I64, ctypes.c_int, ctypes.c_int, _I64, _I64, _D]
             lib.hos_oracle_trispectrum_grad.argtypes = [_D, _I64, _I64, _I64, ctypes.c_int, ctypes.c_int, _D, _D]
             lib.hos_oracle_grad_lag4.argtypes = [_D, _I64, _I64, ctypes.c_int, _D]
             lib.hos_oracle_grad_c2.argtypes = [_D, _D, _I64, _D]
@@ -191,6 +196,39 @@ def trispectrum(x, L: int, N: int = 0, window: int = WIN_PARZEN, remove_mean: bo
     _load().hos_oracle_trispectrum(_p(x), x.size, int(L), int(N), int(window), int(bool(remove_mean)),
                                    int(segment_len), _p(out))
     return _complex(out, (N, N, N))
+
+
+def bispectrum_overlap(x, L: int, N: int = 0, window: int = WIN_PARZEN, remove_mean: bool = True,
+                       segment_len: int = 0, overlap: int = 0) -> np.ndarray:
+    """Parts of segment_len samples every segment_len - overlap samples (trailing
+    samples past the last whole part unused), each demeaned, c3 averaged."""
+    x = _f64(x)
+    N = N or 2 * L
+    out = np.empty(N * N * 2)
+    _load().hos_oracle_bispectrum_overlap(_p(x), x.size, int(L), int(N), int(window), int(bool(remove_mean)),
+                                          int(segment_len), int(overlap), _p(out))
+    return _complex(out, (N, N))
+
+
+def trispectrum_overlap(x, L: int, N: int = 0, window: int = WIN_PARZEN, remove_mean: bool = True,
+                        segment_len: int = 0, overlap: int = 0) -> np.ndarray:
+    x = _f64(x)
+    N = N or 2 * L
+    out = np.empty(N ** 3 * 2)
+    _load().hos_oracle_trispectrum_overlap(_p(x), x.size, int(L), int(N), int(window), int(bool(remove_mean)),
+                                           int(segment_len), int(overlap), _p(out))
+    return _complex(out, (N, N, N))
+
+
+def cumulant_overlap(x, L: int, order: int, remove_mean: bool = True, segment_len: int = 0,
+                     overlap: int = 0) -> np.ndarray:
+    """The parts' average c3 over [-L, L]^2 (order 3) or c4 over [-L, L]^3 (order 4)."""
+    x = _f64(x)
+    W = 2 * L + 1
+    out = np.empty(W ** (order - 1))
+    _load().hos_oracle_cumulant_overlap(_p(x), x.size, int(L), int(order), int(bool(remove_mean)),
+                                        int(segment_len), int(overlap), _p(out))
+    return out.reshape((W,) * (order - 1))
 
 
 def bispectrum_grad(x, L: int, G, N: int = 0, window: int = WIN_PARZEN, remove_mean: bool = True) -> np.ndarray:

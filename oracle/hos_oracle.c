@@ -368,6 +368,84 @@ void hos_oracle_trispectrum(const double* x, int64_t n, int64_t L, int64_t N, in
 }
 
 /* ------------------------------------------------------------------ */
+/* Overlapping parts (the multi-segment averaging of Algorithm DBS steps 1,
+ * 2 and 6 with parts that overlap): parts of m samples starting every
+ * m - overlap samples, K = floor((n - m) / (m - overlap)) + 1 of them;
+ * samples past the last whole part are not used; n <= m gives one part,
+ * the whole series.  Each part minus its own mean (when remove_mean), its
+ * cumulant with its own 1/m, the parts' cumulants averaged, then windowed
+ * and transformed as in hos_oracle_bispectrum / hos_oracle_trispectrum.     */
+static void overlap_parts(int64_t n, int64_t m, int64_t overlap, int64_t* K, int64_t* len, int64_t* step)
+{
+    if (m <= 0 || n <= m) {
+        *K = 1;
+        *len = n;
+        *step = n;
+        return;
+    }
+    *step = m - overlap;
+    *K = (n - m) / *step + 1;
+    *len = m;
+}
+
+/* accumulate the average over the parts of c3 (order 3) or c4 (order 4) */
+static void overlap_cumulant(const double* x, int64_t n, int64_t L, int order, int remove_mean, int64_t m,
+                             int64_t overlap, double* acc)
+{
+    const int64_t W = 2 * L + 1, WW = order == 3 ? W * W : W * W * W;
+    int64_t K, len, step;
+    overlap_parts(n, m, overlap, &K, &len, &step);
+    double* y = (double*)malloc(sizeof(double) * (size_t)len);
+    double* c = (double*)malloc(sizeof(double) * (size_t)WW);
+    for (int64_t q = 0; q < WW; ++q) acc[q] = 0.0;
+    for (int64_t p = 0; p < K; ++p) {
+        hos_oracle_demean(x + p * step, len, len, remove_mean, y);
+        if (order == 3) hos_oracle_c3(y, len, L, c);
+        else hos_oracle_c4(y, len, L, c);
+        for (int64_t q = 0; q < WW; ++q) acc[q] += c[q];
+    }
+    for (int64_t q = 0; q < WW; ++q) acc[q] /= (double)K;
+    free(y);
+    free(c);
+}
+
+void hos_oracle_bispectrum_overlap(const double* x, int64_t n, int64_t L, int64_t N, int window, int remove_mean,
+                                   int64_t seg, int64_t overlap, double* B)
+{
+    const int64_t W = 2 * L + 1;
+    double* acc = (double*)malloc(sizeof(double) * (size_t)(W * W));
+    overlap_cumulant(x, n, L, 3, remove_mean, seg, overlap, acc);
+    for (int64_t a = 0; a < W; ++a)
+        for (int64_t b = 0; b < W; ++b) acc[a * W + b] *= hos_oracle_window2(a - L, b - L, L, window);
+    const double s = 2.0 * HOS_ORACLE_PI;
+    hos_oracle_dft2(acc, L, N, -1.0, 1.0 / (s * s), B);
+    free(acc);
+}
+
+void hos_oracle_trispectrum_overlap(const double* x, int64_t n, int64_t L, int64_t N, int window, int remove_mean,
+                                    int64_t seg, int64_t overlap, double* T)
+{
+    const int64_t W = 2 * L + 1;
+    double* acc = (double*)malloc(sizeof(double) * (size_t)(W * W * W));
+    overlap_cumulant(x, n, L, 4, remove_mean, seg, overlap, acc);
+    for (int64_t a = 0; a < W; ++a)
+        for (int64_t b = 0; b < W; ++b)
+            for (int64_t c = 0; c < W; ++c)
+                acc[(a * W + b) * W + c] *= hos_oracle_window3(a - L, b - L, c - L, L, window);
+    const double s = 2.0 * HOS_ORACLE_PI;
+    hos_oracle_dft3(acc, L, N, -1.0, 1.0 / (s * s * s), T);
+    free(acc);
+}
+
+/* The averaged cumulant alone (no window, no transform), over [-L, L]^2 or
+ * [-L, L]^3, for checking hos_cumulant3 / hos_cumulant4.                    */
+void hos_oracle_cumulant_overlap(const double* x, int64_t n, int64_t L, int order, int remove_mean, int64_t seg,
+                                 int64_t overlap, double* out)
+{
+    overlap_cumulant(x, n, L, order, remove_mean, seg, overlap, out);
+}
+
+/* ------------------------------------------------------------------ */
 /* Gradient of a real loss l(B) through the bispectrum (one part, K = 1).
  * G holds dl/dRe B + i dl/dIm B on the N x N grid (complex interleaved).
  * The chain rule is taken step by step, in reverse order of the forward:
