@@ -111,6 +111,19 @@ typedef struct {
     int32_t flush_chunks; /* 0: automatic; else the most 1024-sample chunks one
                              tile accumulates in FP32 before its partial sum is
                              handed to the cross-chunk reduction (tuning knob)  */
+    int32_t segment_overlap; /* 0: parts do not overlap.  Else 1 <= overlap <
+                             segment_len: parts of exactly segment_len samples
+                             start every segment_len - overlap samples, K =
+                             floor((n - segment_len) / (segment_len - overlap))
+                             + 1 of them; samples past the last whole part are
+                             not used; n <= segment_len gives one part.  The
+                             parts are copied one after another into the
+                             workspace (K * segment_len samples, counted by
+                             hos_workspace_size) and averaged as above.  Only
+                             hos_bispectrum, hos_trispectrum, hos_cumulant3,
+                             hos_cumulant4 (and the no-allocation entry)
+                             accept it; the others return
+                             HOS_ERR_INVALID_ARG for a nonzero value.         */
 } hos_params;
 
 /* Bytes of workspace an operation needs.

@@ -37,11 +37,11 @@ def _torch():
 
 
 def make_params(L, nfft=0, precision="bf16", window="parzen", remove_mean=True, segment_len=0, tile_n=0,
-                flush_chunks=0) -> HosParams:
+                flush_chunks=0, segment_overlap=0) -> HosParams:
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     win = WINDOWS[window] if isinstance(window, str) else int(window)
     return HosParams(int(L), int(nfft or 0), prec, win, int(bool(remove_mean)), int(segment_len or 0),
-                     int(tile_n or 0), int(flush_chunks or 0))
+                     int(tile_n or 0), int(flush_chunks or 0), int(segment_overlap or 0))
 
 
 def _tuned(op, L, n_total, n_series, precision, tile_n, flush_chunks):
@@ -140,16 +140,18 @@ def _dtype_code(x):
 
 
 def bispectrum(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=True, segment_len=0, tile_n=0,
-               flush_chunks=0, out=None, workspace=None, stream=None):
+               flush_chunks=0, out=None, workspace=None, stream=None, segment_overlap=0):
     """Smoothed sample bispectrum B[k1, k2] (complex64, nfft x nfft, default nfft = 2L).
 
     ``precision``: "bf16" (split-bf16 tensor cores), "fp32" (3xTF32 tensor
     cores) or "simt" (FP32 CUDA cores).  Host input returns a host result; a
-    host ``out`` (pinned for speed) receives the result."""
+    host ``out`` (pinned for speed) receives the result.  ``segment_len`` > 0
+    averages parts of that many samples; ``segment_overlap`` makes them
+    overlap (parts start every segment_len - segment_overlap samples)."""
     torch = _torch()
     xd, host = _prepare(x)
     tile_n, flush_chunks = _tuned("bispectrum", L, xd.numel(), 1, precision, tile_n, flush_chunks)
-    p = make_params(L, nfft, precision, window, remove_mean, segment_len, tile_n, flush_chunks)
+    p = make_params(L, nfft, precision, window, remove_mean, segment_len, tile_n, flush_chunks, segment_overlap)
     N = p.nfft or 2 * p.L
     dev, host_out = _out_buffers(out, (N, N), xd.device)
     ws = _workspace(workspace, xd.device)
@@ -243,11 +245,11 @@ def bispectrum_batched(values, offsets, L, nfft=0, precision="bf16", window="par
 
 
 def cumulant3(x, L, precision="bf16", remove_mean=True, segment_len=0, tile_n=0, flush_chunks=0, workspace=None,
-              stream=None):
+              stream=None, segment_overlap=0):
     """Unwindowed sample c3 over [-L, L-1]^2 (float64, (2L, 2L), index w + L)."""
     torch = _torch()
     xd, host = _prepare(x)
-    p = make_params(L, 0, precision, "parzen", remove_mean, segment_len, tile_n, flush_chunks)
+    p = make_params(L, 0, precision, "parzen", remove_mean, segment_len, tile_n, flush_chunks, segment_overlap)
     out = torch.empty((2 * p.L, 2 * p.L), dtype=torch.float64, device=xd.device)
     ws = _workspace(workspace, xd.device)
     ws.get(workspace_size(_native.OP_CUMULANT3, xd.numel(), 1, xd.numel(), p))
@@ -258,11 +260,11 @@ def cumulant3(x, L, precision="bf16", remove_mean=True, segment_len=0, tile_n=0,
 
 
 def trispectrum(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=True, segment_len=0, flush_chunks=0,
-                out=None, workspace=None, stream=None):
+                out=None, workspace=None, stream=None, segment_overlap=0):
     """Smoothed sample trispectrum T[k1, k2, k3] (complex64, nfft^3)."""
     torch = _torch()
     xd, host = _prepare(x)
-    p = make_params(L, nfft, precision, window, remove_mean, segment_len, 0, flush_chunks)
+    p = make_params(L, nfft, precision, window, remove_mean, segment_len, 0, flush_chunks, segment_overlap)
     N = p.nfft or 2 * p.L
     dev, host_out = _out_buffers(out, (N, N, N), xd.device)
     ws = _workspace(workspace, xd.device)
@@ -296,11 +298,12 @@ def trispectrum_batched(values, offsets, L, nfft=0, precision="bf16", window="pa
     return _finish(dev, host_out, host)
 
 
-def cumulant4(x, L, precision="bf16", remove_mean=True, segment_len=0, flush_chunks=0, workspace=None, stream=None):
+def cumulant4(x, L, precision="bf16", remove_mean=True, segment_len=0, flush_chunks=0, workspace=None, stream=None,
+              segment_overlap=0):
     """Unwindowed sample c4 over [-L, L-1]^3 (float64, (2L, 2L, 2L))."""
     torch = _torch()
     xd, host = _prepare(x)
-    p = make_params(L, 0, precision, "parzen", remove_mean, segment_len, 0, flush_chunks)
+    p = make_params(L, 0, precision, "parzen", remove_mean, segment_len, 0, flush_chunks, segment_overlap)
     out = torch.empty((2 * p.L,) * 3, dtype=torch.float64, device=xd.device)
     ws = _workspace(workspace, xd.device)
     ws.get(workspace_size(_native.OP_CUMULANT4, xd.numel(), 1, xd.numel(), p))

@@ -93,6 +93,12 @@ static hos_status check_params(const hos_params* p, int op) {
     if (p->tile_n != 0 && p->tile_n != 32 && p->tile_n != 64 && p->tile_n != 128 && p->tile_n != 256)
         return HOS_ERR_INVALID_ARG;
     if (p->flush_chunks < 0) return HOS_ERR_INVALID_ARG;
+    if (p->segment_overlap < 0) return HOS_ERR_INVALID_ARG;
+    if (p->segment_overlap > 0) {
+        const bool parts_op = (op == HOS_OP_BISPECTRUM || op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT3 ||
+                               op == HOS_OP_CUMULANT4);
+        if (!parts_op || p->segment_len <= 0 || p->segment_overlap >= p->segment_len) return HOS_ERR_INVALID_ARG;
+    }
     if (op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT4 || op == HOS_OP_TRISPECTRUM_BATCHED ||
         op == HOS_OP_TRISPECTRUM_BACKWARD) {
         if (p->L > 64) return HOS_ERR_UNSUPPORTED;
@@ -105,6 +111,26 @@ static hos_status check_params(const hos_params* p, int op) {
     if ((op == HOS_OP_BISPECTRUM_BATCHED || op == HOS_OP_TRISPECTRUM_BATCHED) && p->segment_len != 0)
         return HOS_ERR_INVALID_ARG;
     return HOS_OK;
+}
+
+// Overlapping parts: parts of m = segment_len samples every m - overlap
+// samples are copied one after another into the workspace tail and run as
+// plain parts of m samples.  `on` is false when there is nothing to expand
+// (no overlap, or n <= m: one part).
+struct OverlapPlan {
+    bool on = false;
+    int64_t K = 1, m = 0, step = 0, n2 = 0;
+};
+
+static OverlapPlan overlap_plan(const hos_params* p, int64_t n) {
+    OverlapPlan o;
+    if (!p || p->segment_overlap <= 0 || p->segment_len <= 0 || n <= p->segment_len) return o;
+    o.on = true;
+    o.m = p->segment_len;
+    o.step = o.m - p->segment_overlap;
+    o.K = (n - o.m) / o.step + 1;
+    o.n2 = o.K * o.m;
+    return o;
 }
 
 // skip_zero_window: leave out tiles where the window is zero at every lag
@@ -701,6 +727,42 @@ static hos_status make_planb4(const hos_params* p, int64_t n, PlanB4& P) {
     return HOS_OK;
 }
 
+// Run `core` on x, or, with overlapping parts, on the parts copied one after
+// another into the workspace tail (as plain parts of segment_len samples).
+using PartsCore = hos_status (*)(const void* x, int32_t dtype, int64_t n, const hos_params* p, void* out, void* ws,
+                                 size_t ws_bytes, hos_stream_t stream);
+
+static hos_status overlap_workspace(int32_t op, int64_t n, const hos_params* p, const OverlapPlan& o, size_t* inner,
+                                    size_t* total) {
+    hos_params p2 = *p;
+    p2.segment_overlap = 0;
+    size_t b = 0;
+    hos_status s = hos_workspace_size(op, o.n2, 1, o.n2, &p2, &b);
+    if (s != HOS_OK) return s;
+    *inner = al256(b);
+    *total = *inner + (size_t)o.n2 * sizeof(double);
+    (void)n;
+    return HOS_OK;
+}
+
+static hos_status with_overlap(int32_t op, const void* d_x, int32_t dtype, int64_t n, const hos_params* p, void* out,
+                               void* ws, size_t ws_bytes, hos_stream_t stream, PartsCore core) {
+    if (!d_x || !out || n < 1 || (dtype != HOS_F32 && dtype != HOS_F64)) return HOS_ERR_INVALID_ARG;
+    hos_status s = check_params(p, op);
+    if (s != HOS_OK) return s;
+    const OverlapPlan o = overlap_plan(p, n);
+    hos_params p2 = *p;
+    p2.segment_overlap = 0;
+    if (!o.on) return core(d_x, dtype, n, &p2, out, ws, ws_bytes, stream);
+    size_t inner = 0, total = 0;
+    s = overlap_workspace(op, n, p, o, &inner, &total);
+    if (s != HOS_OK) return s;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < total) return HOS_ERR_WORKSPACE;
+    void* xs = static_cast<uint8_t*>(ws) + inner;
+    HOS_CUDA_TRY(launch_gather_parts(d_x, dtype, o.K, o.m, o.step, xs, reinterpret_cast<cudaStream_t>(stream)));
+    return core(xs, dtype, o.n2, &p2, out, ws, inner, stream);
+}
+
 }  // namespace hos
 
 using namespace hos;
@@ -729,6 +791,18 @@ hos_status hos_workspace_size(int32_t op, int64_t n_total, int32_t n_series, int
                               size_t* bytes) {
     if (!bytes || n_total < 0 || n_series < 1 || max_len < 0) return HOS_ERR_INVALID_ARG;
     if (op < 0 || op > HOS_OP_TRISPECTRUM_BACKWARD) return HOS_ERR_INVALID_ARG;
+    if (p && p->segment_overlap != 0) {
+        hos_status so = check_params(p, op);
+        if (so != HOS_OK) return so;
+        const OverlapPlan o = overlap_plan(p, n_total);
+        if (o.on) {
+            size_t inner = 0;
+            return overlap_workspace(op, n_total, p, o, &inner, bytes);
+        }
+        hos_params p2 = *p;
+        p2.segment_overlap = 0;
+        return hos_workspace_size(op, n_total, n_series, max_len, &p2, bytes);
+    }
     if (op == HOS_OP_TRISPECTRUM_BACKWARD) {
         PlanB4 P4;
         hos_status s4 = make_planb4(p, n_total, P4);
@@ -878,8 +952,8 @@ hos_status hos_bispectrum_direct(const void* d_x, int32_t dtype, int64_t n, int3
     return HOS_OK;
 }
 
-hos_status hos_bispectrum(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, void* d_B, void* ws,
-                          size_t ws_bytes, hos_stream_t stream) {
+static hos_status bispectrum_core(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, void* d_B, void* ws,
+                                  size_t ws_bytes, hos_stream_t stream) {
     if (!d_x || !d_B || n < 1 || (dtype != HOS_F32 && dtype != HOS_F64)) return HOS_ERR_INVALID_ARG;
     Plan P;
     hos_status s = make_plan(HOS_OP_BISPECTRUM, p, n, 1, n, P);
@@ -916,8 +990,9 @@ hos_status hos_bispectrum_batched(const void* d_x, int32_t dtype, const int64_t*
     return s;
 }
 
-hos_status hos_cumulant3(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, double* d_c3, void* ws,
-                         size_t ws_bytes, hos_stream_t stream) {
+static hos_status cumulant3_core(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, void* out, void* ws,
+                                 size_t ws_bytes, hos_stream_t stream) {
+    double* d_c3 = static_cast<double*>(out);
     if (!d_x || !d_c3 || n < 1 || (dtype != HOS_F32 && dtype != HOS_F64)) return HOS_ERR_INVALID_ARG;
     Plan P;
     hos_status s = make_plan(HOS_OP_CUMULANT3, p, n, 1, n, P);
@@ -929,8 +1004,8 @@ hos_status hos_cumulant3(const void* d_x, int32_t dtype, int64_t n, const hos_pa
     return s;
 }
 
-hos_status hos_trispectrum(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, void* d_T, void* ws,
-                           size_t ws_bytes, hos_stream_t stream) {
+static hos_status trispectrum_core(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, void* d_T,
+                                   void* ws, size_t ws_bytes, hos_stream_t stream) {
     if (!d_x || !d_T || n < 1 || (dtype != HOS_F32 && dtype != HOS_F64)) return HOS_ERR_INVALID_ARG;
     Plan4 P;
     hos_status s = make_plan4(HOS_OP_TRISPECTRUM, p, n, P);
@@ -965,8 +1040,9 @@ hos_status hos_trispectrum_batched(const void* d_x, int32_t dtype, const int64_t
     return s;
 }
 
-hos_status hos_cumulant4(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, double* d_c4, void* ws,
-                         size_t ws_bytes, hos_stream_t stream) {
+static hos_status cumulant4_core(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, void* out, void* ws,
+                                 size_t ws_bytes, hos_stream_t stream) {
+    double* d_c4 = static_cast<double*>(out);
     if (!d_x || !d_c4 || n < 1 || (dtype != HOS_F32 && dtype != HOS_F64)) return HOS_ERR_INVALID_ARG;
     Plan4 P;
     hos_status s = make_plan4(HOS_OP_CUMULANT4, p, n, P);
@@ -977,6 +1053,26 @@ hos_status hos_cumulant4(const void* d_x, int32_t dtype, int64_t n, const hos_pa
     tr.mark("");
     return s;
 }
+hos_status hos_bispectrum(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, void* d_B, void* ws,
+                          size_t ws_bytes, hos_stream_t stream) {
+    return with_overlap(HOS_OP_BISPECTRUM, d_x, dtype, n, p, d_B, ws, ws_bytes, stream, bispectrum_core);
+}
+
+hos_status hos_cumulant3(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, double* d_c3, void* ws,
+                         size_t ws_bytes, hos_stream_t stream) {
+    return with_overlap(HOS_OP_CUMULANT3, d_x, dtype, n, p, d_c3, ws, ws_bytes, stream, cumulant3_core);
+}
+
+hos_status hos_trispectrum(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, void* d_T, void* ws,
+                           size_t ws_bytes, hos_stream_t stream) {
+    return with_overlap(HOS_OP_TRISPECTRUM, d_x, dtype, n, p, d_T, ws, ws_bytes, stream, trispectrum_core);
+}
+
+hos_status hos_cumulant4(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, double* d_c4, void* ws,
+                         size_t ws_bytes, hos_stream_t stream) {
+    return with_overlap(HOS_OP_CUMULANT4, d_x, dtype, n, p, d_c4, ws, ws_bytes, stream, cumulant4_core);
+}
+
 hos_status hos_bispectrum_backward(const void* d_x, int32_t dtype, int64_t n, const hos_params* p, const void* d_dB,
                                    void* d_dx, void* ws, size_t ws_bytes, hos_stream_t stream) {
     if (!d_x || !d_dB || !d_dx || n < 1 || (dtype != HOS_F32 && dtype != HOS_F64)) return HOS_ERR_INVALID_ARG;

@@ -91,6 +91,8 @@ cudaError_t launch_planes(const void* x, int dtype, const int64_t* off, const in
                           int64_t ext_lo = 0, int64_t ext_hi = 0);
 cudaError_t launch_window_c3(const double* c3, int L, int window, int Nf, double scale, float* wtab, float* grid,
                              cudaStream_t st);
+cudaError_t launch_gather_parts(const void* x, int dtype, int64_t K, int64_t m, int64_t step, void* out,
+                                cudaStream_t st);
 cudaError_t launch_series_sum(const void* x, int dtype, int64_t n, int nslices, int64_t* off, double* part,
                               double* sum, cudaStream_t st);
 // direct method (direct.cu)

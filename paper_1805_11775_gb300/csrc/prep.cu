@@ -233,4 +233,27 @@ cudaError_t launch_series_sum(const void* x, int dtype, int64_t n, int nslices, 
     return launch_mean(x, dtype, off, 1, nslices, part, -1, sum, st);
 }
 
+// Overlapping parts written out one after another: out[k m + i] = x[k step + i],
+// k < K, i < m (element type T: the caller's float or double).
+template <typename T>
+__global__ void gather_parts_kernel(const T* __restrict__ x, int64_t K, int64_t m, int64_t step, T* __restrict__ out) {
+    const int64_t tot = K * m;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = e / m, i = e - k * m;
+        out[e] = x[k * step + i];
+    }
+}
+
+cudaError_t launch_gather_parts(const void* x, int dtype, int64_t K, int64_t m, int64_t step, void* out,
+                                cudaStream_t st) {
+    int64_t blocks = ceil_div(K * m, 256);
+    if (blocks > 16 * 152) blocks = 16 * 152;
+    if (dtype == HOS_F64)
+        gather_parts_kernel<double><<<(unsigned)blocks, 256, 0, st>>>((const double*)x, K, m, step, (double*)out);
+    else
+        gather_parts_kernel<float><<<(unsigned)blocks, 256, 0, st>>>((const float*)x, K, m, step, (float*)out);
+    count_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace hos

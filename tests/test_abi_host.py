@@ -126,3 +126,24 @@ def test_trispectrum_backward_workspace_and_limits(lib):
     p = _params(L=8, precision=1)
     assert lib.hos_trispectrum_backward(None, 0, 100, ctypes.byref(p), dummy, dummy, ws, 1 << 20, None) == 1
     assert lib.hos_trispectrum_backward(dummy, 0, 100, ctypes.byref(p), dummy, dummy, ws, 64, None) == 3
+
+
+def test_overlap_workspace_and_checks(lib):
+    """Overlapping parts: the workspace holds the parts written out (K x m
+    samples) beyond the plan for K x m samples; bad overlaps are refused on
+    the host, and ops without parts refuse any overlap."""
+    from paper_1805_11775_gb300 import workspace_size, _native, HosError
+    n, m, o = 100_000, 4096, 1024
+    K = (n - m) // (m - o) + 1
+    plain = workspace_size(_native.OP_BISPECTRUM, K * m, 1, K * m, _params(L=64, segment_len=m))
+    ov = workspace_size(_native.OP_BISPECTRUM, n, 1, n, _params(L=64, segment_len=m, segment_overlap=o))
+    assert ov >= plain + K * m * 8
+    same = workspace_size(_native.OP_BISPECTRUM, 3000, 1, 3000, _params(L=64, segment_len=m, segment_overlap=o))
+    assert same == workspace_size(_native.OP_BISPECTRUM, 3000, 1, 3000, _params(L=64, segment_len=m))
+    for bad in (_params(L=8, segment_len=100, segment_overlap=100), _params(L=8, segment_overlap=5),
+                _params(L=8, segment_len=100, segment_overlap=-1)):
+        with pytest.raises(HosError):
+            workspace_size(_native.OP_BISPECTRUM, n, 1, n, bad)
+    for op in (_native.OP_BISPECTRUM_BATCHED, _native.OP_TRISPECTRUM_BACKWARD, _native.OP_SERIES_SUM):
+        with pytest.raises(HosError):
+            workspace_size(op, n, 1, n, _params(L=8, segment_len=100, segment_overlap=5, precision=1))
