@@ -19,8 +19,13 @@ constexpr int REDUCE_THREADS = 256;
 // CTAs whose unit range starts strictly inside the (s, t) unit range,
 // [xlo, xhi) -- those CTAs' first parts, when they begin mid flush-window,
 // live in per-CTA slots.  Also 1/n of each series' time average.
-__global__ void part_ranges_kernel(const C3Geom geo, const SeriesView sv, const int64_t* __restrict__ bnd,
+// bnd (G + 1 values) is staged in shared memory once per block; both CTA
+// searches are binary searches there.
+__global__ void part_ranges_kernel(const C3Geom geo, const SeriesView sv, const int64_t* __restrict__ bnd_g,
                                    TileRec* __restrict__ rec, float2* __restrict__ inv_len, int64_t norm_len) {
+    extern __shared__ int64_t bnd[];
+    for (int g = threadIdx.x; g <= geo.G; g += blockDim.x) bnd[g] = bnd_g[g];
+    __syncthreads();
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= (int64_t)sv.S * geo.ntiles) return;
     const int s = (int)(q / geo.ntiles), t = (int)(q % geo.ntiles);
@@ -32,8 +37,11 @@ __global__ void part_ranges_kernel(const C3Geom geo, const SeriesView sv, const 
         const int mid = (lo + hi) >> 1;
         if (bnd[mid] > ub) hi = mid; else lo = mid + 1;
     }
-    int e = lo;
-    while (e < geo.G && bnd[e] < ue) ++e;
+    int e = lo, eh = geo.G;  // first CTA from lo on starting at or after ue (G if none)
+    while (e < eh) {
+        const int mid = (e + eh) >> 1;
+        if (bnd[mid] >= ue) eh = mid; else e = mid + 1;
+    }
     TileRec r;
     r.slot = sv.win[s] + (int64_t)t * nwin;
     r.ub = ub;
@@ -94,9 +102,9 @@ HOS_DEV double df_to_double(DF a) { return (double)a.h + (double)a.l; }
 // four consecutive elements of vector vi (elements 4 vi .. 4 vi + 3), as
 // double-float: the main parts in groups of 16 windows, each group a TwoSum
 // chain in window order, groups gi, gi + gsplit, ... added in that order;
-// thread row gi = 0 then adds the parts that start at a CTA boundary inside a
-// window, in CTA order.  Not divided by the length.  Loads go BATCH windows
-// at a time.
+// then the parts that start at a CTA boundary inside a window, CTA g on row
+// (g - xlo) % gsplit, in CTA order.  Not divided by the length.  Loads go
+// BATCH windows at a time.
 template <int BATCH>
 HOS_DEV void tile_share4(const float* __restrict__ partials, const TileRec& r, int tsz, int vi, int gi, int gsplit,
                          int F, const int64_t* __restrict__ bnd, int64_t total_win, DF (&acc)[4]) {
@@ -134,14 +142,25 @@ HOS_DEV void tile_share4(const float* __restrict__ partials, const TileRec& r, i
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[c] = df_add(acc[c], DF{hi[c], lo[c]});
     }
-    if (gi != 0) return;
-    for (int g = r.xlo; g < r.xhi; ++g) {
-        if ((int)(bnd[g] - r.ub) % F == 0 || bnd[g] >= bnd[g + 1]) continue;
-        const float4 x = reinterpret_cast<const float4*>(partials + (total_win + g) * (int64_t)tsz)[vi];
-        acc[0] = df_add(acc[0], DF{x.x, 0.0f});
-        acc[1] = df_add(acc[1], DF{x.y, 0.0f});
-        acc[2] = df_add(acc[2], DF{x.z, 0.0f});
-        acc[3] = df_add(acc[3], DF{x.w, 0.0f});
+    // parts that start at a CTA boundary inside a window: CTA g to row
+    // (g - xlo) % gsplit, each row's in CTA order, four loads in flight
+    constexpr int XB = 4;
+    for (int g0 = r.xlo + gi; g0 < r.xhi; g0 += XB * gsplit) {
+        float4 x[XB];
+#pragma unroll
+        for (int u = 0; u < XB; ++u) {
+            const int g = g0 + u * gsplit;
+            const bool use = g < r.xhi && (int)(bnd[g] - r.ub) % F != 0 && bnd[g] < bnd[g + 1];
+            x[u] = use ? reinterpret_cast<const float4*>(partials + (total_win + g) * (int64_t)tsz)[vi]
+                       : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < XB; ++u) {
+            acc[0] = df_add(acc[0], DF{x[u].x, 0.0f});
+            acc[1] = df_add(acc[1], DF{x[u].y, 0.0f});
+            acc[2] = df_add(acc[2], DF{x[u].z, 0.0f});
+            acc[3] = df_add(acc[3], DF{x[u].w, 0.0f});
+        }
     }
 }
 
@@ -357,8 +376,8 @@ static cudaError_t launch_part_index(const C3Geom& geo, const SeriesView& sv, in
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    part_ranges_kernel<<<(unsigned)ceil_div((int64_t)sv.S * geo.ntiles, 256), 256, 0, st>>>(geo, sv, bnd, rec, inv_len,
-                                                                                              norm_len);
+    part_ranges_kernel<<<(unsigned)ceil_div((int64_t)sv.S * geo.ntiles, 256), 256, sizeof(int64_t) * (geo.G + 1), st>>>(
+        geo, sv, bnd, rec, inv_len, norm_len);
     count_launch();
     return cudaGetLastError();
 }
