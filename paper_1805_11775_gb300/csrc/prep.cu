@@ -154,6 +154,32 @@ __global__ void planes_kernel(const T* __restrict__ x, const int64_t* __restrict
     const int64_t p0 = pad[s], p1 = pad[s + 1];
     const int64_t o0 = off[s], len = off[s + 1] - o0;
     const double mu = mean[s];
+    if (split == 1) {
+        // four samples per thread: one 16-byte y store and 8-byte hi and lo
+        // stores (p0 and p1 are multiples of 64)
+        for (int64_t p = p0 + 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); p < p1;
+             p += 4 * (int64_t)gridDim.x * blockDim.x) {
+            float v[4];
+            uint32_t hv[2], lv[2];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int64_t i = p + c - p0 - L;
+                v[c] = (i >= -ext_lo && i < len + ext_hi) ? (float)((double)x[o0 + i] - mu) : 0.0f;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; c += 2) {
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(v[c]), h1 = __float2bfloat16_rn(v[c + 1]);
+                const __nv_bfloat16 l0 = __float2bfloat16_rn(v[c] - __bfloat162float(h0));
+                const __nv_bfloat16 l1 = __float2bfloat16_rn(v[c + 1] - __bfloat162float(h1));
+                hv[c / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                lv[c / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+            *reinterpret_cast<float4*>(y32 + p) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(hi) + p) = make_uint2(hv[0], hv[1]);
+            *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(lo) + p) = make_uint2(lv[0], lv[1]);
+        }
+        return;
+    }
     for (int64_t p = p0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < p1;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = p - p0 - L;
@@ -177,8 +203,10 @@ __global__ void planes_kernel(const T* __restrict__ x, const int64_t* __restrict
 cudaError_t launch_plan_series(int mode, int64_t n, int64_t seg, const int64_t* d_user_off, int S, int L, int ntiles,
                                int flush, int kc, int pad_tail, int64_t* off, int64_t* pad, int64_t* unit,
                                int64_t* win, cudaStream_t st) {
-    plan_series_kernel<<<1, 1024, 0, st>>>(mode, n, seg, d_user_off, S, L, ntiles, flush, kc, pad_tail, off, pad, unit,
-                                           win);
+    int threads = 32;  // one block; its scans take log2(threads) steps
+    while (threads < S && threads < 1024) threads <<= 1;
+    plan_series_kernel<<<1, threads, 0, st>>>(mode, n, seg, d_user_off, S, L, ntiles, flush, kc, pad_tail, off, pad,
+                                              unit, win);
     count_launch();
     return cudaGetLastError();
 }
