@@ -491,7 +491,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches_per_step = hos.launch_count() - n0
     graph = None
-    if args.graph:
+    # one GPU: replay a captured CUDA graph of the step (the launches of every
+    # stage, no host gaps); the time-sliced multi-rank step runs eagerly
+    sliced = args.workload == WORKLOAD and (world > 1 or args.time_slices)
+    if args.graph or (not args.eager and not sliced):
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph):
             step()
@@ -655,7 +658,9 @@ def main():
                     choices=[WORKLOAD, "bispectrum_n2048_L32", "trispectrum_n65536_L32", "batched_4096x_L128",
                              "differentiable_n262144_L128", "differentiable_trispectrum_n65536_L32",
                              "direct_bispectrum_n8192_M3_279"])
-    ap.add_argument("--graph", action="store_true", help="capture one step in a CUDA graph and replay it")
+    ap.add_argument("--graph", action="store_true", help="capture one step in a CUDA graph and replay it "
+                    "(the default on one rank)")
+    ap.add_argument("--eager", action="store_true", help="launch every step's kernels eagerly instead")
     ap.add_argument("--series", type=int, default=0, help="batched workload: use only the first K series")
     ap.add_argument("--time-slices", action="store_true",
                     help="long workload: run the time-sliced path (the N > 1 layout) even on one rank")
