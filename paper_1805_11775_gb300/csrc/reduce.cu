@@ -255,7 +255,10 @@ HOS_DEV void emit_c3x4(const Reduce3Params& P, const float* __restrict__ wtab, i
 // series (gsplit > 1 with NV = 1); many short series take NV = 2 instead.
 // Per series: sum of its parts / its length; parts (segments) average over
 // the group.
-template <int NV, int BATCH>
+// SINGLE_APART: per-series groups whose (series, tile) has one window and no
+// mid-window part are left to reduce3_single_kernel (small code, no i-cache
+// pressure from the general path); this kernel returns for them.
+template <int NV, int BATCH, bool SINGLE_APART = false>
 __global__ void __launch_bounds__(REDUCE_THREADS, BATCH >= 16 ? 2 : 3) reduce3_kernel(const Reduce3Params P, const int64_t* __restrict__ bnd,
                                                                  const TileRec* __restrict__ rec,
                                                                  const float2* __restrict__ inv_len,
@@ -275,6 +278,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS, BATCH >= 16 ? 2 : 3) reduce3_k
         // one window and no part starting inside (most short series): c3 = x / len,
         // the general path's arithmetic, with all NV vector loads in flight at once
         const TileRec r = rec[(int64_t)grp * geo.ntiles + t];
+        if (SINGLE_APART && r.nwin == 1 && r.xlo >= r.xhi) return;
         if (r.nwin == 1 && r.xlo >= r.xhi) {
             const float2 il = inv_len[grp];
             const float4* p4 = reinterpret_cast<const float4*>(P.partials + r.slot * (int64_t)tsz);
@@ -360,6 +364,40 @@ __global__ void __launch_bounds__(REDUCE_THREADS) m4_tile_reduce_kernel(const C3
     dst[1] = make_double2(o[2], o[3]);
 }
 
+// The one-window, no-mid-window-part (series, tile) groups of a per-series
+// reduction: c3 = x / len with NV float4 loads in flight per thread, then
+// the window and the grid store; other groups return (reduce3_kernel takes
+// them).  Same arithmetic as the general path.
+template <int NV>
+__global__ void __launch_bounds__(REDUCE_THREADS) reduce3_single_kernel(const Reduce3Params P,
+                                                                        const TileRec* __restrict__ rec,
+                                                                        const float2* __restrict__ inv_len,
+                                                                        const float* __restrict__ wtab) {
+    const C3Geom& geo = P.geom;
+    const int t = blockIdx.y, grp = blockIdx.z;
+    const int tsz = TILE_M * geo.tile_n, nvec = tsz >> 2;
+    const TileRec r = rec[(int64_t)grp * geo.ntiles + t];
+    if (!(r.nwin == 1 && r.xlo >= r.xhi)) return;  // uniform over the block
+    const float2 il = inv_len[grp];
+    const float4* p4 = reinterpret_cast<const float4*>(P.partials + r.slot * (int64_t)tsz);
+    int vi[NV];
+    float4 x[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        vi[k] = (blockIdx.x * NV + k) * REDUCE_THREADS + threadIdx.x;
+        x[k] = p4[vi[k] < nvec ? vi[k] : 0];
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        if (vi[k] >= nvec) continue;
+        const float xv[4] = {x[k].x, x[k].y, x[k].z, x[k].w};
+        DF v[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = df_mul(DF{xv[c], 0.0f}, DF{il.x, il.y});
+        emit_c3x4(P, wtab, grp, t, 4 * vi[k], v);
+    }
+}
+
 // Rows of threads that split a (series, tile)'s flush windows: one per group
 // of 16 windows, at most 8; 1 when the longest series has one group.
 static int window_split(const C3Geom& geo, int64_t max_len) {
@@ -428,7 +466,13 @@ cudaError_t launch_reduce3(const Reduce3Params& p, int groups, int64_t max_len, 
     if (gsplit == 1 && ceil_div(nvec, REDUCE_THREADS) * p.geom.ntiles * groups >= 4096) {
         // many (short) output groups: four vectors per thread
         dim3 grid((unsigned)ceil_div(nvec, 4 * REDUCE_THREADS), (unsigned)p.geom.ntiles, (unsigned)groups);
-        reduce3_kernel<4, 4><<<grid, REDUCE_THREADS, 0, st>>>(p, bnd, rec, inv_len, wtab, 1);
+        if (p.per_series_groups) {  // one-window groups in their own small kernel
+            reduce3_single_kernel<4><<<grid, REDUCE_THREADS, 0, st>>>(p, rec, inv_len, wtab);
+            count_launch();
+            reduce3_kernel<4, 4, true><<<grid, REDUCE_THREADS, 0, st>>>(p, bnd, rec, inv_len, wtab, 1);
+        } else {
+            reduce3_kernel<4, 4><<<grid, REDUCE_THREADS, 0, st>>>(p, bnd, rec, inv_len, wtab, 1);
+        }
     } else {
         dim3 grid((unsigned)ceil_div(nvec, REDUCE_THREADS / gsplit), (unsigned)p.geom.ntiles, (unsigned)groups);
         // a thread row with several groups of 16 windows keeps all 16 loads of a group in flight;
