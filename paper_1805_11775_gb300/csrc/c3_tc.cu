@@ -170,8 +170,17 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                     bulk_g2s(sm.yi_raw, P.y32 + ib_al, yib, &sm.tma_bar);
                 }
                 ok = warp_wait(&sm.tma_bar, tph, abort, P.status, lim, 1000);
+                if (!ok) {
+                    // the copies just issued still land in this CTA's shared memory:
+                    // wait for them (bounded, whatever the abort flag says) before exiting
+                    if (lane == 0) {
+                        volatile int keep_waiting = 0;
+                        mbar_wait(&sm.tma_bar, tph, &keep_waiting, P.status, lim);
+                    }
+                    __syncwarp();
+                    break;
+                }
                 tph ^= 1;
-                if (!ok) break;
                 {   // realign y(i0 + t) so that builders can use 16-byte broadcast loads
                     const int ish = (int)(ib - ib_al);
                     for (int t = lane; t < csz; t += 32)
