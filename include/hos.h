@@ -93,7 +93,9 @@ typedef enum {
     HOS_OP_CUMULANT3_SLICE = 7,
     HOS_OP_BISPECTRUM_FROM_C3 = 8,
     HOS_OP_TRISPECTRUM_BATCHED = 9,
-    HOS_OP_TRISPECTRUM_BACKWARD = 10
+    HOS_OP_TRISPECTRUM_BACKWARD = 10,
+    HOS_OP_MOMENTS4_SLICE = 11,
+    HOS_OP_TRISPECTRUM_FROM_MOMENTS = 12
 } hos_op;
 
 typedef struct {
@@ -166,6 +168,33 @@ hos_status hos_bispectrum_batched(const void* d_x, int32_t dtype, const int64_t*
 hos_status hos_trispectrum_batched(const void* d_x, int32_t dtype, const int64_t* d_offsets, int32_t S,
                                    int64_t n_total, int64_t max_len, const hos_params* params, void* d_T, void* ws,
                                    size_t ws_bytes, hos_stream_t stream);
+
+/* ---- fourth order over time slices ----------------------------------------
+ * The trispectrum's m4 and c2 are sums over time too: rank r sums over its
+ * own samples i in [a_r, b_r), reading up to L samples before the slice and
+ * 2L - 1 after it (the c2 lags reach 2L - 1) as lags only.  After FP64 sum
+ * all-reduces of the series' total (hos_series_sum), then of m4 and c2,
+ * hos_trispectrum_from_moments forms c4 = m4 - (three c2 c2 products) and
+ * transforms it, in the same FP32 arithmetic as hos_trispectrum.
+ *
+ * hos_moments4_slice (op HOS_OP_MOMENTS4_SLICE; tensor-core precisions,
+ * L <= 64, segment_len = 0):
+ *   d_x        : halo_before + n_slice + halo_after samples (this slice with
+ *                its neighbours' samples around it)
+ *   halo_before <= L, halo_after <= 2L (fewer at the series' ends)
+ *   d_sum      : 1 double, the whole series' sum (all slices added)
+ *   n_total    : length of the whole series (the 1/n of the time average)
+ *   d_m4       : (2L)^3 doubles [w1+L][w2+L][w3+L]: (1/n_total) sum over the
+ *                slice's i of y(i) y(i+w1) y(i+w2) y(i+w3), y = x - mean
+ *   d_c2       : 4L - 1 doubles, index t + 2L - 1: (1/n_total) sum over the
+ *                slice's i of y(i) y(i+|t|) (c2 is even in t once joined)
+ * hos_trispectrum_from_moments (op HOS_OP_TRISPECTRUM_FROM_MOMENTS):
+ *   d_m4, d_c2 : the joined sums; d_T: nfft^3 complex64 as hos_trispectrum.  */
+hos_status hos_moments4_slice(const void* d_x, int32_t dtype, int64_t n_slice, int64_t halo_before, int64_t halo_after,
+                              const double* d_sum, int64_t n_total, const hos_params* params, double* d_m4,
+                              double* d_c2, void* ws, size_t ws_bytes, hos_stream_t stream);
+hos_status hos_trispectrum_from_moments(const double* d_m4, const double* d_c2, const hos_params* params, void* d_T,
+                                        void* ws, size_t ws_bytes, hos_stream_t stream);
 
 /* Adjoint of hos_bispectrum (one part only, segment_len = 0): the gradient of a
  * real loss l through B.

@@ -23,7 +23,7 @@ from ._native import HosError, HosParams
 __all__ = ["bispectrum", "bispectrum_batched", "trispectrum", "trispectrum_batched", "cumulant3", "cumulant4",
            "bispectrum_backward", "trispectrum_backward", "BispectrumFn", "TrispectrumFn", "bispectrum_ad",
            "trispectrum_ad", "bispectrum_direct", "series_sum", "cumulant3_slice", "bispectrum_from_cumulant",
-           "bispectrum_sharded", "Workspace", "workspace_size", "device_status", "reset_device_status",
+           "bispectrum_sharded", "moments4_slice", "trispectrum_from_moments", "trispectrum_sharded", "Workspace", "workspace_size", "device_status", "reset_device_status",
            "selftest_timeout", "set_profiling", "stage_times", "launch_count", "last_contraction", "HosError",
            "PRECISIONS", "WINDOWS"]
 
@@ -385,6 +385,71 @@ def bispectrum_sharded(x_local, L, halo_before, halo_after, n_total, nfft=0, pre
     if distributed:
         dist.all_reduce(c3, op=dist.ReduceOp.SUM, group=group)
     return bispectrum_from_cumulant(c3, L, nfft, window, workspace=workspace)
+
+
+def moments4_slice(x, L, halo_before, halo_after, total_sum, n_total, precision="bf16", remove_mean=True,
+                   flush_chunks=0, workspace=None, stream=None):
+    """One time slice's share of the fourth moment and of c2 of a longer
+    series: (m4 float64 (2L, 2L, 2L), c2 float64 (4L - 1,)).
+
+    ``x`` holds ``halo_before`` (<= L) samples before the slice, the slice,
+    and ``halo_after`` (<= 2L) after it, fewer only at the series' ends
+    (:func:`shard.time_slices` with ``halo_after=2 * L``).  Summing the
+    slices' m4 and c2 gives the whole series' (time averages over n_total)."""
+    torch = _torch()
+    xd, _ = _prepare(x)
+    n_slice = xd.numel() - int(halo_before) - int(halo_after)
+    p = make_params(L, 0, precision, "parzen", remove_mean, 0, 0, flush_chunks)
+    tot = total_sum.to(device=xd.device, dtype=torch.float64).contiguous()
+    m4 = torch.empty((2 * p.L,) * 3, dtype=torch.float64, device=xd.device)
+    c2 = torch.empty(4 * p.L - 1, dtype=torch.float64, device=xd.device)
+    ws = _workspace(workspace, xd.device)
+    ws.get(workspace_size(_native.OP_MOMENTS4_SLICE, max(n_slice, 0), 1, max(n_slice, 0), p))
+    _native.check(_native.lib().hos_moments4_slice(xd.data_ptr(), _dtype_code(xd), n_slice, int(halo_before),
+                                                   int(halo_after), tot.data_ptr(), int(n_total), ctypes.byref(p),
+                                                   m4.data_ptr(), c2.data_ptr(), ws.ptr(), ws.nbytes(),
+                                                   _stream(stream)), "hos_moments4_slice")
+    return m4, c2
+
+
+def trispectrum_from_moments(m4, c2, L, nfft=0, window="parzen", out=None, workspace=None, stream=None):
+    """c4 = m4 - (three c2 c2 products), window, scale and 3-D transform: T
+    from joined time-slice moments (:func:`moments4_slice`)."""
+    torch = _torch()
+    md = m4.to(torch.float64).contiguous()
+    cd = c2.to(device=md.device, dtype=torch.float64).contiguous()
+    p = make_params(L, nfft, "bf16", window)
+    N = p.nfft or 2 * p.L
+    if out is None:
+        out = torch.empty((N, N, N), dtype=torch.complex64, device=md.device)
+    ws = _workspace(workspace, md.device)
+    ws.get(workspace_size(_native.OP_TRISPECTRUM_FROM_MOMENTS, 0, 1, 0, p))
+    _native.check(_native.lib().hos_trispectrum_from_moments(md.data_ptr(), cd.data_ptr(), ctypes.byref(p),
+                                                             out.data_ptr(), ws.ptr(), ws.nbytes(), _stream(stream)),
+                  "hos_trispectrum_from_moments")
+    return out
+
+
+def trispectrum_sharded(x_local, L, halo_before, halo_after, n_total, nfft=0, precision="bf16", window="parzen",
+                        remove_mean=True, group=None, workspace=None):
+    """Trispectrum of one long series whose time slices are spread over the
+    ranks of ``group`` (one GPU each; slices from :func:`shard.time_slices`
+    with ``halo_after=2 * L``).  Three FP64 sum all-reduces: the series'
+    total, the (2L)^3 fourth moment and the 4L - 1 c2.  Every rank returns
+    the full T."""
+    import torch.distributed as dist
+    distributed = dist.is_available() and dist.is_initialized()
+    xd, _ = _prepare(x_local)
+    own = xd[int(halo_before):xd.numel() - int(halo_after)]
+    tot = series_sum(own, workspace=workspace)
+    if distributed:
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM, group=group)
+    m4, c2 = moments4_slice(xd, L, halo_before, halo_after, tot, n_total, precision, remove_mean,
+                            workspace=workspace)
+    if distributed:
+        dist.all_reduce(m4, op=dist.ReduceOp.SUM, group=group)
+        dist.all_reduce(c2, op=dist.ReduceOp.SUM, group=group)
+    return trispectrum_from_moments(m4, c2, L, nfft, window, workspace=workspace)
 
 
 def bispectrum_direct(x, M, M3, remove_mean=True, overlap=0, out=None, workspace=None, stream=None):

@@ -17,7 +17,8 @@ STATUS_NAMES = {0: "HOS_OK", 1: "HOS_ERR_INVALID_ARG", 2: "HOS_ERR_UNSUPPORTED",
                 4: "HOS_ERR_CUDA", 5: "HOS_ERR_TIMEOUT", 6: "HOS_ERR_DEVICE_FAULT"}
 F32, F64 = 0, 1
 (OP_BISPECTRUM, OP_TRISPECTRUM, OP_BISPECTRUM_BATCHED, OP_BISPECTRUM_BACKWARD, OP_CUMULANT3, OP_CUMULANT4,
- OP_SERIES_SUM, OP_CUMULANT3_SLICE, OP_BISPECTRUM_FROM_C3, OP_TRISPECTRUM_BATCHED, OP_TRISPECTRUM_BACKWARD) = range(11)
+ OP_SERIES_SUM, OP_CUMULANT3_SLICE, OP_BISPECTRUM_FROM_C3, OP_TRISPECTRUM_BATCHED, OP_TRISPECTRUM_BACKWARD,
+ OP_MOMENTS4_SLICE, OP_TRISPECTRUM_FROM_MOMENTS) = range(13)
 
 
 class HosParams(ctypes.Structure):
@@ -46,6 +47,9 @@ _SIGS = {
                                _VP, ctypes.c_size_t, _VP],
     "hos_bispectrum_backward": [_VP, ctypes.c_int32, ctypes.c_int64, _P, _VP, _VP, _VP, ctypes.c_size_t, _VP],
     "hos_trispectrum_backward": [_VP, ctypes.c_int32, ctypes.c_int64, _P, _VP, _VP, _VP, ctypes.c_size_t, _VP],
+    "hos_moments4_slice": [_VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_int64, _P,
+                           _VP, _VP, _VP, ctypes.c_size_t, _VP],
+    "hos_trispectrum_from_moments": [_VP, _VP, _P, _VP, _VP, ctypes.c_size_t, _VP],
     "hos_bispectrum_noalloc": [_VP, ctypes.c_int32, ctypes.c_int64, _P, _VP, _VP],
     "hos_cumulant3": [_VP, ctypes.c_int32, ctypes.c_int64, _P, _VP, _VP, ctypes.c_size_t, _VP],
     "hos_cumulant4": [_VP, ctypes.c_int32, ctypes.c_int64, _P, _VP, _VP, ctypes.c_size_t, _VP],

@@ -100,10 +100,13 @@ static hos_status check_params(const hos_params* p, int op) {
         if (!parts_op || p->segment_len <= 0 || p->segment_overlap >= p->segment_len) return HOS_ERR_INVALID_ARG;
     }
     if (op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT4 || op == HOS_OP_TRISPECTRUM_BATCHED ||
-        op == HOS_OP_TRISPECTRUM_BACKWARD) {
+        op == HOS_OP_TRISPECTRUM_BACKWARD || op == HOS_OP_MOMENTS4_SLICE || op == HOS_OP_TRISPECTRUM_FROM_MOMENTS) {
         if (p->L > 64) return HOS_ERR_UNSUPPORTED;
         if (p->window == HOS_WIN_PARZEN_SYM) return HOS_ERR_UNSUPPORTED;
     }
+    // time slices of the fourth order: tensor-core contraction, one part
+    if (op == HOS_OP_MOMENTS4_SLICE && (p->precision == HOS_PREC_SIMT_FP32 || p->segment_len != 0))
+        return p->segment_len != 0 ? HOS_ERR_INVALID_ARG : HOS_ERR_UNSUPPORTED;
     if ((op == HOS_OP_BISPECTRUM_BACKWARD || op == HOS_OP_TRISPECTRUM_BACKWARD) && p->segment_len != 0)
         return HOS_ERR_UNSUPPORTED;
     // the trispectrum adjoint runs on the split-bf16 tensor-core contraction only
@@ -348,6 +351,22 @@ static FromC3Layout from_c3_layout(const hos_params* p) {
     return l;
 }
 
+// hos_trispectrum_from_moments's workspace: grid, twiddles
+struct FromM4Layout {
+    int Nf;
+    size_t grid, tw, total;
+};
+static FromM4Layout from_m4_layout(const hos_params* p) {
+    FromM4Layout l;
+    l.Nf = p->nfft ? p->nfft : 2 * p->L;
+    size_t o = 0;
+    l.grid = o; o = al256(o + 4 * (size_t)l.Nf * l.Nf * l.Nf);
+    l.tw = o; o = al256(o + 8 * (size_t)l.Nf);
+    l.total = o;
+    return l;
+}
+
+
 // Steps shared by the c3 operations: plan, mean, planes, contraction, reduce.
 static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int64_t* d_offsets, const Plan& P,
                          const hos_params* p, void* ws, size_t ws_bytes, cudaStream_t st, Tracer& tr, int red_mode,
@@ -560,9 +579,13 @@ static hos_status make_plan4(int op, const hos_params* p, int64_t n, Plan4& P, i
     return HOS_OK;
 }
 
+// sl: a time slice of a longer series (the mean from the whole series' sum,
+// halo samples around the slice serve as lags only, 1/n of the whole series;
+// mode 2 writes the raw m4 cube and c2_out receives c2).
 static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, const hos_params* p, void* ws,
                          size_t ws_bytes, cudaStream_t st, Tracer& tr, int mode, double* c4out,
-                         const int64_t* d_offsets = nullptr) {
+                         const int64_t* d_offsets = nullptr, const SliceArgs* sl = nullptr,
+                         double* c2_out = nullptr) {
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < P.total) return HOS_ERR_WORKSPACE;
     int64_t* off = at<int64_t>(ws, P.off);
     int64_t* pad = at<int64_t>(ws, P.pad);
@@ -576,15 +599,18 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
     const int kc = P.tc ? P.g4.kc : KC;
     HOS_CUDA_TRY(launch_plan_series(P.batched ? 1 : 0, n, P.seg, d_offsets, P.S, p->L, ntiles, flush, kc, P.pad_tail,
                                     off, pad, unit, win, st));
-    HOS_CUDA_TRY(launch_mean(x, dtype, off, P.S, P.nslices, at<double>(ws, P.mpart), p->remove_mean, mean, st));
+    if (sl) HOS_CUDA_TRY(launch_slice_mean(sl->d_sum, sl->n_total, p->remove_mean, mean, st));
+    else HOS_CUDA_TRY(launch_mean(x, dtype, off, P.S, P.nslices, at<double>(ws, P.mpart), p->remove_mean, mean, st));
     const int64_t maxpad = (int64_t)p->L + P.max_len + KC + P.pad_tail + 64;
     int bx = (int)ceil_div(maxpad, 256 * 4);
     if (bx < 1) bx = 1;
     if (bx > 65535) bx = 65535;
     void* hi = P.tc ? at<void>(ws, P.hi) : nullptr;
     void* lo = P.tc ? at<void>(ws, P.lo) : nullptr;
-    HOS_CUDA_TRY(launch_planes(x, dtype, off, pad, mean, p->L, P.tc ? plane_split(p->precision) : 0, y32, hi, lo,
-                               P.S, bx, st));
+    // a slice's input pointer is its first own sample; its halos lie before and after
+    const void* xs = sl ? static_cast<const uint8_t*>(x) + sl->halo_before * (dtype == HOS_F64 ? 8 : 4) : x;
+    HOS_CUDA_TRY(launch_planes(xs, dtype, off, pad, mean, p->L, P.tc ? plane_split(p->precision) : 0, y32, hi, lo,
+                               P.S, bx, st, sl ? sl->halo_before : 0, sl ? sl->halo_after : 0));
     tr.mark("contract");
     C4ReduceArgs r;
     r.window = p->window;
@@ -603,7 +629,8 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
         return HOS_OK;
     }
     double* c2 = at<double>(ws, P.c2);
-    HOS_CUDA_TRY(launch_c2(y32, off, pad, P.S, p->L, P.c2s, c2, at<float2>(ws, P.c2p), st));
+    HOS_CUDA_TRY(launch_c2(y32, off, pad, P.S, p->L, P.c2s, c2, at<float2>(ws, P.c2p), st, sl ? 1 : 0,
+                           sl ? sl->n_total : 0));
     SeriesView sv{off, pad, unit, win, mean, P.S};
     C3TcParams cp{P.g4, sv, y32, hi, lo, at<float>(ws, P.partials), at<int>(ws, P.status), wait_limit_ns()};
     const bool tf32 = (p->precision == HOS_PREC_FP32);
@@ -612,8 +639,12 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
     tr.mark("reduce");
     double* m4buf = at<double>(ws, P.m4buf);
     HOS_CUDA_TRY(launch_m4_tile_reduce(P.g4, sv, P.max_len, at<float>(ws, P.partials), at<int64_t>(ws, P.bnd),
-                                       at<TileRec>(ws, P.xr), at<float2>(ws, P.ilen), m4buf, st));
+                                       at<TileRec>(ws, P.xr), at<float2>(ws, P.ilen), m4buf, st,
+                                       sl ? sl->n_total : 0));
     HOS_CUDA_TRY(launch_c4_assemble(m4buf, c2, off, P.S, p->L, P.g4.ntiles, P.g4.tile_n, r, P.batched ? 1 : 0, st));
+    if (c2_out)
+        HOS_CUDA_TRY(cudaMemcpyAsync(c2_out, c2, sizeof(double) * (size_t)(4 * p->L - 1), cudaMemcpyDeviceToDevice,
+                                     st));
     return HOS_OK;
 }
 
@@ -787,7 +818,13 @@ const char* hos_last_contraction(void) { return g_last_contraction; }
 hos_status hos_workspace_size(int32_t op, int64_t n_total, int32_t n_series, int64_t max_len, const hos_params* p,
                               size_t* bytes) {
     if (!bytes || n_total < 0 || n_series < 1 || max_len < 0) return HOS_ERR_INVALID_ARG;
-    if (op < 0 || op > HOS_OP_TRISPECTRUM_BACKWARD) return HOS_ERR_INVALID_ARG;
+    if (op < 0 || op > HOS_OP_TRISPECTRUM_FROM_MOMENTS) return HOS_ERR_INVALID_ARG;
+    if (op == HOS_OP_TRISPECTRUM_FROM_MOMENTS) {
+        hos_status sf = check_params(p, op);
+        if (sf != HOS_OK) return sf;
+        *bytes = from_m4_layout(p).total;
+        return HOS_OK;
+    }
     if (p && p->segment_overlap != 0) {
         hos_status so = check_params(p, op);
         if (so != HOS_OK) return so;
@@ -807,7 +844,8 @@ hos_status hos_workspace_size(int32_t op, int64_t n_total, int32_t n_series, int
         *bytes = P4.total;
         return HOS_OK;
     }
-    if (op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT4 || op == HOS_OP_TRISPECTRUM_BATCHED) {
+    if (op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT4 || op == HOS_OP_TRISPECTRUM_BATCHED ||
+        op == HOS_OP_MOMENTS4_SLICE) {
         Plan4 P4;
         hos_status s4 = make_plan4(op, p, n_total, P4, n_series, max_len);
         if (s4 != HOS_OK) return s4;
@@ -882,6 +920,50 @@ hos_status hos_bispectrum_from_cumulant(const double* d_c3, const hos_params* p,
     HOS_CUDA_TRY(launch_window_c3(d_c3, p->L, p->window, l.Nf, kBispecScale, at<float>(ws, l.wtab), grid, st));
     tr.mark("transform");
     s = run_dft2(grid, reinterpret_cast<float2*>(d_B), 1, l.Nf, at<float2>(ws, l.tw), st);
+    tr.mark("");
+    return s;
+}
+
+hos_status hos_moments4_slice(const void* d_x, int32_t dtype, int64_t n_slice, int64_t halo_before, int64_t halo_after,
+                              const double* d_sum, int64_t n_total, const hos_params* p, double* d_m4, double* d_c2,
+                              void* ws, size_t ws_bytes, hos_stream_t stream) {
+    if (!d_x || !d_m4 || !d_c2 || !d_sum || !p || n_slice < 1 || (dtype != HOS_F32 && dtype != HOS_F64))
+        return HOS_ERR_INVALID_ARG;
+    if (halo_before < 0 || halo_after < 0 || halo_before > p->L || halo_after > 2 * p->L) return HOS_ERR_INVALID_ARG;
+    if (n_total < n_slice + halo_before + halo_after) return HOS_ERR_INVALID_ARG;
+    Plan4 P;
+    hos_status s = make_plan4(HOS_OP_MOMENTS4_SLICE, p, n_slice, P);
+    if (s != HOS_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Tracer tr(st);
+    const SliceArgs sl{halo_before, halo_after, d_sum, n_total};
+    s = run_c4(d_x, dtype, n_slice, P, p, ws, ws_bytes, st, tr, 2, d_m4, nullptr, &sl, d_c2);
+    tr.mark("");
+    return s;
+}
+
+hos_status hos_trispectrum_from_moments(const double* d_m4, const double* d_c2, const hos_params* p, void* d_T,
+                                        void* ws, size_t ws_bytes, hos_stream_t stream) {
+    if (!d_m4 || !d_c2 || !d_T) return HOS_ERR_INVALID_ARG;
+    hos_status s = check_params(p, HOS_OP_TRISPECTRUM_FROM_MOMENTS);
+    if (s != HOS_OK) return s;
+    const FromM4Layout l = from_m4_layout(p);
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < l.total) return HOS_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Tracer tr(st);
+    tr.mark("reduce");
+    float* grid = at<float>(ws, l.grid);
+    if (l.Nf > 2 * p->L) HOS_CUDA_TRY(launch_zero_f32(grid, (int64_t)l.Nf * l.Nf * l.Nf, st));
+    C4ReduceArgs r;
+    r.window = p->window;
+    r.nfft = l.Nf;
+    r.mode = 0;
+    r.scale = 1.0 / (8.0 * 3.14159265358979323846 * 3.14159265358979323846 * 3.14159265358979323846);
+    r.grid = grid;
+    r.c4out = nullptr;
+    HOS_CUDA_TRY(launch_c4_from_moments(d_m4, d_c2, p->L, r, st));
+    tr.mark("transform");
+    s = run_dft3(grid, reinterpret_cast<float2*>(d_T), l.Nf, at<float2>(ws, l.tw), st);
     tr.mark("");
     return s;
 }

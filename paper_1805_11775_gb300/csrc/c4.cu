@@ -28,6 +28,11 @@ HOS_HD int pair_index(int w1, int w2, int L) {
 // the chains in a fixed tree.  P = 1 writes FP64 c2 directly; otherwise each
 // slice writes its double-float sum and c2_finish_kernel adds the P slices
 // in order.
+// Time slice of a longer series (tslice = 1): the sum runs over the slice's
+// own samples i in [0, len) and reads y(i + |t|) past the end from the halo
+// the planes hold; lag -t gets the same value as t (the whole series'
+// c2(t) = c2(-t), which is all the joined sum needs).  norm_len > 0 replaces
+// the part's length as the divisor (the whole series' length).
 constexpr int C2_THREADS = 512;
 HOS_DEV float2 df2_add(float2 a, float2 b) {  // (a.h + a.l) + (b.h + b.l), renormalised
     const float sm = a.x + b.x;
@@ -39,16 +44,19 @@ HOS_DEV float2 df2_add(float2 a, float2 b) {  // (a.h + a.l) + (b.h + b.l), reno
 }
 
 __global__ void __launch_bounds__(C2_THREADS) c2_kernel(const float* __restrict__ y32, const int64_t* __restrict__ off,
-                                                        const int64_t* __restrict__ pad, int L, int P,
-                                                        double* __restrict__ c2, float2* __restrict__ c2p) {
+                                                        const int64_t* __restrict__ pad, int L, int P, int tslice,
+                                                        int64_t norm_len, double* __restrict__ c2,
+                                                        float2* __restrict__ c2p) {
     __shared__ float2 sh[C2_THREADS];
     const int T = 2 * L - 1;
-    const int t = (int)blockIdx.x - T;
+    const int bt = (int)blockIdx.x - T;
+    const int t = (tslice && bt < 0) ? -bt : bt;
     const int s = blockIdx.y, z = blockIdx.z;
     const int64_t len = off[s + 1] - off[s];
+    const double nl = (double)(norm_len > 0 ? norm_len : len);
     const float* y = y32 + pad[s] + L;  // y[i], zero-padded on both sides by >= L
     float hi = 0.0f, lo = 0.0f;
-    const int64_t a0 = t < 0 ? -t : 0, a1 = t > 0 ? len - t : len;
+    const int64_t a0 = t < 0 ? -t : 0, a1 = (t > 0 && !tslice) ? len - t : len;
     const int64_t span = a1 > a0 ? a1 - a0 : 0, per = (span + P - 1) / P;
     const int64_t i0 = a0 + per * z, i1 = (i0 + per < a1) ? i0 + per : a1;
 #pragma unroll 4
@@ -69,12 +77,12 @@ __global__ void __launch_bounds__(C2_THREADS) c2_kernel(const float* __restrict_
     }
     if (threadIdx.x != 0) return;
     const int64_t e = (int64_t)s * (2 * T + 1) + blockIdx.x;
-    if (P == 1) c2[e] = len > 0 ? ((double)sh[0].x + (double)sh[0].y) / (double)len : 0.0;
+    if (P == 1) c2[e] = len > 0 ? ((double)sh[0].x + (double)sh[0].y) / nl : 0.0;
     else c2p[e * P + z] = sh[0];
 }
 
 __global__ void c2_finish_kernel(const float2* __restrict__ c2p, const int64_t* __restrict__ off, int S, int L, int P,
-                                 double* __restrict__ c2) {
+                                 int64_t norm_len, double* __restrict__ c2) {
     const int T = 2 * L - 1;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)S * (2 * T + 1)) return;
@@ -82,7 +90,7 @@ __global__ void c2_finish_kernel(const float2* __restrict__ c2p, const int64_t* 
     const int64_t len = off[s + 1] - off[s];
     float2 a = c2p[e * P];
     for (int z = 1; z < P; ++z) a = df2_add(a, c2p[e * P + z]);
-    c2[e] = len > 0 ? ((double)a.x + (double)a.y) / (double)len : 0.0;
+    c2[e] = len > 0 ? ((double)a.x + (double)a.y) / (double)(norm_len > 0 ? norm_len : len) : 0.0;
 }
 
 constexpr int M4_PAIRS = 128;  // pairs per CTA
@@ -262,11 +270,11 @@ __global__ void c4_assemble_kernel(const double* __restrict__ m4buf, const doubl
         if (off[s + 1] <= off[s]) continue;
         const double m4 = m4buf[((int64_t)s * ntiles + t) * tsz + elem];
         const double* c = c2 + (int64_t)s * (2 * T + 1) + T;
-        c4 += m4 - c[w1] * c[w3 - w2] - c[w2] * c[w3 - w1] - c[w3] * c[w2 - w1];
+        c4 += (r.mode == 2) ? m4 : m4 - c[w1] * c[w3 - w2] - c[w2] * c[w3 - w1] - c[w3] * c[w2 - w1];
         ++k;
     }
     if (k > 0) c4 /= (double)k;
-    if (r.mode == 1) {
+    if (r.mode >= 1) {  // 1: raw c4, 2: raw m4 (time slices), both FP64 over the cube
         r.c4out[(int64_t)(per_series ? blockIdx.y : 0) * twoL * twoL * twoL +
                 ((int64_t)(w1 + L) * twoL + (w2 + L)) * twoL + (w3 + L)] = c4;
         return;
@@ -285,15 +293,47 @@ int c2_slices(int S, int64_t max_len) {
 }
 
 cudaError_t launch_c2(const float* y32, const int64_t* off, const int64_t* pad, int S, int L, int P, double* c2,
-                      float2* c2p, cudaStream_t st) {
+                      float2* c2p, cudaStream_t st, int tslice, int64_t norm_len) {
     const int T = 2 * L - 1;
-    c2_kernel<<<dim3((unsigned)(2 * T + 1), (unsigned)S, (unsigned)P), C2_THREADS, 0, st>>>(y32, off, pad, L, P, c2,
-                                                                                             c2p);
+    c2_kernel<<<dim3((unsigned)(2 * T + 1), (unsigned)S, (unsigned)P), C2_THREADS, 0, st>>>(y32, off, pad, L, P, tslice,
+                                                                                             norm_len, c2, c2p);
     count_launch();
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess || P == 1) return err;
     const int64_t tot = (int64_t)S * (2 * T + 1);
-    c2_finish_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(c2p, off, S, L, P, c2);
+    c2_finish_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(c2p, off, S, L, P, norm_len, c2);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// The trispectrum's lag-domain input from a joined fourth moment and c2 (the
+// sums of a series' time slices): c4 = m4 - c2(w1) c2(w3-w2) - c2(w2) c2(w3-w1)
+// - c2(w3) c2(w2-w1) in FP64, then window and scale onto the N^3 grid as
+// c4_assemble_kernel's mode 0 does.  m4: (2L)^3 [w1+L][w2+L][w3+L]; c2: 4L-1
+// values, index t + 2L - 1.
+__global__ void c4_from_moments_kernel(const double* __restrict__ m4, const double* __restrict__ c2, int L,
+                                       C4ReduceArgs r) {
+    const int twoL = 2 * L, T = 2 * L - 1;
+    __shared__ float wsh[2 * 64];
+    for (int i = threadIdx.x; i < twoL; i += blockDim.x)
+        wsh[i] = (r.window == HOS_WIN_RECT) ? (i == 0 ? 0.0f : 1.0f) : (float)parzen(i - L, L);
+    __syncthreads();
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)twoL * twoL * twoL) return;
+    const int w3 = (int)(e % twoL) - L;
+    const int w2 = (int)((e / twoL) % twoL) - L;
+    const int w1 = (int)(e / ((int64_t)twoL * twoL)) - L;
+    const double* c = c2 + T;
+    const double c4 = m4[e] - c[w1] * c[w3 - w2] - c[w2] * c[w3 - w1] - c[w3] * c[w2 - w1];
+    const float wv = wsh[w1 + L] * wsh[w2 + L] * wsh[w3 + L];
+    const int N = r.nfft;  // >= 2L
+    const int k1 = w1 < 0 ? w1 + N : w1, k2 = w2 < 0 ? w2 + N : w2, k3 = w3 < 0 ? w3 + N : w3;
+    r.grid[((int64_t)k1 * N + k2) * N + k3] = (float)c4 * ((float)r.scale * wv);
+}
+
+cudaError_t launch_c4_from_moments(const double* m4, const double* c2, int L, const C4ReduceArgs& r, cudaStream_t st) {
+    const int64_t n3 = 8LL * L * L * L;
+    c4_from_moments_kernel<<<(unsigned)ceil_div(n3, 256), 256, 0, st>>>(m4, c2, L, r);
     count_launch();
     return cudaGetLastError();
 }
@@ -311,7 +351,7 @@ cudaError_t launch_c4(const float* y32, const int64_t* off, const int64_t* pad, 
                       int CG, int64_t total_groups, double* c2, float* partials, const C4ReduceArgs& r,
                       cudaStream_t st) {
     const int T = 2 * L - 1;
-    c2_kernel<<<dim3((unsigned)(2 * T + 1), (unsigned)S), C2_THREADS, 0, st>>>(y32, off, pad, L, 1, c2, nullptr);
+    c2_kernel<<<dim3((unsigned)(2 * T + 1), (unsigned)S), C2_THREADS, 0, st>>>(y32, off, pad, L, 1, 0, 0, c2, nullptr);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -67,7 +67,7 @@ struct LineGeom {
 struct C4ReduceArgs {
     int window;
     int nfft;
-    int mode;  // 0: windowed transform grid (fp32), 1: raw c4 (fp64)
+    int mode;  // 0: windowed transform grid (fp32), 1: raw c4 (fp64), 2: raw m4 (fp64, time slices)
     double scale;
     float* grid;
     double* c4out;
@@ -133,11 +133,13 @@ cudaError_t launch_adjoint4_tc(const float* y32, const uint16_t* hi, const uint1
                                const float* Gs4, uint8_t* gsb, float* t1p, float* t2p, const double* gc2, float* g,
                                int* status, uint64_t limit_ns, int G, cudaStream_t st);
 cudaError_t launch_m4_tile_reduce(const C3Geom& geo, const SeriesView& sv, int64_t max_len, const float* partials,
-                                  int64_t* bnd, TileRec* rec, float2* inv_len, double* m4buf, cudaStream_t st);
+                                  int64_t* bnd, TileRec* rec, float2* inv_len, double* m4buf, cudaStream_t st,
+                                  int64_t norm_len = 0);
 // P slices of each part's samples (c2_slices); c2p: S * (4L - 1) * P float2 when P > 1
 int c2_slices(int S, int64_t max_len);
 cudaError_t launch_c2(const float* y32, const int64_t* off, const int64_t* pad, int S, int L, int P, double* c2,
-                      float2* c2p, cudaStream_t st);
+                      float2* c2p, cudaStream_t st, int tslice = 0, int64_t norm_len = 0);
+cudaError_t launch_c4_from_moments(const double* m4, const double* c2, int L, const C4ReduceArgs& r, cudaStream_t st);
 cudaError_t launch_c4_assemble(const double* m4buf, const double* c2, const int64_t* off, int S, int L, int ntiles,
                                int tile_n, const C4ReduceArgs& r, int per_series, cudaStream_t st);
 cudaError_t launch_timeout_selftest(int* status, uint64_t limit_ns, cudaStream_t st);

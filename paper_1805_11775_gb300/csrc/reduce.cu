@@ -421,8 +421,9 @@ static cudaError_t launch_part_index(const C3Geom& geo, const SeriesView& sv, in
 }
 
 cudaError_t launch_m4_tile_reduce(const C3Geom& geo, const SeriesView& sv, int64_t max_len, const float* partials,
-                                  int64_t* bnd, TileRec* rec, float2* inv_len, double* m4buf, cudaStream_t st) {
-    cudaError_t e = launch_part_index(geo, sv, bnd, rec, inv_len, 0, st);
+                                  int64_t* bnd, TileRec* rec, float2* inv_len, double* m4buf, cudaStream_t st,
+                                  int64_t norm_len) {
+    cudaError_t e = launch_part_index(geo, sv, bnd, rec, inv_len, norm_len, st);
     if (e != cudaSuccess) return e;
     const int64_t nvec = (int64_t)TILE_M * geo.tile_n / 4;
     const int gsplit = window_split(geo, max_len);

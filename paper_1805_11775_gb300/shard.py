@@ -3,9 +3,10 @@
 The estimator shards naturally.  Independent series go to different ranks
 with no data-path collective (weak scaling): ``series_shard`` gives each
 rank a contiguous run of series whose total length is as even as the series
-boundaries allow.  One long series is cut in time (``time_slices``): c3 is a
-sum over time, so each rank sums its slice (with an L-sample halo on each
-side) and two FP64 all-reduces (the series' sum for the mean, then c3) join
+boundaries allow.  One long series is cut in time (``time_slices``): c3, m4
+and c2 are sums over time, so each rank sums its slice (with an L-sample
+halo before it and L, or 2L for the fourth order, after) and FP64
+all-reduces (the series' sum for the mean, then c3, or m4 and c2) join
 them.  ``max_over_ranks`` is the timing reduction the benchmark reports.
 """
 from __future__ import annotations
@@ -32,21 +33,24 @@ def series_shard(offsets, rank: int, world: int):
     return cuts[rank], cuts[rank + 1]
 
 
-def time_slices(n: int, world: int, L: int):
+def time_slices(n: int, world: int, L: int, halo_after: int | None = None):
     """Cut one series of n samples into ``world`` contiguous time slices for
     the cumulant's sum over time: [(a, b, halo_before, halo_after)] per
     rank, slices [a, b) covering [0, n) in order, halos of up to L samples
-    (fewer at the series' ends) that the lags w in [-L, L-1] reach."""
+    (fewer at the series' ends) that the lags w in [-L, L-1] reach.  The
+    fourth order's c2 lags reach 2L - 1 after a sample: pass
+    ``halo_after=2 * L``."""
+    after = L if halo_after is None else halo_after
     out = []
     for r in range(world):
         a, b = (n * r) // world, (n * (r + 1)) // world
-        out.append((a, b, min(L, a), min(L, n - b)))
+        out.append((a, b, min(L, a), min(after, n - b)))
     return out
 
 
-def slice_with_halo(x, rank: int, world: int, L: int):
+def slice_with_halo(x, rank: int, world: int, L: int, halo_after: int | None = None):
     """(x[a - halo_before : b + halo_after], halo_before, halo_after) of ``rank``."""
-    a, b, hb, ha = time_slices(len(x), world, L)[rank]
+    a, b, hb, ha = time_slices(len(x), world, L, halo_after)[rank]
     return x[a - hb:b + ha], hb, ha
 
 

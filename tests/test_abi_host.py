@@ -147,3 +147,28 @@ def test_overlap_workspace_and_checks(lib):
     for op in (_native.OP_BISPECTRUM_BATCHED, _native.OP_TRISPECTRUM_BACKWARD, _native.OP_SERIES_SUM):
         with pytest.raises(HosError):
             workspace_size(op, n, 1, n, _params(L=8, segment_len=100, segment_overlap=5, precision=1))
+
+
+def test_fourth_order_slice_checks(lib):
+    """Time slices of the fourth order: workspace sizes, and halos, precision
+    and segment checks on the host."""
+    from paper_1805_11775_gb300 import workspace_size, _native, HosError
+    a = workspace_size(_native.OP_MOMENTS4_SLICE, 50_000, 1, 50_000, _params(L=32, precision=1))
+    assert a > 0
+    f = workspace_size(_native.OP_TRISPECTRUM_FROM_MOMENTS, 0, 1, 0, _params(L=32, precision=1))
+    assert f >= 64 ** 3 * 4
+    with pytest.raises(HosError):
+        workspace_size(_native.OP_MOMENTS4_SLICE, 50_000, 1, 50_000, _params(L=32, precision=2))
+    with pytest.raises(HosError):
+        workspace_size(_native.OP_MOMENTS4_SLICE, 50_000, 1, 50_000, _params(L=65, precision=1))
+    dummy = ctypes.c_void_p(16)
+    ws = ctypes.c_void_p(256)
+    p = _params(L=8, precision=1)
+    # halo_after 2L + 1 and halo_before L + 1 are refused; so is n_total too short
+    assert lib.hos_moments4_slice(dummy, 0, 1000, 0, 17, dummy, 5000, ctypes.byref(p), dummy, dummy, ws, 1 << 30,
+                                  None) == 1
+    assert lib.hos_moments4_slice(dummy, 0, 1000, 9, 0, dummy, 5000, ctypes.byref(p), dummy, dummy, ws, 1 << 30,
+                                  None) == 1
+    assert lib.hos_moments4_slice(dummy, 0, 1000, 8, 16, dummy, 1000, ctypes.byref(p), dummy, dummy, ws, 1 << 30,
+                                  None) == 1
+    assert lib.hos_trispectrum_from_moments(None, dummy, ctypes.byref(p), dummy, ws, 1 << 30, None) == 1

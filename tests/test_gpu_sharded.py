@@ -105,3 +105,66 @@ def test_slice_argument_errors(hos):
         hos.cumulant3_slice(x, 8, 9, 0, tot, 1000)  # halo longer than L
     with pytest.raises(HosError):
         hos.cumulant3_slice(x, 8, 4, 4, tot, 50)  # n_total shorter than the window
+
+
+# ------------------------------------------------------------------ fourth order
+TOL4 = {"bf16": 2e-4, "fp32": 2e-5}
+
+
+def emulate_ranks4(hos, x, L, world, prec, remove_mean=True):
+    """(m4, c2) of the whole series from `world` slices (halo L before, 2L
+    after), computed one after another; host FP64 sums."""
+    from paper_1805_11775_gb300.shard import slice_with_halo
+    xd = torch.from_numpy(x).cuda()
+    pieces = [slice_with_halo(xd, r, world, L, halo_after=2 * L) for r in range(world)]
+    total = sum(float(hos.series_sum(p[h0:p.numel() - h1]).item()) for p, h0, h1 in pieces)
+    tot = torch.tensor([total], dtype=torch.float64, device="cuda")
+    m4 = np.zeros((2 * L,) * 3)
+    c2 = np.zeros(4 * L - 1)
+    for p, h0, h1 in pieces:
+        a, b = hos.moments4_slice(p, L, h0, h1, tot, x.size, precision=prec, remove_mean=remove_mean)
+        m4 += a.cpu().numpy()
+        c2 += b.cpu().numpy()
+    return m4, c2
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("n,L,world", [(6000, 8, 2), (9001, 16, 3), (4000, 32, 5), (300, 4, 7)])
+def test_fourth_order_slices_match_the_oracle(hos, oracle, prec, n, L, world):
+    """Joined slices: c4 (from the joined m4 and c2) against the oracle's c4,
+    and the trispectrum from the joined moments against the oracle's."""
+    x = hos_synth.ma(n, 17 * n + world)
+    m4, c2 = emulate_ranks4(hos, x, L, world, prec)
+    T = hos.trispectrum_from_moments(torch.from_numpy(m4).cuda(), torch.from_numpy(c2).cuda(), L).cpu().numpy()
+    ref = oracle.trispectrum(x, L, 2 * L)
+    assert normwise(T, ref) <= TOL4[prec]
+    c2f = lambda t: c2[t + 2 * L - 1]  # noqa: E731
+    r4 = oracle.c4(oracle.demean(x), L)[:2 * L, :2 * L, :2 * L]
+    c4 = np.empty_like(m4)
+    for w1 in range(-L, L):
+        for w2 in range(-L, L):
+            w3 = np.arange(-L, L)
+            c4[w1 + L, w2 + L] = (m4[w1 + L, w2 + L] - c2f(w1) * c2[w3 - w2 + 2 * L - 1]
+                                  - c2f(w2) * c2[w3 - w1 + 2 * L - 1] - c2[w3 + 2 * L - 1] * c2f(w2 - w1))
+    assert np.abs(c4 - r4).max() <= TOL4[prec] * np.abs(r4).max()
+
+
+def test_fourth_order_sharded_single_rank_is_the_trispectrum(hos):
+    """One rank (no process group): trispectrum_sharded equals hos_trispectrum
+    to FP32 rounding (the same contraction, the c2 sums split otherwise)."""
+    x = hos_synth.ma(20000, 23)
+    xd = torch.from_numpy(x).cuda()
+    a = hos.trispectrum_sharded(xd, 16, 0, 0, x.size, precision="fp32").cpu().numpy()
+    b = hos.trispectrum(xd, 16, precision="fp32").cpu().numpy()
+    assert normwise(a, b) <= 1e-6
+
+
+def test_fourth_order_slice_argument_errors(hos):
+    x = torch.from_numpy(hos_synth.ma(3000, 29)).cuda()
+    tot = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(hos.HosError):
+        hos.moments4_slice(x, 8, 0, 17, tot, 10000)  # halo after 2L + 1
+    with pytest.raises(hos.HosError):
+        hos.moments4_slice(x, 8, 9, 0, tot, 10000)  # halo before L + 1
+    with pytest.raises(hos.HosError):
+        hos.moments4_slice(x, 8, 0, 0, tot, 10000, precision="simt")

@@ -129,3 +129,77 @@ def test_time_sliced_ranks_sum_to_the_whole_series_c3(tmp_path, oracle, world):
     for r in range(world):
         got = np.load(tmp_path / f"c3_{r}.npy")
         assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def _slice_moments(xh, hb, ha, mean, L, n_total):
+    """(1/n) sums over the slice's own i of y(i)y(i+w1)y(i+w2)y(i+w3) over
+    [-L, L-1]^3 and of y(i)y(i+t), t in [0, 2L-1], y = x - mean on the window
+    xh (zero outside it)."""
+    y = xh - mean
+    m = y.size
+    idx = np.arange(hb, m - ha)
+
+    def lagged(w):
+        j = idx + w
+        return np.where((j >= 0) & (j < m), y[np.clip(j, 0, m - 1)], 0.0)
+
+    ys = {w: lagged(w) for w in range(-L, 2 * L)}
+    m4 = np.zeros((2 * L,) * 3)
+    for w1 in range(-L, L):
+        for w2 in range(-L, L):
+            p = y[idx] * ys[w1] * ys[w2]
+            for w3 in range(-L, L):
+                m4[w1 + L, w2 + L, w3 + L] = np.sum(p * ys[w3]) / n_total
+    c2 = np.array([np.sum(y[idx] * ys[t]) / n_total for t in range(2 * L)])
+    return m4, c2
+
+
+def _slice4_rank_main(rank, world, port, out_dir):
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    x = hos_synth.ma(333, 32)
+    L = 3
+    xh, hb, ha = slice_with_halo(x, rank, world, L, halo_after=2 * L)
+    tot = torch.tensor([np.sum(xh[hb:xh.size - ha])], dtype=torch.float64)
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    m4, c2 = _slice_moments(xh, hb, ha, float(tot[0]) / x.size, L, x.size)
+    m4t, c2t = torch.from_numpy(m4), torch.from_numpy(c2)
+    dist.all_reduce(m4t, op=dist.ReduceOp.SUM)
+    dist.all_reduce(c2t, op=dist.ReduceOp.SUM)
+    np.save(os.path.join(out_dir, f"m4_{rank}.npy"), m4t.numpy())
+    np.save(os.path.join(out_dir, f"c2_{rank}.npy"), c2t.numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_time_sliced_ranks_give_the_whole_series_c4(tmp_path, oracle, world):
+    """Slices with an L-sample halo before and 2L after, joined by FP64 sum
+    all-reduces of the total, of m4 and of c2 (lags >= 0; c2 is even), give
+    the whole series' c4 = m4 - three c2 c2 products."""
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    mp.start_processes(_slice4_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    x = hos_synth.ma(333, 32)
+    L = 3
+    ref = oracle.c4(oracle.demean(x), L)[:2 * L, :2 * L, :2 * L]
+    for r in range(world):
+        m4 = np.load(tmp_path / f"m4_{r}.npy")
+        c2p = np.load(tmp_path / f"c2_{r}.npy")
+        c2 = lambda t: c2p[abs(t)]  # noqa: E731
+        c4 = np.empty_like(m4)
+        for w1 in range(-L, L):
+            for w2 in range(-L, L):
+                for w3 in range(-L, L):
+                    c4[w1 + L, w2 + L, w3 + L] = (m4[w1 + L, w2 + L, w3 + L] - c2(w1) * c2(w3 - w2)
+                                                  - c2(w2) * c2(w3 - w1) - c2(w3) * c2(w2 - w1))
+        assert np.abs(c4 - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_fourth_order_time_slices_reach_2L_after():
+    for n, world, L in [(1000, 3, 8), (97, 4, 30), (10, 8, 4)]:
+        for a, b, hb, ha in time_slices(n, world, L, halo_after=2 * L):
+            assert hb == min(L, a) and ha == min(2 * L, n - b)
