@@ -8,6 +8,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "launch.cuh"
 
 namespace hos {
@@ -16,6 +18,16 @@ static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 static const char* g_last_contraction = "none";
+
+// ---- host-side fault injection ----------------------------------------------------
+// HOS_FAULT (read at every entry): "workspace" makes each entry point report
+// HOS_ERR_WORKSPACE after its argument checks; "cuda" makes the first CUDA
+// call of each entry point report a failure without making it.  Nothing
+// reaches the GPU in either case.
+static bool fault_is(const char* what) {
+    const char* f = std::getenv("HOS_FAULT");
+    return f && std::strcmp(f, what) == 0;
+}
 
 // ---- tracing ------------------------------------------------------------------
 constexpr int MAX_STAGES = 8;
@@ -26,10 +38,13 @@ static bool g_ev_made = false;
 static int g_prof_n = 0;  // events recorded by the last call
 static const char* g_cur_names[MAX_STAGES];
 
+// Stage events (when profiling is on) and an NVTX range per stage (always;
+// no-ops unless a tool is attached).
 struct Tracer {
     cudaStream_t st;
     int n = 0;
     bool on;
+    bool range_open = false;
     explicit Tracer(cudaStream_t s) : st(s) {
         std::lock_guard<std::mutex> lk(g_prof_mu);
         on = g_prof_on;
@@ -39,7 +54,18 @@ struct Tracer {
         }
         if (on) g_prof_n = 0;
     }
+    ~Tracer() {
+        if (range_open) nvtxRangePop();
+    }
     void mark(const char* next_stage) {
+        if (range_open) {
+            nvtxRangePop();
+            range_open = false;
+        }
+        if (next_stage && *next_stage) {
+            nvtxRangePushA(next_stage);
+            range_open = true;
+        }
         if (!on || n > MAX_STAGES) return;
         cudaEventRecord(g_ev[n], st);
         if (n < MAX_STAGES) g_cur_names[n] = next_stage;
@@ -298,6 +324,7 @@ static T* at(void* ws, size_t off) {
 
 #define HOS_CUDA_TRY(expr)                         \
     do {                                           \
+        if (fault_is("cuda")) return HOS_ERR_CUDA;   \
         cudaError_t e__ = (expr);                  \
         if (e__ != cudaSuccess) return HOS_ERR_CUDA; \
     } while (0)
@@ -374,7 +401,9 @@ static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int6
     const C3Geom& g = P.g;
     const Layout& l = P.l;
     const int S = P.S;
-    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < l.total) return HOS_ERR_WORKSPACE;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < l.total ||
+        fault_is("workspace"))
+        return HOS_ERR_WORKSPACE;
     int* status = at<int>(ws, l.status);
     int64_t* off = at<int64_t>(ws, l.off);
     int64_t* pad = at<int64_t>(ws, l.pad);
@@ -586,7 +615,9 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
                          size_t ws_bytes, cudaStream_t st, Tracer& tr, int mode, double* c4out,
                          const int64_t* d_offsets = nullptr, const SliceArgs* sl = nullptr,
                          double* c2_out = nullptr) {
-    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < P.total) return HOS_ERR_WORKSPACE;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < P.total ||
+        fault_is("workspace"))
+        return HOS_ERR_WORKSPACE;
     int64_t* off = at<int64_t>(ws, P.off);
     int64_t* pad = at<int64_t>(ws, P.pad);
     int64_t* unit = at<int64_t>(ws, P.unit);
@@ -785,7 +816,9 @@ static hos_status with_overlap(int32_t op, const void* d_x, int32_t dtype, int64
     size_t inner = 0, total = 0;
     s = overlap_workspace(op, n, p, o, &inner, &total);
     if (s != HOS_OK) return s;
-    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < total) return HOS_ERR_WORKSPACE;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < total ||
+        fault_is("workspace"))
+        return HOS_ERR_WORKSPACE;
     void* xs = static_cast<uint8_t*>(ws) + inner;
     HOS_CUDA_TRY(launch_gather_parts(d_x, dtype, o.K, o.m, o.step, xs, reinterpret_cast<cudaStream_t>(stream)));
     return core(xs, dtype, o.n2, &p2, out, ws, inner, stream);
@@ -879,7 +912,9 @@ hos_status hos_workspace_size(int32_t op, int64_t n_total, int32_t n_series, int
 hos_status hos_series_sum(const void* d_x, int32_t dtype, int64_t n, double* d_sum, void* ws, size_t ws_bytes,
                           hos_stream_t stream) {
     if (!d_x || !d_sum || n < 1 || (dtype != HOS_F32 && dtype != HOS_F64)) return HOS_ERR_INVALID_ARG;
-    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < sum_ws_bytes(n)) return HOS_ERR_WORKSPACE;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < sum_ws_bytes(n) ||
+        fault_is("workspace"))
+        return HOS_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     HOS_CUDA_TRY(launch_series_sum(d_x, dtype, n, sum_slices(n), at<int64_t>(ws, 0), at<double>(ws, 256), d_sum,
                                    st));
@@ -911,7 +946,9 @@ hos_status hos_bispectrum_from_cumulant(const double* d_c3, const hos_params* p,
     hos_status s = check_params(p, HOS_OP_BISPECTRUM_FROM_C3);
     if (s != HOS_OK) return s;
     const FromC3Layout l = from_c3_layout(p);
-    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < l.total) return HOS_ERR_WORKSPACE;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < l.total ||
+        fault_is("workspace"))
+        return HOS_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     Tracer tr(st);
     tr.mark("reduce");
@@ -948,7 +985,9 @@ hos_status hos_trispectrum_from_moments(const double* d_m4, const double* d_c2, 
     hos_status s = check_params(p, HOS_OP_TRISPECTRUM_FROM_MOMENTS);
     if (s != HOS_OK) return s;
     const FromM4Layout l = from_m4_layout(p);
-    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < l.total) return HOS_ERR_WORKSPACE;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < l.total ||
+        fault_is("workspace"))
+        return HOS_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     Tracer tr(st);
     tr.mark("reduce");
@@ -1011,7 +1050,9 @@ hos_status hos_bispectrum_direct(const void* d_x, int32_t dtype, int64_t n, int3
     DirectLayout l;
     hos_status s = direct_layout(n, M, M3, overlap, l);
     if (s != HOS_OK) return s;
-    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < l.total) return HOS_ERR_WORKSPACE;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < l.total ||
+        fault_is("workspace"))
+        return HOS_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     Tracer tr(st);
     tr.mark("prep");
@@ -1037,7 +1078,7 @@ static hos_status bispectrum_core(const void* d_x, int32_t dtype, int64_t n, con
     Plan P;
     hos_status s = make_plan(HOS_OP_BISPECTRUM, p, n, 1, n, P);
     if (s != HOS_OK) return s;
-    if (!ws || ws_bytes < P.l.total) return HOS_ERR_WORKSPACE;
+    if (!ws || ws_bytes < P.l.total || fault_is("workspace")) return HOS_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     Tracer tr(st);
     s = run_c3(HOS_OP_BISPECTRUM, d_x, dtype, n, nullptr, P, p, ws, ws_bytes, st, tr, 0, at<float>(ws, P.l.grid),
@@ -1057,7 +1098,7 @@ hos_status hos_bispectrum_batched(const void* d_x, int32_t dtype, const int64_t*
     Plan P;
     hos_status s = make_plan(HOS_OP_BISPECTRUM_BATCHED, p, n_total, S, max_len, P);
     if (s != HOS_OK) return s;
-    if (!ws || ws_bytes < P.l.total) return HOS_ERR_WORKSPACE;
+    if (!ws || ws_bytes < P.l.total || fault_is("workspace")) return HOS_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     Tracer tr(st);
     s = run_c3(HOS_OP_BISPECTRUM_BATCHED, d_x, dtype, n_total, d_offsets, P, p, ws, ws_bytes, st, tr, 0,
@@ -1089,7 +1130,7 @@ static hos_status trispectrum_core(const void* d_x, int32_t dtype, int64_t n, co
     Plan4 P;
     hos_status s = make_plan4(HOS_OP_TRISPECTRUM, p, n, P);
     if (s != HOS_OK) return s;
-    if (!ws || ws_bytes < P.total) return HOS_ERR_WORKSPACE;
+    if (!ws || ws_bytes < P.total || fault_is("workspace")) return HOS_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     Tracer tr(st);
     s = run_c4(d_x, dtype, n, P, p, ws, ws_bytes, st, tr, 0, nullptr);
@@ -1108,7 +1149,7 @@ hos_status hos_trispectrum_batched(const void* d_x, int32_t dtype, const int64_t
     Plan4 P;
     hos_status s = make_plan4(HOS_OP_TRISPECTRUM_BATCHED, p, n_total, P, S, max_len);
     if (s != HOS_OK) return s;
-    if (!ws || ws_bytes < P.total) return HOS_ERR_WORKSPACE;
+    if (!ws || ws_bytes < P.total || fault_is("workspace")) return HOS_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     Tracer tr(st);
     s = run_c4(d_x, dtype, n_total, P, p, ws, ws_bytes, st, tr, 0, nullptr, d_offsets);
@@ -1158,7 +1199,9 @@ hos_status hos_bispectrum_backward(const void* d_x, int32_t dtype, int64_t n, co
     PlanB P;
     hos_status s = make_planb(p, n, P);
     if (s != HOS_OK) return s;
-    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < P.total) return HOS_ERR_WORKSPACE;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < P.total ||
+        fault_is("workspace"))
+        return HOS_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     Tracer tr(st);
     int64_t* off = at<int64_t>(ws, P.off);
@@ -1214,7 +1257,9 @@ hos_status hos_trispectrum_backward(const void* d_x, int32_t dtype, int64_t n, c
     PlanB4 P;
     hos_status s = make_planb4(p, n, P);
     if (s != HOS_OK) return s;
-    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < P.total) return HOS_ERR_WORKSPACE;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < P.total ||
+        fault_is("workspace"))
+        return HOS_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     Tracer tr(st);
     int64_t* off = at<int64_t>(ws, P.off);

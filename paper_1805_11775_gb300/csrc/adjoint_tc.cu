@@ -274,7 +274,11 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
         }
         if (ok && cur_b >= 0) mma_commit(&sm.b_empty);
         mma_commit(&sm.drain);
-        mbar_wait(&sm.drain, 0, abort, P.status, lim);
+        {   // every MMA must have completed before TMEM is freed, also after an
+            // abort: wait whatever the abort flag says, bounded (at least 0.2 s)
+            volatile int keep_waiting = 0;
+            mbar_wait(&sm.drain, 0, &keep_waiting, P.status, lim > 200000000ull ? lim : 200000000ull);
+        }
     } else if (warp < 4) {
         // ---------------------------------------------------------- epilogue
         const int q = warp;                // TMEM lane quadrant

@@ -422,7 +422,11 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
         }
         // drain every MMA this thread issued before TMEM is released
         mma_commit(&sm.drain);
-        mbar_wait(&sm.drain, 0, abort, P.status, lim);
+        {   // every MMA must have completed before TMEM is freed, also after an
+            // abort: wait whatever the abort flag says, bounded (at least 0.2 s)
+            volatile int keep_waiting = 0;
+            mbar_wait(&sm.drain, 0, &keep_waiting, P.status, lim > 200000000ull ? lim : 200000000ull);
+        }
     }
 
     tc_fence_before();

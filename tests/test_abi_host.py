@@ -172,3 +172,42 @@ def test_fourth_order_slice_checks(lib):
     assert lib.hos_moments4_slice(dummy, 0, 1000, 8, 16, dummy, 1000, ctypes.byref(p), dummy, dummy, ws, 1 << 30,
                                   None) == 1
     assert lib.hos_trispectrum_from_moments(None, dummy, ctypes.byref(p), dummy, ws, 1 << 30, None) == 1
+
+
+_FAULT_CHILD = r'''
+import ctypes, json, sys
+sys.path.insert(0, sys.argv[1])
+from paper_1805_11775_gb300 import _native, make_params
+lib = _native.lib()
+d = ctypes.c_void_p(1 << 20)      # never dereferenced: every call stops before any GPU work
+ws = ctypes.c_void_p(1 << 30)     # 256-byte aligned
+big = ctypes.c_size_t(1 << 40)
+out = {}
+p = make_params(16, precision=1)
+out["bispectrum"] = lib.hos_bispectrum(d, 1, 5000, ctypes.byref(p), d, ws, big, None)
+out["trispectrum"] = lib.hos_trispectrum(d, 1, 5000, ctypes.byref(make_params(8, precision=1)), d, ws, big, None)
+out["backward"] = lib.hos_bispectrum_backward(d, 1, 5000, ctypes.byref(p), d, d, ws, big, None)
+out["tri_backward"] = lib.hos_trispectrum_backward(d, 1, 5000, ctypes.byref(make_params(8, precision=1)), d, d, ws,
+                                                   big, None)
+out["overlap"] = lib.hos_bispectrum(d, 1, 50000, ctypes.byref(make_params(16, precision=1, segment_len=4096,
+                                                                          segment_overlap=1024)), d, ws, big, None)
+print(json.dumps(out))
+'''
+
+
+@pytest.mark.parametrize("fault,status", [("workspace", 3), ("cuda", 4)])
+def test_host_fault_injection(lib, fault, status):
+    """HOS_FAULT=workspace / cuda: every entry point reports the injected
+    status after its argument checks, before anything reaches a GPU (runs
+    here without one)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, HOS_FAULT=fault)
+    r = subprocess.run([sys.executable, "-c", _FAULT_CHILD, root], env=env, capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0, r.stderr
+    got = json.loads(r.stdout.strip().splitlines()[-1])
+    assert all(v == status for v in got.values()), got
