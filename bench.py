@@ -462,26 +462,14 @@ def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
     raise KeyError(name)
 
 
-def run_ours(args):
-    import numpy as np
-    import torch
-
-    import paper_1805_11775_gb300 as hos
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    prec = args.precision
-    wl = make_workload(args.workload, prec, rank, hos, torch, args.series, args.time_slices)
+def time_arm(wl, args, hos, torch, flush_buf, dist, local, world, sliced):
+    """Warm up, capture one step in a CUDA graph (one rank, unless eager),
+    time exactly args.steps steps with CUDA events (L2 flushed before each,
+    outside the events, clocks sampled), then take the stage times from eager
+    profiled passes when the timed steps could not trace them.  Returns
+    (ms per step, max over ranks; stage times; launches in the timed region;
+    clocks; launch mode; wall seconds of the timed region)."""
     step = wl["step"]
-    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
-
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -493,7 +481,6 @@ def run_ours(args):
     graph = None
     # one GPU: replay a captured CUDA graph of the step (the launches of every
     # stage, no host gaps); the time-sliced multi-rank step runs eagerly
-    sliced = args.workload == WORKLOAD and (world > 1 or args.time_slices)
     if args.graph or (not args.eager and not sliced):
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph):
@@ -553,14 +540,44 @@ def run_ours(args):
         hos.set_profiling(False)
     if graph is not None:
         launches = launches_per_step * args.steps  # replays re-run the captured launches
+    mode = "cuda graph replay" if graph is not None else "eager (C ABI per step)"
+    return ms, stage_acc, launches, clk, mode, t_wall
+
+
+def tensor_peak(prec, pk, src):
+    """Dense tensor peak of the contraction's operand type (TFLOP/s)."""
+    if prec == "bf16":
+        return pk["bf16_tflops"], f"bf16 dense, {src} burst"
+    return pk["bf16_tflops"] * (1.1 / 2.25), f"tf32 dense = {src} bf16 burst x 1.1/2.25 (nominal ratio)"
+
+
+def run_ours(args):
+    import torch
+
+    import hos_synth
+    import paper_1805_11775_gb300 as hos
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    prec = args.precision
+    wl = make_workload(args.workload, prec, rank, hos, torch, args.series, args.time_slices)
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+    sliced = args.workload == WORKLOAD and (world > 1 or args.time_slices)
+    ms, stage_acc, launches, clk, mode, t_wall = time_arm(wl, args, hos, torch, flush_buf, dist, local, world, sliced)
     contract_ms = statistics.mean(stage_acc.get("contract", [float("nan")]))
+    contraction = hos.last_contraction()
+    plan = hos.last_plan()
 
     pk, src = peaks()
-    if wl["bound"] == "tensor" and prec == "bf16":
-        peak, peak_note = pk["bf16_tflops"], f"bf16 dense, {src} burst"
-    elif wl["bound"] == "tensor":
-        peak = pk["bf16_tflops"] * (1.1 / 2.25)
-        peak_note = f"tf32 dense = {src} bf16 burst x 1.1/2.25 (nominal ratio)"
+    if wl["bound"] == "tensor":
+        peak, peak_note = tensor_peak(prec, pk, src)
     else:
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         peak_note = "FP32 FFMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
@@ -574,7 +591,7 @@ def run_ours(args):
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     per_clk = 8192 if prec == "bf16" else 4096
     clock_peak = nsm * per_clk * (clk["sm_mhz"] or 2070.0) * 1e6 / 1e12
-    is_tc = hos.last_contraction().startswith("c3_tcgen05")
+    is_tc = contraction.startswith("c3_tcgen05")
     traffic = profiled_traffic(prec) if (is_tc and args.workload == WORKLOAD) else None
 
     e2e_t = []
@@ -613,14 +630,16 @@ def run_ours(args):
         "vs_baseline": value / wl["paper_value"] if "paper_value" in wl else None,
         "dtype": "f32 (transform, products), double-float window sums" if "roof" in wl else
                  {"bf16": "bf16x3 (split-bf16, fp32 accumulate, fp64-class reduce)",
-                  "fp32": "tf32x3 (fp32-class, fp32 accumulate, fp64-class reduce)", "simt": "f32"}[prec],
+                  "fp32": "tf32x3 (fp32-class, fp32 accumulate, fp64-class reduce)",
+                  "tf32": "tf32 (one product, fp32 accumulate, fp64-class reduce)", "simt": "f32"}[prec],
         "data": "synthetic",
-        "config": dict({"workload": args.workload, "precision": prec, "contraction": hos.last_contraction(),
+        "config": dict({"workload": args.workload, "precision": prec, "contraction": contraction,
+                        "plan": plan,
                         "l2": "flushed between timed steps (256 MB write)",
-                        "launch": "cuda graph replay" if graph is not None else "eager (C ABI per step)",
+                        "launch": mode,
                         "parallelism": "replicas" if world > 1 else "single"}, **wl["config"]),
         "stage_ms": {k: statistics.mean(v) for k, v in stage_acc.items()},
-        "roofline": {"bound": wl["bound"], "kernel": hos.last_contraction(), "achieved": achieved, "peak": peak,
+        "roofline": {"bound": wl["bound"], "kernel": contraction, "achieved": achieved, "peak": peak,
                      "unit": roof_unit, "frac": achieved / peak, "traffic": traffic, "peak_source": peak_note,
                      "frac_clock_matched": achieved / clock_peak if wl["bound"] == "tensor" else None,
                      "work": wl["work"]},
@@ -631,13 +650,34 @@ def run_ours(args):
         "wall_s_timed": t_wall,
     }
     line.update(extra)
+    ref_rows = None
     if rank == 0 and not args.no_cpu_baseline and "accuracy" in wl:
         line["accuracy"] = wl["accuracy"]()
     if rank == 0 and not args.no_cpu_baseline and args.workload == WORKLOAD:
-        import hos_synth
         x_host = hos_synth.workload(WORKLOAD)["x"]
-        line["cpu_baseline"], (lo, ref) = cpu_baseline(x_host, 256, x_host.size)
-        line["accuracy"] = accuracy(hos, torch, x_host, 256, prec, lo, ref)
+        line["cpu_baseline"], ref_rows = cpu_baseline(x_host, 256, x_host.size)
+        line["accuracy"] = accuracy(hos, torch, x_host, 256, prec, *ref_rows)
+    if (args.compare and args.compare != prec and world == 1 and "roof" not in wl
+            and args.workload not in ("differentiable_trispectrum_n65536_L32",)):
+        # the same workload in a second precision on the same GPU (the metric's
+        # "split-BF16 vs FP32, same GPU"), timed the same way
+        wl2 = make_workload(args.workload, args.compare, rank, hos, torch, args.series, args.time_slices)
+        ms2, st2, launches2, clk2, mode2, _ = time_arm(wl2, args, hos, torch, flush_buf, dist, local, world, sliced)
+        c2_ms = statistics.mean(st2.get("contract", [float("nan")]))
+        pk2, note2 = tensor_peak(args.compare, pk, src)
+        arm = {"precision": args.compare, "contraction": hos.last_contraction(), "plan": hos.last_plan(),
+               "ms_per_step": ms2, "value": wl2["units"] * world / (ms2 * 1e-3), "unit": wl2.get("unit", UNIT),
+               "launch": mode2, "stage_ms": {k: statistics.mean(v) for k, v in st2.items()},
+               "clocks": clk2, "gpu_launches": launches2}
+        if wl2["bound"] == "tensor":
+            ach2 = wl2["flops"] / (c2_ms * 1e-3) / 1e12
+            arm["roofline"] = {"bound": "tensor", "achieved": ach2, "peak": pk2, "unit": "TFLOP/s",
+                               "frac": ach2 / pk2, "peak_source": note2, "work": wl2["work"]}
+        if ref_rows is not None:
+            arm["accuracy"] = accuracy(hos, torch, x_host, 256, args.compare, *ref_rows)
+        elif rank == 0 and not args.no_cpu_baseline and "accuracy" in wl2:
+            arm["accuracy"] = wl2["accuracy"]()
+        line["compare"] = arm
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -652,7 +692,9 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "simt"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "tf32", "simt"])
+    ap.add_argument("--compare", default="fp32", choices=["", "bf16", "fp32", "tf32", "simt"],
+                    help="also time this precision on the same workload and GPU (\"\" to skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "bispectrum_n2048_L32", "trispectrum_n65536_L32", "batched_4096x_L128",

@@ -70,12 +70,16 @@ typedef enum { HOS_F32 = 0, HOS_F64 = 1 } hos_dtype;
  *   SPLIT_BF16  : x = hi + lo in bf16, three products on the tensor cores
  *                 (tcgen05 kind::f16), FP32 accumulation, FP64-class
  *                 reduction (~1e-5);
+ *   TF32        : one plain TF32 product per term (tcgen05 kind::tf32, the
+ *                 factors rounded to 10 mantissa bits), FP32 accumulation:
+ *                 about 1e-4 to 1e-3, for comparison only (no accuracy
+ *                 target); the adjoint runs it on the CUDA cores;
  *   SIMT_FP32   : plain FP32 FFMA on the CUDA cores (cross-check path).
  * Mean removal is FP64.  The cross-chunk reduction and c2 are FP64-class in
  * every mode: double-float sums (two floats, TwoSum / FMA, about 44-48
  * significant bits) on the FP32 pipes, since GB300 issues FP64 at about 1/64
  * of its FP32 rate.                                                        */
-typedef enum { HOS_PREC_FP32 = 0, HOS_PREC_SPLIT_BF16 = 1, HOS_PREC_SIMT_FP32 = 2 } hos_precision;
+typedef enum { HOS_PREC_FP32 = 0, HOS_PREC_SPLIT_BF16 = 1, HOS_PREC_TF32 = 2, HOS_PREC_SIMT_FP32 = 3 } hos_precision;
 
 /* Lag windows.  PARZEN: d(w1)d(w2)[d(w3)] (separable).  PARZEN_SYM (bispectrum
  * only): d(w1)d(w2)d(w1-w2), which keeps c3's six-fold symmetry.  RECT: 1 for
@@ -321,11 +325,34 @@ hos_status hos_bispectrum_direct(const void* d_x, int32_t dtype, int64_t n, int3
  * status word it needs at zero): calls that overlap in time on the GPU
  * (different streams, or different host threads) race with each other and
  * must be serialised by the caller.  A device-side timeout is recorded in
- * the array's own status word, which callers cannot read; the next call
- * clears it.                                                                */
+ * the array's own status word; read it with hos_bispectrum_noalloc_status
+ * once the stream has completed (the next call clears it).  After a device
+ * reset the address is looked up again on the next call.                   */
 #define HOS_NOALLOC_SCRATCH_BYTES (32u << 20)
 hos_status hos_bispectrum_noalloc(const void* d_x, int32_t dtype, int64_t n, const hos_params* params, void* d_B,
                                   hos_stream_t stream);
+
+/* Read (synchronously) the device status word of the current device's
+ * no-allocation scratch array, as hos_get_device_status does for a caller's
+ * workspace: *status = HOS_OK, HOS_ERR_TIMEOUT or HOS_ERR_DEVICE_FAULT for
+ * the last hos_bispectrum_noalloc call on this device.  Call it after that
+ * call's stream has completed.  Allocates nothing.                          */
+hos_status hos_bispectrum_noalloc_status(int32_t* status);
+
+/* Host-only consistency check of a contraction plan (no GPU is touched): the
+ * series layout, every CTA's walk over the cost-weighted work split, the slot
+ * each partial tile goes to, the reduction's reading of those slots, and the
+ * bounds and 16-byte alignment of every bulk copy the producer would issue,
+ * run on the CPU with the code the kernels use.
+ *   op        : HOS_OP_BISPECTRUM (one series, parts by segment_len),
+ *               HOS_OP_BISPECTRUM_BATCHED (h_offsets: S+1 HOST int64), or
+ *               HOS_OP_TRISPECTRUM (tensor-core fourth-order plan)
+ *   ctas      : 0 = the plan's own CTA count on the current device; else this many
+ *   msg       : optional text buffer for the first violation (or a summary)
+ * Returns HOS_OK, HOS_ERR_DEVICE_FAULT for an inconsistent plan, or the
+ * argument error the entry point would return.                            */
+hos_status hos_check_plan(int32_t op, int64_t n_total, int32_t n_series, const int64_t* h_offsets,
+                          const hos_params* params, int32_t ctas, char* msg, size_t msg_len);
 
 /* Read (synchronously) the device status word of a workspace that a finished
  * call used.  *status = HOS_OK, HOS_ERR_TIMEOUT or HOS_ERR_DEVICE_FAULT.     */
@@ -354,6 +381,11 @@ int64_t hos_launch_count(void);
 
 /* Name of the contraction kernel variant the last call used.               */
 const char* hos_last_contraction(void);
+
+/* The last call's contraction plan as text: the widest lag tile, the tile
+ * count and widths, the flush length, chunk length, CTAs and products per
+ * term (what an autotuner chose, or the automatic choice).                 */
+const char* hos_last_plan(void);
 
 const char* hos_status_string(int32_t status);
 const char* hos_version(void);

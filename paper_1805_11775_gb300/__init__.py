@@ -24,10 +24,10 @@ __all__ = ["bispectrum", "bispectrum_batched", "trispectrum", "trispectrum_batch
            "bispectrum_backward", "trispectrum_backward", "BispectrumFn", "TrispectrumFn", "bispectrum_ad",
            "trispectrum_ad", "bispectrum_direct", "series_sum", "cumulant3_slice", "bispectrum_from_cumulant",
            "bispectrum_sharded", "moments4_slice", "trispectrum_from_moments", "trispectrum_sharded", "Workspace", "workspace_size", "device_status", "reset_device_status",
-           "selftest_timeout", "set_profiling", "stage_times", "launch_count", "last_contraction", "HosError",
+           "selftest_timeout", "set_profiling", "stage_times", "launch_count", "last_contraction", "last_plan", "HosError",
            "PRECISIONS", "WINDOWS"]
 
-PRECISIONS = {"fp32": 0, "3xtf32": 0, "bf16": 1, "split_bf16": 1, "simt": 2, "simt_fp32": 2}
+PRECISIONS = {"fp32": 0, "3xtf32": 0, "bf16": 1, "split_bf16": 1, "tf32": 2, "simt": 3, "simt_fp32": 3}
 WINDOWS = {"parzen": 0, "parzen_sym": 1, "rect": 2}
 
 
@@ -616,3 +616,8 @@ def launch_count() -> int:
 
 def last_contraction() -> str:
     return _native.lib().hos_last_contraction().decode()
+
+
+def last_plan() -> str:
+    """The last call's contraction plan (tile widths, flush, chunk, CTAs), as text."""
+    return _native.lib().hos_last_plan().decode()

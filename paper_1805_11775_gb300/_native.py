@@ -51,6 +51,7 @@ _SIGS = {
                            _VP, _VP, _VP, ctypes.c_size_t, _VP],
     "hos_trispectrum_from_moments": [_VP, _VP, _P, _VP, _VP, ctypes.c_size_t, _VP],
     "hos_bispectrum_noalloc": [_VP, ctypes.c_int32, ctypes.c_int64, _P, _VP, _VP],
+    "hos_bispectrum_noalloc_status": [ctypes.POINTER(ctypes.c_int32)],
     "hos_cumulant3": [_VP, ctypes.c_int32, ctypes.c_int64, _P, _VP, _VP, ctypes.c_size_t, _VP],
     "hos_cumulant4": [_VP, ctypes.c_int32, ctypes.c_int64, _P, _VP, _VP, ctypes.c_size_t, _VP],
     "hos_trispectrum_batched": [_VP, ctypes.c_int32, _VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P, _VP,
@@ -63,6 +64,8 @@ _SIGS = {
                                              ctypes.POINTER(ctypes.c_size_t)],
     "hos_bispectrum_direct": [_VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                               ctypes.c_int32, _VP, _VP, ctypes.c_size_t, _VP],
+    "hos_check_plan": [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _VP, _P, ctypes.c_int32, ctypes.c_char_p,
+                       ctypes.c_size_t],
     "hos_get_device_status": [_VP, ctypes.POINTER(ctypes.c_int32)],
     "hos_reset_device_status": [_VP, _VP],
     "hos_selftest_timeout": [_VP, ctypes.c_size_t, ctypes.c_int32, _VP],
@@ -71,10 +74,12 @@ _SIGS = {
     "hos_stage_name": [ctypes.c_int32],
     "hos_launch_count": [],
     "hos_last_contraction": [],
+    "hos_last_plan": [],
     "hos_status_string": [ctypes.c_int32],
     "hos_version": [],
 }
 _RESTYPES = {"hos_stage_name": ctypes.c_char_p, "hos_last_contraction": ctypes.c_char_p,
+             "hos_last_plan": ctypes.c_char_p,
              "hos_status_string": ctypes.c_char_p, "hos_version": ctypes.c_char_p,
              "hos_launch_count": ctypes.c_int64}
 

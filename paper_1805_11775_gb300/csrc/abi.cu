@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -18,6 +19,20 @@ static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 static const char* g_last_contraction = "none";
+static char g_last_plan[160] = "none";
+
+// Records the contraction plan of the last call (hos_last_plan).
+static void note_plan(const C3Geom& g, int products) {
+    int w256 = 0, wmin = 1 << 30;
+    for (int t = 0; t < g.ntiles; ++t) {
+        const int w = 32 * g.tile_w32[t];
+        if (w == 256) ++w256;
+        if (w < wmin) wmin = w;
+    }
+    snprintf(g_last_plan, sizeof(g_last_plan),
+             "tile_n=%d tiles=%d (256-wide %d, narrowest %d) flush=%d kc=%d ctas=%d products=%d", g.tile_n,
+             g.ntiles, w256, g.ntiles ? wmin : 0, g.flush, g.kc, g.G, products);
+}
 
 // ---- host-side fault injection ----------------------------------------------------
 // HOS_FAULT (read at every entry): "workspace" makes each entry point report
@@ -29,13 +44,48 @@ static bool fault_is(const char* what) {
     return f && std::strcmp(f, what) == 0;
 }
 
+// ---- current context ----------------------------------------------------------
+// Identifier of the calling thread's current CUDA context (unique for the life
+// of the process; a reset device gets a new one), or 0 when there is none yet
+// or the driver cannot say.  The driver entry points are looked up through the
+// runtime, so the library does not link the driver library itself.
+using CtxGetCurrentFn = int (*)(void**);
+using CtxGetIdFn = int (*)(void*, unsigned long long*);
+
+uint64_t current_context_id() {
+    static std::once_flag once;
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    if (!get_current || !get_id) return 0;
+    void* ctx = nullptr;
+    if (get_current(&ctx) != 0 || ctx == nullptr) return 0;
+    unsigned long long id = 0;
+    if (get_id(ctx, &id) != 0) return 0;
+    return (uint64_t)id + 1;  // never 0 for a live context
+}
+
 // ---- tracing ------------------------------------------------------------------
 constexpr int MAX_STAGES = 8;
+constexpr int MAX_DEVICES = 64;
 static std::mutex g_prof_mu;
 static bool g_prof_on = false;
-static cudaEvent_t g_ev[MAX_STAGES + 1];
-static bool g_ev_made = false;
-static int g_prof_n = 0;  // events recorded by the last call
+// Events belong to the device (context) they were created on: one set per
+// device, remade when the device's context has changed.
+static cudaEvent_t g_ev[MAX_DEVICES][MAX_STAGES + 1];
+static uint64_t g_ev_ctx[MAX_DEVICES] = {0};
+static int g_prof_dev = 0;  // device of the last traced call
+static int g_prof_n = 0;    // events recorded by the last call
 static const char* g_cur_names[MAX_STAGES];
 
 // Stage events (when profiling is on) and an NVTX range per stage (always;
@@ -45,14 +95,31 @@ struct Tracer {
     int n = 0;
     bool on;
     bool range_open = false;
+    cudaEvent_t* ev = nullptr;
     explicit Tracer(cudaStream_t s) : st(s) {
         std::lock_guard<std::mutex> lk(g_prof_mu);
         on = g_prof_on;
-        if (on && !g_ev_made) {
-            for (int i = 0; i <= MAX_STAGES; ++i) cudaEventCreate(&g_ev[i]);
-            g_ev_made = true;
+        if (!on) return;
+        int dev = -1;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+            on = false;
+            return;
         }
-        if (on) g_prof_n = 0;
+        // 0: no context made current yet (the first event creation makes the
+        // device's primary context current) or the driver cannot say
+        const uint64_t ctx = current_context_id();
+        if (g_ev_ctx[dev] == 0 || (ctx != 0 && g_ev_ctx[dev] != ctx)) {
+            for (int i = 0; i <= MAX_STAGES; ++i)
+                if (cudaEventCreate(&g_ev[dev][i]) != cudaSuccess) {
+                    on = false;
+                    return;
+                }
+            const uint64_t now = current_context_id();
+            g_ev_ctx[dev] = now ? now : ~0ull;
+        }
+        ev = g_ev[dev];
+        g_prof_dev = dev;
+        g_prof_n = 0;
     }
     ~Tracer() {
         if (range_open) nvtxRangePop();
@@ -67,7 +134,7 @@ struct Tracer {
             range_open = true;
         }
         if (!on || n > MAX_STAGES) return;
-        cudaEventRecord(g_ev[n], st);
+        cudaEventRecord(ev[n], st);
         if (n < MAX_STAGES) g_cur_names[n] = next_stage;
         ++n;
         g_prof_n = n;
@@ -113,7 +180,7 @@ static hos_status check_params(const hos_params* p, int op) {
         const int nf = p->nfft ? p->nfft : 2 * p->L;
         if ((nf & (nf - 1)) != 0 && nf > 2048) return HOS_ERR_UNSUPPORTED;
     }
-    if (p->precision < 0 || p->precision > 2) return HOS_ERR_INVALID_ARG;
+    if (p->precision < 0 || p->precision > 3) return HOS_ERR_INVALID_ARG;
     if (p->window < 0 || p->window > 2) return HOS_ERR_INVALID_ARG;
     if (p->segment_len < 0) return HOS_ERR_INVALID_ARG;
     if (p->tile_n != 0 && p->tile_n != 32 && p->tile_n != 64 && p->tile_n != 128 && p->tile_n != 256)
@@ -162,9 +229,51 @@ static OverlapPlan overlap_plan(const hos_params* p, int64_t n) {
     return o;
 }
 
+// Tiles of the lag square: row block a (128 lags w1) takes the columns from
+// its own diagonal block on, j >= 128a (c3(w1,w2) = c3(w2,w1) fills the rest),
+// cut into tiles of N columns with a narrower last one (a multiple of 32).
 // skip_zero_window: leave out tiles where the window is zero at every lag
 // (PARZEN_SYM: d(w1 - w2) = 0 for |w1 - w2| >= L); the transform grid is
-// zero-filled there.  *zero_skipped counts them.
+// zero-filled there.  Returns the tile count (may exceed MAX_TILES: nothing is
+// written past it).
+static int build_tiles(C3Geom& g, int L, int N, bool skip_zero_window, int* zero_skipped) {
+    const int twoL = 2 * L;
+    int cnt = 0, k = 0, zs = 0;
+    for (int a = 0; a < g.tiles_m; ++a) {
+        const int c0 = a * TILE_M;
+        g.row_c0[a] = (uint16_t)c0;
+        for (int c = c0; c < twoL;) {
+            const int rem = (int)round_up(twoL - c, 32);
+            const int w = rem < N ? rem : N;
+            bool zero = false;
+            if (skip_zero_window) {
+                const int w1lo = -L + a * TILE_M, w1hi = w1lo + TILE_M - 1;
+                const int w2lo = -L + c, w2hi = w2lo + w - 1;
+                int gap = w1lo - w2hi;
+                if (w2lo - w1hi > gap) gap = w2lo - w1hi;
+                zero = gap >= L;  // min |w1 - w2| over the tile
+            }
+            if (zero) {
+                ++zs;
+            } else {
+                if (cnt < MAX_TILES) {
+                    g.tile_a[cnt] = (uint8_t)a;
+                    g.tile_c32[cnt] = (uint8_t)(c / 32);
+                    g.tile_w32[cnt] = (uint8_t)(w / 32);
+                    g.tile_kpre[cnt] = (uint16_t)k;
+                }
+                k += w / 32;
+                ++cnt;
+            }
+            c += w;
+        }
+    }
+    if (cnt <= MAX_TILES) g.tile_kpre[cnt] = (uint16_t)k;
+    g.ktot = k;
+    if (zero_skipped) *zero_skipped = zs;
+    return cnt;
+}
+
 static C3Geom make_geom(const hos_params* p, int G, bool skip_zero_window = false, int* zero_skipped = nullptr) {
     C3Geom g;
     memset(&g, 0, sizeof(g));
@@ -173,53 +282,40 @@ static C3Geom make_geom(const hos_params* p, int G, bool skip_zero_window = fals
     int N = p->tile_n ? p->tile_n : next_pow2(twoL);
     if (N < 32) N = 32;
     if (N > 256) N = 256;
-    g.tile_n = N;
     g.tiles_m = (twoL + TILE_M - 1) / TILE_M;
-    g.tiles_n = (twoL + N - 1) / N;
-    int cnt = 0;
-    for (int a = 0; a < MAX_TILES_M; ++a)
-        for (int b = 0; b < MAX_TILES_N; ++b) g.tile_idx[a][b] = -1;
-    for (int b = 0; b < g.tiles_n; ++b)
-        for (int a = 0; a < g.tiles_m; ++a) {
-            // every w1 of the tile above every w2: mirrored, not computed
-            const bool skip = (a * TILE_M >= b * N + N);
-            if (skip) continue;
-            if (skip_zero_window) {
-                const int w1lo = -p->L + a * TILE_M, w1hi = w1lo + TILE_M - 1;
-                const int w2lo = -p->L + b * N, w2hi = w2lo + N - 1;
-                int gap = w1lo - w2hi;
-                if (w2lo - w1hi > gap) gap = w2lo - w1hi;
-                if (gap >= p->L) {  // min |w1 - w2| over the tile
-                    if (zero_skipped) ++*zero_skipped;
-                    continue;
-                }
-            }
-            g.tile_idx[a][b] = (int8_t)cnt;
-            g.tile_a[cnt] = (uint8_t)a;
-            g.tile_b[cnt] = (uint8_t)b;
-            ++cnt;
-        }
-    g.ntiles = cnt;
+    // tile_n is a hint: narrow tiles over a wide lag square are widened until
+    // the plan has at most MAX_TILES tiles
+    while (build_tiles(g, p->L, N, skip_zero_window, zero_skipped) > MAX_TILES && N < 256) N *= 2;
+    g.tile_n = N;
+    g.ntiles = build_tiles(g, p->L, N, skip_zero_window, zero_skipped);
     // The tensor cores' FP32 accumulation loses a little on every MMA step, one-sidedly,
     // so its error grows with the steps one partial accumulates.  The 3xTF32 path
     // (8 samples per step) hands its partial to the reduction after every
     // 1024-sample chunk; split-bf16 (16 samples per step, 1e-4 target) and SIMT
     // (FP32 FFMA, round to nearest) after 16 chunks.
+    // Plain TF32 is limited by its 10-bit factors, not by the accumulation.
     g.flush = p->flush_chunks ? p->flush_chunks : (p->precision == HOS_PREC_FP32 ? 1 : 16);
     g.kc = KC;
     g.G = G;
-    const int reach = (g.tiles_m * TILE_M > g.tiles_n * N) ? g.tiles_m * TILE_M : g.tiles_n * N;
+    // zero samples after a series: every sample a tile's windows read (the
+    // SIMT kernel reads all N columns of a tile, the tensor cores its width)
+    int reach = g.tiles_m * TILE_M;
+    for (int t = 0; t < g.ntiles; ++t)
+        if (32 * g.tile_c32[t] + N > reach) reach = 32 * g.tile_c32[t] + N;
     g.pad_tail = reach + 64;
     return g;
 }
 
 static int contraction_ctas(int precision) { return precision == HOS_PREC_SIMT_FP32 ? 4 * sm_count() : sm_count(); }
 
+static bool tf32_kind(int precision) { return precision == HOS_PREC_FP32 || precision == HOS_PREC_TF32; }
+// products per lag term on the tensor cores: hi*hi + hi*lo + lo*hi, or hi*hi alone (plain TF32)
+static int tc_products(int precision) { return precision == HOS_PREC_TF32 ? 1 : 3; }
 static int plane_split(int precision) {
-    return precision == HOS_PREC_SPLIT_BF16 ? 1 : (precision == HOS_PREC_FP32 ? 2 : 0);
+    return precision == HOS_PREC_SPLIT_BF16 ? 1 : (tf32_kind(precision) ? 2 : 0);
 }
 static int plane_elt(int precision) {
-    return precision == HOS_PREC_SPLIT_BF16 ? 2 : (precision == HOS_PREC_FP32 ? 4 : 0);
+    return precision == HOS_PREC_SPLIT_BF16 ? 2 : (tf32_kind(precision) ? 4 : 0);
 }
 
 static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -417,8 +513,8 @@ static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int6
 
     tr.mark("prep");
     const int mode = (op == HOS_OP_BISPECTRUM_BATCHED) ? 1 : 0;
-    HOS_CUDA_TRY(launch_plan_series(mode, n, P.seg, d_offsets, S, p->L, g.ntiles, g.flush, g.kc, g.pad_tail, off,
-                                    pad, unit, win, st));
+    HOS_CUDA_TRY(launch_plan_series(mode, n, P.seg, d_offsets, S, p->L, g.ntiles, g.ktot, g.flush, g.kc, g.pad_tail,
+                                    off, pad, unit, win, st));
     const void* xs = x;
     if (sl) {  // the whole series' mean; the slice's first sample follows its halo
         HOS_CUDA_TRY(launch_slice_mean(sl->d_sum, sl->n_total, p->remove_mean, mean, st));
@@ -439,11 +535,14 @@ static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int6
         C3SimtParams cp{g, sv, y32, partials};
         HOS_CUDA_TRY(launch_c3_simt(cp, g.G, st));
         g_last_contraction = "c3_simt_fp32";
+        note_plan(g, 1);
     } else {
-        C3TcParams cp{g, sv, y32, hi, lo, partials, status, wait_limit_ns()};
-        const bool tf32 = (p->precision == HOS_PREC_FP32);
+        C3TcParams cp{g, sv, y32, hi, lo, partials, status, wait_limit_ns(), tc_products(p->precision)};
+        const bool tf32 = tf32_kind(p->precision);
         HOS_CUDA_TRY(launch_c3_tc(tf32, 3, cp, g.G, st));
-        g_last_contraction = tf32 ? "c3_tcgen05_3xtf32" : "c3_tcgen05_split_bf16";
+        g_last_contraction = p->precision == HOS_PREC_TF32 ? "c3_tcgen05_tf32"
+                             : (tf32 ? "c3_tcgen05_3xtf32" : "c3_tcgen05_split_bf16");
+        note_plan(g, tc_products(p->precision));
     }
 
     tr.mark("reduce");
@@ -513,15 +612,16 @@ static C3Geom make_geom4(const hos_params* p, int G) {
     if (N < 32) N = 32;
     g.tile_n = N;
     const int npairs = twoL * (twoL + 1) / 2;
-    g.tiles_m = (npairs + TILE_M - 1) / TILE_M;
-    g.tiles_n = 1;
+    g.tiles_m = (npairs + TILE_M - 1) / TILE_M;  // blocks of pairs (row_c0 is unused)
     g.ntiles = g.tiles_m;
-    for (int a = 0; a < MAX_TILES_M; ++a)
-        for (int b = 0; b < MAX_TILES_N; ++b) g.tile_idx[a][b] = -1;
     for (int t = 0; t < g.ntiles; ++t) {
         g.tile_a[t] = (uint8_t)t;
-        g.tile_b[t] = 0;
+        g.tile_c32[t] = 0;
+        g.tile_w32[t] = (uint8_t)(N / 32);
+        g.tile_kpre[t] = (uint16_t)(t * (N / 32));
     }
+    g.tile_kpre[g.ntiles] = (uint16_t)(g.ntiles * (N / 32));
+    g.ktot = g.ntiles * (N / 32);
     // c4 = m4 - sum c2*c2 cancels, which magnifies the tensor cores' one-sided
     // FP32 accumulation loss: partials go to the reduction after every
     // chunk, and 3xTF32 chunks are 128 samples (48 MMA steps)
@@ -626,10 +726,11 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
     float* y32 = at<float>(ws, P.y32);
     tr.mark("prep");
     const int ntiles = P.tc ? P.g4.ntiles : 1;
+    const int ktot = P.tc ? P.g4.ktot : 1;
     const int flush = P.tc ? P.g4.flush : C4_CHUNK_GROUP;
     const int kc = P.tc ? P.g4.kc : KC;
-    HOS_CUDA_TRY(launch_plan_series(P.batched ? 1 : 0, n, P.seg, d_offsets, P.S, p->L, ntiles, flush, kc, P.pad_tail,
-                                    off, pad, unit, win, st));
+    HOS_CUDA_TRY(launch_plan_series(P.batched ? 1 : 0, n, P.seg, d_offsets, P.S, p->L, ntiles, ktot, flush, kc,
+                                    P.pad_tail, off, pad, unit, win, st));
     if (sl) HOS_CUDA_TRY(launch_slice_mean(sl->d_sum, sl->n_total, p->remove_mean, mean, st));
     else HOS_CUDA_TRY(launch_mean(x, dtype, off, P.S, P.nslices, at<double>(ws, P.mpart), p->remove_mean, mean, st));
     const int64_t maxpad = (int64_t)p->L + P.max_len + KC + P.pad_tail + 64;
@@ -663,10 +764,13 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
     HOS_CUDA_TRY(launch_c2(y32, off, pad, P.S, p->L, P.c2s, c2, at<float2>(ws, P.c2p), st, sl ? 1 : 0,
                            sl ? sl->n_total : 0));
     SeriesView sv{off, pad, unit, win, mean, P.S};
-    C3TcParams cp{P.g4, sv, y32, hi, lo, at<float>(ws, P.partials), at<int>(ws, P.status), wait_limit_ns()};
-    const bool tf32 = (p->precision == HOS_PREC_FP32);
+    C3TcParams cp{P.g4, sv, y32, hi, lo, at<float>(ws, P.partials), at<int>(ws, P.status), wait_limit_ns(),
+                  tc_products(p->precision)};
+    const bool tf32 = tf32_kind(p->precision);
     HOS_CUDA_TRY(launch_c3_tc(tf32, 4, cp, P.g4.G, st));
-    g_last_contraction = tf32 ? "m4_tcgen05_3xtf32" : "m4_tcgen05_split_bf16";
+    g_last_contraction = p->precision == HOS_PREC_TF32 ? "m4_tcgen05_tf32"
+                         : (tf32 ? "m4_tcgen05_3xtf32" : "m4_tcgen05_split_bf16");
+    note_plan(P.g4, tc_products(p->precision));
     tr.mark("reduce");
     double* m4buf = at<double>(ws, P.m4buf);
     HOS_CUDA_TRY(launch_m4_tile_reduce(P.g4, sv, P.max_len, at<float>(ws, P.partials), at<int64_t>(ws, P.bnd),
@@ -847,6 +951,7 @@ const char* hos_status_string(int32_t s) {
 
 int64_t hos_launch_count(void) { return g_launches.load(); }
 const char* hos_last_contraction(void) { return g_last_contraction; }
+const char* hos_last_plan(void) { return g_last_plan; }
 
 hos_status hos_workspace_size(int32_t op, int64_t n_total, int32_t n_series, int64_t max_len, const hos_params* p,
                               size_t* bytes) {
@@ -1209,7 +1314,7 @@ hos_status hos_bispectrum_backward(const void* d_x, int32_t dtype, int64_t n, co
     float* y32 = at<float>(ws, P.y32);
     const int L = p->L, Nf = P.Nf;
     tr.mark("prep");
-    HOS_CUDA_TRY(launch_plan_series(0, n, 0, nullptr, 1, L, 1, 16, KC, P.g.pad_tail, off, pad,
+    HOS_CUDA_TRY(launch_plan_series(0, n, 0, nullptr, 1, L, 1, 1, 16, KC, P.g.pad_tail, off, pad,
                                     at<int64_t>(ws, P.unit), at<int64_t>(ws, P.win), st));
     HOS_CUDA_TRY(launch_mean(d_x, dtype, off, 1, P.nslices, at<double>(ws, P.mpart), p->remove_mean,
                              at<double>(ws, P.mean), st));
@@ -1267,7 +1372,7 @@ hos_status hos_trispectrum_backward(const void* d_x, int32_t dtype, int64_t n, c
     float* y32 = at<float>(ws, P.y32);
     const int L = p->L, Nf = P.Nf;
     tr.mark("prep");
-    HOS_CUDA_TRY(launch_plan_series(0, n, 0, nullptr, 1, L, 1, 16, KC, P.g.pad_tail, off, pad,
+    HOS_CUDA_TRY(launch_plan_series(0, n, 0, nullptr, 1, L, 1, 1, 16, KC, P.g.pad_tail, off, pad,
                                     at<int64_t>(ws, P.unit), at<int64_t>(ws, P.win), st));
     HOS_CUDA_TRY(launch_mean(d_x, dtype, off, 1, P.nslices, at<double>(ws, P.mpart), p->remove_mean,
                              at<double>(ws, P.mean), st));
@@ -1310,6 +1415,164 @@ hos_status hos_trispectrum_backward(const void* d_x, int32_t dtype, int64_t n, c
     return HOS_OK;
 }
 
+// Host mirror of a contraction plan: the series layout, every CTA's walk, the
+// slots its parts write, the reduction's view of those slots and the bounds
+// and alignment of every bulk copy, run on the CPU with the same code the
+// kernels use (series_plan, Walk, tile_record, cta_slot_used).
+hos_status hos_check_plan(int32_t op, int64_t n_total, int32_t n_series, const int64_t* h_offsets,
+                          const hos_params* p, int32_t ctas, char* msg, size_t msg_len) {
+    auto fail = [&](const char* fmt, long long a, long long b, long long c) {
+        if (msg && msg_len) snprintf(msg, msg_len, fmt, a, b, c);
+        return HOS_ERR_DEVICE_FAULT;
+    };
+    if (msg && msg_len) msg[0] = 0;
+    if (!p || n_total < 0 || n_series < 1 || ctas < 0) return HOS_ERR_INVALID_ARG;
+    C3Geom g;
+    int S = 0, order = 3;
+    int64_t seg = 0, plane_len = 0, n_slots = 0;
+    if (op == HOS_OP_BISPECTRUM || op == HOS_OP_BISPECTRUM_BATCHED) {
+        if (op == HOS_OP_BISPECTRUM_BATCHED && !h_offsets) return HOS_ERR_INVALID_ARG;
+        int64_t max_len = n_total;
+        if (op == HOS_OP_BISPECTRUM_BATCHED) {
+            max_len = 0;
+            for (int s = 0; s < n_series; ++s) {
+                if (h_offsets[s + 1] < h_offsets[s]) return HOS_ERR_INVALID_ARG;
+                if (h_offsets[s + 1] - h_offsets[s] > max_len) max_len = h_offsets[s + 1] - h_offsets[s];
+            }
+        }
+        Plan P;
+        hos_status st = make_plan(op, p, n_total, n_series, max_len, P);
+        if (st != HOS_OK) return st;
+        g = P.g;
+        S = P.S;
+        seg = P.seg;
+        plane_len = P.l.plane_len;
+        n_slots = P.l.slots;
+    } else if (op == HOS_OP_TRISPECTRUM) {
+        Plan4 P;
+        hos_status st = make_plan4(op, p, n_total, P);
+        if (st != HOS_OK) return st;
+        if (!P.tc) return HOS_ERR_UNSUPPORTED;
+        g = P.g4;
+        S = P.S;
+        seg = P.seg;
+        order = 4;
+        plane_len = n_total + (int64_t)P.S * ((int64_t)p->L + KC + P.pad_tail + 64);
+        const int64_t chunks = ceil_div(n_total, g.kc) + P.S;
+        n_slots = (int64_t)g.ntiles * (chunks / g.flush + P.S + 1) + g.G;
+    } else {
+        return HOS_ERR_UNSUPPORTED;
+    }
+    if (ctas > 0) {  // another CTA count: the per-CTA slots follow it
+        n_slots += ctas - g.G;
+        g.G = ctas;
+    }
+    if (g.ntiles > MAX_TILES || g.ntiles < 1) return fail("tile count %lld outside 1..%lld", g.ntiles, MAX_TILES, 0);
+    // the plan kernel's layout
+    std::vector<int64_t> off(S + 1), pad(S + 1), unit(S + 1), win(S + 1), bnd(g.G + 1);
+    int64_t cp = 0, cu = 0, cw = 0;
+    for (int s = 0; s < S; ++s) {
+        int64_t o0, o1;
+        if (op == HOS_OP_BISPECTRUM_BATCHED) {
+            o0 = h_offsets[s];
+            o1 = h_offsets[s + 1];
+        } else {
+            o0 = seg ? s * seg : 0;
+            o1 = seg ? ((s + 1) * seg < n_total ? (s + 1) * seg : n_total) : n_total;
+        }
+        const SeriesPlan sp = series_plan(o1 - o0, p->L, g.ntiles, g.ktot, g.flush, g.kc, g.pad_tail);
+        off[s] = o0;
+        pad[s] = cp;
+        unit[s] = cu;
+        win[s] = cw;
+        cp += sp.plen;
+        cu += sp.cost;
+        cw += sp.wins;
+    }
+    off[S] = (op == HOS_OP_BISPECTRUM_BATCHED) ? h_offsets[S] : n_total;
+    pad[S] = cp;
+    unit[S] = cu;
+    win[S] = cw;
+    if (pad[S] > plane_len) return fail("planes need %lld samples, the workspace holds %lld", pad[S], plane_len, 0);
+    for (int q = 0; q <= g.G; ++q) bnd[q] = range_begin(q, unit[S], g.G);
+    const SeriesView sv{off.data(), pad.data(), unit.data(), win.data(), nullptr, S};
+    const int elt = plane_elt(p->precision);
+    // coverage of every (series, tile, chunk); the writer of every slot
+    std::vector<int64_t> tile0(S * (int64_t)g.ntiles + 1, 0);
+    for (int s = 0; s < S; ++s)
+        for (int t = 0; t < g.ntiles; ++t)
+            tile0[(int64_t)s * g.ntiles + t + 1] = tile0[(int64_t)s * g.ntiles + t] + ceil_div(off[s + 1] - off[s], g.kc);
+    std::vector<uint8_t> seen(tile0.back(), 0);
+    std::vector<int32_t> slot_part(n_slots, -1);
+    std::vector<int64_t> part_st;  // (s * ntiles + t) of each part
+    for (int cta = 0; cta < g.G; ++cta) {
+        Walk w;
+        w.init(g, sv, cta, g.G);
+        Part pt;
+        int mid_window = 0;
+        while (w.next(pt)) {
+            if (pt.s < 0 || pt.s >= S || pt.t < 0 || pt.t >= g.ntiles)
+                return fail("CTA %lld: part outside the plan (series %lld, tile %lld)", cta, pt.s, pt.t);
+            const int64_t nch = ceil_div(off[pt.s + 1] - off[pt.s], g.kc);
+            if (!(0 <= pt.c0 && pt.c0 < pt.c1 && pt.c1 <= nch) || (pt.c1 - 1) / g.flush != pt.c0 / g.flush)
+                return fail("CTA %lld: bad chunk range [%lld, %lld)", cta, pt.c0, pt.c1);
+            const int64_t st_idx = (int64_t)pt.s * g.ntiles + pt.t;
+            for (int64_t c = pt.c0; c < pt.c1; ++c) {
+                if (seen[tile0[st_idx] + c]++) return fail("chunk %lld of (series, tile) %lld run twice (CTA %lld)", c,
+                                                           st_idx, cta);
+                // bulk copies of the tensor-core producer (plane and y windows)
+                const int64_t i0 = c * g.kc;
+                const int col0 = 32 * g.tile_c32[pt.t], wt = 32 * g.tile_w32[pt.t];
+                const int64_t wb = pad[pt.s] + i0 + col0, wend = wb + g.kc + wt + 16;
+                const int64_t ab = (order == 3) ? pad[pt.s] + i0 + (int64_t)g.tile_a[pt.t] * TILE_M : pad[pt.s] + i0;
+                if (wend > pad[pt.s + 1] || ab + g.kc + TILE_M > pad[pt.s + 1])
+                    return fail("series %lld chunk %lld: a window reads past the series' block (tile %lld)", pt.s, c,
+                                pt.t);
+                if (elt && ((wb * elt) % 16 != 0 || ((g.kc + wt + 16) * elt) % 16 != 0 || (ab * 4) % 16 != 0))
+                    return fail("series %lld chunk %lld tile %lld: a bulk copy is not 16-byte aligned", pt.s, c, pt.t);
+            }
+            const int64_t nwin = ceil_div(nch, g.flush);
+            const int64_t want = (pt.c0 % g.flush == 0) ? win[pt.s] + (int64_t)pt.t * nwin + pt.c0 / g.flush
+                                                        : win[S] + cta;
+            if (pt.slot != want || pt.slot < 0 || pt.slot >= n_slots)
+                return fail("CTA %lld: part slot %lld, expected %lld", cta, pt.slot, want);
+            if (pt.c0 % g.flush != 0 && ++mid_window > 1)
+                return fail("CTA %lld: %lld parts start inside a window", cta, mid_window, 0);
+            if (slot_part[pt.slot] >= 0) return fail("slot %lld written twice (CTA %lld)", pt.slot, cta, 0);
+            slot_part[pt.slot] = (int32_t)part_st.size();
+            part_st.push_back(st_idx);
+        }
+    }
+    for (size_t q = 0; q < seen.size(); ++q)
+        if (seen[q] != 1) return fail("chunk %lld of the plan run %lld times", (long long)q, seen[q], 0);
+    // the reduction reads every part exactly once, from its own (series, tile)
+    std::vector<uint8_t> read(part_st.size(), 0);
+    for (int s = 0; s < S; ++s)
+        for (int t = 0; t < g.ntiles; ++t) {
+            const TileRec r = tile_record(g, sv, bnd.data(), s, t);
+            const int64_t st_idx = (int64_t)s * g.ntiles + t;
+            for (int f = 0; f < r.nwin; ++f) {
+                const int32_t q = slot_part[r.slot + f];
+                if (q < 0 || part_st[q] != st_idx) return fail("(series, tile) %lld window %lld: main slot %lld unset",
+                                                               st_idx, f, r.slot + f);
+                ++read[q];
+            }
+            for (int cta = r.xlo; cta < r.xhi; ++cta) {
+                if (!cta_slot_used(r, bnd.data(), cta, g.flush)) continue;
+                const int32_t q = slot_part[win[S] + cta];
+                if (q < 0 || part_st[q] != st_idx)
+                    return fail("(series, tile) %lld: CTA %lld slot holds no part of it", st_idx, cta, 0);
+                ++read[q];
+            }
+        }
+    for (size_t q = 0; q < read.size(); ++q)
+        if (read[q] != 1) return fail("part %lld read %lld times by the reduction", (long long)q, read[q], 0);
+    if (msg && msg_len)
+        snprintf(msg, msg_len, "ok: %d series, %d tiles (cost %d per chunk), %d CTAs, %lld parts", S, g.ntiles,
+                 g.ktot, g.G, (long long)part_st.size());
+    return HOS_OK;
+}
+
 hos_status hos_get_device_status(const void* ws, int32_t* status) {
     if (!ws || !status) return HOS_ERR_INVALID_ARG;
     int v = 0;
@@ -1345,9 +1608,10 @@ hos_status hos_get_stage_times(float* ms, int32_t max_stages, int32_t* n_stages)
     int n = g_prof_n - 1;
     if (n < 0) n = 0;
     if (n > max_stages) n = max_stages;
+    const cudaEvent_t* ev = g_ev[g_prof_dev];
     for (int i = 0; i < n; ++i) {
-        if (cudaEventSynchronize(g_ev[i + 1]) != cudaSuccess) return HOS_ERR_CUDA;
-        if (cudaEventElapsedTime(&ms[i], g_ev[i], g_ev[i + 1]) != cudaSuccess) return HOS_ERR_CUDA;
+        if (cudaEventSynchronize(ev[i + 1]) != cudaSuccess) return HOS_ERR_CUDA;
+        if (cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]) != cudaSuccess) return HOS_ERR_CUDA;
     }
     *n_stages = n;
     return HOS_OK;

@@ -567,12 +567,9 @@ static cudaError_t launch_adjoint_tc_order(const float* y32, const uint16_t* hi,
     if (e != cudaSuccess) return e;
     AdjTcParams p{y32, 32 + R - 1, hi, lo, gsb, t1p, t2p, n, L, kpad, nb, nut, status, limit_ns};
     const size_t smem = sizeof(AdjSmem);
-    static bool attr = false;
-    if (!attr) {
-        e = cudaFuncSetAttribute(adjoint_tc_kernel<ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // a per-device (per-context) attribute: set on every launch
+    e = cudaFuncSetAttribute(adjoint_tc_kernel<ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     const int64_t items = (int64_t)nb * nut;
     const int grid = (int)(items < G ? items : G);
     adjoint_tc_kernel<ORDER><<<grid, 192, smem, st>>>(p);

@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(256) c3_simt_kernel(const C3SimtParams P) {
     walk.init(geo, P.ser, blockIdx.x, gridDim.x);
     Part part;
     while (walk.next(part)) {
-        const int a = geo.tile_a[part.t], b = geo.tile_b[part.t];
+        const int a = geo.tile_a[part.t], col0 = 32 * geo.tile_c32[part.t];
         const int64_t base = P.ser.pad[part.s];
         const int64_t slen = P.ser.off[part.s + 1] - P.ser.off[part.s];  // rows i >= len: y(i) = 0
         float acc[8][NC];
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256) c3_simt_kernel(const C3SimtParams P) {
             const int64_t i0 = ch * kc;
             const float* ga = P.y32 + base + i0 + (int64_t)a * TILE_M;
             const float* gi = P.y32 + base + geo.L + i0;
-            const float* gb = P.y32 + base + i0 + (int64_t)b * N;
+            const float* gb = P.y32 + base + i0 + col0;  // all N columns (the reduction reads the tile's width)
             __syncthreads();
             for (int t = threadIdx.x; t < kc + TILE_M; t += 256) ya[t] = ga[t];
             for (int t = threadIdx.x; t < kc; t += 256) yi[t] = (i0 + t < slen) ? gi[t] : 0.0f;

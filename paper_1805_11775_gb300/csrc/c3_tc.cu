@@ -7,8 +7,8 @@
 //     Y[w1, i] = y(i) y(i+w1)          (lag-product rows),
 //     X[i, w2] = y(i + w2)             (Hankel matrix of the series).
 //
-// Operands of one tcgen05.mma (M = 128 rows of w1, N = tile_n columns of w2,
-// K = 16 samples for kind::f16, 8 for kind::tf32):
+// Operands of one tcgen05.mma (M = 128 rows of w1, N = the tile's width in
+// columns of w2, at most 256; K = 16 samples for kind::f16, 8 for kind::tf32):
 //   A = Y, built by four "builder" warps in registers and stored straight into
 //       tensor memory (tcgen05.st); the MMA reads A from TMEM, so shared memory
 //       carries only B.
@@ -20,10 +20,11 @@
 //       block (q, n): the unit shift between Hankel rows falls out of the
 //       layout, with LBO (K direction) and SBO (N direction) equal to the byte
 //       distance of the next 8 (resp. 4) samples.
-//   D = FP32 accumulator, 128 lanes x tile_n columns of TMEM.
+//   D = FP32 accumulator, 128 lanes x (widest tile) columns of TMEM.
 //
 // Precision: y = hi + lo (bf16 pair, or tf32 pair); Y is formed in FP32 and
-// split the same way; three products hi*hi + hi*lo + lo*hi per step.
+// split the same way; three products hi*hi + hi*lo + lo*hi per step (plain
+// TF32: hi*hi alone).
 //
 // Warp roles (320 threads, one CTA per SM, persistent, stream-K ranges):
 //   warps 0-3 builders (TMEM lane quadrants 0-3), warps 4-7 epilogue,
@@ -94,7 +95,6 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
     constexpr uint32_t GROUP_BYTES = 16u * R;      // bytes per R-sample group
     constexpr uint32_t LBO = GROUP_BYTES;          // next core matrix along K: +R samples
     constexpr uint32_t SBO = 16u * 8u;             // next 8 rows along N: +8 samples = 128 bytes
-    const uint32_t idesc = make_idesc(TF32, TILE_M, N);
     const int csz = geo.kc;  // samples per chunk (the role loops below count chunks in kc)
     // TMEM columns: accumulators first -- two buffers when the tile is at most
     // 128 wide (the epilogue drains one while the MMAs fill the other), one of
@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
     const uint32_t acc_cols = (N <= 64) ? 64u : 128u;  // column stride between accumulators
     const uint32_t a_base = (N <= 64) ? 128u : 256u;   // first A stage column
     const int nst = (N <= 64) ? 6 : 4;                 // A stages
+    const bool split = P.products != 1;                // plain TF32 issues hi*hi only
 
     if (threadIdx.x == 0) {
         // one elected arrival per arriving warp
@@ -145,7 +146,8 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
         uint32_t kc = 0, tph = 0;
         bool ok = true;
         while (ok && walk.next(part)) {
-            const int a = geo.tile_a[part.t], b = geo.tile_b[part.t];
+            const int a = geo.tile_a[part.t];
+            const int col0 = 32 * geo.tile_c32[part.t], wt = 32 * geo.tile_w32[part.t];  // this tile's columns
             const int64_t base = P.ser.pad[part.s];
             // rows i >= len carry y(i) = 0 (a time slice keeps its neighbour's
             // samples after it in the plane, for the lags only)
@@ -155,12 +157,12 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                 ok = warp_wait(&sm.empty_b[buf], ((kc >> 1) & 1) ^ 1, abort, P.status, lim, 2000);
                 if (!ok) break;
                 const int64_t i0 = c * csz;
-                const int64_t wb = base + i0 + (int64_t)b * N;            // plane index of window start
+                const int64_t wb = base + i0 + col0;                     // plane index of window start
                 // A window: y(i0 + w1_0 + t) for ORDER 3; y(i0 - L + t) for ORDER 4
                 const int64_t ab = (ORDER == 3) ? base + i0 + (int64_t)a * TILE_M : base + i0;
                 const int64_t ib = base + L + i0;                          // y(i0)
                 const int64_t ib_al = ib & ~(int64_t)3;
-                const uint32_t wbytes = (uint32_t)(csz + N + 16) * ELT;
+                const uint32_t wbytes = (uint32_t)(csz + wt + 16) * ELT;
                 if (lane == 0) {
                     const uint32_t yab = (uint32_t)(csz + TILE_M) * 4, yib = (uint32_t)(csz + 4) * 4;
                     mbar_expect_tx(&sm.tma_bar, 2 * wbytes + yab + yib);
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                     }
                 }
                 // interleave: block (q, r) <- samples [R q + r, R q + r + R)
-                const int ngroups = (csz + N) / R + 2;
+                const int ngroups = (csz + wt) / R + 2;
                 const int nblocks = ngroups * R;
                 for (int blk = lane; blk < nblocks; blk += 32) {
                     const int q = blk / R, r = blk % R;
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                     }
                     const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + a_base + (uint32_t)st * 64u;
                     tmem_st32(ta, H);
-                    tmem_st32(ta + 32u, Lw);
+                    if (split) tmem_st32(ta + 32u, Lw);
                     tmem_wait_st();
                     tc_fence_before();
                     __syncwarp();
@@ -360,7 +362,8 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
             if (!ok) break;
             tc_fence_after();
             float* dst = P.partials + part.slot * (int64_t)(TILE_M * N) + m;
-            for (int cc = 0; cc < N; cc += 32) {
+            const int wt = 32 * geo.tile_w32[part.t];
+            for (int cc = 0; cc < wt; cc += 32) {
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + ab_ * acc_cols + (uint32_t)cc, v);
                 tmem_wait_ld();
@@ -380,6 +383,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
         while (ok && walk.next(part)) {
             const uint32_t ab_ = it % nacc;
             const uint32_t dacc = tmem + ab_ * acc_cols;  // this part's accumulator
+            const uint32_t idesc = make_idesc(TF32, TILE_M, 32 * geo.tile_w32[part.t]);  // N = the tile's width
             ok = mbar_wait(&sm.acc_empty[ab_], ((it / nacc) & 1) ^ 1, abort, P.status, lim);
             if (!ok) break;
             tc_fence_after();
@@ -409,8 +413,10 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                         const uint64_t bl = bl0 + boff16;
                         mma_ts<TF32>(dacc, a_hi, bh, idesc, acc);
                         acc = 1;
-                        mma_ts<TF32>(dacc, a_hi, bl, idesc, 1);
-                        mma_ts<TF32>(dacc, a_lo, bh, idesc, 1);
+                        if (split) {
+                            mma_ts<TF32>(dacc, a_hi, bl, idesc, 1);
+                            mma_ts<TF32>(dacc, a_lo, bh, idesc, 1);
+                        }
                     }
                     mma_commit(&sm.empty_a[st]);
                 }
@@ -445,13 +451,11 @@ static cudaError_t launch_one(const C3TcParams& p, int G, cudaStream_t st) {
     // at least 116 KB so that exactly one CTA (and one 512-column TMEM
     // allocation) lands on each SM
     const size_t smem = sizeof(C3Smem) > 118784 ? sizeof(C3Smem) : 118784;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e =
-            cudaFuncSetAttribute(c3_tc_kernel<TF32, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    // The attribute belongs to the current device (and context): set it on
+    // every launch, so that any device the caller switches to has it.
+    cudaError_t e =
+        cudaFuncSetAttribute(c3_tc_kernel<TF32, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     c3_tc_kernel<TF32, ORDER><<<G, 320, smem, st>>>(p);
     count_launch();
     return cudaGetLastError();

@@ -17,47 +17,54 @@ namespace hos {
 // ---------------------------------------------------------------------------
 // Geometry of the c3 contraction.
 //
-// The lag square [-L, L-1]^2 is cut into tiles of TILE_M (=128) rows (w1) by
-// tile_n columns (w2).  Row m of tile row a is w1 = -L + 128a + m; column j of
-// tile column b is w2 = -L + b*tile_n + j.  Because c3(w1,w2) = c3(w2,w1),
-// a tile whose every w1 exceeds every w2 is not computed; its values are read
-// from the mirrored tile by the reduction.
+// The lag square [-L, L-1]^2 (lag index i = w1 + L, j = w2 + L) is cut into
+// row blocks of TILE_M (=128) lags w1.  Because c3(w1,w2) = c3(w2,w1), row
+// block a computes only the columns j >= row_c0[a] = 128a (from its own
+// diagonal block on); the reduction fills the rest from the mirror.  Each row
+// block's column range is cut into tiles of at most tile_n (the widest, 256)
+// columns; the last tile of a row is narrower (a multiple of 32 columns).  At
+// L = 256 the four row blocks have 512, 384, 256 and 128 columns: 1280 columns
+// of 128 rows against the 1536 of whole 256-wide tiles.
 //
-// Work unit = (series, tile, chunk of KC samples of the time index i).
-// Units are ordered series-major, then tile, then chunk.  The G persistent
-// CTAs take contiguous, equal ranges of units (stream-K).  Within a range,
-// a CTA accumulates consecutive chunks of one (series, tile) in FP32, at most
-// `flush` chunks, then writes one FP32 partial tile ("part") to a slot.
+// Work unit = (series, tile, chunk of kc samples of the time index i), ordered
+// series-major, then tile, then chunk.  A unit's cost is its tile's width in
+// 32-column steps (tile_w32), the MMA work it carries.  The G persistent CTAs
+// take contiguous, equal ranges of the cost axis (stream-K weighted by cost):
+// CTA g runs the units whose cost interval starts inside its range.  Within a
+// range, a CTA accumulates consecutive chunks of one (series, tile) in FP32, at
+// most `flush` chunks, then writes one FP32 partial tile ("part") to a slot.
 // Slots: one per (series, tile, flush-window) -- the part that starts at the
 // window's first chunk -- plus one per CTA for a part that starts at the
-// CTA's first unit inside a window.  The FP64 reduction sums, in a fixed
+// CTA's first unit inside a window.  The FP64-class reduction sums, in a fixed
 // order, the main slot and the CTA slots of every window.
 // ---------------------------------------------------------------------------
 constexpr int TILE_M = 128;
 constexpr int KC = 1024;         // most samples per chunk (shared-memory sizing); plans use geo.kc <= KC
 constexpr int MAX_TILES_M = 16;  // L <= 1024
-constexpr int MAX_TILES_N = 16;
+constexpr int MAX_TILES = 256;   // tiles of one plan
 
 struct C3Geom {
     int L;
     int kc;         // samples per chunk (multiple of 64, <= KC)
-    int tile_n;     // 16..256, power of two
-    int tiles_m;    // ceil(2L / 128)
-    int tiles_n;    // ceil(2L / tile_n)
-    int ntiles;     // tiles computed (after the symmetric skip)
+    int tile_n;     // widest tile, 32..256, power of two (the TMEM accumulator width)
+    int tiles_m;    // row blocks: ceil(2L / 128)
+    int ntiles;     // tiles computed (after the symmetric and zero-window skips)
+    int ktot;       // cost of one chunk of every tile: sum of tile_w32
     int flush;      // chunks per flush window
     int G;          // CTAs of the contraction
     int pad_tail;   // zero samples after the last chunk of a series
-    int8_t tile_idx[MAX_TILES_M][MAX_TILES_N];  // computed-tile index or -1
-    uint8_t tile_a[MAX_TILES_M * MAX_TILES_N];
-    uint8_t tile_b[MAX_TILES_M * MAX_TILES_N];
+    uint16_t row_c0[MAX_TILES_M];    // first column (lag index) computed in row block a
+    uint8_t tile_a[MAX_TILES];       // row block of tile t
+    uint8_t tile_c32[MAX_TILES];     // first column of tile t / 32
+    uint8_t tile_w32[MAX_TILES];     // width of tile t / 32 (cost of one of its chunks)
+    uint16_t tile_kpre[MAX_TILES + 1];  // sum of tile_w32 over the tiles before t
 };
 
 // Per-series layout produced on the device by the plan kernel.
 //   off[S+1]  : input offsets
 //   pad[S+1]  : start of each series' zero-padded block in the sample planes;
 //               sample i of series s sits at pad[s] + L + i
-//   unit[S+1] : prefix of work units  (ntiles * nchunks(s))
+//   unit[S+1] : prefix of work-unit cost  (ktot * nchunks(s))
 //   win[S+1]  : prefix of flush windows (ntiles * ceil(nchunks(s) / flush))
 //   mean[S]   : FP64 mean removed from each series
 struct SeriesView {
@@ -72,10 +79,25 @@ struct SeriesView {
 HOS_HD int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 HOS_HD int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
-// first unit of CTA g (ranges [range_begin(g), range_begin(g+1)))
+// first cost position of CTA g (ranges [range_begin(g), range_begin(g+1)))
 HOS_HD int64_t range_begin(int64_t g, int64_t U, int64_t G) { return (g * U) / G; }
 
-// Deterministic walk of one CTA's unit range, split into parts at (series,
+// One series' share of the plan: its padded block length in the sample
+// planes (L zeros, the chunks, pad_tail zeros, rounded to 64 samples), the
+// cost of its work units and its flush windows over all tiles.
+struct SeriesPlan {
+    int64_t plen, cost, wins;
+};
+HOS_HD SeriesPlan series_plan(int64_t len, int L, int ntiles, int ktot, int flush, int kc, int pad_tail) {
+    const int64_t nch = ceil_div(len, kc);
+    SeriesPlan r;
+    r.plen = round_up((int64_t)L + nch * kc + pad_tail, 64);
+    r.cost = (int64_t)ktot * nch;
+    r.wins = (int64_t)ntiles * ceil_div(nch, flush);
+    return r;
+}
+
+// Deterministic walk of one CTA's cost range, split into parts at (series,
 // tile) boundaries and at flush-window boundaries.
 struct Part {
     int s;           // series
@@ -85,21 +107,23 @@ struct Part {
 };
 
 struct Walk {
-    int64_t u, ue, U, total_win;
+    int64_t u, ue, U, total_win;  // u: cost position from which the next unit may start
     int s, S, g;
     int flush, ntiles, kc;
     const int64_t* unit;
     const int64_t* win;
     const int64_t* off;
+    const C3Geom* geo;
 
-    HOS_DEV void init(const C3Geom& geo, const SeriesView& sv, int gidx, int G) {
+    HOS_HD void init(const C3Geom& geom, const SeriesView& sv, int gidx, int G) {
+        geo = &geom;
         S = sv.S;
         unit = sv.unit;
         win = sv.win;
         off = sv.off;
-        flush = geo.flush;
-        ntiles = geo.ntiles;
-        kc = geo.kc;
+        flush = geom.flush;
+        ntiles = geom.ntiles;
+        kc = geom.kc;
         g = gidx;
         U = unit[S];
         total_win = win[S];
@@ -113,26 +137,37 @@ struct Walk {
         }
         s = lo;
     }
-    HOS_DEV bool next(Part& p) {
-        if (u >= ue) return false;
-        while (s < S - 1 && unit[s + 1] <= u) ++s;
-        const int64_t len = off[s + 1] - off[s];
-        const int64_t nch = ceil_div(len, kc);
-        const int64_t r = u - unit[s];
-        const int t = (int)(r / nch);
-        const int64_t c = r % nch;
-        const int64_t f = c / flush;
-        const int64_t wend = ((f + 1) * flush < nch) ? (f + 1) * flush : nch;
-        int64_t take = wend - c;
-        if (ue - u < take) take = ue - u;
-        const int64_t nwin = ceil_div(nch, flush);
-        p.s = s;
-        p.t = t;
-        p.c0 = c;
-        p.c1 = c + take;
-        p.slot = (c % flush == 0) ? (win[s] + (int64_t)t * nwin + f) : (total_win + g);
-        u += take;
-        return true;
+    HOS_HD bool next(Part& p) {
+        for (;;) {
+            if (u >= ue) return false;
+            while (s < S - 1 && unit[s + 1] <= u) ++s;
+            if (u >= unit[s + 1]) return false;  // past the last unit
+            const int64_t len = off[s + 1] - off[s];
+            const int64_t nch = ceil_div(len, kc);
+            const int64_t r = u - unit[s];
+            int t = 0;  // last tile whose cost range starts at or before r
+            while (t + 1 < ntiles && nch * geo->tile_kpre[t + 1] <= r) ++t;
+            const int64_t k = geo->tile_w32[t];
+            const int64_t tb = unit[s] + nch * geo->tile_kpre[t];  // cost start of (s, t)
+            const int64_t c = ceil_div(u - tb, k);                 // first chunk starting at or after u
+            if (c >= nch) {  // u inside the tile's last chunk: go on at the next tile
+                u = tb + nch * k;
+                continue;
+            }
+            if (tb + c * k >= ue) return false;
+            const int64_t f = c / flush;
+            const int64_t wend = ((f + 1) * flush < nch) ? (f + 1) * flush : nch;
+            const int64_t cap = ceil_div(ue - tb, k);  // chunks of this tile starting before ue
+            const int64_t c1 = wend < cap ? wend : cap;
+            const int64_t nwin = ceil_div(nch, flush);
+            p.s = s;
+            p.t = t;
+            p.c0 = c;
+            p.c1 = c1;
+            p.slot = (c % flush == 0) ? (win[s] + (int64_t)t * nwin + f) : (total_win + g);
+            u = tb + c1 * k;
+            return true;
+        }
     }
 };
 

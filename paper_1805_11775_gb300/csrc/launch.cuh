@@ -16,6 +16,7 @@ struct C3TcParams {
     float* partials;
     int* status;
     uint64_t limit_ns;
+    int products;  // 3: hi*hi + hi*lo + lo*hi (split precision); 1: hi*hi (plain TF32)
 };
 
 struct C3SimtParams {
@@ -30,12 +31,49 @@ struct C3SimtParams {
 // Where the parts of one (series, computed tile) live (reduce.cu).
 struct TileRec {
     int64_t slot;   // first main slot: one per flush window, contiguous
-    int64_t ub;     // first work unit of (series, tile)
+    int64_t ub;     // cost position where (series, tile) starts
     int32_t nwin;   // main slots
-    int32_t xlo;    // CTAs [xlo, xhi) start inside (series, tile)
+    int32_t xlo;    // CTAs [xlo, xhi) whose first unit lies inside (series, tile), after its first
     int32_t xhi;
-    int32_t pad;
+    int32_t k;      // cost of one chunk of the tile (its width / 32)
 };
+
+// The record of (series s, computed tile t), from the CTAs' first cost
+// positions bnd[0..G] (shared by the reduction and the host plan check).
+HOS_HD TileRec tile_record(const C3Geom& geo, const SeriesView& sv, const int64_t* bnd, int s, int t) {
+    const int64_t len = sv.off[s + 1] - sv.off[s];
+    const int64_t nch = ceil_div(len, geo.kc), nwin = ceil_div(nch, geo.flush);
+    const int64_t k = geo.tile_w32[t];
+    const int64_t ub = sv.unit[s] + nch * geo.tile_kpre[t];
+    const int64_t last = ub + (nch - 1) * k;  // cost start of the tile's last chunk
+    int lo = 0, hi = geo.G;  // first CTA starting after ub
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (bnd[mid] > ub) hi = mid; else lo = mid + 1;
+    }
+    int e = lo, eh = geo.G;  // first CTA from lo on whose first unit is past this tile (G if none)
+    while (e < eh) {
+        const int mid = (e + eh) >> 1;
+        if (bnd[mid] > last) eh = mid; else e = mid + 1;
+    }
+    TileRec r;
+    r.slot = sv.win[s] + (int64_t)t * nwin;
+    r.ub = ub;
+    r.nwin = (int)nwin;
+    r.xlo = lo;
+    r.xhi = nch > 0 ? e : lo;
+    r.k = (int32_t)k;
+    return r;
+}
+
+// Whether CTA g (xlo <= g < xhi) wrote a part of this (series, tile) to its
+// own slot: its first chunk there, ceil((bnd[g] - ub) / k), starts mid flush
+// window and inside the CTA's range.
+HOS_HD bool cta_slot_used(const TileRec& r, const int64_t* bnd, int g, int flush) {
+    if (g < r.xlo || g >= r.xhi) return false;
+    const int64_t c = ceil_div(bnd[g] - r.ub, r.k);
+    return c % flush != 0 && r.ub + c * r.k < bnd[g + 1];
+}
 
 struct Reduce3Params {
     C3Geom geom;
@@ -78,9 +116,13 @@ constexpr int C4_PAIRS_PER_CTA = 128;
 constexpr int C4_CHUNK_GROUP = 4;  // 1024-sample chunks per FP32 partial
 
 void count_launch();
+// Identifier of the current CUDA context (changes when a device is reset), or 0
+// when no context is current or the driver cannot say (abi.cu).
+uint64_t current_context_id();
 
+// ktot: cost of one chunk over all tiles (the contraction's C3Geom::ktot)
 cudaError_t launch_plan_series(int mode, int64_t n, int64_t seg, const int64_t* d_user_off, int S, int L, int ntiles,
-                               int flush, int kc, int pad_tail, int64_t* off, int64_t* pad, int64_t* unit,
+                               int ktot, int flush, int kc, int pad_tail, int64_t* off, int64_t* pad, int64_t* unit,
                                int64_t* win, cudaStream_t st);
 // remove_mean < 0: write each series' plain FP64 sum instead of its mean
 cudaError_t launch_mean(const void* x, int dtype, const int64_t* off, int S, int nslices, double* part,

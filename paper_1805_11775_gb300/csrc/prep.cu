@@ -30,8 +30,8 @@ __device__ int64_t block_exclusive_scan(int64_t v, int64_t* sh, int64_t* total) 
 // mode 0: single series of n samples cut into parts of seg (seg <= 0: one part)
 // mode 1: S series given by device offsets d_user_off[S+1]
 __global__ void plan_series_kernel(int mode, int64_t n, int64_t seg, const int64_t* __restrict__ d_user_off, int S,
-                                   int L, int ntiles, int flush, int kc, int pad_tail, int64_t* off, int64_t* pad,
-                                   int64_t* unit, int64_t* win) {
+                                   int L, int ntiles, int ktot, int flush, int kc, int pad_tail, int64_t* off,
+                                   int64_t* pad, int64_t* unit, int64_t* win) {
     __shared__ int64_t sh[1024];
     __shared__ int64_t carry[3];
     if (threadIdx.x == 0) carry[0] = carry[1] = carry[2] = 0;
@@ -49,10 +49,10 @@ __global__ void plan_series_kernel(int mode, int64_t n, int64_t seg, const int64
             }
         }
         const int64_t len = (s < S && o1 > o0) ? (o1 - o0) : 0;
-        const int64_t nch = ceil_div(len, kc);
-        const int64_t plen = (s < S) ? round_up((int64_t)L + nch * kc + pad_tail, 64) : 0;
-        const int64_t nu = (int64_t)ntiles * nch;
-        const int64_t nw = (int64_t)ntiles * ceil_div(nch, flush);
+        const SeriesPlan sp = series_plan(len, L, ntiles, ktot, flush, kc, pad_tail);
+        const int64_t plen = (s < S) ? sp.plen : 0;
+        const int64_t nu = sp.cost;  // cost of the series' units
+        const int64_t nw = sp.wins;
         int64_t tot;
         const int64_t ep = block_exclusive_scan(plen, sh, &tot);
         const int64_t c0 = carry[0];
@@ -201,12 +201,12 @@ __global__ void planes_kernel(const T* __restrict__ x, const int64_t* __restrict
 }
 
 cudaError_t launch_plan_series(int mode, int64_t n, int64_t seg, const int64_t* d_user_off, int S, int L, int ntiles,
-                               int flush, int kc, int pad_tail, int64_t* off, int64_t* pad, int64_t* unit,
+                               int ktot, int flush, int kc, int pad_tail, int64_t* off, int64_t* pad, int64_t* unit,
                                int64_t* win, cudaStream_t st) {
     int threads = 32;  // one block; its scans take log2(threads) steps
     while (threads < S && threads < 1024) threads <<= 1;
-    plan_series_kernel<<<1, threads, 0, st>>>(mode, n, seg, d_user_off, S, L, ntiles, flush, kc, pad_tail, off, pad,
-                                              unit, win);
+    plan_series_kernel<<<1, threads, 0, st>>>(mode, n, seg, d_user_off, S, L, ntiles, ktot, flush, kc, pad_tail, off,
+                                              pad, unit, win);
     count_launch();
     return cudaGetLastError();
 }

@@ -16,11 +16,13 @@ constexpr int REDUCE_THREADS = 256;
 
 // For every (series s, computed tile t) a record of where its parts are:
 // the main slots (one per flush window, contiguous, in chunk order) and the
-// CTAs whose unit range starts strictly inside the (s, t) unit range,
-// [xlo, xhi) -- those CTAs' first parts, when they begin mid flush-window,
-// live in per-CTA slots.  Also 1/n of each series' time average.
-// bnd (G + 1 values) is staged in shared memory once per block; both CTA
-// searches are binary searches there.
+// CTAs whose first unit lies inside (s, t) after its first chunk, [xlo, xhi)
+// -- those CTAs' first parts, when they begin mid flush-window, live in
+// per-CTA slots.  (s, t) covers the cost range [ub, ub + nch k); CTA g's
+// first unit is the first chunk starting at or after bnd[g]: chunk
+// ceil((bnd[g] - ub) / k), inside the tile when bnd[g] <= ub + (nch - 1) k.
+// Also 1/n of each series' time average.  bnd (G + 1 values) is staged in
+// shared memory once per block; both CTA searches are binary searches there.
 __global__ void part_ranges_kernel(const C3Geom geo, const SeriesView sv, const int64_t* __restrict__ bnd_g,
                                    TileRec* __restrict__ rec, float2* __restrict__ inv_len, int64_t norm_len) {
     extern __shared__ int64_t bnd[];
@@ -29,26 +31,8 @@ __global__ void part_ranges_kernel(const C3Geom geo, const SeriesView sv, const 
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= (int64_t)sv.S * geo.ntiles) return;
     const int s = (int)(q / geo.ntiles), t = (int)(q % geo.ntiles);
+    const TileRec r = tile_record(geo, sv, bnd, s, t);
     const int64_t len = sv.off[s + 1] - sv.off[s];
-    const int64_t nch = ceil_div(len, geo.kc), nwin = ceil_div(nch, geo.flush);
-    const int64_t ub = sv.unit[s] + (int64_t)t * nch, ue = ub + nch;
-    int lo = 0, hi = geo.G;  // first CTA starting after ub
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (bnd[mid] > ub) hi = mid; else lo = mid + 1;
-    }
-    int e = lo, eh = geo.G;  // first CTA from lo on starting at or after ue (G if none)
-    while (e < eh) {
-        const int mid = (e + eh) >> 1;
-        if (bnd[mid] >= ue) eh = mid; else e = mid + 1;
-    }
-    TileRec r;
-    r.slot = sv.win[s] + (int64_t)t * nwin;
-    r.ub = ub;
-    r.nwin = (int)nwin;
-    r.xlo = lo;
-    r.xhi = e;
-    r.pad = 0;
     rec[q] = r;
     // 1/n of the time average: the series' own length, or (a time slice of a
     // longer series) that series' length
@@ -150,7 +134,7 @@ HOS_DEV void tile_share4(const float* __restrict__ partials, const TileRec& r, i
 #pragma unroll
         for (int u = 0; u < XB; ++u) {
             const int g = g0 + u * gsplit;
-            const bool use = g < r.xhi && (int)(bnd[g] - r.ub) % F != 0 && bnd[g] < bnd[g + 1];
+            const bool use = cta_slot_used(r, bnd, g, F);
             x[u] = use ? reinterpret_cast<const float4*>(partials + (total_win + g) * (int64_t)tsz)[vi]
                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
@@ -193,13 +177,14 @@ HOS_DEV void combine_rows4(DF (&v)[4], int ei, int gi, int es, int gsplit, float
 HOS_DEV void emit_c3x4(const Reduce3Params& P, const float* __restrict__ wtab, int grp, int t, int elem0,
                        const DF (&v)[4]) {
     const C3Geom& geo = P.geom;
-    const int L = geo.L, N = geo.tile_n;
+    const int L = geo.L;
     const int m0 = elem0 & (TILE_M - 1), j = elem0 >> 7;
-    const int w10 = -L + TILE_M * geo.tile_a[t] + m0, w2 = -L + N * geo.tile_b[t] + j;
+    const int w10 = -L + TILE_M * geo.tile_a[t] + m0, w2 = -L + 32 * geo.tile_c32[t] + j;
     if (w10 >= L || w2 >= L) return;
     const int twoL = 2 * L, Nf = P.nfft;
-    const int ma = (w2 + L) / TILE_M, mb = (w10 + L) / N;  // the same for the four (N is a multiple of 4)
-    const bool write_mirror = geo.tile_idx[ma][mb] < 0;
+    // (w2, w1) is computed when column w1 + L lies in row block (w2 + L) / 128's
+    // range; the same for the four (row_c0 is a multiple of 32)
+    const bool write_mirror = w10 + L < (int)geo.row_c0[(w2 + L) / TILE_M];
     if (P.mode == 1) {
         double* o = P.c3out + (int64_t)grp * twoL * twoL;
 #pragma unroll
@@ -267,7 +252,8 @@ __global__ void __launch_bounds__(REDUCE_THREADS, BATCH >= 16 ? 2 : 3) reduce3_k
     const C3Geom& geo = P.geom;
     const SeriesView& sv = P.ser;
     const int t = blockIdx.y, grp = blockIdx.z;
-    const int tsz = TILE_M * geo.tile_n, nvec = tsz >> 2;
+    // slots hold 128 x tile_n floats; this tile's 128 x width of them are live
+    const int tsz = TILE_M * geo.tile_n, nvec = TILE_M * 32 * geo.tile_w32[t] >> 2;
     const int es = REDUCE_THREADS / gsplit, ei = threadIdx.x % es, gi = threadIdx.x / es;
     const int s0 = P.per_series_groups ? grp : 0, s1 = P.per_series_groups ? grp + 1 : sv.S;
     const int64_t total_win = sv.win[sv.S];
@@ -375,7 +361,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce3_single_kernel(const Re
                                                                         const float* __restrict__ wtab) {
     const C3Geom& geo = P.geom;
     const int t = blockIdx.y, grp = blockIdx.z;
-    const int tsz = TILE_M * geo.tile_n, nvec = tsz >> 2;
+    const int tsz = TILE_M * geo.tile_n, nvec = TILE_M * 32 * geo.tile_w32[t] >> 2;
     const TileRec r = rec[(int64_t)grp * geo.ntiles + t];
     if (!(r.nwin == 1 && r.xlo >= r.xhi)) return;  // uniform over the block
     const float2 il = inv_len[grp];

@@ -67,7 +67,7 @@ def test_invalid_arguments_return_synchronously(lib):
     assert lib.hos_bispectrum(None, 1, 100, ctypes.byref(p), dummy, dummy, 1 << 20, None) == 1
     assert lib.hos_bispectrum(dummy, 7, 100, ctypes.byref(p), dummy, dummy, 1 << 20, None) == 1
     assert lib.hos_bispectrum(dummy, 1, 0, ctypes.byref(p), dummy, dummy, 1 << 20, None) == 1
-    for bad in (dict(L=0), dict(L=32, nfft=10), dict(L=32, precision=9), dict(L=32, window=5),
+    for bad in (dict(L=0), dict(L=32, nfft=10), dict(L=32, precision=4), dict(L=32, precision=-1), dict(L=32, window=5),
                 dict(L=32, tile_n=48), dict(L=32, segment_len=-1)):
         q = _params(**bad)
         assert lib.hos_bispectrum(dummy, 1, 100, ctypes.byref(q), dummy, dummy, 1 << 20, None) == 1, bad
@@ -117,7 +117,8 @@ def test_trispectrum_backward_workspace_and_limits(lib):
     assert a > 32 * n * 4 + 64 ** 3 * 8
     b = workspace_size(_native.OP_TRISPECTRUM_BACKWARD, n, 1, n, _params(L=64, precision=1))
     assert b > a
-    for bad in (_params(L=32, precision=0), _params(L=32, precision=2), _params(L=65, precision=1),
+    for bad in (_params(L=32, precision="fp32"), _params(L=32, precision="tf32"), _params(L=32, precision="simt"),
+                _params(L=65, precision=1),
                 _params(L=32, precision=1, window=1), _params(L=32, precision=1, segment_len=1000)):
         with pytest.raises(HosError):
             workspace_size(_native.OP_TRISPECTRUM_BACKWARD, n, 1, n, bad)
@@ -157,8 +158,9 @@ def test_fourth_order_slice_checks(lib):
     assert a > 0
     f = workspace_size(_native.OP_TRISPECTRUM_FROM_MOMENTS, 0, 1, 0, _params(L=32, precision=1))
     assert f >= 64 ** 3 * 4
+    assert workspace_size(_native.OP_MOMENTS4_SLICE, 50_000, 1, 50_000, _params(L=32, precision="tf32")) > 0
     with pytest.raises(HosError):
-        workspace_size(_native.OP_MOMENTS4_SLICE, 50_000, 1, 50_000, _params(L=32, precision=2))
+        workspace_size(_native.OP_MOMENTS4_SLICE, 50_000, 1, 50_000, _params(L=32, precision="simt"))
     with pytest.raises(HosError):
         workspace_size(_native.OP_MOMENTS4_SLICE, 50_000, 1, 50_000, _params(L=65, precision=1))
     dummy = ctypes.c_void_p(16)

@@ -1,0 +1,109 @@
+"""Host mirror of the contraction plans (no GPU): hos_check_plan runs, on the
+CPU and with the code the kernels use, the series layout, every CTA's walk
+over the cost-weighted stream-K split, the slots the partial tiles go to, the
+reduction's reading of those slots, and the bounds and 16-byte alignment of
+every bulk copy.  A plan passes when every (series, tile, chunk) is run
+exactly once, every partial is read exactly once from its own (series, tile),
+and no copy leaves its series' zero-padded block."""
+import ctypes
+import os
+import shutil
+
+import numpy as np
+import pytest
+
+import hos_synth
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                                reason="nvcc not available")
+
+OP_BISPECTRUM, OP_TRISPECTRUM, OP_BATCHED = 0, 1, 2
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1805_11775_gb300 import build, _native
+    build.build()
+    return _native.lib()
+
+
+def check(lib, op, n, p, ctas, offsets=None):
+    msg = ctypes.create_string_buffer(512)
+    if offsets is not None:
+        offs = np.ascontiguousarray(offsets, dtype=np.int64)
+        rc = lib.hos_check_plan(op, int(offs[-1]), offs.size - 1, offs.ctypes.data, ctypes.byref(p), ctas, msg, 512)
+    else:
+        rc = lib.hos_check_plan(op, n, 1, None, ctypes.byref(p), ctas, msg, 512)
+    return rc, msg.value.decode()
+
+
+def test_workload_plans(lib):
+    from paper_1805_11775_gb300 import make_params
+    for prec in ("bf16", "fp32", "tf32", "simt"):
+        ctas = 608 if prec == "simt" else 152
+        for n, L in ((2048, 32), (1 << 21, 256), (1 << 18, 128)):
+            rc, m = check(lib, OP_BISPECTRUM, n, make_params(L, precision=prec), ctas)
+            assert rc == 0, (prec, n, L, m)
+    w = hos_synth.workload("batched_4096x_L128")
+    for prec in ("bf16", "fp32"):
+        rc, m = check(lib, OP_BATCHED, 0, make_params(128, precision=prec), 152, w["offsets"])
+        assert rc == 0, (prec, m)
+    for prec in ("bf16", "fp32", "tf32"):
+        rc, m = check(lib, OP_TRISPECTRUM, 65536, make_params(32, precision=prec), 152)
+        assert rc == 0, (prec, m)
+
+
+def test_long_plan_has_diagonal_start_tiles(lib):
+    """L = 256: row blocks of 512, 384, 256 and 128 columns -> four 256-wide
+    and two 128-wide tiles, cost 40 per chunk (1280 columns / 32)."""
+    from paper_1805_11775_gb300 import make_params
+    rc, m = check(lib, OP_BISPECTRUM, 1 << 21, make_params(256), 152)
+    assert rc == 0 and "6 tiles (cost 40 per chunk)" in m, m
+    rc, m = check(lib, OP_BISPECTRUM, 1 << 18, make_params(128), 152)
+    assert rc == 0 and "2 tiles (cost 12 per chunk)" in m, m
+
+
+def test_random_single_series_plans(lib):
+    from paper_1805_11775_gb300 import make_params
+    rng = np.random.default_rng(7)
+    for _ in range(300):
+        L = int(rng.choice([1, 2, 3, 5, 16, 31, 32, 40, 64, 100, 127, 128, 129, 200, 256, 300, 512, 700, 1024]))
+        n = int(rng.choice([1, 2, 100, 1023, 1024, 1025, 5000, 40000, 300000]))
+        prec = str(rng.choice(["bf16", "fp32", "tf32", "simt"]))
+        tile = int(rng.choice([0, 0, 32, 64, 128, 256]))
+        flush = int(rng.choice([0, 0, 1, 3, 16, 33]))
+        win = str(rng.choice(["parzen", "parzen_sym", "rect"]))
+        seg = int(rng.choice([0, 0, 0, 700, 4096]))
+        ctas = int(rng.choice([1, 2, 7, 148, 152, 608]))
+        p = make_params(L, precision=prec, tile_n=tile, flush_chunks=flush, window=win, segment_len=seg)
+        rc, m = check(lib, OP_BISPECTRUM, n, p, ctas)
+        assert rc == 0, (L, n, prec, tile, flush, win, seg, ctas, m)
+
+
+def test_random_batched_plans(lib):
+    from paper_1805_11775_gb300 import make_params
+    rng = np.random.default_rng(11)
+    for _ in range(60):
+        S = int(rng.integers(1, 300))
+        lens = rng.integers(0, 6000, S)
+        lens[rng.random(S) < 0.2] = 0  # empty series
+        offs = np.concatenate([[0], np.cumsum(lens)])
+        L = int(rng.choice([4, 32, 64, 100, 128, 256]))
+        prec = str(rng.choice(["bf16", "fp32", "tf32", "simt"]))
+        ctas = int(rng.choice([1, 5, 152, 608]))
+        p = make_params(L, precision=prec, flush_chunks=int(rng.choice([0, 1, 2, 16])))
+        rc, m = check(lib, OP_BATCHED, 0, p, ctas, offs)
+        assert rc == 0, (S, L, prec, ctas, m)
+
+
+def test_random_fourth_order_plans(lib):
+    from paper_1805_11775_gb300 import make_params
+    rng = np.random.default_rng(13)
+    for _ in range(80):
+        L = int(rng.choice([1, 2, 4, 8, 16, 20, 32, 64]))
+        n = int(rng.choice([1, 50, 1000, 4096, 65536, 100001]))
+        prec = str(rng.choice(["bf16", "fp32", "tf32"]))
+        seg = int(rng.choice([0, 0, 1500]))
+        ctas = int(rng.choice([1, 3, 152]))
+        rc, m = check(lib, OP_TRISPECTRUM, n, make_params(L, precision=prec, segment_len=seg), ctas)
+        assert rc == 0, (L, n, prec, seg, ctas, m)
