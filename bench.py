@@ -199,15 +199,27 @@ def principal_mask(N):
     return (k2 <= k1) & (k1 + k2 < N // 2)
 
 
-def c3_tc_flops(L, lens, products):
-    """Executed tensor-core flops of the c3 contraction: computed tiles x 128
-    rows x tile_n columns x padded samples x products x 2."""
-    tile_n = min(256, max(32, 1 << (2 * L - 1).bit_length()))
-    tiles_m, tiles_n = math.ceil(2 * L / 128), math.ceil(2 * L / tile_n)
-    ntiles = sum(1 for b in range(tiles_n) for a in range(tiles_m) if not (a * 128 >= b * tile_n + tile_n))
-    kpad = sum(math.ceil(int(n) / 1024) * 1024 for n in lens)
-    return ntiles * 128 * tile_n * kpad * products * 2, (
-        f"{ntiles} tiles x 128 x {tile_n} x {kpad} padded samples x {products} products x 2 flops")
+def plan_fields(plan):
+    """{'tile_n': .., 'tiles': .., 'cols': .., 'kc': ..} from hos_last_plan's text."""
+    out = {}
+    for tok in plan.split():
+        if "=" in tok:
+            k, v = tok.split("=", 1)
+            if v.isdigit():
+                out[k] = int(v)
+    return out
+
+
+def c3_tc_flops(lens, products, plan):
+    """Executed tensor-core flops of the c3 contraction from the plan the call
+    ran: 128 rows x the tiles' columns added up x padded samples x products x 2
+    (rows from each 128-row block's diagonal block on)."""
+    f = plan_fields(plan)
+    kc = f.get("kc", 1024)
+    kpad = sum(math.ceil(int(n) / kc) * kc for n in lens)
+    return 128 * f["cols"] * kpad * products * 2, (
+        f"{f['tiles']} tiles x 128 rows, {f['cols']} columns in all x {kpad} padded samples x {products} products"
+        f" x 2 flops")
 
 
 def m4_flops(L, n, prec):
@@ -280,7 +292,7 @@ def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
                     h2d=x_host.nbytes, d2h=M * M * 8, config={"n": M, "M": M, "M3": M3, "parts": 1})
     w = hos_synth.workload(name)
     L, N = w["L"], w["N"]
-    products = 3 if prec in ("bf16", "fp32") else 1
+    products = {"bf16": 3, "fp32": 3, "tf32": 1}.get(prec, 1)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if name == "long_bispectrum_n2M_L256" and (world > 1 or time_slices):
         # one series of world x 2^21 samples, cut into time slices (one per
@@ -314,11 +326,13 @@ def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
                 st[k] = st.get(k, 0.0) + v
             return list(st.items())
 
-        flops, work = c3_tc_flops(L, [xh.size - hb - ha], products)
-        return dict(step=step, e2e=e2e, profile=profile, units=units_of(xh.size - hb - ha, L), flops=flops,
-                    work=work, h2d=xh.nbytes, d2h=N * N * 8, bound="tensor" if products == 3 else "alu",
+        lens_ = [xh.size - hb - ha]
+        return dict(step=step, e2e=e2e, profile=profile, units=units_of(xh.size - hb - ha, L),
+                    flops_of=lambda plan: c3_tc_flops(lens_, products, plan), h2d=xh.nbytes, d2h=N * N * 8,
+                    bound="tensor" if prec != "simt" else "alu",
                     config={"n": int(x_all.size), "n_per_rank": int(xh.size - hb - ha), "L": L, "grid": N,
                             "parallelism": f"time slices x{world}, FP64 all-reduce of c3"})
+    from paper_1805_11775_gb300 import tune
     if name in ("long_bispectrum_n2M_L256", "bispectrum_n2048_L32"):
         x_host = w["x"] if rank == 0 else hos_synth.ar2(w["x"].size, 1002 + 100 * rank)
         xd = torch.from_numpy(x_host).cuda()
@@ -327,8 +341,7 @@ def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
         x_pin = torch.from_numpy(x_host).pin_memory()
         o_pin = torch.empty((N, N), dtype=torch.complex64).pin_memory()
         e2e = lambda: hos.bispectrum(x_pin, L, precision=prec, workspace=ws, out=o_pin)
-        flops, work = c3_tc_flops(L, [x_host.size], products)
-        extra = {}
+        extra = {"flops_of": lambda plan: c3_tc_flops([x_host.size], products, plan)}
         if name == "bispectrum_n2048_L32":  # small enough for the whole oracle spectrum
 
             def acc():
@@ -338,9 +351,11 @@ def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
                         "max_rel_err": float(np.abs(out.cpu().numpy() - ref).max() / np.abs(ref).max())}
 
             extra["accuracy"] = acc
-        return dict(step=step, e2e=e2e, units=units_of(x_host.size, L), flops=flops, work=work,
+        if prec != "simt":
+            extra["tune"] = lambda: tune.tune_bispectrum(xd, L, precision=prec)
+        return dict(step=step, e2e=e2e, units=units_of(x_host.size, L),
                     h2d=x_host.nbytes, d2h=N * N * 8, config={"n": int(x_host.size), "L": L, "grid": N},
-                    bound="tensor" if products == 3 else "alu", **extra)
+                    bound="tensor" if products >= 1 and prec != "simt" else "alu", **extra)
     if name == "trispectrum_n65536_L32":
         x_host = w["x"]
         xd = torch.from_numpy(x_host).cuda()
@@ -359,7 +374,7 @@ def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
                     "max_rel_err": float(np.abs(got - ref).max() / np.abs(ref).max()), "sample": "all of T"}
 
         return dict(step=step, e2e=e2e, accuracy=acc, units=units_of(x_host.size, L, k=4), flops=flops,
-                    bound="tensor" if products == 3 else "alu", work=work,
+                    bound="tensor" if prec != "simt" else "alu", work=work,
                     h2d=x_host.nbytes, d2h=N ** 3 * 8, config={"n": int(x_host.size), "L": L, "grid": N})
     if name == "batched_4096x_L128":
         vals, offs = w["x"], w["offsets"]
@@ -377,8 +392,6 @@ def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
         o_pin = torch.empty((S, N, N), dtype=torch.complex64).pin_memory()
         e2e = lambda: hos.bispectrum_batched(v_pin, offs, L, precision=prec, workspace=ws, max_len=max_len,
                                              out=o_pin)
-        flops, work = c3_tc_flops(L, lens, products)
-
         def acc():
             import oracle
             got = out[:8].cpu().numpy()
@@ -389,9 +402,11 @@ def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
             return {"vs": "FP64 oracle", "quantity": "B per series (worst of the sample)", "max_rel_err": err,
                     "sample": "series 0..7, whole grids"}
 
-        return dict(step=step, e2e=e2e, accuracy=acc, units=int((lens * (2 * L + 1) ** 2).sum()), flops=flops,
-                    work=work,
-                    h2d=vals.nbytes + offs.nbytes, d2h=S * N * N * 8, bound="tensor" if products == 3 else "alu",
+        return dict(step=step, e2e=e2e, accuracy=acc, units=int((lens * (2 * L + 1) ** 2).sum()),
+                    flops_of=lambda plan: c3_tc_flops(lens, products, plan),
+                    tune=(lambda: tune.tune_bispectrum_batched(vd, od, L, precision=prec, repeats=3, max_len=max_len))
+                    if prec != "simt" else None,
+                    h2d=vals.nbytes + offs.nbytes, d2h=S * N * N * 8, bound="tensor" if prec != "simt" else "alu",
                     config={"series": S, "total_samples": int(lens.sum()), "L": L, "grid": N},
                     per_series=(vd, offs, L))
     if name == "differentiable_n262144_L128":
@@ -570,10 +585,19 @@ def run_ours(args):
     wl = make_workload(args.workload, prec, rank, hos, torch, args.series, args.time_slices)
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
     sliced = args.workload == WORKLOAD and (world > 1 or args.time_slices)
+    autotune = None
+    if not args.no_tune and not sliced and wl.get("tune"):
+        # the project's autotuner picks the tile width and flush length for
+        # this shape; the timed steps run with automatic knobs, i.e. its choice
+        best, times = wl["tune"]()
+        autotune = {"chosen": {"tile_n": best[0], "flush_chunks": best[1]},
+                    "candidates_ms": {f"tile_n={t} flush={f}": round(v, 4) for (t, f), v in times.items()}}
     ms, stage_acc, launches, clk, mode, t_wall = time_arm(wl, args, hos, torch, flush_buf, dist, local, world, sliced)
     contract_ms = statistics.mean(stage_acc.get("contract", [float("nan")]))
     contraction = hos.last_contraction()
     plan = hos.last_plan()
+    if "flops_of" in wl:  # executed work of the plan the timed calls ran
+        wl["flops"], wl["work"] = wl["flops_of"](plan)
 
     pk, src = peaks()
     if wl["bound"] == "tensor":
@@ -634,7 +658,7 @@ def run_ours(args):
                   "tf32": "tf32 (one product, fp32 accumulate, fp64-class reduce)", "simt": "f32"}[prec],
         "data": "synthetic",
         "config": dict({"workload": args.workload, "precision": prec, "contraction": contraction,
-                        "plan": plan,
+                        "plan": plan, "autotune": autotune,
                         "l2": "flushed between timed steps (256 MB write)",
                         "launch": mode,
                         "parallelism": "replicas" if world > 1 else "single"}, **wl["config"]),
@@ -662,10 +686,17 @@ def run_ours(args):
         # the same workload in a second precision on the same GPU (the metric's
         # "split-BF16 vs FP32, same GPU"), timed the same way
         wl2 = make_workload(args.workload, args.compare, rank, hos, torch, args.series, args.time_slices)
+        tune2 = None
+        if not args.no_tune and wl2.get("tune"):
+            b2, _ = wl2["tune"]()
+            tune2 = {"tile_n": b2[0], "flush_chunks": b2[1]}
         ms2, st2, launches2, clk2, mode2, _ = time_arm(wl2, args, hos, torch, flush_buf, dist, local, world, sliced)
         c2_ms = statistics.mean(st2.get("contract", [float("nan")]))
+        if "flops_of" in wl2:
+            wl2["flops"], wl2["work"] = wl2["flops_of"](hos.last_plan())
         pk2, note2 = tensor_peak(args.compare, pk, src)
         arm = {"precision": args.compare, "contraction": hos.last_contraction(), "plan": hos.last_plan(),
+               "autotune": tune2,
                "ms_per_step": ms2, "value": wl2["units"] * world / (ms2 * 1e-3), "unit": wl2.get("unit", UNIT),
                "launch": mode2, "stage_ms": {k: statistics.mean(v) for k, v in st2.items()},
                "clocks": clk2, "gpu_launches": launches2}
@@ -696,6 +727,7 @@ def main():
     ap.add_argument("--compare", default="fp32", choices=["", "bf16", "fp32", "tf32", "simt"],
                     help="also time this precision on the same workload and GPU (\"\" to skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (automatic tile width and flush)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "bispectrum_n2048_L32", "trispectrum_n65536_L32", "batched_4096x_L128",
                              "differentiable_n262144_L128", "differentiable_trispectrum_n65536_L32",

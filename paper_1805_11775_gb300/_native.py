@@ -10,7 +10,9 @@ import os
 import threading
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_lib", "libhos.so")
+# HOS_LIB selects another build of the library (the bounds-checking variant,
+# _lib/libhos_debug_bounds.so); the default is the in-tree libhos.so
+LIB_PATH = os.environ.get("HOS_LIB") or os.path.join(_PKG, "_lib", "libhos.so")
 
 HOS_OK = 0
 STATUS_NAMES = {0: "HOS_OK", 1: "HOS_ERR_INVALID_ARG", 2: "HOS_ERR_UNSUPPORTED", 3: "HOS_ERR_WORKSPACE",

@@ -29,9 +29,10 @@ static void note_plan(const C3Geom& g, int products) {
         if (w == 256) ++w256;
         if (w < wmin) wmin = w;
     }
+    // cols: the tiles' widths added up (each tile has 128 rows)
     snprintf(g_last_plan, sizeof(g_last_plan),
-             "tile_n=%d tiles=%d (256-wide %d, narrowest %d) flush=%d kc=%d ctas=%d products=%d", g.tile_n,
-             g.ntiles, w256, g.ntiles ? wmin : 0, g.flush, g.kc, g.G, products);
+             "tile_n=%d tiles=%d cols=%d (256-wide %d, narrowest %d) flush=%d kc=%d ctas=%d products=%d", g.tile_n,
+             g.ntiles, 32 * g.ktot, w256, g.ntiles ? wmin : 0, g.flush, g.kc, g.G, products);
 }
 
 // ---- host-side fault injection ----------------------------------------------------
@@ -151,6 +152,18 @@ static int sm_count() {
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
     if (dev >= 0 && dev < 64) cache[dev] = n;
     return n;
+}
+
+// The partial-slot count the contraction's bounds checks use.  In the
+// HOS_DEBUG_BOUNDS build, HOS_DEBUG_SHRINK_SLOTS=1 reports one slot, so that
+// a test can watch the check stop a kernel (it records HOS_ERR_DEVICE_FAULT
+// before any access and the kernel exits) without any access going astray.
+static int64_t debug_slots(int64_t slots) {
+#ifdef HOS_DEBUG_BOUNDS
+    const char* v = std::getenv("HOS_DEBUG_SHRINK_SLOTS");
+    if (v && std::strcmp(v, "1") == 0) return 1;
+#endif
+    return slots;
 }
 
 static uint64_t wait_limit_ns() {
@@ -537,7 +550,8 @@ static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int6
         g_last_contraction = "c3_simt_fp32";
         note_plan(g, 1);
     } else {
-        C3TcParams cp{g, sv, y32, hi, lo, partials, status, wait_limit_ns(), tc_products(p->precision)};
+        C3TcParams cp{g, sv, y32, hi, lo, partials, status, wait_limit_ns(), tc_products(p->precision), l.plane_len,
+                      debug_slots(l.slots)};
         const bool tf32 = tf32_kind(p->precision);
         HOS_CUDA_TRY(launch_c3_tc(tf32, 3, cp, g.G, st));
         g_last_contraction = p->precision == HOS_PREC_TF32 ? "c3_tcgen05_tf32"
@@ -598,7 +612,9 @@ struct Plan4 {
     C3Geom g4;  // tensor-core geometry: tiles = blocks of 128 lag pairs, columns = w3
     size_t status, off, pad, unit, win, mean, mpart, y32, hi, lo, bnd, xr, ilen, m4buf, c2, c2p, partials, grid, tw,
         total;
-    int c2s;  // slices per part of the c2 sums
+    int c2s;        // slices per part of the c2 sums
+    int64_t slots;  // partial slots of the tensor-core contraction
+    int64_t plane_len;
 };
 
 // Geometry of the tensor-core m4 contraction: tile t = pairs [128t, 128t+128)
@@ -673,6 +689,8 @@ static hos_status make_plan4(int op, const hos_params* p, int64_t n, Plan4& P, i
     }
     P.nslices = mean_slices(P.max_len, P.S);
     const int64_t plane_len = n + (int64_t)P.S * ((int64_t)L + KC + P.pad_tail + 64);
+    P.plane_len = plane_len;
+    P.slots = 0;
     size_t o = 0;
     P.status = o; o = al256(o + 256);
     P.off = o; o = al256(o + 8 * (size_t)(P.S + 1));
@@ -690,6 +708,7 @@ static hos_status make_plan4(int op, const hos_params* p, int64_t n, Plan4& P, i
         const int elt = plane_elt(p->precision);
         const int64_t chunks = ceil_div(n, g.kc) + P.S;
         const int64_t slots = (int64_t)g.ntiles * (chunks / g.flush + P.S + 1) + g.G;
+        P.slots = slots;
         const size_t tsz = (size_t)TILE_M * g.tile_n;
         P.hi = o; o = al256(o + (size_t)elt * plane_len + 64);
         P.lo = o; o = al256(o + (size_t)elt * plane_len + 64);
@@ -765,7 +784,7 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
                            sl ? sl->n_total : 0));
     SeriesView sv{off, pad, unit, win, mean, P.S};
     C3TcParams cp{P.g4, sv, y32, hi, lo, at<float>(ws, P.partials), at<int>(ws, P.status), wait_limit_ns(),
-                  tc_products(p->precision)};
+                  tc_products(p->precision), P.plane_len, debug_slots(P.slots)};
     const bool tf32 = tf32_kind(p->precision);
     HOS_CUDA_TRY(launch_c3_tc(tf32, 4, cp, P.g4.G, st));
     g_last_contraction = p->precision == HOS_PREC_TF32 ? "m4_tcgen05_tf32"
@@ -934,7 +953,7 @@ using namespace hos;
 
 extern "C" {
 
-const char* hos_version(void) { return "hos-gb300 0.1 (sm_103a)"; }
+const char* hos_version(void) { return "hos-gb300 0.2 (sm_103a)"; }
 
 const char* hos_status_string(int32_t s) {
     switch (s) {
@@ -1457,9 +1476,8 @@ hos_status hos_check_plan(int32_t op, int64_t n_total, int32_t n_series, const i
         S = P.S;
         seg = P.seg;
         order = 4;
-        plane_len = n_total + (int64_t)P.S * ((int64_t)p->L + KC + P.pad_tail + 64);
-        const int64_t chunks = ceil_div(n_total, g.kc) + P.S;
-        n_slots = (int64_t)g.ntiles * (chunks / g.flush + P.S + 1) + g.G;
+        plane_len = P.plane_len;
+        n_slots = P.slots;
     } else {
         return HOS_ERR_UNSUPPORTED;
     }

@@ -163,6 +163,23 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                 const int64_t ib = base + L + i0;                          // y(i0)
                 const int64_t ib_al = ib & ~(int64_t)3;
                 const uint32_t wbytes = (uint32_t)(csz + wt + 16) * ELT;
+#ifdef HOS_DEBUG_BOUNDS
+                {   // every copy inside this series' padded block, the part's slot inside the
+                    // workspace: otherwise record a fault and stop before any access
+                    const int64_t b0 = P.ser.pad[part.s], b1 = P.ser.pad[part.s + 1];
+                    const int64_t ae = ab + csz + TILE_M;
+                    const bool bad = b1 > P.plane_len || wb < b0 || wb + csz + wt + 16 > b1 || ab < b0 || ae > b1 ||
+                                     ib_al < b0 || ib_al + csz + 4 > b1 || part.slot < 0 || part.slot >= P.n_slots;
+                    if (bad) {
+                        if (lane == 0) {
+                            record_status(P.status, HOS_ERR_DEVICE_FAULT);
+                            *abort = 1;
+                        }
+                        ok = false;
+                        break;
+                    }
+                }
+#endif
                 if (lane == 0) {
                     const uint32_t yab = (uint32_t)(csz + TILE_M) * 4, yib = (uint32_t)(csz + 4) * 4;
                     mbar_expect_tx(&sm.tma_bar, 2 * wbytes + yab + yib);

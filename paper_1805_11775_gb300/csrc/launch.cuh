@@ -16,7 +16,9 @@ struct C3TcParams {
     float* partials;
     int* status;
     uint64_t limit_ns;
-    int products;  // 3: hi*hi + hi*lo + lo*hi (split precision); 1: hi*hi (plain TF32)
+    int products;       // 3: hi*hi + hi*lo + lo*hi (split precision); 1: hi*hi (plain TF32)
+    int64_t plane_len;  // samples in each plane (bounds of the HOS_DEBUG_BOUNDS build)
+    int64_t n_slots;    // partial slots in the workspace (same)
 };
 
 struct C3SimtParams {

@@ -4,9 +4,17 @@ For a problem shape (op, L, size bucket, series-count bucket, precision) it
 times every candidate (tile_n, flush_chunks) through the C ABI with CUDA
 events on the current stream, keeps the fastest, and stores it in a JSON
 cache (``$HOS_TUNE_CACHE``, default ``~/.cache/hos_gb300/tune.json``) keyed by
-the device name.  The public calls consult the cache when the caller leaves
-``tile_n`` / ``flush_chunks`` at 0.  The 3xTF32 path keeps short flushes only:
-its FP32 accumulation error grows with the MMA steps one partial holds.
+the device name and the library version (a rebuilt library with changed
+kernels does not reuse old choices).  The public calls consult the cache when
+the caller leaves ``tile_n`` / ``flush_chunks`` at 0.  The 3xTF32 path keeps
+short flushes only: its FP32 accumulation error grows with the MMA steps one
+partial holds.
+
+tile_n is the widest lag tile: 256 gives each 128-row block of the lag square
+tiles of 256 columns (and a narrower last one), 128 gives 128-column tiles
+throughout (twice the tiles, half the MMA width); the flush length sets how
+many 1024-sample chunks a tile accumulates in FP32 before its partial sum goes
+to the reduction (more: fewer partials to reduce, longer FP32 sums).
 """
 from __future__ import annotations
 
@@ -51,8 +59,13 @@ def _bucket(v: int) -> int:
     return int(math.ceil(math.log2(max(int(v), 1))))
 
 
-def key(device_name: str, op: str, L: int, n_total: int, n_series: int, precision: str) -> str:
-    return f"{device_name}|{op}|L{L}|n2^{_bucket(n_total)}|S2^{_bucket(n_series)}|{precision}"
+def library_version() -> str:
+    from . import _native
+    return _native.lib().hos_version().decode()
+
+
+def key(device_name: str, op: str, L: int, n_total: int, n_series: int, precision: str, version: str = "") -> str:
+    return f"{version}|{device_name}|{op}|L{L}|n2^{_bucket(n_total)}|S2^{_bucket(n_series)}|{precision}"
 
 
 def lookup(op: str, L: int, n_total: int, n_series: int, precision: str):
@@ -60,7 +73,7 @@ def lookup(op: str, L: int, n_total: int, n_series: int, precision: str):
     import torch
     if not torch.cuda.is_available():
         return None
-    k = key(torch.cuda.get_device_name(), op, L, n_total, n_series, precision)
+    k = key(torch.cuda.get_device_name(), op, L, n_total, n_series, precision, library_version())
     v = _load().get(k)
     return (int(v["tile_n"]), int(v["flush_chunks"])) if v else None
 
@@ -91,7 +104,7 @@ def tune(run, op: str, L: int, n_total: int, n_series: int, precision: str, repe
         times[cand] = e0.elapsed_time(e1) / repeats
     best = min(times, key=times.get)
     if store:
-        k = key(torch.cuda.get_device_name(), op, L, n_total, n_series, precision)
+        k = key(torch.cuda.get_device_name(), op, L, n_total, n_series, precision, library_version())
         with _lock:
             _load()[k] = {"tile_n": best[0], "flush_chunks": best[1], "ms": times[best]}
             _save()

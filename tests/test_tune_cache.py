@@ -19,6 +19,12 @@ def test_key_buckets_sizes():
     assert a == b != c
 
 
+def test_key_names_the_library_version():
+    a = tune.key("GB300", "bispectrum", 128, 3000, 1, "bf16", "hos-gb300 0.1")
+    b = tune.key("GB300", "bispectrum", 128, 3000, 1, "bf16", "hos-gb300 0.2")
+    assert a != b
+
+
 def test_corrupt_cache_is_rebuilt(tmp_path, monkeypatch):
     p = tmp_path / "tune.json"
     p.write_text("{not json")
