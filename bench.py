@@ -225,16 +225,19 @@ def c3_tc_flops(lens, products, plan):
 def m4_flops(L, n, prec):
     """Executed flops of the m4 contraction.  Tensor cores: 128-pair tiles of
     the lag triangle w1 <= w2 x next_pow2(2L) columns w3 x padded samples x 3
-    products x 2 (chunks of 1024 samples, 128 for 3xTF32).  SIMT: FFMA over
-    pair rows x w3 rounded to 16 x samples rounded to 4096."""
+    products x 2 (chunks of 1024 samples, 128 for 3xTF32, 256 for split FP16;
+    one product for plain TF32).  SIMT: FFMA over pair rows x w3 rounded to
+    16 x samples rounded to 4096."""
     two_l = 2 * L
     npairs = two_l * (two_l + 1) // 2
     rows = math.ceil(npairs / 128) * 128
-    if prec in ("bf16", "fp32"):
+    if prec in ("bf16", "fp32", "fp16", "tf32"):
         cols = max(32, 1 << (two_l - 1).bit_length())
-        kc = 128 if prec == "fp32" else 1024
+        kc = {"fp32": 128, "fp16": 256}.get(prec, 1024)
         kpad = math.ceil(n / kc) * kc
-        return rows * cols * kpad * 6, f"{rows} lag pairs x {cols} w3 x {kpad} padded samples x 3 products x 2 flops"
+        prod = 1 if prec == "tf32" else 3
+        return rows * cols * kpad * 2 * prod, (f"{rows} lag pairs x {cols} w3 x {kpad} padded samples x {prod} products"
+                                               f" x 2 flops")
     w3 = 16 * math.ceil(two_l / 16)
     kpad = math.ceil(n / 4096) * 4096
     return rows * w3 * kpad * 2, f"{rows} lag pairs x {w3} w3 x {kpad} samples x 2 flops (FFMA)"
@@ -292,7 +295,7 @@ def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
                     h2d=x_host.nbytes, d2h=M * M * 8, config={"n": M, "M": M, "M3": M3, "parts": 1})
     w = hos_synth.workload(name)
     L, N = w["L"], w["N"]
-    products = {"bf16": 3, "fp32": 3, "tf32": 1}.get(prec, 1)
+    products = {"bf16": 3, "fp32": 3, "tf32": 1, "fp16": 3}.get(prec, 1)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if name == "long_bispectrum_n2M_L256" and (world > 1 or time_slices):
         # one series of world x 2^21 samples, cut into time slices (one per
@@ -563,6 +566,8 @@ def tensor_peak(prec, pk, src):
     """Dense tensor peak of the contraction's operand type (TFLOP/s)."""
     if prec == "bf16":
         return pk["bf16_tflops"], f"bf16 dense, {src} burst"
+    if prec == "fp16":  # the same dense rate as bf16 (kind::f16, nominal 2.25 PFLOP/s either way)
+        return pk["bf16_tflops"], f"fp16 dense = {src} bf16 burst (same nominal rate)"
     return pk["bf16_tflops"] * (1.1 / 2.25), f"tf32 dense = {src} bf16 burst x 1.1/2.25 (nominal ratio)"
 
 
@@ -590,8 +595,8 @@ def run_ours(args):
         # the project's autotuner picks the tile width and flush length for
         # this shape; the timed steps run with automatic knobs, i.e. its choice
         best, times = wl["tune"]()
-        autotune = {"chosen": {"tile_n": best[0], "flush_chunks": best[1]},
-                    "candidates_ms": {f"tile_n={t} flush={f}": round(v, 4) for (t, f), v in times.items()}}
+        autotune = {"chosen": {"tile_n": best[0], "flush_chunks": best[1], "chunk_len": best[2]},
+                    "candidates_ms": {f"tile_n={t} flush={f} chunk={c}": round(v, 4) for (t, f, c), v in times.items()}}
     ms, stage_acc, launches, clk, mode, t_wall = time_arm(wl, args, hos, torch, flush_buf, dist, local, world, sliced)
     contract_ms = statistics.mean(stage_acc.get("contract", [float("nan")]))
     contraction = hos.last_contraction()
@@ -613,7 +618,7 @@ def run_ours(args):
     else:
         achieved = wl["flops"] / (contract_ms * 1e-3) / 1e12
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
-    per_clk = 8192 if prec == "bf16" else 4096
+    per_clk = 8192 if prec in ("bf16", "fp16") else 4096
     clock_peak = nsm * per_clk * (clk["sm_mhz"] or 2070.0) * 1e6 / 1e12
     is_tc = contraction.startswith("c3_tcgen05")
     traffic = profiled_traffic(prec) if (is_tc and args.workload == WORKLOAD) else None
@@ -655,7 +660,9 @@ def run_ours(args):
         "dtype": "f32 (transform, products), double-float window sums" if "roof" in wl else
                  {"bf16": "bf16x3 (split-bf16, fp32 accumulate, fp64-class reduce)",
                   "fp32": "tf32x3 (fp32-class, fp32 accumulate, fp64-class reduce)",
-                  "tf32": "tf32 (one product, fp32 accumulate, fp64-class reduce)", "simt": "f32"}[prec],
+                  "tf32": "tf32 (one product, fp32 accumulate, fp64-class reduce)",
+                  "fp16": "f16x3 (split-fp16 of the power-of-two scaled series, fp32 accumulate, fp64-class reduce)",
+                  "simt": "f32"}[prec],
         "data": "synthetic",
         "config": dict({"workload": args.workload, "precision": prec, "contraction": contraction,
                         "plan": plan, "autotune": autotune,
@@ -689,7 +696,7 @@ def run_ours(args):
         tune2 = None
         if not args.no_tune and wl2.get("tune"):
             b2, _ = wl2["tune"]()
-            tune2 = {"tile_n": b2[0], "flush_chunks": b2[1]}
+            tune2 = {"tile_n": b2[0], "flush_chunks": b2[1], "chunk_len": b2[2]}
         ms2, st2, launches2, clk2, mode2, _ = time_arm(wl2, args, hos, torch, flush_buf, dist, local, world, sliced)
         c2_ms = statistics.mean(st2.get("contract", [float("nan")]))
         if "flops_of" in wl2:
@@ -723,8 +730,8 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "tf32", "simt"])
-    ap.add_argument("--compare", default="fp32", choices=["", "bf16", "fp32", "tf32", "simt"],
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "tf32", "simt", "fp16"])
+    ap.add_argument("--compare", default="fp32", choices=["", "bf16", "fp32", "tf32", "simt", "fp16"],
                     help="also time this precision on the same workload and GPU (\"\" to skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (automatic tile width and flush)")

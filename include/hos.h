@@ -74,12 +74,26 @@ typedef enum { HOS_F32 = 0, HOS_F64 = 1 } hos_dtype;
  *                 factors rounded to 10 mantissa bits), FP32 accumulation:
  *                 about 1e-4 to 1e-3, for comparison only (no accuracy
  *                 target); the adjoint runs it on the CUDA cores;
- *   SIMT_FP32   : plain FP32 FFMA on the CUDA cores (cross-check path).
+ *   SIMT_FP32   : plain FP32 FFMA on the CUDA cores (cross-check path);
+ *   SPLIT_FP16  : FP32-class like FP32 at the speed of SPLIT_BF16: each
+ *                 series is scaled by a power of two (exact) that puts its
+ *                 largest |y| at 2^7 (2^4 for the fourth order), then
+ *                 x = hi + lo in FP16 (11 + 11 significant bits), three
+ *                 products on the tensor cores (tcgen05 kind::f16, F16
+ *                 operands), FP32 accumulation over half as many MMA steps
+ *                 as 3xTF32; the scale is divided out in the FP64-class
+ *                 reduction.  The adjoint runs it on the CUDA cores.
  * Mean removal is FP64.  The cross-chunk reduction and c2 are FP64-class in
  * every mode: double-float sums (two floats, TwoSum / FMA, about 44-48
  * significant bits) on the FP32 pipes, since GB300 issues FP64 at about 1/64
  * of its FP32 rate.                                                        */
-typedef enum { HOS_PREC_FP32 = 0, HOS_PREC_SPLIT_BF16 = 1, HOS_PREC_TF32 = 2, HOS_PREC_SIMT_FP32 = 3 } hos_precision;
+typedef enum {
+    HOS_PREC_FP32 = 0,
+    HOS_PREC_SPLIT_BF16 = 1,
+    HOS_PREC_TF32 = 2,
+    HOS_PREC_SIMT_FP32 = 3,
+    HOS_PREC_SPLIT_FP16 = 4
+} hos_precision;
 
 /* Lag windows.  PARZEN: d(w1)d(w2)[d(w3)] (separable).  PARZEN_SYM (bispectrum
  * only): d(w1)d(w2)d(w1-w2), which keeps c3's six-fold symmetry.  RECT: 1 for
@@ -130,6 +144,11 @@ typedef struct {
                              hos_cumulant4 (and the no-allocation entry)
                              accept it; the others return
                              HOS_ERR_INVALID_ARG for a nonzero value.         */
+    int32_t chunk_len;    /* 0: automatic; else samples of the time index one
+                             contraction step covers before moving on (a
+                             multiple of 64, at most 1024; tuning knob: a
+                             shorter chunk makes shorter FP32 sums per partial
+                             and more partials to reduce)                      */
 } hos_params;
 
 /* Bytes of workspace an operation needs.

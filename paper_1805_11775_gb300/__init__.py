@@ -27,7 +27,8 @@ __all__ = ["bispectrum", "bispectrum_batched", "trispectrum", "trispectrum_batch
            "selftest_timeout", "set_profiling", "stage_times", "launch_count", "last_contraction", "last_plan", "HosError",
            "PRECISIONS", "WINDOWS"]
 
-PRECISIONS = {"fp32": 0, "3xtf32": 0, "bf16": 1, "split_bf16": 1, "tf32": 2, "simt": 3, "simt_fp32": 3}
+PRECISIONS = {"fp32": 0, "3xtf32": 0, "bf16": 1, "split_bf16": 1, "tf32": 2, "simt": 3, "simt_fp32": 3, "fp16": 4,
+              "split_fp16": 4}
 WINDOWS = {"parzen": 0, "parzen_sym": 1, "rect": 2}
 
 
@@ -37,20 +38,21 @@ def _torch():
 
 
 def make_params(L, nfft=0, precision="bf16", window="parzen", remove_mean=True, segment_len=0, tile_n=0,
-                flush_chunks=0, segment_overlap=0) -> HosParams:
+                flush_chunks=0, segment_overlap=0, chunk_len=0) -> HosParams:
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     win = WINDOWS[window] if isinstance(window, str) else int(window)
     return HosParams(int(L), int(nfft or 0), prec, win, int(bool(remove_mean)), int(segment_len or 0),
-                     int(tile_n or 0), int(flush_chunks or 0), int(segment_overlap or 0))
+                     int(tile_n or 0), int(flush_chunks or 0), int(segment_overlap or 0), int(chunk_len or 0))
 
 
-def _tuned(op, L, n_total, n_series, precision, tile_n, flush_chunks):
-    """The caller's knobs, else the autotuner's cached choice, else automatic."""
-    if tile_n or flush_chunks:
-        return tile_n, flush_chunks
+def _tuned(op, L, n_total, n_series, precision, tile_n, flush_chunks, chunk_len=0):
+    """The caller's knobs, else the autotuner's cached choice, else automatic:
+    (tile_n, flush_chunks, chunk_len)."""
+    if tile_n or flush_chunks or chunk_len:
+        return tile_n, flush_chunks, chunk_len
     from . import tune
     r = tune.lookup(op, L, n_total, n_series, precision if isinstance(precision, str) else str(precision))
-    return r if r else (0, 0)
+    return r if r else (0, 0, 0)
 
 
 def workspace_size(op: int, n_total: int, n_series: int, max_len: int, params: HosParams) -> int:
@@ -140,18 +142,22 @@ def _dtype_code(x):
 
 
 def bispectrum(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=True, segment_len=0, tile_n=0,
-               flush_chunks=0, out=None, workspace=None, stream=None, segment_overlap=0):
+               flush_chunks=0, out=None, workspace=None, stream=None, segment_overlap=0, chunk_len=0):
     """Smoothed sample bispectrum B[k1, k2] (complex64, nfft x nfft, default nfft = 2L).
 
     ``precision``: "bf16" (split-bf16 tensor cores), "fp32" (3xTF32 tensor
-    cores) or "simt" (FP32 CUDA cores).  Host input returns a host result; a
+    cores), "fp16" (split FP16 of the series scaled by a power of two:
+    FP32-class at the split-bf16 rate), "tf32" (one plain TF32 product, no
+    accuracy target) or "simt" (FP32 CUDA cores).  Host input returns a host result; a
     host ``out`` (pinned for speed) receives the result.  ``segment_len`` > 0
     averages parts of that many samples; ``segment_overlap`` makes them
     overlap (parts start every segment_len - segment_overlap samples)."""
     torch = _torch()
     xd, host = _prepare(x)
-    tile_n, flush_chunks = _tuned("bispectrum", L, xd.numel(), 1, precision, tile_n, flush_chunks)
-    p = make_params(L, nfft, precision, window, remove_mean, segment_len, tile_n, flush_chunks, segment_overlap)
+    tile_n, flush_chunks, chunk_len = _tuned("bispectrum", L, xd.numel(), 1, precision, tile_n, flush_chunks,
+                                             chunk_len)
+    p = make_params(L, nfft, precision, window, remove_mean, segment_len, tile_n, flush_chunks, segment_overlap,
+                    chunk_len)
     N = p.nfft or 2 * p.L
     dev, host_out = _out_buffers(out, (N, N), xd.device)
     ws = _workspace(workspace, xd.device)
@@ -205,7 +211,8 @@ def _batched_pipelined(values, offs, L, p, out, workspace, groups):
 
 
 def bispectrum_batched(values, offsets, L, nfft=0, precision="bf16", window="parzen", remove_mean=True, tile_n=0,
-                       flush_chunks=0, out=None, workspace=None, stream=None, max_len=None, pipeline=4):
+                       flush_chunks=0, out=None, workspace=None, stream=None, max_len=None, pipeline=4,
+                       chunk_len=0):
     """Bispectra of S series concatenated in ``values`` with ``offsets`` (S+1).
 
     Returns (S, nfft, nfft) complex64.  With host ``values`` and a pinned host
@@ -221,9 +228,9 @@ def bispectrum_batched(values, offsets, L, nfft=0, precision="bf16", window="par
             raise TypeError("values must be float32 or float64")
         S = offs_h.size - 1
         if S >= 2 * pipeline:
-            tile_n, flush_chunks = _tuned("bispectrum_batched", L, vals_h.numel(), S, precision, tile_n,
-                                          flush_chunks)
-            p = make_params(L, nfft, precision, window, remove_mean, 0, tile_n, flush_chunks)
+            tile_n, flush_chunks, chunk_len = _tuned("bispectrum_batched", L, vals_h.numel(), S, precision, tile_n,
+                                                     flush_chunks, chunk_len)
+            p = make_params(L, nfft, precision, window, remove_mean, 0, tile_n, flush_chunks, 0, chunk_len)
             return _batched_pipelined(vals_h, offs_h, L, p, out, workspace, pipeline)
     vd, host = _prepare(values)
     offs = torch.as_tensor(offsets, dtype=torch.int64)
@@ -232,8 +239,9 @@ def bispectrum_batched(values, offsets, L, nfft=0, precision="bf16", window="par
         max_len = int((oh[1:] - oh[:-1]).max().item()) if oh.numel() > 1 else 0
     od = offs.to(vd.device, non_blocking=True).contiguous()
     S = od.numel() - 1
-    tile_n, flush_chunks = _tuned("bispectrum_batched", L, vd.numel(), S, precision, tile_n, flush_chunks)
-    p = make_params(L, nfft, precision, window, remove_mean, 0, tile_n, flush_chunks)
+    tile_n, flush_chunks, chunk_len = _tuned("bispectrum_batched", L, vd.numel(), S, precision, tile_n, flush_chunks,
+                                             chunk_len)
+    p = make_params(L, nfft, precision, window, remove_mean, 0, tile_n, flush_chunks, 0, chunk_len)
     N = p.nfft or 2 * p.L
     dev, host_out = _out_buffers(out, (S, N, N), vd.device)
     ws = _workspace(workspace, vd.device)
@@ -245,11 +253,12 @@ def bispectrum_batched(values, offsets, L, nfft=0, precision="bf16", window="par
 
 
 def cumulant3(x, L, precision="bf16", remove_mean=True, segment_len=0, tile_n=0, flush_chunks=0, workspace=None,
-              stream=None, segment_overlap=0):
+              stream=None, segment_overlap=0, chunk_len=0):
     """Unwindowed sample c3 over [-L, L-1]^2 (float64, (2L, 2L), index w + L)."""
     torch = _torch()
     xd, host = _prepare(x)
-    p = make_params(L, 0, precision, "parzen", remove_mean, segment_len, tile_n, flush_chunks, segment_overlap)
+    p = make_params(L, 0, precision, "parzen", remove_mean, segment_len, tile_n, flush_chunks, segment_overlap,
+                    chunk_len)
     out = torch.empty((2 * p.L, 2 * p.L), dtype=torch.float64, device=xd.device)
     ws = _workspace(workspace, xd.device)
     ws.get(workspace_size(_native.OP_CUMULANT3, xd.numel(), 1, xd.numel(), p))
@@ -260,11 +269,12 @@ def cumulant3(x, L, precision="bf16", remove_mean=True, segment_len=0, tile_n=0,
 
 
 def trispectrum(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=True, segment_len=0, flush_chunks=0,
-                out=None, workspace=None, stream=None, segment_overlap=0):
+                out=None, workspace=None, stream=None, segment_overlap=0, chunk_len=0):
     """Smoothed sample trispectrum T[k1, k2, k3] (complex64, nfft^3)."""
     torch = _torch()
     xd, host = _prepare(x)
-    p = make_params(L, nfft, precision, window, remove_mean, segment_len, 0, flush_chunks, segment_overlap)
+    p = make_params(L, nfft, precision, window, remove_mean, segment_len, 0, flush_chunks, segment_overlap,
+                    chunk_len)
     N = p.nfft or 2 * p.L
     dev, host_out = _out_buffers(out, (N, N, N), xd.device)
     ws = _workspace(workspace, xd.device)

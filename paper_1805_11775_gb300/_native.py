@@ -26,7 +26,8 @@ F32, F64 = 0, 1
 class HosParams(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("nfft", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("window", ctypes.c_int32), ("remove_mean", ctypes.c_int32), ("segment_len", ctypes.c_int32),
-                ("tile_n", ctypes.c_int32), ("flush_chunks", ctypes.c_int32), ("segment_overlap", ctypes.c_int32)]
+                ("tile_n", ctypes.c_int32), ("flush_chunks", ctypes.c_int32), ("segment_overlap", ctypes.c_int32),
+                ("chunk_len", ctypes.c_int32)]
 
 
 class HosError(RuntimeError):

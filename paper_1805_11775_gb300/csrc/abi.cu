@@ -166,6 +166,26 @@ static int64_t debug_slots(int64_t slots) {
     return slots;
 }
 
+// The contraction's wait hints per role (producer, builders, epilogue, MMA
+// issuer): try_wait suspend-time hints in ns, 0 = the system's own limit,
+// WAIT_SPIN = poll without suspending.  HOS_C3_WAIT_HINTS="p,b,e,m" (ns, -1
+// for a spin) overrides them.
+static void wait_hints(uint32_t (&h)[4]) {
+    h[0] = 2000;
+    h[1] = 1000;
+    h[2] = 20000;
+    h[3] = 0;
+    const char* v = std::getenv("HOS_C3_WAIT_HINTS");
+    if (!v) return;
+    for (int i = 0; i < 4 && *v; ++i) {
+        char* end = nullptr;
+        const long x = std::strtol(v, &end, 10);
+        if (end == v) break;
+        h[i] = x < 0 ? WAIT_SPIN : (uint32_t)x;
+        v = (*end == ',') ? end + 1 : end;
+    }
+}
+
 static uint64_t wait_limit_ns() {
     const char* v = getenv("HOS_WAIT_LIMIT_MS");
     long ms = v ? atol(v) : 4000;
@@ -193,12 +213,14 @@ static hos_status check_params(const hos_params* p, int op) {
         const int nf = p->nfft ? p->nfft : 2 * p->L;
         if ((nf & (nf - 1)) != 0 && nf > 2048) return HOS_ERR_UNSUPPORTED;
     }
-    if (p->precision < 0 || p->precision > 3) return HOS_ERR_INVALID_ARG;
+    if (p->precision < 0 || p->precision > 4) return HOS_ERR_INVALID_ARG;
     if (p->window < 0 || p->window > 2) return HOS_ERR_INVALID_ARG;
     if (p->segment_len < 0) return HOS_ERR_INVALID_ARG;
     if (p->tile_n != 0 && p->tile_n != 32 && p->tile_n != 64 && p->tile_n != 128 && p->tile_n != 256)
         return HOS_ERR_INVALID_ARG;
     if (p->flush_chunks < 0) return HOS_ERR_INVALID_ARG;
+    if (p->chunk_len != 0 && (p->chunk_len < 64 || p->chunk_len > KC || p->chunk_len % 64 != 0))
+        return HOS_ERR_INVALID_ARG;
     if (p->segment_overlap < 0) return HOS_ERR_INVALID_ARG;
     if (p->segment_overlap > 0) {
         const bool parts_op = (op == HOS_OP_BISPECTRUM || op == HOS_OP_TRISPECTRUM || op == HOS_OP_CUMULANT3 ||
@@ -242,22 +264,29 @@ static OverlapPlan overlap_plan(const hos_params* p, int64_t n) {
     return o;
 }
 
-// Tiles of the lag square: row block a (128 lags w1) takes the columns from
-// its own diagonal block on, j >= 128a (c3(w1,w2) = c3(w2,w1) fills the rest),
-// cut into tiles of N columns with a narrower last one (a multiple of 32).
+// Tiles of the lag square.  c3(w1,w2) = c3(w2,w1), so row block a (128 lags
+// w1) needs only the columns from its own diagonal block on, j >= 128a.
+// Full width (the default): the row's tiles are N columns wide and start at
+// the multiple of N at or below 128a, so the diagonal block's lower part is
+// computed too.  Diagonal start (HOS_TILE_SCHEME=diagonal): the row starts at
+// 128a and its last tile is narrower (a multiple of 32); fewer MMA columns,
+// but on GB300 a 128-column tile's chunk takes about as long as a 256-column
+// one, so full width is faster.
 // skip_zero_window: leave out tiles where the window is zero at every lag
 // (PARZEN_SYM: d(w1 - w2) = 0 for |w1 - w2| >= L); the transform grid is
 // zero-filled there.  Returns the tile count (may exceed MAX_TILES: nothing is
 // written past it).
 static int build_tiles(C3Geom& g, int L, int N, bool skip_zero_window, int* zero_skipped) {
     const int twoL = 2 * L;
+    const char* scheme = std::getenv("HOS_TILE_SCHEME");
+    const bool diagonal = scheme && std::strcmp(scheme, "diagonal") == 0;
     int cnt = 0, k = 0, zs = 0;
     for (int a = 0; a < g.tiles_m; ++a) {
-        const int c0 = a * TILE_M;
+        const int c0 = diagonal ? a * TILE_M : (a * TILE_M / N) * N;
         g.row_c0[a] = (uint16_t)c0;
         for (int c = c0; c < twoL;) {
             const int rem = (int)round_up(twoL - c, 32);
-            const int w = rem < N ? rem : N;
+            const int w = diagonal ? (rem < N ? rem : N) : N;
             bool zero = false;
             if (skip_zero_window) {
                 const int w1lo = -L + a * TILE_M, w1hi = w1lo + TILE_M - 1;
@@ -307,8 +336,11 @@ static C3Geom make_geom(const hos_params* p, int G, bool skip_zero_window = fals
     // 1024-sample chunk; split-bf16 (16 samples per step, 1e-4 target) and SIMT
     // (FP32 FFMA, round to nearest) after 16 chunks.
     // Plain TF32 is limited by its 10-bit factors, not by the accumulation.
-    g.flush = p->flush_chunks ? p->flush_chunks : (p->precision == HOS_PREC_FP32 ? 1 : 16);
-    g.kc = KC;
+    // The FP32-class paths (3xTF32, split FP16: 1e-5 target) hand every chunk's
+    // partial to the reduction.
+    const bool fp32_class = p->precision == HOS_PREC_FP32 || p->precision == HOS_PREC_SPLIT_FP16;
+    g.flush = p->flush_chunks ? p->flush_chunks : (fp32_class ? 1 : 16);
+    g.kc = p->chunk_len ? p->chunk_len : KC;
     g.G = G;
     // zero samples after a series: every sample a tile's windows read (the
     // SIMT kernel reads all N columns of a tile, the tensor cores its width)
@@ -322,13 +354,33 @@ static C3Geom make_geom(const hos_params* p, int G, bool skip_zero_window = fals
 static int contraction_ctas(int precision) { return precision == HOS_PREC_SIMT_FP32 ? 4 * sm_count() : sm_count(); }
 
 static bool tf32_kind(int precision) { return precision == HOS_PREC_FP32 || precision == HOS_PREC_TF32; }
+// operand format of the tensor-core contraction
+static int tc_format(int precision) {
+    return tf32_kind(precision) ? FMT_TF32 : (precision == HOS_PREC_SPLIT_FP16 ? FMT_F16 : FMT_BF16);
+}
 // products per lag term on the tensor cores: hi*hi + hi*lo + lo*hi, or hi*hi alone (plain TF32)
 static int tc_products(int precision) { return precision == HOS_PREC_TF32 ? 1 : 3; }
 static int plane_split(int precision) {
-    return precision == HOS_PREC_SPLIT_BF16 ? 1 : (tf32_kind(precision) ? 2 : 0);
+    if (precision == HOS_PREC_SPLIT_BF16) return 1;
+    if (precision == HOS_PREC_SPLIT_FP16) return 3;
+    return tf32_kind(precision) ? 2 : 0;
 }
 static int plane_elt(int precision) {
-    return precision == HOS_PREC_SPLIT_BF16 ? 2 : (tf32_kind(precision) ? 4 : 0);
+    if (precision == HOS_PREC_SPLIT_BF16 || precision == HOS_PREC_SPLIT_FP16) return 2;
+    return tf32_kind(precision) ? 4 : 0;
+}
+// The FP16 planes put each series' largest |y| at 2^7 (third order: products
+// of two samples up to 2^14) or 2^4 (fourth order: three samples, 2^12),
+// inside FP16's range (65504) with the lo halves mostly normal.
+constexpr int FP16_TOP3 = 7, FP16_TOP4 = 4;
+static const char* contraction_name(int order, int precision) {
+    const bool o3 = order == 3;
+    switch (precision) {
+        case HOS_PREC_TF32: return o3 ? "c3_tcgen05_tf32" : "m4_tcgen05_tf32";
+        case HOS_PREC_FP32: return o3 ? "c3_tcgen05_3xtf32" : "m4_tcgen05_3xtf32";
+        case HOS_PREC_SPLIT_FP16: return o3 ? "c3_tcgen05_split_fp16" : "m4_tcgen05_split_fp16";
+        default: return o3 ? "c3_tcgen05_split_bf16" : "m4_tcgen05_split_bf16";
+    }
 }
 
 static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -342,7 +394,8 @@ static int mean_slices(int64_t len, int S) {
 }
 
 struct Layout {
-    size_t status, off, pad, unit, win, mean, mpart, bnd, xr, ilen, wtab, y32, hi, lo, partials, grid, tw, total;
+    size_t status, off, pad, unit, win, mean, mpart, scale, smax, bnd, xr, ilen, wtab, y32, hi, lo, partials, grid, tw,
+        total;
     int64_t plane_len, slots;
     int nslices;
     int groups;
@@ -366,6 +419,8 @@ static Layout make_layout(int op, const hos_params* p, const C3Geom& g, int64_t 
     l.win = o; o = al256(o + 8 * (size_t)(S + 1));
     l.mean = o; o = al256(o + 8 * (size_t)S);
     l.mpart = o; o = al256(o + 8 * (size_t)S * l.nslices);
+    l.scale = o; o = al256(o + 4 * (size_t)S);
+    l.smax = o; o = al256(o + 4 * (size_t)S);
     l.bnd = o; o = al256(o + 8 * (size_t)(g.G + 1));
     l.xr = o; o = al256(o + sizeof(TileRec) * (size_t)S * g.ntiles);
     l.ilen = o; o = al256(o + 8 * (size_t)S);
@@ -411,7 +466,8 @@ static hos_status make_plan(int op, const hos_params* p, int64_t n_total, int S_
         P.max_len = P.seg ? P.seg : n_total;
         // exact chunk count: full parts plus the (possibly shorter) last one
         const int64_t last = n_total - (P.S - 1) * (P.seg ? P.seg : 0);
-        U_known = (P.S - 1) * ceil_div(P.max_len, KC) + ceil_div(last, KC);  // chunks at KC = make_geom's kc
+        const int kc = p->chunk_len ? p->chunk_len : KC;  // make_geom's chunk length
+        U_known = (P.S - 1) * ceil_div(P.max_len, kc) + ceil_div(last, kc);
     }
     if (P.S > 65535) return HOS_ERR_UNSUPPORTED;
     int G = contraction_ctas(p->precision);
@@ -539,10 +595,16 @@ static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int6
     int bx = (int)ceil_div(maxpad, 256 * 4);
     if (bx < 1) bx = 1;
     if (bx > 65535) bx = 65535;
+    float* scale = nullptr;
+    if (p->precision == HOS_PREC_SPLIT_FP16) {
+        scale = at<float>(ws, l.scale);
+        HOS_CUDA_TRY(launch_series_scale(xs, dtype, off, mean, S, l.nslices, sl ? sl->halo_before : 0,
+                                         sl ? sl->halo_after : 0, FP16_TOP3, at<unsigned>(ws, l.smax), scale, st));
+    }
     HOS_CUDA_TRY(launch_planes(xs, dtype, off, pad, mean, p->L, plane_split(p->precision), y32, hi, lo, S, bx, st,
-                               sl ? sl->halo_before : 0, sl ? sl->halo_after : 0));
+                               sl ? sl->halo_before : 0, sl ? sl->halo_after : 0, scale));
 
-    SeriesView sv{off, pad, unit, win, mean, S};
+    SeriesView sv{off, pad, unit, win, mean, S, scale};
     tr.mark("contract");
     if (p->precision == HOS_PREC_SIMT_FP32) {
         C3SimtParams cp{g, sv, y32, partials};
@@ -551,11 +613,10 @@ static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int6
         note_plan(g, 1);
     } else {
         C3TcParams cp{g, sv, y32, hi, lo, partials, status, wait_limit_ns(), tc_products(p->precision), l.plane_len,
-                      debug_slots(l.slots)};
-        const bool tf32 = tf32_kind(p->precision);
-        HOS_CUDA_TRY(launch_c3_tc(tf32, 3, cp, g.G, st));
-        g_last_contraction = p->precision == HOS_PREC_TF32 ? "c3_tcgen05_tf32"
-                             : (tf32 ? "c3_tcgen05_3xtf32" : "c3_tcgen05_split_bf16");
+                      debug_slots(l.slots), {}};
+        wait_hints(cp.hint);
+        HOS_CUDA_TRY(launch_c3_tc(tc_format(p->precision), 3, cp, g.G, st));
+        g_last_contraction = contraction_name(3, p->precision);
         note_plan(g, tc_products(p->precision));
     }
 
@@ -610,7 +671,8 @@ struct Plan4 {
     int Nf, W3, npb, nslices, pad_tail;
     bool tc;    // tensor-core m4 (split-bf16 / 3xTF32) instead of FP32 SIMT
     C3Geom g4;  // tensor-core geometry: tiles = blocks of 128 lag pairs, columns = w3
-    size_t status, off, pad, unit, win, mean, mpart, y32, hi, lo, bnd, xr, ilen, m4buf, c2, c2p, partials, grid, tw,
+    size_t status, off, pad, unit, win, mean, mpart, scale, smax, y32, hi, lo, bnd, xr, ilen, m4buf, c2, c2p, partials,
+        grid, tw,
         total;
     int c2s;        // slices per part of the c2 sums
     int64_t slots;  // partial slots of the tensor-core contraction
@@ -642,7 +704,9 @@ static C3Geom make_geom4(const hos_params* p, int G) {
     // FP32 accumulation loss: partials go to the reduction after every
     // chunk, and 3xTF32 chunks are 128 samples (48 MMA steps)
     g.flush = p->flush_chunks ? p->flush_chunks : 1;
-    g.kc = (p->precision == HOS_PREC_FP32) ? 128 : KC;
+    // (the same 48 MMA steps per partial for the split FP16 path: 256-sample chunks)
+    g.kc = p->chunk_len ? p->chunk_len
+                        : ((p->precision == HOS_PREC_FP32) ? 128 : (p->precision == HOS_PREC_SPLIT_FP16 ? 256 : KC));
     g.G = G;
     g.pad_tail = 128 + N + 128;
     return g;
@@ -699,6 +763,8 @@ static hos_status make_plan4(int op, const hos_params* p, int64_t n, Plan4& P, i
     P.win = o; o = al256(o + 8 * (size_t)(P.S + 1));
     P.mean = o; o = al256(o + 8 * (size_t)P.S);
     P.mpart = o; o = al256(o + 8 * (size_t)P.S * P.nslices);
+    P.scale = o; o = al256(o + 4 * (size_t)P.S);
+    P.smax = o; o = al256(o + 4 * (size_t)P.S);
     P.y32 = o; o = al256(o + 4 * (size_t)plane_len);
     P.c2 = o; o = al256(o + 8 * (size_t)P.S * (4 * L - 1));
     P.c2s = c2_slices(P.S, P.max_len);
@@ -760,8 +826,14 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
     void* lo = P.tc ? at<void>(ws, P.lo) : nullptr;
     // a slice's input pointer is its first own sample; its halos lie before and after
     const void* xs = sl ? static_cast<const uint8_t*>(x) + sl->halo_before * (dtype == HOS_F64 ? 8 : 4) : x;
+    float* scale = nullptr;
+    if (P.tc && p->precision == HOS_PREC_SPLIT_FP16) {
+        scale = at<float>(ws, P.scale);
+        HOS_CUDA_TRY(launch_series_scale(xs, dtype, off, mean, P.S, P.nslices, sl ? sl->halo_before : 0,
+                                         sl ? sl->halo_after : 0, FP16_TOP4, at<unsigned>(ws, P.smax), scale, st));
+    }
     HOS_CUDA_TRY(launch_planes(xs, dtype, off, pad, mean, p->L, P.tc ? plane_split(p->precision) : 0, y32, hi, lo,
-                               P.S, bx, st, sl ? sl->halo_before : 0, sl ? sl->halo_after : 0));
+                               P.S, bx, st, sl ? sl->halo_before : 0, sl ? sl->halo_after : 0, scale));
     tr.mark("contract");
     C4ReduceArgs r;
     r.window = p->window;
@@ -782,13 +854,12 @@ static hos_status run_c4(const void* x, int dtype, int64_t n, const Plan4& P, co
     double* c2 = at<double>(ws, P.c2);
     HOS_CUDA_TRY(launch_c2(y32, off, pad, P.S, p->L, P.c2s, c2, at<float2>(ws, P.c2p), st, sl ? 1 : 0,
                            sl ? sl->n_total : 0));
-    SeriesView sv{off, pad, unit, win, mean, P.S};
+    SeriesView sv{off, pad, unit, win, mean, P.S, scale};
     C3TcParams cp{P.g4, sv, y32, hi, lo, at<float>(ws, P.partials), at<int>(ws, P.status), wait_limit_ns(),
-                  tc_products(p->precision), P.plane_len, debug_slots(P.slots)};
-    const bool tf32 = tf32_kind(p->precision);
-    HOS_CUDA_TRY(launch_c3_tc(tf32, 4, cp, P.g4.G, st));
-    g_last_contraction = p->precision == HOS_PREC_TF32 ? "m4_tcgen05_tf32"
-                         : (tf32 ? "m4_tcgen05_3xtf32" : "m4_tcgen05_split_bf16");
+                  tc_products(p->precision), P.plane_len, debug_slots(P.slots), {}};
+    wait_hints(cp.hint);
+    HOS_CUDA_TRY(launch_c3_tc(tc_format(p->precision), 4, cp, P.g4.G, st));
+    g_last_contraction = contraction_name(4, p->precision);
     note_plan(P.g4, tc_products(p->precision));
     tr.mark("reduce");
     double* m4buf = at<double>(ws, P.m4buf);

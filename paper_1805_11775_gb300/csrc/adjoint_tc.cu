@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
     AdjSmem& sm = *reinterpret_cast<AdjSmem*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = P.L, K = P.kpad;
-    const uint32_t idesc = make_idesc(false, AU, AW);
+    const uint32_t idesc = make_idesc(FMT_BF16, AU, AW);
     const int64_t items = (int64_t)P.nb * P.nut;
     const int64_t it0 = range_begin(blockIdx.x, items, gridDim.x), it1 = range_begin(blockIdx.x + 1, items, gridDim.x);
 

@@ -22,9 +22,10 @@
 //       distance of the next 8 (resp. 4) samples.
 //   D = FP32 accumulator, 128 lanes x (widest tile) columns of TMEM.
 //
-// Precision: y = hi + lo (bf16 pair, or tf32 pair); Y is formed in FP32 and
-// split the same way; three products hi*hi + hi*lo + lo*hi per step (plain
-// TF32: hi*hi alone).
+// Precision: y = hi + lo (bf16 pair, f16 pair of the series scaled by a
+// power of two, or tf32 pair); Y is formed in FP32 (times the scale's square,
+// or cube for the fourth order) and split the same way; three products
+// hi*hi + hi*lo + lo*hi per step (plain TF32: hi*hi alone).
 //
 // Warp roles (320 threads, one CTA per SM, persistent, stream-K ranges):
 //   warps 0-3 builders (TMEM lane quadrants 0-3), warps 4-7 epilogue,
@@ -80,8 +81,9 @@ HOS_DEV void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 //          w1 = -L + 128a + m; columns are lags w2 of tile column b.
 // ORDER 4: rows of A are lag pairs p = 128a + m with w1 <= w2
 //          (T = y(i) y(i+w1) y(i+w2)); columns are lags w3 = -L + j.
-template <bool TF32, int ORDER>
+template <int FMT, int ORDER>
 __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
+    constexpr bool TF32 = FMT == FMT_TF32;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     C3Smem& sm = *reinterpret_cast<C3Smem*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -152,9 +154,16 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
             // rows i >= len carry y(i) = 0 (a time slice keeps its neighbour's
             // samples after it in the plane, for the lags only)
             const int64_t slen = P.ser.off[part.s + 1] - P.ser.off[part.s];
+            // the row factor carries the series' scale s to the power ORDER - 1 (times the
+            // window's s: the products come out scaled by s^ORDER, divided out in the reduction)
+            float sA = 1.0f;
+            if (P.ser.scale) {
+                const float sc = P.ser.scale[part.s];
+                sA = (ORDER == 3) ? sc * sc : sc * sc * sc;
+            }
             for (int64_t c = part.c0; c < part.c1 && ok; ++c, ++kc) {
                 const int buf = kc & 1;
-                ok = warp_wait(&sm.empty_b[buf], ((kc >> 1) & 1) ^ 1, abort, P.status, lim, 2000);
+                ok = warp_wait(&sm.empty_b[buf], ((kc >> 1) & 1) ^ 1, abort, P.status, lim, P.hint[0]);
                 if (!ok) break;
                 const int64_t i0 = c * csz;
                 const int64_t wb = base + i0 + col0;                     // plane index of window start
@@ -188,7 +197,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                     bulk_g2s(sm.ya[buf][0], P.y32 + ab, yab, &sm.tma_bar);
                     bulk_g2s(sm.yi_raw, P.y32 + ib_al, yib, &sm.tma_bar);
                 }
-                ok = warp_wait(&sm.tma_bar, tph, abort, P.status, lim, 1000);
+                ok = warp_wait(&sm.tma_bar, tph, abort, P.status, lim, P.hint[0]);
                 if (!ok) {
                     // the copies just issued still land in this CTA's shared memory:
                     // wait for them (bounded, whatever the abort flag says) before exiting
@@ -203,7 +212,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                 {   // realign y(i0 + t) so that builders can use 16-byte broadcast loads
                     const int ish = (int)(ib - ib_al);
                     for (int t = lane; t < csz; t += 32)
-                        sm.yi[buf][t] = (i0 + t < slen) ? sm.yi_raw[ish + t] : 0.0f;
+                        sm.yi[buf][t] = (i0 + t < slen) ? sm.yi_raw[ish + t] * sA : 0.0f;
                 }
                 if constexpr (ORDER == 4) {
                     // shifted copies: ya[buf][s][j] = ya[buf][0][j + s].  The last
@@ -281,7 +290,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
             }
             for (int64_t c = part.c0; c < part.c1 && ok; ++c, ++kc) {
                 const int buf = kc & 1;
-                ok = warp_wait(&sm.full_b[buf], (kc >> 1) & 1, abort, P.status, lim, 2000);
+                ok = warp_wait(&sm.full_b[buf], (kc >> 1) & 1, abort, P.status, lim, P.hint[1]);
                 if (!ok) break;
                 const float* ya = sm.ya[buf][0] + (ORDER == 3 ? m : 0);
                 // ORDER 4: y(i + w1) and y(i + w2) from the copies that put them on
@@ -291,7 +300,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                 const float* yi = sm.yi[buf];
                 for (int kb = 0; kb < csz / KB; ++kb, ++ks) {
                     const int st = (int)(ks % (uint32_t)nst);
-                    ok = warp_wait(&sm.empty_a[st], ((ks / (uint32_t)nst) & 1) ^ 1, abort, P.status, lim, 1000);
+                    ok = warp_wait(&sm.empty_a[st], ((ks / (uint32_t)nst) & 1) ^ 1, abort, P.status, lim, P.hint[1]);
                     if (!ok) break;
                     tc_fence_after();  // the MMAs that read this stage have completed
                     uint32_t H[32], Lw[32];
@@ -321,13 +330,12 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                                 const float4 v = pi4[q], a1 = q1[q], a2 = q2[q];
                                 const float p0 = v.x * a1.x * a2.x, p1 = v.y * a1.y * a2.y;
                                 const float p2 = v.z * a1.z * a2.z, p3 = v.w * a1.w * a2.w;
-                                const uint32_t h0 = pack_bf16x2(p0, p1), h1 = pack_bf16x2(p2, p3);
+                                const uint32_t h0 = pack2<FMT>(p0, p1), h1 = pack2<FMT>(p2, p3);
+                                const float2 f0 = unpack2<FMT>(h0), f1 = unpack2<FMT>(h1);
                                 H[2 * q] = h0;
                                 H[2 * q + 1] = h1;
-                                Lw[2 * q] = pack_bf16x2(p0 - __uint_as_float(h0 << 16),
-                                                        p1 - __uint_as_float(h0 & 0xFFFF0000u));
-                                Lw[2 * q + 1] = pack_bf16x2(p2 - __uint_as_float(h1 << 16),
-                                                            p3 - __uint_as_float(h1 & 0xFFFF0000u));
+                                Lw[2 * q] = pack2<FMT>(p0 - f0.x, p1 - f0.y);
+                                Lw[2 * q + 1] = pack2<FMT>(p2 - f1.x, p3 - f1.y);
                             }
                         }
                     } else if constexpr (TF32) {
@@ -349,12 +357,12 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                             const float4 v = pi4[q];
                             const float p0 = v.x * pa[4 * q], p1 = v.y * pa[4 * q + 1];
                             const float p2 = v.z * pa[4 * q + 2], p3 = v.w * pa[4 * q + 3];
-                            const uint32_t h0 = pack_bf16x2(p0, p1), h1 = pack_bf16x2(p2, p3);
+                            const uint32_t h0 = pack2<FMT>(p0, p1), h1 = pack2<FMT>(p2, p3);
+                            const float2 f0 = unpack2<FMT>(h0), f1 = unpack2<FMT>(h1);
                             H[2 * q] = h0;
                             H[2 * q + 1] = h1;
-                            Lw[2 * q] = pack_bf16x2(p0 - __uint_as_float(h0 << 16), p1 - __uint_as_float(h0 & 0xFFFF0000u));
-                            Lw[2 * q + 1] =
-                                pack_bf16x2(p2 - __uint_as_float(h1 << 16), p3 - __uint_as_float(h1 & 0xFFFF0000u));
+                            Lw[2 * q] = pack2<FMT>(p0 - f0.x, p1 - f0.y);
+                            Lw[2 * q + 1] = pack2<FMT>(p2 - f1.x, p3 - f1.y);
                         }
                     }
                     const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + a_base + (uint32_t)st * 64u;
@@ -375,7 +383,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
         bool ok = true;
         while (ok && walk.next(part)) {
             const uint32_t ab_ = it % nacc;
-            ok = warp_wait(&sm.acc_full[ab_], (it / nacc) & 1, abort, P.status, lim, 20000);
+            ok = warp_wait(&sm.acc_full[ab_], (it / nacc) & 1, abort, P.status, lim, P.hint[2]);
             if (!ok) break;
             tc_fence_after();
             float* dst = P.partials + part.slot * (int64_t)(TILE_M * N) + m;
@@ -400,14 +408,14 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
         while (ok && walk.next(part)) {
             const uint32_t ab_ = it % nacc;
             const uint32_t dacc = tmem + ab_ * acc_cols;  // this part's accumulator
-            const uint32_t idesc = make_idesc(TF32, TILE_M, 32 * geo.tile_w32[part.t]);  // N = the tile's width
-            ok = mbar_wait(&sm.acc_empty[ab_], ((it / nacc) & 1) ^ 1, abort, P.status, lim);
+            const uint32_t idesc = make_idesc(FMT, TILE_M, 32 * geo.tile_w32[part.t]);  // N = the tile's width
+            ok = mbar_wait(&sm.acc_empty[ab_], ((it / nacc) & 1) ^ 1, abort, P.status, lim, P.hint[3]);
             if (!ok) break;
             tc_fence_after();
             uint32_t acc = 0;
             for (int64_t c = part.c0; c < part.c1 && ok; ++c, ++kc) {
                 const int buf = kc & 1;
-                ok = mbar_wait(&sm.full_b[buf], (kc >> 1) & 1, abort, P.status, lim);
+                ok = mbar_wait(&sm.full_b[buf], (kc >> 1) & 1, abort, P.status, lim, P.hint[3]);
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t wh = wh0 + (uint32_t)buf * WIN_BYTES, wl = wl0 + (uint32_t)buf * WIN_BYTES;
@@ -417,7 +425,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
                 const uint64_t bh0 = make_sdesc(wh, LBO, SBO), bl0 = make_sdesc(wl, LBO, SBO);
                 for (int kb = 0; kb < csz / KB; ++kb, ++ks) {
                     const int st = (int)(ks % (uint32_t)nst);
-                    ok = mbar_wait(&sm.full_a[st], (ks / (uint32_t)nst) & 1, abort, P.status, lim);
+                    ok = mbar_wait(&sm.full_a[st], (ks / (uint32_t)nst) & 1, abort, P.status, lim, P.hint[3]);
                     if (!ok) break;
                     tc_fence_after();
 #pragma unroll
@@ -463,7 +471,7 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
 
 
 
-template <bool TF32, int ORDER>
+template <int FMT, int ORDER>
 static cudaError_t launch_one(const C3TcParams& p, int G, cudaStream_t st) {
     // at least 116 KB so that exactly one CTA (and one 512-column TMEM
     // allocation) lands on each SM
@@ -471,16 +479,20 @@ static cudaError_t launch_one(const C3TcParams& p, int G, cudaStream_t st) {
     // The attribute belongs to the current device (and context): set it on
     // every launch, so that any device the caller switches to has it.
     cudaError_t e =
-        cudaFuncSetAttribute(c3_tc_kernel<TF32, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(c3_tc_kernel<FMT, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    c3_tc_kernel<TF32, ORDER><<<G, 320, smem, st>>>(p);
+    c3_tc_kernel<FMT, ORDER><<<G, 320, smem, st>>>(p);
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_c3_tc(bool tf32, int order, const C3TcParams& p, int G, cudaStream_t st) {
-    if (order == 4) return tf32 ? launch_one<true, 4>(p, G, st) : launch_one<false, 4>(p, G, st);
-    return tf32 ? launch_one<true, 3>(p, G, st) : launch_one<false, 3>(p, G, st);
+cudaError_t launch_c3_tc(int fmt, int order, const C3TcParams& p, int G, cudaStream_t st) {
+    if (order == 4) {
+        if (fmt == FMT_TF32) return launch_one<FMT_TF32, 4>(p, G, st);
+        return fmt == FMT_F16 ? launch_one<FMT_F16, 4>(p, G, st) : launch_one<FMT_BF16, 4>(p, G, st);
+    }
+    if (fmt == FMT_TF32) return launch_one<FMT_TF32, 3>(p, G, st);
+    return fmt == FMT_F16 ? launch_one<FMT_F16, 3>(p, G, st) : launch_one<FMT_BF16, 3>(p, G, st);
 }
 
 }  // namespace hos

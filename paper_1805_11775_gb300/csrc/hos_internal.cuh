@@ -67,6 +67,7 @@ struct C3Geom {
 //   unit[S+1] : prefix of work-unit cost  (ktot * nchunks(s))
 //   win[S+1]  : prefix of flush windows (ntiles * ceil(nchunks(s) / flush))
 //   mean[S]   : FP64 mean removed from each series
+//   scale[S]  : power-of-two scale of each series' FP16 planes (nullptr: 1)
 struct SeriesView {
     const int64_t* off;
     const int64_t* pad;
@@ -74,7 +75,11 @@ struct SeriesView {
     const int64_t* win;
     const double* mean;
     int S;
+    const float* scale = nullptr;
 };
+
+// Operand formats of the tensor-core contraction.
+enum { FMT_BF16 = 0, FMT_F16 = 1, FMT_TF32 = 2 };
 
 HOS_HD int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 HOS_HD int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
@@ -234,16 +239,33 @@ HOS_DEV bool mbar_try(uint64_t* bar, uint32_t parity, uint32_t hint_ns = 0) {
     return ok != 0;
 }
 
+// Test the phase without suspending the thread.
+HOS_DEV bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// hint_ns of a wait that polls with test_wait and never suspends
+constexpr uint32_t WAIT_SPIN = 0xFFFFFFFFu;
+
 // Wait for the phase with the given parity to complete.  Gives up (returning
 // false) when another thread of the CTA has raised `abort`, or after
 // `limit_ns` nanoseconds, in which case it raises `abort` and records
-// HOS_ERR_TIMEOUT in the device status word.
+// HOS_ERR_TIMEOUT in the device status word.  hint_ns: 0 lets try_wait
+// suspend the thread for the system's own time limit, WAIT_SPIN polls with
+// test_wait (no suspension), other values are try_wait's suspend-time hint.
 HOS_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* status, uint64_t limit_ns,
                        uint32_t hint_ns = 0) {
-    if (mbar_try(bar, parity)) return true;
+    if (hint_ns == WAIT_SPIN ? mbar_test(bar, parity) : mbar_try(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     for (uint32_t it = 1;; ++it) {
-        if (mbar_try(bar, parity, hint_ns)) return true;
+        if (hint_ns == WAIT_SPIN ? mbar_test(bar, parity) : mbar_try(bar, parity, hint_ns)) return true;
         if ((it & 7u) == 0) {
             if (*abort) return false;
             if (global_timer_ns() - t0 > limit_ns) {
@@ -327,9 +349,9 @@ HOS_DEV void mma_commit(uint64_t* bar) {
 
 // Instruction descriptor: FP32 accumulate, A and B K-major, M = 128.
 //   bits 4-5 D format (1 = F32); 7-9 A format; 10-12 B format
-//   (kind::f16: 1 = BF16; kind::tf32: 2 = TF32); 17-22 N>>3; 24-28 M>>4.
-HOS_HD uint32_t make_idesc(bool tf32, int M, int N) {
-    const uint32_t fmt = tf32 ? 2u : 1u;
+//   (kind::f16: 0 = F16, 1 = BF16; kind::tf32: 2 = TF32); 17-22 N>>3; 24-28 M>>4.
+HOS_HD uint32_t make_idesc(int fmt_kind, int M, int N) {
+    const uint32_t fmt = fmt_kind == FMT_TF32 ? 2u : (fmt_kind == FMT_BF16 ? 1u : 0u);
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
@@ -373,6 +395,30 @@ HOS_DEV uint32_t pack_bf16x2(float lo, float hi) {
     uint32_t r;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
     return r;
+}
+// f16x2 pack, round to nearest even; `lo` goes to the low half.
+HOS_DEV uint32_t pack_f16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+// The two halves of a packed pair as floats (exact: every f16 and bf16 value is a float).
+template <int FMT>
+HOS_DEV float2 unpack2(uint32_t v) {
+    if constexpr (FMT == FMT_BF16) {
+        return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xFFFF0000u));
+    } else {
+        float a, b;
+        asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\tcvt.f32.f16 %0, l;\n\tcvt.f32.f16 %1, h;\n\t}"
+            : "=f"(a), "=f"(b)
+            : "r"(v));
+        return make_float2(a, b);
+    }
+}
+template <int FMT>
+HOS_DEV uint32_t pack2(float lo, float hi) {
+    if constexpr (FMT == FMT_BF16) return pack_bf16x2(lo, hi);
+    else return pack_f16x2(lo, hi);
 }
 // tf32 rounding (nearest, ties away), result as an f32 bit pattern
 HOS_DEV uint32_t to_tf32(float x) {

@@ -19,6 +19,8 @@ struct C3TcParams {
     int products;       // 3: hi*hi + hi*lo + lo*hi (split precision); 1: hi*hi (plain TF32)
     int64_t plane_len;  // samples in each plane (bounds of the HOS_DEBUG_BOUNDS build)
     int64_t n_slots;    // partial slots in the workspace (same)
+    // waits of each role (mbar_wait's hint_ns): producer, builders, epilogue, MMA issuer
+    uint32_t hint[4];
 };
 
 struct C3SimtParams {
@@ -130,9 +132,15 @@ cudaError_t launch_plan_series(int mode, int64_t n, int64_t seg, const int64_t* 
 cudaError_t launch_mean(const void* x, int dtype, const int64_t* off, int S, int nslices, double* part,
                         int remove_mean, double* mean, cudaStream_t st);
 // ext_lo / ext_hi: halo samples before / after a time slice (see planes_kernel)
+// split 3 (f16 planes) scales each series by scale[s]
 cudaError_t launch_planes(const void* x, int dtype, const int64_t* off, const int64_t* pad, const double* mean, int L,
                           int split, float* y32, void* hi, void* lo, int S, int blocks_x, cudaStream_t st,
-                          int64_t ext_lo = 0, int64_t ext_hi = 0);
+                          int64_t ext_lo = 0, int64_t ext_hi = 0, const float* scale = nullptr);
+// scale[s] = 2^(top - e), 2^e the least power of two >= max |x - mean| over
+// series s and the ext_lo / ext_hi halo samples around it (mx: S scratch words)
+cudaError_t launch_series_scale(const void* x, int dtype, const int64_t* off, const double* mean, int S,
+                                int nslices, int64_t ext_lo, int64_t ext_hi, int top, unsigned* mx, float* scale,
+                                cudaStream_t st);
 cudaError_t launch_window_c3(const double* c3, int L, int window, int Nf, double scale, float* wtab, float* grid,
                              cudaStream_t st);
 cudaError_t launch_gather_parts(const void* x, int dtype, int64_t K, int64_t m, int64_t step, void* out,
@@ -145,7 +153,8 @@ cudaError_t launch_part_prep(const void* x, int dtype, int64_t K, int64_t M, int
 cudaError_t launch_direct_smooth(const float2* F, int K, int M, int M3, float2* R, float2* Cw, float2* B,
                                  cudaStream_t st);
 cudaError_t launch_slice_mean(const double* sum, int64_t n_total, int remove_mean, double* mean, cudaStream_t st);
-cudaError_t launch_c3_tc(bool tf32, int order, const C3TcParams& p, int G, cudaStream_t st);
+// fmt: FMT_BF16, FMT_F16 or FMT_TF32 (operand format); order 3 (c3) or 4 (m4)
+cudaError_t launch_c3_tc(int fmt, int order, const C3TcParams& p, int G, cudaStream_t st);
 cudaError_t launch_c3_simt(const C3SimtParams& p, int G, cudaStream_t st);
 // max_len: longest series (or part); it only sets how threads split the work.
 cudaError_t launch_reduce3(const Reduce3Params& p, int groups, int64_t max_len, int64_t* bnd, TileRec* rec,

@@ -141,7 +141,8 @@ __global__ void slice_mean_kernel(const double* __restrict__ sum, int64_t n_tota
 
 // y = x - mean into the padded planes.  blockIdx.y = series; the block's
 // x-slices stride over that series' padded block [pad[s], pad[s+1]).
-// split: 0 = none (f32 plane only), 1 = bf16 hi/lo, 2 = tf32 hi/lo (as f32).
+// split: 0 = none (f32 plane only), 1 = bf16 hi/lo, 2 = tf32 hi/lo (as f32),
+// 3 = f16 hi/lo of the series scaled by scale[s] (a power of two: exact).
 // A time slice of a longer series also carries ext_lo samples before and
 // ext_hi after it (its neighbours' halo, x[o0 - ext_lo ..]); they go into the
 // zero padding on either side (ext_lo, ext_hi <= L).
@@ -149,12 +150,13 @@ template <typename T>
 __global__ void planes_kernel(const T* __restrict__ x, const int64_t* __restrict__ off,
                               const int64_t* __restrict__ pad, const double* __restrict__ mean, int L, int split,
                               int64_t ext_lo, int64_t ext_hi, float* __restrict__ y32, void* __restrict__ hi,
-                              void* __restrict__ lo) {
+                              void* __restrict__ lo, const float* __restrict__ scale) {
     const int s = blockIdx.y;
     const int64_t p0 = pad[s], p1 = pad[s + 1];
     const int64_t o0 = off[s], len = off[s + 1] - o0;
     const double mu = mean[s];
-    if (split == 1) {
+    if (split == 1 || split == 3) {
+        const float sc = (split == 3) ? scale[s] : 1.0f;
         // four samples per thread: one 16-byte y store and 8-byte hi and lo
         // stores (p0 and p1 are multiples of 64)
         for (int64_t p = p0 + 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); p < p1;
@@ -168,15 +170,22 @@ __global__ void planes_kernel(const T* __restrict__ x, const int64_t* __restrict
             }
 #pragma unroll
             for (int c = 0; c < 4; c += 2) {
-                const __nv_bfloat16 h0 = __float2bfloat16_rn(v[c]), h1 = __float2bfloat16_rn(v[c + 1]);
-                const __nv_bfloat16 l0 = __float2bfloat16_rn(v[c] - __bfloat162float(h0));
-                const __nv_bfloat16 l1 = __float2bfloat16_rn(v[c + 1] - __bfloat162float(h1));
-                hv[c / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                lv[c / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                if (split == 1) {
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(v[c]), h1 = __float2bfloat16_rn(v[c + 1]);
+                    const __nv_bfloat16 l0 = __float2bfloat16_rn(v[c] - __bfloat162float(h0));
+                    const __nv_bfloat16 l1 = __float2bfloat16_rn(v[c + 1] - __bfloat162float(h1));
+                    hv[c / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                    lv[c / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                } else {
+                    const float a = v[c] * sc, b = v[c + 1] * sc;
+                    hv[c / 2] = pack_f16x2(a, b);
+                    const float2 f = unpack2<FMT_F16>(hv[c / 2]);
+                    lv[c / 2] = pack_f16x2(a - f.x, b - f.y);
+                }
             }
             *reinterpret_cast<float4*>(y32 + p) = make_float4(v[0], v[1], v[2], v[3]);
-            *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(hi) + p) = make_uint2(hv[0], hv[1]);
-            *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(lo) + p) = make_uint2(lv[0], lv[1]);
+            *reinterpret_cast<uint2*>(reinterpret_cast<uint16_t*>(hi) + p) = make_uint2(hv[0], hv[1]);
+            *reinterpret_cast<uint2*>(reinterpret_cast<uint16_t*>(lo) + p) = make_uint2(lv[0], lv[1]);
         }
         return;
     }
@@ -198,6 +207,63 @@ __global__ void planes_kernel(const T* __restrict__ x, const int64_t* __restrict
             reinterpret_cast<uint32_t*>(lo)[p] = to_tf32(v - __uint_as_float(hb));
         }
     }
+}
+
+// Power-of-two scale of each series' FP16 planes.  Pass 1: the largest
+// |x - mean| over the series (and a time slice's halos), per slice of
+// samples, as the bit pattern of a non-negative float (whose integer order is
+// the float order: atomicMax finds the maximum exactly, in any order).  Pass 2:
+// scale = 2^(top - e) with 2^e the least power of two at or above the maximum,
+// so that every |scale y| <= 2^top; 1 for a series of zeros.
+template <typename T>
+__global__ void absmax_kernel(const T* __restrict__ x, const int64_t* __restrict__ off,
+                              const double* __restrict__ mean, int64_t ext_lo, int64_t ext_hi, int nslices,
+                              unsigned* __restrict__ mx) {
+    __shared__ float sh[256];
+    const int s = blockIdx.y;
+    const int64_t o0 = off[s] - ext_lo, len = off[s + 1] - off[s] + ext_lo + ext_hi;
+    const int64_t per = ceil_div(len, nslices);
+    const int64_t b0 = (int64_t)blockIdx.x * per, b1 = b0 + per < len ? b0 + per : len;
+    const double mu = mean[s];
+    float m = 0.0f;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) m = fmaxf(m, fabsf((float)((double)x[o0 + i] - mu)));
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int d = blockDim.x / 2; d > 0; d >>= 1) {
+        if (threadIdx.x < d) sh[threadIdx.x] = fmaxf(sh[threadIdx.x], sh[threadIdx.x + d]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(mx + s, __float_as_uint(sh[0]));
+}
+
+__global__ void scale_kernel(const unsigned* __restrict__ mx, int S, int top, float* __restrict__ scale) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const float m = __uint_as_float(mx[s]);
+    int e = 0;
+    if (m > 0.0f) {
+        frexpf(m, &e);                      // m = f 2^e, 0.5 <= f < 1: m < 2^e
+        if (ldexpf(1.0f, e - 1) == m) --e;  // m a power of two: 2^e = m
+    }
+    scale[s] = (m > 0.0f) ? ldexpf(1.0f, top - e) : 1.0f;
+}
+
+cudaError_t launch_series_scale(const void* x, int dtype, const int64_t* off, const double* mean, int S,
+                                int nslices, int64_t ext_lo, int64_t ext_hi, int top, unsigned* mx, float* scale,
+                                cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned) * (size_t)S, st);
+    if (e != cudaSuccess) return e;
+    dim3 g((unsigned)nslices, (unsigned)S);
+    if (dtype == HOS_F64)
+        absmax_kernel<double><<<g, 256, 0, st>>>((const double*)x, off, mean, ext_lo, ext_hi, nslices, mx);
+    else
+        absmax_kernel<float><<<g, 256, 0, st>>>((const float*)x, off, mean, ext_lo, ext_hi, nslices, mx);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    scale_kernel<<<(unsigned)ceil_div(S, 256), 256, 0, st>>>(mx, S, top, scale);
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_plan_series(int mode, int64_t n, int64_t seg, const int64_t* d_user_off, int S, int L, int ntiles,
@@ -226,14 +292,14 @@ cudaError_t launch_mean(const void* x, int dtype, const int64_t* off, int S, int
 
 cudaError_t launch_planes(const void* x, int dtype, const int64_t* off, const int64_t* pad, const double* mean, int L,
                           int split, float* y32, void* hi, void* lo, int S, int blocks_x, cudaStream_t st,
-                          int64_t ext_lo, int64_t ext_hi) {
+                          int64_t ext_lo, int64_t ext_hi, const float* scale) {
     dim3 g((unsigned)blocks_x, (unsigned)S);
     if (dtype == HOS_F64)
         planes_kernel<double><<<g, 256, 0, st>>>((const double*)x, off, pad, mean, L, split, ext_lo, ext_hi, y32, hi,
-                                                 lo);
+                                                 lo, scale);
     else
         planes_kernel<float><<<g, 256, 0, st>>>((const float*)x, off, pad, mean, L, split, ext_lo, ext_hi, y32, hi,
-                                                lo);
+                                                lo, scale);
     count_launch();
     return cudaGetLastError();
 }

@@ -21,10 +21,13 @@ constexpr int REDUCE_THREADS = 256;
 // per-CTA slots.  (s, t) covers the cost range [ub, ub + nch k); CTA g's
 // first unit is the first chunk starting at or after bnd[g]: chunk
 // ceil((bnd[g] - ub) / k), inside the tile when bnd[g] <= ub + (nch - 1) k.
-// Also 1/n of each series' time average.  bnd (G + 1 values) is staged in
-// shared memory once per block; both CTA searches are binary searches there.
+// Also 1/n of each series' time average (divided by scale^scale_pow when the
+// planes were scaled: the contraction's products carry the series' scale to
+// that power).  bnd (G + 1 values) is staged in shared memory once per block;
+// both CTA searches are binary searches there.
 __global__ void part_ranges_kernel(const C3Geom geo, const SeriesView sv, const int64_t* __restrict__ bnd_g,
-                                   TileRec* __restrict__ rec, float2* __restrict__ inv_len, int64_t norm_len) {
+                                   TileRec* __restrict__ rec, float2* __restrict__ inv_len, int64_t norm_len,
+                                   int scale_pow) {
     extern __shared__ int64_t bnd[];
     for (int g = threadIdx.x; g <= geo.G; g += blockDim.x) bnd[g] = bnd_g[g];
     __syncthreads();
@@ -38,7 +41,10 @@ __global__ void part_ranges_kernel(const C3Geom geo, const SeriesView sv, const 
     // longer series) that series' length
     const int64_t nl = norm_len > 0 ? norm_len : len;
     if (t == 0) {  // as a double-float
-        const double inv = len > 0 ? 1.0 / (double)nl : 0.0;
+        double sp = 1.0;
+        if (sv.scale)
+            for (int k = 0; k < scale_pow; ++k) sp *= (double)sv.scale[s];  // a power of two: exact
+        const double inv = len > 0 ? 1.0 / ((double)nl * sp) : 0.0;
         const float h = (float)inv;
         inv_len[s] = make_float2(h, (float)(inv - (double)h));
     }
@@ -395,13 +401,13 @@ static int window_split(const C3Geom& geo, int64_t max_len) {
 }
 
 static cudaError_t launch_part_index(const C3Geom& geo, const SeriesView& sv, int64_t* bnd, TileRec* rec,
-                                     float2* inv_len, int64_t norm_len, cudaStream_t st) {
+                                     float2* inv_len, int64_t norm_len, int scale_pow, cudaStream_t st) {
     bounds_kernel<<<(unsigned)ceil_div(geo.G + 1, 256), 256, 0, st>>>(sv.unit, sv.S, geo.G, bnd);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     part_ranges_kernel<<<(unsigned)ceil_div((int64_t)sv.S * geo.ntiles, 256), 256, sizeof(int64_t) * (geo.G + 1), st>>>(
-        geo, sv, bnd, rec, inv_len, norm_len);
+        geo, sv, bnd, rec, inv_len, norm_len, scale_pow);
     count_launch();
     return cudaGetLastError();
 }
@@ -409,7 +415,7 @@ static cudaError_t launch_part_index(const C3Geom& geo, const SeriesView& sv, in
 cudaError_t launch_m4_tile_reduce(const C3Geom& geo, const SeriesView& sv, int64_t max_len, const float* partials,
                                   int64_t* bnd, TileRec* rec, float2* inv_len, double* m4buf, cudaStream_t st,
                                   int64_t norm_len) {
-    cudaError_t e = launch_part_index(geo, sv, bnd, rec, inv_len, norm_len, st);
+    cudaError_t e = launch_part_index(geo, sv, bnd, rec, inv_len, norm_len, 4, st);
     if (e != cudaSuccess) return e;
     const int64_t nvec = (int64_t)TILE_M * geo.tile_n / 4;
     const int gsplit = window_split(geo, max_len);
@@ -442,7 +448,7 @@ __global__ void timeout_selftest_kernel(int* status, uint64_t limit_ns) {
 
 cudaError_t launch_reduce3(const Reduce3Params& p, int groups, int64_t max_len, int64_t* bnd, TileRec* rec,
                            float2* inv_len, float* wtab, cudaStream_t st) {
-    cudaError_t e = launch_part_index(p.geom, p.ser, bnd, rec, inv_len, p.norm_len, st);
+    cudaError_t e = launch_part_index(p.geom, p.ser, bnd, rec, inv_len, p.norm_len, 3, st);
     if (e != cudaSuccess) return e;
     window_table_kernel<<<(unsigned)ceil_div(4 * p.geom.L, 256), 256, 0, st>>>(p.geom.L, p.window, wtab);
     count_launch();

@@ -69,27 +69,29 @@ def key(device_name: str, op: str, L: int, n_total: int, n_series: int, precisio
 
 
 def lookup(op: str, L: int, n_total: int, n_series: int, precision: str):
-    """(tile_n, flush_chunks) tuned for this shape on the current device, or None."""
+    """(tile_n, flush_chunks, chunk_len) tuned for this shape on the current device, or None."""
     import torch
     if not torch.cuda.is_available():
         return None
     k = key(torch.cuda.get_device_name(), op, L, n_total, n_series, precision, library_version())
     v = _load().get(k)
-    return (int(v["tile_n"]), int(v["flush_chunks"])) if v else None
+    return (int(v["tile_n"]), int(v["flush_chunks"]), int(v.get("chunk_len", 0))) if v else None
 
 
 def candidates(L: int, precision: str):
+    """(tile_n, flush_chunks, chunk_len) to time; chunk_len 0 is the automatic 1024."""
     two_l = 2 * L
     tiles = sorted({t for t in (128, 256) if t <= max(32, 1 << (two_l - 1).bit_length())} or {0})
-    flushes = (1, 2) if precision in ("fp32", "3xtf32") else (4, 8, 16, 32)
-    return [(t, f) for t in tiles for f in flushes]
+    if precision in ("fp32", "3xtf32"):
+        return [(t, f, c) for t in tiles for f in (1, 2) for c in (0, 512)]
+    return [(t, f, 0) for t in tiles for f in (4, 8, 16, 32)]
 
 
 def tune(run, op: str, L: int, n_total: int, n_series: int, precision: str, repeats: int = 5, store: bool = True):
-    """Time ``run(tile_n, flush_chunks)`` for every candidate; cache the best.
+    """Time ``run(tile_n, flush_chunks, chunk_len)`` for every candidate; cache the best.
 
     ``run`` enqueues one call on the current stream.  Returns
-    (best (tile_n, flush_chunks), {candidate: ms})."""
+    (best (tile_n, flush_chunks, chunk_len), {candidate: ms})."""
     import torch
     times = {}
     for cand in candidates(L, precision):
@@ -106,20 +108,20 @@ def tune(run, op: str, L: int, n_total: int, n_series: int, precision: str, repe
     if store:
         k = key(torch.cuda.get_device_name(), op, L, n_total, n_series, precision, library_version())
         with _lock:
-            _load()[k] = {"tile_n": best[0], "flush_chunks": best[1], "ms": times[best]}
+            _load()[k] = {"tile_n": best[0], "flush_chunks": best[1], "chunk_len": best[2], "ms": times[best]}
             _save()
     return best, times
 
 
 def tune_bispectrum(x, L: int, precision: str = "bf16", repeats: int = 5):
     import paper_1805_11775_gb300 as hos
-    return tune(lambda t, f: hos.bispectrum(x, L, precision=precision, tile_n=t, flush_chunks=f), "bispectrum", L,
-                x.numel(), 1, precision, repeats)
+    return tune(lambda t, f, c: hos.bispectrum(x, L, precision=precision, tile_n=t, flush_chunks=f, chunk_len=c),
+                "bispectrum", L, x.numel(), 1, precision, repeats)
 
 
 def tune_bispectrum_batched(values, offsets, L: int, precision: str = "bf16", repeats: int = 3, max_len=None):
     import paper_1805_11775_gb300 as hos
     S = len(offsets) - 1
-    return tune(lambda t, f: hos.bispectrum_batched(values, offsets, L, precision=precision, tile_n=t, flush_chunks=f,
-                                                    max_len=max_len), "bispectrum_batched", L, values.numel(), S,
-                precision, repeats)
+    return tune(lambda t, f, c: hos.bispectrum_batched(values, offsets, L, precision=precision, tile_n=t,
+                                                       flush_chunks=f, chunk_len=c, max_len=max_len),
+                "bispectrum_batched", L, values.numel(), S, precision, repeats)

@@ -67,8 +67,9 @@ def test_invalid_arguments_return_synchronously(lib):
     assert lib.hos_bispectrum(None, 1, 100, ctypes.byref(p), dummy, dummy, 1 << 20, None) == 1
     assert lib.hos_bispectrum(dummy, 7, 100, ctypes.byref(p), dummy, dummy, 1 << 20, None) == 1
     assert lib.hos_bispectrum(dummy, 1, 0, ctypes.byref(p), dummy, dummy, 1 << 20, None) == 1
-    for bad in (dict(L=0), dict(L=32, nfft=10), dict(L=32, precision=4), dict(L=32, precision=-1), dict(L=32, window=5),
-                dict(L=32, tile_n=48), dict(L=32, segment_len=-1)):
+    for bad in (dict(L=0), dict(L=32, nfft=10), dict(L=32, precision=5), dict(L=32, precision=-1), dict(L=32, window=5),
+                dict(L=32, tile_n=48), dict(L=32, segment_len=-1),
+                dict(L=32, chunk_len=100), dict(L=32, chunk_len=2048), dict(L=32, chunk_len=-64)):
         q = _params(**bad)
         assert lib.hos_bispectrum(dummy, 1, 100, ctypes.byref(q), dummy, dummy, 1 << 20, None) == 1, bad
     big = _params(L=2048)
@@ -118,7 +119,7 @@ def test_trispectrum_backward_workspace_and_limits(lib):
     b = workspace_size(_native.OP_TRISPECTRUM_BACKWARD, n, 1, n, _params(L=64, precision=1))
     assert b > a
     for bad in (_params(L=32, precision="fp32"), _params(L=32, precision="tf32"), _params(L=32, precision="simt"),
-                _params(L=65, precision=1),
+                _params(L=32, precision="fp16"), _params(L=65, precision=1),
                 _params(L=32, precision=1, window=1), _params(L=32, precision=1, segment_len=1000)):
         with pytest.raises(HosError):
             workspace_size(_native.OP_TRISPECTRUM_BACKWARD, n, 1, n, bad)

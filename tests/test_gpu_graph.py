@@ -36,7 +36,7 @@ def _replay_equals_eager(fn):
     assert np.array_equal(a.view(np.uint8), out.cpu().numpy().view(np.uint8))
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp32", "simt"])
+@pytest.mark.parametrize("prec", ["bf16", "fp32", "simt", "fp16"])
 def test_bispectrum_graph(hos, prec):
     x = torch.from_numpy(hos_synth.ar2(20000, 41)).cuda()
     ws = hos.Workspace()
@@ -52,7 +52,7 @@ def test_bispectrum_overlap_graph(hos):
                                                 workspace=ws))
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+@pytest.mark.parametrize("prec", ["bf16", "fp32", "fp16"])
 def test_trispectrum_graph(hos, prec):
     x = torch.from_numpy(hos_synth.ma(30000, 43)).cuda()
     ws = hos.Workspace()

@@ -13,8 +13,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no GPU", allow_module_level=True)
 
-TOL = {"bf16": 1e-4, "fp32": 1e-5, "simt": 1e-5}
-TOL4 = {"bf16": 2e-4, "fp32": 2e-5, "simt": 2e-5}
+TOL = {"bf16": 1e-4, "fp32": 1e-5, "simt": 1e-5, "fp16": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -29,7 +28,7 @@ def normwise(got, ref):
     return np.abs(np.asarray(got, dtype=np.complex128) - ref).max() / np.abs(ref).max()
 
 
-@pytest.mark.parametrize("prec", ["simt", "fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["simt", "fp32", "bf16", "fp16"])
 @pytest.mark.parametrize("n,m,o,L,N,rm", [(5000, 1024, 256, 16, 32, True), (3001, 700, 699, 8, 20, False),
                                           (2100, 1000, 1, 32, 64, True), (9000, 2048, 1024, 40, 80, True)])
 def test_bispectrum_overlap_matches_oracle(hos, oracle, prec, n, m, o, L, N, rm):
@@ -40,17 +39,17 @@ def test_bispectrum_overlap_matches_oracle(hos, oracle, prec, n, m, o, L, N, rm)
     assert normwise(got, ref) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["simt", "fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["simt", "fp32", "bf16", "fp16"])
 def test_trispectrum_overlap_matches_oracle(hos, oracle, prec):
     n, m, o, L = 4000, 1000, 500, 8
     x = hos_synth.ma(n, 31)
     ref = oracle.trispectrum_overlap(x, L, 2 * L, segment_len=m, overlap=o)
     got = hos.trispectrum(torch.from_numpy(x).cuda(), L, precision=prec, segment_len=m,
                           segment_overlap=o).cpu().numpy()
-    assert normwise(got, ref) <= TOL4[prec]
+    assert normwise(got, ref) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 def test_cumulants_overlap_match_oracle(hos, oracle, prec):
     n, m, o = 3000, 800, 300
     x = hos_synth.ar2(n, 33)
@@ -60,7 +59,7 @@ def test_cumulants_overlap_match_oracle(hos, oracle, prec):
     assert np.abs(c3 - r3).max() <= TOL[prec] * np.abs(r3).max()
     c4 = hos.cumulant4(torch.from_numpy(x).cuda(), L4, precision=prec, segment_len=m, segment_overlap=o).cpu().numpy()
     r4 = oracle.cumulant_overlap(x, L4, 4, segment_len=m, overlap=o)[:2 * L4, :2 * L4, :2 * L4]
-    assert np.abs(c4 - r4).max() <= TOL4[prec] * np.abs(r4).max()
+    assert np.abs(c4 - r4).max() <= TOL[prec] * np.abs(r4).max()
 
 
 def test_short_series_with_overlap_is_one_part(hos):

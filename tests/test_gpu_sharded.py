@@ -17,7 +17,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no GPU", allow_module_level=True)
 
-TOL = {"bf16": 1e-4, "fp32": 1e-5, "simt": 1e-5}
+TOL = {"bf16": 1e-4, "fp32": 1e-5, "simt": 1e-5, "fp16": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -55,7 +55,7 @@ def test_series_sum_is_the_fp64_sum(hos):
         assert abs(got - ref) <= 1e-13 * max(1.0, np.abs(x).sum())
 
 
-@pytest.mark.parametrize("prec", ["simt", "fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["simt", "fp32", "bf16", "fp16"])
 @pytest.mark.parametrize("n,L,world", [(5000, 32, 2), (7001, 40, 3), (3000, 128, 5), (100, 32, 5), (2049, 8, 8)])
 def test_slices_sum_to_the_oracle_c3(hos, oracle, prec, n, L, world):
     x = hos_synth.ar2(n, 13 * n + world)
@@ -64,7 +64,7 @@ def test_slices_sum_to_the_oracle_c3(hos, oracle, prec, n, L, world):
     assert np.abs(got - ref).max() <= TOL[prec] * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 def test_slices_match_one_call_and_the_oracle_bispectrum(hos, oracle, prec):
     """Slices of a 2^16-sample series at L = 64 (several chunks per slice,
     ragged slice ends): c3 against one hos_cumulant3 call, B from the summed
@@ -108,7 +108,6 @@ def test_slice_argument_errors(hos):
 
 
 # ------------------------------------------------------------------ fourth order
-TOL4 = {"bf16": 2e-4, "fp32": 2e-5}
 
 
 def emulate_ranks4(hos, x, L, world, prec, remove_mean=True):
@@ -128,7 +127,7 @@ def emulate_ranks4(hos, x, L, world, prec, remove_mean=True):
     return m4, c2
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 @pytest.mark.parametrize("n,L,world", [(6000, 8, 2), (9001, 16, 3), (4000, 32, 5), (300, 4, 7)])
 def test_fourth_order_slices_match_the_oracle(hos, oracle, prec, n, L, world):
     """Joined slices: c4 (from the joined m4 and c2) against the oracle's c4,
@@ -137,7 +136,7 @@ def test_fourth_order_slices_match_the_oracle(hos, oracle, prec, n, L, world):
     m4, c2 = emulate_ranks4(hos, x, L, world, prec)
     T = hos.trispectrum_from_moments(torch.from_numpy(m4).cuda(), torch.from_numpy(c2).cuda(), L).cpu().numpy()
     ref = oracle.trispectrum(x, L, 2 * L)
-    assert normwise(T, ref) <= TOL4[prec]
+    assert normwise(T, ref) <= TOL[prec]
     c2f = lambda t: c2[t + 2 * L - 1]  # noqa: E731
     r4 = oracle.c4(oracle.demean(x), L)[:2 * L, :2 * L, :2 * L]
     c4 = np.empty_like(m4)
@@ -146,7 +145,7 @@ def test_fourth_order_slices_match_the_oracle(hos, oracle, prec, n, L, world):
             w3 = np.arange(-L, L)
             c4[w1 + L, w2 + L] = (m4[w1 + L, w2 + L] - c2f(w1) * c2[w3 - w2 + 2 * L - 1]
                                   - c2f(w2) * c2[w3 - w1 + 2 * L - 1] - c2[w3 + 2 * L - 1] * c2f(w2 - w1))
-    assert np.abs(c4 - r4).max() <= TOL4[prec] * np.abs(r4).max()
+    assert np.abs(c4 - r4).max() <= TOL[prec] * np.abs(r4).max()
 
 
 def test_fourth_order_sharded_single_rank_is_the_trispectrum(hos):

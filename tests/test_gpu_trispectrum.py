@@ -1,7 +1,7 @@
 """GPU parity of the trispectrum path (c2, m4 over symmetric lag pairs, the
 c2*c2 correction, window, 3-axis transform) against the FP64 oracle.
 Normwise tolerances as for the bispectrum: split-bf16 tensor cores 1e-4,
-3xTF32 tensor cores 1e-5, FP32 SIMT 1e-5."""
+3xTF32 and split-FP16 tensor cores 1e-5, FP32 SIMT 1e-5."""
 import math
 
 import numpy as np
@@ -14,8 +14,8 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no GPU", allow_module_level=True)
 
-TOL = {"bf16": 1e-4, "fp32": 1e-5, "simt": 1e-5}
-PRECS = ["simt", "fp32", "bf16"]
+TOL = {"bf16": 1e-4, "fp32": 1e-5, "simt": 1e-5, "fp16": 1e-5}
+PRECS = ["simt", "fp32", "bf16", "fp16"]
 
 
 @pytest.fixture(scope="module")
@@ -98,7 +98,7 @@ def test_trispectrum_transform_sizes(hos, oracle, N):
     assert normwise(got, ref) <= TOL["fp32"]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 def test_trispectrum_batched_matches_oracle_per_series(hos, oracle, prec):
     """Series of uneven length (one empty, one shorter than the lag range) in
     one call: each spectrum against the oracle, and against a single call."""
@@ -113,7 +113,7 @@ def test_trispectrum_batched_matches_oracle_per_series(hos, oracle, prec):
             assert np.abs(got[s]).max() == 0.0
             continue
         ref = oracle.trispectrum(x, L, N)
-        assert normwise(got[s], ref) <= (3 * TOL[prec] if prec == "fp32" else TOL[prec])
+        assert normwise(got[s], ref) <= TOL[prec]
         one = hos.trispectrum(torch.from_numpy(x).cuda(), L, nfft=N, precision=prec).cpu().numpy()
         assert normwise(got[s], one) <= 2 * TOL[prec]
 

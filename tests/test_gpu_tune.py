@@ -39,6 +39,7 @@ def test_tuner_stores_and_applies_its_choice(hos, oracle, tmp_path, monkeypatch)
     got = hos.bispectrum_batched(vd, offs, L, precision="bf16").cpu().numpy()
     plan = hos.last_plan()
     assert f"tile_n={best[0]} " in plan and f"flush={best[1]} " in plan, plan
+    assert f"kc={best[2] or 1024} " in plan, plan
     for s in (0, 7, 23, 47):
         ref = oracle.bispectrum(vals[offs[s]:offs[s + 1]], L, N)
         assert np.abs(got[s] - ref).max() / np.abs(ref).max() <= 1e-4, s

@@ -39,7 +39,7 @@ def check(lib, op, n, p, ctas, offsets=None):
 
 def test_workload_plans(lib):
     from paper_1805_11775_gb300 import make_params
-    for prec in ("bf16", "fp32", "tf32", "simt"):
+    for prec in ("bf16", "fp32", "tf32", "simt", "fp16"):
         ctas = 608 if prec == "simt" else 152
         for n, L in ((2048, 32), (1 << 21, 256), (1 << 18, 128)):
             rc, m = check(lib, OP_BISPECTRUM, n, make_params(L, precision=prec), ctas)
@@ -53,35 +53,46 @@ def test_workload_plans(lib):
         assert rc == 0, (prec, m)
 
 
-def test_long_plan_has_diagonal_start_tiles(lib):
-    """L = 256: row blocks of 512, 384, 256 and 128 columns -> four 256-wide
-    and two 128-wide tiles, cost 40 per chunk (1280 columns / 32)."""
+def test_tile_schemes(lib, monkeypatch):
+    """L = 256.  Full width (default): each row block's 256-wide tiles start at
+    the multiple of 256 at or below its diagonal block, six tiles, cost 48
+    per chunk.  Diagonal start: row blocks of 512, 384, 256 and 128 columns,
+    four 256-wide and two 128-wide tiles, cost 40 (1280 columns / 32)."""
     from paper_1805_11775_gb300 import make_params
+    rc, m = check(lib, OP_BISPECTRUM, 1 << 21, make_params(256), 152)
+    assert rc == 0 and "6 tiles (cost 48 per chunk)" in m, m
+    monkeypatch.setenv("HOS_TILE_SCHEME", "diagonal")
     rc, m = check(lib, OP_BISPECTRUM, 1 << 21, make_params(256), 152)
     assert rc == 0 and "6 tiles (cost 40 per chunk)" in m, m
     rc, m = check(lib, OP_BISPECTRUM, 1 << 18, make_params(128), 152)
     assert rc == 0 and "2 tiles (cost 12 per chunk)" in m, m
 
 
-def test_random_single_series_plans(lib):
+@pytest.mark.parametrize("scheme", ["full", "diagonal"])
+def test_random_single_series_plans(lib, monkeypatch, scheme):
     from paper_1805_11775_gb300 import make_params
+    monkeypatch.setenv("HOS_TILE_SCHEME", scheme)
     rng = np.random.default_rng(7)
     for _ in range(300):
         L = int(rng.choice([1, 2, 3, 5, 16, 31, 32, 40, 64, 100, 127, 128, 129, 200, 256, 300, 512, 700, 1024]))
         n = int(rng.choice([1, 2, 100, 1023, 1024, 1025, 5000, 40000, 300000]))
-        prec = str(rng.choice(["bf16", "fp32", "tf32", "simt"]))
+        prec = str(rng.choice(["bf16", "fp32", "tf32", "simt", "fp16"]))
         tile = int(rng.choice([0, 0, 32, 64, 128, 256]))
         flush = int(rng.choice([0, 0, 1, 3, 16, 33]))
         win = str(rng.choice(["parzen", "parzen_sym", "rect"]))
         seg = int(rng.choice([0, 0, 0, 700, 4096]))
         ctas = int(rng.choice([1, 2, 7, 148, 152, 608]))
-        p = make_params(L, precision=prec, tile_n=tile, flush_chunks=flush, window=win, segment_len=seg)
+        kc = int(rng.choice([0, 0, 64, 256, 512, 960]))
+        p = make_params(L, precision=prec, tile_n=tile, flush_chunks=flush, window=win, segment_len=seg,
+                        chunk_len=kc)
         rc, m = check(lib, OP_BISPECTRUM, n, p, ctas)
-        assert rc == 0, (L, n, prec, tile, flush, win, seg, ctas, m)
+        assert rc == 0, (L, n, prec, tile, flush, win, seg, ctas, kc, m)
 
 
-def test_random_batched_plans(lib):
+@pytest.mark.parametrize("scheme", ["full", "diagonal"])
+def test_random_batched_plans(lib, monkeypatch, scheme):
     from paper_1805_11775_gb300 import make_params
+    monkeypatch.setenv("HOS_TILE_SCHEME", scheme)
     rng = np.random.default_rng(11)
     for _ in range(60):
         S = int(rng.integers(1, 300))
@@ -89,9 +100,10 @@ def test_random_batched_plans(lib):
         lens[rng.random(S) < 0.2] = 0  # empty series
         offs = np.concatenate([[0], np.cumsum(lens)])
         L = int(rng.choice([4, 32, 64, 100, 128, 256]))
-        prec = str(rng.choice(["bf16", "fp32", "tf32", "simt"]))
+        prec = str(rng.choice(["bf16", "fp32", "tf32", "simt", "fp16"]))
         ctas = int(rng.choice([1, 5, 152, 608]))
-        p = make_params(L, precision=prec, flush_chunks=int(rng.choice([0, 1, 2, 16])))
+        p = make_params(L, precision=prec, flush_chunks=int(rng.choice([0, 1, 2, 16])),
+                        chunk_len=int(rng.choice([0, 0, 128, 512])))
         rc, m = check(lib, OP_BATCHED, 0, p, ctas, offs)
         assert rc == 0, (S, L, prec, ctas, m)
 
@@ -102,8 +114,9 @@ def test_random_fourth_order_plans(lib):
     for _ in range(80):
         L = int(rng.choice([1, 2, 4, 8, 16, 20, 32, 64]))
         n = int(rng.choice([1, 50, 1000, 4096, 65536, 100001]))
-        prec = str(rng.choice(["bf16", "fp32", "tf32"]))
+        prec = str(rng.choice(["bf16", "fp32", "tf32", "fp16"]))
         seg = int(rng.choice([0, 0, 1500]))
         ctas = int(rng.choice([1, 3, 152]))
-        rc, m = check(lib, OP_TRISPECTRUM, n, make_params(L, precision=prec, segment_len=seg), ctas)
+        kc = int(rng.choice([0, 0, 64, 256]))
+        rc, m = check(lib, OP_TRISPECTRUM, n, make_params(L, precision=prec, segment_len=seg, chunk_len=kc), ctas)
         assert rc == 0, (L, n, prec, seg, ctas, m)

@@ -7,9 +7,10 @@ from paper_1805_11775_gb300 import tune
 
 
 def test_candidates_respect_precision_and_lag_range():
-    assert all(f <= 2 for _, f in tune.candidates(256, "fp32"))
-    assert {t for t, _ in tune.candidates(256, "bf16")} == {128, 256}
-    assert {t for t, _ in tune.candidates(40, "bf16")} == {128}
+    assert all(f <= 2 for _, f, _ in tune.candidates(256, "fp32"))
+    assert {c for _, _, c in tune.candidates(256, "fp32")} == {0, 512}
+    assert {t for t, _, _ in tune.candidates(256, "bf16")} == {128, 256}
+    assert {t for t, _, _ in tune.candidates(40, "bf16")} == {128}
 
 
 def test_key_buckets_sizes():
