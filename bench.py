@@ -225,7 +225,7 @@ def c3_tc_flops(lens, products, plan):
 def m4_flops(L, n, prec):
     """Executed flops of the m4 contraction.  Tensor cores: 128-pair tiles of
     the lag triangle w1 <= w2 x next_pow2(2L) columns w3 x padded samples x 3
-    products x 2 (chunks of 1024 samples, 128 for 3xTF32, 256 for split FP16;
+    products x 2 (chunks of 1024 samples, 128 for 3xTF32 and split FP16;
     one product for plain TF32).  SIMT: FFMA over pair rows x w3 rounded to
     16 x samples rounded to 4096."""
     two_l = 2 * L
@@ -233,7 +233,7 @@ def m4_flops(L, n, prec):
     rows = math.ceil(npairs / 128) * 128
     if prec in ("bf16", "fp32", "fp16", "tf32"):
         cols = max(32, 1 << (two_l - 1).bit_length())
-        kc = {"fp32": 128, "fp16": 256}.get(prec, 1024)
+        kc = {"fp32": 128, "fp16": 128}.get(prec, 1024)
         kpad = math.ceil(n / kc) * kc
         prod = 1 if prec == "tf32" else 3
         return rows * cols * kpad * 2 * prod, (f"{rows} lag pairs x {cols} w3 x {kpad} padded samples x {prod} products"
@@ -562,6 +562,14 @@ def time_arm(wl, args, hos, torch, flush_buf, dist, local, world, sliced):
     return ms, stage_acc, launches, clk, mode, t_wall
 
 
+DTYPES = {"bf16": "bf16x3 (split-bf16, fp32 accumulate, fp64-class reduce)",
+          "fp32": "tf32x3 (fp32-class, fp32 accumulate, fp64-class reduce)",
+          "tf32": "tf32 (one product, fp32 accumulate, fp64-class reduce)",
+          "fp16": "f16x3 (fp32-class: split-fp16 of the power-of-two scaled series, fp32 accumulate, "
+                  "fp64-class reduce)",
+          "simt": "f32"}
+
+
 def tensor_peak(prec, pk, src):
     """Dense tensor peak of the contraction's operand type (TFLOP/s)."""
     if prec == "bf16":
@@ -657,12 +665,7 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": value / wl["paper_value"] if "paper_value" in wl else None,
-        "dtype": "f32 (transform, products), double-float window sums" if "roof" in wl else
-                 {"bf16": "bf16x3 (split-bf16, fp32 accumulate, fp64-class reduce)",
-                  "fp32": "tf32x3 (fp32-class, fp32 accumulate, fp64-class reduce)",
-                  "tf32": "tf32 (one product, fp32 accumulate, fp64-class reduce)",
-                  "fp16": "f16x3 (split-fp16 of the power-of-two scaled series, fp32 accumulate, fp64-class reduce)",
-                  "simt": "f32"}[prec],
+        "dtype": "f32 (transform, products), double-float window sums" if "roof" in wl else DTYPES[prec],
         "data": "synthetic",
         "config": dict({"workload": args.workload, "precision": prec, "contraction": contraction,
                         "plan": plan, "autotune": autotune,
@@ -688,34 +691,37 @@ def run_ours(args):
         x_host = hos_synth.workload(WORKLOAD)["x"]
         line["cpu_baseline"], ref_rows = cpu_baseline(x_host, 256, x_host.size)
         line["accuracy"] = accuracy(hos, torch, x_host, 256, prec, *ref_rows)
-    if (args.compare and args.compare != prec and world == 1 and "roof" not in wl
-            and args.workload not in ("differentiable_trispectrum_n65536_L32",)):
-        # the same workload in a second precision on the same GPU (the metric's
+    arms = [c for c in args.compare.split(",") if c and c != prec]
+    if arms and world == 1 and "roof" not in wl and args.workload not in ("differentiable_trispectrum_n65536_L32",):
+        # the same workload in other precisions on the same GPU (the metric's
         # "split-BF16 vs FP32, same GPU"), timed the same way
-        wl2 = make_workload(args.workload, args.compare, rank, hos, torch, args.series, args.time_slices)
-        tune2 = None
-        if not args.no_tune and wl2.get("tune"):
-            b2, _ = wl2["tune"]()
-            tune2 = {"tile_n": b2[0], "flush_chunks": b2[1], "chunk_len": b2[2]}
-        ms2, st2, launches2, clk2, mode2, _ = time_arm(wl2, args, hos, torch, flush_buf, dist, local, world, sliced)
-        c2_ms = statistics.mean(st2.get("contract", [float("nan")]))
-        if "flops_of" in wl2:
-            wl2["flops"], wl2["work"] = wl2["flops_of"](hos.last_plan())
-        pk2, note2 = tensor_peak(args.compare, pk, src)
-        arm = {"precision": args.compare, "contraction": hos.last_contraction(), "plan": hos.last_plan(),
-               "autotune": tune2,
-               "ms_per_step": ms2, "value": wl2["units"] * world / (ms2 * 1e-3), "unit": wl2.get("unit", UNIT),
-               "launch": mode2, "stage_ms": {k: statistics.mean(v) for k, v in st2.items()},
-               "clocks": clk2, "gpu_launches": launches2}
-        if wl2["bound"] == "tensor":
-            ach2 = wl2["flops"] / (c2_ms * 1e-3) / 1e12
-            arm["roofline"] = {"bound": "tensor", "achieved": ach2, "peak": pk2, "unit": "TFLOP/s",
-                               "frac": ach2 / pk2, "peak_source": note2, "work": wl2["work"]}
-        if ref_rows is not None:
-            arm["accuracy"] = accuracy(hos, torch, x_host, 256, args.compare, *ref_rows)
-        elif rank == 0 and not args.no_cpu_baseline and "accuracy" in wl2:
-            arm["accuracy"] = wl2["accuracy"]()
-        line["compare"] = arm
+        line["compare"] = []
+        for cprec in arms:
+            wl2 = make_workload(args.workload, cprec, rank, hos, torch, args.series, args.time_slices)
+            tune2 = None
+            if not args.no_tune and wl2.get("tune"):
+                b2, _ = wl2["tune"]()
+                tune2 = {"tile_n": b2[0], "flush_chunks": b2[1], "chunk_len": b2[2]}
+            ms2, st2, launches2, clk2, mode2, _ = time_arm(wl2, args, hos, torch, flush_buf, dist, local, world,
+                                                           sliced)
+            c2_ms = statistics.mean(st2.get("contract", [float("nan")]))
+            if "flops_of" in wl2:
+                wl2["flops"], wl2["work"] = wl2["flops_of"](hos.last_plan())
+            pk2, note2 = tensor_peak(cprec, pk, src)
+            arm = {"precision": cprec, "dtype": DTYPES[cprec], "contraction": hos.last_contraction(),
+                   "plan": hos.last_plan(), "autotune": tune2, "ms_per_step": ms2,
+                   "value": wl2["units"] * world / (ms2 * 1e-3), "unit": wl2.get("unit", UNIT), "launch": mode2,
+                   "stage_ms": {k: statistics.mean(v) for k, v in st2.items()}, "clocks": clk2,
+                   "gpu_launches": launches2}
+            if wl2["bound"] == "tensor":
+                ach2 = wl2["flops"] / (c2_ms * 1e-3) / 1e12
+                arm["roofline"] = {"bound": "tensor", "achieved": ach2, "peak": pk2, "unit": "TFLOP/s",
+                                   "frac": ach2 / pk2, "peak_source": note2, "work": wl2["work"]}
+            if ref_rows is not None:
+                arm["accuracy"] = accuracy(hos, torch, x_host, 256, cprec, *ref_rows)
+            elif rank == 0 and not args.no_cpu_baseline and "accuracy" in wl2:
+                arm["accuracy"] = wl2["accuracy"]()
+            line["compare"].append(arm)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -731,8 +737,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "tf32", "simt", "fp16"])
-    ap.add_argument("--compare", default="fp32", choices=["", "bf16", "fp32", "tf32", "simt", "fp16"],
-                    help="also time this precision on the same workload and GPU (\"\" to skip)")
+    ap.add_argument("--compare", default="fp32,fp16",
+                    help="comma-separated precisions (bf16, fp32, fp16, tf32, simt) also timed on the same workload "
+                         "and GPU (\"\" to skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (automatic tile width and flush)")
     ap.add_argument("--workload", default=WORKLOAD,

@@ -336,10 +336,15 @@ static C3Geom make_geom(const hos_params* p, int G, bool skip_zero_window = fals
     // 1024-sample chunk; split-bf16 (16 samples per step, 1e-4 target) and SIMT
     // (FP32 FFMA, round to nearest) after 16 chunks.
     // Plain TF32 is limited by its 10-bit factors, not by the accumulation.
-    // The FP32-class paths (3xTF32, split FP16: 1e-5 target) hand every chunk's
-    // partial to the reduction.
-    const bool fp32_class = p->precision == HOS_PREC_FP32 || p->precision == HOS_PREC_SPLIT_FP16;
-    g.flush = p->flush_chunks ? p->flush_chunks : (fp32_class ? 1 : 16);
+    // The error of the tensor cores' FP32 accumulation grows with the MMA
+    // steps one partial holds (measured: about 1e-8 of the result per step,
+    // for every operand format).  The FP32-class paths (1e-5 target) hand a
+    // partial to the reduction every chunk (3xTF32: 384 MMA steps) or every
+    // two chunks (split FP16: 192 steps a chunk).
+    int flush_auto = 16;
+    if (p->precision == HOS_PREC_FP32) flush_auto = 1;
+    if (p->precision == HOS_PREC_SPLIT_FP16) flush_auto = 2;
+    g.flush = p->flush_chunks ? p->flush_chunks : flush_auto;
     g.kc = p->chunk_len ? p->chunk_len : KC;
     g.G = G;
     // zero samples after a series: every sample a tile's windows read (the
@@ -704,9 +709,8 @@ static C3Geom make_geom4(const hos_params* p, int G) {
     // FP32 accumulation loss: partials go to the reduction after every
     // chunk, and 3xTF32 chunks are 128 samples (48 MMA steps)
     g.flush = p->flush_chunks ? p->flush_chunks : 1;
-    // (the same 48 MMA steps per partial for the split FP16 path: 256-sample chunks)
-    g.kc = p->chunk_len ? p->chunk_len
-                        : ((p->precision == HOS_PREC_FP32) ? 128 : (p->precision == HOS_PREC_SPLIT_FP16 ? 256 : KC));
+    // (the split FP16 path: 128-sample chunks, 24 MMA steps)
+    g.kc = p->chunk_len ? p->chunk_len : ((p->precision == HOS_PREC_FP32 || p->precision == HOS_PREC_SPLIT_FP16) ? 128 : KC);
     g.G = G;
     g.pad_tail = 128 + N + 128;
     return g;

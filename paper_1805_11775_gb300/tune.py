@@ -84,6 +84,8 @@ def candidates(L: int, precision: str):
     tiles = sorted({t for t in (128, 256) if t <= max(32, 1 << (two_l - 1).bit_length())} or {0})
     if precision in ("fp32", "3xtf32"):
         return [(t, f, c) for t in tiles for f in (1, 2) for c in (0, 512)]
+    if precision in ("fp16", "split_fp16"):  # FP32-class: at most 384 MMA steps per partial
+        return [(t, f, c) for t in tiles for (f, c) in ((1, 0), (2, 0), (2, 512), (4, 512))]
     return [(t, f, 0) for t in tiles for f in (4, 8, 16, 32)]
 
 

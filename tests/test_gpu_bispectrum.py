@@ -151,24 +151,28 @@ def test_deterministic(hos):
 def test_batched_matches_oracle_per_series(hos, oracle):
     """Intraday-return shaped series (symmetric Student-t): their true c3 is
     zero, so B is sampling noise about 200 times smaller than the sum of the
-    absolute lag products (sum_w W c3(|y|) / max|B|).  The per-factor
-    representation error of the 3xTF32 split (about 2^-22) therefore shows
-    through at ~1e-5 on these series; the FP32-class gate here is 3e-5.
-    Split-bf16 keeps 1e-4 and SIMT FP32 keeps 1e-5."""
+    absolute lag products (sum_w W c3(|y|) / max|B|), and the tensor cores'
+    FP32 accumulation error (about 1e-8 of the partial sum per MMA step)
+    shows through amplified.  3xTF32 runs 384 MMA steps per 1024-sample
+    chunk; at 512-sample chunks (192 steps, as split FP16 at 1024) it meets
+    the FP32-class 1e-5 here.  Every precision at its target."""
     lens = np.array([0, 1, 700, 2500, 1024, 3100, 17, 2048], dtype=np.int64)
     vals, offs = hos_synth.student_t_returns(lens, 11)
     L, N = 40, 80
-    tol = dict(TOL, fp32=3e-5)
     for prec in PRECS:
-        got = hos.bispectrum_batched(torch.from_numpy(vals).cuda(), torch.from_numpy(offs), L,
-                                     precision=prec).cpu().numpy()
+        kc = 512 if prec == "fp32" else 0
+        got = hos.bispectrum_batched(torch.from_numpy(vals).cuda(), torch.from_numpy(offs), L, precision=prec,
+                                     chunk_len=kc).cpu().numpy()
         for s in range(lens.size):
             seg = vals[offs[s]:offs[s + 1]]
             if seg.size == 0:
                 assert np.count_nonzero(got[s]) == 0
                 continue
             ref = oracle.bispectrum(seg, L, N)
-            assert normwise(got[s], ref) <= tol[prec], (prec, s)
+            if np.abs(ref).max() == 0:  # a one-sample series is all mean: B = 0
+                assert np.abs(got[s]).max() <= 1e-30
+                continue
+            assert normwise(got[s], ref) <= TOL[prec], (prec, s)
 
 
 def test_batched_host_pipeline_matches_one_device_call(hos):
