@@ -229,8 +229,8 @@ hos_status hos_bispectrum_backward(const void* d_x, int32_t dtype, int64_t n, co
                                    const void* d_dB, void* d_dx, void* ws, size_t ws_bytes, hos_stream_t stream);
 
 /* Adjoint of hos_trispectrum (one part only, segment_len = 0; L <= 64;
- * window PARZEN or RECT; precision SPLIT_BF16 only -- anything else returns
- * HOS_ERR_UNSUPPORTED): the gradient of a real loss l through T.
+ * window PARZEN or RECT; precision SPLIT_BF16 or SPLIT_FP16 -- anything else
+ * returns HOS_ERR_UNSUPPORTED): the gradient of a real loss l through T.
  *   d_dT : nfft^3 complex64 holding dl/dRe T + i dl/dIm T, [k1][k2][k3]
  *   d_dx : n values, same dtype as d_x, receives dl/dx (overwritten)
  * Steps, the chain rule in reverse through the forward (the Problem

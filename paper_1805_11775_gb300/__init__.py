@@ -533,7 +533,7 @@ def bispectrum_ad(x, L, nfft=0, precision="bf16", window="parzen", remove_mean=T
 def trispectrum_backward(x, dT, L, nfft=0, precision="bf16", window="parzen", remove_mean=True, workspace=None,
                          stream=None):
     """dl/dx given dT = dl/dRe T + i dl/dIm T (nfft^3).  Split-bf16 tensor-core
-    adjoint only (precision "bf16"), L <= 64, one part."""
+    adjoint only (precision "bf16" or "fp16"), L <= 64, one part."""
     torch = _torch()
     xd, host = _prepare(x)
     p = make_params(L, nfft, precision, window, remove_mean, 0)

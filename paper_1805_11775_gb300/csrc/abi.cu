@@ -237,8 +237,10 @@ static hos_status check_params(const hos_params* p, int op) {
         return p->segment_len != 0 ? HOS_ERR_INVALID_ARG : HOS_ERR_UNSUPPORTED;
     if ((op == HOS_OP_BISPECTRUM_BACKWARD || op == HOS_OP_TRISPECTRUM_BACKWARD) && p->segment_len != 0)
         return HOS_ERR_UNSUPPORTED;
-    // the trispectrum adjoint runs on the split-bf16 tensor-core contraction only
-    if (op == HOS_OP_TRISPECTRUM_BACKWARD && p->precision != HOS_PREC_SPLIT_BF16) return HOS_ERR_UNSUPPORTED;
+    // the trispectrum adjoint runs on the tensor cores in split precision (bf16 or FP16) only
+    if (op == HOS_OP_TRISPECTRUM_BACKWARD && p->precision != HOS_PREC_SPLIT_BF16 &&
+        p->precision != HOS_PREC_SPLIT_FP16)
+        return HOS_ERR_UNSUPPORTED;
     if ((op == HOS_OP_BISPECTRUM_BATCHED || op == HOS_OP_TRISPECTRUM_BATCHED) && p->segment_len != 0)
         return HOS_ERR_INVALID_ARG;
     return HOS_OK;
@@ -895,9 +897,9 @@ struct PlanB {
     C3Geom g;
     int Nf, nslices;
     int64_t nctas;
-    bool tc;  // tensor-core adjoint (split-bf16, L <= 128)
-    size_t status, off, pad, unit, win, mean, mpart, y32, hi, lo, gc, gs, gsb, t1, t2p, gbuf, gmean, gmpart, tw,
-        total;
+    bool tc;  // tensor-core adjoint (split-bf16 or split FP16, L <= 128)
+    size_t status, off, pad, unit, win, mean, mpart, sc, smx, y32, hi, lo, gc, gs, gsb, t1, t2p, gbuf, gmean, gmpart,
+        tw, total;
 };
 
 static hos_status make_planb(const hos_params* p, int64_t n, PlanB& P) {
@@ -907,7 +909,7 @@ static hos_status make_planb(const hos_params* p, int64_t n, PlanB& P) {
     P.g = make_geom(p, 1);
     // the adjoint reads y(u + w1) windows up to 2L + 256 samples past a row tile
     if (P.g.pad_tail < twoL + 320) P.g.pad_tail = twoL + 320;
-    P.tc = (p->precision == HOS_PREC_SPLIT_BF16) && adjoint_tc_supported(L);
+    P.tc = (p->precision == HOS_PREC_SPLIT_BF16 || p->precision == HOS_PREC_SPLIT_FP16) && adjoint_tc_supported(L);
     P.Nf = p->nfft ? p->nfft : twoL;
     P.nslices = mean_slices(n, 1);
     P.nctas = ceil_div(n, ADJ_ROWS_PER_CTA);
@@ -920,6 +922,8 @@ static hos_status make_planb(const hos_params* p, int64_t n, PlanB& P) {
     P.win = o; o = al256(o + 16);
     P.mean = o; o = al256(o + 8);
     P.mpart = o; o = al256(o + 8 * (size_t)P.nslices);
+    P.sc = o; o = al256(o + 8);
+    P.smx = o; o = al256(o + 8);
     P.y32 = o; o = al256(o + 4 * (size_t)plane_len);
     P.hi = o; o = al256(o + (P.tc ? 2 * (size_t)plane_len + 64 : 0));
     P.lo = o; o = al256(o + (P.tc ? 2 * (size_t)plane_len + 64 : 0));
@@ -940,8 +944,8 @@ static hos_status make_planb(const hos_params* p, int64_t n, PlanB& P) {
 struct PlanB4 {
     C3Geom g;
     int Nf, nslices;
-    size_t status, off, pad, unit, win, mean, mpart, y32, hi, lo, c2, c2p, gc, gs, gsb, gc2, t1, t2p, gbuf, gmean,
-        gmpart, tw, total;
+    size_t status, off, pad, unit, win, mean, mpart, sc, smx, y32, hi, lo, c2, c2p, gc, gs, gsb, gc2, t1, t2p, gbuf,
+        gmean, gmpart, tw, total;
     int c2s;
 };
 
@@ -964,6 +968,8 @@ static hos_status make_planb4(const hos_params* p, int64_t n, PlanB4& P) {
     P.win = o; o = al256(o + 16);
     P.mean = o; o = al256(o + 8);
     P.mpart = o; o = al256(o + 8 * (size_t)P.nslices);
+    P.sc = o; o = al256(o + 8);
+    P.smx = o; o = al256(o + 8);
     P.y32 = o; o = al256(o + 4 * (size_t)plane_len);
     P.hi = o; o = al256(o + 2 * (size_t)plane_len + 64);
     P.lo = o; o = al256(o + 2 * (size_t)plane_len + 64);
@@ -1416,7 +1422,14 @@ hos_status hos_bispectrum_backward(const void* d_x, int32_t dtype, int64_t n, co
     if (bx > 65535) bx = 65535;
     void* hi = P.tc ? at<void>(ws, P.hi) : nullptr;
     void* lo = P.tc ? at<void>(ws, P.lo) : nullptr;
-    HOS_CUDA_TRY(launch_planes(d_x, dtype, off, pad, at<double>(ws, P.mean), L, P.tc ? 1 : 0, y32, hi, lo, 1, bx, st));
+    // split FP16: sc = {series scale, Gs scale} (powers of two), the series' now
+    const bool f16 = P.tc && p->precision == HOS_PREC_SPLIT_FP16;
+    float* sc = f16 ? at<float>(ws, P.sc) : nullptr;
+    if (f16)
+        HOS_CUDA_TRY(launch_series_scale(d_x, dtype, off, at<double>(ws, P.mean), 1, P.nslices, 0, 0, FP16_TOP3,
+                                         at<unsigned>(ws, P.smx), sc, st));
+    HOS_CUDA_TRY(launch_planes(d_x, dtype, off, pad, at<double>(ws, P.mean), L, P.tc ? plane_split(p->precision) : 0,
+                               y32, hi, lo, 1, bx, st, 0, 0, sc));
     tr.mark("transform");
     float2* tw = at<float2>(ws, P.tw);
     float2* gc = at<float2>(ws, P.gc);
@@ -1432,11 +1445,14 @@ hos_status hos_bispectrum_backward(const void* d_x, int32_t dtype, int64_t n, co
     float* g = at<float>(ws, P.gbuf);
     if (P.tc) {
         HOS_CUDA_TRY(launch_gs(gc, Nf, L, p->window, scale, at<float>(ws, P.gs), st));
+        if (f16)
+            HOS_CUDA_TRY(launch_flat_scale(at<float>(ws, P.gs), (int64_t)4 * L * L, FP16_TOP3,
+                                           at<unsigned>(ws, P.smx) + 1, sc + 1, st));
         HOS_CUDA_TRY(launch_adjoint_tc(y32, reinterpret_cast<const uint16_t*>(hi), reinterpret_cast<const uint16_t*>(lo),
                                        n, L, at<float>(ws, P.gs), at<uint8_t>(ws, P.gsb), at<float>(ws, P.t1),
                                        at<float>(ws, P.t2p), g, at<int>(ws, P.status), wait_limit_ns(), sm_count(),
-                                       st));
-        g_last_contraction = "adjoint_tcgen05_split_bf16";
+                                       st, f16 ? FMT_F16 : FMT_BF16, sc));
+        g_last_contraction = f16 ? "adjoint_tcgen05_split_fp16" : "adjoint_tcgen05_split_bf16";
     } else {
         HOS_CUDA_TRY(launch_adjoint(yS, n, L, gc, Nf, p->window, scale, at<float>(ws, P.gs), at<float>(ws, P.t1),
                                     at<float>(ws, P.t2p), g, st));
@@ -1474,7 +1490,13 @@ hos_status hos_trispectrum_backward(const void* d_x, int32_t dtype, int64_t n, c
     if (bx > 65535) bx = 65535;
     void* hi = at<void>(ws, P.hi);
     void* lo = at<void>(ws, P.lo);
-    HOS_CUDA_TRY(launch_planes(d_x, dtype, off, pad, at<double>(ws, P.mean), L, 1, y32, hi, lo, 1, bx, st));
+    const bool f16 = p->precision == HOS_PREC_SPLIT_FP16;
+    float* sc = f16 ? at<float>(ws, P.sc) : nullptr;
+    if (f16)
+        HOS_CUDA_TRY(launch_series_scale(d_x, dtype, off, at<double>(ws, P.mean), 1, P.nslices, 0, 0, FP16_TOP3,
+                                         at<unsigned>(ws, P.smx), sc, st));
+    HOS_CUDA_TRY(launch_planes(d_x, dtype, off, pad, at<double>(ws, P.mean), L, plane_split(p->precision), y32, hi, lo,
+                               1, bx, st, 0, 0, sc));
     double* c2 = at<double>(ws, P.c2);
     HOS_CUDA_TRY(launch_c2(y32, off, pad, 1, L, P.c2s, c2, at<float2>(ws, P.c2p), st));
     tr.mark("transform");
@@ -1497,10 +1519,14 @@ hos_status hos_trispectrum_backward(const void* d_x, int32_t dtype, int64_t n, c
     float* g = at<float>(ws, P.gbuf);
     HOS_CUDA_TRY(launch_gs4(gc, Nf, L, p->window, scale, gs4, st));
     HOS_CUDA_TRY(launch_gc2(gs4, c2, L, gc2, st));
+    if (f16)
+        HOS_CUDA_TRY(launch_flat_scale(gs4, (int64_t)8 * L * L * L, FP16_TOP3, at<unsigned>(ws, P.smx) + 1, sc + 1,
+                                       st));
     HOS_CUDA_TRY(launch_adjoint4_tc(y32, reinterpret_cast<const uint16_t*>(hi), reinterpret_cast<const uint16_t*>(lo),
                                     n, L, gs4, at<uint8_t>(ws, P.gsb), at<float>(ws, P.t1), at<float>(ws, P.t2p), gc2,
-                                    g, at<int>(ws, P.status), wait_limit_ns(), sm_count(), st));
-    g_last_contraction = "adjoint4_tcgen05_split_bf16";
+                                    g, at<int>(ws, P.status), wait_limit_ns(), sm_count(), st,
+                                    f16 ? FMT_F16 : FMT_BF16, sc));
+    g_last_contraction = f16 ? "adjoint4_tcgen05_split_fp16" : "adjoint4_tcgen05_split_bf16";
     tr.mark("reduce");
     HOS_CUDA_TRY(launch_mean(g, HOS_F32, off, 1, P.nslices, at<double>(ws, P.gmpart), p->remove_mean,
                              at<double>(ws, P.gmean), st));

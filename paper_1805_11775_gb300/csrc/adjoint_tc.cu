@@ -1,5 +1,6 @@
 // adjoint_tc.cu -- the adjoint contraction U[u, w1] = sum_w2 y(u + w2) Gs(w1, w2)
-// on the tensor cores (tcgen05, split-bf16, FP32 accumulate), with both
+// on the tensor cores (tcgen05, split-bf16 or split-FP16 of power-of-two scaled
+// operands, FP32 accumulate), with both
 // gradient terms taken in the epilogue:
 //   T1(u) = sum_w1 U[u, w1] y(u + w1)         (row sums, per thread)
 //   T2(j) = sum_w1 U[j - w1, w1] y(j - w1)    (anti-diagonal sums)
@@ -67,7 +68,7 @@ struct __align__(16) AdjSmem {
 struct AdjTcParams {
     const float* y32;       // padded sample planes of the series: y(i) at index L + i
     int t2d;                // floats per warp in t2p: 32 + (w1 values per block) - 1
-    const uint16_t* hi;     // bf16 planes
+    const uint16_t* hi;     // bf16 or f16 planes
     const uint16_t* lo;
     const uint8_t* gsb;     // Gs hi/lo planes per block, canonical layout, 2 * B_BYTES per block
     float* t1p;             // [nb][n_round]
@@ -95,13 +96,13 @@ HOS_DEV void expect_bytes(uint64_t* bar, uint32_t bytes) {
                  : "memory");
 }
 
-template <int ORDER>
+template <int ORDER, int FMT>
 __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     AdjSmem& sm = *reinterpret_cast<AdjSmem*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = P.L, K = P.kpad;
-    const uint32_t idesc = make_idesc(FMT_BF16, AU, AW);
+    const uint32_t idesc = make_idesc(FMT, AU, AW);
     const int64_t items = (int64_t)P.nb * P.nut;
     const int64_t it0 = range_begin(blockIdx.x, items, gridDim.x), it1 = range_begin(blockIdx.x + 1, items, gridDim.x);
 
@@ -424,8 +425,9 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
 // plane, n = row - block start, k = last lag + L (K = kpad, zero beyond 2L).
 // Rows: w1 (third order, nrows = 2L) or (w1, w2) combinations (fourth order,
 // nrows = (2L)^2); Gs is row-major with 2L values per row.
+template <int FMT>
 __global__ void gs_layout_kernel(const float* __restrict__ Gs, int L, int kpad, int nb, int nrows,
-                                 uint8_t* __restrict__ out) {
+                                 const float* __restrict__ gscale, uint8_t* __restrict__ out) {
     const int twoL = 2 * L;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)nb * AW * kpad) return;
@@ -435,12 +437,14 @@ __global__ void gs_layout_kernel(const float* __restrict__ Gs, int L, int kpad, 
     const int w1i = b * AW + n;  // index w1 + L
     float v = 0.f;
     if (w1i < nrows && k < twoL) v = Gs[(int64_t)w1i * twoL + k];
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    if (gscale) v *= gscale[0];  // a power of two: exact
+    const uint32_t hl = pack2<FMT>(v, 0.0f);
+    const float hv = unpack2<FMT>(hl).x;
+    const uint16_t h = (uint16_t)(hl & 0xFFFFu), l = (uint16_t)(pack2<FMT>(v - hv, 0.0f) & 0xFFFFu);
     const size_t off = (size_t)(n % 8) * 16 + (size_t)(n / 8) * 128 + (size_t)(k / 8) * 2048 + (size_t)(k % 8) * 2;
     uint8_t* base = out + (size_t)b * 2 * B_BYTES;
-    *reinterpret_cast<__nv_bfloat16*>(base + off) = h;
-    *reinterpret_cast<__nv_bfloat16*>(base + B_BYTES + off) = l;
+    *reinterpret_cast<uint16_t*>(base + off) = h;
+    *reinterpret_cast<uint16_t*>(base + B_BYTES + off) = l;
 }
 
 // g(j) = sum_b T1p[b][j] + (ORDER - 1) sum over the items (b, ut) covering j
@@ -468,10 +472,13 @@ struct CSum {
 constexpr int GATHER_THREADS = 256;
 template <int ORDER>
 __host__ __device__ constexpr int gather_groups() { return ORDER == 4 ? 4 : 1; }
+// sc: {series scale, Gs scale} of split-FP16 operands (nullptr: unscaled); the
+// contraction's sums carry their product, divided out here (exact: powers of two)
 template <int ORDER>
 __global__ void __launch_bounds__(GATHER_THREADS) adjoint_tc_gather_kernel(
     const float* __restrict__ t1p, const float* __restrict__ t2p, int64_t n, int L, int nb, int64_t nut, int R,
-    const double* __restrict__ gc2, const float* __restrict__ y, float* __restrict__ g) {
+    const double* __restrict__ gc2, const float* __restrict__ y, const float* __restrict__ sc,
+    float* __restrict__ g) {
     // fourth order: gc2 as FP32 and the CTA's samples y(j0 - T .. j0 + GJ - 1 + T)
     __shared__ float gcs[ORDER == 4 ? 4 * 64 : 1];
     __shared__ float ys[ORDER == 4 ? GATHER_THREADS / gather_groups<ORDER>() + 4 * 64 : 1];
@@ -511,10 +518,11 @@ __global__ void __launch_bounds__(GATHER_THREADS) adjoint_tc_gather_kernel(
                 }
             }
         }
-        v.add(t1.hi);
-        v.add(t1.lo);
-        v.add((float)(ORDER - 1) * t2.hi);
-        v.add((float)(ORDER - 1) * t2.lo);
+        const float inv = sc ? 1.0f / (sc[0] * sc[1]) : 1.0f;
+        v.add(t1.hi * inv);
+        v.add(t1.lo * inv);
+        v.add((float)(ORDER - 1) * t2.hi * inv);
+        v.add((float)(ORDER - 1) * t2.lo * inv);
         if constexpr (ORDER == 4) {
             const float* yj = ys + T + jj;  // yj[t] = y(j + t), |t| <= T
             for (int t = -T + grp; t <= T; t += GG) v.add(gcs[t + T] * (yj[t] + yj[-t]));
@@ -553,46 +561,56 @@ size_t adjoint_tc_t1_floats(int L, int64_t n, int order) {
     return (size_t)adj_nb(order, L) * (size_t)ceil_div(n, AU) * AU;
 }
 
-template <int ORDER>
+template <int ORDER, int FMT>
 static cudaError_t launch_adjoint_tc_order(const float* y32, const uint16_t* hi, const uint16_t* lo, int64_t n, int L,
                                            const float* Gs, uint8_t* gsb, float* t1p, float* t2p, const double* gc2,
-                                           float* g, int* status, uint64_t limit_ns, int G, cudaStream_t st) {
+                                           float* g, int* status, uint64_t limit_ns, int G, const float* sc,
+                                           cudaStream_t st) {
     const int kpad = ((2 * L + 15) / 16) * 16;
     const int nb = adj_nb(ORDER, L), R = adj_r(ORDER, L);
     const int64_t nut = ceil_div(n, AU);
     const int64_t tot = (int64_t)nb * AW * kpad;
-    gs_layout_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(Gs, L, kpad, nb, adj_rows(ORDER, L), gsb);
+    gs_layout_kernel<FMT><<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(Gs, L, kpad, nb, adj_rows(ORDER, L),
+                                                                       sc ? sc + 1 : nullptr, gsb);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     AdjTcParams p{y32, 32 + R - 1, hi, lo, gsb, t1p, t2p, n, L, kpad, nb, nut, status, limit_ns};
     const size_t smem = sizeof(AdjSmem);
     // a per-device (per-context) attribute: set on every launch
-    e = cudaFuncSetAttribute(adjoint_tc_kernel<ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(adjoint_tc_kernel<ORDER, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t items = (int64_t)nb * nut;
     const int grid = (int)(items < G ? items : G);
-    adjoint_tc_kernel<ORDER><<<grid, 192, smem, st>>>(p);
+    adjoint_tc_kernel<ORDER, FMT><<<grid, 192, smem, st>>>(p);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     adjoint_tc_gather_kernel<ORDER><<<(unsigned)ceil_div(n, GATHER_THREADS / gather_groups<ORDER>()), GATHER_THREADS,
                                       0, st>>>(
-        t1p, t2p, n, L, nb, nut, R, gc2, y32 + L, g);
+        t1p, t2p, n, L, nb, nut, R, gc2, y32 + L, sc, g);
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_tc(const float* y32, const uint16_t* hi, const uint16_t* lo, int64_t n, int L,
                               const float* Gs, uint8_t* gsb, float* t1p, float* t2p, float* g, int* status,
-                              uint64_t limit_ns, int G, cudaStream_t st) {
-    return launch_adjoint_tc_order<3>(y32, hi, lo, n, L, Gs, gsb, t1p, t2p, nullptr, g, status, limit_ns, G, st);
+                              uint64_t limit_ns, int G, cudaStream_t st, int fmt, const float* sc) {
+    if (fmt == FMT_F16)
+        return launch_adjoint_tc_order<3, FMT_F16>(y32, hi, lo, n, L, Gs, gsb, t1p, t2p, nullptr, g, status, limit_ns,
+                                                   G, sc, st);
+    return launch_adjoint_tc_order<3, FMT_BF16>(y32, hi, lo, n, L, Gs, gsb, t1p, t2p, nullptr, g, status, limit_ns, G,
+                                                nullptr, st);
 }
 
 cudaError_t launch_adjoint4_tc(const float* y32, const uint16_t* hi, const uint16_t* lo, int64_t n, int L,
                                const float* Gs4, uint8_t* gsb, float* t1p, float* t2p, const double* gc2, float* g,
-                               int* status, uint64_t limit_ns, int G, cudaStream_t st) {
-    return launch_adjoint_tc_order<4>(y32, hi, lo, n, L, Gs4, gsb, t1p, t2p, gc2, g, status, limit_ns, G, st);
+                               int* status, uint64_t limit_ns, int G, cudaStream_t st, int fmt, const float* sc) {
+    if (fmt == FMT_F16)
+        return launch_adjoint_tc_order<4, FMT_F16>(y32, hi, lo, n, L, Gs4, gsb, t1p, t2p, gc2, g, status, limit_ns, G,
+                                                   sc, st);
+    return launch_adjoint_tc_order<4, FMT_BF16>(y32, hi, lo, n, L, Gs4, gsb, t1p, t2p, gc2, g, status, limit_ns, G,
+                                                nullptr, st);
 }
 
 }  // namespace hos

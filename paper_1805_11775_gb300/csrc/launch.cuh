@@ -175,16 +175,21 @@ bool adjoint_tc_supported(int L);
 size_t adjoint_tc_gs_bytes(int L, int order = 3);
 size_t adjoint_tc_t2_floats(int L, int64_t n, int order = 3);
 size_t adjoint_tc_t1_floats(int L, int64_t n, int order = 3);
+// fmt FMT_BF16 or FMT_F16; sc (FMT_F16): device {series scale, Gs scale}
 cudaError_t launch_adjoint_tc(const float* y32, const uint16_t* hi, const uint16_t* lo, int64_t n, int L,
                               const float* Gs, uint8_t* gsb, float* t1p, float* t2p, float* g, int* status,
-                              uint64_t limit_ns, int G, cudaStream_t st);
+                              uint64_t limit_ns, int G, cudaStream_t st, int fmt = FMT_BF16,
+                              const float* sc = nullptr);
 cudaError_t launch_gs(const float2* Gc, int N, int L, int window, double scale, float* Gs, cudaStream_t st);
 // trispectrum adjoint (adjoint.cu, adjoint_tc.cu)
 cudaError_t launch_gs4(const float2* Gc, int N, int L, int window, double scale, float* Gs4, cudaStream_t st);
 cudaError_t launch_gc2(const float* Gs4, const double* c2, int L, double* gc2, cudaStream_t st);
 cudaError_t launch_adjoint4_tc(const float* y32, const uint16_t* hi, const uint16_t* lo, int64_t n, int L,
                                const float* Gs4, uint8_t* gsb, float* t1p, float* t2p, const double* gc2, float* g,
-                               int* status, uint64_t limit_ns, int G, cudaStream_t st);
+                               int* status, uint64_t limit_ns, int G, cudaStream_t st, int fmt = FMT_BF16,
+                               const float* sc = nullptr);
+// scale[0] = 2^(top - e), 2^e the least power of two >= max |v[0..count)| (mx: one scratch word)
+cudaError_t launch_flat_scale(const float* v, int64_t count, int top, unsigned* mx, float* scale, cudaStream_t st);
 cudaError_t launch_m4_tile_reduce(const C3Geom& geo, const SeriesView& sv, int64_t max_len, const float* partials,
                                   int64_t* bnd, TileRec* rec, float2* inv_len, double* m4buf, cudaStream_t st,
                                   int64_t norm_len = 0);

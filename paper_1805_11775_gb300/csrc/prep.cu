@@ -266,6 +266,34 @@ cudaError_t launch_series_scale(const void* x, int dtype, const int64_t* off, co
     return cudaGetLastError();
 }
 
+// The same power-of-two scale for one flat array (the adjoint's Gs).
+__global__ void flat_absmax_kernel(const float* __restrict__ v, int64_t count, unsigned* __restrict__ mx) {
+    __shared__ float sh[256];
+    float m = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(v[i]));
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int d = blockDim.x / 2; d > 0; d >>= 1) {
+        if (threadIdx.x < d) sh[threadIdx.x] = fmaxf(sh[threadIdx.x], sh[threadIdx.x + d]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(mx, __float_as_uint(sh[0]));
+}
+
+cudaError_t launch_flat_scale(const float* v, int64_t count, int top, unsigned* mx, float* scale, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    int64_t b = ceil_div(count, 256);
+    flat_absmax_kernel<<<(unsigned)(b < 1024 ? (b > 0 ? b : 1) : 1024), 256, 0, st>>>(v, count, mx);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    scale_kernel<<<1, 32, 0, st>>>(mx, 1, top, scale);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_plan_series(int mode, int64_t n, int64_t seg, const int64_t* d_user_off, int S, int L, int ntiles,
                                int ktot, int flush, int kc, int pad_tail, int64_t* off, int64_t* pad, int64_t* unit,
                                int64_t* win, cudaStream_t st) {

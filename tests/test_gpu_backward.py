@@ -1,7 +1,9 @@
 """GPU parity of the bispectrum adjoint (hos_bispectrum_backward and the
 autograd wrapper) against the oracle's FP64 gradient, which is itself pinned
-by central differences.  Normwise tolerances: 1e-5 for the FP32 adjoint
-(precision "fp32" / "simt"), 1e-4 for the split-bf16 tensor-core adjoint."""
+by central differences.  Normwise tolerances: 1e-5 for the FP32-class
+adjoints (precision "fp32" / "simt" on the CUDA cores, "fp16": split FP16 of
+power-of-two scaled operands on the tensor cores), 1e-4 for the split-bf16
+tensor-core adjoint."""
 import numpy as np
 import pytest
 
@@ -12,7 +14,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no GPU", allow_module_level=True)
 
-TOL = {"fp32": 1e-5, "simt": 1e-5, "bf16": 1e-4}
+TOL = {"fp32": 1e-5, "simt": 1e-5, "bf16": 1e-4, "fp16": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -32,7 +34,7 @@ def normwise(got, ref):
     return np.abs(got - ref).max() / np.abs(ref).max()
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 @pytest.mark.parametrize("n,L,N,window,rm", [(40, 5, 10, "parzen", True), (300, 12, 24, "parzen", False),
                                              (2000, 40, 80, "parzen", True), (1500, 33, 70, "rect", True),
                                              (900, 20, 40, "parzen_sym", False), (5000, 128, 256, "parzen", True),
@@ -62,7 +64,7 @@ def test_backward_transform_sizes(hos, oracle, N):
     assert normwise(got, ref) <= TOL["fp32"]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 def test_autograd_bispectrum_matching_loss(hos, oracle, prec):
     """l = sum over the principal domain of |B(x) - B_target|^2 through
     torch.autograd; the gradient equals the oracle's for the same G."""
@@ -79,7 +81,7 @@ def test_autograd_bispectrum_matching_loss(hos, oracle, prec):
     assert normwise(x.grad.cpu().numpy(), ref) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 def test_backward_full_size_sampled(hos, oracle, prec):
     """n = 2^18 float32 AR(2), L = 128, 256 x 256 grid, loss against the
     bispectrum of a second seeded series: the gradient at sampled samples
@@ -104,17 +106,19 @@ def test_backward_full_size_sampled(hos, oracle, prec):
                                              (2000, 16, 32, "parzen", True), (800, 32, 64, "parzen", False),
                                              (500, 1, 2, "parzen", True), (300, 48, 96, "rect", False),
                                              (200, 64, 128, "parzen", True), (333, 5, 17, "parzen", True)])
-def test_trispectrum_backward_matches_oracle(hos, oracle, n, L, N, window, rm):
-    """Split-bf16 adjoint of the trispectrum against the oracle's FP64 chain
-    rule (pinned by central differences), random complex dl/dT."""
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_trispectrum_backward_matches_oracle(hos, oracle, n, L, N, window, rm, prec):
+    """Split-bf16 and split-FP16 adjoints of the trispectrum against the
+    oracle's FP64 chain rule (pinned by central differences), random complex
+    dl/dT."""
     x = hos_synth.ar2(n, 13 * n + L)
     rng = np.random.default_rng(n + L)
     G = rng.standard_normal((N, N, N)) + 1j * rng.standard_normal((N, N, N))
     wk = {"parzen": oracle.WIN_PARZEN, "rect": oracle.WIN_RECT}[window]
     ref = oracle.trispectrum_grad(x, L, G, N, window=wk, remove_mean=rm)
     got = hos.trispectrum_backward(torch.from_numpy(x).cuda(), torch.from_numpy(G.astype(np.complex64)), L, nfft=N,
-                                   window=window, remove_mean=rm).cpu().numpy()
-    assert normwise(got, ref) <= TOL["bf16"]
+                                   window=window, remove_mean=rm, precision=prec).cpu().numpy()
+    assert normwise(got, ref) <= TOL[prec]
 
 
 def test_autograd_trispectrum_matching_loss(hos, oracle):
