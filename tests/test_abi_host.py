@@ -111,15 +111,17 @@ def test_workspace_size_grows_with_the_problem(lib):
 def test_trispectrum_backward_workspace_and_limits(lib):
     """The trispectrum adjoint's workspace holds the adjoint grid, the per-block
     row partials ((2L)^2 / 128 blocks x n floats) and the rest; precisions other
-    than split-bf16, L > 64 and the symmetric window are refused on the host."""
+    than the split ones (bf16, FP16), L > 64 and the symmetric window are
+    refused on the host."""
     from paper_1805_11775_gb300 import workspace_size, _native, HosError
     n = 1 << 16
     a = workspace_size(_native.OP_TRISPECTRUM_BACKWARD, n, 1, n, _params(L=32, precision=1))
     assert a > 32 * n * 4 + 64 ** 3 * 8
     b = workspace_size(_native.OP_TRISPECTRUM_BACKWARD, n, 1, n, _params(L=64, precision=1))
     assert b > a
+    assert workspace_size(_native.OP_TRISPECTRUM_BACKWARD, n, 1, n, _params(L=32, precision="fp16")) > 0
     for bad in (_params(L=32, precision="fp32"), _params(L=32, precision="tf32"), _params(L=32, precision="simt"),
-                _params(L=32, precision="fp16"), _params(L=65, precision=1),
+                _params(L=65, precision=1),
                 _params(L=32, precision=1, window=1), _params(L=32, precision=1, segment_len=1000)):
         with pytest.raises(HosError):
             workspace_size(_native.OP_TRISPECTRUM_BACKWARD, n, 1, n, bad)
