@@ -23,7 +23,7 @@ import math
 import os
 import threading
 
-_lock = threading.Lock()
+_lock = threading.RLock()  # _load() runs inside tune()'s critical section
 _cache = None
 
 
@@ -108,11 +108,17 @@ def tune(run, op: str, L: int, n_total: int, n_series: int, precision: str, repe
         times[cand] = e0.elapsed_time(e1) / repeats
     best = min(times, key=times.get)
     if store:
-        k = key(torch.cuda.get_device_name(), op, L, n_total, n_series, precision, library_version())
-        with _lock:
-            _load()[k] = {"tile_n": best[0], "flush_chunks": best[1], "chunk_len": best[2], "ms": times[best]}
-            _save()
+        store_choice(key(torch.cuda.get_device_name(), op, L, n_total, n_series, precision, library_version()), best,
+                     times[best])
     return best, times
+
+
+def store_choice(k: str, best, ms: float) -> None:
+    """Record a tuned (tile_n, flush_chunks, chunk_len) under key k and save the cache."""
+    with _lock:
+        cache = _load()
+        cache[k] = {"tile_n": best[0], "flush_chunks": best[1], "chunk_len": best[2], "ms": ms}
+        _save()
 
 
 def tune_bispectrum(x, L: int, precision: str = "bf16", repeats: int = 5):

@@ -327,3 +327,21 @@ def test_batched_fused_tail(hos, oracle, L, window, monkeypatch):
                 continue
             assert normwise(fused[s], refs[s]) <= TOL[prec], (prec, s)
             assert normwise(fused[s], split[s].astype(np.complex128)) <= 2e-6, (prec, s)
+
+
+def test_batched_workload_full_size_sampled(hos, oracle):
+    """The batched workload at full size (4096 intraday-shaped series, lengths
+    2000..20000, L = 128, 256 x 256 grids) in one call: sixteen spectra
+    across the batch (first, last, shortest, longest and twelve spread out)
+    against the oracle at the split-bf16 and split-FP16 targets."""
+    w = hos_synth.workload("batched_4096x_L128")
+    vals, offs = w["x"], w["offsets"]
+    lens = np.diff(offs)
+    pick = sorted({0, lens.size - 1, int(lens.argmin()), int(lens.argmax())} |
+                  set(np.linspace(1, lens.size - 2, 12).astype(int).tolist()))
+    refs = {s: oracle.bispectrum(vals[offs[s]:offs[s + 1]], 128, 256) for s in pick}
+    vd = torch.from_numpy(vals).cuda()
+    for prec in ("bf16", "fp16"):
+        got = hos.bispectrum_batched(vd, offs, 128, precision=prec, max_len=int(lens.max()))
+        for s in pick:
+            assert normwise(got[s].cpu().numpy(), refs[s]) <= TOL[prec], (prec, s)

@@ -35,3 +35,19 @@ def test_corrupt_cache_is_rebuilt(tmp_path, monkeypatch):
     tune._cache["k"] = {"tile_n": 256, "flush_chunks": 8, "ms": 1.0}
     tune._save()
     assert json.loads(p.read_text())["k"]["flush_chunks"] == 8
+
+
+def test_store_choice_round_trip(tmp_path, monkeypatch):
+    """Storing a choice takes the cache lock and loads the cache inside it
+    (the lock is reentrant), saves, and a fresh load finds the choice."""
+    import threading
+    p = tmp_path / "tune.json"
+    monkeypatch.setenv("HOS_TUNE_CACHE", str(p))
+    monkeypatch.setattr(tune, "_cache", None)
+    done = []
+    t = threading.Thread(target=lambda: (tune.store_choice("k|x", (256, 8, 512), 1.5), done.append(1)))
+    t.start()
+    t.join(timeout=10)
+    assert done, "store_choice did not return"
+    monkeypatch.setattr(tune, "_cache", None)
+    assert tune._load()["k|x"] == {"tile_n": 256, "flush_chunks": 8, "chunk_len": 512, "ms": 1.5}
