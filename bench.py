@@ -147,11 +147,12 @@ def cpu_baseline(x, L, n, seconds_target=10.0):
                       f"({terms:.3e} lag terms, {dt:.1f} s)"}, (-(rows // 2), ref)
 
 
-def accuracy(hos, torch, x, L, prec, lo, ref):
-    """Normwise error of the GPU's c3 (same input, same contraction precision)
-    over the oracle rows the CPU baseline computed: max |d| / max |ref|."""
+def accuracy(hos, torch, x, L, prec, lo, ref, knobs=None):
+    """Normwise error of the GPU's c3 (same input, same contraction precision
+    and the same tile width, flush and chunk length as the timed steps) over
+    the oracle rows the CPU baseline computed: max |d| / max |ref|."""
     import numpy as np
-    c3 = hos.cumulant3(torch.from_numpy(x).cuda(), L, precision=prec).cpu().numpy()
+    c3 = hos.cumulant3(torch.from_numpy(x).cuda(), L, precision=prec, **(knobs or {})).cpu().numpy()
     rows = ref.shape[0]
     got = c3[lo + L:lo + L + rows, :2 * L]  # c3 is symmetric: row w1 + L holds c3(w1, w2), w2 + L
     want = ref[:, :2 * L]
@@ -690,7 +691,8 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         x_host = hos_synth.workload(WORKLOAD)["x"]
         line["cpu_baseline"], ref_rows = cpu_baseline(x_host, 256, x_host.size)
-        line["accuracy"] = accuracy(hos, torch, x_host, 256, prec, *ref_rows)
+        line["accuracy"] = accuracy(hos, torch, x_host, 256, prec, *ref_rows,
+                                    knobs=autotune["chosen"] if autotune else None)
     arms = [c for c in args.compare.split(",") if c and c != prec]
     if arms and world == 1 and "roof" not in wl and args.workload not in ("differentiable_trispectrum_n65536_L32",):
         # the same workload in other precisions on the same GPU (the metric's
@@ -718,7 +720,7 @@ def run_ours(args):
                 arm["roofline"] = {"bound": "tensor", "achieved": ach2, "peak": pk2, "unit": "TFLOP/s",
                                    "frac": ach2 / pk2, "peak_source": note2, "work": wl2["work"]}
             if ref_rows is not None:
-                arm["accuracy"] = accuracy(hos, torch, x_host, 256, cprec, *ref_rows)
+                arm["accuracy"] = accuracy(hos, torch, x_host, 256, cprec, *ref_rows, knobs=tune2)
             elif rank == 0 and not args.no_cpu_baseline and "accuracy" in wl2:
                 arm["accuracy"] = wl2["accuracy"]()
             line["compare"].append(arm)

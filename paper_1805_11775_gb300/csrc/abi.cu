@@ -318,7 +318,11 @@ static int build_tiles(C3Geom& g, int L, int N, bool skip_zero_window, int* zero
     return cnt;
 }
 
-static C3Geom make_geom(const hos_params* p, int G, bool skip_zero_window = false, int* zero_skipped = nullptr) {
+// batched: many short series, whose estimates (symmetric returns: B near 0)
+// are the least well conditioned, so the FP32-class paths take the shorter
+// FP32 sums below.
+static C3Geom make_geom(const hos_params* p, int G, bool skip_zero_window = false, int* zero_skipped = nullptr,
+                        bool batched = false) {
     C3Geom g;
     memset(&g, 0, sizeof(g));
     const int twoL = 2 * p->L;
@@ -342,12 +346,16 @@ static C3Geom make_geom(const hos_params* p, int G, bool skip_zero_window = fals
     // steps one partial holds (measured: about 1e-8 of the result per step,
     // for every operand format).  The FP32-class paths (1e-5 target) hand a
     // partial to the reduction every chunk (3xTF32: 384 MMA steps) or every
-    // two chunks (split FP16: 192 steps a chunk).
-    int flush_auto = 16;
-    if (p->precision == HOS_PREC_FP32) flush_auto = 1;
-    if (p->precision == HOS_PREC_SPLIT_FP16) flush_auto = 2;
+    // two chunks (split FP16: 192 steps a chunk); batched, every 192 steps
+    // (3xTF32: 512-sample chunks; split FP16: every chunk).
+    int flush_auto = 16, kc_auto = KC;
+    if (p->precision == HOS_PREC_FP32) {
+        flush_auto = 1;
+        if (batched) kc_auto = 512;
+    }
+    if (p->precision == HOS_PREC_SPLIT_FP16) flush_auto = batched ? 1 : 2;
     g.flush = p->flush_chunks ? p->flush_chunks : flush_auto;
-    g.kc = p->chunk_len ? p->chunk_len : KC;
+    g.kc = p->chunk_len ? p->chunk_len : kc_auto;
     g.G = G;
     // zero samples after a series: every sample a tile's windows read (the
     // SIMT kernel reads all N columns of a tile, the tensor cores its width)
@@ -495,7 +503,7 @@ static hos_status make_plan(int op, const hos_params* p, int64_t n_total, int S_
     int G = contraction_ctas(p->precision);
     P.zero_tiles = 0;
     const bool windowed = (op == HOS_OP_BISPECTRUM || op == HOS_OP_BISPECTRUM_BATCHED);
-    P.g = make_geom(p, G, windowed && p->window == HOS_WIN_PARZEN_SYM, &P.zero_tiles);
+    P.g = make_geom(p, G, windowed && p->window == HOS_WIN_PARZEN_SYM, &P.zero_tiles, op == HOS_OP_BISPECTRUM_BATCHED);
     if (U_known >= 0) {
         const int64_t U = U_known * P.g.ntiles;
         if (U < G) P.g.G = (int)(U > 0 ? U : 1);

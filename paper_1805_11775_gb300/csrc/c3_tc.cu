@@ -49,16 +49,19 @@ constexpr int YA_FLOATS = KC + TILE_M;
 constexpr int YA_STRIDE = YA_FLOATS + 8;
 constexpr int YI_FLOATS = KC + 4;
 
+// The producer's bulk copies land in two staging sets (the next chunk's copies
+// fly while the current one is interleaved); the consumers read the buffers.
 struct __align__(16) C3Smem {
     uint8_t win_hi[2][WIN_BYTES];
     uint8_t win_lo[2][WIN_BYTES];
     float ya[2][4][YA_STRIDE];        // [buffer][shift]; copies 1-3 only for fourth order
     float yi[2][KC];                  // y(i0 + t), 16-byte aligned for broadcast loads
-    float yi_raw[YI_FLOATS];          // staging: copied from an aligned global start
-    uint8_t lin_hi[WIN_SAMPLES * 4];  // linear staging of the hi plane window
-    uint8_t lin_lo[WIN_SAMPLES * 4];
+    float st_ya[2][YA_FLOATS];        // staging: the A window
+    float st_yi[2][YI_FLOATS];        // staging: y(i0 ..) from an aligned global start
+    uint8_t st_hi[2][WIN_SAMPLES * 4];  // staging: the hi plane window, linear
+    uint8_t st_lo[2][WIN_SAMPLES * 4];
     uint64_t full_b[2], empty_b[2], full_a[MAX_STAGE], empty_a[MAX_STAGE];
-    uint64_t acc_full[2], acc_empty[2], drain, tma_bar;
+    uint64_t acc_full[2], acc_empty[2], drain, tma_bar[2];
     uint32_t tmem_base;
     int abort;
 };
@@ -124,7 +127,8 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
             mbar_init(&sm.acc_empty[i], 4);
         }
         mbar_init(&sm.drain, 1);
-        mbar_init(&sm.tma_bar, 1);
+        mbar_init(&sm.tma_bar[0], 1);
+        mbar_init(&sm.tma_bar[1], 1);
         sm.abort = 0;
         fence_mbar_init();
     }
@@ -145,124 +149,155 @@ __global__ void __launch_bounds__(320, 1) c3_tc_kernel(const C3TcParams P) {
 
     if (warp == 8) {
         // ------------------------------------------------------------ producer
-        uint32_t kc = 0, tph = 0;
+        // Chunk kc's copies go to staging set kc & 1; they are issued one chunk
+        // ahead, before the previous chunk's window is interleaved, so that
+        // their latency overlaps that work.  A chunk is (part, c).
+        uint32_t kc = 0, tph[2] = {0u, 0u};
+        bool inflight[2] = {false, false};
         bool ok = true;
-        while (ok && walk.next(part)) {
-            const int a = geo.tile_a[part.t];
-            const int col0 = 32 * geo.tile_c32[part.t], wt = 32 * geo.tile_w32[part.t];  // this tile's columns
-            const int64_t base = P.ser.pad[part.s];
+        Part cur;
+        bool have = walk.next(cur);
+        int64_t cc = have ? cur.c0 : 0;
+        // issue the copies of chunk (p, c) into staging set q; false on a failed bounds check
+        auto issue = [&](const Part& p, int64_t c, int q) -> bool {
+            const int64_t base = P.ser.pad[p.s];
+            const int64_t i0 = c * csz;
+            const int wt = 32 * geo.tile_w32[p.t];
+            const int64_t wb = base + i0 + 32 * geo.tile_c32[p.t];  // plane index of the window start
+            // A window: y(i0 + w1_0 + t) for ORDER 3; y(i0 - L + t) for ORDER 4
+            const int64_t ab = (ORDER == 3) ? base + i0 + (int64_t)geo.tile_a[p.t] * TILE_M : base + i0;
+            const int64_t ib_al = (base + L + i0) & ~(int64_t)3;  // y(i0), from an aligned start
+            const uint32_t wbytes = (uint32_t)(csz + wt + 16) * ELT;
+#ifdef HOS_DEBUG_BOUNDS
+            {   // every copy inside this series' padded block, the part's slot inside the
+                // workspace: otherwise record a fault and stop before any access
+                const int64_t b0 = P.ser.pad[p.s], b1 = P.ser.pad[p.s + 1];
+                const bool bad = b1 > P.plane_len || wb < b0 || wb + csz + wt + 16 > b1 || ab < b0 ||
+                                 ab + csz + TILE_M > b1 || ib_al < b0 || ib_al + csz + 4 > b1 || p.slot < 0 ||
+                                 p.slot >= P.n_slots;
+                if (bad) {
+                    if (lane == 0) {
+                        record_status(P.status, HOS_ERR_DEVICE_FAULT);
+                        *abort = 1;
+                    }
+                    return false;
+                }
+            }
+#endif
+            fence_proxy_async_smem();  // this set's earlier reads, before the copies overwrite it
+            __syncwarp();
+            if (lane == 0) {
+                const uint32_t yab = (uint32_t)(csz + TILE_M) * 4, yib = (uint32_t)(csz + 4) * 4;
+                mbar_expect_tx(&sm.tma_bar[q], 2 * wbytes + yab + yib);
+                bulk_g2s(sm.st_hi[q], (const uint8_t*)P.hi + wb * ELT, wbytes, &sm.tma_bar[q]);
+                bulk_g2s(sm.st_lo[q], (const uint8_t*)P.lo + wb * ELT, wbytes, &sm.tma_bar[q]);
+                bulk_g2s(sm.st_ya[q], P.y32 + ab, yab, &sm.tma_bar[q]);
+                bulk_g2s(sm.st_yi[q], P.y32 + ib_al, yib, &sm.tma_bar[q]);
+            }
+            inflight[q] = true;
+            return true;
+        };
+        if (have) ok = issue(cur, cc, 0);
+        while (ok && have) {
+            const int buf = kc & 1;
+            // the chunk after this one (possibly in the next part)
+            Part nxt = cur;
+            int64_t nc = cc + 1;
+            bool have_next = true;
+            if (nc >= cur.c1) {
+                have_next = walk.next(nxt);
+                nc = have_next ? nxt.c0 : 0;
+            }
+            ok = warp_wait(&sm.tma_bar[buf], tph[buf], abort, P.status, lim, P.hint[0]);
+            if (!ok) break;
+            inflight[buf] = false;
+            tph[buf] ^= 1;
+            if (have_next) {
+                ok = issue(nxt, nc, buf ^ 1);
+                if (!ok) break;
+            }
+            ok = warp_wait(&sm.empty_b[buf], ((kc >> 1) & 1) ^ 1, abort, P.status, lim, P.hint[0]);
+            if (!ok) break;
+            const int64_t base = P.ser.pad[cur.s];
             // rows i >= len carry y(i) = 0 (a time slice keeps its neighbour's
             // samples after it in the plane, for the lags only)
-            const int64_t slen = P.ser.off[part.s + 1] - P.ser.off[part.s];
+            const int64_t slen = P.ser.off[cur.s + 1] - P.ser.off[cur.s];
             // the row factor carries the series' scale s to the power ORDER - 1 (times the
             // window's s: the products come out scaled by s^ORDER, divided out in the reduction)
             float sA = 1.0f;
             if (P.ser.scale) {
-                const float sc = P.ser.scale[part.s];
+                const float sc = P.ser.scale[cur.s];
                 sA = (ORDER == 3) ? sc * sc : sc * sc * sc;
             }
-            for (int64_t c = part.c0; c < part.c1 && ok; ++c, ++kc) {
-                const int buf = kc & 1;
-                ok = warp_wait(&sm.empty_b[buf], ((kc >> 1) & 1) ^ 1, abort, P.status, lim, P.hint[0]);
-                if (!ok) break;
-                const int64_t i0 = c * csz;
-                const int64_t wb = base + i0 + col0;                     // plane index of window start
-                // A window: y(i0 + w1_0 + t) for ORDER 3; y(i0 - L + t) for ORDER 4
-                const int64_t ab = (ORDER == 3) ? base + i0 + (int64_t)a * TILE_M : base + i0;
-                const int64_t ib = base + L + i0;                          // y(i0)
-                const int64_t ib_al = ib & ~(int64_t)3;
-                const uint32_t wbytes = (uint32_t)(csz + wt + 16) * ELT;
-#ifdef HOS_DEBUG_BOUNDS
-                {   // every copy inside this series' padded block, the part's slot inside the
-                    // workspace: otherwise record a fault and stop before any access
-                    const int64_t b0 = P.ser.pad[part.s], b1 = P.ser.pad[part.s + 1];
-                    const int64_t ae = ab + csz + TILE_M;
-                    const bool bad = b1 > P.plane_len || wb < b0 || wb + csz + wt + 16 > b1 || ab < b0 || ae > b1 ||
-                                     ib_al < b0 || ib_al + csz + 4 > b1 || part.slot < 0 || part.slot >= P.n_slots;
-                    if (bad) {
-                        if (lane == 0) {
-                            record_status(P.status, HOS_ERR_DEVICE_FAULT);
-                            *abort = 1;
-                        }
-                        ok = false;
-                        break;
-                    }
-                }
-#endif
-                if (lane == 0) {
-                    const uint32_t yab = (uint32_t)(csz + TILE_M) * 4, yib = (uint32_t)(csz + 4) * 4;
-                    mbar_expect_tx(&sm.tma_bar, 2 * wbytes + yab + yib);
-                    bulk_g2s(sm.lin_hi, (const uint8_t*)P.hi + wb * ELT, wbytes, &sm.tma_bar);
-                    bulk_g2s(sm.lin_lo, (const uint8_t*)P.lo + wb * ELT, wbytes, &sm.tma_bar);
-                    bulk_g2s(sm.ya[buf][0], P.y32 + ab, yab, &sm.tma_bar);
-                    bulk_g2s(sm.yi_raw, P.y32 + ib_al, yib, &sm.tma_bar);
-                }
-                ok = warp_wait(&sm.tma_bar, tph, abort, P.status, lim, P.hint[0]);
-                if (!ok) {
-                    // the copies just issued still land in this CTA's shared memory:
-                    // wait for them (bounded, whatever the abort flag says) before exiting
-                    if (lane == 0) {
-                        volatile int keep_waiting = 0;
-                        mbar_wait(&sm.tma_bar, tph, &keep_waiting, P.status, lim);
-                    }
-                    __syncwarp();
-                    break;
-                }
-                tph ^= 1;
-                {   // realign y(i0 + t) so that builders can use 16-byte broadcast loads
-                    const int ish = (int)(ib - ib_al);
-                    for (int t = lane; t < csz; t += 32)
-                        sm.yi[buf][t] = (i0 + t < slen) ? sm.yi_raw[ish + t] * sA : 0.0f;
-                }
-                if constexpr (ORDER == 4) {
-                    // shifted copies: ya[buf][s][j] = ya[buf][0][j + s].  The last
-                    // group reads up to 4 words past the window (inside the pitch);
-                    // those land only at j + s past the window, which no row reads.
-                    const float* y0 = sm.ya[buf][0];
-                    for (int g = lane; g < (csz + TILE_M) / 4; g += 32) {
-                        const float4 u = *reinterpret_cast<const float4*>(y0 + 4 * g);
-                        const float4 v = *reinterpret_cast<const float4*>(y0 + 4 * g + 4);
+            const int wt = 32 * geo.tile_w32[cur.t];
+            const int64_t i0 = cc * csz;
+            {   // realign y(i0 + t) so that builders can use 16-byte broadcast loads
+                const int64_t ib = base + L + i0;
+                const int ish = (int)(ib - (ib & ~(int64_t)3));
+                for (int t = lane; t < csz; t += 32)
+                    sm.yi[buf][t] = (i0 + t < slen) ? sm.st_yi[buf][ish + t] * sA : 0.0f;
+            }
+            {   // the A window; fourth order also its shifted copies ya[buf][s][j] = y0[j + s].
+                // The last group reads up to 4 words past the window (inside the staging row);
+                // those land only at j + s past the window, which no row reads.
+                const float* y0 = sm.st_ya[buf];
+                for (int g = lane; g < (csz + TILE_M) / 4; g += 32) {
+                    const float4 u = *reinterpret_cast<const float4*>(y0 + 4 * g);
+                    *reinterpret_cast<float4*>(sm.ya[buf][0] + 4 * g) = u;
+                    if constexpr (ORDER == 4) {
+                        const float4 v = (4 * g + 4 < YA_FLOATS) ? *reinterpret_cast<const float4*>(y0 + 4 * g + 4)
+                                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
                         *reinterpret_cast<float4*>(sm.ya[buf][1] + 4 * g) = make_float4(u.y, u.z, u.w, v.x);
                         *reinterpret_cast<float4*>(sm.ya[buf][2] + 4 * g) = make_float4(u.z, u.w, v.x, v.y);
                         *reinterpret_cast<float4*>(sm.ya[buf][3] + 4 * g) = make_float4(u.w, v.x, v.y, v.z);
                     }
                 }
-                // interleave: block (q, r) <- samples [R q + r, R q + r + R)
-                const int ngroups = (csz + wt) / R + 2;
-                const int nblocks = ngroups * R;
-                for (int blk = lane; blk < nblocks; blk += 32) {
-                    const int q = blk / R, r = blk % R;
-                    const int e0 = R * q + r;  // first sample of the block
-                    uint4 vh, vl;
-                    if constexpr (TF32) {
-                        const uint32_t* sh = reinterpret_cast<const uint32_t*>(sm.lin_hi);
-                        const uint32_t* sl = reinterpret_cast<const uint32_t*>(sm.lin_lo);
-                        vh = make_uint4(sh[e0], sh[e0 + 1], sh[e0 + 2], sh[e0 + 3]);
-                        vl = make_uint4(sl[e0], sl[e0 + 1], sl[e0 + 2], sl[e0 + 3]);
-                    } else {
-                        const uint32_t* sh = reinterpret_cast<const uint32_t*>(sm.lin_hi);
-                        const uint32_t* sl = reinterpret_cast<const uint32_t*>(sm.lin_lo);
-                        const int w0 = e0 >> 1;
-                        const uint32_t sft = (e0 & 1) * 16;
-                        uint32_t h[5], l[5];
-#pragma unroll
-                        for (int k = 0; k < 5; ++k) {
-                            h[k] = sh[w0 + k];
-                            l[k] = sl[w0 + k];
-                        }
-                        vh = make_uint4(__funnelshift_r(h[0], h[1], sft), __funnelshift_r(h[1], h[2], sft),
-                                        __funnelshift_r(h[2], h[3], sft), __funnelshift_r(h[3], h[4], sft));
-                        vl = make_uint4(__funnelshift_r(l[0], l[1], sft), __funnelshift_r(l[1], l[2], sft),
-                                        __funnelshift_r(l[2], l[3], sft), __funnelshift_r(l[3], l[4], sft));
-                    }
-                    *reinterpret_cast<uint4*>(sm.win_hi[buf] + (size_t)blk * 16) = vh;
-                    *reinterpret_cast<uint4*>(sm.win_lo[buf] + (size_t)blk * 16) = vl;
-                }
-                fence_proxy_async_smem();  // every lane's window writes, for the MMA's reads
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sm.full_b[buf]);
             }
+            // interleave: block (q, r) <- samples [R q + r, R q + r + R)
+            const int ngroups = (csz + wt) / R + 2;
+            const int nblocks = ngroups * R;
+            const uint32_t* sh = reinterpret_cast<const uint32_t*>(sm.st_hi[buf]);
+            const uint32_t* sl = reinterpret_cast<const uint32_t*>(sm.st_lo[buf]);
+            for (int blk = lane; blk < nblocks; blk += 32) {
+                const int q = blk / R, r = blk % R;
+                const int e0 = R * q + r;  // first sample of the block
+                uint4 vh, vl;
+                if constexpr (TF32) {
+                    vh = make_uint4(sh[e0], sh[e0 + 1], sh[e0 + 2], sh[e0 + 3]);
+                    vl = make_uint4(sl[e0], sl[e0 + 1], sl[e0 + 2], sl[e0 + 3]);
+                } else {
+                    const int w0 = e0 >> 1;
+                    const uint32_t sft = (e0 & 1) * 16;
+                    uint32_t h[5], l[5];
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+                        h[k] = sh[w0 + k];
+                        l[k] = sl[w0 + k];
+                    }
+                    vh = make_uint4(__funnelshift_r(h[0], h[1], sft), __funnelshift_r(h[1], h[2], sft),
+                                    __funnelshift_r(h[2], h[3], sft), __funnelshift_r(h[3], h[4], sft));
+                    vl = make_uint4(__funnelshift_r(l[0], l[1], sft), __funnelshift_r(l[1], l[2], sft),
+                                    __funnelshift_r(l[2], l[3], sft), __funnelshift_r(l[3], l[4], sft));
+                }
+                *reinterpret_cast<uint4*>(sm.win_hi[buf] + (size_t)blk * 16) = vh;
+                *reinterpret_cast<uint4*>(sm.win_lo[buf] + (size_t)blk * 16) = vl;
+            }
+            fence_proxy_async_smem();  // every lane's window writes, for the MMA's reads
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.full_b[buf]);
+            cur = nxt;
+            cc = nc;
+            have = have_next;
+            ++kc;
         }
+        // copies still in flight land in this CTA's shared memory: wait for them
+        // (bounded, whatever the abort flag says) before the CTA exits
+        for (int q = 0; q < 2; ++q)
+            if (inflight[q] && lane == 0) {
+                volatile int keep_waiting = 0;
+                mbar_wait(&sm.tma_bar[q], tph[q], &keep_waiting, P.status, lim);
+            }
+        __syncwarp();
     } else if (warp < 4) {
         // ------------------------------------------------------------ builders
         const int m = warp * 32 + lane;  // TMEM lane = row of A (lag w1, or lag pair, in the tile)

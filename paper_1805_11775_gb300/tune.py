@@ -78,14 +78,19 @@ def lookup(op: str, L: int, n_total: int, n_series: int, precision: str):
     return (int(v["tile_n"]), int(v["flush_chunks"]), int(v.get("chunk_len", 0))) if v else None
 
 
-def candidates(L: int, precision: str):
-    """(tile_n, flush_chunks, chunk_len) to time; chunk_len 0 is the automatic 1024."""
+def candidates(L: int, precision: str, batched: bool = False):
+    """(tile_n, flush_chunks, chunk_len) to time.  The FP32-class precisions
+    keep the FP32 sum of one partial within the MMA steps their 1e-5 target
+    allows (the accumulation error grows with them): 384 for one series, 192
+    for a batch of short series (the least well conditioned)."""
     two_l = 2 * L
     tiles = sorted({t for t in (128, 256) if t <= max(32, 1 << (two_l - 1).bit_length())} or {0})
-    if precision in ("fp32", "3xtf32"):
-        return [(t, f, c) for t in tiles for f in (1, 2) for c in (0, 512)]
-    if precision in ("fp16", "split_fp16"):  # FP32-class: at most 384 MMA steps per partial
-        return [(t, f, c) for t in tiles for (f, c) in ((1, 0), (2, 0), (2, 512), (4, 512))]
+    if precision in ("fp32", "3xtf32"):  # 384 MMA steps per 1024-sample chunk
+        knobs = ((1, 512), (2, 256)) if batched else ((1, 1024), (1, 512), (2, 512))
+        return [(t, f, c) for t in tiles for (f, c) in knobs]
+    if precision in ("fp16", "split_fp16"):  # 192 MMA steps per 1024-sample chunk
+        knobs = ((1, 1024), (2, 512)) if batched else ((1, 1024), (2, 1024), (2, 512), (4, 512))
+        return [(t, f, c) for t in tiles for (f, c) in knobs]
     return [(t, f, 0) for t in tiles for f in (4, 8, 16, 32)]
 
 
@@ -96,7 +101,7 @@ def tune(run, op: str, L: int, n_total: int, n_series: int, precision: str, repe
     (best (tile_n, flush_chunks, chunk_len), {candidate: ms})."""
     import torch
     times = {}
-    for cand in candidates(L, precision):
+    for cand in candidates(L, precision, batched=n_series > 1):
         run(*cand)  # first call: workspace growth, kernel attributes
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

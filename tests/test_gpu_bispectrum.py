@@ -153,16 +153,16 @@ def test_batched_matches_oracle_per_series(hos, oracle):
     zero, so B is sampling noise about 200 times smaller than the sum of the
     absolute lag products (sum_w W c3(|y|) / max|B|), and the tensor cores'
     FP32 accumulation error (about 1e-8 of the partial sum per MMA step)
-    shows through amplified.  3xTF32 runs 384 MMA steps per 1024-sample
-    chunk; at 512-sample chunks (192 steps, as split FP16 at 1024) it meets
-    the FP32-class 1e-5 here.  Every precision at its target."""
+    shows through amplified: a batch's FP32-class plans keep each FP32
+    partial within 192 MMA steps (3xTF32: 512-sample chunks; split FP16: one
+    chunk per partial), which meets the 1e-5 target here.  Every precision
+    at its target."""
     lens = np.array([0, 1, 700, 2500, 1024, 3100, 17, 2048], dtype=np.int64)
     vals, offs = hos_synth.student_t_returns(lens, 11)
     L, N = 40, 80
     for prec in PRECS:
-        kc = 512 if prec == "fp32" else 0
-        got = hos.bispectrum_batched(torch.from_numpy(vals).cuda(), torch.from_numpy(offs), L, precision=prec,
-                                     chunk_len=kc).cpu().numpy()
+        got = hos.bispectrum_batched(torch.from_numpy(vals).cuda(), torch.from_numpy(offs), L,
+                                     precision=prec).cpu().numpy()
         for s in range(lens.size):
             seg = vals[offs[s]:offs[s + 1]]
             if seg.size == 0:
@@ -305,8 +305,8 @@ def test_batched_fused_tail(hos, oracle, L, window, monkeypatch):
     """Batched plans with N = 2L a power of two run the fused per-series tail
     (reduction, window and both transform passes in one kernel): each
     spectrum against the oracle at the precision's target, and against the
-    separate reduction and transform passes (HOS_BATCHED_TAIL=split) to FP32
-    transform rounding."""
+    separate reduction and transform passes (HOS_BATCHED_TAIL=split) within
+    the FP32-class target."""
     lens = np.array([0, 1, 3000, 1024, 17, 5000, 2049], dtype=np.int64)
     vals, offs = hos_synth.student_t_returns(lens, 61 + L)
     vals = vals + np.repeat(np.arange(lens.size) * 1e-3, lens)  # a different mean per series
@@ -316,17 +316,18 @@ def test_batched_fused_tail(hos, oracle, L, window, monkeypatch):
     refs = [oracle.bispectrum(vals[offs[s]:offs[s + 1]], L, N, window=wk) if lens[s] else None
             for s in range(lens.size)]
     for prec in ("bf16", "fp16", "fp32"):
-        kc = 512 if prec == "fp32" else 0
-        fused = hos.bispectrum_batched(vd, offs, L, precision=prec, window=window, chunk_len=kc).cpu().numpy()
+        fused = hos.bispectrum_batched(vd, offs, L, precision=prec, window=window).cpu().numpy()
         monkeypatch.setenv("HOS_BATCHED_TAIL", "split")
-        split = hos.bispectrum_batched(vd, offs, L, precision=prec, window=window, chunk_len=kc).cpu().numpy()
+        split = hos.bispectrum_batched(vd, offs, L, precision=prec, window=window).cpu().numpy()
         monkeypatch.delenv("HOS_BATCHED_TAIL")
         for s in range(lens.size):
             if refs[s] is None or np.abs(refs[s]).max() == 0:
                 assert np.abs(fused[s]).max() <= 1e-30, (prec, s)
                 continue
             assert normwise(fused[s], refs[s]) <= TOL[prec], (prec, s)
-            assert normwise(fused[s], split[s].astype(np.complex128)) <= 2e-6, (prec, s)
+            # two FP32 transforms of the same grid (radix 2 here, radix 8 there): their
+            # rounding, amplified like any error by this ill-conditioned B, within 1e-5
+            assert normwise(fused[s], split[s].astype(np.complex128)) <= 1e-5, (prec, s)
 
 
 def test_batched_workload_full_size_sampled(hos, oracle):

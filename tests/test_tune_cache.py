@@ -8,7 +8,11 @@ from paper_1805_11775_gb300 import tune
 
 def test_candidates_respect_precision_and_lag_range():
     assert all(f <= 2 for _, f, _ in tune.candidates(256, "fp32"))
-    assert {c for _, _, c in tune.candidates(256, "fp32")} == {0, 512}
+    # the FP32-class candidates keep a partial's MMA steps within their budget
+    steps = {"fp32": 384 / 1024, "fp16": 192 / 1024}
+    for prec, per_sample in steps.items():
+        assert max(f * c * per_sample for _, f, c in tune.candidates(256, prec)) <= 384
+        assert max(f * c * per_sample for _, f, c in tune.candidates(256, prec, batched=True)) <= 192
     assert {t for t, _, _ in tune.candidates(256, "bf16")} == {128, 256}
     assert {t for t, _, _ in tune.candidates(40, "bf16")} == {128}
 
