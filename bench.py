@@ -258,10 +258,11 @@ def adjoint4_flops(L, n):
 
 def adjoint_flops(L, n, prec):
     """Executed flops of the adjoint contraction U = Hankel(y) Gs.  Tensor
-    cores (split-bf16, L <= 128): 128-row tiles of u x 128-lag blocks of w1
-    x 2L rounded to 16 lags w2 x 3 products x 2.  SIMT: 2 flops per (u, w1, w2)."""
+    cores (split-bf16 or split FP16, L <= 128): 128-row tiles of u x 128-lag
+    blocks of w1 x 2L rounded to 16 lags w2 x 3 products x 2.  SIMT (fp32,
+    tf32 and simt precisions): 2 flops per (u, w1, w2)."""
     two_l = 2 * L
-    if prec == "bf16" and L <= 128:
+    if prec in ("bf16", "fp16") and L <= 128:
         kpad = 16 * math.ceil(two_l / 16)
         nb, nut = math.ceil(two_l / 128), math.ceil(n / 128)
         return nb * nut * 128 * 128 * kpad * 6, (
@@ -424,7 +425,7 @@ def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
         def step():
             B = hos.bispectrum(xd, L, precision=prec, out=out, workspace=ws)
             G = 2.0 * (B - Bt) * mask  # gradient of sum_principal |B - Bt|^2
-            return hos.bispectrum_backward(xd, G, L, workspace=ws2)
+            return hos.bispectrum_backward(xd, G, L, workspace=ws2, precision=prec)
 
         x_pin = torch.from_numpy(x_host).pin_memory()
 
@@ -432,13 +433,13 @@ def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
             xg = x_pin.to("cuda", non_blocking=True)
             B = hos.bispectrum(xg, L, precision=prec, workspace=ws)
             G = 2.0 * (B - Bt) * mask
-            return hos.bispectrum_backward(xg, G, L, workspace=ws2).cpu()
+            return hos.bispectrum_backward(xg, G, L, workspace=ws2, precision=prec).cpu()
 
         # the step's last call is the adjoint: its contraction is the timed stage
         flops, work = adjoint_flops(L, x_host.size, prec)
         return dict(step=step, e2e=e2e, units=units_of(x_host.size, L), flops=flops, work=work,
                     h2d=x_host.nbytes, d2h=x_host.nbytes,
-                    bound="tensor" if (prec == "bf16" and L <= 128) else "alu",
+                    bound="tensor" if (prec in ("bf16", "fp16") and L <= 128) else "alu",
                     config={"n": int(x_host.size), "L": L, "grid": N, "step": "forward + adjoint"})
     if name == "differentiable_trispectrum_n65536_L32":
         x_host, t_host = w["x"], w["target_x"]
@@ -449,22 +450,22 @@ def make_workload(name, prec, rank, hos, torch, series=0, time_slices=False):
         last_g = {}
 
         def step():
-            T = hos.trispectrum(xd, L, out=out, workspace=ws)
+            T = hos.trispectrum(xd, L, out=out, workspace=ws, precision=prec)
             G = 2.0 * (T - Tt)  # gradient of sum |T - Tt|^2
             last_g["G"] = G
-            return hos.trispectrum_backward(xd, G, L, workspace=ws2)
+            return hos.trispectrum_backward(xd, G, L, workspace=ws2, precision=prec)
 
         x_pin = torch.from_numpy(x_host).pin_memory()
 
         def e2e():
             xg = x_pin.to("cuda", non_blocking=True)
-            T = hos.trispectrum(xg, L, workspace=ws)
-            return hos.trispectrum_backward(xg, 2.0 * (T - Tt), L, workspace=ws2).cpu()
+            T = hos.trispectrum(xg, L, workspace=ws, precision=prec)
+            return hos.trispectrum_backward(xg, 2.0 * (T - Tt), L, workspace=ws2, precision=prec).cpu()
 
         def acc():
             import oracle
             G = last_g["G"]
-            dx = hos.trispectrum_backward(xd, G, L, remove_mean=False).cpu().numpy()
+            dx = hos.trispectrum_backward(xd, G, L, remove_mean=False, precision=prec).cpu().numpy()
             x64 = x_host.astype(np.float64)
             dc4 = oracle.grad_lag4(G.cpu().numpy().astype(np.complex128), L, N)
             dc2 = oracle.grad_c2(dc4, oracle.c2(x64, 2 * L), L)
@@ -694,7 +695,9 @@ def run_ours(args):
         line["accuracy"] = accuracy(hos, torch, x_host, 256, prec, *ref_rows,
                                     knobs=autotune["chosen"] if autotune else None)
     arms = [c for c in args.compare.split(",") if c and c != prec]
-    if arms and world == 1 and "roof" not in wl and args.workload not in ("differentiable_trispectrum_n65536_L32",):
+    if args.workload == "differentiable_trispectrum_n65536_L32":
+        arms = [c for c in arms if c in ("bf16", "fp16")]  # the trispectrum adjoint's precisions
+    if arms and world == 1 and "roof" not in wl:
         # the same workload in other precisions on the same GPU (the metric's
         # "split-BF16 vs FP32, same GPU"), timed the same way
         line["compare"] = []

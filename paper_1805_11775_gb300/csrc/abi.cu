@@ -410,23 +410,11 @@ static int mean_slices(int64_t len, int S) {
 
 struct Layout {
     size_t status, off, pad, unit, win, mean, mpart, scale, smax, bnd, xr, ilen, wtab, y32, hi, lo, partials, grid, tw,
-        tail, total;
+        total;
     int64_t plane_len, slots;
     int nslices;
     int groups;
-    bool fused_tail;  // batched: reduce, window and transform in one kernel per series
-    int tail_ctas;
 };
-
-// The batched bispectrum's fused tail applies when every row block is one tile
-// from lag -L (see batched_tail_kernel); HOS_BATCHED_TAIL=split keeps the
-// separate reduction and transform passes (for measurement).
-static bool use_fused_tail(int op, const C3Geom& g, int Nf) {
-    if (op != HOS_OP_BISPECTRUM_BATCHED) return false;
-    const char* v = std::getenv("HOS_BATCHED_TAIL");
-    if (v && std::strcmp(v, "split") == 0) return false;
-    return batched_tail_supported(g, Nf);
-}
 
 // Carve the workspace.  S series (parts), n_total samples, longest max_len.
 static Layout make_layout(int op, const hos_params* p, const C3Geom& g, int64_t n_total, int S, int64_t max_len) {
@@ -458,11 +446,8 @@ static Layout make_layout(int op, const hos_params* p, const C3Geom& g, int64_t 
     l.lo = o; o = al256(o + (size_t)elt * l.plane_len + 64);
     l.partials = o; o = al256(o + 4 * (size_t)l.slots * TILE_M * g.tile_n);
     const bool spectrum = (op == HOS_OP_BISPECTRUM || op == HOS_OP_BISPECTRUM_BATCHED);
-    l.fused_tail = use_fused_tail(op, g, Nf);
-    l.tail_ctas = sm_count();
-    l.grid = o; o = al256(o + (spectrum && !l.fused_tail ? 4 * (size_t)l.groups * Nf * Nf : 0));
+    l.grid = o; o = al256(o + (spectrum ? 4 * (size_t)l.groups * Nf * Nf : 0));
     l.tw = o; o = al256(o + 8 * (size_t)Nf);
-    l.tail = o; o = al256(o + (l.fused_tail ? batched_tail_scratch_bytes(Nf, l.tail_ctas) : 0));
     l.total = o;
     return l;
 }
@@ -590,11 +575,9 @@ static FromM4Layout from_m4_layout(const hos_params* p) {
 
 
 // Steps shared by the c3 operations: plan, mean, planes, contraction, reduce.
-// spectrum_out: the batched spectra, written by the fused tail when the plan has one
 static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int64_t* d_offsets, const Plan& P,
                          const hos_params* p, void* ws, size_t ws_bytes, cudaStream_t st, Tracer& tr, int red_mode,
-                         float* grid_out, double* c3_out, const SliceArgs* sl = nullptr,
-                         void* spectrum_out = nullptr) {
+                         float* grid_out, double* c3_out, const SliceArgs* sl = nullptr) {
     const C3Geom& g = P.g;
     const Layout& l = P.l;
     const int S = P.S;
@@ -652,26 +635,6 @@ static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int6
         note_plan(g, tc_products(p->precision));
     }
 
-    if (l.fused_tail) {  // the batched tail kernel does the reduction, window and transform
-        tr.mark("tail");
-        Reduce3Params rp;
-        rp.geom = g;
-        rp.ser = sv;
-        rp.partials = partials;
-        rp.window = p->window;
-        rp.nfft = P.Nf;
-        rp.mode = 0;
-        rp.per_series_groups = 1;
-        rp.scale = kBispecScale;
-        rp.grid = nullptr;
-        rp.c3out = nullptr;
-        rp.norm_len = 0;
-        HOS_CUDA_TRY(launch_twiddles(P.Nf, at<float2>(ws, l.tw), st));
-        HOS_CUDA_TRY(launch_batched_tail(rp, l.tail_ctas, at<int64_t>(ws, l.bnd), at<TileRec>(ws, l.xr),
-                                         at<float2>(ws, l.ilen), at<float>(ws, l.wtab), at<float2>(ws, l.tw),
-                                         at<float2>(ws, l.tail), reinterpret_cast<float2*>(spectrum_out), st));
-        return HOS_OK;
-    }
     tr.mark("reduce");
     Reduce3Params rp;
     rp.geom = g;
@@ -1352,12 +1315,8 @@ hos_status hos_bispectrum_batched(const void* d_x, int32_t dtype, const int64_t*
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     Tracer tr(st);
     s = run_c3(HOS_OP_BISPECTRUM_BATCHED, d_x, dtype, n_total, d_offsets, P, p, ws, ws_bytes, st, tr, 0,
-               at<float>(ws, P.l.grid), nullptr, nullptr, d_B);
+               at<float>(ws, P.l.grid), nullptr);
     if (s != HOS_OK) return s;
-    if (P.l.fused_tail) {
-        tr.mark("");
-        return HOS_OK;
-    }
     tr.mark("transform");
     s = run_dft2(at<float>(ws, P.l.grid), reinterpret_cast<float2*>(d_B), S, P.Nf, at<float2>(ws, P.l.tw), st);
     tr.mark("");

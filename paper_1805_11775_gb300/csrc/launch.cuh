@@ -159,12 +159,6 @@ cudaError_t launch_c3_simt(const C3SimtParams& p, int G, cudaStream_t st);
 // max_len: longest series (or part); it only sets how threads split the work.
 cudaError_t launch_reduce3(const Reduce3Params& p, int groups, int64_t max_len, int64_t* bnd, TileRec* rec,
                            float2* inv_len, float* wtab, cudaStream_t st);
-// The fused per-series tail of the batched bispectrum (reduce, window, both
-// transform passes; reduce.cu): plans where it applies, its scratch, launch.
-bool batched_tail_supported(const C3Geom& geo, int nfft);
-size_t batched_tail_scratch_bytes(int nfft, int ctas);
-cudaError_t launch_batched_tail(const Reduce3Params& p, int ctas, int64_t* bnd, TileRec* rec, float2* inv_len,
-                                float* wtab, const float2* tw, float2* scratch, float2* out, cudaStream_t st);
 cudaError_t launch_zero_f32(float* p, int64_t n, cudaStream_t st);
 cudaError_t launch_twiddles(int N, float2* tw, cudaStream_t st);
 cudaError_t launch_lines(bool real_in, const void* in, float2* out, LineGeom g, const float2* tw, int sign,

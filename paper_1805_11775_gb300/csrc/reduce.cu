@@ -480,178 +480,6 @@ cudaError_t launch_reduce3(const Reduce3Params& p, int groups, int64_t max_len, 
     return cudaGetLastError();
 }
 
-// ---- fused batched tail ---------------------------------------------------------
-// For many short series (the batched bispectrum) the reduction, the window and
-// both passes of the 2-D transform run in one persistent kernel per series, so
-// that the windowed grid and the half-spectrum rows never make an HBM round
-// trip: the grid rows live in shared memory, the row transforms go to a
-// per-CTA scratch of N x (N/2 + 1) complex values that stays in L2, and only
-// the spectrum is written to HBM.  It serves plans whose every row block is one
-// tile starting at lag -L (2L <= tile width, N = 2L a power of two, 32..256):
-// then the tiles cover the whole lag square and no value is mirrored.
-//
-// Per series:
-//   A. rows of the lag square in chunks of RC lags w1: each element is the
-//      series' partials summed in the reduction's order and arithmetic
-//      (tile_share4, double-float, 1/n), times the window and (2 pi)^-2 in
-//      FP32 as emit_c3x4 does, stored at grid column k2 = w2 mod N; two real
-//      rows go through one complex N-point FFT (radix 2 in shared memory) and
-//      are separated into their half spectra R[k1][k2], k2 = 0..N/2, written to
-//      the scratch transposed (R[k2][k1]);
-//   B. columns k2 = 0..N/2 in blocks of 32: the N-point FFT over k1 gives
-//      B(k1, k2); the conjugate mirror fills B(N - k1, N - k2) for 0 < k2 < N/2.
-constexpr int TAIL_THREADS = 512;
-constexpr int TAIL_LINES = 32;  // complex lines per shared-memory FFT batch
-
-HOS_DEV float2 tcmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-HOS_DEV int tsk(int i) { return i + (i >> 4); }  // skewed slot: one pad every 16 (banks)
-
-// In-place radix-2 FFTs of nl lines of N points held bit-reversed in buf
-// (line stride SL), forward sign; twiddles tws[k] = e^{-i 2 pi k / N}.
-HOS_DEV void tail_fft_lines(float2* buf, int nl, int N, int lg, int SL, const float2* tws) {
-    for (int sh = 0; sh < lg; ++sh) {
-        const int h = 1 << sh;
-        for (int bf = threadIdx.x; bf < nl * (N / 2); bf += blockDim.x) {
-            const int l = bf >> (lg - 1), k = bf & ((N >> 1) - 1);
-            const int j = k & (h - 1), blk = k >> sh;
-            const int i0 = (blk << (sh + 1)) + j, i1 = i0 + h;
-            const float2 w = tws[j << (lg - 1 - sh)];
-            float2* row = buf + l * SL;
-            const float2 a = row[tsk(i0)], b = tcmul(row[tsk(i1)], w);
-            row[tsk(i0)] = make_float2(a.x + b.x, a.y + b.y);
-            row[tsk(i1)] = make_float2(a.x - b.x, a.y - b.y);
-        }
-        __syncthreads();
-    }
-}
-
-__global__ void __launch_bounds__(TAIL_THREADS) batched_tail_kernel(const Reduce3Params P,
-                                                                     const int64_t* __restrict__ bnd,
-                                                                     const TileRec* __restrict__ rec,
-                                                                     const float2* __restrict__ inv_len,
-                                                                     const float* __restrict__ wtab,
-                                                                     const float2* __restrict__ tw,
-                                                                     float2* __restrict__ scratch,
-                                                                     float2* __restrict__ out) {
-    extern __shared__ float2 tsm[];
-    const C3Geom& geo = P.geom;
-    const SeriesView& sv = P.ser;
-    const int L = geo.L, N = P.nfft, H = N / 2 + 1;
-    int lg = 0;
-    while ((1 << lg) < N) ++lg;
-    const int SL = N + N / 16 + 1;
-    float2* buf = tsm;                     // TAIL_LINES lines of SL
-    float2* tws = tsm + TAIL_LINES * SL;   // N / 2 twiddles
-    for (int k = threadIdx.x; k < N / 2; k += blockDim.x) tws[k] = tw[k];
-    float2* R = scratch + (int64_t)blockIdx.x * H * N;  // R[k2][k1]
-    const int tsz = TILE_M * geo.tile_n;
-    const int64_t total_win = sv.win[sv.S];
-    const int twoL = 2 * L;
-    const int RC = 2 * TAIL_LINES < twoL ? 2 * TAIL_LINES : twoL;  // lag rows per chunk (two per complex line)
-    __syncthreads();
-    for (int s = blockIdx.x; s < sv.S; s += gridDim.x) {
-        const float2 il = inv_len[s];
-        float2* Bs = out + (int64_t)s * N * N;
-        // ---- A: rows of the windowed grid, row transforms
-        for (int r0 = 0; r0 < twoL; r0 += RC) {
-            // element (row i0 + 4q .. +3, column j) from vector vi of tile a; rows of the chunk
-            // land at line (i - r0) / 2, real part for even i, imaginary for odd, slot bitrev(k2)
-            const int nvec = RC / 4 * twoL;
-            for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
-                const int j = v / (RC / 4), q = v % (RC / 4);
-                const int i0 = r0 + 4 * q, a = i0 / TILE_M, m0 = i0 % TILE_M;
-                const TileRec r = rec[(int64_t)s * geo.ntiles + a];
-                DF acc[4];
-                if (r.nwin > 0) {
-                    tile_share4<8>(P.partials, r, tsz, (j * TILE_M + m0) >> 2, 0, 1, geo.flush, bnd, total_win, acc);
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[c] = df_zero();
-                }
-                const int w2 = j - L;
-                const int k2 = w2 < 0 ? w2 + N : w2;
-                const int slot = tsk((int)(__brev((unsigned)k2) >> (32 - lg)));
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int w1 = i0 + c - L;
-                    const DF v3 = df_mul(acc[c], DF{il.x, il.y});
-                    float wv = wtab[w1 + twoL] * wtab[w2 + twoL];
-                    if (P.window == HOS_WIN_PARZEN_SYM) wv *= wtab[w1 - w2 + twoL];
-                    if (P.window == HOS_WIN_RECT && (rect_excluded(w1, L) || rect_excluded(w2, L))) wv = 0.0f;
-                    const float o = (v3.h + v3.l) * ((float)P.scale * wv);
-                    const int row = i0 + c - r0;
-                    float* line = reinterpret_cast<float*>(buf + (row >> 1) * SL + slot);
-                    line[row & 1] = o;
-                }
-            }
-            __syncthreads();
-            tail_fft_lines(buf, RC / 2, N, lg, SL, tws);
-            // separate the two real rows of each line: A = (Z[k] + conj Z[N-k]) / 2,
-            // B = (Z[k] - conj Z[N-k]) / 2i, k = 0..N/2; rows i, i + 1 are grid rows k1 = (w1 mod N)
-            for (int e = threadIdx.x; e < (RC / 2) * H; e += blockDim.x) {
-                const int l = e % (RC / 2), k = e / (RC / 2);
-                const float2 z = buf[l * SL + tsk(k)], zc = buf[l * SL + tsk((N - k) & (N - 1))];
-                const float2 ra = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
-                const float2 rb = make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));
-                const int w1a = r0 + 2 * l - L, w1b = w1a + 1;
-                const int k1a = w1a < 0 ? w1a + N : w1a, k1b = w1b < 0 ? w1b + N : w1b;
-                R[(int64_t)k * N + k1a] = ra;
-                R[(int64_t)k * N + k1b] = rb;
-            }
-            __syncthreads();
-        }
-        // ---- B: column transforms, blocks of TAIL_LINES columns k2
-        for (int c0 = 0; c0 < H; c0 += TAIL_LINES) {
-            const int nc = (H - c0) < TAIL_LINES ? (H - c0) : TAIL_LINES;
-            for (int e = threadIdx.x; e < nc * N; e += blockDim.x) {
-                const int l = e / N, k1 = e % N;
-                buf[l * SL + tsk((int)(__brev((unsigned)k1) >> (32 - lg)))] = R[(int64_t)(c0 + l) * N + k1];
-            }
-            __syncthreads();
-            tail_fft_lines(buf, nc, N, lg, SL, tws);
-            // B(k1, k2) row by row (nc consecutive columns), and the mirror
-            // B(N - k1, N - k2) = conj B(k1, k2) for 0 < k2 < N/2
-            for (int e = threadIdx.x; e < N * nc; e += blockDim.x) {
-                const int k1 = e / nc, l = e % nc, k2 = c0 + l;
-                const float2 v = buf[l * SL + tsk(k1)];
-                Bs[(int64_t)k1 * N + k2] = v;
-                if (k2 > 0 && k2 < N / 2) Bs[(int64_t)((N - k1) & (N - 1)) * N + (N - k2)] = make_float2(v.x, -v.y);
-            }
-            __syncthreads();
-        }
-    }
-}
-
-bool batched_tail_supported(const C3Geom& geo, int nfft) {
-    const int twoL = 2 * geo.L;
-    if (nfft != twoL || twoL < 32 || twoL > 256 || (twoL & (twoL - 1)) != 0) return false;
-    if (geo.tile_n < twoL || geo.ntiles != geo.tiles_m) return false;
-    for (int t = 0; t < geo.ntiles; ++t)
-        if (geo.tile_a[t] != t || geo.tile_c32[t] != 0 || 32 * geo.tile_w32[t] < twoL) return false;
-    return true;
-}
-
-size_t batched_tail_scratch_bytes(int nfft, int ctas) {
-    return (size_t)ctas * (size_t)(nfft / 2 + 1) * (size_t)nfft * sizeof(float2);
-}
-
-cudaError_t launch_batched_tail(const Reduce3Params& p, int ctas, int64_t* bnd, TileRec* rec, float2* inv_len,
-                                float* wtab, const float2* tw, float2* scratch, float2* out, cudaStream_t st) {
-    cudaError_t e = launch_part_index(p.geom, p.ser, bnd, rec, inv_len, p.norm_len, 3, st);
-    if (e != cudaSuccess) return e;
-    window_table_kernel<<<(unsigned)ceil_div(4 * p.geom.L, 256), 256, 0, st>>>(p.geom.L, p.window, wtab);
-    count_launch();
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int N = p.nfft;
-    const size_t smem = (size_t)(TAIL_LINES * (N + N / 16 + 1) + N / 2) * sizeof(float2);
-    e = cudaFuncSetAttribute(batched_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    batched_tail_kernel<<<ctas, TAIL_THREADS, smem, st>>>(p, bnd, rec, inv_len, wtab, tw, scratch, out);
-    count_launch();
-    return cudaGetLastError();
-}
-
 // Window, scale and wrap of a given c3 (hos_cumulant3's layout: element
 // (w2 + L) * 2L + (w1 + L)) onto the transform grid, in the arithmetic of
 // emit_c3x4, so that a c3 from hos_cumulant3 gives hos_bispectrum's grid.

@@ -300,36 +300,6 @@ def test_split_fp16_scales_any_magnitude(hos, oracle):
         assert normwise(got[s], ref) <= TOL["fp16"], s
 
 
-@pytest.mark.parametrize("L,window", [(16, "parzen"), (64, "rect"), (128, "parzen"), (128, "parzen_sym")])
-def test_batched_fused_tail(hos, oracle, L, window, monkeypatch):
-    """Batched plans with N = 2L a power of two run the fused per-series tail
-    (reduction, window and both transform passes in one kernel): each
-    spectrum against the oracle at the precision's target, and against the
-    separate reduction and transform passes (HOS_BATCHED_TAIL=split) within
-    the FP32-class target."""
-    lens = np.array([0, 1, 3000, 1024, 17, 5000, 2049], dtype=np.int64)
-    vals, offs = hos_synth.student_t_returns(lens, 61 + L)
-    vals = vals + np.repeat(np.arange(lens.size) * 1e-3, lens)  # a different mean per series
-    N = 2 * L
-    vd = torch.from_numpy(vals).cuda()
-    wk = {"parzen": oracle.WIN_PARZEN, "parzen_sym": oracle.WIN_PARZEN_SYM, "rect": oracle.WIN_RECT}[window]
-    refs = [oracle.bispectrum(vals[offs[s]:offs[s + 1]], L, N, window=wk) if lens[s] else None
-            for s in range(lens.size)]
-    for prec in ("bf16", "fp16", "fp32"):
-        fused = hos.bispectrum_batched(vd, offs, L, precision=prec, window=window).cpu().numpy()
-        monkeypatch.setenv("HOS_BATCHED_TAIL", "split")
-        split = hos.bispectrum_batched(vd, offs, L, precision=prec, window=window).cpu().numpy()
-        monkeypatch.delenv("HOS_BATCHED_TAIL")
-        for s in range(lens.size):
-            if refs[s] is None or np.abs(refs[s]).max() == 0:
-                assert np.abs(fused[s]).max() <= 1e-30, (prec, s)
-                continue
-            assert normwise(fused[s], refs[s]) <= TOL[prec], (prec, s)
-            # two FP32 transforms of the same grid (radix 2 here, radix 8 there): their
-            # rounding, amplified like any error by this ill-conditioned B, within 1e-5
-            assert normwise(fused[s], split[s].astype(np.complex128)) <= 1e-5, (prec, s)
-
-
 def test_batched_workload_full_size_sampled(hos, oracle):
     """The batched workload at full size (4096 intraday-shaped series, lengths
     2000..20000, L = 128, 256 x 256 grids) in one call: sixteen spectra
