@@ -79,10 +79,11 @@ def lookup(op: str, L: int, n_total: int, n_series: int, precision: str):
 
 
 def candidates(L: int, precision: str, batched: bool = False):
-    """(tile_n, flush_chunks, chunk_len) to time.  The FP32-class precisions
-    keep the FP32 sum of one partial within the MMA steps their 1e-5 target
-    allows (the accumulation error grows with them): 384 for one series, 192
-    for a batch of short series (the least well conditioned)."""
+    """(tile_n, flush_chunks, chunk_len) to time.  Each precision keeps the
+    FP32 sum of one partial within the MMA steps its target allows (the
+    tensor cores' accumulation error grows with them, about 1e-8 a step):
+    FP32-class 384 for one series, 192 for a batch of short series (the
+    least well conditioned); split-bf16 3,072."""
     two_l = 2 * L
     tiles = sorted({t for t in (128, 256) if t <= max(32, 1 << (two_l - 1).bit_length())} or {0})
     if precision in ("fp32", "3xtf32"):  # 384 MMA steps per 1024-sample chunk
@@ -91,7 +92,9 @@ def candidates(L: int, precision: str, batched: bool = False):
     if precision in ("fp16", "split_fp16"):  # 192 MMA steps per 1024-sample chunk
         knobs = ((1, 1024), (2, 512)) if batched else ((1, 1024), (2, 1024), (2, 512), (4, 512))
         return [(t, f, c) for t in tiles for (f, c) in knobs]
-    return [(t, f, 0) for t in tiles for f in (4, 8, 16, 32)]
+    # split-bf16 (1e-4 target): flushes up to 16 chunks (3,072 MMA steps, about
+    # 3e-5 on the long workload), a third of the target
+    return [(t, f, 0) for t in tiles for f in (4, 8, 16)]
 
 
 def tune(run, op: str, L: int, n_total: int, n_series: int, precision: str, repeats: int = 5, store: bool = True):
