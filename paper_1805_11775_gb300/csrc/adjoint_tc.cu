@@ -420,6 +420,452 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Third order with Gs resident in tensor memory.  The same contraction,
+// transposed: D[w1, u] = sum_w2 Gs(w1, w2) y(u + w2), M = 128 lags w1 of one
+// block, N = 128 samples u of an item, K = 16 lags w2 per step:
+//   A = the block's Gs rows (hi and lo), stored into TMEM once per block by
+//       the epilogue warps (TMEM lane m holds row w1 = w1b + m);
+//   B = the Hankel matrix X[w2, u] = y(u + w2), the same interleaved window
+//       read by descriptor (LBO = SBO = 128 bytes);
+//   D = two FP32 accumulators of 128 columns.
+// Only B is read from shared memory: 4 KB per MMA where the shared-memory
+// form reads 8.  TMEM: Gs hi at column 0, lo at 128 (at most 128 columns
+// each), accumulators at 256 and 384.
+// Eight epilogue warps: warp (q, h) = (warp % 4, warp / 4) takes TMEM lanes
+// 32 q .. 32 q + 31 (lags w1b + 32 q + lane) and the 64 columns 64 h ..:
+//   T1(u) = sum_w1 D[w1, u] y(u + w1): each lane's products, reduced across
+//           the warp by a butterfly per 32-column chunk (lane l ends with the
+//           chunk's column l); the four lane quadrants' sums are then added
+//           in quadrant order;
+//   T2(j) = sum_w1 D[w1, j - w1] y(j - w1): lane r writes its products
+//           D[r, c] y(u0 + c) at row r, position r + c of a zero-filled
+//           32 x 96 array, so that each position's column sum is one
+//           anti-diagonal; lanes read four positions per 16-byte load.  The
+//           two column halves' diagonals are added per quadrant.
+// Pairs of FP32 products and sums use the packed f32x2 instructions (each
+// half rounded as its scalar instruction would be).
+// Both results land in the layouts of the shared-memory form (t1p[b][u]; per
+// quadrant q a T2 window at item position 32 q + d), so the gather is the
+// same.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int TM_EPI = 8;               // epilogue warps
+constexpr int TM_THREADS = 32 * (TM_EPI + 2);
+constexpr int YWC = AU + AW + 8;        // pitch of the shifted copies of yw (8 words mod 32)
+constexpr int ZW = 96;                  // skewed row width: 64 columns + 31 lane offsets, rounded
+constexpr int T2H = ZW;                 // one column half's diagonals
+// Each item's sums are added up across warps one item later (so that no warp
+// waits for the others right after its own work); a sum buffer is written
+// again four items on, when every warp has passed the item that read it.
+constexpr int RED = 4;
+
+struct __align__(16) Adj3TmSmem {
+    uint8_t win_hi[NBUF][AWIN * 16];
+    uint8_t win_lo[NBUF][AWIN * 16];
+    uint16_t lin_hi[NBUF][AWIN + 16];
+    uint16_t lin_lo[NBUF][AWIN + 16];
+    float yw[NBUF][AU + AW];    // staging: y(u0 + w1b + t), the y(u + w1) of T1
+    float yu[NBUF][AU + 4];     // staging: y(u0 + t - sh) from a 16-byte aligned start, sh = L & 3
+    float ywc[NBUF][4][YWC];    // ywc[s][t] = y(u0 + w1b + t + s): 16-byte loads at any lag
+    float yua[NBUF][AU];        // yua[c] = y(u0 + c), 16-byte aligned
+    float z[TM_EPI][32 * ZW];   // per warp: row r = lane r's T2 products at positions r .. r + 63, zero elsewhere
+    float t2w[RED][4][2][T2H];  // [item % RED][quadrant][column half] anti-diagonal sums
+    float t1s[RED][4][AU];      // [item % RED][quadrant] T1 column sums
+    uint64_t full[NBUF], empty[NBUF], tma_bar[NBUF], acc_full[2], acc_empty[2], gs_full, gs_empty, t1_bar[RED],
+        drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+// packed pairs: (x0, x1) op (y0, y1), each half rounded to nearest
+HOS_DEV void mul2(float& r0, float& r1, float x0, float x1, float y0, float y1) {
+    asm("{\n\t.reg .b64 a, b, c;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "mul.rn.f32x2 c, a, b;\n\tmov.b64 {%0, %1}, c;\n\t}"
+        : "=f"(r0), "=f"(r1)
+        : "f"(x0), "f"(x1), "f"(y0), "f"(y1));
+}
+HOS_DEV void add2(float& s0, float& s1, float x0, float x1) {
+    asm("{\n\t.reg .b64 a, b;\n\tmov.b64 a, {%0, %1};\n\tmov.b64 b, {%2, %3};\n\t"
+        "add.rn.f32x2 a, a, b;\n\tmov.b64 {%0, %1}, a;\n\t}"
+        : "+f"(s0), "+f"(s1)
+        : "f"(x0), "f"(x1));
+}
+
+}  // namespace
+
+// Gs rows for the TMEM form: per block b and row n (w1 index b * 128 + n), the
+// hi plane's kh words then the lo plane's, word w holding lags 2w and 2w + 1
+// (index w2 + L) of the row, zero past 2L; kh = 2L rounded up to 64, halved.
+template <int FMT>
+__global__ void gs_rows_kernel(const float* __restrict__ Gs, int L, int kh, int nb, int nrows,
+                               const float* __restrict__ gscale, uint32_t* __restrict__ out) {
+    const int twoL = 2 * L;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)nb * AW * kh) return;
+    const int64_t row = e / kh;  // b * 128 + n
+    const int w = (int)(e % kh);
+    const int k0 = 2 * w;
+    float v0 = 0.f, v1 = 0.f;
+    if (row < nrows) {
+        if (k0 < twoL) v0 = Gs[row * twoL + k0];
+        if (k0 + 1 < twoL) v1 = Gs[row * twoL + k0 + 1];
+    }
+    if (gscale) {  // a power of two: exact
+        v0 *= gscale[0];
+        v1 *= gscale[0];
+    }
+    const uint32_t h = pack2<FMT>(v0, v1);
+    const float2 f = unpack2<FMT>(h);
+    out[(row * 2) * kh + w] = h;
+    out[(row * 2 + 1) * kh + w] = pack2<FMT>(v0 - f.x, v1 - f.y);
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(TM_THREADS, 1) adjoint3_tm_kernel(const AdjTcParams P) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    Adj3TmSmem& sm = *reinterpret_cast<Adj3TmSmem*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int L = P.L, K = P.kpad;
+    const int kh = ((K + 63) / 64) * 32;  // words (TMEM columns) per Gs plane row
+    const uint32_t idesc = make_idesc(FMT, AW, AU);
+    const int64_t items = (int64_t)P.nb * P.nut;
+    const int64_t it0 = range_begin(blockIdx.x, items, gridDim.x), it1 = range_begin(blockIdx.x + 1, items, gridDim.x);
+    // the first item's block and u tile; later ones advance without a division
+    const int b_first = (int)(it0 / P.nut);
+    const int64_t ut_first = it0 % P.nut;
+    constexpr uint32_t GS_LO = 128u, ACC0 = 256u;
+    constexpr int PRODUCER = TM_EPI, ISSUER = TM_EPI + 1;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NBUF; ++i) {
+            mbar_init(&sm.full[i], 1);            // one elected arrival per arriving warp
+            mbar_init(&sm.empty[i], 1 + TM_EPI);  // MMA commit + the epilogue warps
+            mbar_init(&sm.tma_bar[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&sm.acc_full[i], 1);
+            mbar_init(&sm.acc_empty[i], TM_EPI);
+        }
+        for (int i = 0; i < RED; ++i) mbar_init(&sm.t1_bar[i], TM_EPI);
+        mbar_init(&sm.gs_full, TM_EPI);
+        mbar_init(&sm.gs_empty, 1);
+        mbar_init(&sm.drain, 1);
+        sm.abort = 0;
+        fence_mbar_init();
+    }
+    for (int i = threadIdx.x; i < TM_EPI * 32 * ZW; i += blockDim.x) (&sm.z[0][0])[i] = 0.f;
+    if (warp == ISSUER) {
+        tmem_alloc(&sm.tmem_base, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem_base;
+    volatile int* abort = &sm.abort;
+    const uint64_t lim = P.limit_ns;
+
+    if (warp == PRODUCER) {
+        // ---------------------------------------------------------- producer
+        bool ok = true;
+        const int64_t cnt = it1 - it0;
+        const int ysh = L & 3;
+        // items whose copies run ahead; the buffer item k + PD reuses was freed by
+        // item k + PD - NBUF = k - 2
+        constexpr int PD = NBUF - 2;
+        int64_t issued = 0, landed = 0;
+        int ib = b_first;  // block and u tile of the next item to issue
+        int64_t iut = ut_first;
+        auto issue = [&](int64_t k) -> bool {
+            const int64_t u0 = iut * AU;
+            const int buf = (int)(k % NBUF);
+            if (!warp_wait(&sm.empty[buf], (uint32_t)((k / NBUF) & 1) ^ 1u, abort, P.status, lim, 2000)) return false;
+            // window of y(u0 - L + t) (plane index u0, 16-byte aligned); yw = y(u0 + w1b + t),
+            // w1b = 128 b - L (plane index u0 + 128 b); yu from an aligned start
+            const uint32_t wsamp = (uint32_t)(AU + K + 16);
+            fence_proxy_async_smem();  // this buffer's earlier generic-proxy accesses, before the copies
+            __syncwarp();
+            if (lane == 0) {
+                expect_bytes(&sm.tma_bar[buf], 2 * wsamp * 2 + (AU + AW) * 4 + (AU + 4) * 4);
+                bulk_copy(sm.lin_hi[buf], P.hi + u0, wsamp * 2, &sm.tma_bar[buf]);
+                bulk_copy(sm.lin_lo[buf], P.lo + u0, wsamp * 2, &sm.tma_bar[buf]);
+                bulk_copy(sm.yw[buf], P.y32 + u0 + (int64_t)ib * AW, (AU + AW) * 4, &sm.tma_bar[buf]);
+                bulk_copy(sm.yu[buf], P.y32 + ((L + u0) & ~(int64_t)3), (AU + 4) * 4, &sm.tma_bar[buf]);
+            }
+            issued = k + 1;
+            if (++iut == P.nut) {
+                iut = 0;
+                ++ib;
+            }
+            return true;
+        };
+        for (int64_t k = 0; k < PD && k < cnt && ok; ++k) ok = issue(k);
+        for (int64_t k = 0; k < cnt && ok; ++k) {
+            const int buf = (int)(k % NBUF);
+            ok = warp_wait(&sm.tma_bar[buf], (uint32_t)((k / NBUF) & 1), abort, P.status, lim, 1000);
+            if (!ok) break;
+            landed = k + 1;
+            // interleave: block (q, r) <- samples [8q + r, 8q + r + 8)
+            const int nblocks = (int)(((AU + K) / 8 + 2) * 8);
+            const uint32_t* sh = reinterpret_cast<const uint32_t*>(sm.lin_hi[buf]);
+            const uint32_t* sl = reinterpret_cast<const uint32_t*>(sm.lin_lo[buf]);
+            for (int blk = lane; blk < nblocks; blk += 32) {
+                const int w0 = blk >> 1;
+                const uint32_t sft = (blk & 1) * 16;
+                uint32_t h[5], l[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    h[q] = sh[w0 + q];
+                    l[q] = sl[w0 + q];
+                }
+                *reinterpret_cast<uint4*>(sm.win_hi[buf] + (size_t)blk * 16) =
+                    make_uint4(__funnelshift_r(h[0], h[1], sft), __funnelshift_r(h[1], h[2], sft),
+                               __funnelshift_r(h[2], h[3], sft), __funnelshift_r(h[3], h[4], sft));
+                *reinterpret_cast<uint4*>(sm.win_lo[buf] + (size_t)blk * 16) =
+                    make_uint4(__funnelshift_r(l[0], l[1], sft), __funnelshift_r(l[1], l[2], sft),
+                               __funnelshift_r(l[2], l[3], sft), __funnelshift_r(l[3], l[4], sft));
+            }
+            // the epilogue's operands: four shifted copies of yw (the last group of
+            // copy s reads up to s words past yw, inside the buffer; those land at
+            // t + s >= AU + AW, which no lane reads) and y(u0 + c) aligned
+            {
+                const float* y0 = sm.yw[buf];
+                for (int g = lane; g < (AU + AW) / 4; g += 32) {
+                    const float4 u = *reinterpret_cast<const float4*>(y0 + 4 * g);
+                    const float4 v = (g + 1 < (AU + AW) / 4) ? *reinterpret_cast<const float4*>(y0 + 4 * g + 4)
+                                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+                    *reinterpret_cast<float4*>(sm.ywc[buf][0] + 4 * g) = u;
+                    *reinterpret_cast<float4*>(sm.ywc[buf][1] + 4 * g) = make_float4(u.y, u.z, u.w, v.x);
+                    *reinterpret_cast<float4*>(sm.ywc[buf][2] + 4 * g) = make_float4(u.z, u.w, v.x, v.y);
+                    *reinterpret_cast<float4*>(sm.ywc[buf][3] + 4 * g) = make_float4(u.w, v.x, v.y, v.z);
+                }
+                for (int t = lane; t < AU; t += 32) sm.yua[buf][t] = sm.yu[buf][ysh + t];
+            }
+            fence_proxy_async_smem();  // every lane's window writes, for the MMA's reads
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.full[buf]);
+            if (k + PD < cnt) ok = issue(k + PD);
+        }
+        // copies issued ahead of a failure still land in this CTA's shared memory:
+        // wait for them (bounded, whatever the abort flag says) before the CTA exits
+        if (!ok && lane == 0) {
+            volatile int keep_waiting = 0;
+            for (int64_t k = landed; k < issued; ++k)
+                mbar_wait(&sm.tma_bar[k % NBUF], (uint32_t)((k / NBUF) & 1), &keep_waiting, P.status, lim);
+        }
+        __syncwarp();
+    } else if (warp == ISSUER && lane == 0) {
+        // ---------------------------------------------------------- MMA issuer
+        int cur_b = -1, b = b_first;
+        int64_t ut = ut_first;
+        uint32_t nbl = 0;
+        bool ok = true;
+        const uint32_t wh0 = smem_u32(sm.win_hi[0]), wl0 = smem_u32(sm.win_lo[0]);
+        for (int64_t k = 0; k < it1 - it0 && ok; ++k) {
+            if (b != cur_b) {
+                // the previous block's MMAs are all issued: their completion frees Gs
+                if (cur_b >= 0) mma_commit(&sm.gs_empty);
+                ok = mbar_wait(&sm.gs_full, nbl & 1, abort, P.status, lim);
+                if (!ok) break;
+                tc_fence_after();
+                cur_b = b;
+                ++nbl;
+            }
+            const int buf = (int)(k % NBUF);
+            const uint32_t ab = (uint32_t)(k & 1);
+            ok = mbar_wait(&sm.acc_empty[ab], ((k >> 1) & 1) ^ 1, abort, P.status, lim);
+            if (!ok) break;
+            ok = mbar_wait(&sm.full[buf], (uint32_t)((k / NBUF) & 1), abort, P.status, lim);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t d = tmem + ACC0 + ab * 128u;
+            const uint32_t wh = wh0 + (uint32_t)buf * (AWIN * 16), wl = wl0 + (uint32_t)buf * (AWIN * 16);
+            uint32_t acc = 0;
+            for (int ks = 0; ks < K / 16; ++ks) {
+                // K = lags w2 (-L + 16 ks ..): window offset 16 ks samples = 2 groups of 128 B
+                const uint64_t bh = make_sdesc(wh + (uint32_t)ks * 256u, 128, 128);
+                const uint64_t bl = make_sdesc(wl + (uint32_t)ks * 256u, 128, 128);
+                const uint32_t ah = tmem + (uint32_t)ks * 8u;  // 16 lags = 8 packed columns
+                mma_ts<false>(d, ah, bh, idesc, acc);
+                acc = 1;
+                mma_ts<false>(d, ah, bl, idesc, 1);
+                mma_ts<false>(d, ah + GS_LO, bh, idesc, 1);
+            }
+            mma_commit(&sm.empty[buf]);
+            mma_commit(&sm.acc_full[ab]);
+            if (++ut == P.nut) {
+                ut = 0;
+                ++b;
+            }
+        }
+        mma_commit(&sm.drain);
+        {   // every MMA must have completed before TMEM is freed, also after an
+            // abort: wait whatever the abort flag says, bounded (at least 0.2 s)
+            volatile int keep_waiting = 0;
+            mbar_wait(&sm.drain, 0, &keep_waiting, P.status, lim > 200000000ull ? lim : 200000000ull);
+        }
+    } else if (warp < TM_EPI) {
+        // ---------------------------------------------------------- epilogue
+        const int q = warp & 3;       // TMEM lane quadrant
+        const int hf = warp >> 2;     // column half
+        const int m = q * 32 + lane;  // row: lag w1 = w1b + m
+        const int cb = 64 * hf;       // first column
+        const uint32_t lrow = (uint32_t)(q * 32) << 16;
+        float* zr = sm.z[warp] + lane * (ZW + 1);  // this lane's row, shifted by the lane
+        const float* zc = sm.z[warp] + 4 * lane;   // positions 4 lane .. 4 lane + 3 of row 0
+        int cur_b = -1, b = b_first;
+        int64_t ut = ut_first;
+        uint32_t nbl = 0;
+        bool ok = true;
+        // the cross-warp sums of item k (block bk, first sample u0k): T1 of columns
+        // 32 q + 16 hf .. + 15 (the four quadrants added in order) and quadrant q's
+        // T2 window entries [80 hf, 80 hf + 80) (half 1 starts 64 positions later)
+        auto finish = [&](int64_t k, int bk, int64_t u0k) -> bool {
+            const int sl = (int)(k % RED);
+            if (!warp_wait(&sm.t1_bar[sl], (uint32_t)((k / RED) & 1), abort, P.status, lim, 200)) return false;
+            if (lane < 16) {
+                const int c = 32 * q + 16 * hf + lane;
+                const float t1 = ((sm.t1s[sl][0][c] + sm.t1s[sl][1][c]) + sm.t1s[sl][2][c]) + sm.t1s[sl][3][c];
+                if (u0k + c < P.n) P.t1p[(int64_t)bk * (P.nut * AU) + u0k + c] = t1;
+            }
+            const float* h0 = sm.t2w[sl][q][0];
+            const float* h1 = sm.t2w[sl][q][1];
+            float* dst = P.t2p + ((it0 + k) * 4 + q) * P.t2d;
+            const int e1 = (80 * hf + 80 < P.t2d) ? 80 * hf + 80 : P.t2d;
+            for (int e = 80 * hf + lane; e < e1; e += 32) {
+                const float x0 = e < T2H ? h0[e] : 0.f;
+                const float x1 = e >= 64 ? h1[e - 64] : 0.f;
+                dst[e] = x0 + x1;
+            }
+            return true;
+        };
+        int prev_b = 0;
+        int64_t prev_u0 = 0;
+        for (int64_t k = 0; k < it1 - it0 && ok; ++k) {
+            const int64_t u0 = ut * AU;
+            if (b != cur_b) {
+                // a new block: once every MMA on the previous one has completed, store
+                // row m of its Gs into TMEM lane m (column half hf: plane hf)
+                ok = warp_wait(&sm.gs_empty, (nbl & 1) ^ 1, abort, P.status, lim, 2000);
+                if (!ok) break;
+                tc_fence_after();
+                const uint4* src =
+                    reinterpret_cast<const uint4*>(P.gsb) + (((size_t)b * AW + m) * 2 + hf) * (size_t)(kh / 4);
+                for (int c = 0; c < kh; c += 32) {
+                    uint32_t v[32];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const uint4 w = src[c / 4 + i];
+                        v[4 * i] = w.x;
+                        v[4 * i + 1] = w.y;
+                        v[4 * i + 2] = w.z;
+                        v[4 * i + 3] = w.w;
+                    }
+                    tmem_st32(tmem + lrow + (uint32_t)hf * GS_LO + (uint32_t)c, v);
+                }
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.gs_full);
+                cur_b = b;
+                ++nbl;
+            }
+            const int buf = (int)(k % NBUF);
+            const uint32_t ab = (uint32_t)(k & 1);
+            const int sl = (int)(k % RED);
+            ok = warp_wait(&sm.full[buf], (uint32_t)((k / NBUF) & 1), abort, P.status, lim, 2000);  // this item's windows
+            if (!ok) break;
+            ok = warp_wait(&sm.acc_full[ab], (k >> 1) & 1, abort, P.status, lim, 5000);
+            if (!ok) break;
+            tc_fence_after();
+            uint32_t v0[32], v1[32];
+            tmem_ld32(tmem + lrow + ACC0 + ab * 128u + (uint32_t)cb, v0);
+            tmem_ld32(tmem + lrow + ACC0 + ab * 128u + (uint32_t)cb + 32u, v1);
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.acc_empty[ab]);  // this warp's columns are read
+            // T1 products D y(u + w1) into a0 / a1 (yw[c] = y(u0 + cb + c + w1), from the copy
+            // that puts it on a 16-byte boundary); T2 products D y(u) into this lane's row
+            float a0[32], a1[32];
+            {
+                const float* yw = sm.ywc[buf][m & 3] + (m & ~3) + cb;
+                const float* yu = sm.yua[buf] + cb;
+#pragma unroll
+                for (int g = 0; g < 16; ++g) {
+                    const float4 w4 = *reinterpret_cast<const float4*>(yw + 4 * g);
+                    const float4 u4 = *reinterpret_cast<const float4*>(yu + 4 * g);
+                    const uint32_t* v = g < 8 ? v0 + 4 * g : v1 + 4 * (g - 8);
+                    float* a = g < 8 ? a0 + 4 * g : a1 + 4 * (g - 8);
+                    const float d0 = __uint_as_float(v[0]), d1 = __uint_as_float(v[1]);
+                    const float d2 = __uint_as_float(v[2]), d3 = __uint_as_float(v[3]);
+                    mul2(a[0], a[1], d0, d1, w4.x, w4.y);
+                    mul2(a[2], a[3], d2, d3, w4.z, w4.w);
+                    float p0, p1, p2, p3;
+                    mul2(p0, p1, d0, d1, u4.x, u4.y);
+                    mul2(p2, p3, d2, d3, u4.z, u4.w);
+                    zr[4 * g] = p0;
+                    zr[4 * g + 1] = p1;
+                    zr[4 * g + 2] = p2;
+                    zr[4 * g + 3] = p3;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.empty[buf]);  // this buffer's y copies are no longer read
+            // butterflies over the lanes (both chunks, independent chains): after the
+            // step of width s, lane l keeps the half of the columns whose bit s matches its own
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const bool up = (lane & s) != 0;
+#pragma unroll
+                for (int i = 0; i < s; ++i) {
+                    const float x0 = up ? a0[i] : a0[i + s], k0 = up ? a0[i + s] : a0[i];
+                    const float x1 = up ? a1[i] : a1[i + s], k1 = up ? a1[i + s] : a1[i];
+                    a0[i] = k0 + __shfl_xor_sync(0xffffffffu, x0, s);
+                    a1[i] = k1 + __shfl_xor_sync(0xffffffffu, x1, s);
+                }
+            }
+            sm.t1s[sl][q][cb + lane] = a0[0];       // columns cb + lane and cb + 32 + lane,
+            sm.t1s[sl][q][cb + 32 + lane] = a1[0];  // summed over the warp's 32 lags
+            // anti-diagonals: lane l < 24 sums positions 4 l .. 4 l + 3 over the 32 rows
+            if (lane < ZW / 4) {
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 8
+                for (int r = 0; r < 32; ++r) {
+                    const float4 z4 = *reinterpret_cast<const float4*>(zc + r * ZW);
+                    add2(s0, s1, z4.x, z4.y);
+                    add2(s2, s3, z4.z, z4.w);
+                }
+                *reinterpret_cast<float4*>(&sm.t2w[sl][q][hf][4 * lane]) = make_float4(s0, s1, s2, s3);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.t1_bar[sl]);  // this warp's sums of item k are in shared memory
+            // the previous item's cross-warp sums
+            if (k > 0) {
+                ok = finish(k - 1, prev_b, prev_u0);
+                if (!ok) break;
+            }
+            prev_b = b;
+            prev_u0 = u0;
+            if (++ut == P.nut) {
+                ut = 0;
+                ++b;
+            }
+        }
+        if (ok && it1 > it0) ok = finish(it1 - it0 - 1, prev_b, prev_u0);
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == ISSUER) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
 // Gs hi/lo per block of 128 B rows in the canonical K-major layout the kernel
 // reads: byte (n % 8) * 16 + (n / 8) * 128 + (k / 8) * 2048 + (k % 8) * 2 of a
 // plane, n = row - block start, k = last lag + L (K = kpad, zero beyond 2L).
@@ -593,14 +1039,45 @@ static cudaError_t launch_adjoint_tc_order(const float* y32, const uint16_t* hi,
     return cudaGetLastError();
 }
 
+// third order, Gs in tensor memory
+template <int FMT>
+static cudaError_t launch_adjoint3_tm(const float* y32, const uint16_t* hi, const uint16_t* lo, int64_t n, int L,
+                                      const float* Gs, uint8_t* gsb, float* t1p, float* t2p, float* g, int* status,
+                                      uint64_t limit_ns, int G, const float* sc, cudaStream_t st) {
+    const int kpad = ((2 * L + 15) / 16) * 16;
+    const int kh = ((kpad + 63) / 64) * 32;
+    const int nb = adj_nb(3, L);
+    const int64_t nut = ceil_div(n, AU);
+    const int64_t tot = (int64_t)nb * AW * kh;
+    gs_rows_kernel<FMT><<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(Gs, L, kh, nb, adj_rows(3, L),
+                                                                     sc ? sc + 1 : nullptr,
+                                                                     reinterpret_cast<uint32_t*>(gsb));
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    AdjTcParams p{y32, 32 + AW - 1, hi, lo, gsb, t1p, t2p, n, L, kpad, nb, nut, status, limit_ns};
+    // at least 116 KB, so that one CTA (and one 512-column TMEM allocation) lands on each SM
+    const size_t smem = sizeof(Adj3TmSmem) > 118784 ? sizeof(Adj3TmSmem) : 118784;
+    e = cudaFuncSetAttribute(adjoint3_tm_kernel<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t items = (int64_t)nb * nut;
+    const int grid = (int)(items < G ? items : G);
+    adjoint3_tm_kernel<FMT><<<grid, TM_THREADS, smem, st>>>(p);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    adjoint_tc_gather_kernel<3><<<(unsigned)ceil_div(n, GATHER_THREADS), GATHER_THREADS, 0, st>>>(
+        t1p, t2p, n, L, nb, nut, AW, nullptr, y32 + L, sc, g);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_adjoint_tc(const float* y32, const uint16_t* hi, const uint16_t* lo, int64_t n, int L,
                               const float* Gs, uint8_t* gsb, float* t1p, float* t2p, float* g, int* status,
                               uint64_t limit_ns, int G, cudaStream_t st, int fmt, const float* sc) {
     if (fmt == FMT_F16)
-        return launch_adjoint_tc_order<3, FMT_F16>(y32, hi, lo, n, L, Gs, gsb, t1p, t2p, nullptr, g, status, limit_ns,
-                                                   G, sc, st);
-    return launch_adjoint_tc_order<3, FMT_BF16>(y32, hi, lo, n, L, Gs, gsb, t1p, t2p, nullptr, g, status, limit_ns, G,
-                                                nullptr, st);
+        return launch_adjoint3_tm<FMT_F16>(y32, hi, lo, n, L, Gs, gsb, t1p, t2p, g, status, limit_ns, G, sc, st);
+    return launch_adjoint3_tm<FMT_BF16>(y32, hi, lo, n, L, Gs, gsb, t1p, t2p, g, status, limit_ns, G, nullptr, st);
 }
 
 cudaError_t launch_adjoint4_tc(const float* y32, const uint16_t* hi, const uint16_t* lo, int64_t n, int L,
