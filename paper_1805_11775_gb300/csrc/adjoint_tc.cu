@@ -1,36 +1,35 @@
-// adjoint_tc.cu -- the adjoint contraction U[u, w1] = sum_w2 y(u + w2) Gs(w1, w2)
-// on the tensor cores (tcgen05, split-bf16 or split-FP16 of power-of-two scaled
-// operands, FP32 accumulate), with both
-// gradient terms taken in the epilogue:
-//   T1(u) = sum_w1 U[u, w1] y(u + w1)         (row sums, per thread)
-//   T2(j) = sum_w1 U[j - w1, w1] y(j - w1)    (anti-diagonal sums)
+// adjoint_tc.cu -- the adjoint contractions of the bispectrum and trispectrum
+// estimators on the tensor cores (tcgen05, split-bf16 or split-FP16 of
+// power-of-two scaled operands, FP32 accumulate), with both gradient terms
+// taken in the epilogue.
 //
-// MMA operands (M = 128 rows u, N = 128 lags w1 of one block, K = 16 lags w2):
-//   A = Hankel X[u, w2] = y(u + w2): the interleaved 1-D window of the forward
+// Third order (adjoint3_tm_kernel, below): U[u, w1] = sum_w2 y(u + w2) Gs(w1, w2)
+// gives the gradient T1 + 2 T2 with
+//   T1(u) = sum_w1 U[u, w1] y(u + w1),   T2(j) = sum_w1 U[j - w1, w1] y(j - w1);
+// it runs transposed, Gs resident in tensor memory (its own comment block).
+//
+// Fourth order (adjoint_tc_kernel<4>, shared-memory operands).  With Gs the
+// symmetrised lag-domain gradient of c4 and
+// E(u, w1) = sum_{w2,w3} Gs(w1, w2, w3) y(u + w2) y(u + w3), the fourth-moment
+// part of the gradient is T1 + 3 T2 with
+//   T1(u) = sum_w1 E(u, w1) y(u + w1),   T2(j) = sum_w1 E(j - w1, w1) y(j - w1).
+// One MMA (M = 128 rows u, N = 128 combinations (w1, w2) of one block, K = 16
+// lags w3) computes D[u, (w1, w2)] = sum_w3 y(u + w3) Gs(w1, w2, w3):
+//   A = Hankel X[u, w3] = y(u + w3): the interleaved 1-D window of the forward
 //       kernel (8 copies shifted by one sample, 16-byte blocks), read straight
-//       by the descriptor (LBO = SBO = 128 bytes) -- never expanded.
-//   B = Gs(w1, w2) of one 128-lag block of w1, K-major canonical layout,
-//       loaded once per block and kept in shared memory (all K = 2L lags).
+//       by the descriptor (LBO = SBO = 128 bytes) -- never expanded;
+//   B = Gs rows of one block of 128 combinations, w2 fastest, K-major
+//       canonical layout, loaded once per block and kept in shared memory;
 //   D = two FP32 TMEM accumulators (128 columns each), so the epilogue drains
 //       one item while the MMAs fill the next.
-// T2 is summed per warp and 32-column chunk: the products U[u, c] y(u) go to
-// shared memory, lane l adds up the chunk's anti-diagonals l and l + 32, and
-// the chunk sums accumulate per warp; the four warps' diagonals are then added
-// in warp order.  Every sum runs in a fixed order.
-//
-// Work items (w1 block b, 128-row tile of u), b-major, split into equal
-// contiguous ranges over the persistent CTAs.  Every wait is bounded.
-//
-// Fourth order (the trispectrum adjoint).  With Gs the symmetrised lag-domain
-// gradient of c4 and E(u, w1) = sum_{w2,w3} Gs(w1, w2, w3) y(u + w2) y(u + w3),
-// the fourth-moment part of the gradient is T1 + 3 T2 with
-//   T1(u) = sum_w1 E(u, w1) y(u + w1),   T2(j) = sum_w1 E(j - w1, w1) y(j - w1).
-// The same MMA computes D[u, (w1, w2)] = sum_w3 y(u + w3) Gs(w1, w2, w3): the
-// B rows are the (w1, w2) combinations, 128 per block, w2 fastest, K = w3.
 // The epilogue forms E(u, w1) = sum_w2 D[u, (w1, w2)] y(u + w2) one w1 run at
 // a time (a run split between two blocks gives two partial E's, which T1 and
 // T2 take linearly) and adds E y(u + w1) to T1 and E y(u) to the warp's T2
 // positions u + w1.
+//
+// Work items (block b, 128-sample tile of u), b-major, split into equal
+// contiguous ranges over the persistent CTAs.  Every sum runs in a fixed
+// order and every wait is bounded.
 #include "launch.cuh"
 
 namespace hos {
@@ -54,10 +53,9 @@ struct __align__(16) AdjSmem {
     uint8_t win_lo[NBUF][AWIN * 16];
     uint16_t lin_hi[NBUF][AWIN + 16];
     uint16_t lin_lo[NBUF][AWIN + 16];
-    float yw[NBUF][AU + AW];   // ORDER 3: y(u0 + w1_0 + t), the y(u + w1) of T1; ORDER 4: y(u0 - L + t)
+    float yw[NBUF][AU + AW];   // y(u0 - L + t)
     float yu[NBUF][AU + 4];    // y(u0 + t - sh) from a 16-byte aligned start, sh = L & 3
     float t2w[4][AU / 4 + AW];  // each warp's anti-diagonal sums (private to the warp)
-    float pw[4][32 * 33];       // third order: one 32 x 32 chunk of U y(u) per warp, row pitch 33
     uint64_t full[NBUF], empty[NBUF], tma_bar[NBUF], acc_full[2], acc_empty[2], b_full, b_empty, btma_bar, drain;
     uint32_t tmem_base;
     int abort;
@@ -98,6 +96,7 @@ HOS_DEV void expect_bytes(uint64_t* bar, uint32_t bytes) {
 
 template <int ORDER, int FMT>
 __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P) {
+    static_assert(ORDER == 4, "third order runs on adjoint3_tm_kernel");
     extern __shared__ __align__(16) uint8_t smem_raw[];
     AdjSmem& sm = *reinterpret_cast<AdjSmem*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -150,16 +149,13 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
         // copies of item k (into buffer k % NBUF) once the consumers are done with
         // the item that used the buffer before (k - NBUF, already published)
         auto issue = [&](int64_t k) -> bool {
-            const int64_t it = it0 + k;
-            const int b = (int)(it / P.nut);
-            const int64_t u0 = (it % P.nut) * AU;
+            const int64_t u0 = ((it0 + k) % P.nut) * AU;
             const int buf = (int)(k % NBUF);
             if (!warp_wait(&sm.empty[buf], (uint32_t)((k / NBUF) & 1) ^ 1u, abort, P.status, lim, 2000)) return false;
             // window of y(u0 - L + t): plane index u0 (multiple of 128, 16-byte aligned for bf16)
             const uint32_t wsamp = (uint32_t)(AU + K + 16);
-            // ORDER 3: yw = y(u0 + w1b + t), w1b the block's first lag (L + u0 + w1b
-            // = u0 + 128 b, aligned); ORDER 4: yw = y(u0 - L + t) (plane index u0)
-            const int64_t yw0 = (ORDER == 3) ? (L + u0 + (int64_t)b * AW - L) : u0;
+            // yw = y(u0 - L + t) (plane index u0)
+            const int64_t yw0 = u0;
             if (lane == 0) {
                 expect_bytes(&sm.tma_bar[buf], 2 * wsamp * 2 + (AU + AW) * 4 + (AU + 4) * 4);
                 bulk_copy(sm.lin_hi[buf], P.hi + u0, wsamp * 2, &sm.tma_bar[buf]);
@@ -297,100 +293,50 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
             if (!ok) break;
             tc_fence_after();
             const float yu = sm.yu[buf][ysh + m];
-            if constexpr (ORDER == 4) {
-                const float* yw = sm.yw[buf] + m;  // yw[t] = y(u - L + t): y(u + w) = yw[w + L]
-                float* t2w = sm.t2w[q];
-                for (int e = lane; e < P.t2d; e += 32) t2w[e] = 0.f;
-                __syncwarp();
-                const int twoL = 2 * L;
-                const int cb0 = b * AW;  // first (w1, w2) combination of the block
-                const int w1i0 = cb0 / twoL;
-                int w1i = w1i0, w2i = cb0 - w1i0 * twoL;
-                float ev = 0.f, t1 = 0.f;
-                auto flush = [&]() {  // end of a w1 run (uniform over the warp)
-                    if (w1i < twoL) {      // combinations past (2L)^2 are zero rows of B
-                        t1 = fmaf(ev, yw[w1i], t1);
-                        t2w[lane + (w1i - w1i0)] += ev * yu;
-                    }
-                    __syncwarp();
-                    ev = 0.f;
-                    w2i = 0;
-                    ++w1i;
-                };
-                auto chunk = [&](const uint32_t* v, int c0) {
-                    if (w2i + 32 <= twoL) {
-                        // the 32 columns lie in one w1 run: fixed offsets from yw + w2i,
-                        // four partial sums
-                        const float* yq = yw + w2i;
-                        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-#pragma unroll
-                        for (int j = 0; j < 32; j += 4) {
-                            p0 = fmaf(__uint_as_float(v[j]), yq[j], p0);
-                            p1 = fmaf(__uint_as_float(v[j + 1]), yq[j + 1], p1);
-                            p2 = fmaf(__uint_as_float(v[j + 2]), yq[j + 2], p2);
-                            p3 = fmaf(__uint_as_float(v[j + 3]), yq[j + 3], p3);
-                        }
-                        ev += (p0 + p1) + (p2 + p3);
-                        w2i += 32;
-                        if (w2i == twoL || c0 + 32 == AW) flush();
-                        return;
-                    }
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        ev = fmaf(__uint_as_float(v[j]), yw[w2i], ev);
-                        if (++w2i == twoL || c0 + j == AW - 1) flush();
-                    }
-                };
-                // two 32-column loads in flight per wait
-                for (int c0 = 0; c0 < AW; c0 += 64) {
-                    uint32_t v0[32], v1[32];
-                    const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + ab * 128u + (uint32_t)c0;
-                    tmem_ld32(ta, v0);
-                    tmem_ld32(ta + 32u, v1);
-                    tmem_wait_ld();
-                    chunk(v0, c0);
-                    chunk(v1, c0 + 32);
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sm.acc_empty[ab]);
-                if (u0 + m < P.n) P.t1p[(int64_t)b * (P.nut * AU) + u0 + m] = t1;
-                float* dst = P.t2p + (it * 4 + q) * P.t2d;
-                for (int e = lane; e < P.t2d; e += 32) dst[e] = t2w[e];
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sm.empty[buf]);
-                continue;
-            }
-            const float* yw = sm.yw[buf] + m;  // y(u + w1_0 + c)
-            float t1 = 0.f;
+            const float* yw = sm.yw[buf] + m;  // yw[t] = y(u - L + t): y(u + w) = yw[w + L]
             float* t2w = sm.t2w[q];
-            float* pw = sm.pw[q];
-            for (int e = lane; e < AU / 4 + AW; e += 32) t2w[e] = 0.f;
+            for (int e = lane; e < P.t2d; e += 32) t2w[e] = 0.f;
             __syncwarp();
-            // per 32-column chunk: T1 per row; the products U[u, c] y(u) go to pw, and
-            // lane l then sums anti-diagonals d = l and d = l + 32 of the chunk
-            // (row r, column d - r), adding them at t2w[c0 + d]
+            const int twoL = 2 * L;
+            const int cb0 = b * AW;  // first (w1, w2) combination of the block
+            const int w1i0 = cb0 / twoL;
+            int w1i = w1i0, w2i = cb0 - w1i0 * twoL;
+            float ev = 0.f, t1 = 0.f;
+            auto flush = [&]() {  // end of a w1 run (uniform over the warp)
+                if (w1i < twoL) {      // combinations past (2L)^2 are zero rows of B
+                    t1 = fmaf(ev, yw[w1i], t1);
+                    t2w[lane + (w1i - w1i0)] += ev * yu;
+                }
+                __syncwarp();
+                ev = 0.f;
+                w2i = 0;
+                ++w1i;
+            };
             auto chunk = [&](const uint32_t* v, int c0) {
+                if (w2i + 32 <= twoL) {
+                    // the 32 columns lie in one w1 run: fixed offsets from yw + w2i,
+                    // four partial sums
+                    const float* yq = yw + w2i;
+                    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        p0 = fmaf(__uint_as_float(v[j]), yq[j], p0);
+                        p1 = fmaf(__uint_as_float(v[j + 1]), yq[j + 1], p1);
+                        p2 = fmaf(__uint_as_float(v[j + 2]), yq[j + 2], p2);
+                        p3 = fmaf(__uint_as_float(v[j + 3]), yq[j + 3], p3);
+                    }
+                    ev += (p0 + p1) + (p2 + p3);
+                    w2i += 32;
+                    if (w2i == twoL || c0 + 32 == AW) flush();
+                    return;
+                }
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float uval = __uint_as_float(v[j]);
-                    t1 = fmaf(uval, yw[c0 + j], t1);
-                    pw[lane * 33 + j] = uval * yu;
+                    ev = fmaf(__uint_as_float(v[j]), yw[w2i], ev);
+                    if (++w2i == twoL || c0 + j == AW - 1) flush();
                 }
-                __syncwarp();
-                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll
-                for (int r = 0; r < 32; r += 2) {
-                    // address 32 r + l (+ 32): bank l, no conflicts
-                    const float pa = pw[r * 33 + (r <= lane ? lane - r : lane + 32 - r)];
-                    const float pb = pw[(r + 1) * 33 + (r + 1 <= lane ? lane - r - 1 : lane + 31 - r)];
-                    if (r <= lane) s0 += pa; else s1 += pa;
-                    if (r + 1 <= lane) s2 += pb; else s3 += pb;
-                }
-                t2w[c0 + lane] += s0 + s2;
-                t2w[c0 + 32 + lane] += s1 + s3;
-                __syncwarp();
             };
+            // two 32-column loads in flight per wait
             for (int c0 = 0; c0 < AW; c0 += 64) {
                 uint32_t v0[32], v1[32];
                 const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + ab * 128u + (uint32_t)c0;
@@ -402,12 +348,12 @@ __global__ void __launch_bounds__(192, 1) adjoint_tc_kernel(const AdjTcParams P)
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&sm.acc_empty[ab]);  // this item's accumulator may be reused
+            if (lane == 0) mbar_arrive(&sm.acc_empty[ab]);
             if (u0 + m < P.n) P.t1p[(int64_t)b * (P.nut * AU) + u0 + m] = t1;
             float* dst = P.t2p + (it * 4 + q) * P.t2d;
             for (int e = lane; e < P.t2d; e += 32) dst[e] = t2w[e];
             __syncwarp();
-            if (lane == 0) mbar_arrive(&sm.empty[buf]);  // yu / yw of this buffer are no longer read
+            if (lane == 0) mbar_arrive(&sm.empty[buf]);
         }
     }
 
