@@ -148,15 +148,24 @@ def cpu_baseline(x, L, n, seconds_target=10.0):
 
 
 def accuracy(hos, torch, x, L, prec, lo, ref, knobs=None):
-    """Normwise error of the GPU's c3 (same input, same contraction precision
-    and the same tile width, flush and chunk length as the timed steps) over
-    the oracle rows the CPU baseline computed: max |d| / max |ref|."""
+    """Normwise error of the timed path's output (same input, contraction
+    precision, plan, tile width, flush and chunk length as the timed steps)
+    over the oracle rows the CPU baseline computed: B is brought back to the
+    lag grid by an FP64 inverse transform, (2 pi)^2 ifft2(B)[w1, w2] =
+    W(w1, w2) c3(w1, w2), and compared with the window times the oracle's c3:
+    max |d| / max |ref|."""
     import numpy as np
-    c3 = hos.cumulant3(torch.from_numpy(x).cuda(), L, precision=prec, **(knobs or {})).cpu().numpy()
+    import oracle
+    B = hos.bispectrum(torch.from_numpy(x).cuda(), L, precision=prec, **(knobs or {}))
+    N = B.shape[0]
+    G = (torch.fft.ifft2(B.to(torch.complex128)).real * (2 * math.pi) ** 2).cpu().numpy()
     rows = ref.shape[0]
-    got = c3[lo + L:lo + L + rows, :2 * L]  # c3 is symmetric: row w1 + L holds c3(w1, w2), w2 + L
-    want = ref[:, :2 * L]
-    return {"vs": "FP64 oracle", "quantity": "c3 (unwindowed cumulant)", "max_rel_err":
+    w1 = np.arange(lo, lo + rows)
+    w2 = np.arange(-L, L)
+    got = G[(w1 % N)[:, None], (w2 % N)[None, :]]
+    win = np.array([[oracle.window2(int(a), int(b), L) for b in w2] for a in w1])
+    want = win * ref[:, :2 * L]
+    return {"vs": "FP64 oracle", "quantity": "W c3 (the lag grid of B, FP64 inverse transform)", "max_rel_err":
             float(np.abs(got - want).max() / np.abs(want).max()),
             "sample": f"rows w1 in [{lo}, {lo + rows - 1}] x w2 in [{-L}, {L - 1}]"}
 

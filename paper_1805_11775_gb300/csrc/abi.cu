@@ -283,9 +283,40 @@ static int build_tiles(C3Geom& g, int L, int N, bool skip_zero_window, int* zero
     const char* scheme = std::getenv("HOS_TILE_SCHEME");
     const bool diagonal = scheme && std::strcmp(scheme, "diagonal") == 0;
     int cnt = 0, k = 0, zs = 0;
+    if (g.sym != C3_SWAP) {
+        // six-fold: rows w1 in [0, L), each row block's columns from its first
+        // row's diagonal w2 = w1 to its last row's w1 + L - 1 (L - 1 under the
+        // band), in tiles of the full width N (a narrower tile costs the MMA
+        // issue of a full one)
+        for (int a = 0; a < g.tiles_m; ++a) {
+            const int r0 = -L + a * TILE_M;
+            const int b_lo = r0 > 0 ? r0 : 0, b_hi = (r0 + TILE_M < L) ? r0 + TILE_M : L;
+            g.row_c0[a] = 0;
+            g.row_t0[a] = (uint8_t)cnt;
+            if (b_lo >= b_hi) continue;
+            const int c_end = (g.sym == C3_SIX_BAND ? L : b_hi - 1 + L) + L;  // last column + 1
+            const int c0 = ((b_lo + L) / 32) * 32;
+            g.row_c0[a] = (uint16_t)c0;
+            for (int c = c0; c < c_end; c += N) {
+                if (cnt < MAX_TILES) {
+                    g.tile_a[cnt] = (uint8_t)a;
+                    g.tile_c32[cnt] = (uint8_t)(c / 32);
+                    g.tile_w32[cnt] = (uint8_t)(N / 32);
+                    g.tile_kpre[cnt] = (uint16_t)k;
+                }
+                k += N / 32;
+                ++cnt;
+            }
+        }
+        if (cnt <= MAX_TILES) g.tile_kpre[cnt] = (uint16_t)k;
+        g.ktot = k;
+        if (zero_skipped) *zero_skipped = 0;
+        return cnt;
+    }
     for (int a = 0; a < g.tiles_m; ++a) {
         const int c0 = diagonal ? a * TILE_M : (a * TILE_M / N) * N;
         g.row_c0[a] = (uint16_t)c0;
+        g.row_t0[a] = (uint8_t)cnt;
         for (int c = c0; c < twoL;) {
             const int rem = (int)round_up(twoL - c, 32);
             const int w = diagonal ? (rem < N ? rem : N) : N;
@@ -322,11 +353,12 @@ static int build_tiles(C3Geom& g, int L, int N, bool skip_zero_window, int* zero
 // are the least well conditioned, so the FP32-class paths take the shorter
 // FP32 sums below.
 static C3Geom make_geom(const hos_params* p, int G, bool skip_zero_window = false, int* zero_skipped = nullptr,
-                        bool batched = false) {
+                        bool batched = false, int sym = C3_SWAP) {
     C3Geom g;
     memset(&g, 0, sizeof(g));
     const int twoL = 2 * p->L;
     g.L = p->L;
+    g.sym = sym;
     int N = p->tile_n ? p->tile_n : next_pow2(twoL);
     if (N < 32) N = 32;
     if (N > 256) N = 256;
@@ -488,7 +520,16 @@ static hos_status make_plan(int op, const hos_params* p, int64_t n_total, int S_
     int G = contraction_ctas(p->precision);
     P.zero_tiles = 0;
     const bool windowed = (op == HOS_OP_BISPECTRUM || op == HOS_OP_BISPECTRUM_BATCHED);
-    P.g = make_geom(p, G, windowed && p->window == HOS_WIN_PARZEN_SYM, &P.zero_tiles, op == HOS_OP_BISPECTRUM_BATCHED);
+    // The windowed spectra of whole series or parts compute the six-fold
+    // fundamental set (a third fewer MMAs at L = 256, half at L = 128); the raw
+    // cumulant (every lag of the square, w = -L included) and time slices
+    // (whose partial sums keep only the swap symmetry) the swap plan.
+    // HOS_TILE_SCHEME=swap (or =diagonal) selects the swap plan for measurement.
+    int sym = C3_SWAP;
+    const char* scheme = std::getenv("HOS_TILE_SCHEME");
+    if (windowed && !scheme) sym = (p->window == HOS_WIN_PARZEN_SYM) ? C3_SIX_BAND : C3_SIX;
+    P.g = make_geom(p, G, windowed && sym == C3_SWAP && p->window == HOS_WIN_PARZEN_SYM, &P.zero_tiles,
+                    op == HOS_OP_BISPECTRUM_BATCHED, sym);
     if (U_known >= 0) {
         const int64_t U = U_known * P.g.ntiles;
         if (U < G) P.g.G = (int)(U > 0 ? U : 1);
@@ -649,7 +690,13 @@ static hos_status run_c3(int op, const void* x, int dtype, int64_t n, const int6
     rp.c3out = c3_out;
     rp.norm_len = sl ? sl->n_total : 0;
     const int groups = rp.per_series_groups ? S : 1;
-    if (red_mode == 0 && (P.Nf > 2 * p->L || P.zero_tiles > 0))
+    rp.tiles_out = partials;
+    rp.n_slots = debug_slots(l.slots);
+    rp.grid_floats = (red_mode == 0) ? (int64_t)groups * P.Nf * P.Nf : 0;
+    rp.status = status;
+    // grid entries no computed lag writes (lags past L when Nf > 2L, skipped
+    // tiles) are zeroed first; the six-fold plans write every entry
+    if (red_mode == 0 && g.sym == C3_SWAP && (P.Nf > 2 * p->L || P.zero_tiles > 0))
         HOS_CUDA_TRY(launch_zero_f32(grid_out, (int64_t)groups * P.Nf * P.Nf, st));
     HOS_CUDA_TRY(launch_reduce3(rp, groups, P.max_len, at<int64_t>(ws, l.bnd), at<TileRec>(ws, l.xr),
                                 at<float2>(ws, l.ilen), at<float>(ws, l.wtab), st));
@@ -1694,6 +1741,56 @@ hos_status hos_check_plan(int32_t op, int64_t n_total, int32_t n_series, const i
         }
     for (size_t q = 0; q < read.size(); ++q)
         if (read[q] != 1) return fail("part %lld read %lld times by the reduction", (long long)q, read[q], 0);
+    if (order == 3) {
+        // every lag pair of the square gets its value from exactly one computed
+        // element: under the swap plan itself or its mirror (the reduction's rule),
+        // under the six-fold plans its one image in the fundamental set
+        const int L = g.L;
+        // computed elements by (row w1 + L, column w2 + L)
+        const int nr = TILE_M * g.tiles_m;
+        int nc = 0;
+        for (int t = 0; t < g.ntiles; ++t)
+            if (32 * (g.tile_c32[t] + g.tile_w32[t]) > nc) nc = 32 * (g.tile_c32[t] + g.tile_w32[t]);
+        std::vector<uint8_t> cov((size_t)nr * nc, 0);
+        for (int t = 0; t < g.ntiles; ++t)
+            for (int r = TILE_M * g.tile_a[t]; r < TILE_M * (g.tile_a[t] + 1); ++r)
+                for (int c = 32 * g.tile_c32[t]; c < 32 * (g.tile_c32[t] + g.tile_w32[t]); ++c)
+                    cov[(size_t)r * nc + c] = 1;
+        auto computed = [&](int w1, int w2) {
+            const int r = w1 + L, c = w2 + L;
+            return r >= 0 && r < nr && c >= 0 && c < nc && cov[(size_t)r * nc + c] != 0;
+        };
+        for (int w1 = -L; w1 < L; ++w1)
+            for (int w2 = -L; w2 < L; ++w2) {
+                int src = 0;
+                if (g.sym == C3_SWAP) {
+                    if (computed(w1, w2)) ++src;
+                    else if (w2 + L < (int)g.row_c0[(w1 + L) / TILE_M] && computed(w2, w1)) ++src;
+                    // a tile the band window weights by zero is left out (the grid is zeroed)
+                    if (src == 0 && p->window == HOS_WIN_PARZEN_SYM &&
+                        lag_window2(w1, w2, L, HOS_WIN_PARZEN_SYM) == 0.0)
+                        continue;
+                } else {
+                    if (w1 == -L || w2 == -L) continue;  // zero weight: the edge the reduction zeroes
+                    int o1[6], o2[6];
+                    c3_orbit(w1, w2, o1, o2);
+                    int reps = 0;
+                    for (int k2 = 0; k2 < 6; ++k2) {
+                        bool dup = false;  // an image met before (the orbit repeats on three lines)
+                        for (int j = 0; j < k2; ++j) dup = dup || (o1[j] == o1[k2] && o2[j] == o2[k2]);
+                        if (dup || !c3_fundamental(L, C3_SIX, o1[k2], o2[k2])) continue;
+                        ++reps;
+                        if (c3_fundamental(L, g.sym, o1[k2], o2[k2]) && computed(o1[k2], o2[k2])) ++src;
+                    }
+                    if (reps != 1) return fail("lag (%lld, %lld): %lld images in the fundamental set", w1, w2, reps);
+                    if (g.sym == C3_SIX_BAND && src == 0) {
+                        // weighted by zero: |w1 - w2|, |w1| or |w2| reaches L on its image
+                        if (lag_window2(w1, w2, L, HOS_WIN_PARZEN_SYM) == 0.0) continue;
+                    }
+                }
+                if (src != 1) return fail("lag (%lld, %lld) of the square has %lld sources", w1, w2, src);
+            }
+    }
     if (msg && msg_len)
         snprintf(msg, msg_len, "ok: %d series, %d tiles (cost %d per chunk), %d CTAs, %lld parts", S, g.ntiles,
                  g.ktot, g.G, (long long)part_st.size());

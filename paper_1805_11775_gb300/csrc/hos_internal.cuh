@@ -53,7 +53,10 @@ struct C3Geom {
     int flush;      // chunks per flush window
     int G;          // CTAs of the contraction
     int pad_tail;   // zero samples after the last chunk of a series
+    int sym;        // lag set: 0 rows w1 in [-L, L) with the swap (w2, w1) (C3_SWAP);
+                    // 1 or 2 the six-fold fundamental set (C3_SIX, C3_SIX_BAND)
     uint16_t row_c0[MAX_TILES_M];    // first column (lag index) computed in row block a
+    uint8_t row_t0[MAX_TILES_M];     // first tile of row block a (its tiles are consecutive)
     uint8_t tile_a[MAX_TILES];       // row block of tile t
     uint8_t tile_c32[MAX_TILES];     // first column of tile t / 32
     uint8_t tile_w32[MAX_TILES];     // width of tile t / 32 (cost of one of its chunks)
@@ -448,5 +451,35 @@ HOS_HD double lag_window3(int w1, int w2, int w3, int L, int kind) {
 }
 // RECT excludes the row/column w = -L that the 2L-wide lag range carries.
 HOS_HD bool rect_excluded(int w, int L) { return w == -L; }
+
+// ---------------------------------------------------------------------------
+// Lag symmetry of the third-order sample cumulant.  With y zero outside the
+// series (or part), c3(w1, w2) = (1/n) sum_i y(i) y(i+w1) y(i+w2) is a sum over
+// every integer i, so c3(w1, w2) = c3(w2, w1) (swap the factors) and
+// c3(w1, w2) = c3(-w1, w2 - w1) (shift i by w1): six lag pairs per value.
+// A time slice's partial sum (i over the slice only) keeps the swap but not
+// the shift.
+// ---------------------------------------------------------------------------
+enum { C3_SWAP = 0, C3_SIX = 1, C3_SIX_BAND = 2 };
+
+// The six lag pairs with the value of c3(w1, w2) (some coincide on the lines
+// w1 = 0, w2 = 0 and w1 = w2).
+HOS_HD void c3_orbit(int w1, int w2, int (&o1)[6], int (&o2)[6]) {
+    o1[0] = w1;      o2[0] = w2;
+    o1[1] = w2;      o2[1] = w1;
+    o1[2] = -w1;     o2[2] = w2 - w1;
+    o1[3] = w2 - w1; o2[3] = -w1;
+    o1[4] = -w2;     o2[4] = w1 - w2;
+    o1[5] = w1 - w2; o2[5] = -w2;
+}
+
+// The fundamental set the six-fold plans compute: w1 in [0, L) and w2 in
+// [w1, w1 + L).  Every lag pair of (-L, L)^2 has exactly one of its six images
+// in it.  C3_SIX_BAND (a window that also vanishes for |w1 - w2| >= L, which
+// is constant on the six images) keeps only w2 < L: the other pairs' values
+// are weighted by zero wherever they land.
+HOS_HD bool c3_fundamental(int L, int sym, int w1, int w2) {
+    return w1 >= 0 && w1 < L && w2 >= w1 && w2 < (sym == C3_SIX_BAND ? L : w1 + L);
+}
 
 }  // namespace hos

@@ -91,6 +91,13 @@ struct Reduce3Params {
     float* grid;
     double* c3out;
     int64_t norm_len;  // > 0: divide by this length instead of each series' own (a time slice)
+    // six-fold plans: the reduced c3 of each (group, tile), written in place over the
+    // first window slot of the group's first part and unfolded onto the grid from there
+    float* tiles_out;
+    // bounds of the HOS_DEBUG_BOUNDS build's checks: partial slots, grid floats, status word
+    int64_t n_slots;
+    int64_t grid_floats;
+    int* status;
 };
 
 struct LineGeom {

@@ -180,10 +180,30 @@ HOS_DEV void combine_rows4(DF (&v)[4], int ei, int gi, int es, int gsplit, float
 // the raw values into the lag array; and their mirrors (w2, w1) when the tile
 // holding those lags is not computed (c3(w1,w2) = c3(w2,w1)).  Rows past the
 // last lag (w1 >= L) are padding.
+// Six-fold plans: the four reduced values go back, as FP32, over the same
+// elements of the result slot (res_slot: the first window slot of the group's
+// first part; -1 for an empty series, which the unfold writes as zero).  The
+// thread that writes an element is the only one that reads it.
+HOS_DEV void keep_c3x4(const Reduce3Params& P, int64_t res_slot, int elem0, const DF (&v)[4]) {
+    if (res_slot < 0) return;
+#ifdef HOS_DEBUG_BOUNDS
+    if (res_slot >= P.n_slots) {
+        record_status(P.status, HOS_ERR_DEVICE_FAULT);
+        return;
+    }
+#endif
+    float4* d = reinterpret_cast<float4*>(P.tiles_out + res_slot * (int64_t)(TILE_M * P.geom.tile_n) + elem0);
+    *d = make_float4(v[0].h + v[0].l, v[1].h + v[1].l, v[2].h + v[2].l, v[3].h + v[3].l);
+}
+
 HOS_DEV void emit_c3x4(const Reduce3Params& P, const float* __restrict__ wtab, int grp, int t, int elem0,
-                       const DF (&v)[4]) {
+                       const DF (&v)[4], int64_t res_slot) {
     const C3Geom& geo = P.geom;
     const int L = geo.L;
+    if (geo.sym != C3_SWAP) {
+        keep_c3x4(P, res_slot, elem0, v);
+        return;
+    }
     const int m0 = elem0 & (TILE_M - 1), j = elem0 >> 7;
     const int w10 = -L + TILE_M * geo.tile_a[t] + m0, w2 = -L + 32 * geo.tile_c32[t] + j;
     if (w10 >= L || w2 >= L) return;
@@ -284,7 +304,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS, BATCH >= 16 ? 2 : 3) reduce3_k
                 DF v[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) v[c] = df_mul(DF{xv[c], 0.0f}, DF{il.x, il.y});
-                emit_c3x4(P, wtab, grp, t, 4 * vi[k], v);
+                emit_c3x4(P, wtab, grp, t, 4 * vi[k], v, r.slot);
             }
             return;
         }
@@ -298,6 +318,12 @@ __global__ void __launch_bounds__(REDUCE_THREADS, BATCH >= 16 ? 2 : 3) reduce3_k
     for (int s = s0; s < s1; ++s) {
         const TileRec r = rec[(int64_t)s * geo.ntiles + t];
         if (r.nwin == 0) continue;  // empty series (uniform over the block)
+#ifdef HOS_DEBUG_BOUNDS
+        if (r.slot < 0 || r.slot + r.nwin > P.n_slots - geo.G || r.xlo < 0 || r.xhi > geo.G) {
+            if (threadIdx.x == 0) record_status(P.status, HOS_ERR_DEVICE_FAULT);
+            return;
+        }
+#endif
         const float2 il = inv_len[s];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
@@ -311,6 +337,9 @@ __global__ void __launch_bounds__(REDUCE_THREADS, BATCH >= 16 ? 2 : 3) reduce3_k
         ++cnt;
     }
     if (gi != 0) return;
+    // six-fold plans keep the result over the first window slot of the group's first part
+    const TileRec r0 = rec[(int64_t)s0 * geo.ntiles + t];
+    const int64_t res_slot = r0.nwin > 0 ? r0.slot : -1;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         if (vi[k] >= nvec) continue;
@@ -322,7 +351,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS, BATCH >= 16 ? 2 : 3) reduce3_k
                 c3[k][c] = DF{h, (float)(q - (double)h)};
             }
         }
-        emit_c3x4(P, wtab, grp, t, 4 * vi[k], c3[k]);
+        emit_c3x4(P, wtab, grp, t, 4 * vi[k], c3[k], res_slot);
     }
 }
 
@@ -370,6 +399,12 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce3_single_kernel(const Re
     const int tsz = TILE_M * geo.tile_n, nvec = TILE_M * 32 * geo.tile_w32[t] >> 2;
     const TileRec r = rec[(int64_t)grp * geo.ntiles + t];
     if (!(r.nwin == 1 && r.xlo >= r.xhi)) return;  // uniform over the block
+#ifdef HOS_DEBUG_BOUNDS
+    if (r.slot < 0 || r.slot >= P.n_slots) {
+        if (threadIdx.x == 0) record_status(P.status, HOS_ERR_DEVICE_FAULT);
+        return;
+    }
+#endif
     const float2 il = inv_len[grp];
     const float4* p4 = reinterpret_cast<const float4*>(P.partials + r.slot * (int64_t)tsz);
     int vi[NV];
@@ -386,7 +421,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce3_single_kernel(const Re
         DF v[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) v[c] = df_mul(DF{xv[c], 0.0f}, DF{il.x, il.y});
-        emit_c3x4(P, wtab, grp, t, 4 * vi[k], v);
+        emit_c3x4(P, wtab, grp, t, 4 * vi[k], v, r.slot);
     }
 }
 
@@ -446,6 +481,148 @@ __global__ void timeout_selftest_kernel(int* status, uint64_t limit_ns) {
     __syncthreads();
 }
 
+// Six-fold plans: every entry of each group's transform grid from the
+// reduced fundamental set.  The lag pair's image in the set (the sector of
+// (w1, w2) fixes which of the six it is), its tile and element, windowed and
+// scaled; entries past the lags (Nf > 2L) and the zero-weight lag -L get 0,
+// as do an empty series' and, under the band, the zero-weight orbits.
+// Writes are coalesced; the reads gather from the group's reduced tiles.
+// One block per grid row (lag w2) of one group; threads along the row.
+__global__ void __launch_bounds__(256) unfold_c3_kernel(const Reduce3Params P, const TileRec* __restrict__ rec,
+                                                        const float* __restrict__ wtab) {
+    const C3Geom& geo = P.geom;
+    const int L = geo.L, twoL = 2 * L, Nf = P.nfft;
+    const int k2 = blockIdx.x, grp = blockIdx.y;
+    __shared__ int64_t slot_s[MAX_TILES];  // result slot of each tile (-1: empty series)
+    for (int t = threadIdx.x; t < geo.ntiles; t += blockDim.x) {
+        const TileRec rr = rec[(int64_t)(P.per_series_groups ? grp : 0) * geo.ntiles + t];
+        slot_s[t] = rr.nwin > 0 ? rr.slot : -1;
+    }
+    __syncthreads();
+    float* row = P.grid + ((int64_t)grp * Nf + k2) * Nf;
+    // lag of an index: k < L -> k, k > Nf - L -> k - Nf; w = -L (zero weight) and
+    // the indices between (Nf > 2L) hold no lag
+    const bool in2 = k2 < L || k2 > Nf - L;
+    const int w2 = k2 < L ? k2 : k2 - Nf;
+    const float sw2 = in2 ? (float)P.scale * wtab[w2 + twoL] : 0.0f;
+    const size_t tsz = (size_t)TILE_M * geo.tile_n;
+    for (int k1 = threadIdx.x; k1 < Nf; k1 += blockDim.x) {
+        float out = 0.0f;
+        if (in2 && (k1 < L || k1 > Nf - L)) {
+            const int w1 = k1 < L ? k1 : k1 - Nf;
+            int b, a;  // the image (b, a) with 0 <= b <= a
+            if (w1 >= 0 && w2 >= 0) {
+                b = w1 < w2 ? w1 : w2;
+                a = w1 < w2 ? w2 : w1;
+            } else if (w2 >= 0) {  // w1 < 0
+                b = -w1;
+                a = w2 - w1;
+            } else if (w1 >= 0) {  // w2 < 0
+                b = -w2;
+                a = w1 - w2;
+            } else if (w2 >= w1) {  // both < 0
+                b = w2 - w1;
+                a = -w1;
+            } else {
+                b = w1 - w2;
+                a = -w2;
+            }
+            if (c3_fundamental(L, geo.sym, b, a)) {
+                const int r = b + L, blk = r >> 7, c = a + L;
+                const int t = geo.row_t0[blk] + (c - geo.row_c0[blk]) / geo.tile_n;
+                const int64_t sl = slot_s[t];
+                if (sl >= 0) {
+                    const float v = P.tiles_out[(size_t)sl * tsz + (size_t)(c - 32 * geo.tile_c32[t]) * TILE_M +
+                                                (r & (TILE_M - 1))];
+                    float wv = wtab[w1 + twoL] * sw2;
+                    if (P.window == HOS_WIN_PARZEN_SYM) wv *= wtab[w1 - w2 + twoL];
+                    out = v * wv;
+                }
+            }
+        }
+        row[k1] = out;
+    }
+}
+
+// The same unfold with one block per group, its reduced tiles staged in
+// shared memory first (coalesced 16-byte loads; rows at a pitch of 129 words,
+// so that a grid row's gathers from there fall on different banks in every
+// sector), for plans whose tiles fit: the many short series of a batch.
+constexpr int UNFOLD_PITCH = TILE_M + 1;
+__global__ void __launch_bounds__(1024) unfold_c3_smem_kernel(const Reduce3Params P, const TileRec* __restrict__ rec,
+                                                              const float* __restrict__ wtab) {
+    extern __shared__ float tl[];  // [tile][column][row], row pitch UNFOLD_PITCH
+    const C3Geom& geo = P.geom;
+    const int L = geo.L, twoL = 2 * L, Nf = P.nfft, N = geo.tile_n;
+    const int grp = blockIdx.x;
+    const size_t tsz = (size_t)TILE_M * N;
+    bool empty = false;
+    for (int t = 0; t < geo.ntiles; ++t) {
+        const TileRec rr = rec[(int64_t)(P.per_series_groups ? grp : 0) * geo.ntiles + t];
+        if (rr.nwin <= 0) {
+            empty = true;  // an empty series: every tile's record says so
+            break;
+        }
+        const float4* src = reinterpret_cast<const float4*>(P.tiles_out + (size_t)rr.slot * tsz);
+        float* dst = tl + (size_t)t * N * UNFOLD_PITCH;
+        for (int q = threadIdx.x; q < (int)(tsz / 4); q += blockDim.x) {
+            const float4 v = src[q];
+            const int col = (4 * q) / TILE_M, row = (4 * q) % TILE_M;
+            float* d = dst + col * UNFOLD_PITCH + row;
+            d[0] = v.x;
+            d[1] = v.y;
+            d[2] = v.z;
+            d[3] = v.w;
+        }
+    }
+    float* wt = tl + (size_t)geo.ntiles * N * UNFOLD_PITCH;  // the window table, 4L values
+    for (int i = threadIdx.x; i < 4 * L; i += blockDim.x) wt[i] = wtab[i];
+    __syncthreads();
+    float* out_g = P.grid + (int64_t)grp * Nf * Nf;
+    const float sc = (float)P.scale;
+    // a warp per grid row (lag w2), lanes along it
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int k2 = threadIdx.x >> 5; k2 < Nf; k2 += nw) {
+        const bool in2 = !empty && (k2 < L || k2 > Nf - L);
+        const int w2 = k2 < L ? k2 : k2 - Nf;
+        const float sw2 = in2 ? sc * wt[w2 + twoL] : 0.0f;
+        float* orow = out_g + (size_t)k2 * Nf;
+        for (int k1 = lane; k1 < Nf; k1 += 32) {
+            float out = 0.0f;
+            if (in2 && (k1 < L || k1 > Nf - L)) {
+                const int w1 = k1 < L ? k1 : k1 - Nf;
+                int b, a;  // the image (b, a) with 0 <= b <= a, as in unfold_c3_kernel
+                if (w1 >= 0 && w2 >= 0) {
+                    b = w1 < w2 ? w1 : w2;
+                    a = w1 < w2 ? w2 : w1;
+                } else if (w2 >= 0) {
+                    b = -w1;
+                    a = w2 - w1;
+                } else if (w1 >= 0) {
+                    b = -w2;
+                    a = w1 - w2;
+                } else if (w2 >= w1) {
+                    b = w2 - w1;
+                    a = -w1;
+                } else {
+                    b = w1 - w2;
+                    a = -w2;
+                }
+                if (c3_fundamental(L, geo.sym, b, a)) {
+                    const int r = b + L, blk = r >> 7, c = a + L;
+                    const int t = geo.row_t0[blk] + (c - geo.row_c0[blk]) / N;
+                    const float v =
+                        tl[((size_t)t * N + (c - 32 * geo.tile_c32[t])) * UNFOLD_PITCH + (r & (TILE_M - 1))];
+                    float wv = wt[w1 + twoL] * sw2;
+                    if (P.window == HOS_WIN_PARZEN_SYM) wv *= wt[w1 - w2 + twoL];
+                    out = v * wv;
+                }
+            }
+            orow[k1] = out;
+        }
+    }
+}
+
 cudaError_t launch_reduce3(const Reduce3Params& p, int groups, int64_t max_len, int64_t* bnd, TileRec* rec,
                            float2* inv_len, float* wtab, cudaStream_t st) {
     cudaError_t e = launch_part_index(p.geom, p.ser, bnd, rec, inv_len, p.norm_len, 3, st);
@@ -475,6 +652,17 @@ cudaError_t launch_reduce3(const Reduce3Params& p, int groups, int64_t max_len, 
             reduce3_kernel<1, 16><<<grid, REDUCE_THREADS, 0, st>>>(p, bnd, rec, inv_len, wtab, gsplit);
         else
             reduce3_kernel<1, 8><<<grid, REDUCE_THREADS, 0, st>>>(p, bnd, rec, inv_len, wtab, gsplit);
+    }
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess || p.geom.sym == C3_SWAP || p.mode != 0) return e;
+    const size_t smem = ((size_t)p.geom.ntiles * p.geom.tile_n * UNFOLD_PITCH + 4 * (size_t)p.geom.L) * sizeof(float);
+    if (smem <= 200 * 1024) {
+        e = cudaFuncSetAttribute(unfold_c3_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        unfold_c3_smem_kernel<<<(unsigned)groups, 1024, smem, st>>>(p, rec, wtab);
+    } else {
+        unfold_c3_kernel<<<dim3((unsigned)p.nfft, (unsigned)groups), 256, 0, st>>>(p, rec, wtab);
     }
     count_launch();
     return cudaGetLastError();

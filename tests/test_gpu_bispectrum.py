@@ -200,6 +200,19 @@ def test_batched_equals_single_calls(hos):
         assert normwise(Bb[s].cpu().numpy(), Bs.cpu().numpy().astype(np.complex128)) <= 2e-5
 
 
+def test_batched_many_series_reduction_matches_single_calls(hos):
+    """128 series and more take the reduction's many-group kernels (four
+    vectors per thread, one-window series in a kernel of their own): each
+    series' spectrum equals its single call's within the split-bf16 target."""
+    lens = hos_synth.intraday_lengths(160, 9)
+    vals, offs = hos_synth.student_t_returns(lens, 9)
+    xb = torch.from_numpy(vals).cuda()
+    Bb = hos.bispectrum_batched(xb, torch.from_numpy(offs), 128, precision="bf16").cpu().numpy()
+    for s in list(range(0, 160, 23)) + [159]:
+        Bs = hos.bispectrum(xb[offs[s]:offs[s + 1]].contiguous(), 128, precision="bf16").cpu().numpy()
+        assert normwise(Bb[s], Bs.astype(np.complex128)) <= 1e-4, s
+
+
 # ------------------------------------------------------------- long workload at full size
 @pytest.fixture(scope="module")
 def long_inputs():

@@ -1,10 +1,11 @@
 """Host mirror of the contraction plans (no GPU): hos_check_plan runs, on the
 CPU and with the code the kernels use, the series layout, every CTA's walk
 over the cost-weighted stream-K split, the slots the partial tiles go to, the
-reduction's reading of those slots, and the bounds and 16-byte alignment of
-every bulk copy.  A plan passes when every (series, tile, chunk) is run
-exactly once, every partial is read exactly once from its own (series, tile),
-and no copy leaves its series' zero-padded block."""
+reduction's reading of those slots, the bounds and 16-byte alignment of
+every bulk copy, and which computed element gives each lag pair of the square
+its value.  A plan passes when every (series, tile, chunk) is run exactly
+once, every partial is read exactly once from its own (series, tile), no copy
+leaves its series' zero-padded block, and every lag pair has one source."""
 import ctypes
 import os
 import shutil
@@ -54,11 +55,22 @@ def test_workload_plans(lib):
 
 
 def test_tile_schemes(lib, monkeypatch):
-    """L = 256.  Full width (default): each row block's 256-wide tiles start at
-    the multiple of 256 at or below its diagonal block, six tiles, cost 48
-    per chunk.  Diagonal start: row blocks of 512, 384, 256 and 128 columns,
-    four 256-wide and two 128-wide tiles, cost 40 (1280 columns / 32)."""
+    """L = 256.  Six-fold (default for the windowed spectra): rows w1 in
+    [0, L), each row block's columns from w1 to w1 + L - 1 in 256-wide tiles,
+    four tiles, cost 32 per chunk (L = 128: one tile).  Swap plan
+    (HOS_TILE_SCHEME=swap): each row block's 256-wide tiles start at the
+    multiple of 256 at or below its diagonal block, six tiles, cost 48.
+    Diagonal start: row blocks of 512, 384, 256 and 128 columns, four
+    256-wide and two 128-wide tiles, cost 40 (1280 columns / 32)."""
     from paper_1805_11775_gb300 import make_params
+    monkeypatch.delenv("HOS_TILE_SCHEME", raising=False)
+    rc, m = check(lib, OP_BISPECTRUM, 1 << 21, make_params(256), 152)
+    assert rc == 0 and "4 tiles (cost 32 per chunk)" in m, m
+    rc, m = check(lib, OP_BISPECTRUM, 1 << 18, make_params(128), 152)
+    assert rc == 0 and "1 tiles (cost 8 per chunk)" in m, m
+    rc, m = check(lib, OP_BISPECTRUM, 1 << 18, make_params(128, window="parzen_sym"), 152)
+    assert rc == 0 and "1 tiles (cost 8 per chunk)" in m, m
+    monkeypatch.setenv("HOS_TILE_SCHEME", "swap")
     rc, m = check(lib, OP_BISPECTRUM, 1 << 21, make_params(256), 152)
     assert rc == 0 and "6 tiles (cost 48 per chunk)" in m, m
     monkeypatch.setenv("HOS_TILE_SCHEME", "diagonal")
@@ -68,10 +80,31 @@ def test_tile_schemes(lib, monkeypatch):
     assert rc == 0 and "2 tiles (cost 12 per chunk)" in m, m
 
 
-@pytest.mark.parametrize("scheme", ["full", "diagonal"])
+def set_scheme(monkeypatch, scheme):
+    if scheme == "six":
+        monkeypatch.delenv("HOS_TILE_SCHEME", raising=False)
+    else:
+        monkeypatch.setenv("HOS_TILE_SCHEME", scheme)
+
+
+def test_fundamental_set_brute_force():
+    """The six-fold plans' reading: with y zero outside the series,
+    c3(w1, w2) = c3(w2, w1) = c3(-w1, w2 - w1), and every lag pair of
+    (-L, L)^2 has exactly one image in {0 <= w1 < L, w1 <= w2 < w1 + L}.
+    Counted here by brute force over the six images, independently of the
+    library."""
+    for L in (1, 2, 3, 5, 8, 13):
+        for w1 in range(-L + 1, L):
+            for w2 in range(-L + 1, L):
+                imgs = {(w1, w2), (w2, w1), (-w1, w2 - w1), (w2 - w1, -w1), (-w2, w1 - w2), (w1 - w2, -w2)}
+                reps = [(a, b) for a, b in imgs if 0 <= a < L and a <= b < a + L]
+                assert len(reps) == 1, (L, w1, w2, reps)
+
+
+@pytest.mark.parametrize("scheme", ["six", "swap", "diagonal"])
 def test_random_single_series_plans(lib, monkeypatch, scheme):
     from paper_1805_11775_gb300 import make_params
-    monkeypatch.setenv("HOS_TILE_SCHEME", scheme)
+    set_scheme(monkeypatch, scheme)
     rng = np.random.default_rng(7)
     for _ in range(300):
         L = int(rng.choice([1, 2, 3, 5, 16, 31, 32, 40, 64, 100, 127, 128, 129, 200, 256, 300, 512, 700, 1024]))
@@ -89,10 +122,10 @@ def test_random_single_series_plans(lib, monkeypatch, scheme):
         assert rc == 0, (L, n, prec, tile, flush, win, seg, ctas, kc, m)
 
 
-@pytest.mark.parametrize("scheme", ["full", "diagonal"])
+@pytest.mark.parametrize("scheme", ["six", "swap", "diagonal"])
 def test_random_batched_plans(lib, monkeypatch, scheme):
     from paper_1805_11775_gb300 import make_params
-    monkeypatch.setenv("HOS_TILE_SCHEME", scheme)
+    set_scheme(monkeypatch, scheme)
     rng = np.random.default_rng(11)
     for _ in range(60):
         S = int(rng.integers(1, 300))
