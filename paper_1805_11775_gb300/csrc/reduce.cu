@@ -657,7 +657,8 @@ cudaError_t launch_reduce3(const Reduce3Params& p, int groups, int64_t max_len, 
     e = cudaGetLastError();
     if (e != cudaSuccess || p.geom.sym == C3_SWAP || p.mode != 0) return e;
     const size_t smem = ((size_t)p.geom.ntiles * p.geom.tile_n * UNFOLD_PITCH + 4 * (size_t)p.geom.L) * sizeof(float);
-    if (smem <= 200 * 1024) {
+    // the staged form takes one block (one SM) per group: for many groups only
+    if (smem <= 200 * 1024 && groups >= 256) {
         e = cudaFuncSetAttribute(unfold_c3_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         unfold_c3_smem_kernel<<<(unsigned)groups, 1024, smem, st>>>(p, rec, wtab);
