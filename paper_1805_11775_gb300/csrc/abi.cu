@@ -1783,6 +1783,11 @@ hos_status hos_check_plan(int32_t op, int64_t n_total, int32_t n_series, const i
                         if (c3_fundamental(L, g.sym, o1[k2], o2[k2]) && computed(o1[k2], o2[k2])) ++src;
                     }
                     if (reps != 1) return fail("lag (%lld, %lld): %lld images in the fundamental set", w1, w2, reps);
+                    // the unfold finds that image from the signs of the lags
+                    int sb, sa;
+                    c3_sector_image(w1, w2, sb, sa);
+                    if (!c3_fundamental(L, C3_SIX, sb, sa))
+                        return fail("lag (%lld, %lld): sector image (%lld, ...) outside the fundamental set", w1, w2, sb);
                     if (g.sym == C3_SIX_BAND && src == 0) {
                         // weighted by zero: |w1 - w2|, |w1| or |w2| reaches L on its image
                         if (lag_window2(w1, w2, L, HOS_WIN_PARZEN_SYM) == 0.0) continue;

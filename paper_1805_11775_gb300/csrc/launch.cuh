@@ -79,6 +79,29 @@ HOS_HD bool cta_slot_used(const TileRec& r, const int64_t* bnd, int g, int flush
     return c % flush != 0 && r.ub + c * r.k < bnd[g + 1];
 }
 
+// The image (b, a) of (w1, w2) with 0 <= b <= a: each sector of the lag
+// plane, told apart by the signs of w1, w2 and w2 - w1, maps to one of the
+// six images.  For (w1, w2) in (-L, L)^2 it is the pair's image in the
+// fundamental set.
+HOS_HD void c3_sector_image(int w1, int w2, int& b, int& a) {
+    if (w1 >= 0 && w2 >= 0) {
+        b = w1 < w2 ? w1 : w2;
+        a = w1 < w2 ? w2 : w1;
+    } else if (w2 >= 0) {  // w1 < 0
+        b = -w1;
+        a = w2 - w1;
+    } else if (w1 >= 0) {  // w2 < 0
+        b = -w2;
+        a = w1 - w2;
+    } else if (w2 >= w1) {  // both < 0
+        b = w2 - w1;
+        a = -w1;
+    } else {
+        b = w1 - w2;
+        a = -w2;
+    }
+}
+
 struct Reduce3Params {
     C3Geom geom;
     SeriesView ser;

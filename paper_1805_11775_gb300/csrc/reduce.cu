@@ -511,22 +511,7 @@ __global__ void __launch_bounds__(256) unfold_c3_kernel(const Reduce3Params P, c
         if (in2 && (k1 < L || k1 > Nf - L)) {
             const int w1 = k1 < L ? k1 : k1 - Nf;
             int b, a;  // the image (b, a) with 0 <= b <= a
-            if (w1 >= 0 && w2 >= 0) {
-                b = w1 < w2 ? w1 : w2;
-                a = w1 < w2 ? w2 : w1;
-            } else if (w2 >= 0) {  // w1 < 0
-                b = -w1;
-                a = w2 - w1;
-            } else if (w1 >= 0) {  // w2 < 0
-                b = -w2;
-                a = w1 - w2;
-            } else if (w2 >= w1) {  // both < 0
-                b = w2 - w1;
-                a = -w1;
-            } else {
-                b = w1 - w2;
-                a = -w2;
-            }
+            c3_sector_image(w1, w2, b, a);
             if (c3_fundamental(L, geo.sym, b, a)) {
                 const int r = b + L, blk = r >> 7, c = a + L;
                 const int t = geo.row_t0[blk] + (c - geo.row_c0[blk]) / geo.tile_n;
@@ -591,23 +576,8 @@ __global__ void __launch_bounds__(1024) unfold_c3_smem_kernel(const Reduce3Param
             float out = 0.0f;
             if (in2 && (k1 < L || k1 > Nf - L)) {
                 const int w1 = k1 < L ? k1 : k1 - Nf;
-                int b, a;  // the image (b, a) with 0 <= b <= a, as in unfold_c3_kernel
-                if (w1 >= 0 && w2 >= 0) {
-                    b = w1 < w2 ? w1 : w2;
-                    a = w1 < w2 ? w2 : w1;
-                } else if (w2 >= 0) {
-                    b = -w1;
-                    a = w2 - w1;
-                } else if (w1 >= 0) {
-                    b = -w2;
-                    a = w1 - w2;
-                } else if (w2 >= w1) {
-                    b = w2 - w1;
-                    a = -w1;
-                } else {
-                    b = w1 - w2;
-                    a = -w2;
-                }
+                int b, a;  // the image (b, a) with 0 <= b <= a
+                c3_sector_image(w1, w2, b, a);
                 if (c3_fundamental(L, geo.sym, b, a)) {
                     const int r = b + L, blk = r >> 7, c = a + L;
                     const int t = geo.row_t0[blk] + (c - geo.row_c0[blk]) / N;

@@ -91,7 +91,7 @@ def test_no_alloc_matches_workspace_entry_point_on_consecutive_calls(lib):
 def test_no_alloc_rejects_problems_beyond_its_fixed_scratch(lib):
     from paper_1805_11775_gb300 import make_params
     x = torch.zeros(1 << 21, dtype=torch.float64, device="cuda")
-    p = make_params(256, precision="bf16")  # needs ~133 MiB of scratch
+    p = make_params(256, precision="bf16")  # needs ~100 MiB of scratch
     out = torch.full((512, 512), 7.0, dtype=torch.complex64, device="cuda")
     st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     assert lib.hos_bispectrum_noalloc(x.data_ptr(), 1, x.numel(), ctypes.byref(p), out.data_ptr(), st) == 3
