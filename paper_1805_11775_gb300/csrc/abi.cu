@@ -1788,6 +1788,16 @@ hos_status hos_check_plan(int32_t op, int64_t n_total, int32_t n_series, const i
                     c3_sector_image(w1, w2, sb, sa);
                     if (!c3_fundamental(L, C3_SIX, sb, sa))
                         return fail("lag (%lld, %lld): sector image (%lld, ...) outside the fundamental set", w1, w2, sb);
+                    if (c3_fundamental(L, g.sym, sb, sa)) {
+                        // the unfold's tile of that image: its row block's first tile plus
+                        // whole tile widths from the block's first column
+                        const int r = sb + L, blk = r / TILE_M, c = sa + L;
+                        const int t = g.row_t0[blk] + (c - g.row_c0[blk]) / g.tile_n;
+                        if (t < 0 || t >= g.ntiles || g.tile_a[t] != blk || c < 32 * g.tile_c32[t] ||
+                            c >= 32 * (g.tile_c32[t] + g.tile_w32[t]))
+                            return fail("lag (%lld, %lld): the unfold looks in tile %lld, which does not hold it", w1,
+                                        w2, t);
+                    }
                     if (g.sym == C3_SIX_BAND && src == 0) {
                         // weighted by zero: |w1 - w2|, |w1| or |w2| reaches L on its image
                         if (lag_window2(w1, w2, L, HOS_WIN_PARZEN_SYM) == 0.0) continue;
