@@ -303,7 +303,9 @@ hos_status hos_cumulant3_slice(const void* d_x, int32_t dtype, int64_t n_slice, 
 /* The last steps of hos_bispectrum from a given c3 (hos_cumulant3's layout):
  * lag window, (2 pi)^-2, wrap onto the nfft grid, 2-D DFT into d_B (as
  * hos_bispectrum).  The window and scale use the same FP32 arithmetic as
- * hos_bispectrum, so c3 from hos_cumulant3 reproduces its output.
+ * hos_bispectrum's swap plan, so c3 from hos_cumulant3 reproduces its output
+ * bit for bit under HOS_TILE_SCHEME=swap, and within the precision's target
+ * under the default six-fold plan.
  * Workspace: hos_workspace_size(HOS_OP_BISPECTRUM_FROM_C3, 0, 1, 0, ...).   */
 hos_status hos_bispectrum_from_cumulant(const double* d_c3, const hos_params* params, void* d_B, void* ws,
                                         size_t ws_bytes, hos_stream_t stream);
