@@ -164,9 +164,11 @@ hos_status hos_workspace_size(int32_t op, int64_t n_total, int32_t n_series, int
  *   d_x : n samples (dtype float32 or float64)
  *   d_B : nfft*nfft complex64, row-major [k1][k2]
  * c3 of a zero-padded series (or part) takes one value at the six lag pairs
- * (w1, w2), (w2, w1), (-w1, w2 - w1) and their swaps; the contraction
- * computes one pair of each six (w1 in [0, L), w2 in [w1, w1 + L)) and the
- * grid takes every lag pair's value from it.  The result equals the window
+ * (w1, w2), (w2, w1), (-w1, w2 - w1) and their swaps; where that needs
+ * fewer tiles than the swap symmetry alone (L >= 128 with the default tile
+ * width), the contraction computes one pair of each six (w1 in [0, L), w2 in
+ * [w1, w1 + L)) and the grid takes every lag pair's value from it.  The
+ * result equals the window
  * and transform of hos_cumulant3's c3 (hos_bispectrum_from_cumulant) within
  * the precision's target; with the environment variable HOS_TILE_SCHEME=swap
  * both contract the same lag pairs and agree bit for bit.                  */

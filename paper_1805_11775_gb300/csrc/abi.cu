@@ -525,11 +525,20 @@ static hos_status make_plan(int op, const hos_params* p, int64_t n_total, int S_
     // cumulant (every lag of the square, w = -L included) and time slices
     // (whose partial sums keep only the swap symmetry) the swap plan.
     // HOS_TILE_SCHEME=swap (or =diagonal) selects the swap plan for measurement.
-    int sym = C3_SWAP;
+    // The six-fold plan is taken where it needs fewer tile columns than the
+    // swap plan (its rows start at a 32-column boundary, so at small L it can
+    // need more; on a tie the swap plan saves the unfold pass).
     const char* scheme = std::getenv("HOS_TILE_SCHEME");
-    if (windowed && !scheme) sym = (p->window == HOS_WIN_PARZEN_SYM) ? C3_SIX_BAND : C3_SIX;
-    P.g = make_geom(p, G, windowed && sym == C3_SWAP && p->window == HOS_WIN_PARZEN_SYM, &P.zero_tiles,
-                    op == HOS_OP_BISPECTRUM_BATCHED, sym);
+    const bool band = p->window == HOS_WIN_PARZEN_SYM;
+    P.g = make_geom(p, G, windowed && band, &P.zero_tiles, op == HOS_OP_BISPECTRUM_BATCHED, C3_SWAP);
+    if (windowed && !scheme) {
+        const C3Geom six = make_geom(p, G, false, nullptr, op == HOS_OP_BISPECTRUM_BATCHED,
+                                     band ? C3_SIX_BAND : C3_SIX);
+        if (six.ktot < P.g.ktot) {
+            P.g = six;
+            P.zero_tiles = 0;
+        }
+    }
     if (U_known >= 0) {
         const int64_t U = U_known * P.g.ntiles;
         if (U < G) P.g.G = (int)(U > 0 ? U : 1);
